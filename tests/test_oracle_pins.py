@@ -1,0 +1,327 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (CPU only)."""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import bcrown_oracle as O
+from oracle import lp_pins as LP
+from paper_2103_06624_gb300 import workloads as wl
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _setup(pb):
+    net = O.OracleNet(pb.layers, pb.C)
+    l, u = O.root_bounds(net, pb.x_lo, pb.x_hi)
+    unst = [np.nonzero(O.unstable_mask(l[p], u[p]))[0] for p in range(pb.P)]
+    props = dict(x_lo=pb.x_lo, x_hi=pb.x_hi, l=l, u=u)
+    return net, props, unst
+
+
+def tiny_problem(seed=5, widths=(3, 6, 6, 3), eps=0.3, K=2):
+    layers = wl.mlp_layers(list(widths), seed)
+    return wl.make_problem("tiny", layers, 1, eps, K, seed)
+
+
+def tiny_conv_problem(seed=3):
+    layers = wl.conv_layers((2, 6, 6), [(3, 3, 2, 1), (4, 3, 1, 1)], [8, 4], seed)
+    return wl.make_problem("tinyconv", layers, 2, 0.1, 3, seed)
+
+
+# ------------------------------------------------------------------ golden worked example
+
+def test_golden_intro_example():
+    g = json.load(open(os.path.join(GOLD, "intro_2d_example.json")))
+    nw = g["network"]
+    layers = [wl.Layer("fc", np.array(nw["W1"], np.float32), np.array(nw["b1"], np.float32), (2,), (2,)),
+              wl.Layer("fc", np.array(nw["W2"], np.float32), np.array(nw["b2"], np.float32), (2,), (1,))]
+    C = np.ones((1, 1), np.float32)
+    net = O.OracleNet(layers, C)
+    x_lo = np.array([g["box"]["x_lo"]])
+    x_hi = np.array([g["box"]["x_hi"]])
+    l, u = O.root_bounds(net, x_lo, x_hi)
+    assert np.allclose(l[0], g["root_bounds_printed_in_paper"]["l"])
+    assert np.allclose(u[0], g["root_bounds_printed_in_paper"]["u"])
+    props = dict(x_lo=x_lo, x_hi=x_hi, l=l, u=u)
+    for case in g["cases"]:
+        s = case["split"]
+        subs = [(0, np.array([1] if s else [], np.int64), np.array([s] if s else [], np.int8))]
+        batch = wl.pack_batch([2], 1, [2], subs)
+        alpha = np.array([case["alpha1"], 0.5])          # neuron 2's alpha is unused
+        beta = np.array([case["beta2"]] if s else [])
+        lb = O.bound(net, props, batch, alpha, beta)
+        assert lb[0] == pytest.approx(case["lb"], abs=1e-12), case
+        ex = LP.exact_min(net, x_lo[0], x_hi[0], l[0], u[0], [(1, 1, s)] if s else [], 0)
+        assert ex == pytest.approx(g["exact_min"][str(s)], abs=1e-9)
+        assert lb[0] <= ex + 1e-12
+
+
+# ------------------------------------------------------------------ three formulas agree
+
+@pytest.mark.parametrize("maker", [tiny_problem, tiny_conv_problem, wl.problem_mlp_small])
+def test_recursion_explicit_dual_agree(maker):
+    pb = maker()
+    net, props, unst = _setup(pb)
+    batch = wl.random_batch(pb, unst, 6, 0, 4, 11)
+    a, b = wl.random_alpha_beta(batch, 2, 3.0)
+    lb = O.bound(net, props, batch, a, b)
+    lbe = O.bound_explicit(net, props, batch, a, b)
+    lbd = O.bound_dual(net, props, batch, a, b)
+    scale = 1.0 + np.abs(lb)
+    assert np.max(np.abs(lb - lbe) / scale) < 1e-12
+    assert np.max(np.abs(lb - lbd) / scale) < 1e-12
+
+
+def test_beta_zero_no_split_is_crown():
+    """beta = 0 with splits present equals CROWN on the split-free net with the same D (Section 3.1):
+    with no split at all, the dual form reduces to Wong & Kolter's / CROWN's."""
+    pb = wl.problem_mlp_small()
+    net, props, unst = _setup(pb)
+    batch = wl.random_batch(pb, unst, 4, 0, 0, 1)
+    a, b = wl.random_alpha_beta(batch, 3)
+    assert batch.n_beta == 0
+    lb = O.bound(net, props, batch, a, b)
+    lbd = O.bound_dual(net, props, batch, a, b)
+    assert np.allclose(lb, lbd, rtol=0, atol=1e-12)
+
+
+def test_eps_zero_closed_form():
+    """At eps = 0 every neuron is stable and the bound is c_k^T f(x0) exactly."""
+    pb = wl.problem_mlp_small(seed=4)
+    pb.x_lo = pb.x0.copy()
+    pb.x_hi = pb.x0.copy()
+    net, props, unst = _setup(pb)
+    assert all(len(u) == 0 for u in unst)
+    batch = wl.random_batch(pb, unst, 2, 0, 0, 0)
+    lb = O.bound(net, props, batch, np.zeros(0), np.zeros(0))
+    f = net.forward(pb.x0[0].astype(np.float64))[0]
+    assert np.allclose(lb.reshape(2, -1), f[None, :], rtol=0, atol=1e-12)
+
+
+def test_linear_net_vertex_bruteforce():
+    """With no unstable neuron the bound is the exact minimum over the box's vertices."""
+    layers = wl.mlp_layers([5, 7, 7, 3], 9)
+    for ly in layers[:-1]:
+        ly.b = ly.b + np.float32(8.0)       # every neuron active on the box
+    pb = wl.make_problem("lin", layers, 1, 0.2, 2, 9)
+    net, props, unst = _setup(pb)
+    assert all(len(u) == 0 for u in unst)
+    batch = wl.random_batch(pb, unst, 1, 0, 0, 0)
+    lb = O.bound(net, props, batch, np.zeros(0), np.zeros(0))
+    verts = np.array(list(itertools.product([0, 1], repeat=5)), np.float64)
+    xs = pb.x_lo[0].astype(np.float64) + verts * (pb.x_hi[0].astype(np.float64) - pb.x_lo[0])
+    f = net.forward(xs)
+    assert np.allclose(lb, f.min(axis=0), rtol=0, atol=1e-12)
+
+
+# ------------------------------------------------------------------ soundness, LP, completeness
+
+def test_soundness_against_samples():
+    pb = wl.problem_mlp_small(seed=1)
+    net, props, unst = _setup(pb)
+    batch = wl.random_batch(pb, unst, 12, 0, 4, 5)
+    rng = np.random.default_rng(0)
+    for trial in range(3):
+        a, b = wl.random_alpha_beta(batch, 10 + trial, 10.0)
+        lb = O.bound(net, props, batch, a, b)
+        for bi in range(batch.B):
+            o, c = batch.split_off[bi], batch.split_cnt[bi]
+            splits = list(zip(batch.split_layer[o:o + c], batch.split_idx[o:o + c], batch.split_sign[o:o + c]))
+            for k in range(pb.K):
+                m, n = LP.sampled_min(net, pb.x_lo[0].astype(float), pb.x_hi[0].astype(float), splits, k,
+                                      20000, rng)
+                assert lb[bi * pb.K + k] <= m + 1e-9
+
+
+def test_lp_corollary():
+    """g(alpha, beta) <= p*_LP for any feasible alpha, beta; optimised g reaches p*_LP (Corollary 3.1)."""
+    pb = tiny_problem()
+    net, props, unst = _setup(pb)
+    batch = wl.random_batch(pb, unst, 6, 0, 3, 0)
+    a, b = wl.random_alpha_beta(batch, 1, 2.0)
+    lb = O.bound(net, props, batch, a, b)
+    cfg = O.AdamCfg(iters=600, lr_alpha=0.05, lr_beta=0.05, decay=0.995)
+    a0, b0 = wl.initial_alpha_beta(batch)
+    lbo, _, _, _ = O.optimize(net, props, batch, a0, b0, cfg)
+    for bi in range(batch.B):
+        o, c = batch.split_off[bi], batch.split_cnt[bi]
+        splits = list(zip(batch.split_layer[o:o + c], batch.split_idx[o:o + c], batch.split_sign[o:o + c]))
+        for k in range(pb.K):
+            r = bi * pb.K + k
+            p = LP.lp_value(net, pb.x_lo[0].astype(float), pb.x_hi[0].astype(float),
+                            props["l"][0], props["u"][0], splits, k)
+            assert lb[r] <= p + 1e-8
+            assert lbo[r] <= p + 1e-8
+            assert p - lbo[r] <= 2e-3 * abs(p) + 1e-5
+
+
+def test_completeness_full_split():
+    """All unstable neurons split: optimised beta reaches the exact per-pattern minimum (Theorem 3.3)."""
+    pb = tiny_problem(seed=5)
+    net, props, unst = _setup(pb)
+    U = len(unst[0])
+    rng = np.random.default_rng(2)
+    subs = []
+    H = int(sum(pb.hidden_widths))
+    for _ in range(4):
+        # signs read off the activation pattern at a random box point, so the subdomain is feasible
+        x = rng.uniform(pb.x_lo[0].astype(np.float64), pb.x_hi[0].astype(np.float64))
+        z = np.concatenate([zi[0] for zi in net.preacts(x)[1:]])
+        assert z.shape[0] == H
+        signs = np.where(z[unst[0]] >= 0, -1, 1).astype(np.int8)
+        subs.append((0, unst[0].astype(np.int64), signs))
+    batch = wl.pack_batch(pb.hidden_widths, pb.K, [U], subs)
+    a0, b0 = wl.initial_alpha_beta(batch)
+    cfg = O.AdamCfg(iters=3000, lr_alpha=0.0, lr_beta=0.05, decay=0.999)
+    lbo, _, _, _ = O.optimize(net, props, batch, a0, b0, cfg)
+    n_checked = 0
+    for bi in range(batch.B):
+        o, c = batch.split_off[bi], batch.split_cnt[bi]
+        splits = list(zip(batch.split_layer[o:o + c], batch.split_idx[o:o + c], batch.split_sign[o:o + c]))
+        for k in range(pb.K):
+            ex = LP.exact_min(net, pb.x_lo[0].astype(float), pb.x_hi[0].astype(float),
+                              props["l"][0], props["u"][0], splits, k)
+            r = bi * pb.K + k
+            if np.isfinite(ex):
+                assert lbo[r] <= ex + 1e-9
+                assert ex - lbo[r] <= 1e-4 * (1 + abs(ex))
+                n_checked += 1
+    assert n_checked > 0
+
+
+# ------------------------------------------------------------------ gradient
+
+@pytest.mark.parametrize("maker", [wl.problem_mlp_small, tiny_conv_problem])
+def test_gradient_finite_differences(maker):
+    pb = maker()
+    net, props, unst = _setup(pb)
+    batch = wl.random_batch(pb, unst, 4, 1, 4, 3)
+    a, b = wl.random_alpha_beta(batch, 4, 2.0)
+    a, b = a.astype(np.float64), b.astype(np.float64)
+    _, da, db = O.grad(net, props, batch, a, b)
+    h = 1e-6
+    rng = np.random.default_rng(0)
+    for vec, g in ((a, da), (b, db)):
+        for idx in rng.choice(len(vec), min(12, len(vec)), replace=False):
+            p, m = vec.copy(), vec.copy()
+            p[idx] += h
+            m[idx] -= h
+            args_p = (p, b) if vec is a else (a, p)
+            args_m = (m, b) if vec is a else (a, m)
+            fp = O.bound(net, props, batch, *args_p).sum()
+            fm = O.bound(net, props, batch, *args_m).sum()
+            fd = (fp - fm) / (2 * h)
+            assert abs(fd - g[idx]) <= 1e-6 * (1 + abs(fd)), (idx, fd, g[idx])
+
+
+# ------------------------------------------------------------------ root bounds
+
+def test_root_bounds_layer1_exact_and_sound():
+    pb = tiny_problem(widths=(4, 6, 5, 2), eps=0.4)
+    net, props, _ = _setup(pb)
+    l, u = props["l"][0], props["u"][0]
+    verts = np.array(list(itertools.product([0, 1], repeat=4)), np.float64)
+    xs = pb.x_lo[0].astype(np.float64) + verts * (pb.x_hi[0].astype(np.float64) - pb.x_lo[0])
+    z1 = net.preacts(xs)[1]
+    assert np.allclose(l[:6], z1.min(axis=0), atol=1e-12)
+    assert np.allclose(u[:6], z1.max(axis=0), atol=1e-12)
+    rng = np.random.default_rng(1)
+    xs = rng.uniform(pb.x_lo[0], pb.x_hi[0], size=(50000, 4))
+    zs = net.preacts(xs)
+    for i in range(1, net.L):
+        lo, hi = net.hoff[i - 1], net.hoff[i]
+        assert np.all(zs[i] >= l[lo:hi] - 1e-12)
+        assert np.all(zs[i] <= u[lo:hi] + 1e-12)
+
+
+# ------------------------------------------------------------------ library-routine pins
+
+def test_conv_matrix_matches_torch_conv2d():
+    torch = pytest.importorskip("torch")
+    import torch.nn.functional as F
+    pb = tiny_conv_problem()
+    rng = np.random.default_rng(0)
+    for ly in pb.layers:
+        if ly.kind != "conv":
+            continue
+        M = O.conv_matrix(ly)
+        x = rng.normal(size=ly.in_shape)
+        ref = F.conv2d(torch.tensor(x)[None], torch.tensor(ly.W.astype(np.float64)), None,
+                       stride=ly.stride, padding=ly.pad)[0].numpy().ravel()
+        assert np.allclose(M @ x.ravel(), ref, atol=1e-12)
+
+
+def test_adam_step_matches_torch():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(0)
+    theta = rng.uniform(0, 1, 50)
+    cfg = O.AdamCfg()
+    p = torch.tensor(theta.copy(), requires_grad=True)
+    opt = torch.optim.Adam([p], lr=cfg.lr_alpha, betas=(cfg.beta1, cfg.beta2), eps=cfg.eps, maximize=True)
+    sched = torch.optim.lr_scheduler.ExponentialLR(opt, cfg.decay)
+    th, m, v = theta.copy(), np.zeros(50), np.zeros(50)
+    for t in range(5):
+        g = rng.normal(size=50)
+        p.grad = torch.tensor(g)
+        opt.step()
+        sched.step()
+        th, m, v = O.adam_ascent_step(th, m, v, g, t, cfg.lr_alpha * cfg.decay ** t, cfg, -np.inf, np.inf)
+        assert np.allclose(th, p.detach().numpy(), atol=1e-12)
+
+
+def test_batch_split_definition():
+    pb = wl.problem_mlp_small()
+    net, props, unst = _setup(pb)
+    batch = wl.random_batch(pb, unst, 3, 1, 2, 0)
+    _, U = O.unstable_ranks(net, props["l"], props["u"])
+    a, b = wl.random_alpha_beta(batch, 0)
+    pick_layer = np.array([1, 2, 1])
+    pick_idx = np.array([3, 5, 7])
+    out = O.batch_split(batch, pb.K, U, pick_layer, pick_idx, a, b)
+    prop, off, cnt, lay, idx, sgn, aoff, a2, b2 = out
+    assert len(prop) == 6
+    for c in range(6):
+        par = c // 2
+        po, pc = batch.split_off[par], batch.split_cnt[par]
+        assert cnt[c] == pc + 1
+        assert list(lay[off[c]:off[c] + pc]) == list(batch.split_layer[po:po + pc])
+        assert lay[off[c] + pc] == pick_layer[par] and idx[off[c] + pc] == pick_idx[par]
+        assert sgn[off[c] + pc] == (-1 if c % 2 == 0 else 1)
+        n = U[0] * pb.K
+        assert np.array_equal(a2[aoff[c]:aoff[c] + n], a[batch.alpha_off[par]:batch.alpha_off[par] + n])
+        for k in range(pb.K):
+            blk = b2[off[c] * pb.K + k * cnt[c]: off[c] * pb.K + (k + 1) * cnt[c]]
+            assert np.array_equal(blk[:-1], b[po * pb.K + k * pc: po * pb.K + (k + 1) * pc])
+            assert blk[-1] == 0.0
+
+
+# ------------------------------------------------------------------ planted mistakes are caught
+
+def test_planted_mistakes_fail_a_pin(monkeypatch):
+    """Each plausible slip in the recursion breaks agreement with the dual form or FD."""
+    pb = wl.problem_mlp_small()
+    net, props, unst = _setup(pb)
+    batch = wl.random_batch(pb, unst, 6, 1, 4, 2)
+    a, b = wl.random_alpha_beta(batch, 5, 2.0)
+    ref = O.bound_dual(net, props, batch, a, b)
+    good_relax = O.relax
+
+    def drop_intercept(A, li, ui, al, sign):
+        D, lam = good_relax(A, li, ui, al, sign)
+        return D, lam * 0.0
+
+    def wrong_branch(A, li, ui, al, sign):
+        return good_relax(-A, li, ui, al, sign)
+
+    for bad in (drop_intercept, wrong_branch):
+        monkeypatch.setattr(O, "relax", bad)
+        lb = O.bound(net, props, batch, a, b)
+        monkeypatch.setattr(O, "relax", good_relax)
+        assert np.max(np.abs(lb - ref)) > 1e-6, bad.__name__
+    # a flipped split sign is caught by the sampled-minimum soundness pin or the dual form
+    sb = wl.Batch(**{**batch.__dict__, "split_sign": (-batch.split_sign).astype(np.int8)})
+    lb_flip = O.bound(net, props, sb, a, b)
+    assert np.max(np.abs(lb_flip - ref)) > 1e-6
