@@ -1,0 +1,371 @@
+"""Throughput of batched beta-CROWN subdomain bounding on one or more GB300s.
+
+One step = one call of bcrown_optimize on a batch of subdomains: 20 projected-
+Adam iterations on alpha, beta (each a bound pass plus its adjoint) and the
+final certifying pass.  Workload (default): the ReLU MLP 784-256x6-10 (He
+init, seeded), x0 ~ U[0,1]^784, eps = 0.015, 9 margin specs, 1024 subdomains
+that are the leaves of a random branch-and-bound tree of depth <= 12.
+
+Prints one JSON line (rank 0).  Under torchrun each rank bounds its own batch
+(weak scaling, no collective on the data path); the barrier and the maximum
+over ranks are for timing only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "subdomain lower bounds/sec (20 alpha,beta iters)"
+UNIT = "subdomains/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
+    ap.add_argument("--subdomains", type=int, default=1024)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=192, help="subdomains timed on the oracle (about 10-20 s)")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------ workload
+
+def build_workload(seed, n_sub, torch, bc, wl):
+    pb = wl.problem_mlp_784(seed=seed)
+    net = bc.load_net(pb.layers, pb.C)
+    x_lo = torch.as_tensor(pb.x_lo).cuda()
+    x_hi = torch.as_tensor(pb.x_hi).cuda()
+    l, u, cnt = bc.root_bounds(net, x_lo, x_hi, bc.ALPHA_ADAPTIVE, 0.5, bc.CERTIFY)
+    l_h, u_h = l.cpu().numpy(), u.cpu().numpy()
+    unst = [np.nonzero((l_h[p] < 0) & (u_h[p] > 0))[0] for p in range(pb.P)]
+    batch = wl.tree_batch(pb, unst, [n_sub], 12, seed + 1)
+    dom = bc.Domain(x_lo, x_hi, l, u)
+    return pb, net, dom, batch, unst, (l_h, u_h)
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_flops_per_row_pass(widths):
+    """FLOPs of one backward pass of one row: sum over layers i = 1..L-1 of 2 d_i d_{i-1}."""
+    return sum(2 * widths[i] * widths[i - 1] for i in range(1, len(widths) - 1))
+
+
+def fp32_simt_peak_tflops(sm_mhz):
+    """152 SMs x 128 FP32 lanes x 2 flop per FMA x clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+# ------------------------------------------------------------------------------ oracle leg
+
+def cpu_oracle_rate(pb, lu, batch_full, n_sample, seed=0):
+    """The FP64 oracle's optimise (20 iters + final bound) on a bounded sample of subdomains."""
+    from oracle import bcrown_oracle as O
+    from paper_2103_06624_gb300 import workloads as wl
+    l_h, u_h = lu
+    onet = O.OracleNet(pb.layers, pb.C)
+    props = dict(x_lo=pb.x_lo, x_hi=pb.x_hi, l=l_h, u=u_h)
+    _, U = O.unstable_ranks(onet, l_h, u_h)
+    idx = np.arange(min(n_sample, batch_full.B))
+    offs = np.concatenate([[0], np.cumsum(pb.hidden_widths)])
+    subs = []
+    for b in idx:
+        o, c = int(batch_full.split_off[b]), int(batch_full.split_cnt[b])
+        g = offs[batch_full.split_layer[o:o + c].astype(np.int64) - 1] + batch_full.split_idx[o:o + c]
+        subs.append((int(batch_full.prop_of[b]), g.astype(np.int64), batch_full.split_sign[o:o + c]))
+    sb = wl.pack_batch(pb.hidden_widths, pb.K, U, subs)
+    a0, b0 = wl.initial_alpha_beta(sb)
+    t0 = time.perf_counter()
+    O.optimize(onet, props, sb, a0, b0)
+    dt = time.perf_counter() - t0
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count()
+    return len(idx) / dt, cores, f"{len(idx)} subdomains x {pb.K} specs, 20 iters + final bound, FP64 NumPy ({dt:.1f} s)"
+
+
+# ------------------------------------------------------------------------------ main
+
+def main():
+    args = parse()
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        run_reference(args, world)
+        return
+
+    torch.cuda.set_device(local)
+    from paper_2103_06624_gb300 import bcrown as bc
+    from paper_2103_06624_gb300 import workloads as wl
+
+    prec = bc.BF16 if args.precision == "bf16" else bc.FP32
+    pb, net, dom, hbatch, unst, lu = build_workload(0, args.subdomains, torch, bc, wl)
+    if prec == bc.BF16:
+        try:
+            _probe = bc.DeviceBatch.from_host(wl.tree_batch(pb, unst, [2], 2, 0))
+            a_, b_ = wl.initial_alpha_beta(wl.tree_batch(pb, unst, [2], 2, 0))
+            bc.bound(net, dom, _probe, torch.as_tensor(a_).cuda(), torch.as_tensor(b_).cuda(), bc.BF16)
+        except bc.BcrownError:
+            prec = bc.FP32
+    db = bc.DeviceBatch.from_host(hbatch)
+    a0, b0 = wl.initial_alpha_beta(hbatch)
+    a_init = torch.as_tensor(a0).cuda()
+    b_init = torch.as_tensor(b0).cuda()
+    alpha = torch.empty_like(a_init)
+    beta = torch.empty_like(b_init)
+    lb = torch.empty(hbatch.B * pb.K, device="cuda")
+    cfg = bc.OptCfg(precision=prec, certify=True)
+    flush = torch.empty(256 * 1024 * 1024 // 4, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        alpha.copy_(a_init)
+        beta.copy_(b_init)
+        bc.optimize(net, dom, db, alpha, beta, cfg, out=lb)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    bc.profile(net, True)
+    launches0 = bc.kernel_launches()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.fill_(float(i))                      # write 256 MB > L2 between timed steps
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    launches = bc.kernel_launches() - launches0
+    clk = clocks.stop()
+    prof = {c: bc.profile_read(net, c) for c in range(6)}
+    bc.profile(net, False)
+    t_ms = sum(a.elapsed_time(b) for a, b in ev)
+    if world > 1:
+        tt = torch.tensor([t_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    ms_per_step = t_ms / args.steps
+    units = hbatch.B * world
+    value = units / (ms_per_step / 1e3)
+    assert bc.status(net) == 0, "device status reported an error"
+
+    # ---------------------------------------------------------------- end to end (host buffers)
+    e2e = measure_e2e(args, bc, torch, net, dom, hbatch, a0, b0, cfg, pb, world)
+
+    # ---------------------------------------------------------------- roofline of the dominant kernel
+    widths = pb.widths
+    rows = hbatch.B * pb.K
+    f_row = algorithmic_flops_per_row_pass(widths)
+    if prof[5][1] > 0:
+        cls = 5
+        flops = rows * 2 * f_row * prof[5][1]
+    else:
+        cls = 0
+        # per step: iters x (backward + forward) + one certify backward
+        flops = rows * f_row * (2 * cfg.iters + 1) * args.steps
+    ms, nl = prof[cls]
+    sm_mhz = clk.get("sm_mhz") or 1432.0
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    if cls == 5:
+        peak = peaks.get("bf16_tflops_sustained", 1700.0)
+        bound, src = "tensor", "of measured (bf16 sustained)"
+    else:
+        peak = fp32_simt_peak_tflops(sm_mhz)
+        bound, src = "alu", f"152 SMs x 128 FP32 FMA x 2 x {sm_mhz:.0f} MHz (median under load)"
+    achieved = flops / (ms / 1e3) / 1e12 if ms > 0 else None
+    roof = {"bound": bound, "kernel": ["k_sgemm+k_conv", "", "", "", "", "k_fused_iter"][cls],
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": None, "peak_source": src,
+            "kernel_ms_per_step": ms / args.steps, "launches_per_step": nl / args.steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, cores, sample = cpu_oracle_rate(pb, lu, hbatch, args.cpu_sample)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        U = [len(u) for u in unst]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16" if prec == bc.BF16 else "f32", "data": "synthetic",
+            "config": {"workload": "mlp_784_256x6_10 eps=0.015, 1024 BaB-tree subdomains (depth<=12), 9 specs, "
+                                   "20 Adam iters + certify pass",
+                       "subdomains_per_gpu": hbatch.B, "specs": pb.K, "rows_per_gpu": rows,
+                       "unstable_neurons": U, "iters": cfg.iters, "precision": args.precision if prec == bc.BF16 else "fp32",
+                       "l2": "flushed (256 MB write between timed steps)"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def measure_e2e(args, bc, torch, net, dom, hbatch, a0, b0, cfg, pb, world):
+    """Same metric through the public API with HOST buffers: each step copies the batch, alpha and
+    beta in from pinned memory and reads lb, alpha, beta back."""
+    host = {}
+    for name in ["prop_of", "split_off", "split_cnt", "split_layer", "split_idx", "split_sign", "alpha_off"]:
+        arr = np.ascontiguousarray(getattr(hbatch, name))
+        if name == "split_idx":
+            arr = arr.astype(np.int32)
+        host[name] = torch.from_numpy(arr).pin_memory()
+    ha = torch.from_numpy(a0).pin_memory()
+    hb = torch.from_numpy(b0).pin_memory()
+    out_lb = torch.empty(hbatch.B * pb.K).pin_memory()
+    out_a = torch.empty_like(ha).pin_memory()
+    out_b = torch.empty_like(hb).pin_memory()
+    dev = {k: torch.empty(v.shape, dtype=v.dtype, device="cuda") for k, v in host.items()}
+    da = torch.empty(ha.shape, device="cuda")
+    dbt = torch.empty(hb.shape, device="cuda")
+    lb = torch.empty(hbatch.B * pb.K, device="cuda")
+    h2d = sum(v.numel() * v.element_size() for v in host.values()) + ha.numel() * 4 + hb.numel() * 4
+    d2h = out_lb.numel() * 4 + out_a.numel() * 4 + out_b.numel() * 4
+
+    def step():
+        for k in dev:
+            dev[k].copy_(host[k], non_blocking=True)
+        da.copy_(ha, non_blocking=True)
+        dbt.copy_(hb, non_blocking=True)
+        b = bc.DeviceBatch(dev["prop_of"], dev["split_off"], dev["split_cnt"], dev["split_layer"], dev["split_idx"],
+                           dev["split_sign"], dev["alpha_off"], hbatch.n_alpha, hbatch.n_beta)
+        bc.optimize(net, dom, b, da, dbt, cfg, out=lb)
+        out_lb.copy_(lb, non_blocking=True)
+        out_a.copy_(da, non_blocking=True)
+        out_b.copy_(dbt, non_blocking=True)
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n = max(3, args.steps // 2)
+    s.record()
+    for _ in range(n):
+        step()
+    e.record()
+    torch.cuda.synchronize()
+    ms = s.elapsed_time(e) / n
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    return {"value": hbatch.B * world / (ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": ms}
+
+
+def run_reference(args, world):
+    """The oracle (FP64 NumPy) timed on the host cores, on a bounded sample of the same workload."""
+    import torch
+    from oracle import bcrown_oracle as O
+    from paper_2103_06624_gb300 import workloads as wl
+    pb = wl.problem_mlp_784(seed=0)
+    onet = O.OracleNet(pb.layers, pb.C)
+    l, u = O.root_bounds(onet, pb.x_lo, pb.x_hi)
+    l, u = l.astype(np.float32), u.astype(np.float32)
+    unst = [np.nonzero((l[p] < 0) & (u[p] > 0))[0] for p in range(pb.P)]
+    batch = wl.tree_batch(pb, unst, [args.subdomains], 12, 1)
+    times = []
+    rate = None
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        rate, cores, sample = cpu_oracle_rate(pb, (l, u), batch, args.cpu_sample)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    ms = 1e3 * statistics.mean(times)
+    value = args.cpu_sample / (ms / 1e3)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "mlp_784_256x6_10 eps=0.015, BaB-tree subdomains (depth<=12), 9 specs, "
+                                   "20 Adam iters + final bound", "sample_subdomains": args.cpu_sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    _ = torch
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,234 @@
+/*
+ * bcrown.h -- C ABI of the GB300 batched beta-CROWN bound library.
+ *
+ * The library computes, for a ReLU network f, an input box [x_lo, x_hi] and
+ * linear specifications c_k, a sound lower bound of c_k^T f(x) on many
+ * branch-and-bound subdomains at once (Wang et al., arXiv 2103.06624,
+ * Theorem 3.1 and Eq. beta_crown_lp), its gradient with respect to the
+ * relaxation slopes alpha and the split multipliers beta, and the projected
+ * Adam ascent on (alpha, beta) of Eq. opt_alpha_beta (Appendix C.1).
+ *
+ * Conventions shared by every call:
+ *  - Status codes are returned (BCROWN_OK = 0, negative on error); no C++
+ *    exception crosses this boundary.  bcrown_last_error() gives a message for
+ *    the calling thread's last failure.
+ *  - bcrown_load_net copies host data.  Every other array argument is a
+ *    caller-owned DEVICE pointer; the call enqueues its kernels on `stream`
+ *    (a cudaStream_t passed as void*) and returns without synchronising.
+ *    Outputs are complete once the stream reaches that point.
+ *  - Problems that only the device can see (a split index out of range, a
+ *    non-finite bound, a wait that ran out of time) are recorded in a device
+ *    status word of the net; bcrown_status() synchronises the stream, returns
+ *    that code and clears it.  A row whose bound is not finite gets -inf,
+ *    which is sound, and sets BCROWN_ERR_NONFINITE; the other rows are written.
+ *  - Calls on one net share the net's device workspace, so calls on the same
+ *    net issued to different streams must not overlap.
+ *
+ * Index conventions (paper notation): layers i = 1..L are the linear layers;
+ * hidden layers are i = 1..L-1 with d_i neurons (for a convolution, flattened
+ * channel-major: c*H*W + y*W + x).  A property's hidden neurons are numbered
+ * layer-major, H = d_1 + ... + d_{L-1}.  Row r = b*K + k is subdomain b under
+ * spec k.
+ */
+#ifndef BCROWN_H
+#define BCROWN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bcrown_net bcrown_net; /* opaque, library-owned */
+
+enum {
+  BCROWN_OK = 0,
+  BCROWN_ERR_ARG = -1,
+  BCROWN_ERR_OOM = -2,
+  BCROWN_ERR_CUDA = -3,
+  BCROWN_ERR_TIMEOUT = -4,
+  BCROWN_ERR_NONFINITE = -5,
+  BCROWN_ERR_UNIMPLEMENTED = -6
+};
+
+enum { BCROWN_LAYER_FC = 0, BCROWN_LAYER_CONV = 1 };
+
+/* Arithmetic of a bound pass.
+ *  FP32    : FP32 coefficients and products, FP32 accumulation.
+ *  BF16    : A.W contractions with BF16 operands and FP32 accumulation on the
+ *            tensor cores (fully connected layers); everything else FP32.  Any
+ *            alpha, beta gives a valid bound (Section 3.1), so this is used for
+ *            the optimisation iterations.
+ *  CERTIFY : FP32 contractions plus a priori rounding-error terms, upper-chord
+ *            constants rounded outward and FP64 round-down sums; the result is
+ *            a lower bound of the exact-arithmetic bound at the same alpha, beta. */
+enum { BCROWN_FP32 = 0, BCROWN_BF16 = 1, BCROWN_CERTIFY = 2 };
+
+/* Lower slope rule for root (intermediate) bounds: ADAPTIVE takes alpha' = 1
+ * where u >= -l else 0; FIXED takes alpha' = alpha_value. */
+enum { BCROWN_ALPHA_ADAPTIVE = 0, BCROWN_ALPHA_FIXED = 1 };
+
+/* Largest split list one subdomain may carry. */
+#define BCROWN_MAX_SPLITS 64
+
+/* One linear layer of Eq. 1, z^(i) = W^(i) h^(i-1) + b^(i); ReLU follows every
+ * layer but the last.  Host pointers, copied by bcrown_load_net.
+ *  fc  : in_c = d_{i-1}, out_c = d_i, the h/w fields 1; W [out_c][in_c] row-major.
+ *  conv: W [out_c][in_c][k][k]; out_h = (in_h + 2 pad - k)/stride + 1 (same for w);
+ *        b has out_c entries (one per channel). */
+typedef struct {
+  int kind;
+  int in_c, in_h, in_w;
+  int out_c, out_h, out_w;
+  int k, stride, pad;
+  const float* W;
+  const float* b;
+} bcrown_layer;
+
+/* Build a network from n_layers layers and a spec matrix C [K][d_L] (host,
+ * row-major).  The spec is merged into the last layer (Section 2.1):
+ * Wbar = C W^(L), bbar = C b^(L).  The last layer must be fully connected.
+ * Returns BCROWN_ERR_ARG on inconsistent shapes, BCROWN_ERR_OOM/CUDA on
+ * device failures; *out is set only on success. */
+int bcrown_load_net(const bcrown_layer* layers, int n_layers, const float* C, int K,
+                    bcrown_net** out);
+
+void bcrown_free_net(bcrown_net* net);
+
+/* Widths d_0..d_L (widths must hold n_layers+1 ints; either pointer may be NULL). */
+int bcrown_net_info(const bcrown_net* net, int* n_layers, int* widths, int* K);
+
+/* The properties a batch refers to: input boxes and root intermediate bounds.
+ * Device pointers, caller-owned, read during the calls that take them. */
+typedef struct {
+  int n_props;
+  const float* x_lo; /* [P][d_0] */
+  const float* x_hi; /* [P][d_0] */
+  const float* l;    /* [P][H] pre-activation lower bounds (Section 2.1) */
+  const float* u;    /* [P][H] pre-activation upper bounds */
+} bcrown_domain;
+
+/* Root intermediate bounds (Section 3.3; CROWN, Lemma 2.2, with alpha' fixed by
+ * the rule and beta' = 0): for every hidden neuron, l and u of z^(i)_j over the
+ * box.  Layer 1 is the exact interval; layer i >= 2 bounds +-z^(i)_j by back-
+ * substitution through layers i-1..1.  With precision BCROWN_CERTIFY the bounds
+ * are computed with outward rounding (sound in floating point), else in FP32.
+ * Outputs: l, u [P][H]; unstable_count [P] (number of l < 0 < u), device. */
+int bcrown_root_bounds(bcrown_net* net, int n_props, const float* x_lo, const float* x_hi,
+                       int alpha_rule, float alpha_value, int precision,
+                       float* l, float* u, int32_t* unstable_count, void* stream);
+
+/* A batch of subdomains (Section 2.3 split sets; Eq. 3 encoding).  Device
+ * pointers, caller-owned.
+ *  prop_of[b]      property of subdomain b
+ *  split_off[b], split_cnt[b]  its splits are entries split_off..+cnt-1 of:
+ *  split_layer[s]  hidden layer i in 1..L-1
+ *  split_idx[s]    neuron index j in layer i
+ *  split_sign[s]   S^(i)_jj: -1 for the split z >= 0, +1 for z < 0
+ *  alpha_off[b]    alpha of row (b,k) for the property's t-th unstable neuron
+ *                  (layer-major order of l < 0 < u) is alpha[alpha_off[b] + k*U_p + t]
+ * beta of split t of subdomain b under spec k is beta[split_off[b]*K + k*split_cnt[b] + t].
+ * n_alpha, n_beta: total lengths of the alpha and beta arrays. */
+typedef struct {
+  int B;
+  const int32_t* prop_of;
+  const int32_t* split_off;
+  const int32_t* split_cnt;
+  const uint8_t* split_layer;
+  const uint32_t* split_idx;
+  const int8_t* split_sign;
+  const int64_t* alpha_off;
+  int64_t n_alpha;
+  int64_t n_beta;
+} bcrown_batch;
+
+/* Lower bound of every row at fixed alpha, beta (Theorem 3.1):
+ *   A^(L-1) = Wbar_k, c = bbar_k; for i = L-1..1:
+ *   Lambda = A D + beta^T S; c += Lambda b + A lambda; A^(i-1) = Lambda W^(i);
+ *   lb = c + sum_m min(A^(0)_m x_lo_m, A^(0)_m x_hi_m).
+ * D, lambda follow Eq. definition_D / definition_lowerb with split overriding
+ * stability.  alpha [n_alpha], beta [n_beta] device; lb [B*K] device output. */
+int bcrown_bound(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* batch,
+                 const float* alpha, const float* beta, int precision, float* lb, void* stream);
+
+/* lb and its gradient: dalpha[t] = A^(i)_j zhat^(i)_j where alpha_j is the slope
+ * in use (unstable, unsplit, A_j >= 0), else 0; dbeta = S_jj zhat^(i)_j, with
+ * zhat the pre-activations along x* (x_lo where A^(0)_m >= 0, else x_hi) pushed
+ * through the relaxed network.  Shapes as alpha/beta.  precision FP32 or BF16. */
+int bcrown_bound_grad(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* batch,
+                      const float* alpha, const float* beta, int precision,
+                      float* lb, float* dalpha, float* dbeta, void* stream);
+
+/* Projected Adam ascent (Eq. opt_alpha_beta; Appendix C.1: 20 iterations, lr
+ * 0.1 for alpha and 0.05 for beta, decayed by 0.98 per iteration).  Iteration t
+ * evaluates lb and its gradient at theta_t with `precision`, keeps per row the
+ * best lb and its theta, then steps uphill with lr0*decay^t, Adam moments
+ * (beta1, beta2, eps) with bias correction, and clamps alpha to [0,1], beta to
+ * >= 0.  At the end one BCROWN_CERTIFY pass (if certify != 0, else FP32) at the
+ * best theta writes lb_out [B*K].  alpha, beta: in = initial values, out = best. */
+typedef struct {
+  int iters;
+  float lr_alpha, lr_beta, decay;
+  float adam_beta1, adam_beta2, adam_eps;
+  int precision; /* of the iterations: BCROWN_FP32 or BCROWN_BF16 */
+  int certify;   /* final pass: nonzero = BCROWN_CERTIFY, 0 = FP32 */
+} bcrown_opt_cfg;
+
+int bcrown_optimize(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* batch,
+                    const bcrown_opt_cfg* cfg, float* alpha, float* beta, float* lb_out,
+                    void* stream);
+
+/* batch_split of Algorithm 1: parent b splits neuron (pick_layer[b], pick_idx[b]).
+ * Child 2b is C^l (z >= 0, S = -1), child 2b+1 is C^u (z < 0, S = +1).  Each
+ * child carries the parent's splits followed by the new one, a copy of the
+ * parent's alpha block and the parent's beta with 0 for the new split.
+ * Outputs (device, caller-allocated for 2B children): prop_of, split_off,
+ * split_cnt [2B]; split_layer, split_idx, split_sign [2*(S_parent + B)];
+ * alpha_off [2B] (packed in child order); alpha [2*n_alpha];
+ * beta [2*(n_beta + B*K)].  child_* pointers describe the result. */
+int bcrown_batch_split(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* parent,
+                       const uint8_t* pick_layer, const uint32_t* pick_idx,
+                       const float* alpha, const float* beta,
+                       int32_t* child_prop_of, int32_t* child_split_off, int32_t* child_split_cnt,
+                       uint8_t* child_split_layer, uint32_t* child_split_idx, int8_t* child_split_sign,
+                       int64_t* child_alpha_off, float* child_alpha, float* child_beta,
+                       void* stream);
+
+/* Per (row, hidden neuron) relaxation code as the kernels use it: 0 inactive
+ * (u <= 0), 1 active (l >= 0), 2 unstable, 3 split z >= 0, 4 split z < 0
+ * (split overrides stability).  codes: device [B*K][H] int8. */
+int bcrown_neuron_codes(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* batch,
+                        int8_t* codes, void* stream);
+
+/* Timing hook.  With enable != 0 the library records a CUDA event pair on the
+ * launching stream around each of its kernels of the classes below; enable = 0
+ * stops recording.  Either call discards earlier records.  bcrown_profile_read
+ * waits for the recorded events and returns the summed device milliseconds and
+ * the launch count of one class. */
+enum {
+  BCROWN_PROF_CONTRACT = 0,   /* A.W contractions (dense or convolution), both directions */
+  BCROWN_PROF_RELAX = 1,      /* relaxation + beta + bias epilogue */
+  BCROWN_PROF_CONCRETIZE = 2, /* concretisation over the box */
+  BCROWN_PROF_ADJOINT = 3,    /* adjoint epilogue (gradients) */
+  BCROWN_PROF_ADAM = 4,       /* projected Adam */
+  BCROWN_PROF_FUSED = 5,      /* fused tensor-core iteration kernel */
+  BCROWN_PROF_NCLASS = 6
+};
+int bcrown_profile(bcrown_net* net, int enable);
+int bcrown_profile_read(bcrown_net* net, int cls, double* total_ms, long long* launches);
+
+/* Number of kernels this library has launched in the process so far (all nets). */
+long long bcrown_kernel_launches(void);
+
+/* Synchronise `stream`, return the device status word of the net (BCROWN_OK or
+ * the first device-detected error since the last call) and clear it. */
+int bcrown_status(bcrown_net* net, void* stream);
+
+/* Message of the calling thread's last error (static storage, never NULL). */
+const char* bcrown_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BCROWN_H */

@@ -1,0 +1,279 @@
+"""Python binding of the C ABI (include/bcrown.h), same names, torch tensors for memory and streams.
+
+Every computation runs in the native library's CUDA kernels; this module only
+marshals arguments (device pointers of contiguous CUDA tensors and the current
+stream).  Calls are asynchronous on the current stream, like the C ABI.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import native as N
+
+FP32, BF16, CERTIFY = N.FP32, N.BF16, N.CERTIFY
+ALPHA_ADAPTIVE, ALPHA_FIXED = N.ALPHA_ADAPTIVE, N.ALPHA_FIXED
+BcrownError = N.BcrownError
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "expected a contiguous CUDA tensor"
+    return C.c_void_p(t.data_ptr()) if t.numel() else None
+
+
+def _dev(a, dtype):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype).contiguous()
+
+
+class Net:
+    """A loaded network (bcrown_load_net); the spec matrix C is merged into the last layer."""
+
+    def __init__(self, layers, C_spec):
+        lib = N.load()
+        keep = []
+        arr = (N.Layer * len(layers))()
+        for i, ly in enumerate(layers):
+            W = np.ascontiguousarray(ly.W, np.float32)
+            b = np.ascontiguousarray(ly.b, np.float32)
+            keep += [W, b]
+            if ly.kind == "fc":
+                arr[i] = N.Layer(N.LAYER_FC, ly.d_in, 1, 1, ly.d_out, 1, 1, 1, 1, 0,
+                                 W.ctypes.data, b.ctypes.data)
+            else:
+                ci, h, w = ly.in_shape
+                co, ho, wo = ly.out_shape
+                arr[i] = N.Layer(N.LAYER_CONV, ci, h, w, co, ho, wo, ly.k, ly.stride, ly.pad,
+                                 W.ctypes.data, b.ctypes.data)
+        Cs = np.ascontiguousarray(C_spec, np.float32)
+        h = C.c_void_p()
+        N.check(lib.bcrown_load_net(arr, len(layers), Cs.ctypes.data, Cs.shape[0], C.byref(h)))
+        self._h = h
+        self.L = len(layers)
+        self.K = int(Cs.shape[0])
+        self.widths = [layers[0].d_in] + [ly.d_out for ly in layers]
+        self.hidden_widths = self.widths[1:self.L]
+        self.H = int(sum(self.hidden_widths))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            N.load().bcrown_free_net(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+@dataclass
+class Domain:
+    """Input boxes and root intermediate bounds of the properties (device tensors)."""
+    x_lo: torch.Tensor
+    x_hi: torch.Tensor
+    l: torch.Tensor
+    u: torch.Tensor
+
+    @property
+    def n_props(self):
+        return int(self.x_lo.shape[0])
+
+    def c(self):
+        return N.Domain(self.n_props, _ptr(self.x_lo), _ptr(self.x_hi), _ptr(self.l), _ptr(self.u))
+
+
+@dataclass
+class DeviceBatch:
+    """A batch of subdomains in the C-ABI layout, on the device."""
+    prop_of: torch.Tensor
+    split_off: torch.Tensor
+    split_cnt: torch.Tensor
+    split_layer: torch.Tensor
+    split_idx: torch.Tensor
+    split_sign: torch.Tensor
+    alpha_off: torch.Tensor
+    n_alpha: int
+    n_beta: int
+
+    @property
+    def B(self):
+        return int(self.prop_of.shape[0])
+
+    @staticmethod
+    def from_host(b):
+        return DeviceBatch(_dev(b.prop_of, torch.int32), _dev(b.split_off, torch.int32),
+                           _dev(b.split_cnt, torch.int32), _dev(b.split_layer, torch.uint8),
+                           _dev(np.asarray(b.split_idx).astype(np.int64), torch.int64).to(torch.int32),
+                           _dev(b.split_sign, torch.int8), _dev(b.alpha_off, torch.int64),
+                           int(b.n_alpha), int(b.n_beta))
+
+    def c(self):
+        return N.Batch(self.B, _ptr(self.prop_of), _ptr(self.split_off), _ptr(self.split_cnt),
+                       _ptr(self.split_layer), _ptr(self.split_idx), _ptr(self.split_sign),
+                       _ptr(self.alpha_off), self.n_alpha, self.n_beta)
+
+
+def domain_from_host(x_lo, x_hi, l, u):
+    return Domain(_dev(x_lo, torch.float32), _dev(x_hi, torch.float32), _dev(l, torch.float32),
+                  _dev(u, torch.float32))
+
+
+def load_net(layers, C_spec):
+    return Net(layers, C_spec)
+
+
+def root_bounds(net, x_lo, x_hi, alpha_rule=ALPHA_ADAPTIVE, alpha_value=0.5, precision=CERTIFY, stream=None):
+    """CROWN root bounds l, u [P, H] and the unstable count per property (device tensors)."""
+    lib = N.load()
+    P = int(x_lo.shape[0])
+    l = torch.empty((P, net.H), device="cuda", dtype=torch.float32)
+    u = torch.empty((P, net.H), device="cuda", dtype=torch.float32)
+    cnt = torch.empty(P, device="cuda", dtype=torch.int32)
+    N.check(lib.bcrown_root_bounds(net.handle, P, _ptr(x_lo), _ptr(x_hi), alpha_rule, float(alpha_value),
+                                   precision, _ptr(l), _ptr(u), _ptr(cnt), _stream(stream)))
+    return l, u, cnt
+
+
+def bound(net, dom, batch, alpha, beta, precision=FP32, out=None, stream=None):
+    lib = N.load()
+    lb = out if out is not None else torch.empty(batch.B * net.K, device="cuda", dtype=torch.float32)
+    d, b = dom.c(), batch.c()
+    N.check(lib.bcrown_bound(net.handle, C.byref(d), C.byref(b), _ptr(alpha), _ptr(beta), precision,
+                             _ptr(lb), _stream(stream)))
+    return lb
+
+
+def bound_grad(net, dom, batch, alpha, beta, precision=FP32, stream=None):
+    lib = N.load()
+    lb = torch.empty(batch.B * net.K, device="cuda", dtype=torch.float32)
+    da = torch.empty(max(batch.n_alpha, 0), device="cuda", dtype=torch.float32)
+    db = torch.empty(max(batch.n_beta, 0), device="cuda", dtype=torch.float32)
+    d, b = dom.c(), batch.c()
+    N.check(lib.bcrown_bound_grad(net.handle, C.byref(d), C.byref(b), _ptr(alpha), _ptr(beta), precision,
+                                  _ptr(lb), _ptr(da), _ptr(db), _stream(stream)))
+    return lb, da, db
+
+
+@dataclass
+class OptCfg:
+    """Projected Adam settings; defaults from Appendix C.1 (20 iterations, lr 0.1/0.05, decay 0.98)."""
+    iters: int = 20
+    lr_alpha: float = 0.1
+    lr_beta: float = 0.05
+    decay: float = 0.98
+    adam_beta1: float = 0.9
+    adam_beta2: float = 0.999
+    adam_eps: float = 1e-8
+    precision: int = FP32
+    certify: bool = True
+
+    def c(self):
+        return N.OptCfg(self.iters, self.lr_alpha, self.lr_beta, self.decay, self.adam_beta1, self.adam_beta2,
+                        self.adam_eps, self.precision, 1 if self.certify else 0)
+
+
+def optimize(net, dom, batch, alpha, beta, cfg=OptCfg(), out=None, stream=None):
+    """Runs the ascent; alpha, beta are overwritten with the per-row best values. Returns lb [B*K]."""
+    lib = N.load()
+    lb = out if out is not None else torch.empty(batch.B * net.K, device="cuda", dtype=torch.float32)
+    d, b, cc = dom.c(), batch.c(), cfg.c()
+    N.check(lib.bcrown_optimize(net.handle, C.byref(d), C.byref(b), C.byref(cc), _ptr(alpha), _ptr(beta),
+                                _ptr(lb), _stream(stream)))
+    return lb
+
+
+def neuron_codes(net, dom, batch, stream=None):
+    lib = N.load()
+    codes = torch.empty((batch.B * net.K, net.H), device="cuda", dtype=torch.int8)
+    d, b = dom.c(), batch.c()
+    N.check(lib.bcrown_neuron_codes(net.handle, C.byref(d), C.byref(b), _ptr(codes), _stream(stream)))
+    return codes
+
+
+def batch_split(net, dom, batch, pick_layer, pick_idx, alpha, beta, U, stream=None):
+    """Children of batch_split (Algorithm 1); U: per-property unstable counts (host ints)."""
+    lib = N.load()
+    B = batch.B
+    K = net.K
+    S = int(batch.split_layer.shape[0])
+    cprop = torch.empty(2 * B, device="cuda", dtype=torch.int32)
+    coff = torch.empty(2 * B, device="cuda", dtype=torch.int32)
+    ccnt = torch.empty(2 * B, device="cuda", dtype=torch.int32)
+    clay = torch.empty(2 * (S + B), device="cuda", dtype=torch.uint8)
+    cidx = torch.empty(2 * (S + B), device="cuda", dtype=torch.int32)
+    csgn = torch.empty(2 * (S + B), device="cuda", dtype=torch.int8)
+    caoff = torch.empty(2 * B, device="cuda", dtype=torch.int64)
+    ca = torch.empty(2 * batch.n_alpha, device="cuda", dtype=torch.float32)
+    cb = torch.empty(2 * (batch.n_beta + B * K), device="cuda", dtype=torch.float32)
+    d, b = dom.c(), batch.c()
+    N.check(lib.bcrown_batch_split(net.handle, C.byref(d), C.byref(b), _ptr(pick_layer), _ptr(pick_idx),
+                                   _ptr(alpha), _ptr(beta), _ptr(cprop), _ptr(coff), _ptr(ccnt), _ptr(clay),
+                                   _ptr(cidx), _ptr(csgn), _ptr(caoff), _ptr(ca), _ptr(cb), _stream(stream)))
+    child = DeviceBatch(cprop, coff, ccnt, clay, cidx, csgn, caoff, 2 * batch.n_alpha, 2 * (batch.n_beta + B * K))
+    return child, ca, cb
+
+
+def status(net, stream=None):
+    """Synchronise and return (and clear) the device status word."""
+    return N.load().bcrown_status(net.handle, _stream(stream))
+
+
+class BoundFunction(torch.autograd.Function):
+    """lb = bound(alpha, beta) with the hand-written adjoint kernel as its backward."""
+
+    @staticmethod
+    def forward(ctx, alpha, beta, net, dom, batch, row_of_alpha, row_of_beta, precision):
+        lb, da, db = bound_grad(net, dom, batch, alpha.detach().contiguous(), beta.detach().contiguous(), precision)
+        ctx.save_for_backward(da, db, row_of_alpha, row_of_beta)
+        return lb
+
+    @staticmethod
+    def backward(ctx, g):
+        da, db, ra, rb = ctx.saved_tensors
+        return da * g[ra], db * g[rb], None, None, None, None, None, None
+
+
+def param_rows(batch, K, U):
+    """Row index of every alpha and beta entry (device int64), for BoundFunction."""
+    B = batch.B
+    prop = batch.prop_of.long()
+    Up = torch.as_tensor(np.asarray(U), device="cuda").long()[prop]                 # [B]
+    rows_b = torch.arange(B, device="cuda") * K
+    ra = torch.repeat_interleave(
+        (rows_b[:, None] + torch.arange(K, device="cuda")[None, :]).reshape(-1),
+        Up.repeat_interleave(K))
+    cnt = batch.split_cnt.long()
+    rb = torch.repeat_interleave(
+        (rows_b[:, None] + torch.arange(K, device="cuda")[None, :]).reshape(-1),
+        cnt.repeat_interleave(K))
+    return ra, rb
+
+
+def profile(net, enable=True):
+    N.check(N.load().bcrown_profile(net.handle, 1 if enable else 0))
+
+
+def profile_read(net, cls):
+    """(total device ms, launches) of one kernel class recorded since profile(net, True)."""
+    t = C.c_double()
+    n = C.c_longlong()
+    N.check(N.load().bcrown_profile_read(net.handle, cls, C.byref(t), C.byref(n)))
+    return t.value, n.value
+
+
+def kernel_launches():
+    return int(N.load().bcrown_kernel_launches())

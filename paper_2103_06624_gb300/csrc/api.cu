@@ -1,0 +1,418 @@
+// C-ABI entry points: root bounds, bound, bound + gradient, projected Adam, batch_split,
+// neuron codes.  Orchestrates the kernels of simt.cu (and the tensor-core path of
+// fused_tc.cu for BCROWN_BF16) on the caller's stream.
+#include <algorithm>
+#include <cmath>
+
+#include "fused_tc.cuh"
+#include "simt.cuh"
+
+using namespace bcrown;
+
+namespace bcrown {
+
+static const size_t kChunkBytes = size_t(2) << 30;  // per-chunk workspace target
+
+static int check_domain(const bcrown_net* net, const bcrown_domain* dom) {
+  if (!dom || dom->n_props < 1 || !dom->x_lo || !dom->x_hi || (net->H > 0 && (!dom->l || !dom->u)))
+    return fail(BCROWN_ERR_ARG, "domain: missing arrays or n_props < 1");
+  return BCROWN_OK;
+}
+
+static int check_batch(const bcrown_batch* bt) {
+  if (!bt || bt->B < 0) return fail(BCROWN_ERR_ARG, "batch: null or negative B");
+  if (bt->B > 0 && (!bt->prop_of || !bt->split_off || !bt->split_cnt || !bt->alpha_off))
+    return fail(BCROWN_ERR_ARG, "batch: missing arrays");
+  if (bt->n_alpha < 0 || bt->n_beta < 0) return fail(BCROWN_ERR_ARG, "batch: negative n_alpha/n_beta");
+  return BCROWN_OK;
+}
+
+static BatchView view_of(const bcrown_batch* bt) {
+  return BatchView{bt->B, bt->prop_of, bt->split_off, bt->split_cnt, bt->split_layer, bt->split_idx,
+                   bt->split_sign, bt->alpha_off};
+}
+
+static double gamma_n(long long n) {
+  const double u = std::ldexp(1.0, -24);
+  double nu = (double)n * u;
+  return nu / (1.0 - nu) * (1.0 + 1e-6);
+}
+
+// Workspace carve-up for one call.
+struct Plan {
+  int P, H, R, Rc;
+  // tables
+  uint8_t* code;
+  int32_t* rank;
+  float* slope;
+  float* icpt;
+  int32_t* U;
+  double* wm;
+  Tables tb;
+  // chunk buffers
+  std::vector<float*> Abuf;  // [L] : Abuf[i] for hidden i (1..L-1), Abuf[0] = A^(0)
+  float* Lam;
+  float* Z0;
+  float* Z1;
+  float* cf;
+  double* cd;
+  double* E;
+  // optimiser state (optional)
+  float *a_cur, *ma, *va, *ga, *b_cur, *mb, *vb, *gb, *best_lb, *lb_t;
+  char* tc_ws;
+  size_t tc_ws_bytes;
+};
+
+static size_t row_bytes(const bcrown_net* net) {
+  size_t f = 0;
+  for (int i = 0; i < net->L; ++i) f += (size_t)net->d[i];  // A^(0..L-1)
+  f += (size_t)net->max_hidden + 2 * (size_t)net->max_width;
+  return f * 4 + 4 + 16 + 3 * 256;
+}
+
+static int make_plan(bcrown_net* net, int P, int R, bool cert, bool opt, int64_t n_alpha, int64_t n_beta,
+                     size_t tc_bytes, Plan& pl) {
+  pl.P = P;
+  pl.H = net->H;
+  pl.R = R;
+  size_t rb = row_bytes(net);
+  long long rc = std::max<long long>(1, (long long)(kChunkBytes / rb));
+  pl.Rc = (int)std::min<long long>(std::max(R, 1), rc);
+  size_t PH = (size_t)P * std::max(net->H, 1);
+  size_t bytes = 0;
+  bytes += align_up(PH) + align_up(PH * 4) * 3 + align_up((size_t)P * 4);
+  if (cert) bytes += align_up(PH * 8);
+  bytes += (size_t)pl.Rc * rb + 16 * 256;
+  if (opt) bytes += align_up((size_t)n_alpha * 4) * 4 + align_up((size_t)n_beta * 4) * 4 + align_up((size_t)R * 4) * 2;
+  bytes += align_up(tc_bytes);
+  int st;
+  void* base = ws_get(net, bytes, &st);
+  if (!base) return st;
+  Arena ar{(char*)base};
+  pl.code = ar.take<uint8_t>(PH);
+  pl.rank = ar.take<int32_t>(PH);
+  pl.slope = ar.take<float>(PH);
+  pl.icpt = ar.take<float>(PH);
+  pl.U = ar.take<int32_t>(P);
+  pl.wm = cert ? ar.take<double>(PH) : nullptr;
+  pl.Abuf.assign(net->L, nullptr);
+  for (int i = 0; i < net->L; ++i) pl.Abuf[i] = ar.take<float>((size_t)pl.Rc * net->d[i]);
+  pl.Lam = ar.take<float>((size_t)pl.Rc * net->max_hidden);
+  pl.Z0 = ar.take<float>((size_t)pl.Rc * net->max_width);
+  pl.Z1 = ar.take<float>((size_t)pl.Rc * net->max_width);
+  pl.cf = ar.take<float>(pl.Rc);
+  pl.cd = ar.take<double>(pl.Rc);
+  pl.E = ar.take<double>(pl.Rc);
+  if (opt) {
+    pl.a_cur = ar.take<float>(n_alpha);
+    pl.ma = ar.take<float>(n_alpha);
+    pl.va = ar.take<float>(n_alpha);
+    pl.ga = ar.take<float>(n_alpha);
+    pl.b_cur = ar.take<float>(n_beta);
+    pl.mb = ar.take<float>(n_beta);
+    pl.vb = ar.take<float>(n_beta);
+    pl.gb = ar.take<float>(n_beta);
+    pl.best_lb = ar.take<float>(R);
+    pl.lb_t = ar.take<float>(R);
+  }
+  pl.tc_ws = tc_bytes ? ar.take<char>(tc_bytes) : nullptr;
+  pl.tc_ws_bytes = tc_bytes;
+  if (ar.off > net->ws.size) return fail(BCROWN_ERR_OOM, "workspace plan overflow");
+  return BCROWN_OK;
+}
+
+static void build_tables(bcrown_net* net, const bcrown_domain* dom, Plan& pl, cudaStream_t s) {
+  launch_tables(dom->n_props, net->H, dom->l, dom->u, pl.tb, pl.code, pl.rank, pl.slope, pl.icpt, pl.U, s);
+}
+
+static void build_wm(bcrown_net* net, const bcrown_domain* dom, Plan& pl, cudaStream_t s) {
+  for (int i = 1; i < net->L; ++i) {
+    long long hprev = i >= 2 ? net->hoff[i - 2] : -1;
+    launch_absw_m(geom_of(net->ly[i - 1]), net->ly[i - 1].W, dom->n_props, net->H, net->hoff[i - 1], hprev, dom->u,
+                  dom->x_lo, dom->x_hi, net->d[0], pl.wm, s);
+  }
+}
+
+static RowsCtx ctx_of(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* bt, const Plan& pl, int r0,
+                      int Rc) {
+  RowsCtx c;
+  c.r0 = r0;
+  c.R = Rc;
+  c.K = net->K;
+  c.P = dom->n_props;
+  c.bt = view_of(bt);
+  c.tb = pl.tb;
+  c.x_lo = dom->x_lo;
+  c.x_hi = dom->x_hi;
+  c.l = dom->l;
+  c.u = dom->u;
+  c.status = net->status;
+  return c;
+}
+
+// Backward contraction of layer i: Aout = Lam W^(i) (fc) or transposed convolution.
+static void contract_bwd(bcrown_net* net, int i, int Rc, const float* Lam, float* Aout, cudaStream_t s) {
+  ProfScope ps(net, BCROWN_PROF_CONTRACT, s);
+  const LayerDev& l = net->ly[i - 1];
+  if (l.kind == BCROWN_LAYER_FC)
+    launch_sgemm(Rc, l.d_in, l.d_out, Lam, l.d_out, l.W, l.d_in, Aout, l.d_in, nullptr, s);
+  else
+    launch_conv_bwd(Rc, geom_of(l), Lam, l.W, Aout, s);
+}
+
+// Forward contraction of layer i: Z = h W^(i)^T + b^(i).
+static void contract_fwd(bcrown_net* net, int i, int Rc, const float* h, float* Z, cudaStream_t s) {
+  ProfScope ps(net, BCROWN_PROF_CONTRACT, s);
+  const LayerDev& l = net->ly[i - 1];
+  if (l.kind == BCROWN_LAYER_FC)
+    launch_sgemm(Rc, l.d_out, l.d_in, h, l.d_in, l.Wt, l.d_out, Z, l.d_out, l.b, s);
+  else
+    launch_conv_fwd(Rc, geom_of(l), h, l.W, l.b, Z, s);
+}
+
+// One chunk of rows: bound (and optionally the gradient) with the SIMT path.
+static void chunk_simt(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* bt, Plan& pl, int r0, int Rc,
+                       bool cert, bool grad, const float* alpha, const float* beta, float* lb, float* dalpha,
+                       float* dbeta, cudaStream_t s) {
+  RowsCtx c = ctx_of(net, dom, bt, pl, r0, Rc);
+  const int L = net->L;
+  long long hoff_top = L >= 2 ? net->hoff[L - 2] : -1;
+  launch_init_top(cert, c, net->d[L - 1], net, hoff_top, pl.Abuf[L - 1], pl.cf, pl.cd, pl.E, s);
+  for (int i = L - 1; i >= 1; --i) {
+    const LayerDev& ly = net->ly[i - 1];
+    {
+      ProfScope ps(net, BCROWN_PROF_RELAX, s);
+      launch_relax(cert, c, i, net->d[i], net->hoff[i - 1], pl.Abuf[i], pl.Lam, ly.b, alpha, bt->n_alpha, beta, bt->n_beta, pl.cf,
+                 pl.cd, pl.E, pl.wm, gamma_n(ly.terms_bwd), s);
+    }
+    contract_bwd(net, i, Rc, pl.Lam, pl.Abuf[i - 1], s);
+  }
+  {
+    ProfScope ps(net, BCROWN_PROF_CONCRETIZE, s);
+    launch_concretize(cert, c, net->d[0], pl.Abuf[0], pl.cf, pl.cd, pl.E, lb, s);
+  }
+  if (!grad) return;
+  launch_xstar(c, net->d[0], pl.Abuf[0], pl.Z0, s);
+  float* h = pl.Z0;
+  float* z = pl.Z1;
+  for (int i = 1; i <= L - 1; ++i) {
+    contract_fwd(net, i, Rc, h, z, s);
+    ProfScope ps(net, BCROWN_PROF_ADJOINT, s);
+    launch_fwd_epi(c, i, net->d[i], net->hoff[i - 1], z, pl.Abuf[i], alpha, bt->n_alpha, dalpha, dbeta, bt->n_beta, s);
+    std::swap(h, z);
+  }
+}
+
+static int run_bound(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* bt, Plan& pl, int precision,
+                     bool grad, const float* alpha, const float* beta, float* lb, float* dalpha, float* dbeta,
+                     cudaStream_t s) {
+  const int R = bt->B * net->K;
+  if (precision == BCROWN_BF16 && tc_supported(net)) {
+    return tc_bound(net, dom, bt, pl.tb, pl.tc_ws, pl.tc_ws_bytes, grad, alpha, beta, lb, dalpha, dbeta, s);
+  }
+  bool cert = precision == BCROWN_CERTIFY;
+  for (int r0 = 0; r0 < R; r0 += pl.Rc) {
+    int Rc = std::min(pl.Rc, R - r0);
+    chunk_simt(net, dom, bt, pl, r0, Rc, cert, grad, alpha, beta, lb, dalpha, dbeta, s);
+  }
+  return BCROWN_OK;
+}
+
+static int check_precision(bcrown_net* net, int precision, bool grad) {
+  if (precision != BCROWN_FP32 && precision != BCROWN_BF16 && precision != BCROWN_CERTIFY)
+    return fail(BCROWN_ERR_ARG, "unknown precision");
+  if (grad && precision == BCROWN_CERTIFY) return fail(BCROWN_ERR_ARG, "gradient in CERTIFY precision is not offered");
+  if (precision == BCROWN_BF16 && !tc_supported(net))
+    return fail(BCROWN_ERR_UNIMPLEMENTED, "BF16 tensor-core path needs a fully connected network with supported widths");
+  return BCROWN_OK;
+}
+
+}  // namespace bcrown
+
+extern "C" int bcrown_bound(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* batch,
+                            const float* alpha, const float* beta, int precision, float* lb, void* stream) {
+  if (!net) return fail(BCROWN_ERR_ARG, "bound: null net");
+  BC_CHECK(check_domain(net, dom));
+  BC_CHECK(check_batch(batch));
+  BC_CHECK(check_precision(net, precision, false));
+  if (batch->B == 0) return BCROWN_OK;
+  if (!lb) return fail(BCROWN_ERR_ARG, "bound: null lb");
+  std::lock_guard<std::mutex> g(net->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  Plan pl;
+  int R = batch->B * net->K;
+  size_t tcb = precision == BCROWN_BF16 ? tc_workspace_bytes(net, R, false) : 0;
+  BC_CHECK(make_plan(net, dom->n_props, R, precision == BCROWN_CERTIFY, false, 0, 0, tcb, pl));
+  build_tables(net, dom, pl, s);
+  if (precision == BCROWN_CERTIFY) build_wm(net, dom, pl, s);
+  BC_CHECK(run_bound(net, dom, batch, pl, precision, false, alpha, beta, lb, nullptr, nullptr, s));
+  BC_CUDA(cudaGetLastError());
+  return BCROWN_OK;
+}
+
+extern "C" int bcrown_bound_grad(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* batch,
+                                 const float* alpha, const float* beta, int precision, float* lb, float* dalpha,
+                                 float* dbeta, void* stream) {
+  if (!net) return fail(BCROWN_ERR_ARG, "bound_grad: null net");
+  BC_CHECK(check_domain(net, dom));
+  BC_CHECK(check_batch(batch));
+  BC_CHECK(check_precision(net, precision, true));
+  if (batch->B == 0) return BCROWN_OK;
+  if (!lb || (batch->n_alpha && !dalpha) || (batch->n_beta && !dbeta))
+    return fail(BCROWN_ERR_ARG, "bound_grad: null output");
+  std::lock_guard<std::mutex> g(net->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  Plan pl;
+  int R = batch->B * net->K;
+  size_t tcb = precision == BCROWN_BF16 ? tc_workspace_bytes(net, R, true) : 0;
+  BC_CHECK(make_plan(net, dom->n_props, R, false, false, 0, 0, tcb, pl));
+  build_tables(net, dom, pl, s);
+  BC_CHECK(run_bound(net, dom, batch, pl, precision, true, alpha, beta, lb, dalpha, dbeta, s));
+  BC_CUDA(cudaGetLastError());
+  return BCROWN_OK;
+}
+
+extern "C" int bcrown_optimize(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* batch,
+                               const bcrown_opt_cfg* cfg, float* alpha, float* beta, float* lb_out, void* stream) {
+  if (!net || !cfg) return fail(BCROWN_ERR_ARG, "optimize: null net or cfg");
+  BC_CHECK(check_domain(net, dom));
+  BC_CHECK(check_batch(batch));
+  BC_CHECK(check_precision(net, cfg->precision, true));
+  if (cfg->iters < 0) return fail(BCROWN_ERR_ARG, "optimize: negative iterations");
+  if (batch->B == 0) return BCROWN_OK;
+  if (!lb_out || (batch->n_alpha && !alpha) || (batch->n_beta && !beta))
+    return fail(BCROWN_ERR_ARG, "optimize: null buffer");
+  std::lock_guard<std::mutex> g(net->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int R = batch->B * net->K;
+  const int64_t na = batch->n_alpha, nb = batch->n_beta;
+  Plan pl;
+  size_t tcb = cfg->precision == BCROWN_BF16 ? tc_workspace_bytes(net, R, true) : 0;
+  bool cert = cfg->certify != 0;
+  BC_CHECK(make_plan(net, dom->n_props, R, cert, true, na, nb, tcb, pl));
+  build_tables(net, dom, pl, s);
+  if (cert) build_wm(net, dom, pl, s);
+  if (na) {
+    BC_CUDA(cudaMemcpyAsync(pl.a_cur, alpha, na * 4, cudaMemcpyDeviceToDevice, s));
+    BC_CUDA(cudaMemsetAsync(pl.ma, 0, na * 4, s));
+    BC_CUDA(cudaMemsetAsync(pl.va, 0, na * 4, s));
+    BC_CUDA(cudaMemsetAsync(pl.ga, 0, na * 4, s));
+  }
+  if (nb) {
+    BC_CUDA(cudaMemcpyAsync(pl.b_cur, beta, nb * 4, cudaMemcpyDeviceToDevice, s));
+    BC_CUDA(cudaMemsetAsync(pl.mb, 0, nb * 4, s));
+    BC_CUDA(cudaMemsetAsync(pl.vb, 0, nb * 4, s));
+    BC_CUDA(cudaMemsetAsync(pl.gb, 0, nb * 4, s));
+  }
+  launch_fill(pl.best_lb, R, -INFINITY, s);
+  BatchView bv = view_of(batch);
+  for (int t = 0; t < cfg->iters; ++t) {
+    BC_CHECK(run_bound(net, dom, batch, pl, cfg->precision, true, pl.a_cur, pl.b_cur, pl.lb_t, pl.ga, pl.gb, s));
+    float fac = std::pow(cfg->decay, (float)t);
+    float bc1 = 1.f - std::pow(cfg->adam_beta1, (float)(t + 1));
+    float bc2 = 1.f - std::pow(cfg->adam_beta2, (float)(t + 1));
+    ProfScope ps(net, BCROWN_PROF_ADAM, s);
+    launch_adam(R, net->K, bv, pl.U, dom->n_props, pl.lb_t, pl.best_lb, pl.a_cur, alpha, pl.ga, pl.ma, pl.va,
+                pl.b_cur, beta, pl.gb, pl.mb, pl.vb, cfg->lr_alpha * fac, cfg->lr_beta * fac, cfg->adam_beta1,
+                cfg->adam_beta2, cfg->adam_eps, bc1, bc2, na, nb, s);
+  }
+  BC_CHECK(run_bound(net, dom, batch, pl, cert ? BCROWN_CERTIFY : BCROWN_FP32, false, alpha, beta, lb_out, nullptr,
+                     nullptr, s));
+  BC_CUDA(cudaGetLastError());
+  return BCROWN_OK;
+}
+
+extern "C" int bcrown_root_bounds(bcrown_net* net, int n_props, const float* x_lo, const float* x_hi,
+                                  int alpha_rule, float alpha_value, int precision, float* l, float* u,
+                                  int32_t* unstable_count, void* stream) {
+  if (!net || n_props < 1 || !x_lo || !x_hi || (net->H > 0 && (!l || !u)))
+    return fail(BCROWN_ERR_ARG, "root_bounds: bad argument");
+  if (alpha_rule != BCROWN_ALPHA_ADAPTIVE && alpha_rule != BCROWN_ALPHA_FIXED)
+    return fail(BCROWN_ERR_ARG, "root_bounds: unknown alpha rule");
+  if (precision != BCROWN_FP32 && precision != BCROWN_CERTIFY)
+    return fail(BCROWN_ERR_ARG, "root_bounds: precision must be FP32 or CERTIFY");
+  std::lock_guard<std::mutex> g(net->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool cert = precision == BCROWN_CERTIFY;
+  const int L = net->L;
+  int maxrows = 2 * std::max(net->max_hidden, 1);
+  Plan pl;
+  BC_CHECK(make_plan(net, n_props, maxrows, cert, false, 0, 0, 0, pl));
+  bcrown_domain dom{n_props, x_lo, x_hi, l, u};
+  for (int top = 1; top <= L - 1; ++top) {
+    // tables and |W| M terms of layers < top are complete once l, u of those layers are.
+    build_tables(net, &dom, pl, s);
+    if (cert) {
+      long long hprev = top >= 2 ? net->hoff[top - 2] : -1;
+      // wm of layers 1..top-1 (recomputed: cheap)
+      for (int m = 1; m < top; ++m) {
+        long long hp = m >= 2 ? net->hoff[m - 2] : -1;
+        launch_absw_m(geom_of(net->ly[m - 1]), net->ly[m - 1].W, n_props, net->H, net->hoff[m - 1], hp, u, x_lo,
+                      x_hi, net->d[0], pl.wm, s);
+      }
+      (void)hprev;
+    }
+    const int d_top = net->d[top];
+    const int rows = 2 * d_top;
+    for (int p = 0; p < n_props; ++p) {
+      for (int q0 = 0; q0 < rows; q0 += pl.Rc) {
+        int Rc = std::min(pl.Rc, rows - q0);
+        launch_root_top(q0, Rc, d_top, net->ly[top - 1].b, pl.Lam, pl.cf, pl.cd, pl.E, s);
+        contract_bwd(net, top, Rc, pl.Lam, pl.Abuf[top - 1], s);
+        for (int m = top - 1; m >= 1; --m) {
+          const LayerDev& ly = net->ly[m - 1];
+          launch_relax_root(cert, Rc, p, net->H, net->d[m], net->hoff[m - 1], l, u, pl.tb, alpha_rule, alpha_value,
+                            pl.Abuf[m], pl.Lam, ly.b, pl.cf, pl.cd, pl.E, pl.wm, gamma_n(ly.terms_bwd), s);
+          contract_bwd(net, m, Rc, pl.Lam, pl.Abuf[m - 1], s);
+        }
+        launch_concretize_root(cert, q0, Rc, p, net->d[0], d_top, net->H, net->hoff[top - 1], x_lo, x_hi, pl.Abuf[0],
+                               pl.cf, pl.cd, pl.E, l, u, s);
+      }
+    }
+  }
+  build_tables(net, &dom, pl, s);
+  launch_copy_count(n_props, net->H, pl.U, unstable_count, s);
+  BC_CUDA(cudaGetLastError());
+  return BCROWN_OK;
+}
+
+extern "C" int bcrown_neuron_codes(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* batch,
+                                   int8_t* codes, void* stream) {
+  if (!net) return fail(BCROWN_ERR_ARG, "neuron_codes: null net");
+  BC_CHECK(check_domain(net, dom));
+  BC_CHECK(check_batch(batch));
+  if (batch->B == 0 || net->H == 0) return BCROWN_OK;
+  if (!codes) return fail(BCROWN_ERR_ARG, "neuron_codes: null output");
+  std::lock_guard<std::mutex> g(net->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  Plan pl;
+  int R = batch->B * net->K;
+  BC_CHECK(make_plan(net, dom->n_props, R, false, false, 0, 0, 0, pl));
+  build_tables(net, dom, pl, s);
+  RowsCtx c = ctx_of(net, dom, batch, pl, 0, R);
+  for (int i = 1; i < net->L; ++i) launch_codes(c, i, net->d[i], net->hoff[i - 1], net->H, codes, s);
+  BC_CUDA(cudaGetLastError());
+  return BCROWN_OK;
+}
+
+extern "C" int bcrown_batch_split(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* parent,
+                                  const uint8_t* pick_layer, const uint32_t* pick_idx, const float* alpha,
+                                  const float* beta, int32_t* c_prop, int32_t* c_off, int32_t* c_cnt,
+                                  uint8_t* c_layer, uint32_t* c_idx, int8_t* c_sign, int64_t* c_aoff,
+                                  float* c_alpha, float* c_beta, void* stream) {
+  if (!net) return fail(BCROWN_ERR_ARG, "batch_split: null net");
+  BC_CHECK(check_domain(net, dom));
+  BC_CHECK(check_batch(parent));
+  if (parent->B == 0) return BCROWN_OK;
+  if (!pick_layer || !pick_idx || !c_prop || !c_off || !c_cnt || !c_layer || !c_idx || !c_sign || !c_aoff)
+    return fail(BCROWN_ERR_ARG, "batch_split: null output");
+  std::lock_guard<std::mutex> g(net->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  Plan pl;
+  BC_CHECK(make_plan(net, dom->n_props, 1, false, false, 0, 0, 0, pl));
+  build_tables(net, dom, pl, s);
+  launch_split(view_of(parent), net->K, pl.U, dom->n_props, pick_layer, pick_idx, alpha, beta, c_prop, c_off, c_cnt,
+               c_aoff, c_layer, c_idx, c_sign, c_alpha, c_beta, net->status, s);
+  BC_CUDA(cudaGetLastError());
+  return BCROWN_OK;
+}

@@ -1,0 +1,939 @@
+// CUDA-core kernels: per-property tables, the relaxation epilogue, FP32 contractions
+// (dense and convolution), concretisation, the adjoint epilogue, projected Adam,
+// batch_split and the rigorous (CERTIFY) variants.
+#include <atomic>
+#include <cmath>
+
+#include "kernels_simt.cuh"
+#include "simt.cuh"
+
+namespace bcrown {
+
+std::atomic<long long> g_launches{0};
+
+// ----------------------------------------------------------------------------------------
+// Per-property tables from l, u: code, unstable rank, upper chord (Lemma 2.1)
+// ----------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_tables(int H, const float* __restrict__ l,
+                                                 const float* __restrict__ u, uint8_t* code,
+                                                 int32_t* rank, float* slope, float* icpt,
+                                                 int32_t* U) {
+  __shared__ int warp_tot[32];
+  __shared__ int running;
+  const int p = blockIdx.x;
+  const float* lp = l + (size_t)p * H;
+  const float* up = u + (size_t)p * H;
+  if (threadIdx.x == 0) running = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int base = 0; base < H; base += blockDim.x) {
+    int n = base + threadIdx.x;
+    float lv = 0.f, uv = 0.f;
+    bool un = false;
+    if (n < H) {
+      lv = lp[n];
+      uv = up[n];
+      un = (lv < 0.f) && (uv > 0.f);
+    }
+    unsigned m = __ballot_sync(0xffffffffu, un);
+    int pre = __popc(m & ((1u << lane) - 1u));
+    if (lane == 0) warp_tot[w] = __popc(m);
+    __syncthreads();
+    int woff = 0, tot = 0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+      if (q < w) woff += warp_tot[q];
+      tot += warp_tot[q];
+    }
+    if (n < H) {
+      size_t g = (size_t)p * H + n;
+      uint8_t c = un ? CODE_UNSTABLE : (lv >= 0.f ? CODE_ACTIVE : CODE_INACTIVE);
+      code[g] = c;
+      rank[g] = un ? running + woff + pre : -1;
+      float sl = 0.f, ic = 0.f;
+      if (un) {
+        sl = uv / (uv - lv);
+        ic = -sl * lv;
+      }
+      slope[g] = sl;
+      icpt[g] = ic;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) running += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) U[p] = running;
+}
+
+// M^(i)_m: bound on |h^(i)_m| (max(u,0) for hidden layers, max(|x_lo|,|x_hi|) at the input)
+__device__ __forceinline__ float hmax_hidden(float uv) { return fmaxf(uv, 0.f); }
+
+// wm[p][hoff_i + j] = sum_m |W^(i)_jm| M^(i-1)_m, rounded up (FP64), for the a priori
+// contraction error of layer i.  fc: direct dot product; conv: direct loops.
+__global__ void k_absw_m(LayerGeom g, const float* __restrict__ W, int P, int H, long long hoff_i,
+                         long long hoff_prev, const float* __restrict__ u, const float* __restrict__ x_lo,
+                         const float* __restrict__ x_hi, int d0, double* __restrict__ wm) {
+  long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long total = (long long)P * g.d_out;
+  if (id >= total) return;
+  int p = (int)(id / g.d_out);
+  int j = (int)(id - (long long)p * g.d_out);
+  auto M = [&](int m) -> double {
+    if (hoff_prev < 0) {
+      float a = fabsf(x_lo[(size_t)p * d0 + m]), b = fabsf(x_hi[(size_t)p * d0 + m]);
+      return (double)fmaxf(a, b);
+    }
+    return (double)hmax_hidden(u[(size_t)p * H + hoff_prev + m]);
+  };
+  double s = 0.0;
+  if (g.kind == BCROWN_LAYER_FC) {
+    const float* w = W + (size_t)j * g.d_in;
+    for (int m = 0; m < g.d_in; ++m) s = __dadd_ru(s, __dmul_ru(fabs((double)w[m]), M(m)));
+  } else {
+    int hw = g.out_h * g.out_w;
+    int co = j / hw, rem = j - co * hw, oy = rem / g.out_w, ox = rem - oy * g.out_w;
+    for (int ci = 0; ci < g.in_c; ++ci)
+      for (int ky = 0; ky < g.k; ++ky) {
+        int iy = oy * g.stride - g.pad + ky;
+        if (iy < 0 || iy >= g.in_h) continue;
+        for (int kx = 0; kx < g.k; ++kx) {
+          int ix = ox * g.stride - g.pad + kx;
+          if (ix < 0 || ix >= g.in_w) continue;
+          double w = fabs((double)W[(((size_t)co * g.in_c + ci) * g.k + ky) * g.k + kx]);
+          s = __dadd_ru(s, __dmul_ru(w, M((ci * g.in_h + iy) * g.in_w + ix)));
+        }
+      }
+  }
+  wm[(size_t)p * H + hoff_i + j] = s;
+}
+
+// ----------------------------------------------------------------------------------------
+// Top of the recursion: A^(L-1) = Wbar_k, c = bbar_k (Theorem 3.1 base case)
+// ----------------------------------------------------------------------------------------
+template <bool CERT>
+__global__ void __launch_bounds__(256) k_init_top(RowsCtx c, int dtop, const float* __restrict__ Wbar,
+                                                  const float* __restrict__ bbar, const double* __restrict__ bbar_rd,
+                                                  const float* __restrict__ Wbar_err, long long hoff_top,
+                                                  float* __restrict__ A, float* __restrict__ cf,
+                                                  double* __restrict__ cd, double* __restrict__ E) {
+  __shared__ double shd[32];
+  int rl = blockIdx.x;
+  int b, k, p;
+  bool ok = row_prop(c, rl, &b, &k, &p);
+  if (!ok) {
+    if (threadIdx.x == 0) flag(c.status, BCROWN_ERR_ARG);
+    p = 0;
+  }
+  const float* w = Wbar + (size_t)k * dtop;
+  double e = 0.0;
+  for (int j = threadIdx.x; j < dtop; j += blockDim.x) {
+    A[(size_t)rl * dtop + j] = w[j];
+    if (CERT) {
+      float M = hoff_top >= 0 ? hmax_hidden(c.u[(size_t)p * c.tb.H + hoff_top + j])
+                              : fmaxf(fabsf(c.x_lo[(size_t)p * dtop + j]), fabsf(c.x_hi[(size_t)p * dtop + j]));
+      e = __dadd_ru(e, __dmul_ru((double)Wbar_err[(size_t)k * dtop + j], (double)M));
+    }
+  }
+  if (CERT) {
+    e = block_dsum<2>(e, shd);
+    if (threadIdx.x == 0) {
+      cd[rl] = ok ? bbar_rd[k] : -INFINITY;
+      E[rl] = e;
+    }
+  } else if (threadIdx.x == 0) {
+    cf[rl] = ok ? bbar[k] : -INFINITY;
+  }
+}
+
+// ----------------------------------------------------------------------------------------
+// Relaxation + beta shift + bias (Eq. definition_D, definition_lowerb, definition_A):
+//   Lambda_j = A_j D_j + beta_j S_jj ;  c += Lambda_j b_j + A_j lambda_j
+// One block per row.  CERT: outward chord constants, FP64 round-down c, error terms.
+// ----------------------------------------------------------------------------------------
+template <bool CERT>
+__global__ void __launch_bounds__(256) k_relax(RowsCtx c, int layer, int d, long long hoff,
+                                               const float* __restrict__ Ain, float* __restrict__ Lam,
+                                               const float* __restrict__ bias, const float* __restrict__ alpha,
+                                               int64_t n_alpha, const float* __restrict__ beta, int64_t n_beta,
+                                               float* __restrict__ cf, double* __restrict__ cd,
+                                               double* __restrict__ E, const double* __restrict__ wm,
+                                               double gamma) {
+  __shared__ SplitSlot slots[BCROWN_MAX_SPLITS];
+  __shared__ int n_slots;
+  __shared__ float shf[32];
+  __shared__ double shd[32];
+  int rl = blockIdx.x;
+  int b, k, p;
+  bool ok = row_prop(c, rl, &b, &k, &p);
+  if (!ok) p = 0;
+  int ns = stage_splits(c, b, layer, d, slots, &n_slots);
+  int cnt = c.bt.split_cnt[b];
+  int Up = c.tb.U[p];
+  long long abase = c.bt.alpha_off[b] + (long long)k * Up;
+  long long bbase = (long long)c.bt.split_off[b] * c.K + (long long)k * cnt;
+  const float* a_row = Ain + (size_t)rl * d;
+  float* lam_row = Lam + (size_t)rl * d;
+  float acc = 0.f;
+  double accd = 0.0, e1 = 0.0, e2 = 0.0;
+  for (int j = threadIdx.x; j < d; j += blockDim.x) {
+    float a = a_row[j];
+    size_t n = (size_t)p * c.tb.H + hoff + j;
+    int s = 0;
+    float bet = 0.f;
+    for (int q = 0; q < ns; ++q)
+      if (slots[q].idx == j) {
+        s = slots[q].sign;
+        long long bi = bbase + slots[q].t;
+        if (bi >= 0 && bi < n_beta) bet = fmaxf(beta[bi], 0.f);
+        else flag(c.status, BCROWN_ERR_ARG);
+      }
+    float D = 0.f, lm = 0.f;
+    uint8_t code = c.tb.code[n];
+    if (s == -1) D = 1.f;
+    else if (s == 1) D = 0.f;
+    else if (code == CODE_ACTIVE) D = 1.f;
+    else if (code == CODE_INACTIVE) D = 0.f;
+    else if (a >= 0.f) {
+      long long ai = abase + c.tb.rank[n];
+      if (ai < 0 || ai >= n_alpha) {
+        flag(c.status, BCROWN_ERR_ARG);
+        D = 0.f;
+      } else {
+        D = fminf(fmaxf(alpha[ai], 0.f), 1.f);
+      }
+    } else {
+      if (CERT) {
+        float lv = c.l[n], uv = c.u[n];
+        D = __fdiv_ru(uv, __fsub_rd(uv, lv));
+        lm = __fmul_ru(D, -lv);
+      } else {
+        D = c.tb.slope[n];
+        lm = c.tb.icpt[n];
+      }
+    }
+    float L = fmaf(a, D, bet * (float)s);
+    lam_row[j] = L;
+    float bj = bias[j];
+    if (CERT) {
+      accd = __dadd_rd(accd, __dadd_rd((double)L * (double)bj, (double)a * (double)lm));
+      bool exact = (s == 0) && (D == 0.f || D == 1.f);
+      if (!exact) {
+        float zmax = fmaxf(fabsf(c.l[n]), fabsf(c.u[n]));
+        double er = __dadd_ru(__dmul_ru(fabs((double)L), 0x1p-23), 0x1p-140);
+        e1 = __dadd_ru(e1, __dmul_ru(er, (double)zmax));
+      }
+      e2 = __dadd_ru(e2, __dmul_ru(fabs((double)L), wm[n]));
+    } else {
+      acc = fmaf(L, bj, fmaf(a, lm, acc));
+    }
+  }
+  if (CERT) {
+    accd = block_dsum<1>(accd, shd);
+    e1 = block_dsum<2>(e1, shd);
+    e2 = block_dsum<2>(e2, shd);
+    if (threadIdx.x == 0) {
+      cd[rl] = __dadd_rd(cd[rl], accd);
+      E[rl] = __dadd_ru(E[rl], __dadd_ru(e1, __dmul_ru(gamma, e2)));
+    }
+  } else {
+    acc = block_sum(acc, shf);
+    if (threadIdx.x == 0) cf[rl] += acc;
+  }
+}
+
+// ----------------------------------------------------------------------------------------
+// FP32 SIMT GEMM  C[M,N] = A[M,K] * B[K,N] (+ bias[N]); row-major, any shape.
+// Each output is a sequential FMA chain over k (error <= gamma_K sum |a b|).
+// ----------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_sgemm(int M, int N, int K, const float* __restrict__ A, int lda,
+                                               const float* __restrict__ B, int ldb, float* __restrict__ C,
+                                               int ldc, const float* __restrict__ bias) {
+  constexpr int BM = 128, BN = 128, BK = 8;
+  __shared__ float As[2][BK][BM + 4];
+  __shared__ float Bs[2][BK][BN + 4];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+
+  float ra[4], rb[4];
+  auto load_regs = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int e = tid + q * 256;
+      int m = e >> 3, kk = e & 7;
+      int gm = m0 + m, gk = k0 + kk;
+      ra[q] = (gm < M && gk < K) ? A[(size_t)gm * lda + gk] : 0.f;
+      int kb = e >> 7, n = e & 127;
+      int gk2 = k0 + kb, gn = n0 + n;
+      rb[q] = (gk2 < K && gn < N) ? B[(size_t)gk2 * ldb + gn] : 0.f;
+    }
+  };
+  auto store_smem = [&](int buf) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int e = tid + q * 256;
+      As[buf][e & 7][e >> 3] = ra[q];
+      Bs[buf][e >> 7][e & 127] = rb[q];
+    }
+  };
+  int nk = (K + BK - 1) / BK;
+  load_regs(0);
+  store_smem(0);
+  __syncthreads();
+  for (int t = 0; t < nk; ++t) {
+    int buf = t & 1;
+    if (t + 1 < nk) load_regs((t + 1) * BK);
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      float av[8], bv[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) av[i] = As[buf][kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) bv[j] = Bs[buf][kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+    if (t + 1 < nk) store_smem(buf ^ 1);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    int gm = m0 + ty + 16 * i;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      int gn = n0 + tx + 16 * j;
+      if (gn < N) C[(size_t)gm * ldc + gn] = acc[i][j] + (bias ? bias[gn] : 0.f);
+    }
+  }
+}
+
+// Backward through a convolution (transposed convolution), one thread per output:
+//   Ain[r, ci, iy, ix] = sum_{co, ky, kx: iy = oy*s - p + ky, ix = ox*s - p + kx} Lam[r, co, oy, ox] W[co, ci, ky, kx]
+__global__ void k_conv_bwd(int R, LayerGeom g, const float* __restrict__ Lam, const float* __restrict__ W,
+                           float* __restrict__ Ain) {
+  long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long per = (long long)g.d_in;
+  if (id >= (long long)R * per) return;
+  int r = (int)(id / per);
+  int rem = (int)(id - (long long)r * per);
+  int hw = g.in_h * g.in_w;
+  int ci = rem / hw, pos = rem - ci * hw, iy = pos / g.in_w, ix = pos - iy * g.in_w;
+  const float* lr = Lam + (size_t)r * g.d_out;
+  float s = 0.f;
+  for (int ky = 0; ky < g.k; ++ky) {
+    int ty = iy + g.pad - ky;
+    if (ty < 0 || ty % g.stride) continue;
+    int oy = ty / g.stride;
+    if (oy >= g.out_h) continue;
+    for (int kx = 0; kx < g.k; ++kx) {
+      int tx = ix + g.pad - kx;
+      if (tx < 0 || tx % g.stride) continue;
+      int ox = tx / g.stride;
+      if (ox >= g.out_w) continue;
+      const float* lp = lr + (size_t)oy * g.out_w + ox;
+      const float* wp = W + ((size_t)ci * g.k + ky) * g.k + kx;
+      for (int co = 0; co < g.out_c; ++co)
+        s = fmaf(lp[(size_t)co * g.out_h * g.out_w], wp[(size_t)co * g.in_c * g.k * g.k], s);
+    }
+  }
+  Ain[id] = s;
+}
+
+// Forward convolution (adjoint pass), one thread per output:
+//   Z[r, co, oy, ox] = b[co] + sum_{ci, ky, kx} W[co, ci, ky, kx] h[r, ci, oy*s - p + ky, ox*s - p + kx]
+__global__ void k_conv_fwd(int R, LayerGeom g, const float* __restrict__ h, const float* __restrict__ W,
+                           const float* __restrict__ bias, float* __restrict__ Z) {
+  long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long per = (long long)g.d_out;
+  if (id >= (long long)R * per) return;
+  int r = (int)(id / per);
+  int rem = (int)(id - (long long)r * per);
+  int hw = g.out_h * g.out_w;
+  int co = rem / hw, pos = rem - co * hw, oy = pos / g.out_w, ox = pos - oy * g.out_w;
+  const float* hr = h + (size_t)r * g.d_in;
+  float s = 0.f;
+  for (int ci = 0; ci < g.in_c; ++ci)
+    for (int ky = 0; ky < g.k; ++ky) {
+      int iy = oy * g.stride - g.pad + ky;
+      if (iy < 0 || iy >= g.in_h) continue;
+      for (int kx = 0; kx < g.k; ++kx) {
+        int ix = ox * g.stride - g.pad + kx;
+        if (ix < 0 || ix >= g.in_w) continue;
+        s = fmaf(W[(((size_t)co * g.in_c + ci) * g.k + ky) * g.k + kx], hr[((size_t)ci * g.in_h + iy) * g.in_w + ix], s);
+      }
+    }
+  Z[id] = s + bias[rem];
+}
+
+// ----------------------------------------------------------------------------------------
+// Concretisation over the box (Eq. beta_crown_lp, Hoelder for an L-infinity box):
+//   lb = c + sum_m min(A_m x_lo_m, A_m x_hi_m)
+// ----------------------------------------------------------------------------------------
+template <bool CERT>
+__global__ void __launch_bounds__(256) k_concretize(RowsCtx c, int d0, const float* __restrict__ A0,
+                                                    const float* __restrict__ cf, const double* __restrict__ cd,
+                                                    const double* __restrict__ E, float* __restrict__ lb) {
+  __shared__ float shf[32];
+  __shared__ double shd[32];
+  int rl = blockIdx.x;
+  int b, k, p;
+  if (!row_prop(c, rl, &b, &k, &p)) p = 0;
+  const float* a = A0 + (size_t)rl * d0;
+  const float* xl = c.x_lo + (size_t)p * d0;
+  const float* xh = c.x_hi + (size_t)p * d0;
+  float s = 0.f;
+  double sd = 0.0;
+  for (int m = threadIdx.x; m < d0; m += blockDim.x) {
+    float am = a[m];
+    if (CERT) {
+      double v = fmin((double)am * (double)xl[m], (double)am * (double)xh[m]);
+      sd = __dadd_rd(sd, v);
+    } else {
+      s += fminf(am * xl[m], am * xh[m]);
+    }
+  }
+  float out;
+  if (CERT) {
+    sd = block_dsum<1>(sd, shd);
+    out = __double2float_rd(__dsub_rd(__dadd_rd(cd[rl], sd), E[rl]));
+  } else {
+    s = block_sum(s, shf);
+    out = cf[rl] + s;
+  }
+  if (threadIdx.x == 0) {
+    if (!isfinite(out)) {
+      flag(c.status, BCROWN_ERR_NONFINITE);
+      out = -INFINITY;
+    }
+    lb[c.r0 + rl] = out;
+  }
+}
+
+// x*: the box corner minimising A^(0) x (x_lo where A^(0)_m >= 0)
+__global__ void k_xstar(RowsCtx c, int d0, const float* __restrict__ A0, float* __restrict__ h0) {
+  long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= (long long)c.R * d0) return;
+  int rl = (int)(id / d0);
+  int m = (int)(id - (long long)rl * d0);
+  int b, k, p;
+  if (!row_prop(c, rl, &b, &k, &p)) p = 0;
+  h0[id] = A0[id] >= 0.f ? c.x_lo[(size_t)p * d0 + m] : c.x_hi[(size_t)p * d0 + m];
+}
+
+// ----------------------------------------------------------------------------------------
+// Adjoint epilogue of hidden layer i: zhat = Z (+ bias already added); gradients
+//   dalpha_j = A_j zhat_j (alpha in use), dbeta_j = S_jj zhat_j ; then h = D zhat + lambda.
+// ----------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_fwd_epi(RowsCtx c, int layer, int d, long long hoff,
+                                                 float* __restrict__ Z, const float* __restrict__ Ai,
+                                                 const float* __restrict__ alpha, int64_t n_alpha,
+                                                 float* __restrict__ dalpha, float* __restrict__ dbeta,
+                                                 int64_t n_beta) {
+  __shared__ SplitSlot slots[BCROWN_MAX_SPLITS];
+  __shared__ int n_slots;
+  int rl = blockIdx.x;
+  int b, k, p;
+  if (!row_prop(c, rl, &b, &k, &p)) p = 0;
+  int ns = stage_splits(c, b, layer, d, slots, &n_slots);
+  int cnt = c.bt.split_cnt[b];
+  int Up = c.tb.U[p];
+  long long abase = c.bt.alpha_off[b] + (long long)k * Up;
+  long long bbase = (long long)c.bt.split_off[b] * c.K + (long long)k * cnt;
+  float* z_row = Z + (size_t)rl * d;
+  const float* a_row = Ai + (size_t)rl * d;
+  for (int j = threadIdx.x; j < d; j += blockDim.x) {
+    float z = z_row[j];
+    float a = a_row[j];
+    size_t n = (size_t)p * c.tb.H + hoff + j;
+    int s = 0, t = -1;
+    for (int q = 0; q < ns; ++q)
+      if (slots[q].idx == j) {
+        s = slots[q].sign;
+        t = slots[q].t;
+      }
+    uint8_t code = c.tb.code[n];
+    float D = 0.f, lm = 0.f;
+    long long ai = -1;
+    if (code == CODE_UNSTABLE) {
+      ai = abase + c.tb.rank[n];
+      if (ai < 0 || ai >= n_alpha) {
+        flag(c.status, BCROWN_ERR_ARG);
+        ai = -1;
+      }
+    }
+    if (s == -1) D = 1.f;
+    else if (s == 1) D = 0.f;
+    else if (code == CODE_ACTIVE) D = 1.f;
+    else if (code == CODE_INACTIVE) D = 0.f;
+    else if (a >= 0.f) D = ai >= 0 ? fminf(fmaxf(alpha[ai], 0.f), 1.f) : 0.f;
+    else {
+      D = c.tb.slope[n];
+      lm = c.tb.icpt[n];
+    }
+    if (ai >= 0) dalpha[ai] = (s == 0 && a >= 0.f) ? a * z : 0.f;
+    if (s != 0) {
+      long long bi = bbase + t;
+      if (bi >= 0 && bi < n_beta) dbeta[bi] = (float)s * z;
+      else flag(c.status, BCROWN_ERR_ARG);
+    }
+    z_row[j] = fmaf(D, z, lm);
+  }
+}
+
+// ----------------------------------------------------------------------------------------
+// Projected Adam ascent with best-row tracking (Eq. opt_alpha_beta; Appendix C.1).
+// One block per row; the row's alpha block and beta block.
+// ----------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_adam(int R, int K, BatchView bt, const int32_t* __restrict__ U,
+                                              int P, const float* __restrict__ lb_t, float* __restrict__ best_lb,
+                                              float* __restrict__ a_cur, float* __restrict__ a_best,
+                                              const float* __restrict__ ga, float* __restrict__ ma,
+                                              float* __restrict__ va, float* __restrict__ b_cur,
+                                              float* __restrict__ b_best, const float* __restrict__ gb,
+                                              float* __restrict__ mb, float* __restrict__ vb, float lr_a,
+                                              float lr_b, float beta1, float beta2, float eps, float bc1,
+                                              float bc2, int64_t n_alpha, int64_t n_beta) {
+  int r = blockIdx.x;
+  int b = r / K, k = r - b * K;
+  int p = bt.prop_of[b];
+  if (p < 0 || p >= P) return;
+  float cur = lb_t[r], best = best_lb[r];
+  bool improved = cur > best;
+  int Up = U[p];
+  long long abase = bt.alpha_off[b] + (long long)k * Up;
+  for (int t = threadIdx.x; t < Up; t += blockDim.x) {
+    long long i = abase + t;
+    if (i < 0 || i >= n_alpha) break;
+    float th = a_cur[i];
+    if (improved) a_best[i] = th;
+    float g = ga[i];
+    float m = beta1 * ma[i] + (1.f - beta1) * g;
+    float v = beta2 * va[i] + (1.f - beta2) * g * g;
+    ma[i] = m;
+    va[i] = v;
+    th += lr_a * (m / bc1) / (sqrtf(v / bc2) + eps);
+    a_cur[i] = fminf(fmaxf(th, 0.f), 1.f);
+  }
+  int cnt = bt.split_cnt[b];
+  long long bbase = (long long)bt.split_off[b] * K + (long long)k * cnt;
+  for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+    long long i = bbase + t;
+    if (i < 0 || i >= n_beta) break;
+    float th = b_cur[i];
+    if (improved) b_best[i] = th;
+    float g = gb[i];
+    float m = beta1 * mb[i] + (1.f - beta1) * g;
+    float v = beta2 * vb[i] + (1.f - beta2) * g * g;
+    mb[i] = m;
+    vb[i] = v;
+    th += lr_b * (m / bc1) / (sqrtf(v / bc2) + eps);
+    b_cur[i] = fmaxf(th, 0.f);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && improved) best_lb[r] = cur;
+}
+
+// ----------------------------------------------------------------------------------------
+// Neuron codes per (row, hidden neuron): split overrides stability
+// ----------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_codes(RowsCtx c, int layer, int d, long long hoff, int H,
+                                               int8_t* __restrict__ out) {
+  __shared__ SplitSlot slots[BCROWN_MAX_SPLITS];
+  __shared__ int n_slots;
+  int rl = blockIdx.x;
+  int b, k, p;
+  if (!row_prop(c, rl, &b, &k, &p)) p = 0;
+  int ns = stage_splits(c, b, layer, d, slots, &n_slots);
+  for (int j = threadIdx.x; j < d; j += blockDim.x) {
+    int s = 0;
+    for (int q = 0; q < ns; ++q)
+      if (slots[q].idx == j) s = slots[q].sign;
+    uint8_t code = c.tb.code[(size_t)p * c.tb.H + hoff + j];
+    int8_t v = (int8_t)code;
+    if (s == -1) v = CODE_SPLIT_POS;
+    if (s == 1) v = CODE_SPLIT_NEG;
+    out[(size_t)(c.r0 + rl) * H + hoff + j] = v;
+  }
+}
+
+// ----------------------------------------------------------------------------------------
+// batch_split (Algorithm 1)
+// ----------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_split_scan(BatchView bt, int K, const int32_t* __restrict__ U, int P,
+                                                     int32_t* c_prop, int32_t* c_off, int32_t* c_cnt,
+                                                     int64_t* c_aoff, int* status) {
+  __shared__ long long w_s[32], w_a[32];
+  __shared__ long long run_s, run_a;
+  if (threadIdx.x == 0) {
+    run_s = 0;
+    run_a = 0;
+  }
+  __syncthreads();
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int base = 0; base < bt.B; base += blockDim.x) {
+    int b = base + threadIdx.x;
+    long long ns = 0, na = 0;
+    int p = 0, cnt = 0;
+    if (b < bt.B) {
+      p = bt.prop_of[b];
+      cnt = bt.split_cnt[b];
+      if (p < 0 || p >= P || cnt < 0 || cnt + 1 > BCROWN_MAX_SPLITS) {
+        flag(status, BCROWN_ERR_ARG);
+        p = 0;
+        cnt = 0;
+      }
+      ns = 2LL * (cnt + 1);
+      na = 2LL * (long long)U[p] * K;
+    }
+    // inclusive warp scans
+    long long xs = ns, xa = na;
+    for (int o = 1; o < 32; o <<= 1) {
+      long long ys = __shfl_up_sync(0xffffffffu, xs, o), ya = __shfl_up_sync(0xffffffffu, xa, o);
+      if (lane >= o) {
+        xs += ys;
+        xa += ya;
+      }
+    }
+    if (lane == 31) {
+      w_s[w] = xs;
+      w_a[w] = xa;
+    }
+    __syncthreads();
+    long long os = 0, oa = 0, ts = 0, ta = 0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+      if (q < w) {
+        os += w_s[q];
+        oa += w_a[q];
+      }
+      ts += w_s[q];
+      ta += w_a[q];
+    }
+    if (b < bt.B) {
+      long long s0 = run_s + os + xs - ns, a0 = run_a + oa + xa - na;
+      for (int h = 0; h < 2; ++h) {
+        c_prop[2 * b + h] = p;
+        c_cnt[2 * b + h] = cnt + 1;
+        c_off[2 * b + h] = (int32_t)(s0 + h * (cnt + 1));
+        c_aoff[2 * b + h] = a0 + h * (long long)U[p] * K;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      run_s += ts;
+      run_a += ta;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(128) k_split_copy(BatchView bt, int K, const int32_t* __restrict__ U, int P,
+                                                    const uint8_t* __restrict__ pick_layer,
+                                                    const uint32_t* __restrict__ pick_idx,
+                                                    const float* __restrict__ alpha, const float* __restrict__ beta,
+                                                    const int32_t* __restrict__ c_off,
+                                                    const int64_t* __restrict__ c_aoff, uint8_t* c_layer,
+                                                    uint32_t* c_idx, int8_t* c_sign, float* c_alpha,
+                                                    float* c_beta) {
+  int child = blockIdx.x;
+  int b = child >> 1, h = child & 1;
+  int p = bt.prop_of[b];
+  int cnt = bt.split_cnt[b];
+  if (p < 0 || p >= P || cnt < 0 || cnt + 1 > BCROWN_MAX_SPLITS) return;
+  int po = bt.split_off[b];
+  int co = c_off[child];
+  for (int t = threadIdx.x; t <= cnt; t += blockDim.x) {
+    if (t < cnt) {
+      c_layer[co + t] = bt.split_layer[po + t];
+      c_idx[co + t] = bt.split_idx[po + t];
+      c_sign[co + t] = bt.split_sign[po + t];
+    } else {
+      c_layer[co + t] = pick_layer[b];
+      c_idx[co + t] = pick_idx[b];
+      c_sign[co + t] = h == 0 ? (int8_t)-1 : (int8_t)1;
+    }
+  }
+  long long n = (long long)U[p] * K;
+  const float* src = alpha + bt.alpha_off[b];
+  float* dst = c_alpha + c_aoff[child];
+  for (long long t = threadIdx.x; t < n; t += blockDim.x) dst[t] = src[t];
+  for (int k = 0; k < K; ++k) {
+    const float* bs = beta + (long long)po * K + (long long)k * cnt;
+    float* bd = c_beta + (long long)co * K + (long long)k * (cnt + 1);
+    for (int t = threadIdx.x; t <= cnt; t += blockDim.x) bd[t] = t < cnt ? bs[t] : 0.f;
+  }
+}
+
+// ----------------------------------------------------------------------------------------
+// Root bounds: rows (j, sign) for hidden layer `top`; the top of the recursion is
+// Lambda = +-e_j at layer `top`, c = +-b_j.
+// ----------------------------------------------------------------------------------------
+__global__ void k_root_top(int q0, int Rc, int d_top, const float* __restrict__ b_top, float* __restrict__ Lam,
+                           float* __restrict__ cf, double* __restrict__ cd, double* __restrict__ E) {
+  long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= (long long)Rc * d_top) return;
+  int rl = (int)(id / d_top);
+  int j = (int)(id - (long long)rl * d_top);
+  int q = q0 + rl;
+  int jj = q < d_top ? q : q - d_top;
+  float sg = q < d_top ? 1.f : -1.f;
+  Lam[id] = (j == jj) ? sg : 0.f;
+  if (j == 0) {
+    float bv = sg * b_top[jj];
+    if (cf) cf[rl] = bv;
+    if (cd) cd[rl] = (double)bv;
+    if (E) E[rl] = 0.0;
+  }
+}
+
+// Relaxation for root rows: no splits, alpha' from the rule.
+template <bool CERT>
+__global__ void __launch_bounds__(256) k_relax_root(int Rc, int p, int H, int d, long long hoff,
+                                                    const float* __restrict__ l, const float* __restrict__ u,
+                                                    Tables tb, int rule, float rule_value,
+                                                    const float* __restrict__ Ain, float* __restrict__ Lam,
+                                                    const float* __restrict__ bias, float* __restrict__ cf,
+                                                    double* __restrict__ cd, double* __restrict__ E,
+                                                    const double* __restrict__ wm, double gamma) {
+  __shared__ float shf[32];
+  __shared__ double shd[32];
+  int rl = blockIdx.x;
+  const float* a_row = Ain + (size_t)rl * d;
+  float* lam_row = Lam + (size_t)rl * d;
+  float acc = 0.f;
+  double accd = 0.0, e1 = 0.0, e2 = 0.0;
+  for (int j = threadIdx.x; j < d; j += blockDim.x) {
+    float a = a_row[j];
+    size_t n = (size_t)p * H + hoff + j;
+    uint8_t code = tb.code[n];
+    float lv = l[n], uv = u[n];
+    float D = 0.f, lm = 0.f;
+    if (code == CODE_ACTIVE) D = 1.f;
+    else if (code == CODE_INACTIVE) D = 0.f;
+    else if (a >= 0.f) D = rule == BCROWN_ALPHA_ADAPTIVE ? (uv >= -lv ? 1.f : 0.f) : rule_value;
+    else if (CERT) {
+      D = __fdiv_ru(uv, __fsub_rd(uv, lv));
+      lm = __fmul_ru(D, -lv);
+    } else {
+      D = tb.slope[n];
+      lm = tb.icpt[n];
+    }
+    float L = a * D;
+    lam_row[j] = L;
+    float bj = bias[j];
+    if (CERT) {
+      accd = __dadd_rd(accd, __dadd_rd((double)L * (double)bj, (double)a * (double)lm));
+      if (!(D == 0.f || D == 1.f)) {
+        float zmax = fmaxf(fabsf(lv), fabsf(uv));
+        double er = __dadd_ru(__dmul_ru(fabs((double)L), 0x1p-23), 0x1p-140);
+        e1 = __dadd_ru(e1, __dmul_ru(er, (double)zmax));
+      }
+      e2 = __dadd_ru(e2, __dmul_ru(fabs((double)L), wm[n]));
+    } else {
+      acc = fmaf(L, bj, fmaf(a, lm, acc));
+    }
+  }
+  if (CERT) {
+    accd = block_dsum<1>(accd, shd);
+    e1 = block_dsum<2>(e1, shd);
+    e2 = block_dsum<2>(e2, shd);
+    if (threadIdx.x == 0) {
+      cd[rl] = __dadd_rd(cd[rl], accd);
+      E[rl] = __dadd_ru(E[rl], __dadd_ru(e1, __dmul_ru(gamma, e2)));
+    }
+  } else {
+    acc = block_sum(acc, shf);
+    if (threadIdx.x == 0) cf[rl] += acc;
+  }
+}
+
+template <bool CERT>
+__global__ void __launch_bounds__(256) k_concretize_root(int q0, int Rc, int p, int d0, int d_top, int H,
+                                                         long long hoff_top, const float* __restrict__ x_lo,
+                                                         const float* __restrict__ x_hi,
+                                                         const float* __restrict__ A0, const float* __restrict__ cf,
+                                                         const double* __restrict__ cd, const double* __restrict__ E,
+                                                         float* __restrict__ l, float* __restrict__ u) {
+  __shared__ float shf[32];
+  __shared__ double shd[32];
+  int rl = blockIdx.x;
+  const float* a = A0 + (size_t)rl * d0;
+  const float* xl = x_lo + (size_t)p * d0;
+  const float* xh = x_hi + (size_t)p * d0;
+  float s = 0.f;
+  double sd = 0.0;
+  for (int m = threadIdx.x; m < d0; m += blockDim.x) {
+    float am = a[m];
+    if (CERT) sd = __dadd_rd(sd, fmin((double)am * (double)xl[m], (double)am * (double)xh[m]));
+    else s += fminf(am * xl[m], am * xh[m]);
+  }
+  float out;
+  if (CERT) {
+    sd = block_dsum<1>(sd, shd);
+    out = __double2float_rd(__dsub_rd(__dadd_rd(cd[rl], sd), E[rl]));
+  } else {
+    s = block_sum(s, shf);
+    out = cf[rl] + s;
+  }
+  if (threadIdx.x == 0) {
+    int q = q0 + rl;
+    if (q < d_top) l[(size_t)p * H + hoff_top + q] = isfinite(out) ? out : -INFINITY;
+    else u[(size_t)p * H + hoff_top + (q - d_top)] = isfinite(out) ? -out : INFINITY;
+  }
+}
+
+__global__ void k_count_unstable(int P, int H, const int32_t* __restrict__ U, int32_t* __restrict__ out) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < P) out[p] = U[p];
+}
+
+// ----------------------------------------------------------------------------------------
+// Host launchers
+// ----------------------------------------------------------------------------------------
+void launch_tables(int P, int H, const float* l, const float* u, Tables& t, uint8_t* code, int32_t* rank,
+                   float* slope, float* icpt, int32_t* U, cudaStream_t s) {
+  if (P > 0) { k_tables<<<P, 1024, 0, s>>>(H, l, u, code, rank, slope, icpt, U); ++g_launches; }
+  t.P = P;
+  t.H = H;
+  t.code = code;
+  t.rank = rank;
+  t.slope = slope;
+  t.icpt = icpt;
+  t.U = U;
+}
+
+void launch_absw_m(const LayerGeom& g, const float* W, int P, int H, long long hoff_i, long long hoff_prev,
+                   const float* u, const float* x_lo, const float* x_hi, int d0, double* wm, cudaStream_t s) {
+  long long n = (long long)P * g.d_out;
+  if (n > 0) { k_absw_m<<<grid1d(n, 128), 128, 0, s>>>(g, W, P, H, hoff_i, hoff_prev, u, x_lo, x_hi, d0, wm); ++g_launches; }
+}
+
+void launch_init_top(bool cert, const RowsCtx& c, int dtop, const bcrown_net* net, long long hoff_top, float* A,
+                     float* cf, double* cd, double* E, cudaStream_t s) {
+  if (c.R <= 0) return;
+  if (cert)
+    { k_init_top<true><<<c.R, 256, 0, s>>>(c, dtop, net->Wbar, net->bbar, net->bbar_rd, net->Wbar_err, hoff_top, A,
+                                         cf, cd, E); ++g_launches; }
+  else
+    { k_init_top<false><<<c.R, 256, 0, s>>>(c, dtop, net->Wbar, net->bbar, net->bbar_rd, net->Wbar_err, hoff_top,
+                                          A, cf, cd, E); ++g_launches; }
+}
+
+void launch_relax(bool cert, const RowsCtx& c, int layer, int d, long long hoff, const float* Ain, float* Lam,
+                  const float* bias, const float* alpha, int64_t n_alpha, const float* beta, int64_t n_beta, float* cf,
+                  double* cd, double* E, const double* wm, double gamma, cudaStream_t s) {
+  if (c.R <= 0) return;
+  if (cert)
+    { k_relax<true><<<c.R, 256, 0, s>>>(c, layer, d, hoff, Ain, Lam, bias, alpha, n_alpha, beta, n_beta, cf, cd, E, wm, gamma); ++g_launches; }
+  else
+    { k_relax<false><<<c.R, 256, 0, s>>>(c, layer, d, hoff, Ain, Lam, bias, alpha, n_alpha, beta, n_beta, cf, cd, E, wm, gamma); ++g_launches; }
+}
+
+void launch_sgemm(int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C, int ldc,
+                  const float* bias, cudaStream_t s) {
+  if (M <= 0 || N <= 0) return;
+  dim3 grid((N + 127) / 128, (M + 127) / 128);
+  { k_sgemm<<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias); ++g_launches; }
+}
+
+void launch_conv_bwd(int R, const LayerGeom& g, const float* Lam, const float* W, float* Ain, cudaStream_t s) {
+  long long n = (long long)R * g.d_in;
+  if (n > 0) { k_conv_bwd<<<grid1d(n, 256), 256, 0, s>>>(R, g, Lam, W, Ain); ++g_launches; }
+}
+
+void launch_conv_fwd(int R, const LayerGeom& g, const float* h, const float* W, const float* bias, float* Z,
+                     cudaStream_t s) {
+  long long n = (long long)R * g.d_out;
+  if (n > 0) { k_conv_fwd<<<grid1d(n, 256), 256, 0, s>>>(R, g, h, W, bias, Z); ++g_launches; }
+}
+
+void launch_concretize(bool cert, const RowsCtx& c, int d0, const float* A0, const float* cf, const double* cd,
+                       const double* E, float* lb, cudaStream_t s) {
+  if (c.R <= 0) return;
+  if (cert) { k_concretize<true><<<c.R, 256, 0, s>>>(c, d0, A0, cf, cd, E, lb); ++g_launches; }
+  else { k_concretize<false><<<c.R, 256, 0, s>>>(c, d0, A0, cf, cd, E, lb); ++g_launches; }
+}
+
+void launch_xstar(const RowsCtx& c, int d0, const float* A0, float* h0, cudaStream_t s) {
+  long long n = (long long)c.R * d0;
+  if (n > 0) { k_xstar<<<grid1d(n, 256), 256, 0, s>>>(c, d0, A0, h0); ++g_launches; }
+}
+
+void launch_fwd_epi(const RowsCtx& c, int layer, int d, long long hoff, float* Z, const float* Ai,
+                    const float* alpha, int64_t n_alpha, float* dalpha, float* dbeta, int64_t n_beta,
+                    cudaStream_t s) {
+  if (c.R <= 0) return;
+  { k_fwd_epi<<<c.R, 256, 0, s>>>(c, layer, d, hoff, Z, Ai, alpha, n_alpha, dalpha, dbeta, n_beta); ++g_launches; }
+}
+
+void launch_adam(int R, int K, const BatchView& bt, const int32_t* U, int P, const float* lb_t, float* best_lb,
+                 float* a_cur, float* a_best, const float* ga, float* ma, float* va, float* b_cur, float* b_best,
+                 const float* gb, float* mb, float* vb, float lr_a, float lr_b, float beta1, float beta2, float eps,
+                 float bc1, float bc2, int64_t n_alpha, int64_t n_beta, cudaStream_t s) {
+  if (R <= 0) return;
+  { k_adam<<<R, 128, 0, s>>>(R, K, bt, U, P, lb_t, best_lb, a_cur, a_best, ga, ma, va, b_cur, b_best, gb, mb, vb, lr_a,
+                           lr_b, beta1, beta2, eps, bc1, bc2, n_alpha, n_beta); ++g_launches; }
+}
+
+void launch_codes(const RowsCtx& c, int layer, int d, long long hoff, int H, int8_t* out, cudaStream_t s) {
+  if (c.R > 0) { k_codes<<<c.R, 256, 0, s>>>(c, layer, d, hoff, H, out); ++g_launches; }
+}
+
+void launch_split(const BatchView& bt, int K, const int32_t* U, int P, const uint8_t* pick_layer,
+                  const uint32_t* pick_idx, const float* alpha, const float* beta, int32_t* c_prop, int32_t* c_off,
+                  int32_t* c_cnt, int64_t* c_aoff, uint8_t* c_layer, uint32_t* c_idx, int8_t* c_sign,
+                  float* c_alpha, float* c_beta, int* status, cudaStream_t s) {
+  if (bt.B <= 0) return;
+  { k_split_scan<<<1, 1024, 0, s>>>(bt, K, U, P, c_prop, c_off, c_cnt, c_aoff, status); ++g_launches; }
+  { k_split_copy<<<2 * bt.B, 128, 0, s>>>(bt, K, U, P, pick_layer, pick_idx, alpha, beta, c_off, c_aoff, c_layer, c_idx,
+                                        c_sign, c_alpha, c_beta); ++g_launches; }
+}
+
+void launch_root_top(int q0, int Rc, int d_top, const float* b_top, float* Lam, float* cf, double* cd, double* E,
+                     cudaStream_t s) {
+  long long n = (long long)Rc * d_top;
+  if (n > 0) { k_root_top<<<grid1d(n, 256), 256, 0, s>>>(q0, Rc, d_top, b_top, Lam, cf, cd, E); ++g_launches; }
+}
+
+void launch_relax_root(bool cert, int Rc, int p, int H, int d, long long hoff, const float* l, const float* u,
+                       const Tables& tb, int rule, float rule_value, const float* Ain, float* Lam, const float* bias,
+                       float* cf, double* cd, double* E, const double* wm, double gamma, cudaStream_t s) {
+  if (Rc <= 0) return;
+  if (cert)
+    { k_relax_root<true><<<Rc, 256, 0, s>>>(Rc, p, H, d, hoff, l, u, tb, rule, rule_value, Ain, Lam, bias, cf, cd, E,
+                                          wm, gamma); ++g_launches; }
+  else
+    { k_relax_root<false><<<Rc, 256, 0, s>>>(Rc, p, H, d, hoff, l, u, tb, rule, rule_value, Ain, Lam, bias, cf, cd, E,
+                                           wm, gamma); ++g_launches; }
+}
+
+void launch_concretize_root(bool cert, int q0, int Rc, int p, int d0, int d_top, int H, long long hoff_top,
+                            const float* x_lo, const float* x_hi, const float* A0, const float* cf, const double* cd,
+                            const double* E, float* l, float* u, cudaStream_t s) {
+  if (Rc <= 0) return;
+  if (cert)
+    { k_concretize_root<true><<<Rc, 256, 0, s>>>(q0, Rc, p, d0, d_top, H, hoff_top, x_lo, x_hi, A0, cf, cd, E, l, u); ++g_launches; }
+  else
+    { k_concretize_root<false><<<Rc, 256, 0, s>>>(q0, Rc, p, d0, d_top, H, hoff_top, x_lo, x_hi, A0, cf, cd, E, l, u); ++g_launches; }
+}
+
+__global__ void k_fill(float* p, long long n, float v) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+void launch_fill(float* p, long long n, float v, cudaStream_t s) {
+  if (n > 0) { k_fill<<<grid1d(n, 256), 256, 0, s>>>(p, n, v); ++g_launches; }
+}
+
+void launch_copy_count(int P, int H, const int32_t* U, int32_t* out, cudaStream_t s) {
+  if (P > 0 && out) { k_count_unstable<<<grid1d(P, 128), 128, 0, s>>>(P, H, U, out); ++g_launches; }
+}
+
+}  // namespace bcrown
