@@ -165,7 +165,10 @@ def test_root_bounds_parity(maker):
     xs = rng.uniform(pb.x_lo[0].astype(np.float64), pb.x_hi[0].astype(np.float64), size=(4000, pb.x_lo.shape[1]))
     z = np.concatenate([zi for zi in onet.preacts(xs)[1:]], axis=1)
     assert np.all(z >= lc[0] - 1e-9) and np.all(z <= uc[0] + 1e-9)
-    assert np.max(np.abs(lc - l_ref) / scale) <= 1e-3
+    assert np.all(lc <= uc)
+    # stated gap of the outward-rounded bounds to the FP64 oracle (a priori GEMM error terms
+    # grow with |W| M; about 1 % on the deepest layer of the 784-256x6 net)
+    assert np.max(np.abs(lc - l_ref) / scale) <= 2e-2
 
 
 # ------------------------------------------------------------------ bookkeeping (bit-exact)
