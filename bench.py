@@ -236,28 +236,34 @@ def main():
     widths = pb.widths
     rows = hbatch.B * pb.K
     f_row = algorithmic_flops_per_row_pass(widths)
-    if prof[5][1] > 0:
-        cls = 5
-        flops = rows * 2 * f_row * prof[5][1]
-    else:
-        cls = 0
-        # per step: iters x (backward + forward) + one certify backward
-        flops = rows * f_row * (2 * cfg.iters + 1) * args.steps
-    ms, nl = prof[cls]
-    sm_mhz = clk.get("sm_mhz") or 1432.0
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-    if cls == 5:
-        peak = peaks.get("bf16_tflops_sustained", 1700.0)
-        bound, src = "tensor", "of measured (bf16 sustained)"
+    sm_mhz = clk.get("sm_mhz") or 1432.0
+    if prof[5][1] > 0:
+        # fused iteration kernel: bound by the alpha/beta and Adam state it must stream
+        ms, nl = prof[5]
+        U = np.array([len(u) for u in unst])[hbatch.prop_of]
+        bytes_per_launch = float(np.sum(pb.K * (24 * U + 24 * hbatch.split_cnt.astype(np.int64) + 8)))
+        achieved = bytes_per_launch * nl / (ms / 1e3) / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        tflops = rows * 2 * f_row * nl / (ms / 1e3) / 1e12
+        tpeak = peaks.get("bf16_tflops_sustained", 1700.0)
+        roof = {"bound": "hbm", "kernel": "k_fused (bound + adjoint + projected Adam, one launch per iteration)",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)",
+                "algorithmic_bytes_per_launch": bytes_per_launch,
+                "bytes_model": "per row: 24 B x unstable neurons (alpha, m, v read+write) + 24 B x splits + 8 B",
+                "tensor_tflops": tflops, "tensor_frac": tflops / tpeak,
+                "kernel_ms_per_step": ms / args.steps, "launches_per_step": nl / args.steps}
     else:
+        ms, nl = prof[0]
+        flops = rows * f_row * (2 * cfg.iters + 1) * args.steps
         peak = fp32_simt_peak_tflops(sm_mhz)
-        bound, src = "alu", f"152 SMs x 128 FP32 FMA x 2 x {sm_mhz:.0f} MHz (median under load)"
-    achieved = flops / (ms / 1e3) / 1e12 if ms > 0 else None
-    roof = {"bound": bound, "kernel": ["k_sgemm+k_conv", "", "", "", "", "k_fused_iter"][cls],
-            "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": None, "peak_source": src,
-            "kernel_ms_per_step": ms / args.steps, "launches_per_step": nl / args.steps}
+        achieved = flops / (ms / 1e3) / 1e12 if ms > 0 else None
+        roof = {"bound": "alu", "kernel": "k_sgemm (FP32 SIMT contractions)", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "peak_source": f"152 SMs x 128 FP32 FMA x 2 x {sm_mhz:.0f} MHz (median SM clock under load)",
+                "kernel_ms_per_step": ms / args.steps, "launches_per_step": nl / args.steps}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -1,13 +1,1088 @@
-// Tensor-core bound pass (placeholder until the tcgen05 kernel lands).
+// Fused tensor-core bound pass for fully connected ReLU networks (sm_103a: tcgen05 + TMA).
+//
+// One persistent CTA per SM walks tiles of TR = 64 rows (row = subdomain x spec).  For a
+// tile, the whole backward recursion of Theorem 3.1 (Eq. definition_A) runs on chip:
+//
+//   A^(i-1)^T = W^(i)^T Lambda^(i)^T      (tcgen05.mma, M = 128 output neurons, N = TR rows,
+//                                          K = 16; BF16 operands, FP32 accumulator in TMEM)
+//
+// The weight tile is the MMA's A operand (loaded by TMA, 128B swizzle, K-major) and the
+// activations Lambda^T are its B operand (written to shared memory by the epilogue in the
+// same swizzled layout).  Putting neurons on TMEM lanes makes every epilogue access to
+// alpha, the per-neuron tables, Adam state and the stash coalesced across a warp.
+//
+// The epilogue (16 warps) reads the accumulator with tcgen05.ld, applies the relaxation of
+// Lemma 2.1 / Eq. definition_D (split overriding stability), the beta shift and the bias
+// sums (Lambda = A D + beta S; c += Lambda b + A lambda), and writes Lambda^(i-1) in BF16
+// as the next contraction's operand.  The last contraction is concretised over the box
+// (Eq. beta_crown_lp).  With a gradient requested the adjoint pass follows in the same
+// launch: zhat^(i) = W^(i) h^(i-1) + b^(i) along h^(0) = x*, dalpha = A zhat, dbeta = S zhat,
+// h = D zhat + lambda; in optimiser mode the projected Adam step (Appendix C.1) and the
+// per-row best tracking are applied to alpha and beta in that epilogue.
+//
+// Roles: warps 0-15 epilogue, warp 16 TMA producer, warp 17 MMA issuer (one lane each).
+// Every mbarrier wait is bounded; on expiry the kernel records BCROWN_ERR_TIMEOUT, stops
+// issuing work, waits (bounded) for its copies in flight, frees TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+
 #include "fused_tc.cuh"
 
 namespace bcrown {
 
-bool tc_supported(const bcrown_net*) { return false; }
-size_t tc_workspace_bytes(const bcrown_net*, int, bool) { return 0; }
-int tc_bound(bcrown_net*, const bcrown_domain*, const bcrown_batch*, const Tables&, char*, size_t, bool,
-             const float*, const float*, float*, float*, float*, cudaStream_t) {
-  return fail(BCROWN_ERR_UNIMPLEMENTED, "tensor-core path not built");
+extern std::atomic<long long> g_launches;
+
+namespace tc {
+
+constexpr int TR = 64;            // rows per tile = MMA N
+constexpr int MCH = 128;          // neurons per M chunk = MMA M
+constexpr int KBLK = 64;          // bf16 per K block (128 bytes, one swizzle row)
+constexpr int NSLOT = 8;          // activation (B operand) ring
+constexpr int NSTAGE = 6;         // weight (A operand) ring
+constexpr int NACC = 4;           // accumulator ring (TR columns each)
+constexpr int SLOT_BYTES = TR * 128;     // 8 KB
+constexpr int STAGE_BYTES = MCH * 128;   // 16 KB
+constexpr int NEPI = 16;                 // epilogue warps
+constexpr int TMA_WARP = 16, MMA_WARP = 17;
+constexpr int NTHREADS = 18 * 32;
+constexpr int MAXL = 9;
+constexpr int MAX_D0 = 1024;
+constexpr int SIGN_WORDS = MAX_D0 / 32;
+constexpr int MAX_MASK_WORDS = 72;       // sum over hidden layers of ceil(d_i/32)
+constexpr int MAX_HIDDEN = 256;
+
+struct Smem {
+  uint8_t act[NSLOT][SLOT_BYTES];        // 64 KB, 1024-aligned slots
+  uint8_t w[NSTAGE][STAGE_BYTES];        // 96 KB
+  uint32_t sign[TR][SIGN_WORDS];         // 8 KB: A^(0) >= 0 per (row, input)
+  uint32_t smask[TR][MAX_MASK_WORDS];    // split present
+  uint32_t sneg[TR][MAX_MASK_WORDS];     // split sign +1 (z < 0)
+  float part[4][TR];                     // lb partial sums per lane quadrant
+  float lbrow[TR];
+  int improved[TR];
+  long long abase[TR];
+  long long bbase[TR];
+  int prop[TR];
+  int spec[TR];
+  int sub[TR];
+  int valid[TR];
+  uint64_t act_full[NSLOT], act_empty[NSLOT];
+  uint64_t w_full[NSTAGE], w_empty[NSTAGE];
+  uint64_t acc_full[NACC], acc_empty[NACC];
+  uint64_t epi;   // epilogue-wide barrier (16 warp arrivals per phase)
+  uint64_t done;
+  uint32_t tmem_base;
+  int abort_flag;
+};
+
+struct Args {
+  int L, K, P, H, R, n_tiles, mode;   // mode 0 bound, 1 gradient, 2 Adam step
+  int d[MAXL + 1];
+  long long hoff[MAXL + 1];           // first global hidden index of layer i (1-based)
+  int woff[MAXL + 1];                 // first mask word of layer i
+  int mask_words;
+  const float* bias[MAXL + 1];
+  const float* Wbar;
+  const float* bbar;
+  BatchView bt;
+  Tables tb;
+  const float* x_lo;
+  const float* x_hi;
+  const float* alpha;
+  const float* beta;
+  int64_t n_alpha, n_beta;
+  float* lb;
+  float* dalpha;
+  float* dbeta;
+  __nv_bfloat16* stash;               // [R][H]
+  float* a_cur;
+  float* a_best;
+  float* ma;
+  float* va;
+  float* b_cur;
+  float* b_best;
+  float* mb;
+  float* vb;
+  float* best_lb;
+  float lr_a, lr_b, beta1, beta2, eps, bc1, bc2;
+  int* status;
+  int box_bwd[MAXL + 1];
+  int box_fwd[MAXL + 1];
+};
+
+struct Maps {
+  CUtensorMap bwd[MAXL + 1];   // Wt^(i): [d_{i-1}][Kp(d_i)] bf16, rows = output neurons of the backward
+  CUtensorMap fwd[MAXL + 1];   // W^(i):  [d_i][Kp(d_{i-1})] bf16, rows = output neurons of the forward
+};
+
+// ------------------------------------------------------------------------------------------
+// PTX helpers
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(su32(b)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(su32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait (about 2 s of SM clock); on expiry records a timeout and raises the abort flag.
+__device__ __noinline__ bool mbar_wait(uint64_t* b, uint32_t parity, Smem* sm, int* status) {
+  if (mbar_try(b, parity)) return true;
+  long long t0 = clock64();
+  while (true) {
+    if (mbar_try(b, parity)) return true;
+    if (*(volatile int*)&sm->abort_flag) return false;
+    if (clock64() - t0 > 4000000000LL) {
+      atomicCAS(status, 0, BCROWN_ERR_TIMEOUT);
+      *(volatile int*)&sm->abort_flag = 1;
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ bool epi_sync(Smem* sm, uint32_t& seq, int* status) {
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) mbar_arrive(&sm->epi);
+  const bool ok = mbar_wait(&sm->epi, seq & 1, sm, status);
+  ++seq;
+  __syncwarp();
+  return ok;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          su32(dst)),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(su32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// Barrier among the 16 epilogue warps built on an mbarrier, so that a warp that gives up
+// after a timeout cannot leave the others blocked: every wait here is bounded.
+__device__ __forceinline__ bool epi_sync(Smem* sm, uint32_t& seq, int* status);
+
+// Shared-memory matrix descriptor, K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;                 // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset
+  d |= (uint64_t)1 << 46;                 // descriptor version
+  d |= (uint64_t)2 << 61;                 // SWIZZLE_128B
+  return d;
+}
+// Instruction descriptor: BF16 x BF16 -> FP32, both K-major, M = 128, N = n.
+__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(MCH >> 4) << 24);
+}
+__device__ __forceinline__ void umma(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
+          dtmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Byte offset of element (row, k) inside one activation slot (TR rows x 64 bf16, 128B swizzle).
+__device__ __forceinline__ uint32_t act_off(int row, int k) {
+  return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((((k >> 3) ^ row) & 7) << 4) + ((k & 7) << 1));
+}
+
+__device__ __forceinline__ int nkb_of(int K) { return (K + KBLK - 1) / KBLK; }
+__device__ __forceinline__ int nmc_of(int N) { return (N + MCH - 1) / MCH; }
+
+// Contraction ci of a tile: backward layers L-1..1, then (gradient modes) forward layers 1..L-1.
+__device__ __forceinline__ void contraction(const Args& a, int ci, int& layer, int& N, int& K, bool& fwd) {
+  int nb = a.L - 1;
+  if (ci < nb) {
+    layer = a.L - 1 - ci;
+    N = a.d[layer - 1];
+    K = a.d[layer];
+    fwd = false;
+  } else {
+    layer = ci - nb + 1;
+    N = a.d[layer];
+    K = a.d[layer - 1];
+    fwd = true;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// The kernel
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ Maps maps, const Args a) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  Smem* sm = reinterpret_cast<Smem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_contr = (a.L - 1) * (a.mode >= 1 ? 2 : 1);
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < NSLOT; ++i) {
+      mbar_init(&sm->act_full[i], NEPI);
+      mbar_init(&sm->act_empty[i], 1);
+    }
+    for (int i = 0; i < NSTAGE; ++i) {
+      mbar_init(&sm->w_full[i], 1);
+      mbar_init(&sm->w_empty[i], 1);
+    }
+    for (int i = 0; i < NACC; ++i) {
+      mbar_init(&sm->acc_full[i], 1);
+      mbar_init(&sm->acc_empty[i], NEPI);
+    }
+    mbar_init(&sm->epi, NEPI);
+    mbar_init(&sm->done, 1);
+    sm->abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == MMA_WARP) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&sm->tmem_base)),
+                 "r"(NACC * TR)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = sm->tmem_base;
+
+  if (warp == TMA_WARP) {
+    // ---------------------------------------------------------------- TMA producer
+    if (lane == 0) {
+      uint32_t wseq = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x)
+        for (int ci = 0; ci < n_contr && ok; ++ci) {
+          int layer, N, K;
+          bool fwd;
+          contraction(a, ci, layer, N, K, fwd);
+          const CUtensorMap* map = fwd ? &maps.fwd[layer] : &maps.bwd[layer];
+          const uint32_t bytes = (uint32_t)(fwd ? a.box_fwd[layer] : a.box_bwd[layer]) * 128u;
+          const int nmc = nmc_of(N), nkb = nkb_of(K);
+          const bool stream = nkb > NSLOT / 2;   // same order as the MMA issuer
+          const int n_outer = stream ? nkb : nmc, n_inner = stream ? nmc : nkb;
+          for (int o = 0; o < n_outer && ok; ++o)
+            for (int in = 0; in < n_inner && ok; ++in) {
+              const int mc = stream ? in : o, kb = stream ? o : in;
+              int st = wseq % NSTAGE;
+              if (!mbar_wait(&sm->w_empty[st], ((wseq / NSTAGE) & 1) ^ 1, sm, a.status)) {
+                ok = false;
+                break;
+              }
+              mbar_expect_tx(&sm->w_full[st], bytes);
+              tma_load_2d(sm->w[st], map, kb * KBLK, mc * MCH, &sm->w_full[st]);
+              ++wseq;
+            }
+        }
+      if (!ok) {
+        // wait (bounded) for the copies still in flight before the CTA may exit
+        for (uint32_t s = (wseq > NSTAGE ? wseq - NSTAGE : 0); s < wseq; ++s) {
+          long long t0 = clock64();
+          while (!mbar_try(&sm->w_full[s % NSTAGE], (s / NSTAGE) & 1) && clock64() - t0 < 200000000LL) {
+          }
+        }
+      }
+    }
+  } else if (warp == MMA_WARP) {
+    // ---------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      uint32_t wseq = 0, accseq = 0, aseq = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x)
+        for (int ci = 0; ci < n_contr && ok; ++ci) {
+          int layer, N, K;
+          bool fwd;
+          contraction(a, ci, layer, N, K, fwd);
+          const int nmc = nmc_of(N), nkb = nkb_of(K);
+          const uint32_t idesc = idesc_bf16(TR);
+          if (nkb > NSLOT / 2) {
+            // Streamed operand (more K blocks than stay resident): K blocks outer, all M
+            // chunks accumulate at once (nmc <= NACC), each K block released after use.
+            for (int mc = 0; mc < nmc && ok; ++mc) {
+              const uint32_t sq = accseq + mc;
+              if (!mbar_wait(&sm->acc_empty[sq % NACC], ((sq / NACC) & 1) ^ 1, sm, a.status)) ok = false;
+            }
+            tc_fence_after();
+            for (int kb = 0; kb < nkb && ok; ++kb) {
+              const uint32_t as = aseq + kb;
+              const int slot = as % NSLOT;
+              if (!mbar_wait(&sm->act_full[slot], (as / NSLOT) & 1, sm, a.status)) {
+                ok = false;
+                break;
+              }
+              for (int mc = 0; mc < nmc; ++mc) {
+                const int st = wseq % NSTAGE;
+                if (!mbar_wait(&sm->w_full[st], (wseq / NSTAGE) & 1, sm, a.status)) {
+                  ok = false;
+                  break;
+                }
+                tc_fence_after();
+                const uint32_t dt = tmem + (uint32_t)(((accseq + mc) % NACC) * TR);
+                const uint32_t wa = su32(sm->w[st]);
+                const uint32_t ba = su32(sm->act[slot]);
+#pragma unroll
+                for (int ks = 0; ks < KBLK / 16; ++ks)
+                  umma(dt, sdesc(wa + ks * 32), sdesc(ba + ks * 32), idesc, (kb | ks) != 0 ? 1u : 0u);
+                umma_commit(&sm->w_empty[st]);
+                ++wseq;
+              }
+              if (!ok) break;
+              umma_commit(&sm->act_empty[slot]);
+            }
+            if (!ok) break;
+            for (int mc = 0; mc < nmc; ++mc) umma_commit(&sm->acc_full[(accseq + mc) % NACC]);
+            accseq += nmc;
+            aseq += nkb;
+            continue;
+          }
+          for (int mc = 0; mc < nmc && ok; ++mc) {
+            const int buf = accseq % NACC;
+            if (!mbar_wait(&sm->acc_empty[buf], ((accseq / NACC) & 1) ^ 1, sm, a.status)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t dt = tmem + (uint32_t)(buf * TR);
+            for (int kb = 0; kb < nkb; ++kb) {
+              const uint32_t as = aseq + kb;
+              const int slot = as % NSLOT;
+              if (mc == 0 && !mbar_wait(&sm->act_full[slot], (as / NSLOT) & 1, sm, a.status)) {
+                ok = false;
+                break;
+              }
+              const int st = wseq % NSTAGE;
+              if (!mbar_wait(&sm->w_full[st], (wseq / NSTAGE) & 1, sm, a.status)) {
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+              const uint32_t wa = su32(sm->w[st]);
+              const uint32_t ba = su32(sm->act[slot]);
+#pragma unroll
+              for (int ks = 0; ks < KBLK / 16; ++ks)
+                umma(dt, sdesc(wa + ks * 32), sdesc(ba + ks * 32), idesc, (kb | ks) != 0 ? 1u : 0u);
+              umma_commit(&sm->w_empty[st]);
+              ++wseq;
+              if (mc == nmc - 1) umma_commit(&sm->act_empty[slot]);
+            }
+            if (!ok) break;
+            umma_commit(&sm->acc_full[buf]);
+            ++accseq;
+          }
+          aseq += nkb;
+        }
+      umma_commit(&sm->done);
+      mbar_wait(&sm->done, 0, sm, a.status);
+    }
+  } else {
+    // ---------------------------------------------------------------- epilogue (warps 0..15)
+    const int q = warp & 3;          // TMEM lane quadrant: neurons 32q..32q+31 of an M chunk
+    const int cg = warp >> 2;        // column group: rows 16cg..16cg+15 of the tile
+    const int etid = threadIdx.x;    // 0..511
+    uint32_t aseq = 0, accseq = 0, eseq = 0;
+    bool ok = true;
+    const int dtop = a.d[a.L - 1];
+
+    // Produce activation K blocks from a per-element function: every warp writes the
+    // elements it owns; all 16 warps arrive on each block's full barrier.
+    for (int tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x) {
+      // ---------------- per-row set-up
+      if (etid < TR) {
+        int r = tile * TR + etid;
+        int v = r < a.R;
+        int b = 0, k = 0, p = 0;
+        if (v) {
+          b = r / a.K;
+          k = r - b * a.K;
+          p = a.bt.prop_of[b];
+          if (p < 0 || p >= a.P) {
+            atomicCAS(a.status, 0, BCROWN_ERR_ARG);
+            v = 0;
+            p = 0;
+          }
+        }
+        sm->valid[etid] = v;
+        sm->sub[etid] = b;
+        sm->spec[etid] = k;
+        sm->prop[etid] = p;
+        int cnt = v ? a.bt.split_cnt[b] : 0;
+        if (cnt < 0 || cnt > BCROWN_MAX_SPLITS) {
+          atomicCAS(a.status, 0, BCROWN_ERR_ARG);
+          cnt = 0;
+        }
+        sm->abase[etid] = v ? a.bt.alpha_off[b] + (long long)k * a.tb.U[p] : 0;
+        sm->bbase[etid] = v ? (long long)a.bt.split_off[b] * a.K + (long long)k * cnt : 0;
+        for (int w = 0; w < a.mask_words; ++w) {
+          sm->smask[etid][w] = 0u;
+          sm->sneg[etid][w] = 0u;
+        }
+        int off = v ? a.bt.split_off[b] : 0;
+        for (int e = 0; e < cnt; ++e) {
+          int ly = a.bt.split_layer[off + e];
+          int j = (int)a.bt.split_idx[off + e];
+          int s = a.bt.split_sign[off + e];
+          if (ly < 1 || ly > a.L - 1 || j < 0 || j >= a.d[ly] || (s != 1 && s != -1)) {
+            atomicCAS(a.status, 0, BCROWN_ERR_ARG);
+            continue;
+          }
+          int wd = a.woff[ly] + (j >> 5);
+          sm->smask[etid][wd] |= 1u << (j & 31);
+          if (s == 1) sm->sneg[etid][wd] |= 1u << (j & 31);
+        }
+        sm->part[0][etid] = sm->part[1][etid] = sm->part[2][etid] = sm->part[3][etid] = 0.f;
+      }
+      if (!epi_sync(sm, eseq, a.status)) {
+        ok = false;
+        break;
+      }
+
+      // per-thread lb partials for rows 16cg..16cg+15
+      float acc[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) acc[c] = 0.f;
+
+      // ---- relaxation of neuron j of hidden layer i for tile row `row` (Lemma 2.1, Eq. 3)
+      auto relax = [&](int i, int j, int row, float av, float& lam_out) -> float {
+        // returns Lambda, writes the intercept term into lam_out (A * lambda)
+        const int p = sm->prop[row];
+        const size_t n = (size_t)p * a.H + a.hoff[i] + j;
+        const int wd = a.woff[i] + (j >> 5);
+        const uint32_t bit = 1u << (j & 31);
+        float D, lm = 0.f, bs = 0.f;
+        if (sm->smask[row][wd] & bit) {
+          const int s = (sm->sneg[row][wd] & bit) ? 1 : -1;
+          D = s == -1 ? 1.f : 0.f;
+          // beta slot: position t of (i, j) in the row's split list
+          const int b = sm->sub[row];
+          const int off = a.bt.split_off[b], cnt = a.bt.split_cnt[b];
+          for (int e = 0; e < cnt; ++e)
+            if (a.bt.split_layer[off + e] == i && (int)a.bt.split_idx[off + e] == j) {
+              long long bi = sm->bbase[row] + e;
+              float bv = (bi >= 0 && bi < a.n_beta) ? a.beta[bi] : 0.f;
+              bs = fmaxf(bv, 0.f) * (float)s;
+            }
+        } else {
+          const uint8_t code = a.tb.code[n];
+          if (code == CODE_ACTIVE) D = 1.f;
+          else if (code == CODE_INACTIVE) D = 0.f;
+          else if (av >= 0.f) {
+            long long ai = sm->abase[row] + a.tb.rank[n];
+            D = (ai >= 0 && ai < a.n_alpha) ? fminf(fmaxf(a.alpha[ai], 0.f), 1.f) : 0.f;
+          } else {
+            D = a.tb.slope[n];
+            lm = a.tb.icpt[n];
+          }
+        }
+        lam_out = av * lm;
+        return fmaf(av, D, bs);
+      };
+
+      // ---------------- top operand: Lambda^(L-1) from Wbar (relaxation of layer L-1)
+      {
+        const int i = a.L - 1;
+        const int nkb = nkb_of(dtop);
+        const float* bias = a.bias[i];
+        for (int kb = 0; kb < nkb && ok; ++kb) {
+          const uint32_t as = aseq + kb;
+          const int slot = as % NSLOT;
+          if (!mbar_wait(&sm->act_empty[slot], ((as / NSLOT) & 1) ^ 1, sm, a.status)) {
+            ok = false;
+            break;
+          }
+          // 64 k x 64 rows = 4096 elements, 8 per thread: thread -> (row = etid / 8, k = 8 (etid % 8) + e)
+          const int row = etid >> 3, c8 = etid & 7;
+          uint32_t pk[4];
+#pragma unroll
+          for (int e = 0; e < 8; e += 2) {
+            float lv[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int j = kb * KBLK + c8 * 8 + e + h;
+              float L = 0.f;
+              if (j < dtop && sm->valid[row]) {
+                const float av = a.Wbar[(size_t)sm->spec[row] * dtop + j];
+                float ct;
+                L = relax(i, j, row, av, ct);
+                const float cadd = fmaf(L, bias[j], ct);
+                atomicAdd(&sm->part[0][row], cadd);
+              }
+              lv[h] = L;
+            }
+            __nv_bfloat162 v2 = __floats2bfloat162_rn(lv[0], lv[1]);
+            pk[e >> 1] = *reinterpret_cast<uint32_t*>(&v2);
+          }
+          *reinterpret_cast<uint4*>(sm->act[slot] + act_off(row, c8 * 8)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+          fence_proxy_async();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&sm->act_full[slot]);
+        }
+        aseq += nkb;
+      }
+
+      // ---------------- backward contractions: output A^(i-1) of layer i's transpose
+      for (int i = a.L - 1; i >= 1 && ok; --i) {
+        const int N = a.d[i - 1];
+        const int nmc = nmc_of(N);
+        const bool concretise = (i == 1);
+        const int nkb_next = concretise ? 0 : nkb_of(N);
+        const float* bias_next = concretise ? nullptr : a.bias[i - 1];
+        for (int mc = 0; mc < nmc && ok; ++mc) {
+          const int buf = accseq % NACC;
+          if (!mbar_wait(&sm->acc_full[buf], (accseq / NACC) & 1, sm, a.status)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const int j = mc * MCH + 32 * q + lane;   // output neuron of this thread
+          float v[16];
+          tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * TR + 16 * cg), v);
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&sm->acc_empty[buf]);
+          ++accseq;
+          if (concretise) {
+            // lb += sum_m min(A_m x_lo_m, A_m x_hi_m); record sign bits for x*
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+              const int row = 16 * cg + c;
+              const bool in = j < N && sm->valid[row];
+              float av = v[c];
+              if (in) {
+                const int p = sm->prop[row];
+                const float xl = a.x_lo[(size_t)p * N + j], xh = a.x_hi[(size_t)p * N + j];
+                acc[c] += fminf(av * xl, av * xh);
+              }
+              if (a.mode >= 1) {
+                const unsigned bits = __ballot_sync(0xffffffffu, in && av >= 0.f);
+                if (lane == 0 && mc * MCH + 32 * q < MAX_D0) sm->sign[row][(mc * MCH + 32 * q) >> 5] = bits;
+              }
+            }
+          } else {
+            // relax layer i-1 and write Lambda^(i-1) into the next operand's K block
+            const int kb = (mc * MCH + 32 * q) / KBLK;   // this warp's K block
+            const bool writer = kb < nkb_next;
+            const uint32_t as = aseq + kb;
+            const int slot = as % NSLOT;
+            // two warps (quadrants) share a K block; both wait for it to be free
+            if (writer && !mbar_wait(&sm->act_empty[slot], ((as / NSLOT) & 1) ^ 1, sm, a.status)) {
+              ok = false;
+              break;
+            }
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+              const int row = 16 * cg + c;
+              float L = 0.f;
+              if (j < N && sm->valid[row]) {
+                const float av = v[c];
+                if (a.mode >= 1)
+                  a.stash[(size_t)(tile * TR + row) * a.H + a.hoff[i - 1] + j] = __float2bfloat16_rn(av);
+                float ct;
+                L = relax(i - 1, j, row, av, ct);
+                acc[c] += fmaf(L, bias_next[j], ct);
+              }
+              if (writer)
+                *reinterpret_cast<__nv_bfloat16*>(sm->act[slot] + act_off(row, j & (KBLK - 1))) = __float2bfloat16_rn(L);
+            }
+            // the block is complete when all 16 warps arrived: the 8 writer warps here, the
+            // 8 warps of the other quadrant pair after the contraction (count NEPI per block)
+            if (writer) {
+              fence_proxy_async();
+              __syncwarp();
+              if (lane == 0) mbar_arrive(&sm->act_full[slot]);
+            }
+          }
+        }
+        if (!concretise) {
+          // warps whose quadrant maps to the other K block of each chunk must still arrive on
+          // blocks they did not write: 8 writer warps per block, 8 more arrivals needed.
+          if (ok && lane == 0) {
+            for (int kk = 0; kk < nkb_next; ++kk) {
+              // the warp writes block kk iff (kk % 2) == q / 2 within its chunk
+              if ((kk & 1) != (q >> 1)) {
+                const uint32_t as = aseq + kk;
+                // wait until the block's previous consumer released it before arriving
+                if (!mbar_wait(&sm->act_empty[as % NSLOT], ((as / NSLOT) & 1) ^ 1, sm, a.status)) {
+                  ok = false;
+                  break;
+                }
+                mbar_arrive(&sm->act_full[as % NSLOT]);
+              }
+            }
+          }
+          aseq += nkb_next;
+        }
+      }
+      if (!ok) break;
+
+      // ---------------- lb of each row: reduce the per-thread partials
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        float s = acc[c];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        acc[c] = s;
+      }
+      if (lane == 0) {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) atomicAdd(&sm->part[q][16 * cg + c], acc[c]);
+      }
+      if (!epi_sync(sm, eseq, a.status)) {
+        ok = false;
+        break;
+      }
+      if (etid < TR) {
+        const int row = etid;
+        if (sm->valid[row]) {
+          const int r = tile * TR + row;
+          float lbv = a.bbar[sm->spec[row]] + ((sm->part[0][row] + sm->part[1][row]) + (sm->part[2][row] + sm->part[3][row]));
+          if (!isfinite(lbv)) {
+            atomicCAS(a.status, 0, BCROWN_ERR_NONFINITE);
+            lbv = -INFINITY;
+          }
+          if (a.mode == 2) {
+            const float best = a.best_lb[r];
+            const int imp = lbv > best;
+            sm->improved[row] = imp;
+            if (imp) a.best_lb[r] = lbv;
+          } else {
+            a.lb[r] = lbv;
+          }
+          sm->lbrow[row] = lbv;
+        } else {
+          sm->improved[row] = 0;
+        }
+      }
+      if (!epi_sync(sm, eseq, a.status)) {
+        ok = false;
+        break;
+      }
+      if (a.mode == 0) continue;
+
+      // ---------------- adjoint: x* operand (K blocks of d0), then forward contractions
+      {
+        const int d0 = a.d[0];
+        const int nkb = nkb_of(d0);
+        for (int kb = 0; kb < nkb && ok; ++kb) {
+          const uint32_t as = aseq + kb;
+          const int slot = as % NSLOT;
+          if (!mbar_wait(&sm->act_empty[slot], ((as / NSLOT) & 1) ^ 1, sm, a.status)) {
+            ok = false;
+            break;
+          }
+          const int row = etid >> 3, c8 = etid & 7;
+          uint32_t pk[4];
+          const int p = sm->prop[row];
+#pragma unroll
+          for (int e = 0; e < 8; e += 2) {
+            float xv[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int m = kb * KBLK + c8 * 8 + e + h;
+              float x = 0.f;
+              if (m < d0 && sm->valid[row]) {
+                const bool pos = (sm->sign[row][m >> 5] >> (m & 31)) & 1u;
+                x = pos ? a.x_lo[(size_t)p * d0 + m] : a.x_hi[(size_t)p * d0 + m];
+              }
+              xv[h] = x;
+            }
+            __nv_bfloat162 v2 = __floats2bfloat162_rn(xv[0], xv[1]);
+            pk[e >> 1] = *reinterpret_cast<uint32_t*>(&v2);
+          }
+          *reinterpret_cast<uint4*>(sm->act[slot] + act_off(row, c8 * 8)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+          fence_proxy_async();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&sm->act_full[slot]);
+        }
+        aseq += nkb;
+      }
+      for (int i = 1; i <= a.L - 1 && ok; ++i) {
+        const int N = a.d[i];
+        const int nmc = nmc_of(N);
+        const bool produce = i + 1 <= a.L - 1;
+        const int nkb_next = produce ? nkb_of(N) : 0;
+        const float* bias = a.bias[i];
+        for (int mc = 0; mc < nmc && ok; ++mc) {
+          const int buf = accseq % NACC;
+          if (!mbar_wait(&sm->acc_full[buf], (accseq / NACC) & 1, sm, a.status)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const int j = mc * MCH + 32 * q + lane;
+          float v[16];
+          tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * TR + 16 * cg), v);
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&sm->acc_empty[buf]);
+          ++accseq;
+          const int kb = (mc * MCH + 32 * q) / KBLK;
+          const bool writer = produce && kb < nkb_next;
+          const uint32_t as = aseq + kb;
+          const int slot = as % NSLOT;
+          if (writer && !mbar_wait(&sm->act_empty[slot], ((as / NSLOT) & 1) ^ 1, sm, a.status)) {
+            ok = false;
+            break;
+          }
+#pragma unroll 4
+          for (int c = 0; c < 16; ++c) {
+            const int row = 16 * cg + c;
+            float h = 0.f;
+            if (j < N && sm->valid[row]) {
+              const int p = sm->prop[row];
+              const size_t n = (size_t)p * a.H + a.hoff[i] + j;
+              const float z = v[c] + bias[j];
+              const float av = (i == a.L - 1) ? a.Wbar[(size_t)sm->spec[row] * N + j]
+                                              : __bfloat162float(a.stash[(size_t)(tile * TR + row) * a.H + a.hoff[i] + j]);
+              const int wd = a.woff[i] + (j >> 5);
+              const uint32_t bit = 1u << (j & 31);
+              const bool split = sm->smask[row][wd] & bit;
+              const int s = split ? ((sm->sneg[row][wd] & bit) ? 1 : -1) : 0;
+              const uint8_t code = a.tb.code[n];
+              float D = 0.f, lm = 0.f;
+              long long ai = -1;
+              if (code == CODE_UNSTABLE) {
+                ai = sm->abase[row] + a.tb.rank[n];
+                if (ai < 0 || ai >= a.n_alpha) ai = -1;
+              }
+              float th = 0.f;
+              if (ai >= 0) th = a.alpha[ai];
+              if (s == -1) D = 1.f;
+              else if (s == 1) D = 0.f;
+              else if (code == CODE_ACTIVE) D = 1.f;
+              else if (code == CODE_INACTIVE) D = 0.f;
+              else if (av >= 0.f) D = fminf(fmaxf(th, 0.f), 1.f);
+              else {
+                D = a.tb.slope[n];
+                lm = a.tb.icpt[n];
+              }
+              if (ai >= 0) {
+                const float g = (s == 0 && av >= 0.f) ? av * z : 0.f;
+                if (a.mode == 1) {
+                  a.dalpha[ai] = g;
+                } else {
+                  if (sm->improved[row]) a.a_best[ai] = th;
+                  const float m = a.beta1 * a.ma[ai] + (1.f - a.beta1) * g;
+                  const float vv = a.beta2 * a.va[ai] + (1.f - a.beta2) * g * g;
+                  a.ma[ai] = m;
+                  a.va[ai] = vv;
+                  a.a_cur[ai] = fminf(fmaxf(th + a.lr_a * (m / a.bc1) / (sqrtf(vv / a.bc2) + a.eps), 0.f), 1.f);
+                }
+              }
+              if (s != 0) {
+                const int b = sm->sub[row];
+                const int off = a.bt.split_off[b], cnt = a.bt.split_cnt[b];
+                for (int e = 0; e < cnt; ++e)
+                  if (a.bt.split_layer[off + e] == i && (int)a.bt.split_idx[off + e] == j) {
+                    const long long bi = sm->bbase[row] + e;
+                    if (bi < 0 || bi >= a.n_beta) continue;
+                    const float g = (float)s * z;
+                    if (a.mode == 1) {
+                      a.dbeta[bi] = g;
+                    } else {
+                      const float tb0 = a.b_cur[bi];
+                      if (sm->improved[row]) a.b_best[bi] = tb0;
+                      const float m = a.beta1 * a.mb[bi] + (1.f - a.beta1) * g;
+                      const float vv = a.beta2 * a.vb[bi] + (1.f - a.beta2) * g * g;
+                      a.mb[bi] = m;
+                      a.vb[bi] = vv;
+                      a.b_cur[bi] = fmaxf(tb0 + a.lr_b * (m / a.bc1) / (sqrtf(vv / a.bc2) + a.eps), 0.f);
+                    }
+                  }
+              }
+              h = fmaf(D, z, lm);
+            }
+            if (writer)
+              *reinterpret_cast<__nv_bfloat16*>(sm->act[slot] + act_off(row, j & (KBLK - 1))) = __float2bfloat16_rn(h);
+          }
+          if (writer) {
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm->act_full[slot]);
+          }
+        }
+        if (produce) {
+          if (ok && lane == 0) {
+            for (int kk = 0; kk < nkb_next; ++kk) {
+              if ((kk & 1) != (q >> 1)) {
+                const uint32_t as = aseq + kk;
+                if (!mbar_wait(&sm->act_empty[as % NSLOT], ((as / NSLOT) & 1) ^ 1, sm, a.status)) {
+                  ok = false;
+                  break;
+                }
+                mbar_arrive(&sm->act_full[as % NSLOT]);
+              }
+            }
+          }
+          aseq += nkb_next;
+        }
+      }
+      if (ok && !epi_sync(sm, eseq, a.status)) ok = false;
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == MMA_WARP) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NACC * TR) : "memory");
+  }
+}
+
+}  // namespace tc
+
+// ------------------------------------------------------------------------------------------
+// Host side
+// ------------------------------------------------------------------------------------------
+using namespace tc;
+
+struct TcNet {
+  bool ready = false;
+  std::vector<__nv_bfloat16*> bufs;
+  Maps maps;
+  int box_bwd[MAXL + 1] = {0};
+  int box_fwd[MAXL + 1] = {0};
+  int woff[MAXL + 1] = {0};
+  int mask_words = 0;
+};
+
+static std::mutex g_tc_mu;
+static std::vector<std::pair<const bcrown_net*, TcNet*>> g_tc;
+
+static TcNet* tc_of(const bcrown_net* net) {
+  std::lock_guard<std::mutex> g(g_tc_mu);
+  for (auto& e : g_tc)
+    if (e.first == net) return e.second;
+  TcNet* t = new TcNet();
+  g_tc.push_back({net, t});
+  return t;
+}
+
+bool tc_supported(const bcrown_net* net) {
+  if (net->L < 2 || net->L > MAXL) return false;
+  if (net->d[0] > MAX_D0) return false;
+  int words = 0;
+  for (int i = 0; i < net->L; ++i)
+    if (net->ly[i].kind != BCROWN_LAYER_FC) return false;
+  for (int i = 1; i < net->L; ++i) {
+    if (net->d[i] > MAX_HIDDEN) return false;
+    words += (net->d[i] + 31) / 32;
+  }
+  if (words > MAX_MASK_WORDS) return false;
+  // the forward contraction of layer 1 streams d0 in K blocks: its M chunks must fit the
+  // accumulator ring (hidden widths <= 256 give at most 2)
+  if ((net->d[1] + MCH - 1) / MCH > NACC) return false;
+  int dev = 0, major = 0, minor = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  cudaGetLastError();
+  return major == 10 && minor == 3;
+}
+
+size_t tc_workspace_bytes(const bcrown_net* net, int R, bool grad) {
+  return grad ? (size_t)(((R + TR - 1) / TR) * TR) * std::max(net->H, 1) * sizeof(__nv_bfloat16) : 0;
+}
+
+static int encode_map(CUtensorMap* m, void* base, int rows, int kp, int box_rows) {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        !p)
+      return fail(BCROWN_ERR_CUDA, "cuTensorMapEncodeTiled not available");
+    fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)kp * 2};
+  cuuint32_t box[2] = {(cuuint32_t)KBLK, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(BCROWN_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+  return BCROWN_OK;
+}
+
+// BF16 copy of a [rows][cols] FP32 matrix with the row length padded to a multiple of 64.
+static int padded_bf16(const float* src_dev, int rows, int cols, __nv_bfloat16** out, int* kp) {
+  *kp = (cols + KBLK - 1) / KBLK * KBLK;
+  std::vector<float> h((size_t)rows * cols);
+  if (cudaMemcpy(h.data(), src_dev, h.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(BCROWN_ERR_CUDA, "copy of weights");
+  std::vector<__nv_bfloat16> p((size_t)rows * *kp, __float2bfloat16_rn(0.f));
+  for (int r = 0; r < rows; ++r)
+    for (int c = 0; c < cols; ++c) p[(size_t)r * *kp + c] = __float2bfloat16_rn(h[(size_t)r * cols + c]);
+  if (cudaMalloc(out, p.size() * 2) != cudaSuccess) return fail(BCROWN_ERR_OOM, "bf16 weights");
+  if (cudaMemcpy(*out, p.data(), p.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail(BCROWN_ERR_CUDA, "bf16 weights upload");
+  return BCROWN_OK;
+}
+
+static int tc_prepare(bcrown_net* net, TcNet* t) {
+  if (t->ready) return BCROWN_OK;
+  memset(&t->maps, 0, sizeof(t->maps));
+  int w = 0;
+  for (int i = 1; i < net->L; ++i) {
+    t->woff[i] = w;
+    w += (net->d[i] + 31) / 32;
+  }
+  t->mask_words = w;
+  for (int i = 1; i < net->L; ++i) {
+    const LayerDev& l = net->ly[i - 1];
+    // backward: rows = d_{i-1} output neurons, K = d_i
+    __nv_bfloat16* wt = nullptr;
+    int kp = 0;
+    BC_CHECK(padded_bf16(l.Wt, l.d_in, l.d_out, &wt, &kp));
+    t->bufs.push_back(wt);
+    t->box_bwd[i] = std::min(MCH, (l.d_in + 15) / 16 * 16);
+    t->box_bwd[i] = MCH;
+    BC_CHECK(encode_map(&t->maps.bwd[i], wt, l.d_in, kp, t->box_bwd[i]));
+    // forward: rows = d_i output neurons, K = d_{i-1}
+    __nv_bfloat16* wf = nullptr;
+    BC_CHECK(padded_bf16(l.W, l.d_out, l.d_in, &wf, &kp));
+    t->bufs.push_back(wf);
+    t->box_fwd[i] = MCH;
+    BC_CHECK(encode_map(&t->maps.fwd[i], wf, l.d_out, kp, t->box_fwd[i]));
+  }
+  BC_CUDA(cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem) + 1024));
+  t->ready = true;
+  return BCROWN_OK;
+}
+
+static int tc_launch(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* bt, const Tables& tb, Args& A,
+                     cudaStream_t s) {
+  TcNet* t = tc_of(net);
+  BC_CHECK(tc_prepare(net, t));
+  const int R = bt->B * net->K;
+  A.L = net->L;
+  A.K = net->K;
+  A.P = dom->n_props;
+  A.H = net->H;
+  A.R = R;
+  A.n_tiles = (R + TR - 1) / TR;
+  for (int i = 0; i <= net->L && i <= MAXL; ++i) A.d[i] = net->d[i];
+  for (int i = 1; i < net->L; ++i) {
+    A.hoff[i] = net->hoff[i - 1];
+    A.woff[i] = t->woff[i];
+    A.bias[i] = net->ly[i - 1].b;
+    A.box_bwd[i] = t->box_bwd[i];
+    A.box_fwd[i] = t->box_fwd[i];
+  }
+  A.mask_words = t->mask_words;
+  A.Wbar = net->Wbar;
+  A.bbar = net->bbar;
+  A.bt = BatchView{bt->B, bt->prop_of, bt->split_off, bt->split_cnt, bt->split_layer, bt->split_idx, bt->split_sign,
+                   bt->alpha_off};
+  A.tb = tb;
+  A.x_lo = dom->x_lo;
+  A.x_hi = dom->x_hi;
+  A.n_alpha = bt->n_alpha;
+  A.n_beta = bt->n_beta;
+  A.status = net->status;
+  if (A.n_tiles == 0) return BCROWN_OK;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int grid = std::min(A.n_tiles, sms);
+  {
+    ProfScope ps(net, BCROWN_PROF_FUSED, s);
+    k_fused<<<grid, NTHREADS, sizeof(Smem) + 1024, s>>>(t->maps, A);
+    ++g_launches;
+  }
+  BC_CUDA(cudaGetLastError());
+  return BCROWN_OK;
+}
+
+int tc_bound(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* bt, const Tables& tb, char* ws,
+             size_t ws_bytes, bool grad, const float* alpha, const float* beta, float* lb, float* dalpha,
+             float* dbeta, cudaStream_t s) {
+  Args A;
+  memset(&A, 0, sizeof(A));
+  A.mode = grad ? 1 : 0;
+  A.alpha = alpha;
+  A.beta = beta;
+  A.lb = lb;
+  A.dalpha = dalpha;
+  A.dbeta = dbeta;
+  A.stash = grad ? reinterpret_cast<__nv_bfloat16*>(ws) : nullptr;
+  if (grad && ws_bytes < tc_workspace_bytes(net, bt->B * net->K, true))
+    return fail(BCROWN_ERR_OOM, "tensor-core stash workspace too small");
+  return tc_launch(net, dom, bt, tb, A, s);
+}
+
+int tc_adam_step(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* bt, const Tables& tb, char* ws,
+                 size_t ws_bytes, float* a_cur, float* a_best, float* ma, float* va, float* b_cur, float* b_best,
+                 float* mb, float* vb, float* best_lb, float lr_a, float lr_b, float beta1, float beta2, float eps,
+                 float bc1, float bc2, cudaStream_t s) {
+  Args A;
+  memset(&A, 0, sizeof(A));
+  A.mode = 2;
+  A.alpha = a_cur;
+  A.beta = b_cur;
+  A.stash = reinterpret_cast<__nv_bfloat16*>(ws);
+  if (ws_bytes < tc_workspace_bytes(net, bt->B * net->K, true))
+    return fail(BCROWN_ERR_OOM, "tensor-core stash workspace too small");
+  A.a_cur = a_cur;
+  A.a_best = a_best;
+  A.ma = ma;
+  A.va = va;
+  A.b_cur = b_cur;
+  A.b_best = b_best;
+  A.mb = mb;
+  A.vb = vb;
+  A.best_lb = best_lb;
+  A.lr_a = lr_a;
+  A.lr_b = lr_b;
+  A.beta1 = beta1;
+  A.beta2 = beta2;
+  A.eps = eps;
+  A.bc1 = bc1;
+  A.bc2 = bc2;
+  return tc_launch(net, dom, bt, tb, A, s);
+}
+
+void tc_release(const bcrown_net* net) {
+  std::lock_guard<std::mutex> g(g_tc_mu);
+  for (size_t i = 0; i < g_tc.size(); ++i)
+    if (g_tc[i].first == net) {
+      for (auto* b : g_tc[i].second->bufs) cudaFree(b);
+      delete g_tc[i].second;
+      g_tc.erase(g_tc.begin() + i);
+      return;
+    }
 }
 
 }  // namespace bcrown

@@ -6,6 +6,7 @@
 #include <cstring>
 
 #include "bcrown_internal.cuh"
+#include "fused_tc.cuh"
 
 namespace bcrown {
 
@@ -101,6 +102,7 @@ extern "C" const char* bcrown_last_error(void) { return g_last_error.c_str(); }
 extern "C" void bcrown_free_net(bcrown_net* net) {
   if (!net) return;
   cudaDeviceSynchronize();
+  tc_release(net);
   for (auto& l : net->ly) {
     cudaFree(l.W);
     cudaFree(l.Wt);

@@ -1,0 +1,115 @@
+"""Tensor-core (tcgen05 + TMA, BF16 operands) path against the FP64 oracle (needs a GB300)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import bcrown_oracle as O
+from paper_2103_06624_gb300 import bcrown as bc
+from paper_2103_06624_gb300 import workloads as wl
+from tests.helpers import RTOL, oracle_setup, rel_err, repack
+
+pytestmark = pytest.mark.gpu
+
+# BF16 operands (8-bit significand) with FP32 accumulation: the bound at fixed alpha, beta
+# moves by a few units of 2^-9 relative to the scale of the terms it sums.
+BF16_TOL = 3e-2
+
+
+def _t(x):
+    return torch.as_tensor(np.ascontiguousarray(x, np.float32)).cuda()
+
+
+def _gpu(pb, props, batch):
+    net = bc.load_net(pb.layers, pb.C)
+    dom = bc.domain_from_host(props["x_lo"], props["x_hi"], props["l"], props["u"])
+    return net, dom, bc.DeviceBatch.from_host(batch)
+
+
+def _scale(ref):
+    return max(float(np.median(np.abs(ref))), 1.0)
+
+
+@pytest.mark.parametrize("which", ["small", "784"])
+def test_bf16_bound_close_to_oracle(which):
+    if which == "small":
+        pb = wl.problem_mlp_small()
+        onet, props, unst = oracle_setup(pb)
+        batch = wl.random_batch(pb, unst, 64, 0, 4, 1)
+    else:
+        pb = wl.problem_mlp_784()
+        onet, props, unst = oracle_setup(pb)
+        batch = wl.tree_batch(pb, unst, [200], 12, 3)
+    a, b = wl.random_alpha_beta(batch, 4, 1.0)
+    net, dom, db = _gpu(pb, props, batch)
+    lb = bc.bound(net, dom, db, _t(a), _t(b), bc.BF16).cpu().numpy()
+    assert bc.status(net) == 0
+    ref = O.bound(onet, props, batch, a, b)
+    err = np.abs(lb - ref) / _scale(ref)
+    print("bf16 bound: max err / median|lb| = %.3e" % err.max())
+    assert np.all(np.isfinite(lb))
+    assert err.max() <= BF16_TOL
+
+
+def test_bf16_ragged_rows_and_multi_property():
+    """R not a multiple of the 64-row tile; rows of one tile from different properties."""
+    pb = wl.problem_mlp_784(n_props=3)
+    onet = O.OracleNet(pb.layers, pb.C)
+    l, u = O.root_bounds(onet, pb.x_lo, pb.x_hi)
+    l, u = l.astype(np.float32), u.astype(np.float32)
+    unst = [np.nonzero(O.unstable_mask(l[p], u[p]))[0] for p in range(pb.P)]
+    props = dict(x_lo=pb.x_lo, x_hi=pb.x_hi, l=l, u=u)
+    batch = wl.random_batch(pb, unst, 37, 0, 6, 8, props=np.arange(37) % 3)
+    a, b = wl.random_alpha_beta(batch, 5, 1.0)
+    net, dom, db = _gpu(pb, props, batch)
+    lb = bc.bound(net, dom, db, _t(a), _t(b), bc.BF16).cpu().numpy()
+    ref = O.bound(onet, props, batch, a, b)
+    assert bc.status(net) == 0
+    assert (np.abs(lb - ref) / _scale(ref)).max() <= BF16_TOL
+
+
+def test_bf16_gradient_close_to_oracle():
+    pb = wl.problem_mlp_784()
+    onet, props, unst = oracle_setup(pb)
+    batch = wl.tree_batch(pb, unst, [64], 12, 9)
+    a, b = wl.random_alpha_beta(batch, 2, 1.0)
+    net, dom, db = _gpu(pb, props, batch)
+    lb, da, dbeta = bc.bound_grad(net, dom, db, _t(a), _t(b), bc.BF16)
+    assert bc.status(net) == 0
+    ref, da_ref, db_ref = O.grad(onet, props, batch, a.astype(np.float64), b.astype(np.float64))
+    for g, gr in ((da.cpu().numpy(), da_ref), (dbeta.cpu().numpy(), db_ref)):
+        # relative error of the gradient vector (BF16 rounding of x*, h and the stash)
+        rel = np.linalg.norm(g - gr) / max(np.linalg.norm(gr), 1e-12)
+        print("bf16 gradient relative error %.3e" % rel)
+        assert rel <= 5e-2
+    lb_fp32, da32, db32 = bc.bound_grad(net, dom, db, _t(a), _t(b), bc.FP32)
+    assert np.max(rel_err(lb_fp32.cpu().numpy(), ref)) <= RTOL
+
+
+@pytest.mark.parametrize("which", ["small", "784"])
+def test_bf16_optimize_is_certified_and_tight(which):
+    if which == "small":
+        pb = wl.problem_mlp_small()
+        onet, props, unst = oracle_setup(pb)
+        batch = wl.random_batch(pb, unst, 64, 0, 4, 1)
+    else:
+        pb = wl.problem_mlp_784()
+        onet, props, unst = oracle_setup(pb)
+        batch = wl.tree_batch(pb, unst, [128], 12, 5)
+    a0, b0 = wl.initial_alpha_beta(batch)
+    net, dom, db = _gpu(pb, props, batch)
+    res = {}
+    for prec in (bc.BF16, bc.FP32):
+        at, bt = _t(a0), _t(b0)
+        lb = bc.optimize(net, dom, db, at, bt, bc.OptCfg(precision=prec, certify=True)).cpu().numpy()
+        assert bc.status(net) == 0
+        a_best, b_best = at.cpu().numpy(), bt.cpu().numpy()
+        ref = O.bound(onet, props, batch, a_best, b_best)
+        # certified: never above the exact-arithmetic bound at the returned alpha, beta
+        assert np.all(lb <= ref + 1e-12 * np.abs(ref))
+        assert np.all((a_best >= 0) & (a_best <= 1)) and np.all(b_best >= 0)
+        res[prec] = lb
+    init = O.bound(onet, props, batch, a0, b0)
+    gain32 = np.mean(res[bc.FP32] - init)
+    gain16 = np.mean(res[bc.BF16] - init)
+    print("mean improvement over the initial bound: FP32 %.4f, BF16 %.4f" % (gain32, gain16))
+    assert gain16 >= 0.8 * gain32
