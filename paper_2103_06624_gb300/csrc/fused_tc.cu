@@ -70,6 +70,7 @@ struct Smem {
   int spec[TR];
   int sub[TR];
   int valid[TR];
+  int uniform_p;                         // property shared by every valid row of the tile, or -1
   uint64_t act_full[NSLOT], act_empty[NSLOT];
   uint64_t w_full[NSTAGE], w_empty[NSTAGE];
   uint64_t acc_full[NACC], acc_empty[NACC];
@@ -242,10 +243,22 @@ __device__ __forceinline__ void contraction(const Args& a, int ci, int& layer, i
   }
 }
 
+// Index into beta of split (layer i, neuron j) of a tile row, or -1 (scans the row's split list).
+__device__ __noinline__ long long beta_slot(const Args& a, const Smem* sm, int row, int i, int j) {
+  const int b = sm->sub[row];
+  const int off = a.bt.split_off[b], cnt = a.bt.split_cnt[b];
+  for (int e = 0; e < cnt && e < BCROWN_MAX_SPLITS; ++e)
+    if (a.bt.split_layer[off + e] == i && (int)a.bt.split_idx[off + e] == j) {
+      const long long bi = sm->bbase[row] + e;
+      return (bi >= 0 && bi < a.n_beta) ? bi : -1;
+    }
+  return -1;
+}
+
 // ------------------------------------------------------------------------------------------
 // The kernel
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ Maps maps, const Args a) {
+__global__ void __maxnreg__(112) k_fused(const __grid_constant__ Maps maps, const Args a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   Smem* sm = reinterpret_cast<Smem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -465,6 +478,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
         }
         sm->part[0][etid] = sm->part[1][etid] = sm->part[2][etid] = sm->part[3][etid] = 0.f;
       }
+      if (etid == 0) {
+        // rows of a tile usually come from one property: then per-neuron tables are loaded once
+        const int r0 = tile * TR, r1 = min(a.R, r0 + TR) - 1;
+        int pu = -1;
+        if (r0 <= r1) {
+          const int b0 = r0 / a.K, b1 = r1 / a.K;
+          pu = a.bt.prop_of[b0];
+          for (int b = b0 + 1; b <= b1; ++b)
+            if (a.bt.prop_of[b] != pu) pu = -1;
+          if (pu < 0 || pu >= a.P) pu = -1;
+        }
+        sm->uniform_p = pu;
+      }
       if (!epi_sync(sm, eseq, a.status)) {
         ok = false;
         break;
@@ -474,42 +500,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
       float acc[16];
 #pragma unroll
       for (int c = 0; c < 16; ++c) acc[c] = 0.f;
-
-      // ---- relaxation of neuron j of hidden layer i for tile row `row` (Lemma 2.1, Eq. 3)
-      auto relax = [&](int i, int j, int row, float av, float& lam_out) -> float {
-        // returns Lambda, writes the intercept term into lam_out (A * lambda)
-        const int p = sm->prop[row];
-        const size_t n = (size_t)p * a.H + a.hoff[i] + j;
-        const int wd = a.woff[i] + (j >> 5);
-        const uint32_t bit = 1u << (j & 31);
-        float D, lm = 0.f, bs = 0.f;
-        if (sm->smask[row][wd] & bit) {
-          const int s = (sm->sneg[row][wd] & bit) ? 1 : -1;
-          D = s == -1 ? 1.f : 0.f;
-          // beta slot: position t of (i, j) in the row's split list
-          const int b = sm->sub[row];
-          const int off = a.bt.split_off[b], cnt = a.bt.split_cnt[b];
-          for (int e = 0; e < cnt; ++e)
-            if (a.bt.split_layer[off + e] == i && (int)a.bt.split_idx[off + e] == j) {
-              long long bi = sm->bbase[row] + e;
-              float bv = (bi >= 0 && bi < a.n_beta) ? a.beta[bi] : 0.f;
-              bs = fmaxf(bv, 0.f) * (float)s;
-            }
-        } else {
-          const uint8_t code = a.tb.code[n];
-          if (code == CODE_ACTIVE) D = 1.f;
-          else if (code == CODE_INACTIVE) D = 0.f;
-          else if (av >= 0.f) {
-            long long ai = sm->abase[row] + a.tb.rank[n];
-            D = (ai >= 0 && ai < a.n_alpha) ? fminf(fmaxf(a.alpha[ai], 0.f), 1.f) : 0.f;
-          } else {
-            D = a.tb.slope[n];
-            lm = a.tb.icpt[n];
-          }
-        }
-        lam_out = av * lm;
-        return fmaf(av, D, bs);
-      };
 
       // ---------------- top operand: Lambda^(L-1) from Wbar (relaxation of layer L-1)
       {
@@ -525,26 +515,68 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
           }
           // 64 k x 64 rows = 4096 elements, 8 per thread: thread -> (row = etid / 8, k = 8 (etid % 8) + e)
           const int row = etid >> 3, c8 = etid & 7;
+          const bool rv = sm->valid[row];
+          const int pr = sm->prop[row];
+          float av[8], al[8], slope[8], icpt[8];
+          int code[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const int j = kb * KBLK + c8 * 8 + e;
+            av[e] = 0.f;
+            al[e] = 0.f;
+            slope[e] = icpt[e] = 0.f;
+            code[e] = -1;
+            if (j < dtop && rv) {
+              const size_t n = (size_t)pr * a.H + a.hoff[i] + j;
+              av[e] = a.Wbar[(size_t)sm->spec[row] * dtop + j];
+              code[e] = a.tb.code[n];
+              slope[e] = a.tb.slope[n];
+              icpt[e] = a.tb.icpt[n];
+            }
+          }
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const int j = kb * KBLK + c8 * 8 + e;
+            if (code[e] == CODE_UNSTABLE) {
+              const long long ai = sm->abase[row] + a.tb.rank[(size_t)pr * a.H + a.hoff[i] + j];
+              if (ai >= 0 && ai < a.n_alpha) al[e] = a.alpha[ai];
+            }
+          }
+          float csum = 0.f;
           uint32_t pk[4];
 #pragma unroll
           for (int e = 0; e < 8; e += 2) {
             float lv[2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-              const int j = kb * KBLK + c8 * 8 + e + h;
+              const int ee = e + h;
+              const int j = kb * KBLK + c8 * 8 + ee;
               float L = 0.f;
-              if (j < dtop && sm->valid[row]) {
-                const float av = a.Wbar[(size_t)sm->spec[row] * dtop + j];
-                float ct;
-                L = relax(i, j, row, av, ct);
-                const float cadd = fmaf(L, bias[j], ct);
-                atomicAdd(&sm->part[0][row], cadd);
+              if (code[ee] >= 0) {
+                const int wd = a.woff[i] + (j >> 5);
+                const uint32_t bit = 1u << (j & 31);
+                float D, lm = 0.f, bs = 0.f;
+                if (sm->smask[row][wd] & bit) {
+                  const int sg = (sm->sneg[row][wd] & bit) ? 1 : -1;
+                  D = sg == -1 ? 1.f : 0.f;
+                  const long long bi = beta_slot(a, sm, row, i, j);
+                  if (bi >= 0) bs = fmaxf(a.beta[bi], 0.f) * (float)sg;
+                } else if (code[ee] == CODE_ACTIVE) D = 1.f;
+                else if (code[ee] == CODE_INACTIVE) D = 0.f;
+                else if (av[ee] >= 0.f) D = fminf(fmaxf(al[ee], 0.f), 1.f);
+                else {
+                  D = slope[ee];
+                  lm = icpt[ee];
+                }
+                L = fmaf(av[ee], D, bs);
+                csum += fmaf(L, bias[j], av[ee] * lm);
               }
               lv[h] = L;
             }
             __nv_bfloat162 v2 = __floats2bfloat162_rn(lv[0], lv[1]);
             pk[e >> 1] = *reinterpret_cast<uint32_t*>(&v2);
           }
+          if (rv) atomicAdd(&sm->part[0][row], csum);
           *reinterpret_cast<uint4*>(sm->act[slot] + act_off(row, c8 * 8)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
           fence_proxy_async();
           __syncwarp();
@@ -576,14 +608,24 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
           ++accseq;
           if (concretise) {
             // lb += sum_m min(A_m x_lo_m, A_m x_hi_m); record sign bits for x*
+            const int pu = sm->uniform_p;
+            float uxl = 0.f, uxh = 0.f;
+            if (pu >= 0 && j < N) {
+              uxl = a.x_lo[(size_t)pu * N + j];
+              uxh = a.x_hi[(size_t)pu * N + j];
+            }
 #pragma unroll
             for (int c = 0; c < 16; ++c) {
               const int row = 16 * cg + c;
               const bool in = j < N && sm->valid[row];
               float av = v[c];
               if (in) {
-                const int p = sm->prop[row];
-                const float xl = a.x_lo[(size_t)p * N + j], xh = a.x_hi[(size_t)p * N + j];
+                float xl = uxl, xh = uxh;
+                if (pu < 0) {
+                  const int p = sm->prop[row];
+                  xl = a.x_lo[(size_t)p * N + j];
+                  xh = a.x_hi[(size_t)p * N + j];
+                }
                 acc[c] += fminf(av * xl, av * xh);
               }
               if (a.mode >= 1) {
@@ -602,17 +644,71 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
               ok = false;
               break;
             }
+            const int li = i - 1;
+            const bool jin = j < N;
+            const int pu = sm->uniform_p;
+            int ucode = CODE_INACTIVE, urank = 0;
+            float uslope = 0.f, uicpt = 0.f;
+            if (pu >= 0 && jin) {
+              const size_t n = (size_t)pu * a.H + a.hoff[li] + j;
+              ucode = a.tb.code[n];
+              urank = a.tb.rank[n];
+              uslope = a.tb.slope[n];
+              uicpt = a.tb.icpt[n];
+            }
+            const float bj = jin ? bias_next[j] : 0.f;
+            float al[16];
+            // issue the alpha loads of all 16 rows before using any of them
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+              const int row = 16 * cg + c;
+              al[c] = 0.f;
+              if (jin && sm->valid[row]) {
+                int code = ucode, rank = urank;
+                if (pu < 0) {
+                  const size_t n = (size_t)sm->prop[row] * a.H + a.hoff[li] + j;
+                  code = a.tb.code[n];
+                  rank = a.tb.rank[n];
+                }
+                if (code == CODE_UNSTABLE) {
+                  const long long ai = sm->abase[row] + rank;
+                  if (ai >= 0 && ai < a.n_alpha) al[c] = a.alpha[ai];
+                }
+              }
+            }
+            const int wd = a.woff[li] + (j >> 5);
+            const uint32_t bit = 1u << (j & 31);
 #pragma unroll
             for (int c = 0; c < 16; ++c) {
               const int row = 16 * cg + c;
               float L = 0.f;
-              if (j < N && sm->valid[row]) {
+              if (jin && sm->valid[row]) {
                 const float av = v[c];
                 if (a.mode >= 1)
-                  a.stash[(size_t)(tile * TR + row) * a.H + a.hoff[i - 1] + j] = __float2bfloat16_rn(av);
-                float ct;
-                L = relax(i - 1, j, row, av, ct);
-                acc[c] += fmaf(L, bias_next[j], ct);
+                  a.stash[(size_t)(tile * TR + row) * a.H + a.hoff[li] + j] = __float2bfloat16_rn(av);
+                int code = ucode;
+                float slope = uslope, icpt = uicpt;
+                if (pu < 0) {
+                  const size_t n = (size_t)sm->prop[row] * a.H + a.hoff[li] + j;
+                  code = a.tb.code[n];
+                  slope = a.tb.slope[n];
+                  icpt = a.tb.icpt[n];
+                }
+                float D, lm = 0.f, bs = 0.f;
+                if (sm->smask[row][wd] & bit) {
+                  const int sg = (sm->sneg[row][wd] & bit) ? 1 : -1;
+                  D = sg == -1 ? 1.f : 0.f;
+                  const long long bi = beta_slot(a, sm, row, li, j);
+                  if (bi >= 0) bs = fmaxf(a.beta[bi], 0.f) * (float)sg;
+                } else if (code == CODE_ACTIVE) D = 1.f;
+                else if (code == CODE_INACTIVE) D = 0.f;
+                else if (av >= 0.f) D = fminf(fmaxf(al[c], 0.f), 1.f);
+                else {
+                  D = slope;
+                  lm = icpt;
+                }
+                L = fmaf(av, D, bs);
+                acc[c] += fmaf(L, bj, av * lm);
               }
               if (writer)
                 *reinterpret_cast<__nv_bfloat16*>(sm->act[slot] + act_off(row, j & (KBLK - 1))) = __float2bfloat16_rn(L);
@@ -756,59 +852,95 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
             ok = false;
             break;
           }
-#pragma unroll 4
-          for (int c = 0; c < 16; ++c) {
-            const int row = 16 * cg + c;
-            float h = 0.f;
-            if (j < N && sm->valid[row]) {
-              const int p = sm->prop[row];
-              const size_t n = (size_t)p * a.H + a.hoff[i] + j;
-              const float z = v[c] + bias[j];
-              const float av = (i == a.L - 1) ? a.Wbar[(size_t)sm->spec[row] * N + j]
-                                              : __bfloat162float(a.stash[(size_t)(tile * TR + row) * a.H + a.hoff[i] + j]);
-              const int wd = a.woff[i] + (j >> 5);
-              const uint32_t bit = 1u << (j & 31);
-              const bool split = sm->smask[row][wd] & bit;
-              const int s = split ? ((sm->sneg[row][wd] & bit) ? 1 : -1) : 0;
-              const uint8_t code = a.tb.code[n];
-              float D = 0.f, lm = 0.f;
-              long long ai = -1;
-              if (code == CODE_UNSTABLE) {
-                ai = sm->abase[row] + a.tb.rank[n];
-                if (ai < 0 || ai >= a.n_alpha) ai = -1;
-              }
-              float th = 0.f;
-              if (ai >= 0) th = a.alpha[ai];
-              if (s == -1) D = 1.f;
-              else if (s == 1) D = 0.f;
-              else if (code == CODE_ACTIVE) D = 1.f;
-              else if (code == CODE_INACTIVE) D = 0.f;
-              else if (av >= 0.f) D = fminf(fmaxf(th, 0.f), 1.f);
-              else {
-                D = a.tb.slope[n];
-                lm = a.tb.icpt[n];
-              }
-              if (ai >= 0) {
-                const float g = (s == 0 && av >= 0.f) ? av * z : 0.f;
-                if (a.mode == 1) {
-                  a.dalpha[ai] = g;
-                } else {
-                  if (sm->improved[row]) a.a_best[ai] = th;
-                  const float m = a.beta1 * a.ma[ai] + (1.f - a.beta1) * g;
-                  const float vv = a.beta2 * a.va[ai] + (1.f - a.beta2) * g * g;
-                  a.ma[ai] = m;
-                  a.va[ai] = vv;
-                  a.a_cur[ai] = fminf(fmaxf(th + a.lr_a * (m / a.bc1) / (sqrtf(vv / a.bc2) + a.eps), 0.f), 1.f);
+          const bool jin = j < N;
+          const int pu = sm->uniform_p;
+          int ucode = CODE_INACTIVE, urank = 0;
+          float uslope = 0.f, uicpt = 0.f;
+          if (pu >= 0 && jin) {
+            const size_t n = (size_t)pu * a.H + a.hoff[i] + j;
+            ucode = a.tb.code[n];
+            urank = a.tb.rank[n];
+            uslope = a.tb.slope[n];
+            uicpt = a.tb.icpt[n];
+          }
+          const float bj = jin ? bias[j] : 0.f;
+          const int wd = a.woff[i] + (j >> 5);
+          const uint32_t bit = 1u << (j & 31);
+#pragma unroll
+          for (int h8 = 0; h8 < 4; ++h8) {
+            float av[4], th[4], mm[4], vq[4];
+            long long ai[4];
+            // loads of 8 rows first (stash, alpha, Adam moments), then the arithmetic
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              const int row = 16 * cg + 4 * h8 + c;
+              av[c] = th[c] = mm[c] = vq[c] = 0.f;
+              ai[c] = -1;
+              if (jin && sm->valid[row]) {
+                av[c] = (i == a.L - 1) ? a.Wbar[(size_t)sm->spec[row] * N + j]
+                                       : __bfloat162float(a.stash[(size_t)(tile * TR + row) * a.H + a.hoff[i] + j]);
+                int code = ucode, rank = urank;
+                if (pu < 0) {
+                  const size_t n = (size_t)sm->prop[row] * a.H + a.hoff[i] + j;
+                  code = a.tb.code[n];
+                  rank = a.tb.rank[n];
+                }
+                if (code == CODE_UNSTABLE) {
+                  const long long x = sm->abase[row] + rank;
+                  if (x >= 0 && x < a.n_alpha) {
+                    ai[c] = x;
+                    th[c] = a.alpha[x];
+                    if (a.mode == 2) {
+                      mm[c] = a.ma[x];
+                      vq[c] = a.va[x];
+                    }
+                  }
                 }
               }
-              if (s != 0) {
-                const int b = sm->sub[row];
-                const int off = a.bt.split_off[b], cnt = a.bt.split_cnt[b];
-                for (int e = 0; e < cnt; ++e)
-                  if (a.bt.split_layer[off + e] == i && (int)a.bt.split_idx[off + e] == j) {
-                    const long long bi = sm->bbase[row] + e;
-                    if (bi < 0 || bi >= a.n_beta) continue;
-                    const float g = (float)s * z;
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              const int row = 16 * cg + 4 * h8 + c;
+              float hv = 0.f;
+              if (jin && sm->valid[row]) {
+                const float z = v[4 * h8 + c] + bj;
+                int code = ucode;
+                float slope = uslope, icpt = uicpt;
+                if (pu < 0) {
+                  const size_t n = (size_t)sm->prop[row] * a.H + a.hoff[i] + j;
+                  code = a.tb.code[n];
+                  slope = a.tb.slope[n];
+                  icpt = a.tb.icpt[n];
+                }
+                const bool split = sm->smask[row][wd] & bit;
+                const int sg = split ? ((sm->sneg[row][wd] & bit) ? 1 : -1) : 0;
+                float D, lm = 0.f;
+                if (sg == -1) D = 1.f;
+                else if (sg == 1) D = 0.f;
+                else if (code == CODE_ACTIVE) D = 1.f;
+                else if (code == CODE_INACTIVE) D = 0.f;
+                else if (av[c] >= 0.f) D = fminf(fmaxf(th[c], 0.f), 1.f);
+                else {
+                  D = slope;
+                  lm = icpt;
+                }
+                if (ai[c] >= 0) {
+                  const float g = (sg == 0 && av[c] >= 0.f) ? av[c] * z : 0.f;
+                  if (a.mode == 1) {
+                    a.dalpha[ai[c]] = g;
+                  } else {
+                    if (sm->improved[row]) a.a_best[ai[c]] = th[c];
+                    const float m = a.beta1 * mm[c] + (1.f - a.beta1) * g;
+                    const float vv = a.beta2 * vq[c] + (1.f - a.beta2) * g * g;
+                    a.ma[ai[c]] = m;
+                    a.va[ai[c]] = vv;
+                    a.a_cur[ai[c]] = fminf(fmaxf(th[c] + a.lr_a * (m / a.bc1) / (sqrtf(vv / a.bc2) + a.eps), 0.f), 1.f);
+                  }
+                }
+                if (sg != 0) {
+                  const long long bi = beta_slot(a, sm, row, i, j);
+                  if (bi >= 0) {
+                    const float g = (float)sg * z;
                     if (a.mode == 1) {
                       a.dbeta[bi] = g;
                     } else {
@@ -821,11 +953,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
                       a.b_cur[bi] = fmaxf(tb0 + a.lr_b * (m / a.bc1) / (sqrtf(vv / a.bc2) + a.eps), 0.f);
                     }
                   }
+                }
+                hv = fmaf(D, z, lm);
               }
-              h = fmaf(D, z, lm);
+              if (writer)
+                *reinterpret_cast<__nv_bfloat16*>(sm->act[slot] + act_off(row, j & (KBLK - 1))) = __float2bfloat16_rn(hv);
             }
-            if (writer)
-              *reinterpret_cast<__nv_bfloat16*>(sm->act[slot] + act_off(row, j & (KBLK - 1))) = __float2bfloat16_rn(h);
           }
           if (writer) {
             fence_proxy_async();
