@@ -70,6 +70,8 @@ struct Smem {
   int spec[TR];
   int sub[TR];
   int valid[TR];
+  int nsplit[TR];
+  uint16_t skey[TR][BCROWN_MAX_SPLITS];  // (layer << 8) | neuron of the row's splits, in list order
   int uniform_p;                         // property shared by every valid row of the tile, or -1
   uint64_t act_full[NSLOT], act_empty[NSLOT];
   uint64_t w_full[NSTAGE], w_empty[NSTAGE];
@@ -79,6 +81,8 @@ struct Smem {
   uint32_t tmem_base;
   int abort_flag;
 };
+
+static_assert(sizeof(Smem) + 1024 <= 232448, "shared memory plan exceeds 227 KB per CTA");
 
 struct Args {
   int L, K, P, H, R, n_tiles, mode;   // mode 0 bound, 1 gradient, 2 Adam step
@@ -244,11 +248,11 @@ __device__ __forceinline__ void contraction(const Args& a, int ci, int& layer, i
 }
 
 // Index into beta of split (layer i, neuron j) of a tile row, or -1 (scans the row's split list).
-__device__ __noinline__ long long beta_slot(const Args& a, const Smem* sm, int row, int i, int j) {
-  const int b = sm->sub[row];
-  const int off = a.bt.split_off[b], cnt = a.bt.split_cnt[b];
-  for (int e = 0; e < cnt && e < BCROWN_MAX_SPLITS; ++e)
-    if (a.bt.split_layer[off + e] == i && (int)a.bt.split_idx[off + e] == j) {
+__device__ __forceinline__ long long beta_slot(const Args& a, const Smem* sm, int row, int i, int j) {
+  const uint16_t key = (uint16_t)((i << 8) | j);
+  const int cnt = sm->nsplit[row];
+  for (int e = 0; e < cnt; ++e)
+    if (sm->skey[row][e] == key) {
       const long long bi = sm->bbase[row] + e;
       return (bi >= 0 && bi < a.n_beta) ? bi : -1;
     }
@@ -464,14 +468,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
           sm->sneg[etid][w] = 0u;
         }
         int off = v ? a.bt.split_off[b] : 0;
+        sm->nsplit[etid] = cnt;
         for (int e = 0; e < cnt; ++e) {
           int ly = a.bt.split_layer[off + e];
           int j = (int)a.bt.split_idx[off + e];
           int s = a.bt.split_sign[off + e];
+          sm->skey[etid][e] = 0xFFFFu;
           if (ly < 1 || ly > a.L - 1 || j < 0 || j >= a.d[ly] || (s != 1 && s != -1)) {
             atomicCAS(a.status, 0, BCROWN_ERR_ARG);
             continue;
           }
+          sm->skey[etid][e] = (uint16_t)((ly << 8) | j);
           int wd = a.woff[ly] + (j >> 5);
           sm->smask[etid][wd] |= 1u << (j & 31);
           if (s == 1) sm->sneg[etid][wd] |= 1u << (j & 31);
