@@ -220,6 +220,28 @@ int bcrown_profile_read(bcrown_net* net, int cls, double* total_ms, long long* l
 /* Number of kernels this library has launched in the process so far (all nets). */
 long long bcrown_kernel_launches(void);
 
+/* Size in bytes of the fixed device scratch of bcrown_bound_static (set when the library is built). */
+#define BCROWN_STATIC_SCRATCH_BYTES (16u << 20)
+
+/* bcrown_bound_static -- the FP32 bound pass of bcrown_bound (BCROWN_FP32), for callers that
+ * cannot allocate device memory.  The paper has no counterpart: this entry point exists for
+ * hosts that must not call cudaMalloc while the pass runs -- a program capturing the stream
+ * into a CUDA graph, a real-time loop that cannot take cudaMalloc's implicit synchronisation,
+ * a process confined to a device-memory budget handed out by its own allocator.
+ *
+ * It allocates nothing.  Its scratch (per-neuron tables and row-chunk buffers) is one
+ * file-scope device array of BCROWN_STATIC_SCRATCH_BYTES bytes that every GPU loading the
+ * library holds until the process exits.  The caller passes inputs and outputs exactly as for
+ * bcrown_bound.  The first call on a device looks the array's device address up (once per
+ * device, with that device current); make that first call before any stream capture begins.
+ * Problems whose per-property tables and a single row do not fit in the array are rejected
+ * with BCROWN_ERR_ARG and a message naming the limit; larger batches are processed in row
+ * chunks that fit.  Every call shares the one array and it keeps the last call's contents
+ * (each call writes every part of it that it reads, so nothing needs clearing): calls that
+ * overlap on the GPU -- on different streams, or from different host threads -- race. */
+int bcrown_bound_static(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* batch,
+                        const float* alpha, const float* beta, float* lb, void* stream);
+
 /* Synchronise `stream`, return the device status word of the net (BCROWN_OK or
  * the first device-detected error since the last call) and clear it. */
 int bcrown_status(bcrown_net* net, void* stream);

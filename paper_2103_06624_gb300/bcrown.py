@@ -157,6 +157,17 @@ def bound(net, dom, batch, alpha, beta, precision=FP32, out=None, stream=None):
     return lb
 
 
+def bound_static(net, dom, batch, alpha, beta, out=None, stream=None):
+    """FP32 bound through bcrown_bound_static: no device allocation by the library (its scratch
+    is a fixed array built into the library), for callers that cannot allocate."""
+    lib = N.load()
+    lb = out if out is not None else torch.empty(batch.B * net.K, device="cuda", dtype=torch.float32)
+    d, b = dom.c(), batch.c()
+    N.check(lib.bcrown_bound_static(net.handle, C.byref(d), C.byref(b), _ptr(alpha), _ptr(beta), _ptr(lb),
+                                    _stream(stream)))
+    return lb
+
+
 def bound_grad(net, dom, batch, alpha, beta, precision=FP32, stream=None):
     lib = N.load()
     lb = torch.empty(batch.B * net.K, device="cuda", dtype=torch.float32)

@@ -20,7 +20,7 @@ MAX_SPLITS = 64
 EXPORTS = ["bcrown_load_net", "bcrown_free_net", "bcrown_net_info", "bcrown_root_bounds", "bcrown_bound",
            "bcrown_bound_grad", "bcrown_optimize", "bcrown_batch_split", "bcrown_neuron_codes",
            "bcrown_status", "bcrown_last_error", "bcrown_profile", "bcrown_profile_read",
-           "bcrown_kernel_launches"]
+           "bcrown_kernel_launches", "bcrown_bound_static"]
 PROF_CONTRACT, PROF_RELAX, PROF_CONCRETIZE, PROF_ADJOINT, PROF_ADAM, PROF_FUSED = range(6)
 
 
@@ -82,6 +82,7 @@ def load(path=LIB_PATH):
         "bcrown_profile": ([vp, i32], i32),
         "bcrown_profile_read": ([vp, i32, C.POINTER(C.c_double), C.POINTER(C.c_longlong)], i32),
         "bcrown_kernel_launches": ([], C.c_longlong),
+        "bcrown_bound_static": ([vp, C.POINTER(Domain), C.POINTER(Batch), vp, vp, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
