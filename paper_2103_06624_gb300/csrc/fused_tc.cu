@@ -42,7 +42,7 @@ constexpr int TR = 64;            // rows per tile = MMA N
 constexpr int MCH = 128;          // neurons per M chunk = MMA M
 constexpr int KBLK = 64;          // bf16 per K block (128 bytes, one swizzle row)
 constexpr int NSLOT = 8;          // activation (B operand) ring
-constexpr int NSTAGE = 6;         // weight (A operand) ring
+constexpr int NSTAGE = 4;         // weight (A operand) ring
 constexpr int NACC = 4;           // accumulator ring (TR columns each)
 constexpr int SLOT_BYTES = TR * 128;     // 8 KB
 constexpr int STAGE_BYTES = MCH * 128;   // 16 KB
@@ -52,15 +52,17 @@ constexpr int NTHREADS = 18 * 32;
 constexpr int MAXL = 9;
 constexpr int MAX_D0 = 1024;
 constexpr int SIGN_WORDS = MAX_D0 / 32;
-constexpr int MAX_MASK_WORDS = 72;       // sum over hidden layers of ceil(d_i/32)
+constexpr int MAX_MASK_WORDS = 48;       // sum over hidden layers of ceil(d_i/32)
+constexpr int MAX_H = MAX_MASK_WORDS * 32;  // hidden neurons whose tables a tile stages
 constexpr int MAX_HIDDEN = 256;
 
 struct Smem {
   uint8_t act[NSLOT][SLOT_BYTES];        // 64 KB, 1024-aligned slots
   uint8_t w[NSTAGE][STAGE_BYTES];        // 96 KB
   uint32_t sign[TR][SIGN_WORDS];         // 8 KB: A^(0) >= 0 per (row, input)
-  uint32_t smask[TR][MAX_MASK_WORDS];    // split present
-  uint32_t sneg[TR][MAX_MASK_WORDS];     // split sign +1 (z < 0)
+  uint32_t smask[MAX_MASK_WORDS][TR];    // split present, [word][row]: a warp reads its 16 rows at once
+  uint32_t sneg[MAX_MASK_WORDS][TR];     // split sign +1 (z < 0)
+  unsigned long long wrows[MAX_MASK_WORDS];  // rows with any split in mask word w
   float part[4][TR];                     // lb partial sums per lane quadrant
   float lbrow[TR];
   int improved[TR];
@@ -71,7 +73,14 @@ struct Smem {
   int sub[TR];
   int valid[TR];
   int nsplit[TR];
-  uint16_t skey[TR][BCROWN_MAX_SPLITS];  // (layer << 8) | neuron of the row's splits, in list order
+  uint8_t sorig[TR][BCROWN_MAX_SPLITS];  // the row's splits in (mask word, bit) order: list position
+  float sbeta[TR][BCROWN_MAX_SPLITS];    //   and beta (clamped at 0)
+  uint8_t wfirst[MAX_MASK_WORDS][TR];    // splits of the row in mask words before w
+  uint32_t tcode[MAX_H];                 // uniform tiles: code << 16 | unstable rank, per hidden neuron
+  float tslope[MAX_H];                   //   upper chord slope
+  float ticpt[MAX_H];                    //   upper chord intercept
+  float sxlo[MAX_D0];                    //   input box
+  float sxhi[MAX_D0];
   int uniform_p;                         // property shared by every valid row of the tile, or -1
   uint64_t act_full[NSLOT], act_empty[NSLOT];
   uint64_t w_full[NSTAGE], w_empty[NSTAGE];
@@ -163,12 +172,21 @@ __device__ __noinline__ bool mbar_wait(uint64_t* b, uint32_t parity, Smem* sm, i
     }
   }
 }
+// Wait by a whole warp: one lane polls the barrier (512 polling threads would flood the
+// shared-memory pipe every other warp needs), then the warp reconverges.
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t* b, uint32_t parity, Smem* sm, int* status) {
+  __syncwarp();
+  int ok = 1;
+  if ((threadIdx.x & 31) == 0) ok = mbar_wait(b, parity, sm, status) ? 1 : 0;
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  __syncwarp();
+  return ok != 0;
+}
 __device__ __forceinline__ bool epi_sync(Smem* sm, uint32_t& seq, int* status) {
   __syncwarp();
   if ((threadIdx.x & 31) == 0) mbar_arrive(&sm->epi);
-  const bool ok = mbar_wait(&sm->epi, seq & 1, sm, status);
+  const bool ok = mbar_wait_warp(&sm->epi, seq & 1, sm, status);
   ++seq;
-  __syncwarp();
   return ok;
 }
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
@@ -223,6 +241,108 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr)
+               : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Loads issued where they are written (volatile asm keeps them ahead of the barrier waits that
+// follow, instead of letting the compiler sink them to their first use); 0 when pred is false.
+__device__ __forceinline__ float ldg_f32(const float* p, bool pred) {
+  float v;
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\tmov.f32 %0, 0f00000000;\n\t@q ld.global.f32 %0, [%1];\n\t}"
+               : "=f"(v)
+               : "l"(p), "r"((uint32_t)pred)
+               : "memory");
+  return v;
+}
+__device__ __forceinline__ float ldg_bf16(const __nv_bfloat16* p, bool pred) {
+  uint16_t v;
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\tmov.u16 %0, 0;\n\t@q ld.global.u16 %0, [%1];\n\t}"
+               : "=h"(v)
+               : "l"(p), "r"((uint32_t)pred)
+               : "memory");
+  return __uint_as_float(((uint32_t)v) << 16);
+}
+
+// Sum of v[r] over the 32 lanes of a warp, for r = 0..15, scattered so that lanes 2r and 2r+1
+// both hold the sum for r (16 shuffles instead of 80).
+__device__ __forceinline__ float reduce16(float (&v)[16]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const bool hi = lane & 16;
+    const float send = hi ? v[i] : v[i + 8];
+    const float keep = hi ? v[i + 8] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const bool hi = lane & 8;
+    const float send = hi ? v[i] : v[i + 4];
+    const float keep = hi ? v[i + 4] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const bool hi = lane & 4;
+    const float send = hi ? v[i] : v[i + 2];
+    const float keep = hi ? v[i + 2] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  {
+    const bool hi = lane & 2;
+    const float send = hi ? v[0] : v[1];
+    const float keep = hi ? v[1] : v[0];
+    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+// Sum of v[r] over the 32 lanes, r = 0..7, scattered: lanes 4r..4r+3 hold the sum for r.
+__device__ __forceinline__ float reduce8(float (&v)[8]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const bool hi = lane & 16;
+    const float send = hi ? v[i] : v[i + 4];
+    const float keep = hi ? v[i + 4] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const bool hi = lane & 8;
+    const float send = hi ? v[i] : v[i + 2];
+    const float keep = hi ? v[i + 2] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  {
+    const bool hi = lane & 4;
+    const float send = hi ? v[0] : v[1];
+    const float keep = hi ? v[1] : v[0];
+    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  float r = v[0] + __shfl_xor_sync(0xffffffffu, v[0], 2);
+  return r + __shfl_xor_sync(0xffffffffu, r, 1);
+}
+
+// L2 prefetch of [p, p + bytes): only the 16-byte aligned interior, so it stays in bounds.
+__device__ __forceinline__ void prefetch_l2(const void* p, long long bytes) {
+  uintptr_t lo = ((uintptr_t)p + 15) & ~(uintptr_t)15;
+  uintptr_t hi = ((uintptr_t)p + (uintptr_t)bytes) & ~(uintptr_t)15;
+  while (lo < hi) {
+    uint32_t n = (uint32_t)min((uintptr_t)(1u << 20), hi - lo);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"(n) : "memory");
+    lo += n;
+  }
+}
+
 // Byte offset of element (row, k) inside one activation slot (TR rows x 64 bf16, 128B swizzle).
 __device__ __forceinline__ uint32_t act_off(int row, int k) {
   return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((((k >> 3) ^ row) & 7) << 4) + ((k & 7) << 1));
@@ -248,15 +368,10 @@ __device__ __forceinline__ void contraction(const Args& a, int ci, int& layer, i
 }
 
 // Index into beta of split (layer i, neuron j) of a tile row, or -1 (scans the row's split list).
-__device__ __forceinline__ long long beta_slot(const Args& a, const Smem* sm, int row, int i, int j) {
-  const uint16_t key = (uint16_t)((i << 8) | j);
-  const int cnt = sm->nsplit[row];
-  for (int e = 0; e < cnt; ++e)
-    if (sm->skey[row][e] == key) {
-      const long long bi = sm->bbase[row] + e;
-      return (bi >= 0 && bi < a.n_beta) ? bi : -1;
-    }
-  return -1;
+// Slot of the split at (mask word w, bit) of a tile row, in the row's sorted split order:
+// the splits in earlier words plus those below `bit` in word w (O(1), no search).
+__device__ __forceinline__ int split_slot(const Smem* sm, int row, int w, int bit) {
+  return (int)sm->wfirst[w][row] + __popc(sm->smask[w][row] & ((1u << bit) - 1u));
 }
 
 // ------------------------------------------------------------------------------------------
@@ -264,7 +379,10 @@ __device__ __forceinline__ long long beta_slot(const Args& a, const Smem* sm, in
 // ------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ Maps maps, const Args a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
-  Smem* sm = reinterpret_cast<Smem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  // pointer arithmetic on the shared array (not through an integer) keeps the shared address
+  // space visible to the compiler, so accesses through `sm` are shared loads/stores
+  const uint32_t pad = (1024u - (su32(smem_raw) & 1023u)) & 1023u;
+  Smem* sm = reinterpret_cast<Smem*>(smem_raw + pad);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n_contr = (a.L - 1) * (a.mode >= 1 ? 2 : 1);
 
@@ -464,26 +582,60 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
         sm->abase[etid] = v ? a.bt.alpha_off[b] + (long long)k * a.tb.U[p] : 0;
         sm->bbase[etid] = v ? (long long)a.bt.split_off[b] * a.K + (long long)k * cnt : 0;
         for (int w = 0; w < a.mask_words; ++w) {
-          sm->smask[etid][w] = 0u;
-          sm->sneg[etid][w] = 0u;
+          sm->smask[w][etid] = 0u;
+          sm->sneg[w][etid] = 0u;
         }
+
         int off = v ? a.bt.split_off[b] : 0;
         sm->nsplit[etid] = cnt;
+        // pass 1: split masks; pass 2: slots in (word, bit) order with their beta
         for (int e = 0; e < cnt; ++e) {
           int ly = a.bt.split_layer[off + e];
           int j = (int)a.bt.split_idx[off + e];
           int s = a.bt.split_sign[off + e];
-          sm->skey[etid][e] = 0xFFFFu;
           if (ly < 1 || ly > a.L - 1 || j < 0 || j >= a.d[ly] || (s != 1 && s != -1)) {
             atomicCAS(a.status, 0, BCROWN_ERR_ARG);
             continue;
           }
-          sm->skey[etid][e] = (uint16_t)((ly << 8) | j);
           int wd = a.woff[ly] + (j >> 5);
-          sm->smask[etid][wd] |= 1u << (j & 31);
-          if (s == 1) sm->sneg[etid][wd] |= 1u << (j & 31);
+          sm->smask[wd][etid] |= 1u << (j & 31);
+          if (s == 1) sm->sneg[wd][etid] |= 1u << (j & 31);
+        }
+        {
+          int run = 0;
+          for (int w = 0; w < a.mask_words; ++w) {
+            sm->wfirst[w][etid] = (uint8_t)run;
+            run += __popc(sm->smask[w][etid]);
+          }
+        }
+        for (int e = 0; e < cnt; ++e) {
+          int ly = a.bt.split_layer[off + e];
+          int j = (int)a.bt.split_idx[off + e];
+          int s = a.bt.split_sign[off + e];
+          if (ly < 1 || ly > a.L - 1 || j < 0 || j >= a.d[ly] || (s != 1 && s != -1)) continue;
+          const int kslot = split_slot(sm, etid, a.woff[ly] + (j >> 5), j & 31);
+          const long long bi = sm->bbase[etid] + e;
+          sm->sorig[etid][kslot] = (uint8_t)e;
+          sm->sbeta[etid][kslot] = (bi >= 0 && bi < a.n_beta) ? fmaxf(ldg_f32(a.beta + bi, true), 0.f) : 0.f;
         }
         sm->part[0][etid] = sm->part[1][etid] = sm->part[2][etid] = sm->part[3][etid] = 0.f;
+      }
+      if (etid == 32) {
+        // the tile's alpha block (rows are packed in order) and, when optimising, its Adam
+        // moments: pull them towards L2 now, they are read layer by layer below
+        const int r0 = tile * TR, r1 = min(a.R, r0 + TR) - 1;
+        if (r0 <= r1) {
+          const int b0 = r0 / a.K, b1 = r1 / a.K;
+          const long long lo = a.bt.alpha_off[b0] + (long long)(r0 - b0 * a.K) * a.tb.U[a.bt.prop_of[b0]];
+          const long long hi = a.bt.alpha_off[b1] + (long long)(r1 - b1 * a.K + 1) * a.tb.U[a.bt.prop_of[b1]];
+          if (lo >= 0 && hi <= a.n_alpha && hi > lo) {
+            prefetch_l2(a.alpha + lo, (hi - lo) * 4);
+            if (a.mode == 2) {
+              prefetch_l2(a.ma + lo, (hi - lo) * 4);
+              prefetch_l2(a.va + lo, (hi - lo) * 4);
+            }
+          }
+        }
       }
       if (etid == 0) {
         // rows of a tile usually come from one property: then per-neuron tables are loaded once
@@ -502,11 +654,34 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
         ok = false;
         break;
       }
+      {
+        // uniform tile: stage the property's per-neuron tables and input box in shared memory
+        const int pu = sm->uniform_p;
+        if (pu >= 0) {
+          for (int n = etid; n < a.H; n += NEPI * 32) {
+            const size_t g = (size_t)pu * a.H + n;
+            const int rk = a.tb.rank[g];
+            sm->tcode[n] = ((uint32_t)a.tb.code[g] << 16) | (uint32_t)(rk < 0 ? 0xFFFF : (rk & 0xFFFF));
+            sm->tslope[n] = a.tb.slope[g];
+            sm->ticpt[n] = a.tb.icpt[g];
+          }
+          for (int m = etid; m < a.d[0]; m += NEPI * 32) {
+            sm->sxlo[m] = a.x_lo[(size_t)pu * a.d[0] + m];
+            sm->sxhi[m] = a.x_hi[(size_t)pu * a.d[0] + m];
+          }
+        }
+        for (int w = etid; w < a.mask_words; w += NEPI * 32) {
+          unsigned long long m = 0ull;
+          for (int r = 0; r < TR; ++r)
+            if (sm->smask[w][r]) m |= 1ull << r;
+          sm->wrows[w] = m;
+        }
+        if (!epi_sync(sm, eseq, a.status)) {
+          ok = false;
+          break;
+        }
+      }
 
-      // per-thread lb partials for rows 16cg..16cg+15
-      float acc[16];
-#pragma unroll
-      for (int c = 0; c < 16; ++c) acc[c] = 0.f;
 
       // ---------------- top operand: Lambda^(L-1) from Wbar (relaxation of layer L-1)
       {
@@ -516,7 +691,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
         for (int kb = 0; kb < nkb && ok; ++kb) {
           const uint32_t as = aseq + kb;
           const int slot = as % NSLOT;
-          if (!mbar_wait(&sm->act_empty[slot], ((as / NSLOT) & 1) ^ 1, sm, a.status)) {
+          if (!mbar_wait_warp(&sm->act_empty[slot], ((as / NSLOT) & 1) ^ 1, sm, a.status)) {
             ok = false;
             break;
           }
@@ -533,21 +708,26 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
             al[e] = 0.f;
             slope[e] = icpt[e] = 0.f;
             code[e] = -1;
+            int rk = 0;
             if (j < dtop && rv) {
-              const size_t n = (size_t)pr * a.H + a.hoff[i] + j;
-              av[e] = a.Wbar[(size_t)sm->spec[row] * dtop + j];
-              code[e] = a.tb.code[n];
-              slope[e] = a.tb.slope[n];
-              icpt[e] = a.tb.icpt[n];
+              av[e] = ldg_f32(a.Wbar + (size_t)sm->spec[row] * dtop + j, true);
+              if (sm->uniform_p >= 0) {
+                const int n = (int)a.hoff[i] + j;
+                const uint32_t tcv = sm->tcode[n];
+                code[e] = (int)(tcv >> 16);
+                rk = (int)(tcv & 0xFFFF);
+                slope[e] = sm->tslope[n];
+                icpt[e] = sm->ticpt[n];
+              } else {
+                const size_t n = (size_t)pr * a.H + a.hoff[i] + j;
+                code[e] = a.tb.code[n];
+                rk = a.tb.rank[n];
+                slope[e] = a.tb.slope[n];
+                icpt[e] = a.tb.icpt[n];
+              }
             }
-          }
-#pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            const int j = kb * KBLK + c8 * 8 + e;
-            if (code[e] == CODE_UNSTABLE) {
-              const long long ai = sm->abase[row] + a.tb.rank[(size_t)pr * a.H + a.hoff[i] + j];
-              if (ai >= 0 && ai < a.n_alpha) al[e] = a.alpha[ai];
-            }
+            const long long ai = sm->abase[row] + rk;
+            al[e] = ldg_f32(a.alpha + ai, code[e] == CODE_UNSTABLE && ai >= 0 && ai < a.n_alpha);
           }
           float csum = 0.f;
           uint32_t pk[4];
@@ -563,11 +743,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
                 const int wd = a.woff[i] + (j >> 5);
                 const uint32_t bit = 1u << (j & 31);
                 float D, lm = 0.f, bs = 0.f;
-                if (sm->smask[row][wd] & bit) {
-                  const int sg = (sm->sneg[row][wd] & bit) ? 1 : -1;
+                if (sm->smask[wd][row] & bit) {
+                  const int sg = (sm->sneg[wd][row] & bit) ? 1 : -1;
                   D = sg == -1 ? 1.f : 0.f;
-                  const long long bi = beta_slot(a, sm, row, i, j);
-                  if (bi >= 0) bs = fmaxf(a.beta[bi], 0.f) * (float)sg;
+                  bs = sm->sbeta[row][split_slot(sm, row, wd, j & 31)] * (float)sg;
                 } else if (code[ee] == CODE_ACTIVE) D = 1.f;
                 else if (code[ee] == CODE_INACTIVE) D = 0.f;
                 else if (av[ee] >= 0.f) D = fminf(fmaxf(al[ee], 0.f), 1.f);
@@ -601,148 +780,231 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
         const float* bias_next = concretise ? nullptr : a.bias[i - 1];
         for (int mc = 0; mc < nmc && ok; ++mc) {
           const int buf = accseq % NACC;
-          if (!mbar_wait(&sm->acc_full[buf], (accseq / NACC) & 1, sm, a.status)) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
           const int j = mc * MCH + 32 * q + lane;   // output neuron of this thread
-          float v[16];
-          tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * TR + 16 * cg), v);
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&sm->acc_empty[buf]);
-          ++accseq;
+          const bool jin = j < N;
+          const int pu = sm->uniform_p;
+          const int li = i - 1;
+          float uxl = 0.f, uxh = 0.f;
+          int ucode = CODE_INACTIVE, urank = 0;
+          float uslope = 0.f, uicpt = 0.f, bj = 0.f;
           if (concretise) {
-            // lb += sum_m min(A_m x_lo_m, A_m x_hi_m); record sign bits for x*
-            const int pu = sm->uniform_p;
-            float uxl = 0.f, uxh = 0.f;
-            if (pu >= 0 && j < N) {
-              uxl = a.x_lo[(size_t)pu * N + j];
-              uxh = a.x_hi[(size_t)pu * N + j];
-            }
-#pragma unroll
-            for (int c = 0; c < 16; ++c) {
-              const int row = 16 * cg + c;
-              const bool in = j < N && sm->valid[row];
-              float av = v[c];
-              if (in) {
-                float xl = uxl, xh = uxh;
-                if (pu < 0) {
-                  const int p = sm->prop[row];
-                  xl = a.x_lo[(size_t)p * N + j];
-                  xh = a.x_hi[(size_t)p * N + j];
-                }
-                acc[c] += fminf(av * xl, av * xh);
-              }
-              if (a.mode >= 1) {
-                const unsigned bits = __ballot_sync(0xffffffffu, in && av >= 0.f);
-                if (lane == 0 && mc * MCH + 32 * q < MAX_D0) sm->sign[row][(mc * MCH + 32 * q) >> 5] = bits;
-              }
+            if (pu >= 0 && jin) {
+              uxl = sm->sxlo[j];
+              uxh = sm->sxhi[j];
             }
           } else {
-            // relax layer i-1 and write Lambda^(i-1) into the next operand's K block
-            const int kb = (mc * MCH + 32 * q) / KBLK;   // this warp's K block
-            const bool writer = kb < nkb_next;
-            const uint32_t as = aseq + kb;
-            const int slot = as % NSLOT;
-            // two warps (quadrants) share a K block; both wait for it to be free
-            if (writer && !mbar_wait(&sm->act_empty[slot], ((as / NSLOT) & 1) ^ 1, sm, a.status)) {
-              ok = false;
-              break;
-            }
-            const int li = i - 1;
-            const bool jin = j < N;
-            const int pu = sm->uniform_p;
-            int ucode = CODE_INACTIVE, urank = 0;
-            float uslope = 0.f, uicpt = 0.f;
             if (pu >= 0 && jin) {
-              const size_t n = (size_t)pu * a.H + a.hoff[li] + j;
-              ucode = a.tb.code[n];
-              urank = a.tb.rank[n];
-              uslope = a.tb.slope[n];
-              uicpt = a.tb.icpt[n];
+              const int n = (int)a.hoff[li] + j;
+              const uint32_t tcv = sm->tcode[n];
+              ucode = (int)(tcv >> 16);
+              urank = (int)(tcv & 0xFFFF);
+              uslope = sm->tslope[n];
+              uicpt = sm->ticpt[n];
             }
-            const float bj = jin ? bias_next[j] : 0.f;
-            float al[16];
-            // issue the alpha loads of all 16 rows before using any of them
+            if (jin) bj = bias_next[j];
+          }
+          // alpha of 8 rows: loads that do not depend on the accumulator
+          auto load_al = [&](int h, float (&al)[8]) {
 #pragma unroll
-            for (int c = 0; c < 16; ++c) {
-              const int row = 16 * cg + c;
+            for (int c = 0; c < 8; ++c) {
+              const int row = 16 * cg + 8 * h + c;
               al[c] = 0.f;
-              if (jin && sm->valid[row]) {
+              if (!concretise && jin && sm->valid[row]) {
                 int code = ucode, rank = urank;
                 if (pu < 0) {
                   const size_t n = (size_t)sm->prop[row] * a.H + a.hoff[li] + j;
                   code = a.tb.code[n];
                   rank = a.tb.rank[n];
                 }
-                if (code == CODE_UNSTABLE) {
-                  const long long ai = sm->abase[row] + rank;
-                  if (ai >= 0 && ai < a.n_alpha) al[c] = a.alpha[ai];
-                }
+                const long long ai = sm->abase[row] + rank;
+                al[c] = ldg_f32(a.alpha + ai, code == CODE_UNSTABLE && ai >= 0 && ai < a.n_alpha);
               }
             }
-            const int wd = a.woff[li] + (j >> 5);
-            const uint32_t bit = 1u << (j & 31);
+          };
+          const int kb = (mc * MCH + 32 * q) / KBLK;   // this warp's K block of the next operand
+          const bool writer = !concretise && kb < nkb_next;
+          const uint32_t as = aseq + kb;
+          const int slot = as % NSLOT;
+          const int wd = concretise ? 0 : a.woff[li] + (j >> 5);
+          const uint32_t bit = 1u << (j & 31);
+          // 8 rows of the chunk: concretisation, or relaxation of layer i-1 into the next operand
+          auto process = [&](int h, const float (&v)[8], const float (&al)[8]) {
+            float cc[8];
 #pragma unroll
-            for (int c = 0; c < 16; ++c) {
-              const int row = 16 * cg + c;
-              float L = 0.f;
-              if (jin && sm->valid[row]) {
-                const float av = v[c];
-                if (a.mode >= 1)
-                  a.stash[(size_t)(tile * TR + row) * a.H + a.hoff[li] + j] = __float2bfloat16_rn(av);
-                int code = ucode;
-                float slope = uslope, icpt = uicpt;
-                if (pu < 0) {
-                  const size_t n = (size_t)sm->prop[row] * a.H + a.hoff[li] + j;
-                  code = a.tb.code[n];
-                  slope = a.tb.slope[n];
-                  icpt = a.tb.icpt[n];
+            for (int c = 0; c < 8; ++c) {
+              const int row = 16 * cg + 8 * h + c;
+              cc[c] = 0.f;
+              const bool in = jin && sm->valid[row];
+              const float av = v[c];
+              if (concretise) {
+                if (in) {
+                  float xl = uxl, xh = uxh;
+                  if (pu < 0) {
+                    const int p = sm->prop[row];
+                    xl = a.x_lo[(size_t)p * N + j];
+                    xh = a.x_hi[(size_t)p * N + j];
+                  }
+                  cc[c] = fminf(av * xl, av * xh);
                 }
-                float D, lm = 0.f, bs = 0.f;
-                if (sm->smask[row][wd] & bit) {
-                  const int sg = (sm->sneg[row][wd] & bit) ? 1 : -1;
-                  D = sg == -1 ? 1.f : 0.f;
-                  const long long bi = beta_slot(a, sm, row, li, j);
-                  if (bi >= 0) bs = fmaxf(a.beta[bi], 0.f) * (float)sg;
-                } else if (code == CODE_ACTIVE) D = 1.f;
-                else if (code == CODE_INACTIVE) D = 0.f;
-                else if (av >= 0.f) D = fminf(fmaxf(al[c], 0.f), 1.f);
-                else {
-                  D = slope;
-                  lm = icpt;
+                if (a.mode >= 1) {
+                  const unsigned bits = __ballot_sync(0xffffffffu, in && av >= 0.f);
+                  if (lane == 0 && mc * MCH + 32 * q < MAX_D0) sm->sign[row][(mc * MCH + 32 * q) >> 5] = bits;
                 }
-                L = fmaf(av, D, bs);
-                acc[c] += fmaf(L, bj, av * lm);
+              } else {
+                float L = 0.f;
+                if (in) {
+                  if (a.mode >= 1)
+                    a.stash[(size_t)(tile * TR + row) * a.H + a.hoff[li] + j] = __float2bfloat16_rn(av);
+                  int code = ucode;
+                  float slope = uslope, icpt = uicpt;
+                  if (pu < 0) {
+                    const size_t n = (size_t)sm->prop[row] * a.H + a.hoff[li] + j;
+                    code = a.tb.code[n];
+                    slope = a.tb.slope[n];
+                    icpt = a.tb.icpt[n];
+                  }
+                  float D, lm = 0.f, bs = 0.f;
+                  if (((sm->wrows[wd] >> row) & 1ull) && (sm->smask[wd][row] & bit)) {
+                    const int sg = (sm->sneg[wd][row] & bit) ? 1 : -1;
+                    D = sg == -1 ? 1.f : 0.f;
+                    bs = sm->sbeta[row][split_slot(sm, row, wd, lane)] * (float)sg;
+                  } else if (code == CODE_ACTIVE) D = 1.f;
+                  else if (code == CODE_INACTIVE) D = 0.f;
+                  else if (av >= 0.f) D = fminf(fmaxf(al[c], 0.f), 1.f);
+                  else {
+                    D = slope;
+                    lm = icpt;
+                  }
+                  L = fmaf(av, D, bs);
+                  cc[c] = fmaf(L, bj, av * lm);
+                }
+                if (writer)
+                  *reinterpret_cast<__nv_bfloat16*>(sm->act[slot] + act_off(row, j & (KBLK - 1))) = __float2bfloat16_rn(L);
               }
-              if (writer)
-                *reinterpret_cast<__nv_bfloat16*>(sm->act[slot] + act_off(row, j & (KBLK - 1))) = __float2bfloat16_rn(L);
             }
-            // the block is complete when all 16 warps arrived: the 8 writer warps here, the
-            // 8 warps of the other quadrant pair after the contraction (count NEPI per block)
-            if (writer) {
-              fence_proxy_async();
-              __syncwarp();
-              if (lane == 0) mbar_arrive(&sm->act_full[slot]);
+            const float rs = reduce8(cc);
+            if ((lane & 3) == 0) atomicAdd(&sm->part[q][16 * cg + 8 * h + (lane >> 2)], rs);
+          };
+          const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * TR + 16 * cg);
+          if (pu >= 0) {
+            // ---- property-uniform tile: the neuron's code is the same on all 16 rows
+            const int nvalid = min(TR, a.R - tile * TR);
+            const bool unst = !concretise && jin && ucode == CODE_UNSTABLE;
+            float al[16];
+            const uint32_t rbits = concretise ? 0u : (uint32_t)(sm->wrows[wd] >> (16 * cg)) & 0xFFFFu;
+            {
+              const long long abase_j = (long long)urank;
+#pragma unroll
+              for (int c = 0; c < 16; ++c) {
+                const int row = 16 * cg + c;
+                const long long ai = sm->abase[row] + abase_j;
+                al[c] = ldg_f32(a.alpha + ai, unst && row < nvalid && ai < a.n_alpha);
+              }
             }
+            if (!mbar_wait_warp(&sm->acc_full[buf], (accseq / NACC) & 1, sm, a.status)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            if (writer && !mbar_wait_warp(&sm->act_empty[slot], ((as / NSLOT) & 1) ^ 1, sm, a.status)) {
+              ok = false;
+              break;
+            }
+            const bool act = ucode == CODE_ACTIVE;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              float v[8];
+              tmem_ld8(tbase + 8 * h, v);
+              if (h == 1) {
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sm->acc_empty[buf]);
+                ++accseq;
+              }
+              float cc[8];
+#pragma unroll
+              for (int c8 = 0; c8 < 8; ++c8) {
+                const int c = 8 * h + c8;
+                const int row = 16 * cg + c;
+                const bool in = jin && row < nvalid;
+                const float av = in ? v[c8] : 0.f;
+                if (concretise) {
+                  cc[c8] = fminf(av * uxl, av * uxh);
+                  if (a.mode >= 1) {
+                    const unsigned bits = __ballot_sync(0xffffffffu, in && av >= 0.f);
+                    if (lane == 0 && mc * MCH + 32 * q < MAX_D0) sm->sign[row][(mc * MCH + 32 * q) >> 5] = bits;
+                  }
+                } else {
+                  // Lemma 2.1: D = 1 active, 0 inactive, alpha (A >= 0) or the chord slope (A < 0)
+                  const bool pos = av >= 0.f;
+                  float D = act ? 1.f : (unst ? (pos ? fminf(fmaxf(al[c], 0.f), 1.f) : uslope) : 0.f);
+                  float lm = (unst && !pos) ? uicpt : 0.f;
+                  float bs = 0.f;
+                  if (((rbits >> c) & 1u) && (sm->smask[wd][row] & bit)) {
+                    // split neuron (Eq. 3): D = 1 for z >= 0, 0 for z < 0, plus beta S
+                    const int sg = (sm->sneg[wd][row] & bit) ? 1 : -1;
+                    D = sg == -1 ? 1.f : 0.f;
+                    lm = 0.f;
+                    bs = sm->sbeta[row][split_slot(sm, row, wd, lane)] * (float)sg;
+                  }
+                  const float L = in ? fmaf(av, D, bs) : 0.f;
+                  cc[c8] = fmaf(L, bj, av * lm);
+                  if (a.mode >= 1 && in)
+                    a.stash[(size_t)(tile * TR + row) * a.H + a.hoff[li] + j] = __float2bfloat16_rn(av);
+                  if (writer)
+                    *reinterpret_cast<__nv_bfloat16*>(sm->act[slot] + act_off(row, j & (KBLK - 1))) = __float2bfloat16_rn(L);
+                }
+              }
+              const float rs = reduce8(cc);
+              if ((lane & 3) == 0) atomicAdd(&sm->part[q][16 * cg + 8 * h + (lane >> 2)], rs);
+            }
+          } else {
+          float al0[8], al1[8];
+          load_al(0, al0);   // issued before waiting for the accumulator
+          if (!mbar_wait_warp(&sm->acc_full[buf], (accseq / NACC) & 1, sm, a.status)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          float v0[8];
+          tmem_ld8(tbase, v0);
+          load_al(1, al1);
+          // two warps (quadrants) share a K block; both wait for it to be free
+          if (writer && !mbar_wait_warp(&sm->act_empty[slot], ((as / NSLOT) & 1) ^ 1, sm, a.status)) {
+            ok = false;
+            break;
+          }
+          process(0, v0, al0);
+          float v1[8];
+          tmem_ld8(tbase + 8, v1);
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&sm->acc_empty[buf]);
+          ++accseq;
+          process(1, v1, al1);
+          }
+          // the block is complete when all 16 warps arrived: the 8 writer warps here, the
+          // 8 warps of the other quadrant pair after the contraction (count NEPI per block)
+          if (writer) {
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm->act_full[slot]);
           }
         }
         if (!concretise) {
           // warps whose quadrant maps to the other K block of each chunk must still arrive on
           // blocks they did not write: 8 writer warps per block, 8 more arrivals needed.
-          if (ok && lane == 0) {
+          if (ok) {
             for (int kk = 0; kk < nkb_next; ++kk) {
               // the warp writes block kk iff (kk % 2) == q / 2 within its chunk
               if ((kk & 1) != (q >> 1)) {
                 const uint32_t as = aseq + kk;
                 // wait until the block's previous consumer released it before arriving
-                if (!mbar_wait(&sm->act_empty[as % NSLOT], ((as / NSLOT) & 1) ^ 1, sm, a.status)) {
+                if (!mbar_wait_warp(&sm->act_empty[as % NSLOT], ((as / NSLOT) & 1) ^ 1, sm, a.status)) {
                   ok = false;
                   break;
                 }
-                mbar_arrive(&sm->act_full[as % NSLOT]);
+                if (lane == 0) mbar_arrive(&sm->act_full[as % NSLOT]);
               }
             }
           }
@@ -751,17 +1013,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
       }
       if (!ok) break;
 
-      // ---------------- lb of each row: reduce the per-thread partials
-#pragma unroll
-      for (int c = 0; c < 16; ++c) {
-        float s = acc[c];
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        acc[c] = s;
-      }
-      if (lane == 0) {
-#pragma unroll
-        for (int c = 0; c < 16; ++c) atomicAdd(&sm->part[q][16 * cg + c], acc[c]);
-      }
+      // ---------------- lb of each row: the four lane quadrants' partial sums
       if (!epi_sync(sm, eseq, a.status)) {
         ok = false;
         break;
@@ -801,7 +1053,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
         for (int kb = 0; kb < nkb && ok; ++kb) {
           const uint32_t as = aseq + kb;
           const int slot = as % NSLOT;
-          if (!mbar_wait(&sm->act_empty[slot], ((as / NSLOT) & 1) ^ 1, sm, a.status)) {
+          if (!mbar_wait_warp(&sm->act_empty[slot], ((as / NSLOT) & 1) ^ 1, sm, a.status)) {
             ok = false;
             break;
           }
@@ -817,7 +1069,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
               float x = 0.f;
               if (m < d0 && sm->valid[row]) {
                 const bool pos = (sm->sign[row][m >> 5] >> (m & 31)) & 1u;
-                x = pos ? a.x_lo[(size_t)p * d0 + m] : a.x_hi[(size_t)p * d0 + m];
+                if (sm->uniform_p >= 0) x = pos ? sm->sxlo[m] : sm->sxhi[m];
+                else x = pos ? a.x_lo[(size_t)p * d0 + m] : a.x_hi[(size_t)p * d0 + m];
               }
               xv[h] = x;
             }
@@ -839,88 +1092,80 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
         const float* bias = a.bias[i];
         for (int mc = 0; mc < nmc && ok; ++mc) {
           const int buf = accseq % NACC;
-          if (!mbar_wait(&sm->acc_full[buf], (accseq / NACC) & 1, sm, a.status)) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
           const int j = mc * MCH + 32 * q + lane;
-          float v[16];
-          tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * TR + 16 * cg), v);
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&sm->acc_empty[buf]);
-          ++accseq;
-          const int kb = (mc * MCH + 32 * q) / KBLK;
-          const bool writer = produce && kb < nkb_next;
-          const uint32_t as = aseq + kb;
-          const int slot = as % NSLOT;
-          if (writer && !mbar_wait(&sm->act_empty[slot], ((as / NSLOT) & 1) ^ 1, sm, a.status)) {
-            ok = false;
-            break;
-          }
           const bool jin = j < N;
           const int pu = sm->uniform_p;
           int ucode = CODE_INACTIVE, urank = 0;
           float uslope = 0.f, uicpt = 0.f;
           if (pu >= 0 && jin) {
-            const size_t n = (size_t)pu * a.H + a.hoff[i] + j;
-            ucode = a.tb.code[n];
-            urank = a.tb.rank[n];
-            uslope = a.tb.slope[n];
-            uicpt = a.tb.icpt[n];
+            const int n = (int)a.hoff[i] + j;
+            const uint32_t tcv = sm->tcode[n];
+            ucode = (int)(tcv >> 16);
+            urank = (int)(tcv & 0xFFFF);
+            uslope = sm->tslope[n];
+            uicpt = sm->ticpt[n];
           }
           const float bj = jin ? bias[j] : 0.f;
           const int wd = a.woff[i] + (j >> 5);
           const uint32_t bit = 1u << (j & 31);
+          // per-row inputs of 8 rows: A^(i)_j (stash), alpha, Adam moments
+          auto load8 = [&](int h, float (&av)[8], float (&th)[8]) {
 #pragma unroll
-          for (int h8 = 0; h8 < 4; ++h8) {
-            float av[4], th[4], mm[4], vq[4];
-            long long ai[4];
-            // loads of 8 rows first (stash, alpha, Adam moments), then the arithmetic
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-              const int row = 16 * cg + 4 * h8 + c;
-              av[c] = th[c] = mm[c] = vq[c] = 0.f;
-              ai[c] = -1;
+            for (int c = 0; c < 8; ++c) {
+              const int row = 16 * cg + 8 * h + c;
+              av[c] = th[c] = 0.f;
               if (jin && sm->valid[row]) {
-                av[c] = (i == a.L - 1) ? a.Wbar[(size_t)sm->spec[row] * N + j]
-                                       : __bfloat162float(a.stash[(size_t)(tile * TR + row) * a.H + a.hoff[i] + j]);
+                if (i == a.L - 1) av[c] = ldg_f32(a.Wbar + (size_t)sm->spec[row] * N + j, true);
+                else av[c] = ldg_bf16(a.stash + (size_t)(tile * TR + row) * a.H + a.hoff[i] + j, true);
                 int code = ucode, rank = urank;
                 if (pu < 0) {
                   const size_t n = (size_t)sm->prop[row] * a.H + a.hoff[i] + j;
                   code = a.tb.code[n];
                   rank = a.tb.rank[n];
                 }
-                if (code == CODE_UNSTABLE) {
-                  const long long x = sm->abase[row] + rank;
-                  if (x >= 0 && x < a.n_alpha) {
-                    ai[c] = x;
-                    th[c] = a.alpha[x];
-                    if (a.mode == 2) {
-                      mm[c] = a.ma[x];
-                      vq[c] = a.va[x];
-                    }
-                  }
-                }
+                const long long x = sm->abase[row] + rank;
+                th[c] = ldg_f32(a.alpha + x, code == CODE_UNSTABLE && x >= 0 && x < a.n_alpha);
               }
             }
+          };
+          float avA[8], thA[8];
+          load8(0, avA, thA);   // issued before waiting for the accumulator
+          if (!mbar_wait_warp(&sm->acc_full[buf], (accseq / NACC) & 1, sm, a.status)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * TR + 16 * cg);
+          float v0[8];
+          tmem_ld8(tbase, v0);
+          float avB[8], thB[8];
+          load8(1, avB, thB);
+          const int kb = (mc * MCH + 32 * q) / KBLK;
+          const bool writer = produce && kb < nkb_next;
+          const uint32_t as = aseq + kb;
+          const int slot = as % NSLOT;
+          if (writer && !mbar_wait_warp(&sm->act_empty[slot], ((as / NSLOT) & 1) ^ 1, sm, a.status)) {
+            ok = false;
+            break;
+          }
+          auto compute8 = [&](int h, const float (&vz)[8], const float (&av)[8], const float (&th)[8]) {
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-              const int row = 16 * cg + 4 * h8 + c;
+            for (int c = 0; c < 8; ++c) {
+              const int row = 16 * cg + 8 * h + c;
               float hv = 0.f;
               if (jin && sm->valid[row]) {
-                const float z = v[4 * h8 + c] + bj;
-                int code = ucode;
+                const float z = vz[c] + bj;
+                int code = ucode, rank = urank;
                 float slope = uslope, icpt = uicpt;
                 if (pu < 0) {
                   const size_t n = (size_t)sm->prop[row] * a.H + a.hoff[i] + j;
                   code = a.tb.code[n];
+                  rank = a.tb.rank[n];
                   slope = a.tb.slope[n];
                   icpt = a.tb.icpt[n];
                 }
-                const bool split = sm->smask[row][wd] & bit;
-                const int sg = split ? ((sm->sneg[row][wd] & bit) ? 1 : -1) : 0;
+                const bool split = sm->smask[wd][row] & bit;
+                const int sg = split ? ((sm->sneg[wd][row] & bit) ? 1 : -1) : 0;
                 float D, lm = 0.f;
                 if (sg == -1) D = 1.f;
                 else if (sg == 1) D = 0.f;
@@ -931,21 +1176,25 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
                   D = slope;
                   lm = icpt;
                 }
-                if (ai[c] >= 0) {
-                  const float g = (sg == 0 && av[c] >= 0.f) ? av[c] * z : 0.f;
-                  if (a.mode == 1) {
-                    a.dalpha[ai[c]] = g;
-                  } else {
-                    if (sm->improved[row]) a.a_best[ai[c]] = th[c];
-                    const float m = a.beta1 * mm[c] + (1.f - a.beta1) * g;
-                    const float vv = a.beta2 * vq[c] + (1.f - a.beta2) * g * g;
-                    a.ma[ai[c]] = m;
-                    a.va[ai[c]] = vv;
-                    a.a_cur[ai[c]] = fminf(fmaxf(th[c] + a.lr_a * (m / a.bc1) / (sqrtf(vv / a.bc2) + a.eps), 0.f), 1.f);
+                if (code == CODE_UNSTABLE) {
+                  const long long ai = sm->abase[row] + rank;
+                  if (ai >= 0 && ai < a.n_alpha) {
+                    const float g = (sg == 0 && av[c] >= 0.f) ? av[c] * z : 0.f;
+                    if (a.mode == 1) {
+                      a.dalpha[ai] = g;
+                    } else {
+                      if (sm->improved[row]) a.a_best[ai] = th[c];
+                      const float m = a.beta1 * a.ma[ai] + (1.f - a.beta1) * g;
+                      const float vv = a.beta2 * a.va[ai] + (1.f - a.beta2) * g * g;
+                      a.ma[ai] = m;
+                      a.va[ai] = vv;
+                      a.a_cur[ai] = fminf(fmaxf(th[c] + a.lr_a * (m / a.bc1) / (sqrtf(vv / a.bc2) + a.eps), 0.f), 1.f);
+                    }
                   }
                 }
                 if (sg != 0) {
-                  const long long bi = beta_slot(a, sm, row, i, j);
+                  long long bi = sm->bbase[row] + sm->sorig[row][split_slot(sm, row, wd, j & 31)];
+                  if (bi >= a.n_beta) bi = -1;
                   if (bi >= 0) {
                     const float g = (float)sg * z;
                     if (a.mode == 1) {
@@ -966,7 +1215,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
               if (writer)
                 *reinterpret_cast<__nv_bfloat16*>(sm->act[slot] + act_off(row, j & (KBLK - 1))) = __float2bfloat16_rn(hv);
             }
-          }
+          };
+          compute8(0, v0, avA, thA);
+          float v1[8];
+          tmem_ld8(tbase + 8, v1);
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&sm->acc_empty[buf]);
+          ++accseq;
+          compute8(1, v1, avB, thB);
           if (writer) {
             fence_proxy_async();
             __syncwarp();
@@ -974,15 +1231,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
           }
         }
         if (produce) {
-          if (ok && lane == 0) {
+          if (ok) {
             for (int kk = 0; kk < nkb_next; ++kk) {
               if ((kk & 1) != (q >> 1)) {
                 const uint32_t as = aseq + kk;
-                if (!mbar_wait(&sm->act_empty[as % NSLOT], ((as / NSLOT) & 1) ^ 1, sm, a.status)) {
+                if (!mbar_wait_warp(&sm->act_empty[as % NSLOT], ((as / NSLOT) & 1) ^ 1, sm, a.status)) {
                   ok = false;
                   break;
                 }
-                mbar_arrive(&sm->act_full[as % NSLOT]);
+                if (lane == 0) mbar_arrive(&sm->act_full[as % NSLOT]);
               }
             }
           }
@@ -1040,7 +1297,7 @@ bool tc_supported(const bcrown_net* net) {
     if (net->d[i] > MAX_HIDDEN) return false;
     words += (net->d[i] + 31) / 32;
   }
-  if (words > MAX_MASK_WORDS) return false;
+  if (words > MAX_MASK_WORDS || net->H > MAX_H) return false;
   // the forward contraction of layer 1 streams d0 in K blocks: its M chunks must fit the
   // accumulator ring (hidden widths <= 256 give at most 2)
   if ((net->d[1] + MCH - 1) / MCH > NACC) return false;
