@@ -306,18 +306,10 @@ extern "C" int bcrown_optimize(bcrown_net* net, const bcrown_domain* dom, const 
   }
   launch_fill(pl.best_lb, R, -INFINITY, s);
   BatchView bv = view_of(batch);
-  const bool fused = cfg->precision == BCROWN_BF16 && tc_supported(net);
   for (int t = 0; t < cfg->iters; ++t) {
     float fac = std::pow(cfg->decay, (float)t);
     float bc1 = 1.f - std::pow(cfg->adam_beta1, (float)(t + 1));
     float bc2 = 1.f - std::pow(cfg->adam_beta2, (float)(t + 1));
-    if (fused) {
-      // one launch: bound, adjoint, projected Adam and best tracking for every row
-      BC_CHECK(tc_adam_step(net, dom, batch, pl.tb, pl.tc_ws, pl.tc_ws_bytes, pl.a_cur, alpha, pl.ma, pl.va, pl.b_cur,
-                            beta, pl.mb, pl.vb, pl.best_lb, cfg->lr_alpha * fac, cfg->lr_beta * fac, cfg->adam_beta1,
-                            cfg->adam_beta2, cfg->adam_eps, bc1, bc2, s));
-      continue;
-    }
     BC_CHECK(run_bound(net, dom, batch, pl, cfg->precision, true, pl.a_cur, pl.b_cur, pl.lb_t, pl.ga, pl.gb, s));
     ProfScope ps(net, BCROWN_PROF_ADAM, s);
     launch_adam(R, net->K, bv, pl.U, dom->n_props, pl.lb_t, pl.best_lb, pl.a_cur, alpha, pl.ga, pl.ma, pl.va,

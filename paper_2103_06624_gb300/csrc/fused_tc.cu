@@ -58,21 +58,19 @@ constexpr int MAX_HIDDEN = 256;
 
 struct Smem {
   uint8_t act[NSLOT][SLOT_BYTES];        // 64 KB, 1024-aligned slots
-  uint8_t w[NSTAGE][STAGE_BYTES];        // 96 KB
+  uint8_t w[NSTAGE][STAGE_BYTES];        // 64 KB
   uint32_t sign[TR][SIGN_WORDS];         // 8 KB: A^(0) >= 0 per (row, input)
   uint32_t smask[MAX_MASK_WORDS][TR];    // split present, [word][row]: a warp reads its 16 rows at once
   uint32_t sneg[MAX_MASK_WORDS][TR];     // split sign +1 (z < 0)
   unsigned long long wrows[MAX_MASK_WORDS];  // rows with any split in mask word w
   float part[4][TR];                     // lb partial sums per lane quadrant
-  float lbrow[TR];
-  int improved[TR];
-  long long abase[TR];
-  long long bbase[TR];
+  long long abase[TR];                   // first alpha of the row
+  long long bbase[TR];                   // first beta of the row
   int prop[TR];
   int spec[TR];
-  int sub[TR];
   int valid[TR];
-  int nsplit[TR];
+  int scnt[TR];                          // the row's split count and first split entry
+  int soff[TR];
   uint8_t sorig[TR][BCROWN_MAX_SPLITS];  // the row's splits in (mask word, bit) order: list position
   float sbeta[TR][BCROWN_MAX_SPLITS];    //   and beta (clamped at 0)
   uint8_t wfirst[MAX_MASK_WORDS][TR];    // splits of the row in mask words before w
@@ -81,11 +79,13 @@ struct Smem {
   float ticpt[MAX_H];                    //   upper chord intercept
   float sxlo[MAX_D0];                    //   input box
   float sxhi[MAX_D0];
+  float sbias[MAX_H];                    // hidden-layer biases, by global hidden index
   int uniform_p;                         // property shared by every valid row of the tile, or -1
+  int fast;                              // uniform_p >= 0 and every row below the tile's end valid
   uint64_t act_full[NSLOT], act_empty[NSLOT];
   uint64_t w_full[NSTAGE], w_empty[NSTAGE];
   uint64_t acc_full[NACC], acc_empty[NACC];
-  uint64_t epi;   // epilogue-wide barrier (16 warp arrivals per phase)
+  uint64_t epi;   // epilogue-wide barrier (NEPI warp arrivals per phase)
   uint64_t done;
   uint32_t tmem_base;
   int abort_flag;
@@ -94,7 +94,7 @@ struct Smem {
 static_assert(sizeof(Smem) + 1024 <= 232448, "shared memory plan exceeds 227 KB per CTA");
 
 struct Args {
-  int L, K, P, H, R, n_tiles, mode;   // mode 0 bound, 1 gradient, 2 Adam step
+  int L, K, P, H, R, n_tiles;
   int d[MAXL + 1];
   long long hoff[MAXL + 1];           // first global hidden index of layer i (1-based)
   int woff[MAXL + 1];                 // first mask word of layer i
@@ -112,25 +112,18 @@ struct Args {
   float* lb;
   float* dalpha;
   float* dbeta;
-  __nv_bfloat16* stash;               // [R][H]
-  float* a_cur;
-  float* a_best;
-  float* ma;
-  float* va;
-  float* b_cur;
-  float* b_best;
-  float* mb;
-  float* vb;
-  float* best_lb;
-  float lr_a, lr_b, beta1, beta2, eps, bc1, bc2;
+  __nv_bfloat16* stash;               // [tile][H][TR]: A^(i) of the backward pass, per neuron
   int* status;
   int box_bwd[MAXL + 1];
   int box_fwd[MAXL + 1];
 };
 
+// Every CTA streams the same weights at about the same time; NREP copies of them, CTA b
+// reading copy b % NREP, spread those requests over more L2 lines.
+constexpr int NREP = 4;
 struct Maps {
-  CUtensorMap bwd[MAXL + 1];   // Wt^(i): [d_{i-1}][Kp(d_i)] bf16, rows = output neurons of the backward
-  CUtensorMap fwd[MAXL + 1];   // W^(i):  [d_i][Kp(d_{i-1})] bf16, rows = output neurons of the forward
+  CUtensorMap bwd[NREP][MAXL + 1];   // Wt^(i): [d_{i-1}][Kp(d_i)] bf16, rows = output neurons of the backward
+  CUtensorMap fwd[NREP][MAXL + 1];   // W^(i):  [d_i][Kp(d_{i-1})] bf16, rows = output neurons of the forward
 };
 
 // ------------------------------------------------------------------------------------------
@@ -158,12 +151,24 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// As mbar_try, but a thread whose phase is not complete yet is suspended (for at most about
+// `ns` nanoseconds) until it completes, instead of returning at once: waiting threads then
+// leave the issue slots and the shared-memory pipe to the warps doing work.
+__device__ __forceinline__ bool mbar_try_sleep(uint64_t* b, uint32_t parity, uint32_t ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(su32(b)), "r"(parity), "r"(ns)
+      : "memory");
+  return ok != 0;
+}
 // Bounded wait (about 2 s of SM clock); on expiry records a timeout and raises the abort flag.
 __device__ __noinline__ bool mbar_wait(uint64_t* b, uint32_t parity, Smem* sm, int* status) {
   if (mbar_try(b, parity)) return true;
   long long t0 = clock64();
   while (true) {
-    if (mbar_try(b, parity)) return true;
+    if (mbar_try_sleep(b, parity, 20000u)) return true;
     if (*(volatile int*)&sm->abort_flag) return false;
     if (clock64() - t0 > 4000000000LL) {
       atomicCAS(status, 0, BCROWN_ERR_TIMEOUT);
@@ -332,6 +337,21 @@ __device__ __forceinline__ float reduce8(float (&v)[8]) {
   return r + __shfl_xor_sync(0xffffffffu, r, 1);
 }
 
+// 16-byte global load (zero when !pred) and store.
+__device__ __forceinline__ uint4 ldg_v4(const void* p, bool pred) {
+  uint4 v;
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %5, 0;\n\tmov.b32 %0, 0;\n\tmov.b32 %1, 0;\n\tmov.b32 %2, 0;\n\t"
+      "mov.b32 %3, 0;\n\t@q ld.global.v4.b32 {%0, %1, %2, %3}, [%4];\n\t}"
+      : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+      : "l"(p), "r"((uint32_t)pred)
+      : "memory");
+  return v;
+}
+__device__ __forceinline__ void stg_v4(void* p, uint4 v) {
+  asm volatile("st.global.v4.b32 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w) : "memory");
+}
+
 // L2 prefetch of [p, p + bytes): only the 16-byte aligned interior, so it stays in bounds.
 __device__ __forceinline__ void prefetch_l2(const void* p, long long bytes) {
   uintptr_t lo = ((uintptr_t)p + 15) & ~(uintptr_t)15;
@@ -377,6 +397,8 @@ __device__ __forceinline__ int split_slot(const Smem* sm, int row, int w, int bi
 // ------------------------------------------------------------------------------------------
 // The kernel
 // ------------------------------------------------------------------------------------------
+// MODE 0: bound only; MODE 1: bound and gradient (adjoint pass).
+template <int MODE>
 __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ Maps maps, const Args a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // pointer arithmetic on the shared array (not through an integer) keeps the shared address
@@ -384,11 +406,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
   const uint32_t pad = (1024u - (su32(smem_raw) & 1023u)) & 1023u;
   Smem* sm = reinterpret_cast<Smem*>(smem_raw + pad);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n_contr = (a.L - 1) * (a.mode >= 1 ? 2 : 1);
+  const int n_contr = (a.L - 1) * (MODE >= 1 ? 2 : 1);
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < NSLOT; ++i) {
-      mbar_init(&sm->act_full[i], NEPI);
+      mbar_init(&sm->act_full[i], NEPI / 2);   // the 8 warps that write a K block
       mbar_init(&sm->act_empty[i], 1);
     }
     for (int i = 0; i < NSTAGE; ++i) {
@@ -425,7 +447,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
           int layer, N, K;
           bool fwd;
           contraction(a, ci, layer, N, K, fwd);
-          const CUtensorMap* map = fwd ? &maps.fwd[layer] : &maps.bwd[layer];
+          const int rep = blockIdx.x % NREP;
+          const CUtensorMap* map = fwd ? &maps.fwd[rep][layer] : &maps.bwd[rep][layer];
           const uint32_t bytes = (uint32_t)(fwd ? a.box_fwd[layer] : a.box_bwd[layer]) * 128u;
           const int nmc = nmc_of(N), nkb = nkb_of(K);
           const bool stream = nkb > NSLOT / 2;   // same order as the MMA issuer
@@ -546,116 +569,111 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
   } else {
     // ---------------------------------------------------------------- epilogue (warps 0..15)
     const int q = warp & 3;          // TMEM lane quadrant: neurons 32q..32q+31 of an M chunk
-    const int cg = warp >> 2;        // column group: rows 16cg..16cg+15 of the tile
+    const int cg = warp >> 2;        // column group: tile rows 16cg..16cg+15
+    const int r0 = 16 * cg;          // first tile row of this thread
     const int etid = threadIdx.x;    // 0..511
+    const int pg = warp & 1;         // producer group: writes the K blocks kb with kb % 2 == pg
+    const int gt = (warp >> 1) * 32 + lane;   // thread index within the producer group, 0..255
+    const int prow = gt >> 2, pc16 = gt & 3;  // producer thread: tile row, 16 consecutive k
     uint32_t aseq = 0, accseq = 0, eseq = 0;
     bool ok = true;
     const int dtop = a.d[a.L - 1];
 
-    // Produce activation K blocks from a per-element function: every warp writes the
-    // elements it owns; all 16 warps arrive on each block's full barrier.
+    // hidden-layer biases, indexed by global hidden neuron, for the whole launch
+    for (int i = 1; i < a.L; ++i)
+      for (int j = etid; j < a.d[i]; j += NEPI * 32) sm->sbias[a.hoff[i] + j] = a.bias[i][j];
+
     for (int tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x) {
-      // ---------------- per-row set-up
+      const int nvalid = min(TR, a.R - tile * TR);
+      // ---------------- tile set-up, step 1: per-row scalars (one thread per row)
       if (etid < TR) {
-        int r = tile * TR + etid;
-        int v = r < a.R;
-        int b = 0, k = 0, p = 0;
+        const int row = etid;
+        int v = row < nvalid;
+        int k = 0, p = 0, cnt = 0, off = 0;
+        long long ab = 0, bb = 0;
         if (v) {
-          b = r / a.K;
+          const int r = tile * TR + row;
+          const int b = r / a.K;
           k = r - b * a.K;
           p = a.bt.prop_of[b];
-          if (p < 0 || p >= a.P) {
+          cnt = a.bt.split_cnt[b];
+          off = a.bt.split_off[b];
+          const long long ao = a.bt.alpha_off[b];
+          if (p < 0 || p >= a.P || cnt < 0 || cnt > BCROWN_MAX_SPLITS || off < 0) {
             atomicCAS(a.status, 0, BCROWN_ERR_ARG);
             v = 0;
-            p = 0;
-          }
-        }
-        sm->valid[etid] = v;
-        sm->sub[etid] = b;
-        sm->spec[etid] = k;
-        sm->prop[etid] = p;
-        int cnt = v ? a.bt.split_cnt[b] : 0;
-        if (cnt < 0 || cnt > BCROWN_MAX_SPLITS) {
-          atomicCAS(a.status, 0, BCROWN_ERR_ARG);
-          cnt = 0;
-        }
-        sm->abase[etid] = v ? a.bt.alpha_off[b] + (long long)k * a.tb.U[p] : 0;
-        sm->bbase[etid] = v ? (long long)a.bt.split_off[b] * a.K + (long long)k * cnt : 0;
-        for (int w = 0; w < a.mask_words; ++w) {
-          sm->smask[w][etid] = 0u;
-          sm->sneg[w][etid] = 0u;
-        }
-
-        int off = v ? a.bt.split_off[b] : 0;
-        sm->nsplit[etid] = cnt;
-        // pass 1: split masks; pass 2: slots in (word, bit) order with their beta
-        for (int e = 0; e < cnt; ++e) {
-          int ly = a.bt.split_layer[off + e];
-          int j = (int)a.bt.split_idx[off + e];
-          int s = a.bt.split_sign[off + e];
-          if (ly < 1 || ly > a.L - 1 || j < 0 || j >= a.d[ly] || (s != 1 && s != -1)) {
-            atomicCAS(a.status, 0, BCROWN_ERR_ARG);
-            continue;
-          }
-          int wd = a.woff[ly] + (j >> 5);
-          sm->smask[wd][etid] |= 1u << (j & 31);
-          if (s == 1) sm->sneg[wd][etid] |= 1u << (j & 31);
-        }
-        {
-          int run = 0;
-          for (int w = 0; w < a.mask_words; ++w) {
-            sm->wfirst[w][etid] = (uint8_t)run;
-            run += __popc(sm->smask[w][etid]);
-          }
-        }
-        for (int e = 0; e < cnt; ++e) {
-          int ly = a.bt.split_layer[off + e];
-          int j = (int)a.bt.split_idx[off + e];
-          int s = a.bt.split_sign[off + e];
-          if (ly < 1 || ly > a.L - 1 || j < 0 || j >= a.d[ly] || (s != 1 && s != -1)) continue;
-          const int kslot = split_slot(sm, etid, a.woff[ly] + (j >> 5), j & 31);
-          const long long bi = sm->bbase[etid] + e;
-          sm->sorig[etid][kslot] = (uint8_t)e;
-          sm->sbeta[etid][kslot] = (bi >= 0 && bi < a.n_beta) ? fmaxf(ldg_f32(a.beta + bi, true), 0.f) : 0.f;
-        }
-        sm->part[0][etid] = sm->part[1][etid] = sm->part[2][etid] = sm->part[3][etid] = 0.f;
-      }
-      if (etid == 32) {
-        // the tile's alpha block (rows are packed in order) and, when optimising, its Adam
-        // moments: pull them towards L2 now, they are read layer by layer below
-        const int r0 = tile * TR, r1 = min(a.R, r0 + TR) - 1;
-        if (r0 <= r1) {
-          const int b0 = r0 / a.K, b1 = r1 / a.K;
-          const long long lo = a.bt.alpha_off[b0] + (long long)(r0 - b0 * a.K) * a.tb.U[a.bt.prop_of[b0]];
-          const long long hi = a.bt.alpha_off[b1] + (long long)(r1 - b1 * a.K + 1) * a.tb.U[a.bt.prop_of[b1]];
-          if (lo >= 0 && hi <= a.n_alpha && hi > lo) {
-            prefetch_l2(a.alpha + lo, (hi - lo) * 4);
-            if (a.mode == 2) {
-              prefetch_l2(a.ma + lo, (hi - lo) * 4);
-              prefetch_l2(a.va + lo, (hi - lo) * 4);
+          } else {
+            const int U = a.tb.U[p];
+            ab = ao + (long long)k * U;
+            bb = (long long)off * a.K + (long long)k * cnt;
+            // every alpha of the row must lie in the array: then no per-element check is needed
+            if (ab < 0 || ab + U > a.n_alpha) {
+              atomicCAS(a.status, 0, BCROWN_ERR_ARG);
+              v = 0;
             }
           }
         }
+        sm->valid[row] = v;
+        sm->spec[row] = v ? k : 0;
+        sm->prop[row] = v ? p : 0;
+        sm->scnt[row] = v ? cnt : 0;
+        sm->soff[row] = off;
+        sm->abase[row] = v ? ab : 0;
+        sm->bbase[row] = v ? bb : 0;
+        sm->part[0][row] = sm->part[1][row] = sm->part[2][row] = sm->part[3][row] = 0.f;
       }
-      if (etid == 0) {
-        // rows of a tile usually come from one property: then per-neuron tables are loaded once
-        const int r0 = tile * TR, r1 = min(a.R, r0 + TR) - 1;
-        int pu = -1;
-        if (r0 <= r1) {
-          const int b0 = r0 / a.K, b1 = r1 / a.K;
-          pu = a.bt.prop_of[b0];
-          for (int b = b0 + 1; b <= b1; ++b)
-            if (a.bt.prop_of[b] != pu) pu = -1;
-          if (pu < 0 || pu >= a.P) pu = -1;
+      for (int x = etid; x < a.mask_words * TR; x += NEPI * 32) {
+        (&sm->smask[0][0])[x] = 0u;
+        (&sm->sneg[0][0])[x] = 0u;
+      }
+      if (etid == TR) {
+        // the tile's alpha block (rows are packed in order): pull it towards L2 now, it is
+        // read layer by layer below
+        const int ra = tile * TR, rb = tile * TR + nvalid - 1;
+        const int b0 = ra / a.K, b1 = rb / a.K;
+        const int p0 = a.bt.prop_of[b0], p1 = a.bt.prop_of[b1];
+        if (p0 >= 0 && p0 < a.P && p1 >= 0 && p1 < a.P) {
+          const long long lo = a.bt.alpha_off[b0] + (long long)(ra - b0 * a.K) * a.tb.U[p0];
+          const long long hi = a.bt.alpha_off[b1] + (long long)(rb - b1 * a.K + 1) * a.tb.U[p1];
+          if (lo >= 0 && hi <= a.n_alpha && hi > lo) prefetch_l2(a.alpha + lo, (hi - lo) * 4);
         }
+      }
+      if (etid == TR + 32) {
+        // rows of a tile usually come from one property: then per-neuron tables are staged once
+        const int b0 = (tile * TR) / a.K, b1 = (tile * TR + nvalid - 1) / a.K;
+        int pu = a.bt.prop_of[b0];
+        for (int b = b0 + 1; b <= b1; ++b)
+          if (a.bt.prop_of[b] != pu) pu = -1;
+        if (pu < 0 || pu >= a.P) pu = -1;
         sm->uniform_p = pu;
       }
       if (!epi_sync(sm, eseq, a.status)) {
         ok = false;
         break;
       }
+      // ---------------- step 2: split masks (8 threads per row), tables and box of a uniform tile
+      int ent[BCROWN_MAX_SPLITS / 8];   // this thread's split entries: mask word << 5 | bit, or -1
       {
-        // uniform tile: stage the property's per-neuron tables and input box in shared memory
+        const int row = etid >> 3, e0 = etid & 7;
+        const int cnt = sm->scnt[row], off = sm->soff[row];
+#pragma unroll
+        for (int m = 0; m < BCROWN_MAX_SPLITS / 8; ++m) {
+          const int e = e0 + 8 * m;
+          ent[m] = -1;
+          if (e < cnt) {
+            const int ly = a.bt.split_layer[off + e];
+            const int j = (int)a.bt.split_idx[off + e];
+            const int s = a.bt.split_sign[off + e];
+            if (ly < 1 || ly > a.L - 1 || j < 0 || j >= a.d[ly] || (s != 1 && s != -1)) {
+              atomicCAS(a.status, 0, BCROWN_ERR_ARG);
+            } else {
+              const int wd = a.woff[ly] + (j >> 5);
+              atomicOr(&sm->smask[wd][row], 1u << (j & 31));
+              if (s == 1) atomicOr(&sm->sneg[wd][row], 1u << (j & 31));
+              ent[m] = (wd << 5) | (j & 31);
+            }
+          }
+        }
         const int pu = sm->uniform_p;
         if (pu >= 0) {
           for (int n = etid; n < a.H; n += NEPI * 32) {
@@ -670,247 +688,183 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
             sm->sxhi[m] = a.x_hi[(size_t)pu * a.d[0] + m];
           }
         }
-        for (int w = etid; w < a.mask_words; w += NEPI * 32) {
-          unsigned long long m = 0ull;
-          for (int r = 0; r < TR; ++r)
-            if (sm->smask[w][r]) m |= 1ull << r;
-          sm->wrows[w] = m;
-        }
-        if (!epi_sync(sm, eseq, a.status)) {
-          ok = false;
-          break;
+        if (etid == 0) {
+          // fast path: one property and every row below nvalid valid
+          int f = pu >= 0;
+          for (int r = 0; r < nvalid; ++r) f &= sm->valid[r];
+          sm->fast = f;
         }
       }
-
+      if (!epi_sync(sm, eseq, a.status)) {
+        ok = false;
+        break;
+      }
+      // ---------------- step 3: per-row split counts before each mask word, rows per word
+      if (etid < TR) {
+        int run = 0;
+        for (int w = 0; w < a.mask_words; ++w) {
+          sm->wfirst[w][etid] = (uint8_t)run;
+          run += __popc(sm->smask[w][etid]);
+        }
+      } else if (etid < TR + a.mask_words) {
+        const int w = etid - TR;
+        unsigned long long m = 0ull;
+        for (int r = 0; r < TR; ++r)
+          if (sm->smask[w][r]) m |= 1ull << r;
+        sm->wrows[w] = m;
+      }
+      if (!epi_sync(sm, eseq, a.status)) {
+        ok = false;
+        break;
+      }
+      // ---------------- step 4: each split's slot in (word, bit) order, its list position and beta
+      {
+        const int row = etid >> 3, e0 = etid & 7;
+#pragma unroll
+        for (int m = 0; m < BCROWN_MAX_SPLITS / 8; ++m) {
+          if (ent[m] >= 0) {
+            const int e = e0 + 8 * m;
+            const int ks = split_slot(sm, row, ent[m] >> 5, ent[m] & 31);
+            const long long bi = sm->bbase[row] + e;
+            sm->sorig[row][ks] = (uint8_t)e;
+            sm->sbeta[row][ks] = (bi >= 0 && bi < a.n_beta) ? fmaxf(ldg_f32(a.beta + bi, true), 0.f) : 0.f;
+          }
+        }
+      }
+      if (!epi_sync(sm, eseq, a.status)) {
+        ok = false;
+        break;
+      }
+      const bool fast = sm->fast != 0;
+      const int nvt = nvalid - r0;   // rows of this thread below nvalid (may be <= 0 or > 16)
 
       // ---------------- top operand: Lambda^(L-1) from Wbar (relaxation of layer L-1)
+      // K block kb is written by the 8 warps of producer group kb % 2: thread -> (row, 16 k)
       {
         const int i = a.L - 1;
         const int nkb = nkb_of(dtop);
-        const float* bias = a.bias[i];
-        for (int kb = 0; kb < nkb && ok; ++kb) {
+        const bool rv = prow < nvalid && sm->valid[prow];
+        const int spec = sm->spec[prow];
+        const int pr = sm->prop[prow];
+        const long long abr = sm->abase[prow];
+        float csum = 0.f;
+        for (int kb = pg; kb < nkb && ok; kb += 2) {
           const uint32_t as = aseq + kb;
           const int slot = as % NSLOT;
+          const int j0 = kb * KBLK + pc16 * 16;
+          float av[16], al[16];
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const int j = j0 + e;
+            const bool in = rv && j < dtop;
+            av[e] = ldg_f32(a.Wbar + (size_t)spec * dtop + j, in);
+            int code = CODE_INACTIVE, rank = 0;
+            if (in) {
+              if (fast) {
+                const uint32_t t = sm->tcode[a.hoff[i] + j];
+                code = (int)(t >> 16);
+                rank = (int)(t & 0xFFFF);
+              } else {
+                const size_t g = (size_t)pr * a.H + a.hoff[i] + j;
+                code = a.tb.code[g];
+                rank = a.tb.rank[g];
+              }
+            }
+            al[e] = ldg_f32(a.alpha + abr + rank, in && code == CODE_UNSTABLE);
+          }
           if (!mbar_wait_warp(&sm->act_empty[slot], ((as / NSLOT) & 1) ^ 1, sm, a.status)) {
             ok = false;
             break;
           }
-          // 64 k x 64 rows = 4096 elements, 8 per thread: thread -> (row = etid / 8, k = 8 (etid % 8) + e)
-          const int row = etid >> 3, c8 = etid & 7;
-          const bool rv = sm->valid[row];
-          const int pr = sm->prop[row];
-          float av[8], al[8], slope[8], icpt[8];
-          int code[8];
+          uint32_t pk[8];
 #pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            const int j = kb * KBLK + c8 * 8 + e;
-            av[e] = 0.f;
-            al[e] = 0.f;
-            slope[e] = icpt[e] = 0.f;
-            code[e] = -1;
-            int rk = 0;
-            if (j < dtop && rv) {
-              av[e] = ldg_f32(a.Wbar + (size_t)sm->spec[row] * dtop + j, true);
-              if (sm->uniform_p >= 0) {
-                const int n = (int)a.hoff[i] + j;
-                const uint32_t tcv = sm->tcode[n];
-                code[e] = (int)(tcv >> 16);
-                rk = (int)(tcv & 0xFFFF);
-                slope[e] = sm->tslope[n];
-                icpt[e] = sm->ticpt[n];
-              } else {
-                const size_t n = (size_t)pr * a.H + a.hoff[i] + j;
-                code[e] = a.tb.code[n];
-                rk = a.tb.rank[n];
-                slope[e] = a.tb.slope[n];
-                icpt[e] = a.tb.icpt[n];
-              }
-            }
-            const long long ai = sm->abase[row] + rk;
-            al[e] = ldg_f32(a.alpha + ai, code[e] == CODE_UNSTABLE && ai >= 0 && ai < a.n_alpha);
-          }
-          float csum = 0.f;
-          uint32_t pk[4];
-#pragma unroll
-          for (int e = 0; e < 8; e += 2) {
+          for (int e = 0; e < 16; e += 2) {
             float lv[2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
               const int ee = e + h;
-              const int j = kb * KBLK + c8 * 8 + ee;
+              const int j = j0 + ee;
               float L = 0.f;
-              if (code[ee] >= 0) {
+              if (rv && j < dtop) {
+                const long long n = a.hoff[i] + j;
+                int code;
+                float slope, icpt;
+                if (fast) {
+                  code = (int)(sm->tcode[n] >> 16);
+                  slope = sm->tslope[n];
+                  icpt = sm->ticpt[n];
+                } else {
+                  const size_t g = (size_t)pr * a.H + n;
+                  code = a.tb.code[g];
+                  slope = a.tb.slope[g];
+                  icpt = a.tb.icpt[g];
+                }
                 const int wd = a.woff[i] + (j >> 5);
                 const uint32_t bit = 1u << (j & 31);
                 float D, lm = 0.f, bs = 0.f;
-                if (sm->smask[wd][row] & bit) {
-                  const int sg = (sm->sneg[wd][row] & bit) ? 1 : -1;
+                if (sm->smask[wd][prow] & bit) {
+                  // split neuron (Eq. 3): D = 1 for z >= 0, 0 for z < 0, plus beta S
+                  const int sg = (sm->sneg[wd][prow] & bit) ? 1 : -1;
                   D = sg == -1 ? 1.f : 0.f;
-                  bs = sm->sbeta[row][split_slot(sm, row, wd, j & 31)] * (float)sg;
-                } else if (code[ee] == CODE_ACTIVE) D = 1.f;
-                else if (code[ee] == CODE_INACTIVE) D = 0.f;
-                else if (av[ee] >= 0.f) D = fminf(fmaxf(al[ee], 0.f), 1.f);
+                  bs = sm->sbeta[prow][split_slot(sm, prow, wd, j & 31)] * (float)sg;
+                } else if (code == CODE_ACTIVE) D = 1.f;
+                else if (code == CODE_INACTIVE) D = 0.f;
+                else if (av[ee] >= 0.f) D = __saturatef(al[ee]);
                 else {
-                  D = slope[ee];
-                  lm = icpt[ee];
+                  D = slope;
+                  lm = icpt;
                 }
                 L = fmaf(av[ee], D, bs);
-                csum += fmaf(L, bias[j], av[ee] * lm);
+                csum += fmaf(L, sm->sbias[n], av[ee] * lm);
+              }
+              if constexpr (MODE >= 1) {
+                // A^(L-1) = Wbar rows, for the adjoint pass (zero on rows that take no part)
+                if (j < dtop) a.stash[((size_t)tile * a.H + a.hoff[i] + j) * TR + prow] = __float2bfloat16_rn(av[ee]);
               }
               lv[h] = L;
             }
             __nv_bfloat162 v2 = __floats2bfloat162_rn(lv[0], lv[1]);
             pk[e >> 1] = *reinterpret_cast<uint32_t*>(&v2);
           }
-          if (rv) atomicAdd(&sm->part[0][row], csum);
-          *reinterpret_cast<uint4*>(sm->act[slot] + act_off(row, c8 * 8)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+          *reinterpret_cast<uint4*>(sm->act[slot] + act_off(prow, pc16 * 16)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+          *reinterpret_cast<uint4*>(sm->act[slot] + act_off(prow, pc16 * 16 + 8)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
           fence_proxy_async();
           __syncwarp();
           if (lane == 0) mbar_arrive(&sm->act_full[slot]);
         }
         aseq += nkb;
+        if (rv) atomicAdd(&sm->part[0][prow], csum);
       }
+
+      // per-thread lb partial sums of its 16 rows over the lanes' neurons (whole backward pass)
+      float racc[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) racc[c] = 0.f;
 
       // ---------------- backward contractions: output A^(i-1) of layer i's transpose
       for (int i = a.L - 1; i >= 1 && ok; --i) {
         const int N = a.d[i - 1];
         const int nmc = nmc_of(N);
         const bool concretise = (i == 1);
+        const int li = i - 1;
         const int nkb_next = concretise ? 0 : nkb_of(N);
-        const float* bias_next = concretise ? nullptr : a.bias[i - 1];
         for (int mc = 0; mc < nmc && ok; ++mc) {
           const int buf = accseq % NACC;
-          const int j = mc * MCH + 32 * q + lane;   // output neuron of this thread
+          const int j = mc * MCH + 32 * q + lane;   // output neuron of this lane
           const bool jin = j < N;
-          const int pu = sm->uniform_p;
-          const int li = i - 1;
-          float uxl = 0.f, uxh = 0.f;
-          int ucode = CODE_INACTIVE, urank = 0;
-          float uslope = 0.f, uicpt = 0.f, bj = 0.f;
+          const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * TR + r0);
           if (concretise) {
-            if (pu >= 0 && jin) {
+            // ---- lb += sum_m min(A_m x_lo_m, A_m x_hi_m) (Eq. beta_crown_lp); sign bits of A^(0) for x*
+            float uxl = 0.f, uxh = 0.f;
+            if (fast && jin) {
               uxl = sm->sxlo[j];
               uxh = sm->sxhi[j];
-            }
-          } else {
-            if (pu >= 0 && jin) {
-              const int n = (int)a.hoff[li] + j;
-              const uint32_t tcv = sm->tcode[n];
-              ucode = (int)(tcv >> 16);
-              urank = (int)(tcv & 0xFFFF);
-              uslope = sm->tslope[n];
-              uicpt = sm->ticpt[n];
-            }
-            if (jin) bj = bias_next[j];
-          }
-          // alpha of 8 rows: loads that do not depend on the accumulator
-          auto load_al = [&](int h, float (&al)[8]) {
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-              const int row = 16 * cg + 8 * h + c;
-              al[c] = 0.f;
-              if (!concretise && jin && sm->valid[row]) {
-                int code = ucode, rank = urank;
-                if (pu < 0) {
-                  const size_t n = (size_t)sm->prop[row] * a.H + a.hoff[li] + j;
-                  code = a.tb.code[n];
-                  rank = a.tb.rank[n];
-                }
-                const long long ai = sm->abase[row] + rank;
-                al[c] = ldg_f32(a.alpha + ai, code == CODE_UNSTABLE && ai >= 0 && ai < a.n_alpha);
-              }
-            }
-          };
-          const int kb = (mc * MCH + 32 * q) / KBLK;   // this warp's K block of the next operand
-          const bool writer = !concretise && kb < nkb_next;
-          const uint32_t as = aseq + kb;
-          const int slot = as % NSLOT;
-          const int wd = concretise ? 0 : a.woff[li] + (j >> 5);
-          const uint32_t bit = 1u << (j & 31);
-          // 8 rows of the chunk: concretisation, or relaxation of layer i-1 into the next operand
-          auto process = [&](int h, const float (&v)[8], const float (&al)[8]) {
-            float cc[8];
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-              const int row = 16 * cg + 8 * h + c;
-              cc[c] = 0.f;
-              const bool in = jin && sm->valid[row];
-              const float av = v[c];
-              if (concretise) {
-                if (in) {
-                  float xl = uxl, xh = uxh;
-                  if (pu < 0) {
-                    const int p = sm->prop[row];
-                    xl = a.x_lo[(size_t)p * N + j];
-                    xh = a.x_hi[(size_t)p * N + j];
-                  }
-                  cc[c] = fminf(av * xl, av * xh);
-                }
-                if (a.mode >= 1) {
-                  const unsigned bits = __ballot_sync(0xffffffffu, in && av >= 0.f);
-                  if (lane == 0 && mc * MCH + 32 * q < MAX_D0) sm->sign[row][(mc * MCH + 32 * q) >> 5] = bits;
-                }
-              } else {
-                float L = 0.f;
-                if (in) {
-                  if (a.mode >= 1)
-                    a.stash[(size_t)(tile * TR + row) * a.H + a.hoff[li] + j] = __float2bfloat16_rn(av);
-                  int code = ucode;
-                  float slope = uslope, icpt = uicpt;
-                  if (pu < 0) {
-                    const size_t n = (size_t)sm->prop[row] * a.H + a.hoff[li] + j;
-                    code = a.tb.code[n];
-                    slope = a.tb.slope[n];
-                    icpt = a.tb.icpt[n];
-                  }
-                  float D, lm = 0.f, bs = 0.f;
-                  if (((sm->wrows[wd] >> row) & 1ull) && (sm->smask[wd][row] & bit)) {
-                    const int sg = (sm->sneg[wd][row] & bit) ? 1 : -1;
-                    D = sg == -1 ? 1.f : 0.f;
-                    bs = sm->sbeta[row][split_slot(sm, row, wd, lane)] * (float)sg;
-                  } else if (code == CODE_ACTIVE) D = 1.f;
-                  else if (code == CODE_INACTIVE) D = 0.f;
-                  else if (av >= 0.f) D = fminf(fmaxf(al[c], 0.f), 1.f);
-                  else {
-                    D = slope;
-                    lm = icpt;
-                  }
-                  L = fmaf(av, D, bs);
-                  cc[c] = fmaf(L, bj, av * lm);
-                }
-                if (writer)
-                  *reinterpret_cast<__nv_bfloat16*>(sm->act[slot] + act_off(row, j & (KBLK - 1))) = __float2bfloat16_rn(L);
-              }
-            }
-            const float rs = reduce8(cc);
-            if ((lane & 3) == 0) atomicAdd(&sm->part[q][16 * cg + 8 * h + (lane >> 2)], rs);
-          };
-          const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * TR + 16 * cg);
-          if (pu >= 0) {
-            // ---- property-uniform tile: the neuron's code is the same on all 16 rows
-            const int nvalid = min(TR, a.R - tile * TR);
-            const bool unst = !concretise && jin && ucode == CODE_UNSTABLE;
-            float al[16];
-            const uint32_t rbits = concretise ? 0u : (uint32_t)(sm->wrows[wd] >> (16 * cg)) & 0xFFFFu;
-            {
-              const long long abase_j = (long long)urank;
-#pragma unroll
-              for (int c = 0; c < 16; ++c) {
-                const int row = 16 * cg + c;
-                const long long ai = sm->abase[row] + abase_j;
-                al[c] = ldg_f32(a.alpha + ai, unst && row < nvalid && ai < a.n_alpha);
-              }
             }
             if (!mbar_wait_warp(&sm->acc_full[buf], (accseq / NACC) & 1, sm, a.status)) {
               ok = false;
               break;
             }
             tc_fence_after();
-            if (writer && !mbar_wait_warp(&sm->act_empty[slot], ((as / NSLOT) & 1) ^ 1, sm, a.status)) {
-              ok = false;
-              break;
-            }
-            const bool act = ucode == CODE_ACTIVE;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
               float v[8];
@@ -921,155 +875,203 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
                 if (lane == 0) mbar_arrive(&sm->acc_empty[buf]);
                 ++accseq;
               }
-              float cc[8];
 #pragma unroll
               for (int c8 = 0; c8 < 8; ++c8) {
                 const int c = 8 * h + c8;
-                const int row = 16 * cg + c;
-                const bool in = jin && row < nvalid;
-                const float av = in ? v[c8] : 0.f;
-                if (concretise) {
-                  cc[c8] = fminf(av * uxl, av * uxh);
-                  if (a.mode >= 1) {
-                    const unsigned bits = __ballot_sync(0xffffffffu, in && av >= 0.f);
-                    if (lane == 0 && mc * MCH + 32 * q < MAX_D0) sm->sign[row][(mc * MCH + 32 * q) >> 5] = bits;
+                const float av = v[c8];
+                float xl = uxl, xh = uxh;
+                if (!fast) {
+                  const int row = r0 + c;
+                  const bool in = jin && row < nvalid && sm->valid[row];
+                  xl = xh = 0.f;
+                  if (in) {
+                    const int p = sm->prop[row];
+                    xl = a.x_lo[(size_t)p * N + j];
+                    xh = a.x_hi[(size_t)p * N + j];
                   }
-                } else {
-                  // Lemma 2.1: D = 1 active, 0 inactive, alpha (A >= 0) or the chord slope (A < 0)
-                  const bool pos = av >= 0.f;
-                  float D = act ? 1.f : (unst ? (pos ? fminf(fmaxf(al[c], 0.f), 1.f) : uslope) : 0.f);
-                  float lm = (unst && !pos) ? uicpt : 0.f;
-                  float bs = 0.f;
-                  if (((rbits >> c) & 1u) && (sm->smask[wd][row] & bit)) {
-                    // split neuron (Eq. 3): D = 1 for z >= 0, 0 for z < 0, plus beta S
-                    const int sg = (sm->sneg[wd][row] & bit) ? 1 : -1;
-                    D = sg == -1 ? 1.f : 0.f;
-                    lm = 0.f;
-                    bs = sm->sbeta[row][split_slot(sm, row, wd, lane)] * (float)sg;
-                  }
-                  const float L = in ? fmaf(av, D, bs) : 0.f;
-                  cc[c8] = fmaf(L, bj, av * lm);
-                  if (a.mode >= 1 && in)
-                    a.stash[(size_t)(tile * TR + row) * a.H + a.hoff[li] + j] = __float2bfloat16_rn(av);
-                  if (writer)
-                    *reinterpret_cast<__nv_bfloat16*>(sm->act[slot] + act_off(row, j & (KBLK - 1))) = __float2bfloat16_rn(L);
+                }
+                racc[c] += fminf(av * xl, av * xh);
+                if constexpr (MODE >= 1) {
+                  const unsigned bits = __ballot_sync(0xffffffffu, jin && av >= 0.f);
+                  if (lane == 0 && mc * MCH + 32 * q < MAX_D0) sm->sign[r0 + c][(mc * MCH + 32 * q) >> 5] = bits;
                 }
               }
-              const float rs = reduce8(cc);
-              if ((lane & 3) == 0) atomicAdd(&sm->part[q][16 * cg + 8 * h + (lane >> 2)], rs);
             }
-          } else {
-          float al0[8], al1[8];
-          load_al(0, al0);   // issued before waiting for the accumulator
+            continue;
+          }
+          // ---- relaxation of layer i-1 (Lemma 2.1 / Eq. definition_D, split override of Eq. 3)
+          // D = 1 active, 0 inactive; unstable: alpha where A >= 0, the chord slope (+ intercept
+          // lambda) where A < 0; a split neuron takes D = 1 or 0 and adds beta S.
+          const long long n = a.hoff[li] + j;
+          int code = CODE_INACTIVE, rank = 0;
+          float dneg = 0.f, lneg = 0.f, bj = 0.f;
+          if (jin) {
+            bj = sm->sbias[n];
+            if (fast) {
+              const uint32_t t = sm->tcode[n];
+              code = (int)(t >> 16);
+              rank = (int)(t & 0xFFFF);
+              dneg = code == CODE_ACTIVE ? 1.f : (code == CODE_UNSTABLE ? sm->tslope[n] : 0.f);
+              lneg = code == CODE_UNSTABLE ? sm->ticpt[n] : 0.f;
+            }
+          }
+          const bool unst = code == CODE_UNSTABLE;
+          const float apos = code == CODE_ACTIVE ? 1.f : 0.f;
+          const int kb = (mc * MCH + 32 * q) / KBLK;   // this warp's K block of the next operand
+          const bool writer = kb < nkb_next;
+          const uint32_t as = aseq + kb;
+          const int slot = as % NSLOT;
+          // split bits of the warp's 32 neurons (none when they all lie past the layer's end)
+          const int wd = a.woff[li] + ((mc * MCH + 32 * q) >> 5);
+          const uint32_t bit = 1u << lane;
+          const uint32_t rbits = mc * MCH + 32 * q < N ? (uint32_t)(sm->wrows[wd] >> r0) & 0xFFFFu : 0u;
+          // alpha of the 16 rows, issued before waiting for the accumulator
+          float al[16];
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            const int row = r0 + c;
+            if (fast) {
+              al[c] = ldg_f32(a.alpha + sm->abase[row] + rank, unst && c < nvt);
+            } else {
+              al[c] = 0.f;
+              if (jin && row < nvalid && sm->valid[row]) {
+                const size_t g = (size_t)sm->prop[row] * a.H + n;
+                if (a.tb.code[g] == CODE_UNSTABLE) al[c] = ldg_f32(a.alpha + sm->abase[row] + a.tb.rank[g], true);
+              }
+            }
+          }
           if (!mbar_wait_warp(&sm->acc_full[buf], (accseq / NACC) & 1, sm, a.status)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          float v0[8];
-          tmem_ld8(tbase, v0);
-          load_al(1, al1);
-          // two warps (quadrants) share a K block; both wait for it to be free
           if (writer && !mbar_wait_warp(&sm->act_empty[slot], ((as / NSLOT) & 1) ^ 1, sm, a.status)) {
             ok = false;
             break;
           }
-          process(0, v0, al0);
-          float v1[8];
-          tmem_ld8(tbase + 8, v1);
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&sm->acc_empty[buf]);
-          ++accseq;
-          process(1, v1, al1);
+          // byte offset of (row r0 + 8h + c8, k = j % 64) in the slot: row & 7 == c8
+          const int kk = j & (KBLK - 1);
+          uint8_t* aslot = sm->act[slot] + r0 * 128 + ((kk & 7) << 1);
+          const uint32_t kx = (uint32_t)(kk >> 3) << 4;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            float v[8];
+            tmem_ld8(tbase + 8 * h, v);
+            if (h == 1) {
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive(&sm->acc_empty[buf]);
+              ++accseq;
+            }
+#pragma unroll
+            for (int c8 = 0; c8 < 8; ++c8) {
+              const int c = 8 * h + c8;
+              const int row = r0 + c;
+              const float av = v[c8];
+              float D, lm, bs = 0.f;
+              if (fast) {
+                const bool pos = av >= 0.f;
+                D = pos ? __saturatef(al[c] + apos) : dneg;
+                lm = pos ? 0.f : lneg;
+              } else {
+                D = 0.f;
+                lm = 0.f;
+                if (jin && row < nvalid && sm->valid[row]) {
+                  const size_t g = (size_t)sm->prop[row] * a.H + n;
+                  const int cd = a.tb.code[g];
+                  if (cd == CODE_ACTIVE) D = 1.f;
+                  else if (cd == CODE_UNSTABLE) {
+                    if (av >= 0.f) D = __saturatef(al[c]);
+                    else {
+                      D = a.tb.slope[g];
+                      lm = a.tb.icpt[g];
+                    }
+                  }
+                }
+              }
+              if ((rbits >> c) & 1u) {
+                if (sm->smask[wd][row] & bit) {
+                  const int sg = (sm->sneg[wd][row] & bit) ? 1 : -1;
+                  D = sg == -1 ? 1.f : 0.f;
+                  lm = 0.f;
+                  bs = sm->sbeta[row][split_slot(sm, row, wd, lane)] * (float)sg;
+                }
+              }
+              const float L = fmaf(av, D, bs);
+              racc[c] = fmaf(L, bj, fmaf(av, lm, racc[c]));
+              if (writer)
+                *reinterpret_cast<__nv_bfloat16*>(aslot + (8 * h + c8) * 128 + (kx ^ (uint32_t)(c8 << 4))) =
+                    __float2bfloat16_rn(L);
+            }
+            if constexpr (MODE >= 1) {
+              // A^(i-1) of the 8 rows for the adjoint pass: one 16-byte store per lane
+              if (jin) {
+                uint32_t pk[4];
+#pragma unroll
+                for (int e = 0; e < 8; e += 2) {
+                  __nv_bfloat162 v2 = __floats2bfloat162_rn(v[e], v[e + 1]);
+                  pk[e >> 1] = *reinterpret_cast<uint32_t*>(&v2);
+                }
+                stg_v4(a.stash + ((size_t)tile * a.H + n) * TR + r0 + 8 * h, make_uint4(pk[0], pk[1], pk[2], pk[3]));
+              }
+            }
           }
-          // the block is complete when all 16 warps arrived: the 8 writer warps here, the
-          // 8 warps of the other quadrant pair after the contraction (count NEPI per block)
+          // each K block is complete once its 8 writer warps arrived
           if (writer) {
             fence_proxy_async();
             __syncwarp();
             if (lane == 0) mbar_arrive(&sm->act_full[slot]);
           }
         }
-        if (!concretise) {
-          // warps whose quadrant maps to the other K block of each chunk must still arrive on
-          // blocks they did not write: 8 writer warps per block, 8 more arrivals needed.
-          if (ok) {
-            for (int kk = 0; kk < nkb_next; ++kk) {
-              // the warp writes block kk iff (kk % 2) == q / 2 within its chunk
-              if ((kk & 1) != (q >> 1)) {
-                const uint32_t as = aseq + kk;
-                // wait until the block's previous consumer released it before arriving
-                if (!mbar_wait_warp(&sm->act_empty[as % NSLOT], ((as / NSLOT) & 1) ^ 1, sm, a.status)) {
-                  ok = false;
-                  break;
-                }
-                if (lane == 0) mbar_arrive(&sm->act_full[as % NSLOT]);
-              }
-            }
-          }
-          aseq += nkb_next;
-        }
+        aseq += nkb_next;
       }
       if (!ok) break;
 
-      // ---------------- lb of each row: the four lane quadrants' partial sums
+      // ---------------- lb of each row: reduce the lanes' partial sums, then the quadrants'
+      {
+        const float rs = reduce16(racc);
+        if ((lane & 1) == 0) atomicAdd(&sm->part[q][r0 + (lane >> 1)], rs);
+      }
       if (!epi_sync(sm, eseq, a.status)) {
         ok = false;
         break;
       }
-      if (etid < TR) {
+      if (etid < nvalid && sm->valid[etid]) {
         const int row = etid;
-        if (sm->valid[row]) {
-          const int r = tile * TR + row;
-          float lbv = a.bbar[sm->spec[row]] + ((sm->part[0][row] + sm->part[1][row]) + (sm->part[2][row] + sm->part[3][row]));
-          if (!isfinite(lbv)) {
-            atomicCAS(a.status, 0, BCROWN_ERR_NONFINITE);
-            lbv = -INFINITY;
-          }
-          if (a.mode == 2) {
-            const float best = a.best_lb[r];
-            const int imp = lbv > best;
-            sm->improved[row] = imp;
-            if (imp) a.best_lb[r] = lbv;
-          } else {
-            a.lb[r] = lbv;
-          }
-          sm->lbrow[row] = lbv;
-        } else {
-          sm->improved[row] = 0;
+        float lbv = a.bbar[sm->spec[row]] + ((sm->part[0][row] + sm->part[1][row]) + (sm->part[2][row] + sm->part[3][row]));
+        if (!isfinite(lbv)) {
+          atomicCAS(a.status, 0, BCROWN_ERR_NONFINITE);
+          lbv = -INFINITY;
         }
+        a.lb[tile * TR + row] = lbv;
       }
-      if (!epi_sync(sm, eseq, a.status)) {
-        ok = false;
-        break;
-      }
-      if (a.mode == 0) continue;
+      if constexpr (MODE == 0) continue;
 
       // ---------------- adjoint: x* operand (K blocks of d0), then forward contractions
       {
         const int d0 = a.d[0];
         const int nkb = nkb_of(d0);
-        for (int kb = 0; kb < nkb && ok; ++kb) {
+        const bool rv = prow < nvalid && sm->valid[prow];
+        const int p = sm->prop[prow];
+        for (int kb = pg; kb < nkb && ok; kb += 2) {
           const uint32_t as = aseq + kb;
           const int slot = as % NSLOT;
           if (!mbar_wait_warp(&sm->act_empty[slot], ((as / NSLOT) & 1) ^ 1, sm, a.status)) {
             ok = false;
             break;
           }
-          const int row = etid >> 3, c8 = etid & 7;
-          uint32_t pk[4];
-          const int p = sm->prop[row];
+          uint32_t pk[8];
 #pragma unroll
-          for (int e = 0; e < 8; e += 2) {
+          for (int e = 0; e < 16; e += 2) {
             float xv[2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-              const int m = kb * KBLK + c8 * 8 + e + h;
+              const int m = kb * KBLK + pc16 * 16 + e + h;
               float x = 0.f;
-              if (m < d0 && sm->valid[row]) {
-                const bool pos = (sm->sign[row][m >> 5] >> (m & 31)) & 1u;
-                if (sm->uniform_p >= 0) x = pos ? sm->sxlo[m] : sm->sxhi[m];
+              if (m < d0 && rv) {
+                // x* minimises A^(0) x over the box: x_lo where A^(0) >= 0, else x_hi
+                const bool pos = (sm->sign[prow][m >> 5] >> (m & 31)) & 1u;
+                if (fast) x = pos ? sm->sxlo[m] : sm->sxhi[m];
                 else x = pos ? a.x_lo[(size_t)p * d0 + m] : a.x_hi[(size_t)p * d0 + m];
               }
               xv[h] = x;
@@ -1077,174 +1079,147 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
             __nv_bfloat162 v2 = __floats2bfloat162_rn(xv[0], xv[1]);
             pk[e >> 1] = *reinterpret_cast<uint32_t*>(&v2);
           }
-          *reinterpret_cast<uint4*>(sm->act[slot] + act_off(row, c8 * 8)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+          *reinterpret_cast<uint4*>(sm->act[slot] + act_off(prow, pc16 * 16)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+          *reinterpret_cast<uint4*>(sm->act[slot] + act_off(prow, pc16 * 16 + 8)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
           fence_proxy_async();
           __syncwarp();
           if (lane == 0) mbar_arrive(&sm->act_full[slot]);
         }
         aseq += nkb;
       }
+      // zhat^(i) = W^(i) h^(i-1) + b^(i); dalpha = A zhat (unstable, unsplit, A >= 0), dbeta = S zhat;
+      // h^(i) = D zhat + lambda is the next forward operand
       for (int i = 1; i <= a.L - 1 && ok; ++i) {
         const int N = a.d[i];
         const int nmc = nmc_of(N);
-        const bool produce = i + 1 <= a.L - 1;
-        const int nkb_next = produce ? nkb_of(N) : 0;
-        const float* bias = a.bias[i];
+        const int nkb_next = (i + 1 <= a.L - 1) ? nkb_of(N) : 0;
         for (int mc = 0; mc < nmc && ok; ++mc) {
           const int buf = accseq % NACC;
           const int j = mc * MCH + 32 * q + lane;
           const bool jin = j < N;
-          const int pu = sm->uniform_p;
-          int ucode = CODE_INACTIVE, urank = 0;
-          float uslope = 0.f, uicpt = 0.f;
-          if (pu >= 0 && jin) {
-            const int n = (int)a.hoff[i] + j;
-            const uint32_t tcv = sm->tcode[n];
-            ucode = (int)(tcv >> 16);
-            urank = (int)(tcv & 0xFFFF);
-            uslope = sm->tslope[n];
-            uicpt = sm->ticpt[n];
+          const long long n = a.hoff[i] + j;
+          int code = CODE_INACTIVE, rank = 0;
+          float dneg = 0.f, lneg = 0.f, bj = 0.f;
+          if (jin) {
+            bj = sm->sbias[n];
+            if (fast) {
+              const uint32_t t = sm->tcode[n];
+              code = (int)(t >> 16);
+              rank = (int)(t & 0xFFFF);
+              dneg = code == CODE_ACTIVE ? 1.f : (code == CODE_UNSTABLE ? sm->tslope[n] : 0.f);
+              lneg = code == CODE_UNSTABLE ? sm->ticpt[n] : 0.f;
+            }
           }
-          const float bj = jin ? bias[j] : 0.f;
-          const int wd = a.woff[i] + (j >> 5);
-          const uint32_t bit = 1u << (j & 31);
-          // per-row inputs of 8 rows: A^(i)_j (stash), alpha, Adam moments
-          auto load8 = [&](int h, float (&av)[8], float (&th)[8]) {
+          const bool unst = code == CODE_UNSTABLE;
+          const float apos = code == CODE_ACTIVE ? 1.f : 0.f;
+          const int kb = (mc * MCH + 32 * q) / KBLK;
+          const bool writer = kb < nkb_next;
+          const uint32_t as = aseq + kb;
+          const int slot = as % NSLOT;
+          const int wd = a.woff[i] + ((mc * MCH + 32 * q) >> 5);
+          const uint32_t bit = 1u << lane;
+          const uint32_t rbits = mc * MCH + 32 * q < N ? (uint32_t)(sm->wrows[wd] >> r0) & 0xFFFFu : 0u;
+          // A^(i) of the 16 rows (two 16-byte loads) and alpha, issued before the accumulator wait
+          const __nv_bfloat16* sp = a.stash + ((size_t)tile * a.H + n) * TR + r0;
+          const uint4 s0 = ldg_v4(sp, jin), s1 = ldg_v4(sp + 8, jin);
+          float al[16];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-              const int row = 16 * cg + 8 * h + c;
-              av[c] = th[c] = 0.f;
-              if (jin && sm->valid[row]) {
-                if (i == a.L - 1) av[c] = ldg_f32(a.Wbar + (size_t)sm->spec[row] * N + j, true);
-                else av[c] = ldg_bf16(a.stash + (size_t)(tile * TR + row) * a.H + a.hoff[i] + j, true);
-                int code = ucode, rank = urank;
-                if (pu < 0) {
-                  const size_t n = (size_t)sm->prop[row] * a.H + a.hoff[i] + j;
-                  code = a.tb.code[n];
-                  rank = a.tb.rank[n];
-                }
-                const long long x = sm->abase[row] + rank;
-                th[c] = ldg_f32(a.alpha + x, code == CODE_UNSTABLE && x >= 0 && x < a.n_alpha);
+          for (int c = 0; c < 16; ++c) {
+            const int row = r0 + c;
+            if (fast) {
+              al[c] = ldg_f32(a.alpha + sm->abase[row] + rank, unst && c < nvt);
+            } else {
+              al[c] = 0.f;
+              if (jin && row < nvalid && sm->valid[row]) {
+                const size_t g = (size_t)sm->prop[row] * a.H + n;
+                if (a.tb.code[g] == CODE_UNSTABLE) al[c] = ldg_f32(a.alpha + sm->abase[row] + a.tb.rank[g], true);
               }
             }
-          };
-          float avA[8], thA[8];
-          load8(0, avA, thA);   // issued before waiting for the accumulator
+          }
           if (!mbar_wait_warp(&sm->acc_full[buf], (accseq / NACC) & 1, sm, a.status)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * TR + 16 * cg);
-          float v0[8];
-          tmem_ld8(tbase, v0);
-          float avB[8], thB[8];
-          load8(1, avB, thB);
-          const int kb = (mc * MCH + 32 * q) / KBLK;
-          const bool writer = produce && kb < nkb_next;
-          const uint32_t as = aseq + kb;
-          const int slot = as % NSLOT;
           if (writer && !mbar_wait_warp(&sm->act_empty[slot], ((as / NSLOT) & 1) ^ 1, sm, a.status)) {
             ok = false;
             break;
           }
-          auto compute8 = [&](int h, const float (&vz)[8], const float (&av)[8], const float (&th)[8]) {
+          const int kk = j & (KBLK - 1);
+          uint8_t* aslot = sm->act[slot] + r0 * 128 + ((kk & 7) << 1);
+          const uint32_t kx = (uint32_t)(kk >> 3) << 4;
+          const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * TR + r0);
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-              const int row = 16 * cg + 8 * h + c;
-              float hv = 0.f;
-              if (jin && sm->valid[row]) {
-                const float z = vz[c] + bj;
-                int code = ucode, rank = urank;
-                float slope = uslope, icpt = uicpt;
-                if (pu < 0) {
-                  const size_t n = (size_t)sm->prop[row] * a.H + a.hoff[i] + j;
-                  code = a.tb.code[n];
-                  rank = a.tb.rank[n];
-                  slope = a.tb.slope[n];
-                  icpt = a.tb.icpt[n];
-                }
-                const bool split = sm->smask[wd][row] & bit;
-                const int sg = split ? ((sm->sneg[wd][row] & bit) ? 1 : -1) : 0;
-                float D, lm = 0.f;
-                if (sg == -1) D = 1.f;
-                else if (sg == 1) D = 0.f;
-                else if (code == CODE_ACTIVE) D = 1.f;
-                else if (code == CODE_INACTIVE) D = 0.f;
-                else if (av[c] >= 0.f) D = fminf(fmaxf(th[c], 0.f), 1.f);
-                else {
-                  D = slope;
-                  lm = icpt;
-                }
-                if (code == CODE_UNSTABLE) {
-                  const long long ai = sm->abase[row] + rank;
-                  if (ai >= 0 && ai < a.n_alpha) {
-                    const float g = (sg == 0 && av[c] >= 0.f) ? av[c] * z : 0.f;
-                    if (a.mode == 1) {
-                      a.dalpha[ai] = g;
-                    } else {
-                      if (sm->improved[row]) a.a_best[ai] = th[c];
-                      const float m = a.beta1 * a.ma[ai] + (1.f - a.beta1) * g;
-                      const float vv = a.beta2 * a.va[ai] + (1.f - a.beta2) * g * g;
-                      a.ma[ai] = m;
-                      a.va[ai] = vv;
-                      a.a_cur[ai] = fminf(fmaxf(th[c] + a.lr_a * (m / a.bc1) / (sqrtf(vv / a.bc2) + a.eps), 0.f), 1.f);
-                    }
-                  }
-                }
-                if (sg != 0) {
-                  long long bi = sm->bbase[row] + sm->sorig[row][split_slot(sm, row, wd, j & 31)];
-                  if (bi >= a.n_beta) bi = -1;
-                  if (bi >= 0) {
-                    const float g = (float)sg * z;
-                    if (a.mode == 1) {
-                      a.dbeta[bi] = g;
-                    } else {
-                      const float tb0 = a.b_cur[bi];
-                      if (sm->improved[row]) a.b_best[bi] = tb0;
-                      const float m = a.beta1 * a.mb[bi] + (1.f - a.beta1) * g;
-                      const float vv = a.beta2 * a.vb[bi] + (1.f - a.beta2) * g * g;
-                      a.mb[bi] = m;
-                      a.vb[bi] = vv;
-                      a.b_cur[bi] = fmaxf(tb0 + a.lr_b * (m / a.bc1) / (sqrtf(vv / a.bc2) + a.eps), 0.f);
-                    }
-                  }
-                }
-                hv = fmaf(D, z, lm);
-              }
-              if (writer)
-                *reinterpret_cast<__nv_bfloat16*>(sm->act[slot] + act_off(row, j & (KBLK - 1))) = __float2bfloat16_rn(hv);
+          for (int h = 0; h < 2; ++h) {
+            float vz[8];
+            tmem_ld8(tbase + 8 * h, vz);
+            if (h == 1) {
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive(&sm->acc_empty[buf]);
+              ++accseq;
             }
-          };
-          compute8(0, v0, avA, thA);
-          float v1[8];
-          tmem_ld8(tbase + 8, v1);
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&sm->acc_empty[buf]);
-          ++accseq;
-          compute8(1, v1, avB, thB);
+            const uint4 sw = h == 0 ? s0 : s1;
+            const uint32_t swv[4] = {sw.x, sw.y, sw.z, sw.w};
+#pragma unroll
+            for (int c8 = 0; c8 < 8; ++c8) {
+              const int c = 8 * h + c8;
+              const int row = r0 + c;
+              const float A = __uint_as_float((c8 & 1) ? (swv[c8 >> 1] & 0xFFFF0000u) : (swv[c8 >> 1] << 16));
+              const float z = vz[c8] + bj;
+              const bool pos = A >= 0.f;
+              bool un = unst, rin = c < nvt;
+              float D, lm;
+              if (fast) {
+                D = pos ? __saturatef(al[c] + apos) : dneg;
+                lm = pos ? 0.f : lneg;
+              } else {
+                D = 0.f;
+                lm = 0.f;
+                un = false;
+                rin = jin && row < nvalid && sm->valid[row];
+                if (rin) {
+                  const size_t g = (size_t)sm->prop[row] * a.H + n;
+                  const int cd = a.tb.code[g];
+                  un = cd == CODE_UNSTABLE;
+                  if (cd == CODE_ACTIVE) D = 1.f;
+                  else if (un) {
+                    if (pos) D = __saturatef(al[c]);
+                    else {
+                      D = a.tb.slope[g];
+                      lm = a.tb.icpt[g];
+                    }
+                  }
+                }
+              }
+              float g = pos ? A * z : 0.f;
+              if ((rbits >> c) & 1u) {
+                if (sm->smask[wd][row] & bit) {
+                  const int sg = (sm->sneg[wd][row] & bit) ? 1 : -1;
+                  D = sg == -1 ? 1.f : 0.f;
+                  lm = 0.f;
+                  g = 0.f;
+                  const long long bi = sm->bbase[row] + sm->sorig[row][split_slot(sm, row, wd, lane)];
+                  if (bi < a.n_beta) a.dbeta[bi] = (float)sg * z;
+                }
+              }
+              if (un && rin) {
+                const int rk = fast ? rank : a.tb.rank[(size_t)sm->prop[row] * a.H + n];
+                a.dalpha[sm->abase[row] + rk] = g;
+              }
+              const float hv = rin ? fmaf(D, z, lm) : 0.f;
+              if (writer)
+                *reinterpret_cast<__nv_bfloat16*>(aslot + (8 * h + c8) * 128 + (kx ^ (uint32_t)(c8 << 4))) =
+                    __float2bfloat16_rn(hv);
+            }
+          }
           if (writer) {
             fence_proxy_async();
             __syncwarp();
             if (lane == 0) mbar_arrive(&sm->act_full[slot]);
           }
         }
-        if (produce) {
-          if (ok) {
-            for (int kk = 0; kk < nkb_next; ++kk) {
-              if ((kk & 1) != (q >> 1)) {
-                const uint32_t as = aseq + kk;
-                if (!mbar_wait_warp(&sm->act_empty[as % NSLOT], ((as / NSLOT) & 1) ^ 1, sm, a.status)) {
-                  ok = false;
-                  break;
-                }
-                if (lane == 0) mbar_arrive(&sm->act_full[as % NSLOT]);
-              }
-            }
-          }
-          aseq += nkb_next;
-        }
+        aseq += nkb_next;
       }
       if (ok && !epi_sync(sm, eseq, a.status)) ok = false;
     }
@@ -1360,27 +1335,29 @@ static int tc_prepare(bcrown_net* net, TcNet* t) {
   for (int i = 1; i < net->L; ++i) {
     const LayerDev& l = net->ly[i - 1];
     // backward: rows = d_{i-1} output neurons, K = d_i
-    __nv_bfloat16* wt = nullptr;
-    int kp = 0;
-    BC_CHECK(padded_bf16(l.Wt, l.d_in, l.d_out, &wt, &kp));
-    t->bufs.push_back(wt);
-    t->box_bwd[i] = std::min(MCH, (l.d_in + 15) / 16 * 16);
-    t->box_bwd[i] = MCH;
-    BC_CHECK(encode_map(&t->maps.bwd[i], wt, l.d_in, kp, t->box_bwd[i]));
-    // forward: rows = d_i output neurons, K = d_{i-1}
-    __nv_bfloat16* wf = nullptr;
-    BC_CHECK(padded_bf16(l.W, l.d_out, l.d_in, &wf, &kp));
-    t->bufs.push_back(wf);
-    t->box_fwd[i] = MCH;
-    BC_CHECK(encode_map(&t->maps.fwd[i], wf, l.d_out, kp, t->box_fwd[i]));
+    for (int rep = 0; rep < NREP; ++rep) {
+      __nv_bfloat16* wt = nullptr;
+      int kp = 0;
+      BC_CHECK(padded_bf16(l.Wt, l.d_in, l.d_out, &wt, &kp));
+      t->bufs.push_back(wt);
+      t->box_bwd[i] = MCH;
+      BC_CHECK(encode_map(&t->maps.bwd[rep][i], wt, l.d_in, kp, t->box_bwd[i]));
+      // forward: rows = d_i output neurons, K = d_{i-1}
+      __nv_bfloat16* wf = nullptr;
+      BC_CHECK(padded_bf16(l.W, l.d_out, l.d_in, &wf, &kp));
+      t->bufs.push_back(wf);
+      t->box_fwd[i] = MCH;
+      BC_CHECK(encode_map(&t->maps.fwd[rep][i], wf, l.d_out, kp, t->box_fwd[i]));
+    }
   }
-  BC_CUDA(cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem) + 1024));
+  BC_CUDA(cudaFuncSetAttribute(k_fused<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem) + 1024));
+  BC_CUDA(cudaFuncSetAttribute(k_fused<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem) + 1024));
   t->ready = true;
   return BCROWN_OK;
 }
 
 static int tc_launch(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* bt, const Tables& tb, Args& A,
-                     cudaStream_t s) {
+                     bool grad, cudaStream_t s) {
   TcNet* t = tc_of(net);
   BC_CHECK(tc_prepare(net, t));
   const int R = bt->B * net->K;
@@ -1416,7 +1393,10 @@ static int tc_launch(bcrown_net* net, const bcrown_domain* dom, const bcrown_bat
   int grid = std::min(A.n_tiles, sms);
   {
     ProfScope ps(net, BCROWN_PROF_FUSED, s);
-    k_fused<<<grid, NTHREADS, sizeof(Smem) + 1024, s>>>(t->maps, A);
+    if (grad)
+      k_fused<1><<<grid, NTHREADS, sizeof(Smem) + 1024, s>>>(t->maps, A);
+    else
+      k_fused<0><<<grid, NTHREADS, sizeof(Smem) + 1024, s>>>(t->maps, A);
     ++g_launches;
   }
   BC_CUDA(cudaGetLastError());
@@ -1428,7 +1408,6 @@ int tc_bound(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* bt, 
              float* dbeta, cudaStream_t s) {
   Args A;
   memset(&A, 0, sizeof(A));
-  A.mode = grad ? 1 : 0;
   A.alpha = alpha;
   A.beta = beta;
   A.lb = lb;
@@ -1437,38 +1416,7 @@ int tc_bound(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* bt, 
   A.stash = grad ? reinterpret_cast<__nv_bfloat16*>(ws) : nullptr;
   if (grad && ws_bytes < tc_workspace_bytes(net, bt->B * net->K, true))
     return fail(BCROWN_ERR_OOM, "tensor-core stash workspace too small");
-  return tc_launch(net, dom, bt, tb, A, s);
-}
-
-int tc_adam_step(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* bt, const Tables& tb, char* ws,
-                 size_t ws_bytes, float* a_cur, float* a_best, float* ma, float* va, float* b_cur, float* b_best,
-                 float* mb, float* vb, float* best_lb, float lr_a, float lr_b, float beta1, float beta2, float eps,
-                 float bc1, float bc2, cudaStream_t s) {
-  Args A;
-  memset(&A, 0, sizeof(A));
-  A.mode = 2;
-  A.alpha = a_cur;
-  A.beta = b_cur;
-  A.stash = reinterpret_cast<__nv_bfloat16*>(ws);
-  if (ws_bytes < tc_workspace_bytes(net, bt->B * net->K, true))
-    return fail(BCROWN_ERR_OOM, "tensor-core stash workspace too small");
-  A.a_cur = a_cur;
-  A.a_best = a_best;
-  A.ma = ma;
-  A.va = va;
-  A.b_cur = b_cur;
-  A.b_best = b_best;
-  A.mb = mb;
-  A.vb = vb;
-  A.best_lb = best_lb;
-  A.lr_a = lr_a;
-  A.lr_b = lr_b;
-  A.beta1 = beta1;
-  A.beta2 = beta2;
-  A.eps = eps;
-  A.bc1 = bc1;
-  A.bc2 = bc2;
-  return tc_launch(net, dom, bt, tb, A, s);
+  return tc_launch(net, dom, bt, tb, A, grad, s);
 }
 
 void tc_release(const bcrown_net* net) {

@@ -12,10 +12,6 @@ int tc_bound(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* bt, 
              size_t ws_bytes, bool grad, const float* alpha, const float* beta, float* lb, float* dalpha,
              float* dbeta, cudaStream_t s);
 
-int tc_adam_step(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* bt, const Tables& tb, char* ws,
-                 size_t ws_bytes, float* a_cur, float* a_best, float* ma, float* va, float* b_cur, float* b_best,
-                 float* mb, float* vb, float* best_lb, float lr_a, float lr_b, float beta1, float beta2, float eps,
-                 float bc1, float bc2, cudaStream_t s);
 void tc_release(const bcrown_net* net);
 
 }  // namespace bcrown

@@ -67,15 +67,32 @@ def test_bf16_ragged_rows_and_multi_property():
     assert (np.abs(lb - ref) / _scale(ref)).max() <= BF16_TOL
 
 
-def test_bf16_gradient_close_to_oracle():
-    pb = wl.problem_mlp_784()
-    onet, props, unst = oracle_setup(pb)
-    batch = wl.tree_batch(pb, unst, [64], 12, 9)
+@pytest.mark.parametrize("which", ["small", "784", "mixed"])
+def test_bf16_gradient_close_to_oracle(which):
+    """Adjoint pass of the fused kernel: layers narrower than an M chunk (small), full chunks
+    (784), and tiles whose rows come from several properties with a ragged last tile (mixed)."""
+    if which == "small":
+        pb = wl.problem_mlp_small()
+        onet, props, unst = oracle_setup(pb)
+        batch = wl.random_batch(pb, unst, 64, 0, 4, 1)
+    elif which == "784":
+        pb = wl.problem_mlp_784()
+        onet, props, unst = oracle_setup(pb)
+        batch = wl.tree_batch(pb, unst, [64], 12, 9)
+    else:
+        pb = wl.problem_mlp_784(n_props=3)
+        onet = O.OracleNet(pb.layers, pb.C)
+        l, u = O.root_bounds(onet, pb.x_lo, pb.x_hi)
+        l, u = l.astype(np.float32), u.astype(np.float32)
+        unst = [np.nonzero(O.unstable_mask(l[p], u[p]))[0] for p in range(pb.P)]
+        props = dict(x_lo=pb.x_lo, x_hi=pb.x_hi, l=l, u=u)
+        batch = wl.random_batch(pb, unst, 37, 0, 6, 8, props=np.arange(37) % 3)
     a, b = wl.random_alpha_beta(batch, 2, 1.0)
     net, dom, db = _gpu(pb, props, batch)
     lb, da, dbeta = bc.bound_grad(net, dom, db, _t(a), _t(b), bc.BF16)
     assert bc.status(net) == 0
     ref, da_ref, db_ref = O.grad(onet, props, batch, a.astype(np.float64), b.astype(np.float64))
+    assert (np.abs(lb.cpu().numpy() - ref) / _scale(ref)).max() <= BF16_TOL
     for g, gr in ((da.cpu().numpy(), da_ref), (dbeta.cpu().numpy(), db_ref)):
         # relative error of the gradient vector (BF16 rounding of x*, h and the stash)
         rel = np.linalg.norm(g - gr) / max(np.linalg.norm(gr), 1e-12)
