@@ -81,6 +81,7 @@ struct Smem {
   float sxhi[MAX_D0];
   float sbias[MAX_H];                    // hidden-layer biases, by global hidden index
   int uniform_p;                         // property shared by every valid row of the tile, or -1
+  uint32_t badw[2];                      // rows below the tile's end that are not valid (bit mask)
   int fast;                              // uniform_p >= 0 and every row below the tile's end valid
   uint64_t act_full[NSLOT], act_empty[NSLOT];
   uint64_t w_full[NSTAGE], w_empty[NSTAGE];
@@ -577,7 +578,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
     const int prow = gt >> 2, pc16 = gt & 3;  // producer thread: tile row, 16 consecutive k
     uint32_t aseq = 0, accseq = 0, eseq = 0;
     bool ok = true;
-    const int dtop = a.d[a.L - 1];
 
     // hidden-layer biases, indexed by global hidden neuron, for the whole launch
     for (int i = 1; i < a.L; ++i)
@@ -621,6 +621,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
         sm->abase[row] = v ? ab : 0;
         sm->bbase[row] = v ? bb : 0;
         sm->part[0][row] = sm->part[1][row] = sm->part[2][row] = sm->part[3][row] = 0.f;
+        const unsigned bad = __ballot_sync(0xffffffffu, row < nvalid && !v);   // warps 0 and 1
+        if (lane == 0) sm->badw[warp] = bad;
       }
       for (int x = etid; x < a.mask_words * TR; x += NEPI * 32) {
         (&sm->smask[0][0])[x] = 0u;
@@ -676,24 +678,47 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
         }
         const int pu = sm->uniform_p;
         if (pu >= 0) {
-          for (int n = etid; n < a.H; n += NEPI * 32) {
-            const size_t g = (size_t)pu * a.H + n;
-            const int rk = a.tb.rank[g];
-            sm->tcode[n] = ((uint32_t)a.tb.code[g] << 16) | (uint32_t)(rk < 0 ? 0xFFFF : (rk & 0xFFFF));
-            sm->tslope[n] = a.tb.slope[g];
-            sm->ticpt[n] = a.tb.icpt[g];
+          // all loads first, then the stores (3 neurons and 2 inputs per thread at most)
+          constexpr int NT = (MAX_H + NEPI * 32 - 1) / (NEPI * 32), NX = (MAX_D0 + NEPI * 32 - 1) / (NEPI * 32);
+          int cd[NT], rk[NT];
+          float sl[NT], ic[NT], xl[NX], xh[NX];
+#pragma unroll
+          for (int u = 0; u < NT; ++u) {
+            const int nn = etid + u * NEPI * 32;
+            const size_t g = (size_t)pu * a.H + nn;
+            const bool in = nn < a.H;
+            cd[u] = in ? a.tb.code[g] : 0;
+            rk[u] = in ? a.tb.rank[g] : 0;
+            sl[u] = in ? a.tb.slope[g] : 0.f;
+            ic[u] = in ? a.tb.icpt[g] : 0.f;
           }
-          for (int m = etid; m < a.d[0]; m += NEPI * 32) {
-            sm->sxlo[m] = a.x_lo[(size_t)pu * a.d[0] + m];
-            sm->sxhi[m] = a.x_hi[(size_t)pu * a.d[0] + m];
+#pragma unroll
+          for (int u = 0; u < NX; ++u) {
+            const int m = etid + u * NEPI * 32;
+            const bool in = m < a.d[0];
+            xl[u] = in ? a.x_lo[(size_t)pu * a.d[0] + m] : 0.f;
+            xh[u] = in ? a.x_hi[(size_t)pu * a.d[0] + m] : 0.f;
+          }
+#pragma unroll
+          for (int u = 0; u < NT; ++u) {
+            const int nn = etid + u * NEPI * 32;
+            if (nn < a.H) {
+              sm->tcode[nn] = ((uint32_t)cd[u] << 16) | (uint32_t)(rk[u] < 0 ? 0xFFFF : (rk[u] & 0xFFFF));
+              sm->tslope[nn] = sl[u];
+              sm->ticpt[nn] = ic[u];
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < NX; ++u) {
+            const int m = etid + u * NEPI * 32;
+            if (m < a.d[0]) {
+              sm->sxlo[m] = xl[u];
+              sm->sxhi[m] = xh[u];
+            }
           }
         }
-        if (etid == 0) {
-          // fast path: one property and every row below nvalid valid
-          int f = pu >= 0;
-          for (int r = 0; r < nvalid; ++r) f &= sm->valid[r];
-          sm->fast = f;
-        }
+        // fast path: one property and every row below the tile's end valid
+        if (etid == 0) sm->fast = pu >= 0 && sm->badw[0] == 0u && sm->badw[1] == 0u;
       }
       if (!epi_sync(sm, eseq, a.status)) {
         ok = false;
@@ -703,15 +728,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
       if (etid < TR) {
         int run = 0;
         for (int w = 0; w < a.mask_words; ++w) {
+          const uint32_t m = sm->smask[w][etid];
           sm->wfirst[w][etid] = (uint8_t)run;
-          run += __popc(sm->smask[w][etid]);
+          run += __popc(m);
+          const unsigned rows = __ballot_sync(0xffffffffu, m != 0u);
+          if (lane == 0) reinterpret_cast<uint32_t*>(&sm->wrows[w])[warp] = rows;   // rows 32 warp ..
         }
-      } else if (etid < TR + a.mask_words) {
-        const int w = etid - TR;
-        unsigned long long m = 0ull;
-        for (int r = 0; r < TR; ++r)
-          if (sm->smask[w][r]) m |= 1ull << r;
-        sm->wrows[w] = m;
       }
       if (!epi_sync(sm, eseq, a.status)) {
         ok = false;
@@ -720,14 +742,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
       // ---------------- step 4: each split's slot in (word, bit) order, its list position and beta
       {
         const int row = etid >> 3, e0 = etid & 7;
+        float bv[BCROWN_MAX_SPLITS / 8];
+#pragma unroll
+        for (int m = 0; m < BCROWN_MAX_SPLITS / 8; ++m) {
+          const long long bi = sm->bbase[row] + e0 + 8 * m;
+          bv[m] = ldg_f32(a.beta + bi, ent[m] >= 0 && bi >= 0 && bi < a.n_beta);
+        }
 #pragma unroll
         for (int m = 0; m < BCROWN_MAX_SPLITS / 8; ++m) {
           if (ent[m] >= 0) {
-            const int e = e0 + 8 * m;
             const int ks = split_slot(sm, row, ent[m] >> 5, ent[m] & 31);
-            const long long bi = sm->bbase[row] + e;
-            sm->sorig[row][ks] = (uint8_t)e;
-            sm->sbeta[row][ks] = (bi >= 0 && bi < a.n_beta) ? fmaxf(ldg_f32(a.beta + bi, true), 0.f) : 0.f;
+            sm->sorig[row][ks] = (uint8_t)(e0 + 8 * m);
+            sm->sbeta[row][ks] = fmaxf(bv[m], 0.f);
           }
         }
       }
@@ -738,111 +764,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
       const bool fast = sm->fast != 0;
       const int nvt = nvalid - r0;   // rows of this thread below nvalid (may be <= 0 or > 16)
 
-      // ---------------- top operand: Lambda^(L-1) from Wbar (relaxation of layer L-1)
-      // K block kb is written by the 8 warps of producer group kb % 2: thread -> (row, 16 k)
-      {
-        const int i = a.L - 1;
-        const int nkb = nkb_of(dtop);
-        const bool rv = prow < nvalid && sm->valid[prow];
-        const int spec = sm->spec[prow];
-        const int pr = sm->prop[prow];
-        const long long abr = sm->abase[prow];
-        float csum = 0.f;
-        for (int kb = pg; kb < nkb && ok; kb += 2) {
-          const uint32_t as = aseq + kb;
-          const int slot = as % NSLOT;
-          const int j0 = kb * KBLK + pc16 * 16;
-          float av[16], al[16];
-#pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            const int j = j0 + e;
-            const bool in = rv && j < dtop;
-            av[e] = ldg_f32(a.Wbar + (size_t)spec * dtop + j, in);
-            int code = CODE_INACTIVE, rank = 0;
-            if (in) {
-              if (fast) {
-                const uint32_t t = sm->tcode[a.hoff[i] + j];
-                code = (int)(t >> 16);
-                rank = (int)(t & 0xFFFF);
-              } else {
-                const size_t g = (size_t)pr * a.H + a.hoff[i] + j;
-                code = a.tb.code[g];
-                rank = a.tb.rank[g];
-              }
-            }
-            al[e] = ldg_f32(a.alpha + abr + rank, in && code == CODE_UNSTABLE);
-          }
-          if (!mbar_wait_warp(&sm->act_empty[slot], ((as / NSLOT) & 1) ^ 1, sm, a.status)) {
-            ok = false;
-            break;
-          }
-          uint32_t pk[8];
-#pragma unroll
-          for (int e = 0; e < 16; e += 2) {
-            float lv[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const int ee = e + h;
-              const int j = j0 + ee;
-              float L = 0.f;
-              if (rv && j < dtop) {
-                const long long n = a.hoff[i] + j;
-                int code;
-                float slope, icpt;
-                if (fast) {
-                  code = (int)(sm->tcode[n] >> 16);
-                  slope = sm->tslope[n];
-                  icpt = sm->ticpt[n];
-                } else {
-                  const size_t g = (size_t)pr * a.H + n;
-                  code = a.tb.code[g];
-                  slope = a.tb.slope[g];
-                  icpt = a.tb.icpt[g];
-                }
-                const int wd = a.woff[i] + (j >> 5);
-                const uint32_t bit = 1u << (j & 31);
-                float D, lm = 0.f, bs = 0.f;
-                if (sm->smask[wd][prow] & bit) {
-                  // split neuron (Eq. 3): D = 1 for z >= 0, 0 for z < 0, plus beta S
-                  const int sg = (sm->sneg[wd][prow] & bit) ? 1 : -1;
-                  D = sg == -1 ? 1.f : 0.f;
-                  bs = sm->sbeta[prow][split_slot(sm, prow, wd, j & 31)] * (float)sg;
-                } else if (code == CODE_ACTIVE) D = 1.f;
-                else if (code == CODE_INACTIVE) D = 0.f;
-                else if (av[ee] >= 0.f) D = __saturatef(al[ee]);
-                else {
-                  D = slope;
-                  lm = icpt;
-                }
-                L = fmaf(av[ee], D, bs);
-                csum += fmaf(L, sm->sbias[n], av[ee] * lm);
-              }
-              if constexpr (MODE >= 1) {
-                // A^(L-1) = Wbar rows, for the adjoint pass (zero on rows that take no part)
-                if (j < dtop) a.stash[((size_t)tile * a.H + a.hoff[i] + j) * TR + prow] = __float2bfloat16_rn(av[ee]);
-              }
-              lv[h] = L;
-            }
-            __nv_bfloat162 v2 = __floats2bfloat162_rn(lv[0], lv[1]);
-            pk[e >> 1] = *reinterpret_cast<uint32_t*>(&v2);
-          }
-          *reinterpret_cast<uint4*>(sm->act[slot] + act_off(prow, pc16 * 16)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-          *reinterpret_cast<uint4*>(sm->act[slot] + act_off(prow, pc16 * 16 + 8)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-          fence_proxy_async();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&sm->act_full[slot]);
-        }
-        aseq += nkb;
-        if (rv) atomicAdd(&sm->part[0][prow], csum);
-      }
-
       // per-thread lb partial sums of its 16 rows over the lanes' neurons (whole backward pass)
       float racc[16];
 #pragma unroll
       for (int c = 0; c < 16; ++c) racc[c] = 0.f;
 
-      // ---------------- backward contractions: output A^(i-1) of layer i's transpose
-      for (int i = a.L - 1; i >= 1 && ok; --i) {
+      // ---------------- backward pass: A^(i-1) = Lambda^(i) W^(i) from the accumulator, relaxed
+      // into the next operand Lambda^(i-1).  i = L is the top: A^(L-1) = Wbar (no contraction).
+      for (int i = a.L; i >= 1 && ok; --i) {
+        const bool top = (i == a.L);
         const int N = a.d[i - 1];
         const int nmc = nmc_of(N);
         const bool concretise = (i == 1);
@@ -852,8 +782,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
           const int buf = accseq % NACC;
           const int j = mc * MCH + 32 * q + lane;   // output neuron of this lane
           const bool jin = j < N;
-          const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * TR + r0);
           if (concretise) {
+            const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * TR + r0);
             // ---- lb += sum_m min(A_m x_lo_m, A_m x_hi_m) (Eq. beta_crown_lp); sign bits of A^(0) for x*
             float uxl = 0.f, uxh = 0.f;
             if (fast && jin) {
@@ -940,29 +870,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
               }
             }
           }
-          if (!mbar_wait_warp(&sm->acc_full[buf], (accseq / NACC) & 1, sm, a.status)) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          if (writer && !mbar_wait_warp(&sm->act_empty[slot], ((as / NSLOT) & 1) ^ 1, sm, a.status)) {
-            ok = false;
-            break;
-          }
           // byte offset of (row r0 + 8h + c8, k = j % 64) in the slot: row & 7 == c8
           const int kk = j & (KBLK - 1);
           uint8_t* aslot = sm->act[slot] + r0 * 128 + ((kk & 7) << 1);
           const uint32_t kx = (uint32_t)(kk >> 3) << 4;
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            float v[8];
-            tmem_ld8(tbase + 8 * h, v);
-            if (h == 1) {
-              tc_fence_before();
-              __syncwarp();
-              if (lane == 0) mbar_arrive(&sm->acc_empty[buf]);
-              ++accseq;
-            }
+          // rows r0 + 8h .. r0 + 8h + 7 of A^(i-1)_j: relaxation, lb terms, operand and stash
+          auto relax8 = [&](const int h, const float (&v)[8]) {
 #pragma unroll
             for (int c8 = 0; c8 < 8; ++c8) {
               const int c = 8 * h + c8;
@@ -1015,6 +928,39 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
                 stg_v4(a.stash + ((size_t)tile * a.H + n) * TR + r0 + 8 * h, make_uint4(pk[0], pk[1], pk[2], pk[3]));
               }
             }
+          };
+          if (!top) {
+            if (!mbar_wait_warp(&sm->acc_full[buf], (accseq / NACC) & 1, sm, a.status)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+          }
+          if (writer && !mbar_wait_warp(&sm->act_empty[slot], ((as / NSLOT) & 1) ^ 1, sm, a.status)) {
+            ok = false;
+            break;
+          }
+          const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * TR + r0);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            float v[8];
+            if (top) {
+              // A^(L-1) = Wbar rows of the rows' specifications
+#pragma unroll
+              for (int c8 = 0; c8 < 8; ++c8) {
+                const int row = r0 + 8 * h + c8;
+                v[c8] = ldg_f32(a.Wbar + (size_t)sm->spec[row] * N + j, jin && row < nvalid && sm->valid[row]);
+              }
+            } else {
+              tmem_ld8(tbase + 8 * h, v);
+              if (h == 1) {
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sm->acc_empty[buf]);
+                ++accseq;
+              }
+            }
+            relax8(h, v);
           }
           // each K block is complete once its 8 writer warps arrived
           if (writer) {
