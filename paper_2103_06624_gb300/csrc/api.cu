@@ -47,7 +47,7 @@ struct Plan {
   float* slope;
   float* icpt;
   int32_t* U;
-  double* wm;
+  float* wm;
   Tables tb;
   // chunk buffers
   std::vector<float*> Abuf;  // [L] : Abuf[i] for hidden i (1..L-1), Abuf[0] = A^(0)
@@ -81,7 +81,7 @@ static int make_plan(bcrown_net* net, int P, int R, bool cert, bool opt, int64_t
   size_t PH = (size_t)P * std::max(net->H, 1);
   size_t bytes = 0;
   bytes += align_up(PH) + align_up(PH * 4) * 3 + align_up((size_t)P * 4);
-  if (cert) bytes += align_up(PH * 8);
+  if (cert) bytes += align_up(PH * 4);
   bytes += (size_t)pl.Rc * rb + 16 * 256;
   if (opt) bytes += align_up((size_t)n_alpha * 4) * 4 + align_up((size_t)n_beta * 4) * 4 + align_up((size_t)R * 4) * 2;
   bytes += align_up(tc_bytes);
@@ -94,7 +94,7 @@ static int make_plan(bcrown_net* net, int P, int R, bool cert, bool opt, int64_t
   pl.slope = ar.take<float>(PH);
   pl.icpt = ar.take<float>(PH);
   pl.U = ar.take<int32_t>(P);
-  pl.wm = cert ? ar.take<double>(PH) : nullptr;
+  pl.wm = cert ? ar.take<float>(PH) : nullptr;
   pl.Abuf.assign(net->L, nullptr);
   for (int i = 0; i < net->L; ++i) pl.Abuf[i] = ar.take<float>((size_t)pl.Rc * net->d[i]);
   pl.Lam = ar.take<float>((size_t)pl.Rc * net->max_hidden);

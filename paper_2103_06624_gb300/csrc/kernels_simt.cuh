@@ -99,6 +99,30 @@ __device__ __forceinline__ double warp_dsum(double v) {
   return v;
 }
 
+// FP32 sums with a rounding direction: MODE 0 nearest, 1 down (toward -inf), 2 up.  Directed
+// rounding at every step makes the result a lower (1) or upper (2) bound of the exact sum.
+template <int MODE>
+__device__ __forceinline__ float fadd(float a, float b) {
+  if (MODE == 1) return __fadd_rd(a, b);
+  if (MODE == 2) return __fadd_ru(a, b);
+  return a + b;
+}
+template <int MODE>
+__device__ __forceinline__ float block_fsum(float v, float* sh) {
+  for (int o = 16; o > 0; o >>= 1) v = fadd<MODE>(v, __shfl_xor_sync(0xffffffffu, v, o));
+  int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
+  __syncthreads();
+  if (ln == 0) sh[w] = v;
+  __syncthreads();
+  int nw = (blockDim.x + 31) >> 5;
+  float s = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.f;
+  if (w == 0)
+    for (int o = 16; o > 0; o >>= 1) s = fadd<MODE>(s, __shfl_xor_sync(0xffffffffu, s, o));
+  if (threadIdx.x == 0) sh[0] = s;
+  __syncthreads();
+  return sh[0];
+}
+
 // Sum over the block (result valid in every thread).  `sh` needs 32 entries.
 __device__ __forceinline__ float block_sum(float v, float* sh) {
   v = warp_sum(v);

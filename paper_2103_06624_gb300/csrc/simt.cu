@@ -51,8 +51,10 @@ __global__ void __launch_bounds__(1024) k_tables(int H, const float* __restrict_
       rank[g] = un ? running + woff + pre : -1;
       float sl = 0.f, ic = 0.f;
       if (un) {
-        sl = uv / (uv - lv);
-        ic = -sl * lv;
+        // upper chord u (z - l) / (u - l) with its slope and intercept rounded up: still an
+        // upper bound of ReLU on [l, u] (z - l >= 0 there), so every precision may use it
+        sl = __fdiv_ru(uv, __fsub_rd(uv, lv));
+        ic = __fmul_ru(sl, -lv);
       }
       slope[g] = sl;
       icpt[g] = ic;
@@ -67,43 +69,40 @@ __global__ void __launch_bounds__(1024) k_tables(int H, const float* __restrict_
 // M^(i)_m: bound on |h^(i)_m| (max(u,0) for hidden layers, max(|x_lo|,|x_hi|) at the input)
 __device__ __forceinline__ float hmax_hidden(float uv) { return fmaxf(uv, 0.f); }
 
-// wm[p][hoff_i + j] = sum_m |W^(i)_jm| M^(i-1)_m, rounded up (FP64), for the a priori
-// contraction error of layer i.  fc: direct dot product; conv: direct loops.
-__global__ void k_absw_m(LayerGeom g, const float* __restrict__ W, int P, int H, long long hoff_i,
-                         long long hoff_prev, const float* __restrict__ u, const float* __restrict__ x_lo,
-                         const float* __restrict__ x_hi, int d0, double* __restrict__ wm) {
-  long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  long long total = (long long)P * g.d_out;
+// wm[p][hoff_i + j] = sum_m |W^(i)_jm| M^(i-1)_m, every product and sum rounded up (FP32),
+// for the a priori contraction error of layer i.  One warp per output neuron.
+__global__ void __launch_bounds__(256) k_absw_m(LayerGeom g, const float* __restrict__ W, int P, int H,
+                                                long long hoff_i, long long hoff_prev, const float* __restrict__ u,
+                                                const float* __restrict__ x_lo, const float* __restrict__ x_hi,
+                                                int d0, float* __restrict__ wm) {
+  const long long id = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const long long total = (long long)P * g.d_out;
   if (id >= total) return;
-  int p = (int)(id / g.d_out);
-  int j = (int)(id - (long long)p * g.d_out);
-  auto M = [&](int m) -> double {
-    if (hoff_prev < 0) {
-      float a = fabsf(x_lo[(size_t)p * d0 + m]), b = fabsf(x_hi[(size_t)p * d0 + m]);
-      return (double)fmaxf(a, b);
-    }
-    return (double)hmax_hidden(u[(size_t)p * H + hoff_prev + m]);
+  const int p = (int)(id / g.d_out);
+  const int j = (int)(id - (long long)p * g.d_out);
+  auto M = [&](int m) -> float {
+    if (hoff_prev < 0) return fmaxf(fabsf(x_lo[(size_t)p * d0 + m]), fabsf(x_hi[(size_t)p * d0 + m]));
+    return hmax_hidden(u[(size_t)p * H + hoff_prev + m]);
   };
-  double s = 0.0;
+  float s = 0.f;
   if (g.kind == BCROWN_LAYER_FC) {
     const float* w = W + (size_t)j * g.d_in;
-    for (int m = 0; m < g.d_in; ++m) s = __dadd_ru(s, __dmul_ru(fabs((double)w[m]), M(m)));
+    for (int m = lane; m < g.d_in; m += 32) s = __fadd_ru(s, __fmul_ru(fabsf(w[m]), M(m)));
   } else {
-    int hw = g.out_h * g.out_w;
-    int co = j / hw, rem = j - co * hw, oy = rem / g.out_w, ox = rem - oy * g.out_w;
-    for (int ci = 0; ci < g.in_c; ++ci)
-      for (int ky = 0; ky < g.k; ++ky) {
-        int iy = oy * g.stride - g.pad + ky;
-        if (iy < 0 || iy >= g.in_h) continue;
-        for (int kx = 0; kx < g.k; ++kx) {
-          int ix = ox * g.stride - g.pad + kx;
-          if (ix < 0 || ix >= g.in_w) continue;
-          double w = fabs((double)W[(((size_t)co * g.in_c + ci) * g.k + ky) * g.k + kx]);
-          s = __dadd_ru(s, __dmul_ru(w, M((ci * g.in_h + iy) * g.in_w + ix)));
-        }
-      }
+    const int hw = g.out_h * g.out_w;
+    const int co = j / hw, rem = j - co * hw, oy = rem / g.out_w, ox = rem - oy * g.out_w;
+    const int kk = g.k * g.k;
+    for (int t = lane; t < g.in_c * kk; t += 32) {
+      const int ci = t / kk, r = t - ci * kk, ky = r / g.k, kx = r - ky * g.k;
+      const int iy = oy * g.stride - g.pad + ky, ix = ox * g.stride - g.pad + kx;
+      if (iy < 0 || iy >= g.in_h || ix < 0 || ix >= g.in_w) continue;
+      const float w = fabsf(W[(((size_t)co * g.in_c + ci) * g.k + ky) * g.k + kx]);
+      s = __fadd_ru(s, __fmul_ru(w, M((ci * g.in_h + iy) * g.in_w + ix)));
+    }
   }
-  wm[(size_t)p * H + hoff_i + j] = s;
+  for (int o = 16; o > 0; o >>= 1) s = __fadd_ru(s, __shfl_xor_sync(0xffffffffu, s, o));
+  if (lane == 0) wm[(size_t)p * H + hoff_i + j] = s;
 }
 
 // ----------------------------------------------------------------------------------------
@@ -115,7 +114,7 @@ __global__ void __launch_bounds__(256) k_init_top(RowsCtx c, int dtop, const flo
                                                   const float* __restrict__ Wbar_err, long long hoff_top,
                                                   float* __restrict__ A, float* __restrict__ cf,
                                                   double* __restrict__ cd, double* __restrict__ E) {
-  __shared__ double shd[32];
+  __shared__ float shf[32];
   int rl = blockIdx.x;
   int b, k, p;
   bool ok = row_prop(c, rl, &b, &k, &p);
@@ -124,17 +123,17 @@ __global__ void __launch_bounds__(256) k_init_top(RowsCtx c, int dtop, const flo
     p = 0;
   }
   const float* w = Wbar + (size_t)k * dtop;
-  double e = 0.0;
+  float e = 0.f;
   for (int j = threadIdx.x; j < dtop; j += blockDim.x) {
     A[(size_t)rl * dtop + j] = w[j];
     if (CERT) {
       float M = hoff_top >= 0 ? hmax_hidden(c.u[(size_t)p * c.tb.H + hoff_top + j])
                               : fmaxf(fabsf(c.x_lo[(size_t)p * dtop + j]), fabsf(c.x_hi[(size_t)p * dtop + j]));
-      e = __dadd_ru(e, __dmul_ru((double)Wbar_err[(size_t)k * dtop + j], (double)M));
+      e = __fadd_ru(e, __fmul_ru(Wbar_err[(size_t)k * dtop + j], M));
     }
   }
   if (CERT) {
-    e = block_dsum<2>(e, shd);
+    e = block_fsum<2>(e, shf);
     if (threadIdx.x == 0) {
       cd[rl] = ok ? bbar_rd[k] : -INFINITY;
       E[rl] = e;
@@ -155,12 +154,11 @@ __global__ void __launch_bounds__(256) k_relax(RowsCtx c, int layer, int d, long
                                                const float* __restrict__ bias, const float* __restrict__ alpha,
                                                int64_t n_alpha, const float* __restrict__ beta, int64_t n_beta,
                                                float* __restrict__ cf, double* __restrict__ cd,
-                                               double* __restrict__ E, const double* __restrict__ wm,
+                                               double* __restrict__ E, const float* __restrict__ wm,
                                                double gamma) {
   __shared__ SplitSlot slots[BCROWN_MAX_SPLITS];
   __shared__ int n_slots;
   __shared__ float shf[32];
-  __shared__ double shd[32];
   int rl = blockIdx.x;
   int b, k, p;
   bool ok = row_prop(c, rl, &b, &k, &p);
@@ -172,8 +170,9 @@ __global__ void __launch_bounds__(256) k_relax(RowsCtx c, int layer, int d, long
   long long bbase = (long long)c.bt.split_off[b] * c.K + (long long)k * cnt;
   const float* a_row = Ain + (size_t)rl * d;
   float* lam_row = Lam + (size_t)rl * d;
-  float acc = 0.f;
-  double accd = 0.0, e1 = 0.0, e2 = 0.0;
+  // CERT: acc is a lower bound of sum_j Lambda_j b_j + A_j lambda_j (every operation rounded
+  // down); e1, e2 are upper bounds (rounded up) of the error terms below.
+  float acc = 0.f, e1 = 0.f, e2 = 0.f;
   for (int j = threadIdx.x; j < d; j += blockDim.x) {
     float a = a_row[j];
     size_t n = (size_t)p * c.tb.H + hoff + j;
@@ -201,38 +200,35 @@ __global__ void __launch_bounds__(256) k_relax(RowsCtx c, int layer, int d, long
         D = fminf(fmaxf(alpha[ai], 0.f), 1.f);
       }
     } else {
-      if (CERT) {
-        float lv = c.l[n], uv = c.u[n];
-        D = __fdiv_ru(uv, __fsub_rd(uv, lv));
-        lm = __fmul_ru(D, -lv);
-      } else {
-        D = c.tb.slope[n];
-        lm = c.tb.icpt[n];
-      }
+      // upper chord, slope and intercept rounded up (outward) in the tables
+      D = c.tb.slope[n];
+      lm = c.tb.icpt[n];
     }
     float L = fmaf(a, D, bet * (float)s);
     lam_row[j] = L;
     float bj = bias[j];
     if (CERT) {
-      accd = __dadd_rd(accd, __dadd_rd((double)L * (double)bj, (double)a * (double)lm));
+      acc = __fadd_rd(acc, __fadd_rd(__fmul_rd(L, bj), __fmul_rd(a, lm)));
       bool exact = (s == 0) && (D == 0.f || D == 1.f);
       if (!exact) {
+        // Lambda_j was rounded once: |error| <= 2^-23 |Lambda_j| (+ an underflow margin),
+        // acting on |z_j| <= max(|l_j|, |u_j|)
         float zmax = fmaxf(fabsf(c.l[n]), fabsf(c.u[n]));
-        double er = __dadd_ru(__dmul_ru(fabs((double)L), 0x1p-23), 0x1p-140);
-        e1 = __dadd_ru(e1, __dmul_ru(er, (double)zmax));
+        float er = __fmaf_ru(fabsf(L), 0x1p-23f, 0x1p-140f);
+        e1 = __fadd_ru(e1, __fmul_ru(er, zmax));
       }
-      e2 = __dadd_ru(e2, __dmul_ru(fabs((double)L), wm[n]));
+      e2 = __fadd_ru(e2, __fmul_ru(fabsf(L), wm[n]));
     } else {
       acc = fmaf(L, bj, fmaf(a, lm, acc));
     }
   }
   if (CERT) {
-    accd = block_dsum<1>(accd, shd);
-    e1 = block_dsum<2>(e1, shd);
-    e2 = block_dsum<2>(e2, shd);
+    acc = block_fsum<1>(acc, shf);
+    e1 = block_fsum<2>(e1, shf);
+    e2 = block_fsum<2>(e2, shf);
     if (threadIdx.x == 0) {
-      cd[rl] = __dadd_rd(cd[rl], accd);
-      E[rl] = __dadd_ru(E[rl], __dadd_ru(e1, __dmul_ru(gamma, e2)));
+      cd[rl] = __dadd_rd(cd[rl], (double)acc);
+      E[rl] = __dadd_ru(E[rl], __dadd_ru((double)e1, __dmul_ru(gamma, (double)e2)));
     }
   } else {
     acc = block_sum(acc, shf);
@@ -381,7 +377,6 @@ __global__ void __launch_bounds__(256) k_concretize(RowsCtx c, int d0, const flo
                                                     const float* __restrict__ cf, const double* __restrict__ cd,
                                                     const double* __restrict__ E, float* __restrict__ lb) {
   __shared__ float shf[32];
-  __shared__ double shd[32];
   int rl = blockIdx.x;
   int b, k, p;
   if (!row_prop(c, rl, &b, &k, &p)) p = 0;
@@ -389,20 +384,19 @@ __global__ void __launch_bounds__(256) k_concretize(RowsCtx c, int d0, const flo
   const float* xl = c.x_lo + (size_t)p * d0;
   const float* xh = c.x_hi + (size_t)p * d0;
   float s = 0.f;
-  double sd = 0.0;
   for (int m = threadIdx.x; m < d0; m += blockDim.x) {
     float am = a[m];
     if (CERT) {
-      double v = fmin((double)am * (double)xl[m], (double)am * (double)xh[m]);
-      sd = __dadd_rd(sd, v);
+      // products rounded down, then summed rounded down: a lower bound of sum_m min(...)
+      s = __fadd_rd(s, fminf(__fmul_rd(am, xl[m]), __fmul_rd(am, xh[m])));
     } else {
       s += fminf(am * xl[m], am * xh[m]);
     }
   }
   float out;
   if (CERT) {
-    sd = block_dsum<1>(sd, shd);
-    out = __double2float_rd(__dsub_rd(__dadd_rd(cd[rl], sd), E[rl]));
+    s = block_fsum<1>(s, shf);
+    out = __double2float_rd(__dsub_rd(__dadd_rd(cd[rl], (double)s), E[rl]));
   } else {
     s = block_sum(s, shf);
     out = cf[rl] + s;
@@ -491,40 +485,74 @@ __global__ void __launch_bounds__(256) k_fwd_epi(RowsCtx c, int layer, int d, lo
 // Projected Adam ascent with best-row tracking (Eq. opt_alpha_beta; Appendix C.1).
 // One block per row; the row's alpha block and beta block.
 // ----------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_adam(int R, int K, BatchView bt, const int32_t* __restrict__ U,
-                                              int P, const float* __restrict__ lb_t, float* __restrict__ best_lb,
-                                              float* __restrict__ a_cur, float* __restrict__ a_best,
-                                              const float* __restrict__ ga, float* __restrict__ ma,
-                                              float* __restrict__ va, float* __restrict__ b_cur,
-                                              float* __restrict__ b_best, const float* __restrict__ gb,
-                                              float* __restrict__ mb, float* __restrict__ vb, float lr_a,
-                                              float lr_b, float beta1, float beta2, float eps, float bc1,
-                                              float bc2, int64_t n_alpha, int64_t n_beta) {
-  int r = blockIdx.x;
-  int b = r / K, k = r - b * K;
-  int p = bt.prop_of[b];
+// One projected Adam step of one alpha (projection onto [0, 1]).
+__device__ __forceinline__ float adam_alpha(float th, float g, float& m, float& v, float lr, float beta1, float beta2,
+                                            float eps, float bc1, float bc2) {
+  m = beta1 * m + (1.f - beta1) * g;
+  v = beta2 * v + (1.f - beta2) * g * g;
+  th += lr * (m / bc1) / (sqrtf(v / bc2) + eps);
+  return fminf(fmaxf(th, 0.f), 1.f);
+}
+
+// One warp per row: the row's alphas in 16-byte accesses where the arrays allow it.
+constexpr int ADAM_ROWS_PER_BLOCK = 8;
+__global__ void __launch_bounds__(32 * ADAM_ROWS_PER_BLOCK) k_adam(
+    int R, int K, BatchView bt, const int32_t* __restrict__ U, int P, const float* __restrict__ lb_t,
+    float* __restrict__ best_lb, float* __restrict__ a_cur, float* __restrict__ a_best,
+    const float* __restrict__ ga, float* __restrict__ ma, float* __restrict__ va, float* __restrict__ b_cur,
+    float* __restrict__ b_best, const float* __restrict__ gb, float* __restrict__ mb, float* __restrict__ vb,
+    float lr_a, float lr_b, float beta1, float beta2, float eps, float bc1, float bc2, int64_t n_alpha,
+    int64_t n_beta) {
+  const int lane = threadIdx.x & 31;
+  const int r = blockIdx.x * ADAM_ROWS_PER_BLOCK + (threadIdx.x >> 5);
+  if (r >= R) return;
+  const int b = r / K, k = r - b * K;
+  const int p = bt.prop_of[b];
   if (p < 0 || p >= P) return;
-  float cur = lb_t[r], best = best_lb[r];
-  bool improved = cur > best;
-  int Up = U[p];
-  long long abase = bt.alpha_off[b] + (long long)k * Up;
-  for (int t = threadIdx.x; t < Up; t += blockDim.x) {
-    long long i = abase + t;
-    if (i < 0 || i >= n_alpha) break;
-    float th = a_cur[i];
+  const float cur = lb_t[r];
+  const bool improved = cur > best_lb[r];
+  const int Up = U[p];
+  const long long abase = bt.alpha_off[b] + (long long)k * Up;
+  // the row's alphas that lie in the array
+  const long long aend = abase < 0 ? abase : min(abase + (long long)Up, (long long)n_alpha);
+  auto one = [&](long long i) {
+    const float th = a_cur[i];
     if (improved) a_best[i] = th;
-    float g = ga[i];
-    float m = beta1 * ma[i] + (1.f - beta1) * g;
-    float v = beta2 * va[i] + (1.f - beta2) * g * g;
+    float m = ma[i], v = va[i];
+    a_cur[i] = adam_alpha(th, ga[i], m, v, lr_a, beta1, beta2, eps, bc1, bc2);
     ma[i] = m;
     va[i] = v;
-    th += lr_a * (m / bc1) / (sqrtf(v / bc2) + eps);
-    a_cur[i] = fminf(fmaxf(th, 0.f), 1.f);
+  };
+  const bool vec = ((reinterpret_cast<uintptr_t>(a_cur) | reinterpret_cast<uintptr_t>(a_best) |
+                     reinterpret_cast<uintptr_t>(ga) | reinterpret_cast<uintptr_t>(ma) |
+                     reinterpret_cast<uintptr_t>(va)) & 15u) == 0;
+  long long v0 = aend, v1 = aend;   // [v0, v1): 4-aligned body updated with 16-byte accesses
+  if (vec && aend > abase) {
+    v0 = min(aend, (abase + 3) & ~3LL);
+    v1 = v0 + ((aend - v0) & ~3LL);
   }
-  int cnt = bt.split_cnt[b];
-  long long bbase = (long long)bt.split_off[b] * K + (long long)k * cnt;
-  for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-    long long i = bbase + t;
+  for (long long i = abase + lane; i < v0; i += 32) one(i);
+  for (long long i = v1 + lane; i < aend; i += 32) one(i);
+#pragma unroll 2
+  for (long long i = v0 + 4 * lane; i < v1; i += 128) {
+    const float4 th = *reinterpret_cast<const float4*>(a_cur + i);
+    const float4 g = *reinterpret_cast<const float4*>(ga + i);
+    float4 m = *reinterpret_cast<const float4*>(ma + i);
+    float4 v = *reinterpret_cast<const float4*>(va + i);
+    if (improved) *reinterpret_cast<float4*>(a_best + i) = th;
+    float4 o;
+    o.x = adam_alpha(th.x, g.x, m.x, v.x, lr_a, beta1, beta2, eps, bc1, bc2);
+    o.y = adam_alpha(th.y, g.y, m.y, v.y, lr_a, beta1, beta2, eps, bc1, bc2);
+    o.z = adam_alpha(th.z, g.z, m.z, v.z, lr_a, beta1, beta2, eps, bc1, bc2);
+    o.w = adam_alpha(th.w, g.w, m.w, v.w, lr_a, beta1, beta2, eps, bc1, bc2);
+    *reinterpret_cast<float4*>(a_cur + i) = o;
+    *reinterpret_cast<float4*>(ma + i) = m;
+    *reinterpret_cast<float4*>(va + i) = v;
+  }
+  const int cnt = bt.split_cnt[b];
+  const long long bbase = (long long)bt.split_off[b] * K + (long long)k * cnt;
+  for (int t = lane; t < cnt; t += 32) {
+    const long long i = bbase + t;
     if (i < 0 || i >= n_beta) break;
     float th = b_cur[i];
     if (improved) b_best[i] = th;
@@ -536,8 +564,8 @@ __global__ void __launch_bounds__(128) k_adam(int R, int K, BatchView bt, const 
     th += lr_b * (m / bc1) / (sqrtf(v / bc2) + eps);
     b_cur[i] = fmaxf(th, 0.f);
   }
-  __syncthreads();
-  if (threadIdx.x == 0 && improved) best_lb[r] = cur;
+  __syncwarp();
+  if (lane == 0 && improved) best_lb[r] = cur;
 }
 
 // ----------------------------------------------------------------------------------------
@@ -700,14 +728,13 @@ __global__ void __launch_bounds__(256) k_relax_root(int Rc, int p, int H, int d,
                                                     const float* __restrict__ Ain, float* __restrict__ Lam,
                                                     const float* __restrict__ bias, float* __restrict__ cf,
                                                     double* __restrict__ cd, double* __restrict__ E,
-                                                    const double* __restrict__ wm, double gamma) {
+                                                    const float* __restrict__ wm, double gamma) {
   __shared__ float shf[32];
-  __shared__ double shd[32];
   int rl = blockIdx.x;
   const float* a_row = Ain + (size_t)rl * d;
   float* lam_row = Lam + (size_t)rl * d;
-  float acc = 0.f;
-  double accd = 0.0, e1 = 0.0, e2 = 0.0;
+  // CERT: acc rounded down, e1 and e2 rounded up (as in k_relax)
+  float acc = 0.f, e1 = 0.f, e2 = 0.f;
   for (int j = threadIdx.x; j < d; j += blockDim.x) {
     float a = a_row[j];
     size_t n = (size_t)p * H + hoff + j;
@@ -717,10 +744,7 @@ __global__ void __launch_bounds__(256) k_relax_root(int Rc, int p, int H, int d,
     if (code == CODE_ACTIVE) D = 1.f;
     else if (code == CODE_INACTIVE) D = 0.f;
     else if (a >= 0.f) D = rule == BCROWN_ALPHA_ADAPTIVE ? (uv >= -lv ? 1.f : 0.f) : rule_value;
-    else if (CERT) {
-      D = __fdiv_ru(uv, __fsub_rd(uv, lv));
-      lm = __fmul_ru(D, -lv);
-    } else {
+    else {
       D = tb.slope[n];
       lm = tb.icpt[n];
     }
@@ -728,24 +752,24 @@ __global__ void __launch_bounds__(256) k_relax_root(int Rc, int p, int H, int d,
     lam_row[j] = L;
     float bj = bias[j];
     if (CERT) {
-      accd = __dadd_rd(accd, __dadd_rd((double)L * (double)bj, (double)a * (double)lm));
+      acc = __fadd_rd(acc, __fadd_rd(__fmul_rd(L, bj), __fmul_rd(a, lm)));
       if (!(D == 0.f || D == 1.f)) {
         float zmax = fmaxf(fabsf(lv), fabsf(uv));
-        double er = __dadd_ru(__dmul_ru(fabs((double)L), 0x1p-23), 0x1p-140);
-        e1 = __dadd_ru(e1, __dmul_ru(er, (double)zmax));
+        float er = __fmaf_ru(fabsf(L), 0x1p-23f, 0x1p-140f);
+        e1 = __fadd_ru(e1, __fmul_ru(er, zmax));
       }
-      e2 = __dadd_ru(e2, __dmul_ru(fabs((double)L), wm[n]));
+      e2 = __fadd_ru(e2, __fmul_ru(fabsf(L), wm[n]));
     } else {
       acc = fmaf(L, bj, fmaf(a, lm, acc));
     }
   }
   if (CERT) {
-    accd = block_dsum<1>(accd, shd);
-    e1 = block_dsum<2>(e1, shd);
-    e2 = block_dsum<2>(e2, shd);
+    acc = block_fsum<1>(acc, shf);
+    e1 = block_fsum<2>(e1, shf);
+    e2 = block_fsum<2>(e2, shf);
     if (threadIdx.x == 0) {
-      cd[rl] = __dadd_rd(cd[rl], accd);
-      E[rl] = __dadd_ru(E[rl], __dadd_ru(e1, __dmul_ru(gamma, e2)));
+      cd[rl] = __dadd_rd(cd[rl], (double)acc);
+      E[rl] = __dadd_ru(E[rl], __dadd_ru((double)e1, __dmul_ru(gamma, (double)e2)));
     }
   } else {
     acc = block_sum(acc, shf);
@@ -761,22 +785,20 @@ __global__ void __launch_bounds__(256) k_concretize_root(int q0, int Rc, int p, 
                                                          const double* __restrict__ cd, const double* __restrict__ E,
                                                          float* __restrict__ l, float* __restrict__ u) {
   __shared__ float shf[32];
-  __shared__ double shd[32];
   int rl = blockIdx.x;
   const float* a = A0 + (size_t)rl * d0;
   const float* xl = x_lo + (size_t)p * d0;
   const float* xh = x_hi + (size_t)p * d0;
   float s = 0.f;
-  double sd = 0.0;
   for (int m = threadIdx.x; m < d0; m += blockDim.x) {
     float am = a[m];
-    if (CERT) sd = __dadd_rd(sd, fmin((double)am * (double)xl[m], (double)am * (double)xh[m]));
+    if (CERT) s = __fadd_rd(s, fminf(__fmul_rd(am, xl[m]), __fmul_rd(am, xh[m])));
     else s += fminf(am * xl[m], am * xh[m]);
   }
   float out;
   if (CERT) {
-    sd = block_dsum<1>(sd, shd);
-    out = __double2float_rd(__dsub_rd(__dadd_rd(cd[rl], sd), E[rl]));
+    s = block_fsum<1>(s, shf);
+    out = __double2float_rd(__dsub_rd(__dadd_rd(cd[rl], (double)s), E[rl]));
   } else {
     s = block_sum(s, shf);
     out = cf[rl] + s;
@@ -809,9 +831,9 @@ void launch_tables(int P, int H, const float* l, const float* u, Tables& t, uint
 }
 
 void launch_absw_m(const LayerGeom& g, const float* W, int P, int H, long long hoff_i, long long hoff_prev,
-                   const float* u, const float* x_lo, const float* x_hi, int d0, double* wm, cudaStream_t s) {
+                   const float* u, const float* x_lo, const float* x_hi, int d0, float* wm, cudaStream_t s) {
   long long n = (long long)P * g.d_out;
-  if (n > 0) { k_absw_m<<<grid1d(n, 128), 128, 0, s>>>(g, W, P, H, hoff_i, hoff_prev, u, x_lo, x_hi, d0, wm); ++g_launches; }
+  if (n > 0) { k_absw_m<<<grid1d(n * 32, 256), 256, 0, s>>>(g, W, P, H, hoff_i, hoff_prev, u, x_lo, x_hi, d0, wm); ++g_launches; }
 }
 
 void launch_init_top(bool cert, const RowsCtx& c, int dtop, const bcrown_net* net, long long hoff_top, float* A,
@@ -827,7 +849,7 @@ void launch_init_top(bool cert, const RowsCtx& c, int dtop, const bcrown_net* ne
 
 void launch_relax(bool cert, const RowsCtx& c, int layer, int d, long long hoff, const float* Ain, float* Lam,
                   const float* bias, const float* alpha, int64_t n_alpha, const float* beta, int64_t n_beta, float* cf,
-                  double* cd, double* E, const double* wm, double gamma, cudaStream_t s) {
+                  double* cd, double* E, const float* wm, double gamma, cudaStream_t s) {
   if (c.R <= 0) return;
   if (cert)
     { k_relax<true><<<c.R, 256, 0, s>>>(c, layer, d, hoff, Ain, Lam, bias, alpha, n_alpha, beta, n_beta, cf, cd, E, wm, gamma); ++g_launches; }
@@ -877,8 +899,12 @@ void launch_adam(int R, int K, const BatchView& bt, const int32_t* U, int P, con
                  const float* gb, float* mb, float* vb, float lr_a, float lr_b, float beta1, float beta2, float eps,
                  float bc1, float bc2, int64_t n_alpha, int64_t n_beta, cudaStream_t s) {
   if (R <= 0) return;
-  { k_adam<<<R, 128, 0, s>>>(R, K, bt, U, P, lb_t, best_lb, a_cur, a_best, ga, ma, va, b_cur, b_best, gb, mb, vb, lr_a,
-                           lr_b, beta1, beta2, eps, bc1, bc2, n_alpha, n_beta); ++g_launches; }
+  if (R > 0) {
+    k_adam<<<(R + ADAM_ROWS_PER_BLOCK - 1) / ADAM_ROWS_PER_BLOCK, 32 * ADAM_ROWS_PER_BLOCK, 0, s>>>(
+        R, K, bt, U, P, lb_t, best_lb, a_cur, a_best, ga, ma, va, b_cur, b_best, gb, mb, vb, lr_a, lr_b, beta1, beta2,
+        eps, bc1, bc2, n_alpha, n_beta);
+    ++g_launches;
+  }
 }
 
 void launch_codes(const RowsCtx& c, int layer, int d, long long hoff, int H, int8_t* out, cudaStream_t s) {
@@ -903,7 +929,7 @@ void launch_root_top(int q0, int Rc, int d_top, const float* b_top, float* Lam, 
 
 void launch_relax_root(bool cert, int Rc, int p, int H, int d, long long hoff, const float* l, const float* u,
                        const Tables& tb, int rule, float rule_value, const float* Ain, float* Lam, const float* bias,
-                       float* cf, double* cd, double* E, const double* wm, double gamma, cudaStream_t s) {
+                       float* cf, double* cd, double* E, const float* wm, double gamma, cudaStream_t s) {
   if (Rc <= 0) return;
   if (cert)
     { k_relax_root<true><<<Rc, 256, 0, s>>>(Rc, p, H, d, hoff, l, u, tb, rule, rule_value, Ain, Lam, bias, cf, cd, E,

@@ -8,12 +8,12 @@ namespace bcrown {
 void launch_tables(int P, int H, const float* l, const float* u, Tables& t, uint8_t* code, int32_t* rank,
                    float* slope, float* icpt, int32_t* U, cudaStream_t s);
 void launch_absw_m(const LayerGeom& g, const float* W, int P, int H, long long hoff_i, long long hoff_prev,
-                   const float* u, const float* x_lo, const float* x_hi, int d0, double* wm, cudaStream_t s);
+                   const float* u, const float* x_lo, const float* x_hi, int d0, float* wm, cudaStream_t s);
 void launch_init_top(bool cert, const RowsCtx& c, int dtop, const bcrown_net* net, long long hoff_top, float* A,
                      float* cf, double* cd, double* E, cudaStream_t s);
 void launch_relax(bool cert, const RowsCtx& c, int layer, int d, long long hoff, const float* Ain, float* Lam,
                   const float* bias, const float* alpha, int64_t n_alpha, const float* beta, int64_t n_beta, float* cf,
-                  double* cd, double* E, const double* wm, double gamma, cudaStream_t s);
+                  double* cd, double* E, const float* wm, double gamma, cudaStream_t s);
 void launch_sgemm(int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C, int ldc,
                   const float* bias, cudaStream_t s);
 void launch_conv_bwd(int R, const LayerGeom& g, const float* Lam, const float* W, float* Ain, cudaStream_t s);
@@ -38,7 +38,7 @@ void launch_root_top(int q0, int Rc, int d_top, const float* b_top, float* Lam, 
                      cudaStream_t s);
 void launch_relax_root(bool cert, int Rc, int p, int H, int d, long long hoff, const float* l, const float* u,
                        const Tables& tb, int rule, float rule_value, const float* Ain, float* Lam, const float* bias,
-                       float* cf, double* cd, double* E, const double* wm, double gamma, cudaStream_t s);
+                       float* cf, double* cd, double* E, const float* wm, double gamma, cudaStream_t s);
 void launch_concretize_root(bool cert, int q0, int Rc, int p, int d0, int d_top, int H, long long hoff_top,
                             const float* x_lo, const float* x_hi, const float* A0, const float* cf, const double* cd,
                             const double* E, float* l, float* u, cudaStream_t s);
