@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
     ap.add_argument("--subdomains", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample", type=int, default=192, help="subdomains timed on the oracle (about 10-20 s)")
+    ap.add_argument("--cpu-sample", type=int, default=640, help="subdomains timed on the oracle (about 10-20 s)")
     return ap.parse_args()
 
 
@@ -121,6 +121,22 @@ def fp32_simt_peak_tflops(sm_mhz):
 
 
 # ------------------------------------------------------------------------------ oracle leg
+
+def measured_traffic(name, algorithmic_bytes):
+    """DRAM bytes per launch of a kernel from the committed ncu summary profiles/<name>.json, or
+    None when the kernel source has changed since those counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", name + ".json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    src = os.path.join(ROOT, rec["source"])
+    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["source_sha256"]:
+        return None
+    return {"dram_bytes_per_launch": rec["dram_bytes_per_launch"],
+            "vs_algorithmic": rec["dram_bytes_per_launch"] / algorithmic_bytes,
+            "from": "profiles/" + name + ".json (ncu capture of the same workload)"}
+
 
 def cpu_oracle_rate(pb, lu, batch_full, n_sample, seed=0):
     """The FP64 oracle's optimise (20 iters + final bound) on a bounded sample of subdomains."""
@@ -240,21 +256,31 @@ def main():
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     sm_mhz = clk.get("sm_mhz") or 1432.0
     if prof[5][1] > 0:
-        # fused iteration kernel: bound by the alpha/beta and Adam state it must stream
+        # fused bound + adjoint kernel (one launch per Adam iteration): the data it must move are
+        # the alpha/beta it reads, the gradients it writes and the bound of each row
         ms, nl = prof[5]
         U = np.array([len(u) for u in unst])[hbatch.prop_of]
-        bytes_per_launch = float(np.sum(pb.K * (24 * U + 24 * hbatch.split_cnt.astype(np.int64) + 8)))
+        bytes_per_launch = float(np.sum(pb.K * (8 * U + 8 * hbatch.split_cnt.astype(np.int64) + 4)))
         achieved = bytes_per_launch * nl / (ms / 1e3) / 1e9
         peak = peaks.get("hbm_gbs", 6800.0)
         tflops = rows * 2 * f_row * nl / (ms / 1e3) / 1e12
         tpeak = peaks.get("bf16_tflops_sustained", 1700.0)
-        roof = {"bound": "hbm", "kernel": "k_fused (bound + adjoint + projected Adam, one launch per iteration)",
-                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+        roof = {"bound": "hbm", "kernel": "k_fused<1> (tcgen05 bound + adjoint pass, one launch per iteration)",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "traffic_note": None,
                 "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)",
                 "algorithmic_bytes_per_launch": bytes_per_launch,
-                "bytes_model": "per row: 24 B x unstable neurons (alpha, m, v read+write) + 24 B x splits + 8 B",
+                "bytes_model": "per row: 8 B x unstable neurons (alpha read, dalpha write) + 8 B x splits "
+                               "(beta read, dbeta write) + 4 B (lb)",
                 "tensor_tflops": tflops, "tensor_frac": tflops / tpeak,
-                "kernel_ms_per_step": ms / args.steps, "launches_per_step": nl / args.steps}
+                "tensor_peak_source": "of measured (MEASURED_PEAKS.json bf16_tflops_sustained)",
+                "kernel_ms_per_step": ms / args.steps, "launches_per_step": nl / args.steps,
+                "step_ms_by_class": {n: prof[c][0] / args.steps for c, n in enumerate(
+                    ["contract", "relax", "concretize", "adjoint", "adam", "fused"])}}
+        tr = measured_traffic("k_fused_grad", bytes_per_launch)
+        if tr is not None:
+            roof["traffic"] = tr["dram_bytes_per_launch"]
+            roof["traffic_note"] = tr
     else:
         ms, nl = prof[0]
         flops = rows * f_row * (2 * cfg.iters + 1) * args.steps

@@ -485,13 +485,14 @@ __global__ void __launch_bounds__(256) k_fwd_epi(RowsCtx c, int layer, int d, lo
 // Projected Adam ascent with best-row tracking (Eq. opt_alpha_beta; Appendix C.1).
 // One block per row; the row's alpha block and beta block.
 // ----------------------------------------------------------------------------------------
-// One projected Adam step of one alpha (projection onto [0, 1]).
+// One projected Adam step of one alpha (projection onto [0, 1]); ib1, ib2 are the reciprocals
+// of the bias corrections, so an element costs one square root and one (fast) division.
 __device__ __forceinline__ float adam_alpha(float th, float g, float& m, float& v, float lr, float beta1, float beta2,
-                                            float eps, float bc1, float bc2) {
+                                            float eps, float ib1, float ib2) {
   m = beta1 * m + (1.f - beta1) * g;
   v = beta2 * v + (1.f - beta2) * g * g;
-  th += lr * (m / bc1) / (sqrtf(v / bc2) + eps);
-  return fminf(fmaxf(th, 0.f), 1.f);
+  th += __fdividef(lr * (m * ib1), sqrtf(v * ib2) + eps);
+  return __saturatef(th);
 }
 
 // One warp per row: the row's alphas in 16-byte accesses where the arrays allow it.
@@ -511,6 +512,7 @@ __global__ void __launch_bounds__(32 * ADAM_ROWS_PER_BLOCK) k_adam(
   if (p < 0 || p >= P) return;
   const float cur = lb_t[r];
   const bool improved = cur > best_lb[r];
+  const float ib1 = 1.f / bc1, ib2 = 1.f / bc2;
   const int Up = U[p];
   const long long abase = bt.alpha_off[b] + (long long)k * Up;
   // the row's alphas that lie in the array
@@ -519,7 +521,7 @@ __global__ void __launch_bounds__(32 * ADAM_ROWS_PER_BLOCK) k_adam(
     const float th = a_cur[i];
     if (improved) a_best[i] = th;
     float m = ma[i], v = va[i];
-    a_cur[i] = adam_alpha(th, ga[i], m, v, lr_a, beta1, beta2, eps, bc1, bc2);
+    a_cur[i] = adam_alpha(th, ga[i], m, v, lr_a, beta1, beta2, eps, ib1, ib2);
     ma[i] = m;
     va[i] = v;
   };
@@ -541,10 +543,10 @@ __global__ void __launch_bounds__(32 * ADAM_ROWS_PER_BLOCK) k_adam(
     float4 v = *reinterpret_cast<const float4*>(va + i);
     if (improved) *reinterpret_cast<float4*>(a_best + i) = th;
     float4 o;
-    o.x = adam_alpha(th.x, g.x, m.x, v.x, lr_a, beta1, beta2, eps, bc1, bc2);
-    o.y = adam_alpha(th.y, g.y, m.y, v.y, lr_a, beta1, beta2, eps, bc1, bc2);
-    o.z = adam_alpha(th.z, g.z, m.z, v.z, lr_a, beta1, beta2, eps, bc1, bc2);
-    o.w = adam_alpha(th.w, g.w, m.w, v.w, lr_a, beta1, beta2, eps, bc1, bc2);
+    o.x = adam_alpha(th.x, g.x, m.x, v.x, lr_a, beta1, beta2, eps, ib1, ib2);
+    o.y = adam_alpha(th.y, g.y, m.y, v.y, lr_a, beta1, beta2, eps, ib1, ib2);
+    o.z = adam_alpha(th.z, g.z, m.z, v.z, lr_a, beta1, beta2, eps, ib1, ib2);
+    o.w = adam_alpha(th.w, g.w, m.w, v.w, lr_a, beta1, beta2, eps, ib1, ib2);
     *reinterpret_cast<float4*>(a_cur + i) = o;
     *reinterpret_cast<float4*>(ma + i) = m;
     *reinterpret_cast<float4*>(va + i) = v;
