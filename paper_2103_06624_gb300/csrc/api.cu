@@ -203,12 +203,14 @@ static void chunk_simt(bcrown_net* net, const bcrown_domain* dom, const bcrown_b
   }
 }
 
+// tc_plan: group the batch's rows into property tiles first (false when an earlier call on the
+// same batch and plan already did).
 static int run_bound(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* bt, Plan& pl, int precision,
                      bool grad, const float* alpha, const float* beta, float* lb, float* dalpha, float* dbeta,
-                     cudaStream_t s) {
+                     cudaStream_t s, bool tc_plan = true) {
   const int R = bt->B * net->K;
   if (precision == BCROWN_BF16 && tc_supported(net)) {
-    return tc_bound(net, dom, bt, pl.tb, pl.tc_ws, pl.tc_ws_bytes, grad, alpha, beta, lb, dalpha, dbeta, s);
+    return tc_bound(net, dom, bt, pl.tb, pl.tc_ws, pl.tc_ws_bytes, grad, tc_plan, alpha, beta, lb, dalpha, dbeta, s);
   }
   bool cert = precision == BCROWN_CERTIFY;
   for (int r0 = 0; r0 < R; r0 += pl.Rc) {
@@ -241,7 +243,7 @@ extern "C" int bcrown_bound(bcrown_net* net, const bcrown_domain* dom, const bcr
   cudaStream_t s = (cudaStream_t)stream;
   Plan pl;
   int R = batch->B * net->K;
-  size_t tcb = precision == BCROWN_BF16 ? tc_workspace_bytes(net, R, false) : 0;
+  size_t tcb = precision == BCROWN_BF16 ? tc_workspace_bytes(net, batch->B, dom->n_props, false) : 0;
   BC_CHECK(make_plan(net, dom->n_props, R, precision == BCROWN_CERTIFY, false, 0, 0, tcb, pl));
   build_tables(net, dom, pl, s);
   if (precision == BCROWN_CERTIFY) build_wm(net, dom, pl, s);
@@ -264,7 +266,7 @@ extern "C" int bcrown_bound_grad(bcrown_net* net, const bcrown_domain* dom, cons
   cudaStream_t s = (cudaStream_t)stream;
   Plan pl;
   int R = batch->B * net->K;
-  size_t tcb = precision == BCROWN_BF16 ? tc_workspace_bytes(net, R, true) : 0;
+  size_t tcb = precision == BCROWN_BF16 ? tc_workspace_bytes(net, batch->B, dom->n_props, true) : 0;
   BC_CHECK(make_plan(net, dom->n_props, R, false, false, 0, 0, tcb, pl));
   build_tables(net, dom, pl, s);
   BC_CHECK(run_bound(net, dom, batch, pl, precision, true, alpha, beta, lb, dalpha, dbeta, s));
@@ -287,7 +289,7 @@ extern "C" int bcrown_optimize(bcrown_net* net, const bcrown_domain* dom, const 
   const int R = batch->B * net->K;
   const int64_t na = batch->n_alpha, nb = batch->n_beta;
   Plan pl;
-  size_t tcb = cfg->precision == BCROWN_BF16 ? tc_workspace_bytes(net, R, true) : 0;
+  size_t tcb = cfg->precision == BCROWN_BF16 ? tc_workspace_bytes(net, batch->B, dom->n_props, true) : 0;
   bool cert = cfg->certify != 0;
   BC_CHECK(make_plan(net, dom->n_props, R, cert, true, na, nb, tcb, pl));
   build_tables(net, dom, pl, s);
@@ -310,7 +312,8 @@ extern "C" int bcrown_optimize(bcrown_net* net, const bcrown_domain* dom, const 
     float fac = std::pow(cfg->decay, (float)t);
     float bc1 = 1.f - std::pow(cfg->adam_beta1, (float)(t + 1));
     float bc2 = 1.f - std::pow(cfg->adam_beta2, (float)(t + 1));
-    BC_CHECK(run_bound(net, dom, batch, pl, cfg->precision, true, pl.a_cur, pl.b_cur, pl.lb_t, pl.ga, pl.gb, s));
+    BC_CHECK(run_bound(net, dom, batch, pl, cfg->precision, true, pl.a_cur, pl.b_cur, pl.lb_t, pl.ga, pl.gb, s,
+                       t == 0));
     ProfScope ps(net, BCROWN_PROF_ADAM, s);
     launch_adam(R, net->K, bv, pl.U, dom->n_props, pl.lb_t, pl.best_lb, pl.a_cur, alpha, pl.ga, pl.ma, pl.va,
                 pl.b_cur, beta, pl.gb, pl.mb, pl.vb, cfg->lr_alpha * fac, cfg->lr_beta * fac, cfg->adam_beta1,

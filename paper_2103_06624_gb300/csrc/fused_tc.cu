@@ -66,7 +66,7 @@ struct Smem {
   float part[4][TR];                     // lb partial sums per lane quadrant
   long long abase[TR];                   // first alpha of the row
   long long bbase[TR];                   // first beta of the row
-  int prop[TR];
+  int rowid[TR];                         // global row of each tile slot (-1: empty)
   int spec[TR];
   int valid[TR];
   int scnt[TR];                          // the row's split count and first split entry
@@ -74,15 +74,13 @@ struct Smem {
   uint8_t sorig[TR][BCROWN_MAX_SPLITS];  // the row's splits in (mask word, bit) order: list position
   float sbeta[TR][BCROWN_MAX_SPLITS];    //   and beta (clamped at 0)
   uint8_t wfirst[MAX_MASK_WORDS][TR];    // splits of the row in mask words before w
-  uint32_t tcode[MAX_H];                 // uniform tiles: code << 16 | unstable rank, per hidden neuron
+  uint32_t tcode[MAX_H];                 // the tile's property: code << 16 | unstable rank, per hidden neuron
   float tslope[MAX_H];                   //   upper chord slope
   float ticpt[MAX_H];                    //   upper chord intercept
   float sxlo[MAX_D0];                    //   input box
   float sxhi[MAX_D0];
   float sbias[MAX_H];                    // hidden-layer biases, by global hidden index
-  int uniform_p;                         // property shared by every valid row of the tile, or -1
-  uint32_t badw[2];                      // rows below the tile's end that are not valid (bit mask)
-  int fast;                              // uniform_p >= 0 and every row below the tile's end valid
+  unsigned long long vrows;              // tile slots holding a valid row
   uint64_t act_full[NSLOT], act_empty[NSLOT];
   uint64_t w_full[NSTAGE], w_empty[NSTAGE];
   uint64_t acc_full[NACC], acc_empty[NACC];
@@ -95,7 +93,10 @@ struct Smem {
 static_assert(sizeof(Smem) + 1024 <= 232448, "shared memory plan exceeds 227 KB per CTA");
 
 struct Args {
-  int L, K, P, H, R, n_tiles;
+  int L, K, P, H, R;
+  const int* n_tiles;                 // tiles to process (written by the row planner)
+  const int* tile_prop;               // [tile] property of every row of the tile
+  const int* rowmap;                  // [tile][TR] global row of each slot, -1 when empty
   int d[MAXL + 1];
   long long hoff[MAXL + 1];           // first global hidden index of layer i (1-based)
   int woff[MAXL + 1];                 // first mask word of layer i
@@ -408,6 +409,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
   Smem* sm = reinterpret_cast<Smem*>(smem_raw + pad);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n_contr = (a.L - 1) * (MODE >= 1 ? 2 : 1);
+  const int n_tiles = *a.n_tiles;
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < NSLOT; ++i) {
@@ -443,7 +445,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
     if (lane == 0) {
       uint32_t wseq = 0;
       bool ok = true;
-      for (int tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x)
+      for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x)
         for (int ci = 0; ci < n_contr && ok; ++ci) {
           int layer, N, K;
           bool fwd;
@@ -481,7 +483,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
     if (lane == 0) {
       uint32_t wseq = 0, accseq = 0, aseq = 0;
       bool ok = true;
-      for (int tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x)
+      for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x)
         for (int ci = 0; ci < n_contr && ok; ++ci) {
           int layer, N, K;
           bool fwd;
@@ -583,77 +585,52 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
     for (int i = 1; i < a.L; ++i)
       for (int j = etid; j < a.d[i]; j += NEPI * 32) sm->sbias[a.hoff[i] + j] = a.bias[i][j];
 
-    for (int tile = blockIdx.x; tile < a.n_tiles && ok; tile += gridDim.x) {
-      const int nvalid = min(TR, a.R - tile * TR);
+    for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+      // Every row of a tile belongs to one property (the rows are grouped by property before
+      // the launch); slots past the property's last row are empty.
+      const int p = a.tile_prop[tile];
       // ---------------- tile set-up, step 1: per-row scalars (one thread per row)
       if (etid < TR) {
         const int row = etid;
-        int v = row < nvalid;
-        int k = 0, p = 0, cnt = 0, off = 0;
+        const int r = a.rowmap[(size_t)tile * TR + row];
+        int v = r >= 0 && r < a.R && p >= 0 && p < a.P;
+        int k = 0, cnt = 0, off = 0;
         long long ab = 0, bb = 0;
         if (v) {
-          const int r = tile * TR + row;
           const int b = r / a.K;
           k = r - b * a.K;
-          p = a.bt.prop_of[b];
           cnt = a.bt.split_cnt[b];
           off = a.bt.split_off[b];
           const long long ao = a.bt.alpha_off[b];
-          if (p < 0 || p >= a.P || cnt < 0 || cnt > BCROWN_MAX_SPLITS || off < 0) {
+          const int U = a.tb.U[p];
+          ab = ao + (long long)k * U;
+          bb = (long long)off * a.K + (long long)k * cnt;
+          // every alpha of the row must lie in the array: then no per-element check is needed
+          if (cnt < 0 || cnt > BCROWN_MAX_SPLITS || off < 0 || ab < 0 || ab + U > a.n_alpha) {
             atomicCAS(a.status, 0, BCROWN_ERR_ARG);
             v = 0;
-          } else {
-            const int U = a.tb.U[p];
-            ab = ao + (long long)k * U;
-            bb = (long long)off * a.K + (long long)k * cnt;
-            // every alpha of the row must lie in the array: then no per-element check is needed
-            if (ab < 0 || ab + U > a.n_alpha) {
-              atomicCAS(a.status, 0, BCROWN_ERR_ARG);
-              v = 0;
-            }
           }
         }
         sm->valid[row] = v;
+        sm->rowid[row] = v ? r : -1;
         sm->spec[row] = v ? k : 0;
-        sm->prop[row] = v ? p : 0;
         sm->scnt[row] = v ? cnt : 0;
         sm->soff[row] = off;
         sm->abase[row] = v ? ab : 0;
         sm->bbase[row] = v ? bb : 0;
         sm->part[0][row] = sm->part[1][row] = sm->part[2][row] = sm->part[3][row] = 0.f;
-        const unsigned bad = __ballot_sync(0xffffffffu, row < nvalid && !v);   // warps 0 and 1
-        if (lane == 0) sm->badw[warp] = bad;
+        const unsigned vb = __ballot_sync(0xffffffffu, v != 0);   // warps 0 and 1
+        if (lane == 0) reinterpret_cast<uint32_t*>(&sm->vrows)[warp] = vb;
       }
       for (int x = etid; x < a.mask_words * TR; x += NEPI * 32) {
         (&sm->smask[0][0])[x] = 0u;
         (&sm->sneg[0][0])[x] = 0u;
       }
-      if (etid == TR) {
-        // the tile's alpha block (rows are packed in order): pull it towards L2 now, it is
-        // read layer by layer below
-        const int ra = tile * TR, rb = tile * TR + nvalid - 1;
-        const int b0 = ra / a.K, b1 = rb / a.K;
-        const int p0 = a.bt.prop_of[b0], p1 = a.bt.prop_of[b1];
-        if (p0 >= 0 && p0 < a.P && p1 >= 0 && p1 < a.P) {
-          const long long lo = a.bt.alpha_off[b0] + (long long)(ra - b0 * a.K) * a.tb.U[p0];
-          const long long hi = a.bt.alpha_off[b1] + (long long)(rb - b1 * a.K + 1) * a.tb.U[p1];
-          if (lo >= 0 && hi <= a.n_alpha && hi > lo) prefetch_l2(a.alpha + lo, (hi - lo) * 4);
-        }
-      }
-      if (etid == TR + 32) {
-        // rows of a tile usually come from one property: then per-neuron tables are staged once
-        const int b0 = (tile * TR) / a.K, b1 = (tile * TR + nvalid - 1) / a.K;
-        int pu = a.bt.prop_of[b0];
-        for (int b = b0 + 1; b <= b1; ++b)
-          if (a.bt.prop_of[b] != pu) pu = -1;
-        if (pu < 0 || pu >= a.P) pu = -1;
-        sm->uniform_p = pu;
-      }
       if (!epi_sync(sm, eseq, a.status)) {
         ok = false;
         break;
       }
-      // ---------------- step 2: split masks (8 threads per row), tables and box of a uniform tile
+      // ---------------- step 2: split masks (8 threads per row); the property's tables and box
       int ent[BCROWN_MAX_SPLITS / 8];   // this thread's split entries: mask word << 5 | bit, or -1
       {
         const int row = etid >> 3, e0 = etid & 7;
@@ -676,49 +653,45 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
             }
           }
         }
-        const int pu = sm->uniform_p;
-        if (pu >= 0) {
-          // all loads first, then the stores (3 neurons and 2 inputs per thread at most)
-          constexpr int NT = (MAX_H + NEPI * 32 - 1) / (NEPI * 32), NX = (MAX_D0 + NEPI * 32 - 1) / (NEPI * 32);
-          int cd[NT], rk[NT];
-          float sl[NT], ic[NT], xl[NX], xh[NX];
+        const int pp = (p >= 0 && p < a.P) ? p : 0;
+        // all loads first, then the stores (3 neurons and 2 inputs per thread at most)
+        constexpr int NT = (MAX_H + NEPI * 32 - 1) / (NEPI * 32), NX = (MAX_D0 + NEPI * 32 - 1) / (NEPI * 32);
+        int cd[NT], rk[NT];
+        float sl[NT], ic[NT], xl[NX], xh[NX];
 #pragma unroll
-          for (int u = 0; u < NT; ++u) {
-            const int nn = etid + u * NEPI * 32;
-            const size_t g = (size_t)pu * a.H + nn;
-            const bool in = nn < a.H;
-            cd[u] = in ? a.tb.code[g] : 0;
-            rk[u] = in ? a.tb.rank[g] : 0;
-            sl[u] = in ? a.tb.slope[g] : 0.f;
-            ic[u] = in ? a.tb.icpt[g] : 0.f;
-          }
+        for (int u = 0; u < NT; ++u) {
+          const int nn = etid + u * NEPI * 32;
+          const size_t g = (size_t)pp * a.H + nn;
+          const bool in = nn < a.H;
+          cd[u] = in ? a.tb.code[g] : 0;
+          rk[u] = in ? a.tb.rank[g] : 0;
+          sl[u] = in ? a.tb.slope[g] : 0.f;
+          ic[u] = in ? a.tb.icpt[g] : 0.f;
+        }
 #pragma unroll
-          for (int u = 0; u < NX; ++u) {
-            const int m = etid + u * NEPI * 32;
-            const bool in = m < a.d[0];
-            xl[u] = in ? a.x_lo[(size_t)pu * a.d[0] + m] : 0.f;
-            xh[u] = in ? a.x_hi[(size_t)pu * a.d[0] + m] : 0.f;
-          }
+        for (int u = 0; u < NX; ++u) {
+          const int m = etid + u * NEPI * 32;
+          const bool in = m < a.d[0];
+          xl[u] = in ? a.x_lo[(size_t)pp * a.d[0] + m] : 0.f;
+          xh[u] = in ? a.x_hi[(size_t)pp * a.d[0] + m] : 0.f;
+        }
 #pragma unroll
-          for (int u = 0; u < NT; ++u) {
-            const int nn = etid + u * NEPI * 32;
-            if (nn < a.H) {
-              sm->tcode[nn] = ((uint32_t)cd[u] << 16) | (uint32_t)(rk[u] < 0 ? 0xFFFF : (rk[u] & 0xFFFF));
-              sm->tslope[nn] = sl[u];
-              sm->ticpt[nn] = ic[u];
-            }
-          }
-#pragma unroll
-          for (int u = 0; u < NX; ++u) {
-            const int m = etid + u * NEPI * 32;
-            if (m < a.d[0]) {
-              sm->sxlo[m] = xl[u];
-              sm->sxhi[m] = xh[u];
-            }
+        for (int u = 0; u < NT; ++u) {
+          const int nn = etid + u * NEPI * 32;
+          if (nn < a.H) {
+            sm->tcode[nn] = ((uint32_t)cd[u] << 16) | (uint32_t)(rk[u] < 0 ? 0xFFFF : (rk[u] & 0xFFFF));
+            sm->tslope[nn] = sl[u];
+            sm->ticpt[nn] = ic[u];
           }
         }
-        // fast path: one property and every row below the tile's end valid
-        if (etid == 0) sm->fast = pu >= 0 && sm->badw[0] == 0u && sm->badw[1] == 0u;
+#pragma unroll
+        for (int u = 0; u < NX; ++u) {
+          const int m = etid + u * NEPI * 32;
+          if (m < a.d[0]) {
+            sm->sxlo[m] = xl[u];
+            sm->sxhi[m] = xh[u];
+          }
+        }
       }
       if (!epi_sync(sm, eseq, a.status)) {
         ok = false;
@@ -761,8 +734,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
         ok = false;
         break;
       }
-      const bool fast = sm->fast != 0;
-      const int nvt = nvalid - r0;   // rows of this thread below nvalid (may be <= 0 or > 16)
+      // rows of this thread that take part (bit c: tile row r0 + c); empty rows have all-zero
+      // operands, so they only need their global loads and stores masked
+      const uint32_t vbits = (uint32_t)(sm->vrows >> r0) & 0xFFFFu;
 
       // per-thread lb partial sums of its 16 rows over the lanes' neurons (whole backward pass)
       float racc[16];
@@ -783,13 +757,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
           const int j = mc * MCH + 32 * q + lane;   // output neuron of this lane
           const bool jin = j < N;
           if (concretise) {
-            const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * TR + r0);
             // ---- lb += sum_m min(A_m x_lo_m, A_m x_hi_m) (Eq. beta_crown_lp); sign bits of A^(0) for x*
-            float uxl = 0.f, uxh = 0.f;
-            if (fast && jin) {
-              uxl = sm->sxlo[j];
-              uxh = sm->sxhi[j];
-            }
+            const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * TR + r0);
+            const float uxl = jin ? sm->sxlo[j] : 0.f, uxh = jin ? sm->sxhi[j] : 0.f;
             if (!mbar_wait_warp(&sm->acc_full[buf], (accseq / NACC) & 1, sm, a.status)) {
               ok = false;
               break;
@@ -809,18 +779,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
               for (int c8 = 0; c8 < 8; ++c8) {
                 const int c = 8 * h + c8;
                 const float av = v[c8];
-                float xl = uxl, xh = uxh;
-                if (!fast) {
-                  const int row = r0 + c;
-                  const bool in = jin && row < nvalid && sm->valid[row];
-                  xl = xh = 0.f;
-                  if (in) {
-                    const int p = sm->prop[row];
-                    xl = a.x_lo[(size_t)p * N + j];
-                    xh = a.x_hi[(size_t)p * N + j];
-                  }
-                }
-                racc[c] += fminf(av * xl, av * xh);
+                racc[c] += fminf(av * uxl, av * uxh);
                 if constexpr (MODE >= 1) {
                   const unsigned bits = __ballot_sync(0xffffffffu, jin && av >= 0.f);
                   if (lane == 0 && mc * MCH + 32 * q < MAX_D0) sm->sign[r0 + c][(mc * MCH + 32 * q) >> 5] = bits;
@@ -837,13 +796,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
           float dneg = 0.f, lneg = 0.f, bj = 0.f;
           if (jin) {
             bj = sm->sbias[n];
-            if (fast) {
-              const uint32_t t = sm->tcode[n];
-              code = (int)(t >> 16);
-              rank = (int)(t & 0xFFFF);
-              dneg = code == CODE_ACTIVE ? 1.f : (code == CODE_UNSTABLE ? sm->tslope[n] : 0.f);
-              lneg = code == CODE_UNSTABLE ? sm->ticpt[n] : 0.f;
-            }
+            const uint32_t t = sm->tcode[n];
+            code = (int)(t >> 16);
+            rank = (int)(t & 0xFFFF);
+            dneg = code == CODE_ACTIVE ? 1.f : (code == CODE_UNSTABLE ? sm->tslope[n] : 0.f);
+            lneg = code == CODE_UNSTABLE ? sm->ticpt[n] : 0.f;
           }
           const bool unst = code == CODE_UNSTABLE;
           const float apos = code == CODE_ACTIVE ? 1.f : 0.f;
@@ -858,18 +815,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
           // alpha of the 16 rows, issued before waiting for the accumulator
           float al[16];
 #pragma unroll
-          for (int c = 0; c < 16; ++c) {
-            const int row = r0 + c;
-            if (fast) {
-              al[c] = ldg_f32(a.alpha + sm->abase[row] + rank, unst && c < nvt);
-            } else {
-              al[c] = 0.f;
-              if (jin && row < nvalid && sm->valid[row]) {
-                const size_t g = (size_t)sm->prop[row] * a.H + n;
-                if (a.tb.code[g] == CODE_UNSTABLE) al[c] = ldg_f32(a.alpha + sm->abase[row] + a.tb.rank[g], true);
-              }
-            }
-          }
+          for (int c = 0; c < 16; ++c) al[c] = ldg_f32(a.alpha + sm->abase[r0 + c] + rank, unst && ((vbits >> c) & 1u));
           // byte offset of (row r0 + 8h + c8, k = j % 64) in the slot: row & 7 == c8
           const int kk = j & (KBLK - 1);
           uint8_t* aslot = sm->act[slot] + r0 * 128 + ((kk & 7) << 1);
@@ -881,27 +827,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
               const int c = 8 * h + c8;
               const int row = r0 + c;
               const float av = v[c8];
-              float D, lm, bs = 0.f;
-              if (fast) {
-                const bool pos = av >= 0.f;
-                D = pos ? __saturatef(al[c] + apos) : dneg;
-                lm = pos ? 0.f : lneg;
-              } else {
-                D = 0.f;
-                lm = 0.f;
-                if (jin && row < nvalid && sm->valid[row]) {
-                  const size_t g = (size_t)sm->prop[row] * a.H + n;
-                  const int cd = a.tb.code[g];
-                  if (cd == CODE_ACTIVE) D = 1.f;
-                  else if (cd == CODE_UNSTABLE) {
-                    if (av >= 0.f) D = __saturatef(al[c]);
-                    else {
-                      D = a.tb.slope[g];
-                      lm = a.tb.icpt[g];
-                    }
-                  }
-                }
-              }
+              const bool pos = av >= 0.f;
+              float D = pos ? __saturatef(al[c] + apos) : dneg;
+              float lm = pos ? 0.f : lneg;
+              float bs = 0.f;
               if ((rbits >> c) & 1u) {
                 if (sm->smask[wd][row] & bit) {
                   const int sg = (sm->sneg[wd][row] & bit) ? 1 : -1;
@@ -948,8 +877,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
               // A^(L-1) = Wbar rows of the rows' specifications
 #pragma unroll
               for (int c8 = 0; c8 < 8; ++c8) {
-                const int row = r0 + 8 * h + c8;
-                v[c8] = ldg_f32(a.Wbar + (size_t)sm->spec[row] * N + j, jin && row < nvalid && sm->valid[row]);
+                const int c = 8 * h + c8;
+                v[c8] = ldg_f32(a.Wbar + (size_t)sm->spec[r0 + c] * N + j, jin && ((vbits >> c) & 1u));
               }
             } else {
               tmem_ld8(tbase + 8 * h, v);
@@ -982,14 +911,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
         ok = false;
         break;
       }
-      if (etid < nvalid && sm->valid[etid]) {
+      if (etid < TR && sm->valid[etid]) {
         const int row = etid;
         float lbv = a.bbar[sm->spec[row]] + ((sm->part[0][row] + sm->part[1][row]) + (sm->part[2][row] + sm->part[3][row]));
         if (!isfinite(lbv)) {
           atomicCAS(a.status, 0, BCROWN_ERR_NONFINITE);
           lbv = -INFINITY;
         }
-        a.lb[tile * TR + row] = lbv;
+        a.lb[sm->rowid[row]] = lbv;
       }
       if constexpr (MODE == 0) continue;
 
@@ -997,8 +926,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
       {
         const int d0 = a.d[0];
         const int nkb = nkb_of(d0);
-        const bool rv = prow < nvalid && sm->valid[prow];
-        const int p = sm->prop[prow];
+        const bool rv = sm->valid[prow] != 0;
         for (int kb = pg; kb < nkb && ok; kb += 2) {
           const uint32_t as = aseq + kb;
           const int slot = as % NSLOT;
@@ -1017,8 +945,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
               if (m < d0 && rv) {
                 // x* minimises A^(0) x over the box: x_lo where A^(0) >= 0, else x_hi
                 const bool pos = (sm->sign[prow][m >> 5] >> (m & 31)) & 1u;
-                if (fast) x = pos ? sm->sxlo[m] : sm->sxhi[m];
-                else x = pos ? a.x_lo[(size_t)p * d0 + m] : a.x_hi[(size_t)p * d0 + m];
+                x = pos ? sm->sxlo[m] : sm->sxhi[m];
               }
               xv[h] = x;
             }
@@ -1048,13 +975,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
           float dneg = 0.f, lneg = 0.f, bj = 0.f;
           if (jin) {
             bj = sm->sbias[n];
-            if (fast) {
-              const uint32_t t = sm->tcode[n];
-              code = (int)(t >> 16);
-              rank = (int)(t & 0xFFFF);
-              dneg = code == CODE_ACTIVE ? 1.f : (code == CODE_UNSTABLE ? sm->tslope[n] : 0.f);
-              lneg = code == CODE_UNSTABLE ? sm->ticpt[n] : 0.f;
-            }
+            const uint32_t t = sm->tcode[n];
+            code = (int)(t >> 16);
+            rank = (int)(t & 0xFFFF);
+            dneg = code == CODE_ACTIVE ? 1.f : (code == CODE_UNSTABLE ? sm->tslope[n] : 0.f);
+            lneg = code == CODE_UNSTABLE ? sm->ticpt[n] : 0.f;
           }
           const bool unst = code == CODE_UNSTABLE;
           const float apos = code == CODE_ACTIVE ? 1.f : 0.f;
@@ -1070,18 +995,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
           const uint4 s0 = ldg_v4(sp, jin), s1 = ldg_v4(sp + 8, jin);
           float al[16];
 #pragma unroll
-          for (int c = 0; c < 16; ++c) {
-            const int row = r0 + c;
-            if (fast) {
-              al[c] = ldg_f32(a.alpha + sm->abase[row] + rank, unst && c < nvt);
-            } else {
-              al[c] = 0.f;
-              if (jin && row < nvalid && sm->valid[row]) {
-                const size_t g = (size_t)sm->prop[row] * a.H + n;
-                if (a.tb.code[g] == CODE_UNSTABLE) al[c] = ldg_f32(a.alpha + sm->abase[row] + a.tb.rank[g], true);
-              }
-            }
-          }
+          for (int c = 0; c < 16; ++c) al[c] = ldg_f32(a.alpha + sm->abase[r0 + c] + rank, unst && ((vbits >> c) & 1u));
           if (!mbar_wait_warp(&sm->acc_full[buf], (accseq / NACC) & 1, sm, a.status)) {
             ok = false;
             break;
@@ -1111,33 +1025,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
             for (int c8 = 0; c8 < 8; ++c8) {
               const int c = 8 * h + c8;
               const int row = r0 + c;
+              const bool rin = (vbits >> c) & 1u;
               const float A = __uint_as_float((c8 & 1) ? (swv[c8 >> 1] & 0xFFFF0000u) : (swv[c8 >> 1] << 16));
               const float z = vz[c8] + bj;
               const bool pos = A >= 0.f;
-              bool un = unst, rin = c < nvt;
-              float D, lm;
-              if (fast) {
-                D = pos ? __saturatef(al[c] + apos) : dneg;
-                lm = pos ? 0.f : lneg;
-              } else {
-                D = 0.f;
-                lm = 0.f;
-                un = false;
-                rin = jin && row < nvalid && sm->valid[row];
-                if (rin) {
-                  const size_t g = (size_t)sm->prop[row] * a.H + n;
-                  const int cd = a.tb.code[g];
-                  un = cd == CODE_UNSTABLE;
-                  if (cd == CODE_ACTIVE) D = 1.f;
-                  else if (un) {
-                    if (pos) D = __saturatef(al[c]);
-                    else {
-                      D = a.tb.slope[g];
-                      lm = a.tb.icpt[g];
-                    }
-                  }
-                }
-              }
+              float D = pos ? __saturatef(al[c] + apos) : dneg;
+              float lm = pos ? 0.f : lneg;
               float g = pos ? A * z : 0.f;
               if ((rbits >> c) & 1u) {
                 if (sm->smask[wd][row] & bit) {
@@ -1149,10 +1042,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
                   if (bi < a.n_beta) a.dbeta[bi] = (float)sg * z;
                 }
               }
-              if (un && rin) {
-                const int rk = fast ? rank : a.tb.rank[(size_t)sm->prop[row] * a.H + n];
-                a.dalpha[sm->abase[row] + rk] = g;
-              }
+              if (unst && rin) a.dalpha[sm->abase[row] + rank] = g;
               const float hv = rin ? fmaf(D, z, lm) : 0.f;
               if (writer)
                 *reinterpret_cast<__nv_bfloat16*>(aslot + (8 * h + c8) * 128 + (kx ^ (uint32_t)(c8 << 4))) =
@@ -1177,6 +1067,107 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NACC * TR) : "memory");
   }
+}
+
+// ------------------------------------------------------------------------------------------
+// Row planner: group the rows (subdomain, spec) by property into tiles of TR rows, so that the
+// fused kernel stages one property's tables per tile.  Row results do not depend on the tile a
+// row lands in (each row is one column of every contraction), so the order inside a property
+// is free; it is taken from atomic counters.
+// ------------------------------------------------------------------------------------------
+__global__ void k_plan_count(int B, int P, const int32_t* __restrict__ prop_of, int* __restrict__ cnt, int* status) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
+    const int p = prop_of[b];
+    if (p < 0 || p >= P) {
+      atomicCAS(status, 0, BCROWN_ERR_ARG);
+      continue;
+    }
+    atomicAdd(&cnt[p], 1);
+  }
+}
+
+// Exclusive prefix sums over the properties of their subdomains and of their tiles (one block).
+__global__ void __launch_bounds__(1024) k_plan_scan(int P, int K, const int* __restrict__ cnt, int* __restrict__ cursor,
+                                                    int* __restrict__ sub_base, int* __restrict__ tile_base,
+                                                    int* __restrict__ n_tiles) {
+  __shared__ int ws[32], wt[32];
+  __shared__ int run_s, run_t;
+  if (threadIdx.x == 0) run_s = run_t = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int base = 0; base < P; base += blockDim.x) {
+    const int p = base + threadIdx.x;
+    const int c = p < P ? cnt[p] : 0;
+    const int t = (int)(((long long)c * K + TR - 1) / TR);
+    int is = c, it = t;   // inclusive scans within the warp
+    for (int o = 1; o < 32; o <<= 1) {
+      const int xs = __shfl_up_sync(0xffffffffu, is, o), xt = __shfl_up_sync(0xffffffffu, it, o);
+      if (lane >= o) {
+        is += xs;
+        it += xt;
+      }
+    }
+    if (lane == 31) {
+      ws[w] = is;
+      wt[w] = it;
+    }
+    __syncthreads();
+    int os = run_s, ot = run_t;
+    for (int q = 0; q < w; ++q) {
+      os += ws[q];
+      ot += wt[q];
+    }
+    if (p < P) {
+      sub_base[p] = os + is - c;
+      tile_base[p] = ot + it - t;
+      cursor[p] = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) {
+      run_s = os + is;
+      run_t = ot + it;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    sub_base[P] = run_s;
+    tile_base[P] = run_t;
+    *n_tiles = run_t;
+  }
+}
+
+__global__ void k_plan_scatter(int B, int P, const int32_t* __restrict__ prop_of, const int* __restrict__ sub_base,
+                               int* __restrict__ cursor, int* __restrict__ perm) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
+    const int p = prop_of[b];
+    if (p < 0 || p >= P) continue;
+    perm[sub_base[p] + atomicAdd(&cursor[p], 1)] = b;
+  }
+}
+
+// Slot s of tile t: the property whose tiles contain t, and the global row in that slot.
+__global__ void k_plan_rows(int max_tiles, int K, int P, const int* __restrict__ n_tiles,
+                            const int* __restrict__ tile_base, const int* __restrict__ sub_base,
+                            const int* __restrict__ perm, int* __restrict__ tile_prop, int* __restrict__ rowmap) {
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= (long long)max_tiles * TR) return;
+  const int t = (int)(id / TR), sl = (int)(id - (long long)t * TR);
+  if (t >= *n_tiles) {
+    rowmap[id] = -1;
+    if (sl == 0) tile_prop[t] = -1;
+    return;
+  }
+  int lo = 0, hi = P - 1;   // smallest p with tile_base[p + 1] > t
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (tile_base[mid + 1] > t) hi = mid;
+    else lo = mid + 1;
+  }
+  const int p = lo;
+  const long long i = (long long)(t - tile_base[p]) * TR + sl;
+  const long long rows_p = (long long)(sub_base[p + 1] - sub_base[p]) * K;
+  rowmap[id] = i < rows_p ? (int)((long long)perm[sub_base[p] + i / K] * K + i % K) : -1;
+  if (sl == 0) tile_prop[t] = p;
 }
 
 }  // namespace tc
@@ -1230,8 +1221,39 @@ bool tc_supported(const bcrown_net* net) {
   return major == 10 && minor == 3;
 }
 
-size_t tc_workspace_bytes(const bcrown_net* net, int R, bool grad) {
-  return grad ? (size_t)(((R + TR - 1) / TR) * TR) * std::max(net->H, 1) * sizeof(__nv_bfloat16) : 0;
+// Tiles the planner can produce: every property may end in one partly filled tile.
+static long long max_tiles_of(int B, int K, int P) { return ((long long)B * K + TR - 1) / TR + P; }
+
+// Workspace: the row plan (counters, prefix sums, permutation, tile -> property, row map), then,
+// for the gradient, the BF16 stash [tile][H][TR].
+struct TcPlan {
+  int *cnt, *cursor, *sub_base, *tile_base, *n_tiles, *perm, *tile_prop, *rowmap;
+  __nv_bfloat16* stash;
+};
+static size_t carve(char* base, int B, int K, int P, int H, bool grad, TcPlan* out) {
+  const long long T = max_tiles_of(B, K, P);
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> char* {
+    char* p = base ? base + off : nullptr;
+    off += align_up(bytes);
+    return p;
+  };
+  TcPlan pl;
+  pl.cnt = (int*)take((size_t)(P + 1) * 4);
+  pl.cursor = (int*)take((size_t)(P + 1) * 4);
+  pl.sub_base = (int*)take((size_t)(P + 1) * 4);
+  pl.tile_base = (int*)take((size_t)(P + 1) * 4);
+  pl.n_tiles = (int*)take(4);
+  pl.perm = (int*)take((size_t)std::max(B, 1) * 4);
+  pl.tile_prop = (int*)take((size_t)T * 4);
+  pl.rowmap = (int*)take((size_t)T * TR * 4);
+  pl.stash = grad ? (__nv_bfloat16*)take((size_t)T * TR * std::max(H, 1) * sizeof(__nv_bfloat16)) : nullptr;
+  if (out) *out = pl;
+  return off;
+}
+
+size_t tc_workspace_bytes(const bcrown_net* net, int B, int P, bool grad) {
+  return carve(nullptr, B, net->K, P, net->H, grad, nullptr);
 }
 
 static int encode_map(CUtensorMap* m, void* base, int rows, int kp, int box_rows) {
@@ -1303,16 +1325,36 @@ static int tc_prepare(bcrown_net* net, TcNet* t) {
 }
 
 static int tc_launch(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* bt, const Tables& tb, Args& A,
-                     bool grad, cudaStream_t s) {
+                     char* ws, size_t ws_bytes, bool grad, bool plan, cudaStream_t s) {
   TcNet* t = tc_of(net);
   BC_CHECK(tc_prepare(net, t));
-  const int R = bt->B * net->K;
+  const int B = bt->B, K = net->K, P = dom->n_props;
+  const int R = B * K;
+  if (R == 0) return BCROWN_OK;
+  if (!ws || ws_bytes < tc_workspace_bytes(net, B, P, grad))
+    return fail(BCROWN_ERR_OOM, "tensor-core workspace too small");
+  TcPlan pl;
+  carve(ws, B, K, P, net->H, grad, &pl);
+  const long long T = max_tiles_of(B, K, P);
+  if (plan) {
+    BC_CUDA(cudaMemsetAsync(pl.cnt, 0, (size_t)(P + 1) * 4, s));
+    const int gb = (int)std::min<long long>((B + 255) / 256, 4096);
+    k_plan_count<<<gb, 256, 0, s>>>(B, P, bt->prop_of, pl.cnt, net->status);
+    k_plan_scan<<<1, 1024, 0, s>>>(P, K, pl.cnt, pl.cursor, pl.sub_base, pl.tile_base, pl.n_tiles);
+    k_plan_scatter<<<gb, 256, 0, s>>>(B, P, bt->prop_of, pl.sub_base, pl.cursor, pl.perm);
+    k_plan_rows<<<(int)((T * TR + 255) / 256), 256, 0, s>>>((int)T, K, P, pl.n_tiles, pl.tile_base, pl.sub_base,
+                                                           pl.perm, pl.tile_prop, pl.rowmap);
+    g_launches += 4;
+  }
   A.L = net->L;
-  A.K = net->K;
-  A.P = dom->n_props;
+  A.K = K;
+  A.P = P;
   A.H = net->H;
   A.R = R;
-  A.n_tiles = (R + TR - 1) / TR;
+  A.n_tiles = pl.n_tiles;
+  A.tile_prop = pl.tile_prop;
+  A.rowmap = pl.rowmap;
+  A.stash = pl.stash;
   for (int i = 0; i <= net->L && i <= MAXL; ++i) A.d[i] = net->d[i];
   for (int i = 1; i < net->L; ++i) {
     A.hoff[i] = net->hoff[i - 1];
@@ -1332,11 +1374,11 @@ static int tc_launch(bcrown_net* net, const bcrown_domain* dom, const bcrown_bat
   A.n_alpha = bt->n_alpha;
   A.n_beta = bt->n_beta;
   A.status = net->status;
-  if (A.n_tiles == 0) return BCROWN_OK;
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int grid = std::min(A.n_tiles, sms);
+  // one CTA per SM at most; the planned tile count (at most T) is read on the device
+  const int grid = (int)std::min<long long>(T, sms);
   {
     ProfScope ps(net, BCROWN_PROF_FUSED, s);
     if (grad)
@@ -1350,7 +1392,7 @@ static int tc_launch(bcrown_net* net, const bcrown_domain* dom, const bcrown_bat
 }
 
 int tc_bound(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* bt, const Tables& tb, char* ws,
-             size_t ws_bytes, bool grad, const float* alpha, const float* beta, float* lb, float* dalpha,
+             size_t ws_bytes, bool grad, bool plan, const float* alpha, const float* beta, float* lb, float* dalpha,
              float* dbeta, cudaStream_t s) {
   Args A;
   memset(&A, 0, sizeof(A));
@@ -1359,10 +1401,7 @@ int tc_bound(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* bt, 
   A.lb = lb;
   A.dalpha = dalpha;
   A.dbeta = dbeta;
-  A.stash = grad ? reinterpret_cast<__nv_bfloat16*>(ws) : nullptr;
-  if (grad && ws_bytes < tc_workspace_bytes(net, bt->B * net->K, true))
-    return fail(BCROWN_ERR_OOM, "tensor-core stash workspace too small");
-  return tc_launch(net, dom, bt, tb, A, grad, s);
+  return tc_launch(net, dom, bt, tb, A, ws, ws_bytes, grad, plan, s);
 }
 
 void tc_release(const bcrown_net* net) {
