@@ -120,12 +120,9 @@ struct Args {
   int box_fwd[MAXL + 1];
 };
 
-// Every CTA streams the same weights at about the same time; NREP copies of them, CTA b
-// reading copy b % NREP, spread those requests over more L2 lines.
-constexpr int NREP = 4;
 struct Maps {
-  CUtensorMap bwd[NREP][MAXL + 1];   // Wt^(i): [d_{i-1}][Kp(d_i)] bf16, rows = output neurons of the backward
-  CUtensorMap fwd[NREP][MAXL + 1];   // W^(i):  [d_i][Kp(d_{i-1})] bf16, rows = output neurons of the forward
+  CUtensorMap bwd[MAXL + 1];   // Wt^(i): [d_{i-1}][Kp(d_i)] bf16, rows = output neurons of the backward
+  CUtensorMap fwd[MAXL + 1];   // W^(i):  [d_i][Kp(d_{i-1})] bf16, rows = output neurons of the forward
 };
 
 // ------------------------------------------------------------------------------------------
@@ -166,7 +163,8 @@ __device__ __forceinline__ bool mbar_try_sleep(uint64_t* b, uint32_t parity, uin
   return ok != 0;
 }
 // Bounded wait (about 2 s of SM clock); on expiry records a timeout and raises the abort flag.
-__device__ __noinline__ bool mbar_wait(uint64_t* b, uint32_t parity, Smem* sm, int* status) {
+// Inlined: as a called function it cost the single-thread MMA and TMA loops ~0.2 us per wait.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, Smem* sm, int* status) {
   if (mbar_try(b, parity)) return true;
   long long t0 = clock64();
   while (true) {
@@ -450,8 +448,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
           int layer, N, K;
           bool fwd;
           contraction(a, ci, layer, N, K, fwd);
-          const int rep = blockIdx.x % NREP;
-          const CUtensorMap* map = fwd ? &maps.fwd[rep][layer] : &maps.bwd[rep][layer];
+          const CUtensorMap* map = fwd ? &maps.fwd[layer] : &maps.bwd[layer];
           const uint32_t bytes = (uint32_t)(fwd ? a.box_fwd[layer] : a.box_bwd[layer]) * 128u;
           const int nmc = nmc_of(N), nkb = nkb_of(K);
           const bool stream = nkb > NSLOT / 2;   // same order as the MMA issuer
@@ -1303,20 +1300,18 @@ static int tc_prepare(bcrown_net* net, TcNet* t) {
   for (int i = 1; i < net->L; ++i) {
     const LayerDev& l = net->ly[i - 1];
     // backward: rows = d_{i-1} output neurons, K = d_i
-    for (int rep = 0; rep < NREP; ++rep) {
-      __nv_bfloat16* wt = nullptr;
-      int kp = 0;
-      BC_CHECK(padded_bf16(l.Wt, l.d_in, l.d_out, &wt, &kp));
-      t->bufs.push_back(wt);
-      t->box_bwd[i] = MCH;
-      BC_CHECK(encode_map(&t->maps.bwd[rep][i], wt, l.d_in, kp, t->box_bwd[i]));
-      // forward: rows = d_i output neurons, K = d_{i-1}
-      __nv_bfloat16* wf = nullptr;
-      BC_CHECK(padded_bf16(l.W, l.d_out, l.d_in, &wf, &kp));
-      t->bufs.push_back(wf);
-      t->box_fwd[i] = MCH;
-      BC_CHECK(encode_map(&t->maps.fwd[rep][i], wf, l.d_out, kp, t->box_fwd[i]));
-    }
+    __nv_bfloat16* wt = nullptr;
+    int kp = 0;
+    BC_CHECK(padded_bf16(l.Wt, l.d_in, l.d_out, &wt, &kp));
+    t->bufs.push_back(wt);
+    t->box_bwd[i] = MCH;
+    BC_CHECK(encode_map(&t->maps.bwd[i], wt, l.d_in, kp, t->box_bwd[i]));
+    // forward: rows = d_i output neurons, K = d_{i-1}
+    __nv_bfloat16* wf = nullptr;
+    BC_CHECK(padded_bf16(l.W, l.d_out, l.d_in, &wf, &kp));
+    t->bufs.push_back(wf);
+    t->box_fwd[i] = MCH;
+    BC_CHECK(encode_map(&t->maps.fwd[i], wf, l.d_out, kp, t->box_fwd[i]));
   }
   BC_CUDA(cudaFuncSetAttribute(k_fused<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem) + 1024));
   BC_CUDA(cudaFuncSetAttribute(k_fused<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem) + 1024));
