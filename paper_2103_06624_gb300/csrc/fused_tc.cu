@@ -53,6 +53,7 @@ constexpr int MAXL = 9;
 constexpr int MAX_D0 = 1024;
 constexpr int SIGN_WORDS = MAX_D0 / 32;
 constexpr int MAX_MASK_WORDS = 48;       // sum over hidden layers of ceil(d_i/32)
+static_assert(MAX_MASK_WORDS % 8 == 0, "set-up step 3 splits the mask words over 8 threads per row");
 constexpr int MAX_H = MAX_MASK_WORDS * 32;  // hidden neurons whose tables a tile stages
 constexpr int MAX_HIDDEN = 256;
 
@@ -623,6 +624,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
         (&sm->smask[0][0])[x] = 0u;
         (&sm->sneg[0][0])[x] = 0u;
       }
+      if (etid < a.mask_words) sm->wrows[etid] = 0ull;
       if (!epi_sync(sm, eseq, a.status)) {
         ok = false;
         break;
@@ -694,15 +696,33 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
         ok = false;
         break;
       }
-      // ---------------- step 3: per-row split counts before each mask word, rows per word
-      if (etid < TR) {
-        int run = 0;
-        for (int w = 0; w < a.mask_words; ++w) {
-          const uint32_t m = sm->smask[w][etid];
-          sm->wfirst[w][etid] = (uint8_t)run;
-          run += __popc(m);
-          const unsigned rows = __ballot_sync(0xffffffffu, m != 0u);
-          if (lane == 0) reinterpret_cast<uint32_t*>(&sm->wrows[w])[warp] = rows;   // rows 32 warp ..
+      // ---------------- step 3: per-row split counts before each mask word (a prefix over the
+      // row's 8 threads, 6 words each) and the rows with a split in each word (shared atomics)
+      {
+        const int row = etid >> 3, part = etid & 7;
+        constexpr int WPT = MAX_MASK_WORDS / 8;
+        int cw[WPT];
+        int loc = 0;
+#pragma unroll
+        for (int u = 0; u < WPT; ++u) {
+          const int w = part * WPT + u;
+          const uint32_t m = w < a.mask_words ? sm->smask[w][row] : 0u;
+          cw[u] = __popc(m);
+          loc += cw[u];
+          if (m) atomicOr(&sm->wrows[w], 1ull << row);
+        }
+        int incl = loc;
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, incl, o, 8);
+          if (part >= o) incl += y;
+        }
+        int run = incl - loc;
+#pragma unroll
+        for (int u = 0; u < WPT; ++u) {
+          const int w = part * WPT + u;
+          if (w < a.mask_words) sm->wfirst[w][row] = (uint8_t)run;
+          run += cw[u];
         }
       }
       if (!epi_sync(sm, eseq, a.status)) {
