@@ -223,11 +223,18 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
 __host__ __device__ constexpr uint32_t idesc_bf16(int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(MCH >> 4) << 24);
 }
-__device__ __forceinline__ void umma(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+// One 64-wide K block: four MMAs of K = 16.  Descriptors of consecutive 16-element K steps
+// differ by 32 bytes in the start address (field unit 16 bytes: +2); `acc` = 0 starts the
+// accumulator with the first MMA.
+__device__ __forceinline__ void umma_kblock(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
   asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
-          dtmem),
-      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %4, 0;\n\tsetp.eq.b32 q, 0, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %5, %6, %3, q;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %7, %8, %3, q;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %9, %10, %3, q;\n\t}" ::"r"(dtmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc), "l"(ad + 2), "l"(bd + 2), "l"(ad + 4), "l"(bd + 4), "l"(ad + 6),
+      "l"(bd + 6)
       : "memory");
 }
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
@@ -256,6 +263,21 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Split form of tmem_ld8: the load, then the wait.  The wait names the registers as in-out
+// operands, so no use of them can be scheduled before it.
+__device__ __forceinline__ void tmem_ld8_issue(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_wait8(uint32_t (&r)[8]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7])
+               :
+               : "memory");
 }
 
 // Loads issued where they are written (volatile asm keeps them ahead of the barrier waits that
@@ -513,9 +535,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
                 const uint32_t dt = tmem + (uint32_t)(((accseq + mc) % NACC) * TR);
                 const uint32_t wa = su32(sm->w[st]);
                 const uint32_t ba = su32(sm->act[slot]);
-#pragma unroll
-                for (int ks = 0; ks < KBLK / 16; ++ks)
-                  umma(dt, sdesc(wa + ks * 32), sdesc(ba + ks * 32), idesc, (kb | ks) != 0 ? 1u : 0u);
+                umma_kblock(dt, sdesc(wa), sdesc(ba), idesc, kb != 0 ? 1u : 0u);
                 umma_commit(&sm->w_empty[st]);
                 ++wseq;
               }
@@ -551,9 +571,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
               tc_fence_after();
               const uint32_t wa = su32(sm->w[st]);
               const uint32_t ba = su32(sm->act[slot]);
-#pragma unroll
-              for (int ks = 0; ks < KBLK / 16; ++ks)
-                umma(dt, sdesc(wa + ks * 32), sdesc(ba + ks * 32), idesc, (kb | ks) != 0 ? 1u : 0u);
+              umma_kblock(dt, sdesc(wa), sdesc(ba), idesc, kb != 0 ? 1u : 0u);
               umma_commit(&sm->w_empty[st]);
               ++wseq;
               if (mc == nmc - 1) umma_commit(&sm->act_empty[slot]);
@@ -887,26 +905,36 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
             break;
           }
           const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * TR + r0);
+          if (top) {
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            float v[8];
-            if (top) {
+            for (int h = 0; h < 2; ++h) {
               // A^(L-1) = Wbar rows of the rows' specifications
+              float v[8];
 #pragma unroll
               for (int c8 = 0; c8 < 8; ++c8) {
                 const int c = 8 * h + c8;
                 v[c8] = ldg_f32(a.Wbar + (size_t)sm->spec[r0 + c] * N + j, jin && ((vbits >> c) & 1u));
               }
-            } else {
-              tmem_ld8(tbase + 8 * h, v);
-              if (h == 1) {
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&sm->acc_empty[buf]);
-                ++accseq;
-              }
+              relax8(h, v);
             }
-            relax8(h, v);
+          } else {
+            // rows r0..r0+7, then r0+8..r0+15: the second load runs under the first half's work
+            uint32_t u0[8], u1[8];
+            tmem_ld8_issue(tbase, u0);
+            tmem_wait8(u0);
+            tmem_ld8_issue(tbase + 8, u1);
+            float v[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = __uint_as_float(u0[e]);
+            relax8(0, v);
+            tmem_wait8(u1);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm->acc_empty[buf]);
+            ++accseq;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = __uint_as_float(u1[e]);
+            relax8(1, v);
           }
           // each K block is complete once its 8 writer warps arrived
           if (writer) {
@@ -1026,16 +1054,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
           uint8_t* aslot = sm->act[slot] + r0 * 128 + ((kk & 7) << 1);
           const uint32_t kx = (uint32_t)(kk >> 3) << 4;
           const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * TR + r0);
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            float vz[8];
-            tmem_ld8(tbase + 8 * h, vz);
-            if (h == 1) {
-              tc_fence_before();
-              __syncwarp();
-              if (lane == 0) mbar_arrive(&sm->acc_empty[buf]);
-              ++accseq;
-            }
+          // rows r0 + 8h .. r0 + 8h + 7: zhat, gradients, next operand
+          auto fwd8 = [&](const int h, const uint32_t (&u)[8]) {
             const uint4 sw = h == 0 ? s0 : s1;
             const uint32_t swv[4] = {sw.x, sw.y, sw.z, sw.w};
 #pragma unroll
@@ -1044,7 +1064,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
               const int row = r0 + c;
               const bool rin = (vbits >> c) & 1u;
               const float A = __uint_as_float((c8 & 1) ? (swv[c8 >> 1] & 0xFFFF0000u) : (swv[c8 >> 1] << 16));
-              const float z = vz[c8] + bj;
+              const float z = __uint_as_float(u[c8]) + bj;
               const bool pos = A >= 0.f;
               float D = pos ? __saturatef(al[c] + apos) : dneg;
               float lm = pos ? 0.f : lneg;
@@ -1065,7 +1085,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
                 *reinterpret_cast<__nv_bfloat16*>(aslot + (8 * h + c8) * 128 + (kx ^ (uint32_t)(c8 << 4))) =
                     __float2bfloat16_rn(hv);
             }
-          }
+          };
+          uint32_t u0[8], u1[8];
+          tmem_ld8_issue(tbase, u0);
+          tmem_wait8(u0);
+          tmem_ld8_issue(tbase + 8, u1);
+          fwd8(0, u0);
+          tmem_wait8(u1);
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&sm->acc_empty[buf]);
+          ++accseq;
+          fwd8(1, u1);
           if (writer) {
             fence_proxy_async();
             __syncwarp();
