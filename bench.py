@@ -39,6 +39,7 @@ def parse():
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
     ap.add_argument("--subdomains", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp32-form", action="store_true", help="skip timing the plain FP32 form beside BF16")
     ap.add_argument("--cpu-sample", type=int, default=640, help="subdomains timed on the oracle (about 10-20 s)")
     return ap.parse_args()
 
@@ -248,6 +249,39 @@ def main():
     # ---------------------------------------------------------------- end to end (host buffers)
     e2e = measure_e2e(args, bc, torch, net, dom, hbatch, a0, b0, cfg, pb, world)
 
+    # ---------------------------------------------------------------- the plain FP32 form, same GPU
+    # Same workload and step (20 iterations + certifying pass) with FP32 SIMT contractions; the
+    # certified bounds of both forms are compared to state the tightness at which they are equal.
+    lb_main = lb.clone()
+    forms = None
+    if prec == bc.BF16 and not args.no_fp32_form:
+        cfg32 = bc.OptCfg(precision=bc.FP32, certify=True)
+        lb32 = torch.empty_like(lb)
+
+        def step32():
+            alpha.copy_(a_init)
+            beta.copy_(b_init)
+            bc.optimize(net, dom, db, alpha, beta, cfg32, out=lb32)
+
+        step32()
+        torch.cuda.synchronize()
+        n32 = 2
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(0.0)
+        e0.record(stream)
+        for _ in range(n32):
+            step32()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms32 = e0.elapsed_time(e1) / n32
+        d = (lb_main - lb32).double().cpu().numpy()
+        forms = {"fp32": {"value": hbatch.B * world / (ms32 / 1e3), "unit": UNIT, "ms_per_step": ms32,
+                          "steps": n32},
+                 "bf16_over_fp32": (ms32 / ms_per_step),
+                 "certified_lb_bf16_minus_fp32": {"mean": float(d.mean()), "min": float(d.min()),
+                                                  "max": float(d.max())},
+                 "mean_certified_lb": {"bf16": float(lb_main.double().mean()), "fp32": float(lb32.double().mean())}}
+
     # ---------------------------------------------------------------- roofline of the dominant kernel
     widths = pb.widths
     rows = hbatch.B * pb.K
@@ -308,7 +342,7 @@ def main():
                        "unstable_neurons": U, "iters": cfg.iters, "precision": args.precision if prec == bc.BF16 else "fp32",
                        "l2": "flushed (256 MB write between timed steps)"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clk,
+            "clocks": clk, "forms": forms,
         }
         print(json.dumps(line))
     if world > 1:

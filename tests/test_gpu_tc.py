@@ -130,3 +130,35 @@ def test_bf16_optimize_is_certified_and_tight(which):
     gain16 = np.mean(res[bc.BF16] - init)
     print("mean improvement over the initial bound: FP32 %.4f, BF16 %.4f" % (gain32, gain16))
     assert gain16 >= 0.8 * gain32
+
+
+def test_batching_64_properties_sampled():
+    """The batching workload: 64 properties on the 784-256x6-10 net with log-uniform 16-4096
+    subdomains each (about 47k subdomains, 420k rows, tree depths up to 20) in one launch per
+    call.  Sampled rows against the oracle, BF16 and FP32; then a short BF16 optimisation whose
+    certified bounds stay below the exact bounds at the returned alpha, beta."""
+    pb = wl.problem_mlp_784(n_props=64)
+    onet, props, unst = oracle_setup(pb)
+    counts = wl.loguniform_counts(64, 16, 4096, 0)
+    batch = wl.tree_batch(pb, unst, list(counts), 20, 4)
+    a, b = wl.random_alpha_beta(batch, 6, 1.0)
+    net, dom, db = _gpu(pb, props, batch)
+    U = np.array([len(x) for x in unst])
+    rng = np.random.default_rng(0)
+    idx = np.sort(rng.choice(batch.B, 24, replace=False))
+    sub, sa, sb = repack(pb, batch, U, idx, a, b)
+    ref = O.bound(onet, props, sub, sa, sb).reshape(len(idx), pb.K)
+    rows = (idx[:, None] * pb.K + np.arange(pb.K)[None, :])
+    lb16 = bc.bound(net, dom, db, _t(a), _t(b), bc.BF16).cpu().numpy()
+    assert bc.status(net) == 0
+    assert np.all(np.isfinite(lb16))
+    assert (np.abs(lb16[rows] - ref) / _scale(ref)).max() <= BF16_TOL
+    lb32 = bc.bound(net, dom, db, _t(a), _t(b), bc.FP32).cpu().numpy()
+    assert np.max(rel_err(lb32[rows], ref)) <= RTOL
+    a0, b0 = wl.initial_alpha_beta(batch)
+    at, bt = _t(a0), _t(b0)
+    lbc = bc.optimize(net, dom, db, at, bt, bc.OptCfg(iters=3, precision=bc.BF16, certify=True)).cpu().numpy()
+    assert bc.status(net) == 0
+    _, ra, rb = repack(pb, batch, U, idx, at.cpu().numpy(), bt.cpu().numpy())
+    ref_opt = O.bound(onet, props, sub, ra, rb).reshape(len(idx), pb.K)
+    assert np.all(lbc[rows] <= ref_opt + 1e-12 * np.abs(ref_opt))
