@@ -146,53 +146,84 @@ __global__ void __launch_bounds__(256) k_init_top(RowsCtx c, int dtop, const flo
 // ----------------------------------------------------------------------------------------
 // Relaxation + beta shift + bias (Eq. definition_D, definition_lowerb, definition_A):
 //   Lambda_j = A_j D_j + beta_j S_jj ;  c += Lambda_j b_j + A_j lambda_j
-// One block per row.  CERT: outward chord constants, FP64 round-down c, error terms.
+// One warp per row (RELAX_ROWS rows per block): the row's splits of this layer are compacted
+// into shared memory by ballots, neurons are strided over the lanes, sums are warp reductions.
+// CERT: outward chord constants (from the tables), c summed rounded down, error terms rounded up.
 // ----------------------------------------------------------------------------------------
+constexpr int RELAX_ROWS = 8;
 template <bool CERT>
-__global__ void __launch_bounds__(256) k_relax(RowsCtx c, int layer, int d, long long hoff,
-                                               const float* __restrict__ Ain, float* __restrict__ Lam,
-                                               const float* __restrict__ bias, const float* __restrict__ alpha,
-                                               int64_t n_alpha, const float* __restrict__ beta, int64_t n_beta,
-                                               float* __restrict__ cf, double* __restrict__ cd,
-                                               double* __restrict__ E, const float* __restrict__ wm,
-                                               double gamma) {
-  __shared__ SplitSlot slots[BCROWN_MAX_SPLITS];
-  __shared__ int n_slots;
-  __shared__ float shf[32];
-  int rl = blockIdx.x;
+__global__ void __launch_bounds__(32 * RELAX_ROWS) k_relax(RowsCtx c, int layer, int d, long long hoff,
+                                                          const float* __restrict__ Ain, float* __restrict__ Lam,
+                                                          const float* __restrict__ bias,
+                                                          const float* __restrict__ alpha, int64_t n_alpha,
+                                                          const float* __restrict__ beta, int64_t n_beta,
+                                                          float* __restrict__ cf, double* __restrict__ cd,
+                                                          double* __restrict__ E, const float* __restrict__ wm,
+                                                          double gamma) {
+  __shared__ SplitSlot slots[RELAX_ROWS][BCROWN_MAX_SPLITS];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rl = blockIdx.x * RELAX_ROWS + w;
+  if (rl >= c.R) return;   // whole warps only; nothing below synchronises the block
   int b, k, p;
   bool ok = row_prop(c, rl, &b, &k, &p);
   if (!ok) p = 0;
-  int ns = stage_splits(c, b, layer, d, slots, &n_slots);
   int cnt = c.bt.split_cnt[b];
-  int Up = c.tb.U[p];
-  long long abase = c.bt.alpha_off[b] + (long long)k * Up;
-  long long bbase = (long long)c.bt.split_off[b] * c.K + (long long)k * cnt;
+  const int off = c.bt.split_off[b];
+  if (cnt < 0 || cnt > BCROWN_MAX_SPLITS) {
+    if (lane == 0) flag(c.status, BCROWN_ERR_ARG);
+    cnt = 0;
+  }
+  // this layer's splits of the row, in list order
+  int ns = 0;
+  for (int t0 = 0; t0 < cnt; t0 += 32) {
+    const int t = t0 + lane;
+    bool keep = false;
+    int j = 0, sg = 0;
+    if (t < cnt) {
+      const int ly = c.bt.split_layer[off + t];
+      j = (int)c.bt.split_idx[off + t];
+      sg = c.bt.split_sign[off + t];
+      if (sg != -1 && sg != 1) flag(c.status, BCROWN_ERR_ARG);
+      else if (ly == layer) {
+        if (j < 0 || j >= d) flag(c.status, BCROWN_ERR_ARG);
+        else keep = true;
+      }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (keep) slots[w][ns + __popc(m & ((1u << lane) - 1u))] = SplitSlot{j, sg, t};
+    ns += __popc(m);
+  }
+  __syncwarp();
+  const SplitSlot* sl = slots[w];
+  const int Up = c.tb.U[p];
+  const long long abase = c.bt.alpha_off[b] + (long long)k * Up;
+  const long long bbase = (long long)off * c.K + (long long)k * cnt;
   const float* a_row = Ain + (size_t)rl * d;
   float* lam_row = Lam + (size_t)rl * d;
   // CERT: acc is a lower bound of sum_j Lambda_j b_j + A_j lambda_j (every operation rounded
   // down); e1, e2 are upper bounds (rounded up) of the error terms below.
   float acc = 0.f, e1 = 0.f, e2 = 0.f;
-  for (int j = threadIdx.x; j < d; j += blockDim.x) {
-    float a = a_row[j];
-    size_t n = (size_t)p * c.tb.H + hoff + j;
+#pragma unroll 4
+  for (int j = lane; j < d; j += 32) {
+    const float a = a_row[j];
+    const size_t n = (size_t)p * c.tb.H + hoff + j;
     int s = 0;
     float bet = 0.f;
     for (int q = 0; q < ns; ++q)
-      if (slots[q].idx == j) {
-        s = slots[q].sign;
-        long long bi = bbase + slots[q].t;
+      if (sl[q].idx == j) {
+        s = sl[q].sign;
+        const long long bi = bbase + sl[q].t;
         if (bi >= 0 && bi < n_beta) bet = fmaxf(beta[bi], 0.f);
         else flag(c.status, BCROWN_ERR_ARG);
       }
     float D = 0.f, lm = 0.f;
-    uint8_t code = c.tb.code[n];
+    const uint8_t code = c.tb.code[n];
     if (s == -1) D = 1.f;
     else if (s == 1) D = 0.f;
     else if (code == CODE_ACTIVE) D = 1.f;
     else if (code == CODE_INACTIVE) D = 0.f;
     else if (a >= 0.f) {
-      long long ai = abase + c.tb.rank[n];
+      const long long ai = abase + c.tb.rank[n];
       if (ai < 0 || ai >= n_alpha) {
         flag(c.status, BCROWN_ERR_ARG);
         D = 0.f;
@@ -204,17 +235,17 @@ __global__ void __launch_bounds__(256) k_relax(RowsCtx c, int layer, int d, long
       D = c.tb.slope[n];
       lm = c.tb.icpt[n];
     }
-    float L = fmaf(a, D, bet * (float)s);
+    const float L = fmaf(a, D, bet * (float)s);
     lam_row[j] = L;
-    float bj = bias[j];
+    const float bj = bias[j];
     if (CERT) {
       acc = __fadd_rd(acc, __fadd_rd(__fmul_rd(L, bj), __fmul_rd(a, lm)));
-      bool exact = (s == 0) && (D == 0.f || D == 1.f);
+      const bool exact = (s == 0) && (D == 0.f || D == 1.f);
       if (!exact) {
         // Lambda_j was rounded once: |error| <= 2^-23 |Lambda_j| (+ an underflow margin),
         // acting on |z_j| <= max(|l_j|, |u_j|)
-        float zmax = fmaxf(fabsf(c.l[n]), fabsf(c.u[n]));
-        float er = __fmaf_ru(fabsf(L), 0x1p-23f, 0x1p-140f);
+        const float zmax = fmaxf(fabsf(c.l[n]), fabsf(c.u[n]));
+        const float er = __fmaf_ru(fabsf(L), 0x1p-23f, 0x1p-140f);
         e1 = __fadd_ru(e1, __fmul_ru(er, zmax));
       }
       e2 = __fadd_ru(e2, __fmul_ru(fabsf(L), wm[n]));
@@ -223,16 +254,18 @@ __global__ void __launch_bounds__(256) k_relax(RowsCtx c, int layer, int d, long
     }
   }
   if (CERT) {
-    acc = block_fsum<1>(acc, shf);
-    e1 = block_fsum<2>(e1, shf);
-    e2 = block_fsum<2>(e2, shf);
-    if (threadIdx.x == 0) {
+    for (int o = 16; o > 0; o >>= 1) {
+      acc = __fadd_rd(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+      e1 = __fadd_ru(e1, __shfl_xor_sync(0xffffffffu, e1, o));
+      e2 = __fadd_ru(e2, __shfl_xor_sync(0xffffffffu, e2, o));
+    }
+    if (lane == 0) {
       cd[rl] = __dadd_rd(cd[rl], (double)acc);
       E[rl] = __dadd_ru(E[rl], __dadd_ru((double)e1, __dmul_ru(gamma, (double)e2)));
     }
   } else {
-    acc = block_sum(acc, shf);
-    if (threadIdx.x == 0) cf[rl] += acc;
+    acc = warp_sum(acc);
+    if (lane == 0) cf[rl] += acc;
   }
 }
 
@@ -243,37 +276,40 @@ __global__ void __launch_bounds__(256) k_relax(RowsCtx c, int layer, int d, long
 __global__ void __launch_bounds__(256) k_sgemm(int M, int N, int K, const float* __restrict__ A, int lda,
                                                const float* __restrict__ B, int ldb, float* __restrict__ C,
                                                int ldc, const float* __restrict__ bias) {
-  constexpr int BM = 128, BN = 128, BK = 8;
-  __shared__ float As[2][BK][BM + 4];
-  __shared__ float Bs[2][BK][BN + 4];
+  constexpr int BM = 128, BN = 128, BK = 16;
+  constexpr int LPT = BM * BK / 256;   // elements of each operand a thread stages per k step
+  __shared__ __align__(16) float As[2][BK][BM + 4];
+  __shared__ __align__(16) float Bs[2][BK][BN + 4];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  // thread (tx, ty): rows 4ty..4ty+3 and 64+4ty..64+4ty+3, columns 4tx.. and 64+4tx.. of the
+  // tile, so its shared-memory operands are two 16-byte loads per matrix per k
   float acc[8][8];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
 
-  float ra[4], rb[4];
+  float ra[LPT], rb[LPT];
   auto load_regs = [&](int k0) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < LPT; ++q) {
       int e = tid + q * 256;
-      int m = e >> 3, kk = e & 7;
+      int m = e / BK, kk = e % BK;
       int gm = m0 + m, gk = k0 + kk;
       ra[q] = (gm < M && gk < K) ? A[(size_t)gm * lda + gk] : 0.f;
-      int kb = e >> 7, n = e & 127;
+      int kb = e / BN, n = e % BN;
       int gk2 = k0 + kb, gn = n0 + n;
       rb[q] = (gk2 < K && gn < N) ? B[(size_t)gk2 * ldb + gn] : 0.f;
     }
   };
   auto store_smem = [&](int buf) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < LPT; ++q) {
       int e = tid + q * 256;
-      As[buf][e & 7][e >> 3] = ra[q];
-      Bs[buf][e >> 7][e & 127] = rb[q];
+      As[buf][e % BK][e / BK] = ra[q];
+      Bs[buf][e / BN][e % BN] = rb[q];
     }
   };
   int nk = (K + BK - 1) / BK;
@@ -285,11 +321,12 @@ __global__ void __launch_bounds__(256) k_sgemm(int M, int N, int K, const float*
     if (t + 1 < nk) load_regs((t + 1) * BK);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      float av[8], bv[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) av[i] = As[buf][kk][ty + 16 * i];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) bv[j] = Bs[buf][kk][tx + 16 * j];
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][4 * ty]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][64 + 4 * ty]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][4 * tx]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][64 + 4 * tx]);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
       for (int i = 0; i < 8; ++i)
 #pragma unroll
@@ -300,11 +337,11 @@ __global__ void __launch_bounds__(256) k_sgemm(int M, int N, int K, const float*
   }
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
-    int gm = m0 + ty + 16 * i;
+    int gm = m0 + (i < 4 ? 4 * ty + i : 64 + 4 * ty + i - 4);
     if (gm >= M) continue;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      int gn = n0 + tx + 16 * j;
+      int gn = n0 + (j < 4 ? 4 * tx + j : 64 + 4 * tx + j - 4);
       if (gn < N) C[(size_t)gm * ldc + gn] = acc[i][j] + (bias ? bias[gn] : 0.f);
     }
   }
@@ -854,9 +891,9 @@ void launch_relax(bool cert, const RowsCtx& c, int layer, int d, long long hoff,
                   double* cd, double* E, const float* wm, double gamma, cudaStream_t s) {
   if (c.R <= 0) return;
   if (cert)
-    { k_relax<true><<<c.R, 256, 0, s>>>(c, layer, d, hoff, Ain, Lam, bias, alpha, n_alpha, beta, n_beta, cf, cd, E, wm, gamma); ++g_launches; }
+    { k_relax<true><<<(c.R + RELAX_ROWS - 1) / RELAX_ROWS, 32 * RELAX_ROWS, 0, s>>>(c, layer, d, hoff, Ain, Lam, bias, alpha, n_alpha, beta, n_beta, cf, cd, E, wm, gamma); ++g_launches; }
   else
-    { k_relax<false><<<c.R, 256, 0, s>>>(c, layer, d, hoff, Ain, Lam, bias, alpha, n_alpha, beta, n_beta, cf, cd, E, wm, gamma); ++g_launches; }
+    { k_relax<false><<<(c.R + RELAX_ROWS - 1) / RELAX_ROWS, 32 * RELAX_ROWS, 0, s>>>(c, layer, d, hoff, Ain, Lam, bias, alpha, n_alpha, beta, n_beta, cf, cd, E, wm, gamma); ++g_launches; }
 }
 
 void launch_sgemm(int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C, int ldc,
