@@ -638,38 +638,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
         const unsigned vb = __ballot_sync(0xffffffffu, v != 0);   // warps 0 and 1
         if (lane == 0) reinterpret_cast<uint32_t*>(&sm->vrows)[warp] = vb;
       }
-      for (int x = etid; x < a.mask_words * TR; x += NEPI * 32) {
-        (&sm->smask[0][0])[x] = 0u;
-        (&sm->sneg[0][0])[x] = 0u;
-      }
-      if (etid < a.mask_words) sm->wrows[etid] = 0ull;
-      if (!epi_sync(sm, eseq, a.status)) {
-        ok = false;
-        break;
-      }
-      // ---------------- step 2: split masks (8 threads per row); the property's tables and box
-      int ent[BCROWN_MAX_SPLITS / 8];   // this thread's split entries: mask word << 5 | bit, or -1
       {
-        const int row = etid >> 3, e0 = etid & 7;
-        const int cnt = sm->scnt[row], off = sm->soff[row];
-#pragma unroll
-        for (int m = 0; m < BCROWN_MAX_SPLITS / 8; ++m) {
-          const int e = e0 + 8 * m;
-          ent[m] = -1;
-          if (e < cnt) {
-            const int ly = a.bt.split_layer[off + e];
-            const int j = (int)a.bt.split_idx[off + e];
-            const int s = a.bt.split_sign[off + e];
-            if (ly < 1 || ly > a.L - 1 || j < 0 || j >= a.d[ly] || (s != 1 && s != -1)) {
-              atomicCAS(a.status, 0, BCROWN_ERR_ARG);
-            } else {
-              const int wd = a.woff[ly] + (j >> 5);
-              atomicOr(&sm->smask[wd][row], 1u << (j & 31));
-              if (s == 1) atomicOr(&sm->sneg[wd][row], 1u << (j & 31));
-              ent[m] = (wd << 5) | (j & 31);
-            }
-          }
-        }
+        // the property's per-neuron tables and input box
         const int pp = (p >= 0 && p < a.P) ? p : 0;
         // all loads first, then the stores (3 neurons and 2 inputs per thread at most)
         constexpr int NT = (MAX_H + NEPI * 32 - 1) / (NEPI * 32), NX = (MAX_D0 + NEPI * 32 - 1) / (NEPI * 32);
@@ -707,6 +677,45 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
           if (m < a.d[0]) {
             sm->sxlo[m] = xl[u];
             sm->sxhi[m] = xh[u];
+          }
+        }
+      }
+      for (int x = etid; x < a.mask_words * TR; x += NEPI * 32) {
+        (&sm->smask[0][0])[x] = 0u;
+        (&sm->sneg[0][0])[x] = 0u;
+      }
+      if (etid < a.mask_words) sm->wrows[etid] = 0ull;
+      if (!epi_sync(sm, eseq, a.status)) {
+        ok = false;
+        break;
+      }
+      // ---------------- step 2: split masks (8 threads per row) and the splits' beta
+      int ent[BCROWN_MAX_SPLITS / 8];   // this thread's split entries: mask word << 5 | bit, or -1
+      float bv[BCROWN_MAX_SPLITS / 8];  // and their beta (loaded now, stored in step 4)
+      {
+        const int row = etid >> 3, e0 = etid & 7;
+        const int cnt = sm->scnt[row], off = sm->soff[row];
+#pragma unroll
+        for (int m = 0; m < BCROWN_MAX_SPLITS / 8; ++m) {
+          const long long bi = sm->bbase[row] + e0 + 8 * m;
+          bv[m] = ldg_f32(a.beta + bi, e0 + 8 * m < cnt && bi >= 0 && bi < a.n_beta);
+        }
+#pragma unroll
+        for (int m = 0; m < BCROWN_MAX_SPLITS / 8; ++m) {
+          const int e = e0 + 8 * m;
+          ent[m] = -1;
+          if (e < cnt) {
+            const int ly = a.bt.split_layer[off + e];
+            const int j = (int)a.bt.split_idx[off + e];
+            const int s = a.bt.split_sign[off + e];
+            if (ly < 1 || ly > a.L - 1 || j < 0 || j >= a.d[ly] || (s != 1 && s != -1)) {
+              atomicCAS(a.status, 0, BCROWN_ERR_ARG);
+            } else {
+              const int wd = a.woff[ly] + (j >> 5);
+              atomicOr(&sm->smask[wd][row], 1u << (j & 31));
+              if (s == 1) atomicOr(&sm->sneg[wd][row], 1u << (j & 31));
+              ent[m] = (wd << 5) | (j & 31);
+            }
           }
         }
       }
@@ -750,12 +759,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
       // ---------------- step 4: each split's slot in (word, bit) order, its list position and beta
       {
         const int row = etid >> 3, e0 = etid & 7;
-        float bv[BCROWN_MAX_SPLITS / 8];
-#pragma unroll
-        for (int m = 0; m < BCROWN_MAX_SPLITS / 8; ++m) {
-          const long long bi = sm->bbase[row] + e0 + 8 * m;
-          bv[m] = ldg_f32(a.beta + bi, ent[m] >= 0 && bi >= 0 && bi < a.n_beta);
-        }
 #pragma unroll
         for (int m = 0; m < BCROWN_MAX_SPLITS / 8; ++m) {
           if (ent[m] >= 0) {
