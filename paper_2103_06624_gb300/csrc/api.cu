@@ -296,9 +296,11 @@ extern "C" int bcrown_optimize(bcrown_net* net, const bcrown_domain* dom, const 
   if (cert) build_wm(net, dom, pl, s);
   if (na) {
     BC_CUDA(cudaMemcpyAsync(pl.a_cur, alpha, na * 4, cudaMemcpyDeviceToDevice, s));
-    BC_CUDA(cudaMemsetAsync(pl.ma, 0, na * 4, s));
-    BC_CUDA(cudaMemsetAsync(pl.va, 0, na * 4, s));
-    BC_CUDA(cudaMemsetAsync(pl.ga, 0, na * 4, s));
+    // the BF16 path keeps alpha's gradient and moments in BF16 (the first half of each buffer)
+    const size_t st = (cfg->precision == BCROWN_BF16 && tc_supported(net)) ? 2 : 4;
+    BC_CUDA(cudaMemsetAsync(pl.ma, 0, na * st, s));
+    BC_CUDA(cudaMemsetAsync(pl.va, 0, na * st, s));
+    BC_CUDA(cudaMemsetAsync(pl.ga, 0, na * st, s));
   }
   if (nb) {
     BC_CUDA(cudaMemcpyAsync(pl.b_cur, beta, nb * 4, cudaMemcpyDeviceToDevice, s));
@@ -308,10 +310,23 @@ extern "C" int bcrown_optimize(bcrown_net* net, const bcrown_domain* dom, const 
   }
   launch_fill(pl.best_lb, R, -INFINITY, s);
   BatchView bv = view_of(batch);
+  const bool fused16 = cfg->precision == BCROWN_BF16 && tc_supported(net);
   for (int t = 0; t < cfg->iters; ++t) {
     float fac = std::pow(cfg->decay, (float)t);
     float bc1 = 1.f - std::pow(cfg->adam_beta1, (float)(t + 1));
     float bc2 = 1.f - std::pow(cfg->adam_beta2, (float)(t + 1));
+    if (fused16) {
+      // BF16 path: gradient and Adam moments of alpha in BF16 (the FP32 buffers hold them)
+      __nv_bfloat16* ga16 = reinterpret_cast<__nv_bfloat16*>(pl.ga);
+      BC_CHECK(tc_bound(net, dom, batch, pl.tb, pl.tc_ws, pl.tc_ws_bytes, true, t == 0, pl.a_cur, pl.b_cur, pl.lb_t,
+                        nullptr, pl.gb, s, ga16));
+      ProfScope ps(net, BCROWN_PROF_ADAM, s);
+      launch_adam16(R, net->K, bv, pl.U, dom->n_props, pl.lb_t, pl.best_lb, pl.a_cur, alpha, ga16,
+                    reinterpret_cast<__nv_bfloat16*>(pl.ma), reinterpret_cast<__nv_bfloat16*>(pl.va), pl.b_cur, beta,
+                    pl.gb, pl.mb, pl.vb, cfg->lr_alpha * fac, cfg->lr_beta * fac, cfg->adam_beta1, cfg->adam_beta2,
+                    cfg->adam_eps, bc1, bc2, na, nb, s);
+      continue;
+    }
     BC_CHECK(run_bound(net, dom, batch, pl, cfg->precision, true, pl.a_cur, pl.b_cur, pl.lb_t, pl.ga, pl.gb, s,
                        t == 0));
     ProfScope ps(net, BCROWN_PROF_ADAM, s);

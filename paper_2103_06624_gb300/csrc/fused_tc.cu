@@ -114,6 +114,7 @@ struct Args {
   int64_t n_alpha, n_beta;
   float* lb;
   float* dalpha;
+  __nv_bfloat16* dalpha16;            // MODE 2: dlb/dalpha rounded to BF16 (optimiser input)
   float* dbeta;
   __nv_bfloat16* stash;               // [tile][H][TR]: A^(i) of the backward pass, per neuron
   int* status;
@@ -420,7 +421,8 @@ __device__ __forceinline__ int split_slot(const Smem* sm, int row, int w, int bi
 // ------------------------------------------------------------------------------------------
 // The kernel
 // ------------------------------------------------------------------------------------------
-// MODE 0: bound only; MODE 1: bound and gradient (adjoint pass).
+// MODE 0: bound only; MODE 1: bound and gradient (adjoint pass); MODE 2: as MODE 1 with dlb/dalpha
+// stored in BF16 (the optimiser's own gradient buffer).
 template <int MODE>
 __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ Maps maps, const Args a) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -1082,7 +1084,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_fused(const __grid_constant__ M
                   if (bi < a.n_beta) a.dbeta[bi] = (float)sg * z;
                 }
               }
-              if (unst && rin) a.dalpha[sm->abase[row] + rank] = g;
+              if (unst && rin) {
+                if constexpr (MODE == 2) a.dalpha16[sm->abase[row] + rank] = __float2bfloat16_rn(g);
+                else a.dalpha[sm->abase[row] + rank] = g;
+              }
               const float hv = rin ? fmaf(D, z, lm) : 0.f;
               if (writer)
                 *reinterpret_cast<__nv_bfloat16*>(aslot + (8 * h + c8) * 128 + (kx ^ (uint32_t)(c8 << 4))) =
@@ -1369,12 +1374,14 @@ static int tc_prepare(bcrown_net* net, TcNet* t) {
   }
   BC_CUDA(cudaFuncSetAttribute(k_fused<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem) + 1024));
   BC_CUDA(cudaFuncSetAttribute(k_fused<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem) + 1024));
+  BC_CUDA(cudaFuncSetAttribute(k_fused<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem) + 1024));
   t->ready = true;
   return BCROWN_OK;
 }
 
 static int tc_launch(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* bt, const Tables& tb, Args& A,
-                     char* ws, size_t ws_bytes, bool grad, bool plan, cudaStream_t s) {
+                     char* ws, size_t ws_bytes, int mode, bool plan, cudaStream_t s) {
+  const bool grad = mode >= 1;
   TcNet* t = tc_of(net);
   BC_CHECK(tc_prepare(net, t));
   const int B = bt->B, K = net->K, P = dom->n_props;
@@ -1430,7 +1437,9 @@ static int tc_launch(bcrown_net* net, const bcrown_domain* dom, const bcrown_bat
   const int grid = (int)std::min<long long>(T, sms);
   {
     ProfScope ps(net, BCROWN_PROF_FUSED, s);
-    if (grad)
+    if (mode == 2)
+      k_fused<2><<<grid, NTHREADS, sizeof(Smem) + 1024, s>>>(t->maps, A);
+    else if (mode == 1)
       k_fused<1><<<grid, NTHREADS, sizeof(Smem) + 1024, s>>>(t->maps, A);
     else
       k_fused<0><<<grid, NTHREADS, sizeof(Smem) + 1024, s>>>(t->maps, A);
@@ -1442,15 +1451,16 @@ static int tc_launch(bcrown_net* net, const bcrown_domain* dom, const bcrown_bat
 
 int tc_bound(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* bt, const Tables& tb, char* ws,
              size_t ws_bytes, bool grad, bool plan, const float* alpha, const float* beta, float* lb, float* dalpha,
-             float* dbeta, cudaStream_t s) {
+             float* dbeta, cudaStream_t s, __nv_bfloat16* dalpha16) {
   Args A;
   memset(&A, 0, sizeof(A));
   A.alpha = alpha;
   A.beta = beta;
   A.lb = lb;
   A.dalpha = dalpha;
+  A.dalpha16 = dalpha16;
   A.dbeta = dbeta;
-  return tc_launch(net, dom, bt, tb, A, ws, ws_bytes, grad, plan, s);
+  return tc_launch(net, dom, bt, tb, A, ws, ws_bytes, !grad ? 0 : (dalpha16 ? 2 : 1), plan, s);
 }
 
 void tc_release(const bcrown_net* net) {

@@ -607,6 +607,92 @@ __global__ void __launch_bounds__(32 * ADAM_ROWS_PER_BLOCK) k_adam(
   if (lane == 0 && improved) best_lb[r] = cur;
 }
 
+// The same step with the gradient and both moments of alpha held in BF16 (the BF16 path's
+// optimiser state): 22 instead of 32 bytes moved per alpha.  The moments are rounded to BF16
+// after each update; beta's state stays FP32.
+__device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
+__device__ __forceinline__ uint32_t bf16_pack(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+__global__ void __launch_bounds__(32 * ADAM_ROWS_PER_BLOCK) k_adam16(
+    int R, int K, BatchView bt, const int32_t* __restrict__ U, int P, const float* __restrict__ lb_t,
+    float* __restrict__ best_lb, float* __restrict__ a_cur, float* __restrict__ a_best,
+    const __nv_bfloat16* __restrict__ ga, __nv_bfloat16* __restrict__ ma, __nv_bfloat16* __restrict__ va,
+    float* __restrict__ b_cur, float* __restrict__ b_best, const float* __restrict__ gb, float* __restrict__ mb,
+    float* __restrict__ vb, float lr_a, float lr_b, float beta1, float beta2, float eps, float bc1, float bc2,
+    int64_t n_alpha, int64_t n_beta) {
+  const int lane = threadIdx.x & 31;
+  const int r = blockIdx.x * ADAM_ROWS_PER_BLOCK + (threadIdx.x >> 5);
+  if (r >= R) return;
+  const int b = r / K, k = r - b * K;
+  const int p = bt.prop_of[b];
+  if (p < 0 || p >= P) return;
+  const float cur = lb_t[r];
+  const bool improved = cur > best_lb[r];
+  const float ib1 = 1.f / bc1, ib2 = 1.f / bc2;
+  const int Up = U[p];
+  const long long abase = bt.alpha_off[b] + (long long)k * Up;
+  const long long aend = abase < 0 ? abase : min(abase + (long long)Up, (long long)n_alpha);
+  auto one = [&](long long i) {
+    const float th = a_cur[i];
+    if (improved) a_best[i] = th;
+    float m = __bfloat162float(ma[i]), v = __bfloat162float(va[i]);
+    a_cur[i] = adam_alpha(th, __bfloat162float(ga[i]), m, v, lr_a, beta1, beta2, eps, ib1, ib2);
+    ma[i] = __float2bfloat16_rn(m);
+    va[i] = __float2bfloat16_rn(v);
+  };
+  // 4-aligned body: 16-byte alpha accesses, 8-byte BF16 accesses
+  const bool vec = ((reinterpret_cast<uintptr_t>(a_cur) | reinterpret_cast<uintptr_t>(a_best)) & 15u) == 0 &&
+                   ((reinterpret_cast<uintptr_t>(ga) | reinterpret_cast<uintptr_t>(ma) |
+                     reinterpret_cast<uintptr_t>(va)) & 7u) == 0;
+  long long v0 = aend, v1 = aend;
+  if (vec && aend > abase) {
+    v0 = min(aend, (abase + 3) & ~3LL);
+    v1 = v0 + ((aend - v0) & ~3LL);
+  }
+  for (long long i = abase + lane; i < v0; i += 32) one(i);
+  for (long long i = v1 + lane; i < aend; i += 32) one(i);
+#pragma unroll 2
+  for (long long i = v0 + 4 * lane; i < v1; i += 128) {
+    const float4 th = *reinterpret_cast<const float4*>(a_cur + i);
+    const uint2 g2 = *reinterpret_cast<const uint2*>(ga + i);
+    const uint2 m2 = *reinterpret_cast<const uint2*>(ma + i);
+    const uint2 w2 = *reinterpret_cast<const uint2*>(va + i);
+    if (improved) *reinterpret_cast<float4*>(a_best + i) = th;
+    float m[4] = {bf16_lo(m2.x), bf16_hi(m2.x), bf16_lo(m2.y), bf16_hi(m2.y)};
+    float v[4] = {bf16_lo(w2.x), bf16_hi(w2.x), bf16_lo(w2.y), bf16_hi(w2.y)};
+    const float g[4] = {bf16_lo(g2.x), bf16_hi(g2.x), bf16_lo(g2.y), bf16_hi(g2.y)};
+    float4 o;
+    o.x = adam_alpha(th.x, g[0], m[0], v[0], lr_a, beta1, beta2, eps, ib1, ib2);
+    o.y = adam_alpha(th.y, g[1], m[1], v[1], lr_a, beta1, beta2, eps, ib1, ib2);
+    o.z = adam_alpha(th.z, g[2], m[2], v[2], lr_a, beta1, beta2, eps, ib1, ib2);
+    o.w = adam_alpha(th.w, g[3], m[3], v[3], lr_a, beta1, beta2, eps, ib1, ib2);
+    *reinterpret_cast<float4*>(a_cur + i) = o;
+    *reinterpret_cast<uint2*>(ma + i) = make_uint2(bf16_pack(m[0], m[1]), bf16_pack(m[2], m[3]));
+    *reinterpret_cast<uint2*>(va + i) = make_uint2(bf16_pack(v[0], v[1]), bf16_pack(v[2], v[3]));
+  }
+  const int cnt = bt.split_cnt[b];
+  const long long bbase = (long long)bt.split_off[b] * K + (long long)k * cnt;
+  for (int t = lane; t < cnt; t += 32) {
+    const long long i = bbase + t;
+    if (i < 0 || i >= n_beta) break;
+    float th = b_cur[i];
+    if (improved) b_best[i] = th;
+    float g = gb[i];
+    float m = beta1 * mb[i] + (1.f - beta1) * g;
+    float v = beta2 * vb[i] + (1.f - beta2) * g * g;
+    mb[i] = m;
+    vb[i] = v;
+    th += lr_b * (m / bc1) / (sqrtf(v / bc2) + eps);
+    b_cur[i] = fmaxf(th, 0.f);
+  }
+  __syncwarp();
+  if (lane == 0 && improved) best_lb[r] = cur;
+}
+
 // ----------------------------------------------------------------------------------------
 // Neuron codes per (row, hidden neuron): split overrides stability
 // ----------------------------------------------------------------------------------------
@@ -944,6 +1030,18 @@ void launch_adam(int R, int K, const BatchView& bt, const int32_t* U, int P, con
         eps, bc1, bc2, n_alpha, n_beta);
     ++g_launches;
   }
+}
+
+void launch_adam16(int R, int K, const BatchView& bt, const int32_t* U, int P, const float* lb_t, float* best_lb,
+                   float* a_cur, float* a_best, const __nv_bfloat16* ga, __nv_bfloat16* ma, __nv_bfloat16* va,
+                   float* b_cur, float* b_best, const float* gb, float* mb, float* vb, float lr_a, float lr_b,
+                   float beta1, float beta2, float eps, float bc1, float bc2, int64_t n_alpha, int64_t n_beta,
+                   cudaStream_t s) {
+  if (R <= 0) return;
+  k_adam16<<<(R + ADAM_ROWS_PER_BLOCK - 1) / ADAM_ROWS_PER_BLOCK, 32 * ADAM_ROWS_PER_BLOCK, 0, s>>>(
+      R, K, bt, U, P, lb_t, best_lb, a_cur, a_best, ga, ma, va, b_cur, b_best, gb, mb, vb, lr_a, lr_b, beta1, beta2,
+      eps, bc1, bc2, n_alpha, n_beta);
+  ++g_launches;
 }
 
 void launch_codes(const RowsCtx& c, int layer, int d, long long hoff, int H, int8_t* out, cudaStream_t s) {

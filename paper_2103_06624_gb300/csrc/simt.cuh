@@ -29,6 +29,12 @@ void launch_adam(int R, int K, const BatchView& bt, const int32_t* U, int P, con
                  float* a_cur, float* a_best, const float* ga, float* ma, float* va, float* b_cur, float* b_best,
                  const float* gb, float* mb, float* vb, float lr_a, float lr_b, float beta1, float beta2, float eps,
                  float bc1, float bc2, int64_t n_alpha, int64_t n_beta, cudaStream_t s);
+// As launch_adam with the alpha gradient and moments in BF16.
+void launch_adam16(int R, int K, const BatchView& bt, const int32_t* U, int P, const float* lb_t, float* best_lb,
+                   float* a_cur, float* a_best, const __nv_bfloat16* ga, __nv_bfloat16* ma, __nv_bfloat16* va,
+                   float* b_cur, float* b_best, const float* gb, float* mb, float* vb, float lr_a, float lr_b,
+                   float beta1, float beta2, float eps, float bc1, float bc2, int64_t n_alpha, int64_t n_beta,
+                   cudaStream_t s);
 void launch_codes(const RowsCtx& c, int layer, int d, long long hoff, int H, int8_t* out, cudaStream_t s);
 void launch_split(const BatchView& bt, int K, const int32_t* U, int P, const uint8_t* pick_layer,
                   const uint32_t* pick_idx, const float* alpha, const float* beta, int32_t* c_prop, int32_t* c_off,
