@@ -294,18 +294,18 @@ def main():
         # the alpha/beta it reads, the gradients it writes and the bound of each row
         ms, nl = prof[5]
         U = np.array([len(u) for u in unst])[hbatch.prop_of]
-        bytes_per_launch = float(np.sum(pb.K * (8 * U + 8 * hbatch.split_cnt.astype(np.int64) + 4)))
+        bytes_per_launch = float(np.sum(pb.K * (6 * U + 8 * hbatch.split_cnt.astype(np.int64) + 4)))
         achieved = bytes_per_launch * nl / (ms / 1e3) / 1e9
         peak = peaks.get("hbm_gbs", 6800.0)
         tflops = rows * 2 * f_row * nl / (ms / 1e3) / 1e12
         tpeak = peaks.get("bf16_tflops_sustained", 1700.0)
-        roof = {"bound": "hbm", "kernel": "k_fused<1> (tcgen05 bound + adjoint pass, one launch per iteration)",
+        roof = {"bound": "hbm", "kernel": "k_fused<2> (tcgen05 bound + adjoint pass, one launch per iteration)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": None, "traffic_note": None,
                 "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)",
                 "algorithmic_bytes_per_launch": bytes_per_launch,
-                "bytes_model": "per row: 8 B x unstable neurons (alpha read, dalpha write) + 8 B x splits "
-                               "(beta read, dbeta write) + 4 B (lb)",
+                "bytes_model": "per row: 6 B x unstable neurons (alpha read FP32, dalpha written BF16) + 8 B x "
+                               "splits (beta read, dbeta write) + 4 B (lb)",
                 "tensor_tflops": tflops, "tensor_frac": tflops / tpeak,
                 "tensor_peak_source": "of measured (MEASURED_PEAKS.json bf16_tflops_sustained)",
                 "kernel_ms_per_step": ms / args.steps, "launches_per_step": nl / args.steps,
