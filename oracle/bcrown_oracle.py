@@ -489,6 +489,32 @@ def root_bounds(net, x_lo, x_hi, rule=ALPHA_ADAPTIVE, value=0.5):
     return l, u
 
 
+def interval_bounds(net, x_lo, x_hi):
+    """l, u [P, H] by interval propagation: z^(i) in W^(i) [h_lo, h_hi] + b^(i) with
+    h = ReLU(z), layer by layer from the box (centre/radius form, |W| for the radius).
+
+    Valid (sound, looser than CROWN) intermediate bounds for any network size; the bound of
+    Theorem 3.1 only needs some l <= z <= u (Section 2.1), so they serve where CROWN root
+    bounds over very wide layers are out of reach for this oracle.
+    """
+    x_lo = np.atleast_2d(np.asarray(x_lo, np.float64))
+    x_hi = np.atleast_2d(np.asarray(x_hi, np.float64))
+    P = x_lo.shape[0]
+    H = int(sum(net.hidden))
+    l = np.zeros((P, H))
+    u = np.zeros((P, H))
+    for p in range(P):
+        lo, hi = x_lo[p], x_hi[p]
+        for i in range(1, net.L):
+            mid, rad = 0.5 * (lo + hi), 0.5 * (hi - lo)
+            c = _mv(net.W[i], mid[None, :])[0] + net.b[i]
+            r = _mv(abs(net.W[i]), rad[None, :])[0]
+            l[p, net.hoff[i - 1]:net.hoff[i]] = c - r
+            u[p, net.hoff[i - 1]:net.hoff[i]] = c + r
+            lo, hi = np.maximum(c - r, 0.0), np.maximum(c + r, 0.0)
+    return l, u
+
+
 # --------------------------------------------------------------------------------------
 # Projected Adam ascent on alpha in [0,1], beta >= 0 (Eq. opt_alpha_beta; Appendix C.1)
 # --------------------------------------------------------------------------------------

@@ -271,3 +271,30 @@ def test_power_of_two_scaling_is_bit_exact():
     net4 = bc.load_net(pb.layers, pb.C * 4.0)
     lb4 = bc.bound(net4, dom, db, _t(a), _t(b * 4.0)).cpu().numpy()
     assert np.array_equal(lb4, lb * 4.0)
+
+
+def test_conv_c5_bound_parity_and_certify_sampled():
+    """The precision workload's net (3x32x32 -> four 3x3 conv layers -> fc 8192-512-10,
+    123,392 hidden neurons).  Intermediate bounds by the oracle's interval propagation (CROWN
+    root bounds over 65,536-wide layers are out of reach for the oracle; any valid l <= z <= u
+    serves the bound).  FP32 within 1e-5 of the FP64 oracle; the certified pass never above it,
+    with its gap printed."""
+    pb = wl.problem_conv_big()
+    onet = O.OracleNet(pb.layers, pb.C)
+    l, u = O.interval_bounds(onet, pb.x_lo, pb.x_hi)
+    l, u = l.astype(np.float32), u.astype(np.float32)
+    unst = [np.nonzero(O.unstable_mask(l[0], u[0]))[0]]
+    props = dict(x_lo=pb.x_lo, x_hi=pb.x_hi, l=l, u=u)
+    batch = wl.tree_batch(pb, unst, [6], 24, 3)
+    a, b = wl.random_alpha_beta(batch, 4, 1.0)
+    net, dom, db = _gpu(pb, props, batch)
+    ref = O.bound(onet, props, batch, a, b)
+    lb = bc.bound(net, dom, db, _t(a), _t(b), bc.FP32).cpu().numpy()
+    assert bc.status(net) == 0
+    assert np.max(rel_err(lb, ref)) <= RTOL
+    lbc = bc.bound(net, dom, db, _t(a), _t(b), bc.CERTIFY).cpu().numpy()
+    assert bc.status(net) == 0
+    assert np.all(lbc <= ref)
+    gap = np.max((ref - lbc) / np.maximum(np.abs(ref), 1.0))
+    print("conv c5 certified gap (relative): %.3e" % gap)
+    assert gap <= 2e-2

@@ -237,6 +237,28 @@ def test_root_bounds_layer1_exact_and_sound():
         assert np.all(zs[i] <= u[lo:hi] + 1e-12)
 
 
+def test_interval_bounds_exact_layer1_sound_and_degenerate():
+    """Interval bounds: layer 1 is the exact interval (= CROWN's), every layer contains the
+    pre-activations of box samples, and a zero-width box collapses them onto z(x0)."""
+    for pb in (tiny_problem(widths=(4, 6, 5, 2), eps=0.4), tiny_conv_problem()):
+        net, props, _ = _setup(pb)
+        l, u = O.interval_bounds(net, pb.x_lo, pb.x_hi)
+        h1 = net.hoff[1]
+        assert np.allclose(l[0, :h1], props["l"][0][:h1], atol=1e-6)
+        assert np.allclose(u[0, :h1], props["u"][0][:h1], atol=1e-6)
+        rng = np.random.default_rng(2)
+        xs = rng.uniform(pb.x_lo[0], pb.x_hi[0], size=(20000, pb.x_lo.shape[1]))
+        zs = net.preacts(xs)
+        for i in range(1, net.L):
+            lo, hi = net.hoff[i - 1], net.hoff[i]
+            assert np.all(zs[i] >= l[0, lo:hi] - 1e-12)
+            assert np.all(zs[i] <= u[0, lo:hi] + 1e-12)
+        x0 = 0.5 * (pb.x_lo[0].astype(np.float64) + pb.x_hi[0])
+        l0, u0 = O.interval_bounds(net, x0[None, :], x0[None, :])
+        z0 = np.concatenate([z[0] for z in net.preacts(x0[None, :])[1:]])
+        assert np.allclose(l0[0], z0, atol=1e-12) and np.allclose(u0[0], z0, atol=1e-12)
+
+
 # ------------------------------------------------------------------ library-routine pins
 
 def test_conv_matrix_matches_torch_conv2d():
