@@ -1,6 +1,7 @@
 // CUDA-core kernels: per-property tables, the relaxation epilogue, FP32 contractions
 // (dense and convolution), concretisation, the adjoint epilogue, projected Adam,
 // batch_split and the rigorous (CERTIFY) variants.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 
@@ -347,62 +348,141 @@ __global__ void __launch_bounds__(256) k_sgemm(int M, int N, int K, const float*
   }
 }
 
-// Backward through a convolution (transposed convolution), one thread per output:
-//   Ain[r, ci, iy, ix] = sum_{co, ky, kx: iy = oy*s - p + ky, ix = ox*s - p + kx} Lam[r, co, oy, ox] W[co, ci, ky, kx]
-__global__ void k_conv_bwd(int R, LayerGeom g, const float* __restrict__ Lam, const float* __restrict__ W,
-                           float* __restrict__ Ain) {
-  long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  long long per = (long long)g.d_in;
-  if (id >= (long long)R * per) return;
-  int r = (int)(id / per);
-  int rem = (int)(id - (long long)r * per);
-  int hw = g.in_h * g.in_w;
-  int ci = rem / hw, pos = rem - ci * hw, iy = pos / g.in_w, ix = pos - iy * g.in_w;
-  const float* lr = Lam + (size_t)r * g.d_out;
-  float s = 0.f;
-  for (int ky = 0; ky < g.k; ++ky) {
-    int ty = iy + g.pad - ky;
-    if (ty < 0 || ty % g.stride) continue;
-    int oy = ty / g.stride;
-    if (oy >= g.out_h) continue;
-    for (int kx = 0; kx < g.k; ++kx) {
-      int tx = ix + g.pad - kx;
-      if (tx < 0 || tx % g.stride) continue;
-      int ox = tx / g.stride;
-      if (ox >= g.out_w) continue;
-      const float* lp = lr + (size_t)oy * g.out_w + ox;
-      const float* wp = W + ((size_t)ci * g.k + ky) * g.k + kx;
-      for (int co = 0; co < g.out_c; ++co)
-        s = fmaf(lp[(size_t)co * g.out_h * g.out_w], wp[(size_t)co * g.in_c * g.k * g.k], s);
-    }
-  }
-  Ain[id] = s;
-}
+// Convolutions, both directions, register-blocked: a thread owns one spatial position of one
+// row and CB = 8 channels of the result; the weights of a slice of the summed channels are
+// staged in shared memory as [channel][tap][8 result channels] (two 16-byte reads per tap),
+// the operand is read once per (channel, tap) and feeds 8 FMAs.  Every output is still one
+// sequential FMA chain over its terms (taps outer, channels inner), which the certifying pass's
+// a priori error bound assumes.
+constexpr int CONV_CB = 8;          // result channels per thread
+constexpr int CONV_POS = 128;       // positions per block (threads)
+constexpr int CONV_SMEM_FLOATS = 8192;   // 32 KB of staged weights per slice
 
-// Forward convolution (adjoint pass), one thread per output:
-//   Z[r, co, oy, ox] = b[co] + sum_{ci, ky, kx} W[co, ci, ky, kx] h[r, ci, oy*s - p + ky, ox*s - p + kx]
-__global__ void k_conv_fwd(int R, LayerGeom g, const float* __restrict__ h, const float* __restrict__ W,
-                           const float* __restrict__ bias, float* __restrict__ Z) {
-  long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  long long per = (long long)g.d_out;
-  if (id >= (long long)R * per) return;
-  int r = (int)(id / per);
-  int rem = (int)(id - (long long)r * per);
-  int hw = g.out_h * g.out_w;
-  int co = rem / hw, pos = rem - co * hw, oy = pos / g.out_w, ox = pos - oy * g.out_w;
-  const float* hr = h + (size_t)r * g.d_in;
-  float s = 0.f;
-  for (int ci = 0; ci < g.in_c; ++ci)
-    for (int ky = 0; ky < g.k; ++ky) {
-      int iy = oy * g.stride - g.pad + ky;
-      if (iy < 0 || iy >= g.in_h) continue;
-      for (int kx = 0; kx < g.k; ++kx) {
-        int ix = ox * g.stride - g.pad + kx;
-        if (ix < 0 || ix >= g.in_w) continue;
-        s = fmaf(W[(((size_t)co * g.in_c + ci) * g.k + ky) * g.k + kx], hr[((size_t)ci * g.in_h + iy) * g.in_w + ix], s);
+// Backward (transposed convolution):
+//   Ain[r, ci, iy, ix] = sum_{co, ky, kx: iy = oy*s - p + ky, ix = ox*s - p + kx} Lam[r, co, oy, ox] W[co, ci, ky, kx]
+// grid: (position tiles, channel groups of CB, rows).
+__global__ void __launch_bounds__(CONV_POS) k_conv_bwd(int R, LayerGeom g, const float* __restrict__ Lam,
+                                                       const float* __restrict__ W, float* __restrict__ Ain) {
+  __shared__ __align__(16) float Ws[CONV_SMEM_FLOATS];
+  const int kk = g.k * g.k;
+  const int r = blockIdx.z;
+  const int ci0 = blockIdx.y * CONV_CB;
+  const int hw_in = g.in_h * g.in_w, hw_out = g.out_h * g.out_w;
+  const int pos = blockIdx.x * CONV_POS + threadIdx.x;
+  const bool pin = pos < hw_in;
+  const int iy = pin ? pos / g.in_w : 0, ix = pin ? pos - (pos / g.in_w) * g.in_w : 0;
+  const float* lr = Lam + (size_t)r * g.d_out;
+  float acc[CONV_CB];
+#pragma unroll
+  for (int c = 0; c < CONV_CB; ++c) acc[c] = 0.f;
+  const int coch = max(1, CONV_SMEM_FLOATS / (kk * CONV_CB));   // output channels per slice
+  for (int co0 = 0; co0 < g.out_c; co0 += coch) {
+    const int nco = min(coch, g.out_c - co0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nco * kk * CONV_CB; e += CONV_POS) {
+      const int c = e % CONV_CB, t = (e / CONV_CB) % kk, col = e / (CONV_CB * kk);
+      const int ci = ci0 + c;
+      Ws[e] = ci < g.in_c ? W[((size_t)(co0 + col) * g.in_c + ci) * kk + t] : 0.f;
+    }
+    __syncthreads();
+    if (pin) {
+      for (int ky = 0; ky < g.k; ++ky) {
+        const int ty = iy + g.pad - ky;
+        if (ty < 0 || ty % g.stride) continue;
+        const int oy = ty / g.stride;
+        if (oy >= g.out_h) continue;
+        for (int kx = 0; kx < g.k; ++kx) {
+          const int tx = ix + g.pad - kx;
+          if (tx < 0 || tx % g.stride) continue;
+          const int ox = tx / g.stride;
+          if (ox >= g.out_w) continue;
+          const float* lp = lr + (size_t)co0 * hw_out + (size_t)oy * g.out_w + ox;
+          const float* wp = Ws + (ky * g.k + kx) * CONV_CB;
+          for (int col = 0; col < nco; ++col) {
+            const float v = lp[(size_t)col * hw_out];
+            const float4 w0 = *reinterpret_cast<const float4*>(wp + (size_t)col * kk * CONV_CB);
+            const float4 w1 = *reinterpret_cast<const float4*>(wp + (size_t)col * kk * CONV_CB + 4);
+            acc[0] = fmaf(v, w0.x, acc[0]);
+            acc[1] = fmaf(v, w0.y, acc[1]);
+            acc[2] = fmaf(v, w0.z, acc[2]);
+            acc[3] = fmaf(v, w0.w, acc[3]);
+            acc[4] = fmaf(v, w1.x, acc[4]);
+            acc[5] = fmaf(v, w1.y, acc[5]);
+            acc[6] = fmaf(v, w1.z, acc[6]);
+            acc[7] = fmaf(v, w1.w, acc[7]);
+          }
+        }
       }
     }
-  Z[id] = s + bias[rem];
+  }
+  if (pin) {
+    float* ar = Ain + (size_t)r * g.d_in + pos;
+#pragma unroll
+    for (int c = 0; c < CONV_CB; ++c)
+      if (ci0 + c < g.in_c) ar[(size_t)(ci0 + c) * hw_in] = acc[c];
+  }
+}
+
+// Forward convolution (adjoint pass):
+//   Z[r, co, oy, ox] = b[co] + sum_{ci, ky, kx} W[co, ci, ky, kx] h[r, ci, oy*s - p + ky, ox*s - p + kx]
+// grid: (position tiles, channel groups of CB, rows).
+__global__ void __launch_bounds__(CONV_POS) k_conv_fwd(int R, LayerGeom g, const float* __restrict__ h,
+                                                       const float* __restrict__ W, const float* __restrict__ bias,
+                                                       float* __restrict__ Z) {
+  __shared__ __align__(16) float Ws[CONV_SMEM_FLOATS];
+  const int kk = g.k * g.k;
+  const int r = blockIdx.z;
+  const int co0 = blockIdx.y * CONV_CB;
+  const int hw_in = g.in_h * g.in_w, hw_out = g.out_h * g.out_w;
+  const int pos = blockIdx.x * CONV_POS + threadIdx.x;
+  const bool pin = pos < hw_out;
+  const int oy = pin ? pos / g.out_w : 0, ox = pin ? pos - (pos / g.out_w) * g.out_w : 0;
+  const float* hr = h + (size_t)r * g.d_in;
+  float acc[CONV_CB];
+#pragma unroll
+  for (int c = 0; c < CONV_CB; ++c) acc[c] = 0.f;
+  const int cich = max(1, CONV_SMEM_FLOATS / (kk * CONV_CB));   // input channels per slice
+  for (int ci0 = 0; ci0 < g.in_c; ci0 += cich) {
+    const int nci = min(cich, g.in_c - ci0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nci * kk * CONV_CB; e += CONV_POS) {
+      const int c = e % CONV_CB, t = (e / CONV_CB) % kk, cl = e / (CONV_CB * kk);
+      const int co = co0 + c;
+      Ws[e] = co < g.out_c ? W[((size_t)co * g.in_c + ci0 + cl) * kk + t] : 0.f;
+    }
+    __syncthreads();
+    if (pin) {
+      for (int ky = 0; ky < g.k; ++ky) {
+        const int iy = oy * g.stride - g.pad + ky;
+        if (iy < 0 || iy >= g.in_h) continue;
+        for (int kx = 0; kx < g.k; ++kx) {
+          const int ix = ox * g.stride - g.pad + kx;
+          if (ix < 0 || ix >= g.in_w) continue;
+          const float* hp = hr + (size_t)ci0 * hw_in + (size_t)iy * g.in_w + ix;
+          const float* wp = Ws + (ky * g.k + kx) * CONV_CB;
+          for (int cl = 0; cl < nci; ++cl) {
+            const float v = hp[(size_t)cl * hw_in];
+            const float4 w0 = *reinterpret_cast<const float4*>(wp + (size_t)cl * kk * CONV_CB);
+            const float4 w1 = *reinterpret_cast<const float4*>(wp + (size_t)cl * kk * CONV_CB + 4);
+            acc[0] = fmaf(w0.x, v, acc[0]);
+            acc[1] = fmaf(w0.y, v, acc[1]);
+            acc[2] = fmaf(w0.z, v, acc[2]);
+            acc[3] = fmaf(w0.w, v, acc[3]);
+            acc[4] = fmaf(w1.x, v, acc[4]);
+            acc[5] = fmaf(w1.y, v, acc[5]);
+            acc[6] = fmaf(w1.z, v, acc[6]);
+            acc[7] = fmaf(w1.w, v, acc[7]);
+          }
+        }
+      }
+    }
+  }
+  if (pin) {
+    float* zr = Z + (size_t)r * g.d_out + pos;
+#pragma unroll
+    for (int c = 0; c < CONV_CB; ++c)
+      if (co0 + c < g.out_c) zr[(size_t)(co0 + c) * hw_out] = acc[c] + bias[(size_t)(co0 + c) * hw_out + pos];
+  }
 }
 
 // ----------------------------------------------------------------------------------------
@@ -990,14 +1070,25 @@ void launch_sgemm(int M, int N, int K, const float* A, int lda, const float* B, 
 }
 
 void launch_conv_bwd(int R, const LayerGeom& g, const float* Lam, const float* W, float* Ain, cudaStream_t s) {
-  long long n = (long long)R * g.d_in;
-  if (n > 0) { k_conv_bwd<<<grid1d(n, 256), 256, 0, s>>>(R, g, Lam, W, Ain); ++g_launches; }
+  if (R <= 0 || g.d_in <= 0) return;
+  // rows on grid.z (at most 65535 per launch)
+  for (int r0 = 0; r0 < R; r0 += 65535) {
+    const int rn = std::min(R - r0, 65535);
+    dim3 grid((g.in_h * g.in_w + CONV_POS - 1) / CONV_POS, (g.in_c + CONV_CB - 1) / CONV_CB, rn);
+    k_conv_bwd<<<grid, CONV_POS, 0, s>>>(rn, g, Lam + (size_t)r0 * g.d_out, W, Ain + (size_t)r0 * g.d_in);
+    ++g_launches;
+  }
 }
 
 void launch_conv_fwd(int R, const LayerGeom& g, const float* h, const float* W, const float* bias, float* Z,
                      cudaStream_t s) {
-  long long n = (long long)R * g.d_out;
-  if (n > 0) { k_conv_fwd<<<grid1d(n, 256), 256, 0, s>>>(R, g, h, W, bias, Z); ++g_launches; }
+  if (R <= 0 || g.d_out <= 0) return;
+  for (int r0 = 0; r0 < R; r0 += 65535) {
+    const int rn = std::min(R - r0, 65535);
+    dim3 grid((g.out_h * g.out_w + CONV_POS - 1) / CONV_POS, (g.out_c + CONV_CB - 1) / CONV_CB, rn);
+    k_conv_fwd<<<grid, CONV_POS, 0, s>>>(rn, g, h + (size_t)r0 * g.d_in, W, bias, Z + (size_t)r0 * g.d_out);
+    ++g_launches;
+  }
 }
 
 void launch_concretize(bool cert, const RowsCtx& c, int d0, const float* A0, const float* cf, const double* cd,
