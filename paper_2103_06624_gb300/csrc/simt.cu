@@ -349,12 +349,12 @@ __global__ void __launch_bounds__(256) k_sgemm(int M, int N, int K, const float*
 }
 
 // Convolutions, both directions, register-blocked: a thread owns one spatial position of one
-// row and CB = 8 channels of the result; the weights of a slice of the summed channels are
-// staged in shared memory as [channel][tap][8 result channels] (two 16-byte reads per tap),
-// the operand is read once per (channel, tap) and feeds 8 FMAs.  Every output is still one
+// row and CB = 16 channels of the result; the weights of a slice of the summed channels are
+// staged in shared memory as [channel][tap][CB result channels] (16-byte reads),
+// the operand is read once per (channel, tap) and feeds CB FMAs.  Every output is still one
 // sequential FMA chain over its terms (taps outer, channels inner), which the certifying pass's
 // a priori error bound assumes.
-constexpr int CONV_CB = 8;          // result channels per thread
+constexpr int CONV_CB = 16;         // result channels per thread (multiple of 4)
 constexpr int CONV_POS = 128;       // positions per block (threads)
 constexpr int CONV_SMEM_FLOATS = 8192;   // 32 KB of staged weights per slice
 
@@ -400,16 +400,14 @@ __global__ void __launch_bounds__(CONV_POS) k_conv_bwd(int R, LayerGeom g, const
           const float* wp = Ws + (ky * g.k + kx) * CONV_CB;
           for (int col = 0; col < nco; ++col) {
             const float v = lp[(size_t)col * hw_out];
-            const float4 w0 = *reinterpret_cast<const float4*>(wp + (size_t)col * kk * CONV_CB);
-            const float4 w1 = *reinterpret_cast<const float4*>(wp + (size_t)col * kk * CONV_CB + 4);
-            acc[0] = fmaf(v, w0.x, acc[0]);
-            acc[1] = fmaf(v, w0.y, acc[1]);
-            acc[2] = fmaf(v, w0.z, acc[2]);
-            acc[3] = fmaf(v, w0.w, acc[3]);
-            acc[4] = fmaf(v, w1.x, acc[4]);
-            acc[5] = fmaf(v, w1.y, acc[5]);
-            acc[6] = fmaf(v, w1.z, acc[6]);
-            acc[7] = fmaf(v, w1.w, acc[7]);
+#pragma unroll
+            for (int q4 = 0; q4 < CONV_CB / 4; ++q4) {
+              const float4 w = *reinterpret_cast<const float4*>(wp + (size_t)col * kk * CONV_CB + 4 * q4);
+              acc[4 * q4 + 0] = fmaf(v, w.x, acc[4 * q4 + 0]);
+              acc[4 * q4 + 1] = fmaf(v, w.y, acc[4 * q4 + 1]);
+              acc[4 * q4 + 2] = fmaf(v, w.z, acc[4 * q4 + 2]);
+              acc[4 * q4 + 3] = fmaf(v, w.w, acc[4 * q4 + 3]);
+            }
           }
         }
       }
@@ -462,16 +460,14 @@ __global__ void __launch_bounds__(CONV_POS) k_conv_fwd(int R, LayerGeom g, const
           const float* wp = Ws + (ky * g.k + kx) * CONV_CB;
           for (int cl = 0; cl < nci; ++cl) {
             const float v = hp[(size_t)cl * hw_in];
-            const float4 w0 = *reinterpret_cast<const float4*>(wp + (size_t)cl * kk * CONV_CB);
-            const float4 w1 = *reinterpret_cast<const float4*>(wp + (size_t)cl * kk * CONV_CB + 4);
-            acc[0] = fmaf(w0.x, v, acc[0]);
-            acc[1] = fmaf(w0.y, v, acc[1]);
-            acc[2] = fmaf(w0.z, v, acc[2]);
-            acc[3] = fmaf(w0.w, v, acc[3]);
-            acc[4] = fmaf(w1.x, v, acc[4]);
-            acc[5] = fmaf(w1.y, v, acc[5]);
-            acc[6] = fmaf(w1.z, v, acc[6]);
-            acc[7] = fmaf(w1.w, v, acc[7]);
+#pragma unroll
+            for (int q4 = 0; q4 < CONV_CB / 4; ++q4) {
+              const float4 w = *reinterpret_cast<const float4*>(wp + (size_t)cl * kk * CONV_CB + 4 * q4);
+              acc[4 * q4 + 0] = fmaf(w.x, v, acc[4 * q4 + 0]);
+              acc[4 * q4 + 1] = fmaf(w.y, v, acc[4 * q4 + 1]);
+              acc[4 * q4 + 2] = fmaf(w.z, v, acc[4 * q4 + 2]);
+              acc[4 * q4 + 3] = fmaf(w.w, v, acc[4 * q4 + 3]);
+            }
           }
         }
       }
