@@ -151,122 +151,156 @@ __global__ void __launch_bounds__(256) k_init_top(RowsCtx c, int dtop, const flo
 // into shared memory by ballots, neurons are strided over the lanes, sums are warp reductions.
 // CERT: outward chord constants (from the tables), c summed rounded down, error terms rounded up.
 // ----------------------------------------------------------------------------------------
-constexpr int RELAX_ROWS = 8;
-template <bool CERT>
-__global__ void __launch_bounds__(32 * RELAX_ROWS) k_relax(RowsCtx c, int layer, int d, long long hoff,
-                                                          const float* __restrict__ Ain, float* __restrict__ Lam,
-                                                          const float* __restrict__ bias,
-                                                          const float* __restrict__ alpha, int64_t n_alpha,
-                                                          const float* __restrict__ beta, int64_t n_beta,
-                                                          float* __restrict__ cf, double* __restrict__ cd,
-                                                          double* __restrict__ E, const float* __restrict__ wm,
-                                                          double gamma) {
-  __shared__ SplitSlot slots[RELAX_ROWS][BCROWN_MAX_SPLITS];
+constexpr int RELAX_WARPS = 8;   // warps per block; WPR of them share a row (wide layers: all 8)
+template <bool CERT, int WPR>
+__global__ void __launch_bounds__(32 * RELAX_WARPS) k_relax(RowsCtx c, int layer, int d, long long hoff,
+                                                           const float* __restrict__ Ain, float* __restrict__ Lam,
+                                                           const float* __restrict__ bias,
+                                                           const float* __restrict__ alpha, int64_t n_alpha,
+                                                           const float* __restrict__ beta, int64_t n_beta,
+                                                           float* __restrict__ cf, double* __restrict__ cd,
+                                                           double* __restrict__ E, const float* __restrict__ wm,
+                                                           double gamma) {
+  constexpr int RPB = RELAX_WARPS / WPR;   // rows per block
+  __shared__ SplitSlot slots[RPB][BCROWN_MAX_SPLITS];
+  __shared__ int nslots[RPB];
+  __shared__ float red[RELAX_WARPS][3];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int rl = blockIdx.x * RELAX_ROWS + w;
-  if (rl >= c.R) return;   // whole warps only; nothing below synchronises the block
-  int b, k, p;
-  bool ok = row_prop(c, rl, &b, &k, &p);
-  if (!ok) p = 0;
-  int cnt = c.bt.split_cnt[b];
-  const int off = c.bt.split_off[b];
-  if (cnt < 0 || cnt > BCROWN_MAX_SPLITS) {
-    if (lane == 0) flag(c.status, BCROWN_ERR_ARG);
-    cnt = 0;
-  }
-  // this layer's splits of the row, in list order
-  int ns = 0;
-  for (int t0 = 0; t0 < cnt; t0 += 32) {
-    const int t = t0 + lane;
-    bool keep = false;
-    int j = 0, sg = 0;
-    if (t < cnt) {
-      const int ly = c.bt.split_layer[off + t];
-      j = (int)c.bt.split_idx[off + t];
-      sg = c.bt.split_sign[off + t];
-      if (sg != -1 && sg != 1) flag(c.status, BCROWN_ERR_ARG);
-      else if (ly == layer) {
-        if (j < 0 || j >= d) flag(c.status, BCROWN_ERR_ARG);
-        else keep = true;
-      }
+  const int rs = w / WPR, sub = w - rs * WPR;   // row slot in the block, warp within the row
+  const int rl = blockIdx.x * RPB + rs;
+  const bool live = rl < c.R;   // dead warps still take part in the block barriers
+  int b = 0, k = 0, p = 0, cnt = 0, off = 0;
+  if (live) {
+    if (!row_prop(c, rl, &b, &k, &p)) p = 0;
+    cnt = c.bt.split_cnt[b];
+    off = c.bt.split_off[b];
+    if (cnt < 0 || cnt > BCROWN_MAX_SPLITS) {
+      if (lane == 0 && sub == 0) flag(c.status, BCROWN_ERR_ARG);
+      cnt = 0;
     }
-    const unsigned m = __ballot_sync(0xffffffffu, keep);
-    if (keep) slots[w][ns + __popc(m & ((1u << lane) - 1u))] = SplitSlot{j, sg, t};
-    ns += __popc(m);
   }
-  __syncwarp();
-  const SplitSlot* sl = slots[w];
-  const int Up = c.tb.U[p];
-  const long long abase = c.bt.alpha_off[b] + (long long)k * Up;
-  const long long bbase = (long long)off * c.K + (long long)k * cnt;
-  const float* a_row = Ain + (size_t)rl * d;
-  float* lam_row = Lam + (size_t)rl * d;
-  // CERT: acc is a lower bound of sum_j Lambda_j b_j + A_j lambda_j (every operation rounded
-  // down); e1, e2 are upper bounds (rounded up) of the error terms below.
+  // this layer's splits of the row, in list order (first warp of the row)
+  if (live && sub == 0) {
+    int ns = 0;
+    for (int t0 = 0; t0 < cnt; t0 += 32) {
+      const int t = t0 + lane;
+      bool keep = false;
+      int j = 0, sg = 0;
+      if (t < cnt) {
+        const int ly = c.bt.split_layer[off + t];
+        j = (int)c.bt.split_idx[off + t];
+        sg = c.bt.split_sign[off + t];
+        if (sg != -1 && sg != 1) flag(c.status, BCROWN_ERR_ARG);
+        else if (ly == layer) {
+          if (j < 0 || j >= d) flag(c.status, BCROWN_ERR_ARG);
+          else keep = true;
+        }
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, keep);
+      if (keep) slots[rs][ns + __popc(m & ((1u << lane) - 1u))] = SplitSlot{j, sg, t};
+      ns += __popc(m);
+    }
+    if (lane == 0) nslots[rs] = ns;
+  }
+  if (WPR > 1) __syncthreads();
+  else __syncwarp();
   float acc = 0.f, e1 = 0.f, e2 = 0.f;
+  if (live) {
+    const int ns = nslots[rs];
+    const SplitSlot* sl = slots[rs];
+    const int Up = c.tb.U[p];
+    const long long abase = c.bt.alpha_off[b] + (long long)k * Up;
+    const long long bbase = (long long)off * c.K + (long long)k * cnt;
+    const float* a_row = Ain + (size_t)rl * d;
+    float* lam_row = Lam + (size_t)rl * d;
+    // CERT: acc is a lower bound of sum_j Lambda_j b_j + A_j lambda_j (every operation rounded
+    // down); e1, e2 are upper bounds (rounded up) of the error terms below.
 #pragma unroll 4
-  for (int j = lane; j < d; j += 32) {
-    const float a = a_row[j];
-    const size_t n = (size_t)p * c.tb.H + hoff + j;
-    int s = 0;
-    float bet = 0.f;
-    for (int q = 0; q < ns; ++q)
-      if (sl[q].idx == j) {
-        s = sl[q].sign;
-        const long long bi = bbase + sl[q].t;
-        if (bi >= 0 && bi < n_beta) bet = fmaxf(beta[bi], 0.f);
-        else flag(c.status, BCROWN_ERR_ARG);
-      }
-    float D = 0.f, lm = 0.f;
-    const uint8_t code = c.tb.code[n];
-    if (s == -1) D = 1.f;
-    else if (s == 1) D = 0.f;
-    else if (code == CODE_ACTIVE) D = 1.f;
-    else if (code == CODE_INACTIVE) D = 0.f;
-    else if (a >= 0.f) {
-      const long long ai = abase + c.tb.rank[n];
-      if (ai < 0 || ai >= n_alpha) {
-        flag(c.status, BCROWN_ERR_ARG);
-        D = 0.f;
+    for (int j = sub * 32 + lane; j < d; j += 32 * WPR) {
+      const float a = a_row[j];
+      const size_t n = (size_t)p * c.tb.H + hoff + j;
+      int s = 0;
+      float bet = 0.f;
+      for (int q = 0; q < ns; ++q)
+        if (sl[q].idx == j) {
+          s = sl[q].sign;
+          const long long bi = bbase + sl[q].t;
+          if (bi >= 0 && bi < n_beta) bet = fmaxf(beta[bi], 0.f);
+          else flag(c.status, BCROWN_ERR_ARG);
+        }
+      float D = 0.f, lm = 0.f;
+      const uint8_t code = c.tb.code[n];
+      if (s == -1) D = 1.f;
+      else if (s == 1) D = 0.f;
+      else if (code == CODE_ACTIVE) D = 1.f;
+      else if (code == CODE_INACTIVE) D = 0.f;
+      else if (a >= 0.f) {
+        const long long ai = abase + c.tb.rank[n];
+        if (ai < 0 || ai >= n_alpha) {
+          flag(c.status, BCROWN_ERR_ARG);
+          D = 0.f;
+        } else {
+          D = fminf(fmaxf(alpha[ai], 0.f), 1.f);
+        }
       } else {
-        D = fminf(fmaxf(alpha[ai], 0.f), 1.f);
+        // upper chord, slope and intercept rounded up (outward) in the tables
+        D = c.tb.slope[n];
+        lm = c.tb.icpt[n];
       }
-    } else {
-      // upper chord, slope and intercept rounded up (outward) in the tables
-      D = c.tb.slope[n];
-      lm = c.tb.icpt[n];
+      const float L = fmaf(a, D, bet * (float)s);
+      lam_row[j] = L;
+      const float bj = bias[j];
+      if (CERT) {
+        acc = __fadd_rd(acc, __fadd_rd(__fmul_rd(L, bj), __fmul_rd(a, lm)));
+        const bool exact = (s == 0) && (D == 0.f || D == 1.f);
+        if (!exact) {
+          // Lambda_j was rounded once: |error| <= 2^-23 |Lambda_j| (+ an underflow margin),
+          // acting on |z_j| <= max(|l_j|, |u_j|)
+          const float zmax = fmaxf(fabsf(c.l[n]), fabsf(c.u[n]));
+          const float er = __fmaf_ru(fabsf(L), 0x1p-23f, 0x1p-140f);
+          e1 = __fadd_ru(e1, __fmul_ru(er, zmax));
+        }
+        e2 = __fadd_ru(e2, __fmul_ru(fabsf(L), wm[n]));
+      } else {
+        acc = fmaf(L, bj, fmaf(a, lm, acc));
+      }
     }
-    const float L = fmaf(a, D, bet * (float)s);
-    lam_row[j] = L;
-    const float bj = bias[j];
-    if (CERT) {
-      acc = __fadd_rd(acc, __fadd_rd(__fmul_rd(L, bj), __fmul_rd(a, lm)));
-      const bool exact = (s == 0) && (D == 0.f || D == 1.f);
-      if (!exact) {
-        // Lambda_j was rounded once: |error| <= 2^-23 |Lambda_j| (+ an underflow margin),
-        // acting on |z_j| <= max(|l_j|, |u_j|)
-        const float zmax = fmaxf(fabsf(c.l[n]), fabsf(c.u[n]));
-        const float er = __fmaf_ru(fabsf(L), 0x1p-23f, 0x1p-140f);
-        e1 = __fadd_ru(e1, __fmul_ru(er, zmax));
+    for (int o = 16; o > 0; o >>= 1) {
+      if (CERT) {
+        acc = __fadd_rd(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+        e1 = __fadd_ru(e1, __shfl_xor_sync(0xffffffffu, e1, o));
+        e2 = __fadd_ru(e2, __shfl_xor_sync(0xffffffffu, e2, o));
+      } else {
+        acc += __shfl_xor_sync(0xffffffffu, acc, o);
       }
-      e2 = __fadd_ru(e2, __fmul_ru(fabsf(L), wm[n]));
-    } else {
-      acc = fmaf(L, bj, fmaf(a, lm, acc));
     }
   }
-  if (CERT) {
-    for (int o = 16; o > 0; o >>= 1) {
-      acc = __fadd_rd(acc, __shfl_xor_sync(0xffffffffu, acc, o));
-      e1 = __fadd_ru(e1, __shfl_xor_sync(0xffffffffu, e1, o));
-      e2 = __fadd_ru(e2, __shfl_xor_sync(0xffffffffu, e2, o));
-    }
+  if (WPR > 1) {
+    // the row's warps combine their sums (same rounding directions)
     if (lane == 0) {
+      red[w][0] = acc;
+      red[w][1] = e1;
+      red[w][2] = e2;
+    }
+    __syncthreads();
+    if (live && sub == 0 && lane == 0)
+      for (int q = 1; q < WPR; ++q) {
+        if (CERT) {
+          acc = __fadd_rd(acc, red[w + q][0]);
+          e1 = __fadd_ru(e1, red[w + q][1]);
+          e2 = __fadd_ru(e2, red[w + q][2]);
+        } else {
+          acc += red[w + q][0];
+        }
+      }
+  }
+  if (live && sub == 0 && lane == 0) {
+    if (CERT) {
       cd[rl] = __dadd_rd(cd[rl], (double)acc);
       E[rl] = __dadd_ru(E[rl], __dadd_ru((double)e1, __dmul_ru(gamma, (double)e2)));
+    } else {
+      cf[rl] += acc;
     }
-  } else {
-    acc = warp_sum(acc);
-    if (lane == 0) cf[rl] += acc;
   }
 }
 
@@ -1052,10 +1086,19 @@ void launch_relax(bool cert, const RowsCtx& c, int layer, int d, long long hoff,
                   const float* bias, const float* alpha, int64_t n_alpha, const float* beta, int64_t n_beta, float* cf,
                   double* cd, double* E, const float* wm, double gamma, cudaStream_t s) {
   if (c.R <= 0) return;
-  if (cert)
-    { k_relax<true><<<(c.R + RELAX_ROWS - 1) / RELAX_ROWS, 32 * RELAX_ROWS, 0, s>>>(c, layer, d, hoff, Ain, Lam, bias, alpha, n_alpha, beta, n_beta, cf, cd, E, wm, gamma); ++g_launches; }
+  // one warp per row up to 2048 neurons, a whole block per row beyond
+  const bool wide = d > 2048;
+  const int rpb = wide ? 1 : RELAX_WARPS;
+  const int grid = (c.R + rpb - 1) / rpb;
+  if (cert && wide)
+    k_relax<true, RELAX_WARPS><<<grid, 32 * RELAX_WARPS, 0, s>>>(c, layer, d, hoff, Ain, Lam, bias, alpha, n_alpha, beta, n_beta, cf, cd, E, wm, gamma);
+  else if (cert)
+    k_relax<true, 1><<<grid, 32 * RELAX_WARPS, 0, s>>>(c, layer, d, hoff, Ain, Lam, bias, alpha, n_alpha, beta, n_beta, cf, cd, E, wm, gamma);
+  else if (wide)
+    k_relax<false, RELAX_WARPS><<<grid, 32 * RELAX_WARPS, 0, s>>>(c, layer, d, hoff, Ain, Lam, bias, alpha, n_alpha, beta, n_beta, cf, cd, E, wm, gamma);
   else
-    { k_relax<false><<<(c.R + RELAX_ROWS - 1) / RELAX_ROWS, 32 * RELAX_ROWS, 0, s>>>(c, layer, d, hoff, Ain, Lam, bias, alpha, n_alpha, beta, n_beta, cf, cd, E, wm, gamma); ++g_launches; }
+    k_relax<false, 1><<<grid, 32 * RELAX_WARPS, 0, s>>>(c, layer, d, hoff, Ain, Lam, bias, alpha, n_alpha, beta, n_beta, cf, cd, E, wm, gamma);
+  ++g_launches;
 }
 
 void launch_sgemm(int M, int N, int K, const float* A, int lda, const float* B, int ldb, float* C, int ldc,
