@@ -56,12 +56,17 @@ enum { BCROWN_LAYER_FC = 0, BCROWN_LAYER_CONV = 1 };
 /* Arithmetic of a bound pass.
  *  FP32    : FP32 coefficients and products, FP32 accumulation.
  *  BF16    : A.W contractions with BF16 operands and FP32 accumulation on the
- *            tensor cores (fully connected layers); everything else FP32.  Any
- *            alpha, beta gives a valid bound (Section 3.1), so this is used for
- *            the optimisation iterations.
+ *            tensor cores; everything else FP32.  Fully connected networks (hidden
+ *            widths <= 256, at most 1536 hidden neurons, input <= 1024) run one fused
+ *            kernel per call; networks with conv layers (<= 256 channels) run their
+ *            conv layers as tensor-core GEMMs over an im2col operand and their fully
+ *            connected layers in FP32.  Any alpha, beta gives a valid bound (Section
+ *            3.1), so this is used for the optimisation iterations.  Other networks
+ *            get BCROWN_ERR_UNIMPLEMENTED.
  *  CERTIFY : FP32 contractions plus a priori rounding-error terms, upper-chord
- *            constants rounded outward and FP64 round-down sums; the result is
- *            a lower bound of the exact-arithmetic bound at the same alpha, beta. */
+ *            constants rounded outward and sums rounded down (error terms rounded
+ *            up); the result is a lower bound of the exact-arithmetic bound at the
+ *            same alpha, beta. */
 enum { BCROWN_FP32 = 0, BCROWN_BF16 = 1, BCROWN_CERTIFY = 2 };
 
 /* Lower slope rule for root (intermediate) bounds: ADAPTIVE takes alpha' = 1

@@ -61,6 +61,9 @@ struct Plan {
   float *a_cur, *ma, *va, *ga, *b_cur, *mb, *vb, *gb, *best_lb, *lb_t;
   char* tc_ws;
   size_t tc_ws_bytes;
+  // BF16 conv layers on the tensor cores: the im2col operand of one chunk (null when unused)
+  char* col = nullptr;
+  size_t col_bytes = 0;
 };
 
 static size_t row_bytes(const bcrown_net* net) {
@@ -71,11 +74,11 @@ static size_t row_bytes(const bcrown_net* net) {
 }
 
 static int make_plan(bcrown_net* net, int P, int R, bool cert, bool opt, int64_t n_alpha, int64_t n_beta,
-                     size_t tc_bytes, Plan& pl) {
+                     size_t tc_bytes, Plan& pl, size_t col_per_row = 0) {
   pl.P = P;
   pl.H = net->H;
   pl.R = R;
-  size_t rb = row_bytes(net);
+  size_t rb = row_bytes(net) + col_per_row;
   long long rc = std::max<long long>(1, (long long)(kChunkBytes / rb));
   pl.Rc = (int)std::min<long long>(std::max(R, 1), rc);
   size_t PH = (size_t)P * std::max(net->H, 1);
@@ -103,6 +106,10 @@ static int make_plan(bcrown_net* net, int P, int R, bool cert, bool opt, int64_t
   pl.cf = ar.take<float>(pl.Rc);
   pl.cd = ar.take<double>(pl.Rc);
   pl.E = ar.take<double>(pl.Rc);
+  if (col_per_row) {
+    pl.col_bytes = (size_t)pl.Rc * col_per_row;
+    pl.col = ar.take<char>(pl.col_bytes);
+  }
   if (opt) {
     pl.a_cur = ar.take<float>(n_alpha);
     pl.ma = ar.take<float>(n_alpha);
@@ -151,29 +158,39 @@ static RowsCtx ctx_of(bcrown_net* net, const bcrown_domain* dom, const bcrown_ba
 }
 
 // Backward contraction of layer i: Aout = Lam W^(i) (fc) or transposed convolution.
-static void contract_bwd(bcrown_net* net, int i, int Rc, const float* Lam, float* Aout, cudaStream_t s) {
+// tc: conv layers as BF16 tensor-core GEMMs over an im2col operand in pl.col (BF16 precision).
+static int contract_bwd(bcrown_net* net, int i, int Rc, const float* Lam, float* Aout, cudaStream_t s,
+                        const Plan* tc = nullptr) {
   ProfScope ps(net, BCROWN_PROF_CONTRACT, s);
   const LayerDev& l = net->ly[i - 1];
   if (l.kind == BCROWN_LAYER_FC)
     launch_sgemm(Rc, l.d_in, l.d_out, Lam, l.d_out, l.W, l.d_in, Aout, l.d_in, nullptr, s);
+  else if (tc)
+    return tcg_conv(net, i, false, Rc, Lam, Aout, nullptr, tc->col, tc->col_bytes, s);
   else
     launch_conv_bwd(Rc, geom_of(l), Lam, l.W, Aout, s);
+  return BCROWN_OK;
 }
 
 // Forward contraction of layer i: Z = h W^(i)^T + b^(i).
-static void contract_fwd(bcrown_net* net, int i, int Rc, const float* h, float* Z, cudaStream_t s) {
+static int contract_fwd(bcrown_net* net, int i, int Rc, const float* h, float* Z, cudaStream_t s,
+                        const Plan* tc = nullptr) {
   ProfScope ps(net, BCROWN_PROF_CONTRACT, s);
   const LayerDev& l = net->ly[i - 1];
   if (l.kind == BCROWN_LAYER_FC)
     launch_sgemm(Rc, l.d_out, l.d_in, h, l.d_in, l.Wt, l.d_out, Z, l.d_out, l.b, s);
+  else if (tc)
+    return tcg_conv(net, i, true, Rc, h, Z, l.b, tc->col, tc->col_bytes, s);
   else
     launch_conv_fwd(Rc, geom_of(l), h, l.W, l.b, Z, s);
+  return BCROWN_OK;
 }
 
 // One chunk of rows: bound (and optionally the gradient) with the SIMT path.
-static void chunk_simt(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* bt, Plan& pl, int r0, int Rc,
-                       bool cert, bool grad, const float* alpha, const float* beta, float* lb, float* dalpha,
-                       float* dbeta, cudaStream_t s) {
+static int chunk_simt(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* bt, Plan& pl, int r0, int Rc,
+                      bool cert, bool grad, const float* alpha, const float* beta, float* lb, float* dalpha,
+                      float* dbeta, cudaStream_t s, bool tc_conv = false) {
+  const Plan* tc = tc_conv ? &pl : nullptr;
   RowsCtx c = ctx_of(net, dom, bt, pl, r0, Rc);
   const int L = net->L;
   long long hoff_top = L >= 2 ? net->hoff[L - 2] : -1;
@@ -185,22 +202,23 @@ static void chunk_simt(bcrown_net* net, const bcrown_domain* dom, const bcrown_b
       launch_relax(cert, c, i, net->d[i], net->hoff[i - 1], pl.Abuf[i], pl.Lam, ly.b, alpha, bt->n_alpha, beta, bt->n_beta, pl.cf,
                  pl.cd, pl.E, pl.wm, gamma_n(ly.terms_bwd), s);
     }
-    contract_bwd(net, i, Rc, pl.Lam, pl.Abuf[i - 1], s);
+    BC_CHECK(contract_bwd(net, i, Rc, pl.Lam, pl.Abuf[i - 1], s, tc));
   }
   {
     ProfScope ps(net, BCROWN_PROF_CONCRETIZE, s);
     launch_concretize(cert, c, net->d[0], pl.Abuf[0], pl.cf, pl.cd, pl.E, lb, s);
   }
-  if (!grad) return;
+  if (!grad) return BCROWN_OK;
   launch_xstar(c, net->d[0], pl.Abuf[0], pl.Z0, s);
   float* h = pl.Z0;
   float* z = pl.Z1;
   for (int i = 1; i <= L - 1; ++i) {
-    contract_fwd(net, i, Rc, h, z, s);
+    BC_CHECK(contract_fwd(net, i, Rc, h, z, s, tc));
     ProfScope ps(net, BCROWN_PROF_ADJOINT, s);
     launch_fwd_epi(c, i, net->d[i], net->hoff[i - 1], z, pl.Abuf[i], alpha, bt->n_alpha, dalpha, dbeta, bt->n_beta, s);
     std::swap(h, z);
   }
+  return BCROWN_OK;
 }
 
 // tc_plan: group the batch's rows into property tiles first (false when an earlier call on the
@@ -213,9 +231,12 @@ static int run_bound(bcrown_net* net, const bcrown_domain* dom, const bcrown_bat
     return tc_bound(net, dom, bt, pl.tb, pl.tc_ws, pl.tc_ws_bytes, grad, tc_plan, alpha, beta, lb, dalpha, dbeta, s);
   }
   bool cert = precision == BCROWN_CERTIFY;
+  // BF16 on a conv net: conv contractions on the tensor cores (the rest of the layer-by-layer path
+  // stays FP32); planned when the plan has an im2col buffer
+  const bool tc_conv = precision == BCROWN_BF16 && pl.col != nullptr;
   for (int r0 = 0; r0 < R; r0 += pl.Rc) {
     int Rc = std::min(pl.Rc, R - r0);
-    chunk_simt(net, dom, bt, pl, r0, Rc, cert, grad, alpha, beta, lb, dalpha, dbeta, s);
+    BC_CHECK(chunk_simt(net, dom, bt, pl, r0, Rc, cert, grad, alpha, beta, lb, dalpha, dbeta, s, tc_conv));
   }
   return BCROWN_OK;
 }
@@ -224,8 +245,10 @@ static int check_precision(bcrown_net* net, int precision, bool grad) {
   if (precision != BCROWN_FP32 && precision != BCROWN_BF16 && precision != BCROWN_CERTIFY)
     return fail(BCROWN_ERR_ARG, "unknown precision");
   if (grad && precision == BCROWN_CERTIFY) return fail(BCROWN_ERR_ARG, "gradient in CERTIFY precision is not offered");
-  if (precision == BCROWN_BF16 && !tc_supported(net))
-    return fail(BCROWN_ERR_UNIMPLEMENTED, "BF16 tensor-core path needs a fully connected network with supported widths");
+  if (precision == BCROWN_BF16 && !tc_supported(net) && !tcg_supported(net))
+    return fail(BCROWN_ERR_UNIMPLEMENTED,
+                "BF16 tensor-core path needs a fully connected network with supported widths or conv layers of at "
+                "most 256 channels");
   return BCROWN_OK;
 }
 
@@ -244,7 +267,8 @@ extern "C" int bcrown_bound(bcrown_net* net, const bcrown_domain* dom, const bcr
   Plan pl;
   int R = batch->B * net->K;
   size_t tcb = precision == BCROWN_BF16 ? tc_workspace_bytes(net, batch->B, dom->n_props, false) : 0;
-  BC_CHECK(make_plan(net, dom->n_props, R, precision == BCROWN_CERTIFY, false, 0, 0, tcb, pl));
+  BC_CHECK(make_plan(net, dom->n_props, R, precision == BCROWN_CERTIFY, false, 0, 0, tcb, pl,
+                     precision == BCROWN_BF16 && tcg_supported(net) ? tcg_col_bytes_per_row(net) : 0));
   build_tables(net, dom, pl, s);
   if (precision == BCROWN_CERTIFY) build_wm(net, dom, pl, s);
   BC_CHECK(run_bound(net, dom, batch, pl, precision, false, alpha, beta, lb, nullptr, nullptr, s));
@@ -267,7 +291,8 @@ extern "C" int bcrown_bound_grad(bcrown_net* net, const bcrown_domain* dom, cons
   Plan pl;
   int R = batch->B * net->K;
   size_t tcb = precision == BCROWN_BF16 ? tc_workspace_bytes(net, batch->B, dom->n_props, true) : 0;
-  BC_CHECK(make_plan(net, dom->n_props, R, false, false, 0, 0, tcb, pl));
+  BC_CHECK(make_plan(net, dom->n_props, R, false, false, 0, 0, tcb, pl,
+                     precision == BCROWN_BF16 && tcg_supported(net) ? tcg_col_bytes_per_row(net) : 0));
   build_tables(net, dom, pl, s);
   BC_CHECK(run_bound(net, dom, batch, pl, precision, true, alpha, beta, lb, dalpha, dbeta, s));
   BC_CUDA(cudaGetLastError());
@@ -291,7 +316,8 @@ extern "C" int bcrown_optimize(bcrown_net* net, const bcrown_domain* dom, const 
   Plan pl;
   size_t tcb = cfg->precision == BCROWN_BF16 ? tc_workspace_bytes(net, batch->B, dom->n_props, true) : 0;
   bool cert = cfg->certify != 0;
-  BC_CHECK(make_plan(net, dom->n_props, R, cert, true, na, nb, tcb, pl));
+  BC_CHECK(make_plan(net, dom->n_props, R, cert, true, na, nb, tcb, pl,
+                     cfg->precision == BCROWN_BF16 && tcg_supported(net) ? tcg_col_bytes_per_row(net) : 0));
   build_tables(net, dom, pl, s);
   if (cert) build_wm(net, dom, pl, s);
   if (na) {

@@ -1226,6 +1226,236 @@ __global__ void k_plan_rows(int max_tiles, int K, int P, const int* __restrict__
   if (sl == 0) tile_prop[t] = p;
 }
 
+// ------------------------------------------------------------------------------------------
+// Convolutions on the tensor cores (BF16 precision of the layer-by-layer path): the contraction
+// of a conv layer as one GEMM over an im2col operand.
+//   backward:  Ain[r][ci][p] = sum_K Col[(r, p)][K] Wb[ci][K],   K = (co, ky, kx)
+//   forward:   Z[r][co][p]   = sum_K Col[(r, p)][K] Wf[co][K] + b, K = (ci, ky, kx)
+// Col is gathered into BF16 (zero where a tap falls outside the map or off the stride grid) by
+// k_im2col_*; k_tcg multiplies it with the BF16 weights: M = rows x positions (tiles of 128 on
+// the TMEM lanes), N = channels (padded to 16), K in blocks of 64 streamed by TMA.
+// ------------------------------------------------------------------------------------------
+constexpr int TCG_NS = 4;         // pipeline stages (A: 128 x 64, B: Np x 64)
+constexpr int TCG_THREADS = 192;  // warps 0-3 epilogue, 4 TMA, 5 MMA
+
+// Backward im2col: 32 consecutive rows m per block.  Lanes walk the 32 positions for one K at a
+// time (K uniform per warp: coalesced reads of Lambda), into a shared tile [32][Kp + 8]; the
+// tile's rows then leave in 16-byte stores.
+constexpr int IM2COL_ROWS = 32;
+constexpr int IM2COL_MAX_KP = 2048;
+__global__ void __launch_bounds__(256) k_im2col_bwd(long long M, int P, LayerGeom g, int Kp,
+                                                    const float* __restrict__ Lam,
+                                                    __nv_bfloat16* __restrict__ col) {
+  extern __shared__ __align__(16) uint8_t im_raw[];
+  __nv_bfloat16* tile = reinterpret_cast<__nv_bfloat16*>(im_raw);
+  const int S = Kp + 8;   // row stride (bf16): keeps 16-byte alignment, spreads the banks
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long m0 = (long long)blockIdx.x * IM2COL_ROWS;
+  const long long m = m0 + lane;
+  const bool mv = m < M;
+  const int r = mv ? (int)(m / P) : 0;
+  const int pos = mv ? (int)(m - (long long)r * P) : 0;
+  const int iy = pos / g.in_w, ix = pos - (pos / g.in_w) * g.in_w;
+  const int kk = g.k * g.k, hw_out = g.out_h * g.out_w, Kr = g.out_c * kk;
+  const float* lr = Lam + (size_t)r * g.d_out;
+  for (int K = w; K < Kp; K += 8) {
+    float x = 0.f;
+    if (K < Kr) {
+      const int co = K / kk, t = K - co * kk, ky = t / g.k, kx = t - (t / g.k) * g.k;
+      const int ty = iy + g.pad - ky, tx = ix + g.pad - kx;
+      if (mv && ty >= 0 && tx >= 0 && ty % g.stride == 0 && tx % g.stride == 0) {
+        const int oy = ty / g.stride, ox = tx / g.stride;
+        if (oy < g.out_h && ox < g.out_w) x = lr[(size_t)co * hw_out + oy * g.out_w + ox];
+      }
+    }
+    tile[lane * S + K] = __float2bfloat16_rn(x);
+  }
+  __syncthreads();
+  const int cpr = Kp / 8;
+  for (int e = threadIdx.x; e < IM2COL_ROWS * cpr; e += 256) {
+    const int row = e / cpr, c = e - (e / cpr) * cpr;
+    if (m0 + row < M)
+      *reinterpret_cast<uint4*>(col + (m0 + row) * Kp + c * 8) = *reinterpret_cast<const uint4*>(tile + row * S + c * 8);
+  }
+}
+
+__global__ void k_im2col_fwd(long long M, int P, LayerGeom g, int Kp, const float* __restrict__ h,
+                             __nv_bfloat16* __restrict__ col) {
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int kc = Kp / 8;
+  if (id >= M * kc) return;
+  const long long m = id / kc;
+  const int K0 = (int)(id - m * kc) * 8;
+  const int r = (int)(m / P), pos = (int)(m - (long long)r * P);
+  const int oy = pos / g.out_w, ox = pos - (pos / g.out_w) * g.out_w;
+  const int kk = g.k * g.k, hw_in = g.in_h * g.in_w;
+  const float* hr = h + (size_t)r * g.d_in;
+  uint32_t pk[4];
+#pragma unroll
+  for (int e = 0; e < 8; e += 2) {
+    float v[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int K = K0 + e + q;
+      float x = 0.f;
+      if (K < g.in_c * kk) {
+        const int ci = K / kk, t = K - ci * kk, ky = t / g.k, kx = t - (t / g.k) * g.k;
+        const int iy = oy * g.stride - g.pad + ky, ix = ox * g.stride - g.pad + kx;
+        if (iy >= 0 && iy < g.in_h && ix >= 0 && ix < g.in_w) x = hr[(size_t)ci * hw_in + iy * g.in_w + ix];
+      }
+      v[q] = x;
+    }
+    __nv_bfloat162 b2 = __floats2bfloat162_rn(v[0], v[1]);
+    pk[e >> 1] = *reinterpret_cast<uint32_t*>(&b2);
+  }
+  *reinterpret_cast<uint4*>(col + m * Kp + K0) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+}
+
+// Bounded wait for k_tcg (same limit and error reporting as mbar_wait).
+__device__ __forceinline__ bool tcg_wait(uint64_t* b, uint32_t parity, volatile int* abort, int* status) {
+  if (mbar_try(b, parity)) return true;
+  long long t0 = clock64();
+  while (true) {
+    if (mbar_try_sleep(b, parity, 20000u)) return true;
+    if (*abort) return false;
+    if (clock64() - t0 > 4000000000LL) {
+      atomicCAS(status, 0, BCROWN_ERR_TIMEOUT);
+      *abort = 1;
+      return false;
+    }
+  }
+}
+
+// out[r * stride + n * P + p] = (Col x W^T)[m = r * P + p][n] (+ bias[n * P + p]) for n < N.
+__global__ void __launch_bounds__(TCG_THREADS, 1) k_tcg(const __grid_constant__ CUtensorMap mapA,
+                                                        const __grid_constant__ CUtensorMap mapB, long long M, int N,
+                                                        int Np, int nkb, int P, long long stride,
+                                                        float* __restrict__ out, const float* __restrict__ bias,
+                                                        int* status) {
+  extern __shared__ __align__(1024) uint8_t tsm_raw[];
+  const uint32_t pad = (1024u - (su32(tsm_raw) & 1023u)) & 1023u;
+  uint8_t* base = tsm_raw + pad;
+  const int bbytes = Np * 128;
+  uint8_t* sA = base;                                  // TCG_NS x 16 KB
+  uint8_t* sB = base + TCG_NS * 16384;                 // TCG_NS x Np*128
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + TCG_NS * bbytes);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + TCG_NS;
+  uint64_t* acc_full = bars + 2 * TCG_NS;
+  uint64_t* acc_empty = bars + 2 * TCG_NS + 2;
+  uint32_t* tbase_sm = reinterpret_cast<uint32_t*>(bars + 2 * TCG_NS + 4);
+  volatile int* abort = reinterpret_cast<volatile int*>(tbase_sm + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long ntiles = (M + 127) / 128;
+  // two accumulators of Np columns, allocated as a power of two >= 32
+  const uint32_t tcols = Np <= 16 ? 32u : (Np <= 32 ? 64u : (Np <= 64 ? 128u : (Np <= 128 ? 256u : 512u)));
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < TCG_NS; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&acc_full[i], 1);
+      mbar_init(&acc_empty[i], 4);
+    }
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 5) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tbase_sm)), "r"(tcols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tbase_sm;
+  if (warp == 4) {
+    if (lane == 0) {
+      uint32_t seq = 0;
+      bool ok = true;
+      for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x)
+        for (int kb = 0; kb < nkb; ++kb, ++seq) {
+          const int st = seq % TCG_NS;
+          if (!tcg_wait(&empty[st], ((seq / TCG_NS) & 1) ^ 1, abort, status)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&full[st], 16384u + (uint32_t)bbytes);
+          tma_load_2d(sA + st * 16384, &mapA, kb * 64, (int)(tile * 128), &full[st]);
+          tma_load_2d(sB + st * bbytes, &mapB, kb * 64, 0, &full[st]);
+        }
+      if (!ok) {
+        for (uint32_t q = (seq > TCG_NS ? seq - TCG_NS : 0); q < seq; ++q) {
+          long long t0 = clock64();
+          while (!mbar_try(&full[q % TCG_NS], (q / TCG_NS) & 1) && clock64() - t0 < 200000000LL) {
+          }
+        }
+      }
+    }
+  } else if (warp == 5) {
+    if (lane == 0) {
+      uint32_t seq = 0, accseq = 0;
+      bool ok = true;
+      const uint32_t idesc = idesc_bf16(Np);
+      for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++accseq) {
+        const int buf = accseq & 1;
+        if (!tcg_wait(&acc_empty[buf], ((accseq >> 1) & 1) ^ 1, abort, status)) break;
+        tc_fence_after();
+        const uint32_t dt = tmem + (uint32_t)(buf * Np);
+        for (int kb = 0; kb < nkb; ++kb, ++seq) {
+          const int st = seq % TCG_NS;
+          if (!tcg_wait(&full[st], (seq / TCG_NS) & 1, abort, status)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          umma_kblock(dt, sdesc(su32(sA + st * 16384)), sdesc(su32(sB + st * bbytes)), idesc, kb != 0 ? 1u : 0u);
+          umma_commit(&empty[st]);
+        }
+        if (!ok) break;
+        umma_commit(&acc_full[buf]);
+      }
+    }
+  } else {
+    // epilogue: warp w owns TMEM lanes (tile rows) 32w..32w+31
+    uint32_t accseq = 0;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++accseq) {
+      const int buf = accseq & 1;
+      int okw = 1;
+      if (lane == 0) okw = tcg_wait(&acc_full[buf], (accseq >> 1) & 1, abort, status) ? 1 : 0;
+      okw = __shfl_sync(0xffffffffu, okw, 0);
+      if (!okw) break;
+      tc_fence_after();
+      const long long m = tile * 128 + 32 * warp + lane;
+      const bool min_ = m < M;
+      const long long r = min_ ? m / P : 0;
+      const int p = min_ ? (int)(m - r * P) : 0;
+      float* orow = out + r * stride + p;
+      for (int n0 = 0; n0 < Np; n0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(buf * Np + n0), v);
+        if (min_) {
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const int n = n0 + e;
+            if (n < N) orow[(size_t)n * P] = v[e] + (bias ? bias[(size_t)n * P + p] : 0.f);
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[buf]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 5) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols) : "memory");
+  }
+}
+
 }  // namespace tc
 
 // ------------------------------------------------------------------------------------------
@@ -1241,6 +1471,13 @@ struct TcNet {
   int box_fwd[MAXL + 1] = {0};
   int woff[MAXL + 1] = {0};
   int mask_words = 0;
+  // conv layers on the tensor cores: BF16 weight matrices [Np][Kp] for the backward (rows =
+  // input channels) and the forward (rows = output channels), with their TMA maps
+  bool conv_ready = false;
+  struct ConvW {
+    int Np_b = 0, Kp_b = 0, Np_f = 0, Kp_f = 0;
+    CUtensorMap mb, mf;
+  } conv[MAXL + 1];
 };
 
 static std::mutex g_tc_mu;
@@ -1461,6 +1698,121 @@ int tc_bound(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* bt, 
   A.dalpha16 = dalpha16;
   A.dbeta = dbeta;
   return tc_launch(net, dom, bt, tb, A, ws, ws_bytes, !grad ? 0 : (dalpha16 ? 2 : 1), plan, s);
+}
+
+// ---------------------------------------------------------------- conv layers on tensor cores
+static int pad_to(int x, int m) { return (x + m - 1) / m * m; }
+
+bool tcg_supported(const bcrown_net* net) {
+  bool conv = false;
+  for (int i = 0; i < net->L; ++i) {
+    const LayerDev& l = net->ly[i];
+    if (l.kind != BCROWN_LAYER_CONV) continue;
+    conv = true;
+    if (pad_to(l.in_c, 16) > 256 || pad_to(l.out_c, 16) > 256) return false;
+    if (pad_to(l.out_c * l.k * l.k, 64) > IM2COL_MAX_KP) return false;
+  }
+  if (!conv) return false;
+  int dev = 0, major = 0, minor = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  cudaGetLastError();
+  return major == 10 && minor == 3;
+}
+
+size_t tcg_col_bytes_per_row(const bcrown_net* net) {
+  size_t b = 0;
+  for (int i = 0; i < net->L; ++i) {
+    const LayerDev& l = net->ly[i];
+    if (l.kind != BCROWN_LAYER_CONV) continue;
+    const size_t kk = (size_t)l.k * l.k;
+    const size_t bwd = (size_t)l.in_h * l.in_w * pad_to((int)(l.out_c * kk), 64);
+    const size_t fwd = (size_t)l.out_h * l.out_w * pad_to((int)(l.in_c * kk), 64);
+    b = std::max(b, std::max(bwd, fwd) * sizeof(__nv_bfloat16));
+  }
+  return b;
+}
+
+static int tcg_prepare(bcrown_net* net, TcNet* t) {
+  if (t->conv_ready) return BCROWN_OK;
+  for (int i = 1; i <= net->L; ++i) {
+    const LayerDev& l = net->ly[i - 1];
+    if (l.kind != BCROWN_LAYER_CONV) continue;
+    const int kk = l.k * l.k;
+    std::vector<float> w((size_t)l.out_c * l.in_c * kk);
+    if (cudaMemcpy(w.data(), l.W, w.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(BCROWN_ERR_CUDA, "copy of conv weights");
+    TcNet::ConvW& c = t->conv[i];
+    c.Np_b = pad_to(l.in_c, 16);
+    c.Kp_b = pad_to(l.out_c * kk, 64);
+    c.Np_f = pad_to(l.out_c, 16);
+    c.Kp_f = pad_to(l.in_c * kk, 64);
+    std::vector<__nv_bfloat16> wb((size_t)c.Np_b * c.Kp_b, __float2bfloat16_rn(0.f));
+    std::vector<__nv_bfloat16> wf((size_t)c.Np_f * c.Kp_f, __float2bfloat16_rn(0.f));
+    for (int co = 0; co < l.out_c; ++co)
+      for (int ci = 0; ci < l.in_c; ++ci)
+        for (int q = 0; q < kk; ++q) {
+          const __nv_bfloat16 v = __float2bfloat16_rn(w[((size_t)co * l.in_c + ci) * kk + q]);
+          wb[(size_t)ci * c.Kp_b + co * kk + q] = v;   // backward: K = (co, tap)
+          wf[(size_t)co * c.Kp_f + ci * kk + q] = v;   // forward:  K = (ci, tap)
+        }
+    __nv_bfloat16 *db = nullptr, *df = nullptr;
+    if (cudaMalloc(&db, wb.size() * 2) != cudaSuccess || cudaMalloc(&df, wf.size() * 2) != cudaSuccess)
+      return fail(BCROWN_ERR_OOM, "bf16 conv weights");
+    t->bufs.push_back(db);
+    t->bufs.push_back(df);
+    if (cudaMemcpy(db, wb.data(), wb.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(df, wf.data(), wf.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail(BCROWN_ERR_CUDA, "bf16 conv weights upload");
+    BC_CHECK(encode_map(&c.mb, db, c.Np_b, c.Kp_b, c.Np_b));
+    BC_CHECK(encode_map(&c.mf, df, c.Np_f, c.Kp_f, c.Np_f));
+  }
+  const int smem = 1024 + TCG_NS * (16384 + 256 * 128) + 256;
+  BC_CUDA(cudaFuncSetAttribute(k_tcg, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  BC_CUDA(cudaFuncSetAttribute(k_im2col_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               IM2COL_ROWS * (IM2COL_MAX_KP + 8) * (int)sizeof(__nv_bfloat16)));
+  t->conv_ready = true;
+  return BCROWN_OK;
+}
+
+int tcg_conv(bcrown_net* net, int i, bool fwd, int R, const float* src, float* dst, const float* bias, char* col,
+             size_t col_bytes, cudaStream_t s) {
+  TcNet* t = tc_of(net);
+  BC_CHECK(tcg_prepare(net, t));
+  const LayerDev& l = net->ly[i - 1];
+  const LayerGeom g = geom_of(l);
+  const TcNet::ConvW& c = t->conv[i];
+  const int P = fwd ? l.out_h * l.out_w : l.in_h * l.in_w;
+  const int N = fwd ? l.out_c : l.in_c;
+  const int Np = fwd ? c.Np_f : c.Np_b;
+  const int Kp = fwd ? c.Kp_f : c.Kp_b;
+  const long long M = (long long)R * P;
+  if (M <= 0) return BCROWN_OK;
+  if ((size_t)M * Kp * sizeof(__nv_bfloat16) > col_bytes) return fail(BCROWN_ERR_OOM, "im2col workspace too small");
+  __nv_bfloat16* cb = reinterpret_cast<__nv_bfloat16*>(col);
+  const long long nthr = M * (Kp / 8);
+  if (fwd) {
+    k_im2col_fwd<<<(unsigned)((nthr + 255) / 256), 256, 0, s>>>(M, P, g, Kp, src, cb);
+  } else {
+    const int smem = IM2COL_ROWS * (Kp + 8) * (int)sizeof(__nv_bfloat16);
+    k_im2col_bwd<<<(unsigned)((M + IM2COL_ROWS - 1) / IM2COL_ROWS), 256, smem, s>>>(M, P, g, Kp, src, cb);
+  }
+  ++g_launches;
+  CUtensorMap mA;
+  BC_CHECK(encode_map(&mA, cb, (int)M, Kp, 128));
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long ntiles = (M + 127) / 128;
+  const int grid = (int)std::min<long long>(ntiles, 2LL * sms);
+  const int smem = 1024 + TCG_NS * (16384 + Np * 128) + 256;
+  k_tcg<<<grid, TCG_THREADS, smem, s>>>(mA, fwd ? c.mf : c.mb, M, N, Np, Kp / 64, P,
+                                        fwd ? (long long)l.d_out : (long long)l.d_in, dst, fwd ? bias : nullptr,
+                                        net->status);
+  ++g_launches;
+  BC_CUDA(cudaGetLastError());
+  return BCROWN_OK;
 }
 
 void tc_release(const bcrown_net* net) {

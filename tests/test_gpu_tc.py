@@ -162,3 +162,52 @@ def test_batching_64_properties_sampled():
     _, ra, rb = repack(pb, batch, U, idx, at.cpu().numpy(), bt.cpu().numpy())
     ref_opt = O.bound(onet, props, sub, ra, rb).reshape(len(idx), pb.K)
     assert np.all(lbc[rows] <= ref_opt + 1e-12 * np.abs(ref_opt))
+
+
+def _tiny_conv():
+    layers = wl.conv_layers((2, 6, 6), [(3, 3, 2, 1), (4, 3, 1, 1)], [8, 4], 3)
+    return wl.make_problem("tinyconv", layers, 2, 0.1, 3, 3)
+
+
+@pytest.mark.parametrize("which", ["tiny", "c3"])
+def test_bf16_conv_bound_and_gradient_close_to_oracle(which):
+    """Conv layers as BF16 tensor-core GEMMs over an im2col operand: a tiny net (channel counts
+    and K far below one tile, stride 2, two properties) and the c3 net (4x4 kernels, stride 2)."""
+    if which == "tiny":
+        pb = _tiny_conv()
+        onet, props, unst = oracle_setup(pb)
+        batch = wl.random_batch(pb, unst, 24, 0, 4, 1, props=np.arange(24) % 2)
+    else:
+        pb = wl.problem_conv_small()
+        onet, props, unst = oracle_setup(pb)
+        batch = wl.tree_batch(pb, unst, [24], 16, 7)
+    a, b = wl.random_alpha_beta(batch, 3, 1.0)
+    net, dom, db = _gpu(pb, props, batch)
+    lb = bc.bound(net, dom, db, _t(a), _t(b), bc.BF16).cpu().numpy()
+    assert bc.status(net) == 0
+    ref = O.bound(onet, props, batch, a, b)
+    err = np.abs(lb - ref) / _scale(ref)
+    print("bf16 conv bound: max err / median|lb| = %.3e" % err.max())
+    assert err.max() <= BF16_TOL
+    lbg, da, dbeta = bc.bound_grad(net, dom, db, _t(a), _t(b), bc.BF16)
+    assert bc.status(net) == 0
+    ref_g, da_ref, db_ref = O.grad(onet, props, batch, a.astype(np.float64), b.astype(np.float64))
+    for g, gr in ((da.cpu().numpy(), da_ref), (dbeta.cpu().numpy(), db_ref)):
+        rel = np.linalg.norm(g - gr) / max(np.linalg.norm(gr), 1e-12)
+        print("bf16 conv gradient relative error %.3e" % rel)
+        assert rel <= 5e-2
+
+
+def test_bf16_conv_optimize_is_certified():
+    pb = wl.problem_conv_small()
+    onet, props, unst = oracle_setup(pb)
+    batch = wl.tree_batch(pb, unst, [16], 16, 5)
+    a0, b0 = wl.initial_alpha_beta(batch)
+    net, dom, db = _gpu(pb, props, batch)
+    at, bt = _t(a0), _t(b0)
+    lb = bc.optimize(net, dom, db, at, bt, bc.OptCfg(precision=bc.BF16, certify=True)).cpu().numpy()
+    assert bc.status(net) == 0
+    ref = O.bound(onet, props, batch, at.cpu().numpy(), bt.cpu().numpy())
+    assert np.all(lb <= ref + 1e-12 * np.abs(ref))
+    init = O.bound(onet, props, batch, a0, b0)
+    assert np.mean(lb - init) > 0
