@@ -1228,88 +1228,84 @@ __global__ void k_plan_rows(int max_tiles, int K, int P, const int* __restrict__
 
 // ------------------------------------------------------------------------------------------
 // Convolutions on the tensor cores (BF16 precision of the layer-by-layer path): the contraction
-// of a conv layer as one GEMM over an im2col operand.
-//   backward:  Ain[r][ci][p] = sum_K Col[(r, p)][K] Wb[ci][K],   K = (co, ky, kx)
-//   forward:   Z[r][co][p]   = sum_K Col[(r, p)][K] Wf[co][K] + b, K = (ci, ky, kx)
-// Col is gathered into BF16 (zero where a tap falls outside the map or off the stride grid) by
-// k_im2col_*; k_tcg multiplies it with the BF16 weights: M = rows x positions (tiles of 128 on
-// the TMEM lanes), N = channels (padded to 16), K in blocks of 64 streamed by TMA.
+// of a conv layer as GEMMs over an im2col operand.
+//   forward:   Z[r][co][p] = sum_K Col[(r, p)][K] Wf[co][K] + b,   K = (ci, ky, kx)
+//   backward:  the transposed convolution Ain[r][ci][p] = sum Lambda[r][co][q] W[co][ci][tap]
+//              over the (q, tap) with p = q * s - pad + tap.  For stride s the input positions
+//              fall into s x s phases (p_y mod s, p_x mod s); within a phase only the taps
+//              ky = ky0 + s * dy (dy < ceil(k / s)) reach the stride grid, and the source
+//              position is q_y = i + off - dy for the phase's i-th row.  Each phase is one GEMM
+//              with K = (co, dy, dx) and its own weight matrix, so the operand holds no
+//              structural zeros of the stride.
+// Col is gathered into BF16 by k_im2col from a per-K table (source channel offset, signed tap
+// offsets: no divisions in the inner loop); k_tcg multiplies it with the BF16 weights:
+// M = rows x positions (tiles of 128 on the TMEM lanes), N = channels (padded to 16), K in
+// blocks of 64 streamed by TMA.
 // ------------------------------------------------------------------------------------------
 constexpr int TCG_NS = 4;         // pipeline stages (A: 128 x 64, B: Np x 64)
 constexpr int TCG_THREADS = 192;  // warps 0-3 epilogue, 4 TMA, 5 MMA
 
-// Backward im2col: 32 consecutive rows m per block.  Lanes walk the 32 positions for one K at a
-// time (K uniform per warp: coalesced reads of Lambda), into a shared tile [32][Kp + 8]; the
-// tile's rows then leave in 16-byte stores.
+// One gather: row m = (r, pp), pp = i * nJ + j; source position (y0 + dy_K, x0 + dx_K) with
+// y0 = i * ms + cy, x0 = j * ms + cx, in a [C][Hs][Ws] map of row r (d_src floats per row).
+struct Im2colPass {
+  long long M;
+  int Pm, nJ, ms, cy, cx, Hs, Ws, d_src, Kp;
+  const int2* tab;  // [Kp]: {channel offset C * Hs * Ws, or -1 for a zero column; (dy & 0xffff) | dx << 16}
+};
+
+// 32 consecutive rows m per block.  Lanes walk the 32 rows for one pair of K at a time (K
+// uniform per warp: coalesced source reads) into a shared tile [32][Kp + 8], whose rows then
+// leave in 16-byte stores.
 constexpr int IM2COL_ROWS = 32;
 constexpr int IM2COL_MAX_KP = 2048;
-__global__ void __launch_bounds__(256) k_im2col_bwd(long long M, int P, LayerGeom g, int Kp,
-                                                    const float* __restrict__ Lam,
-                                                    __nv_bfloat16* __restrict__ col) {
+inline int im2col_smem(int Kp) { return Kp * (int)sizeof(int2) + IM2COL_ROWS * (Kp + 8) * 2; }
+__global__ void __launch_bounds__(256) k_im2col(Im2colPass q, const float* __restrict__ src,
+                                                __nv_bfloat16* __restrict__ col) {
   extern __shared__ __align__(16) uint8_t im_raw[];
-  __nv_bfloat16* tile = reinterpret_cast<__nv_bfloat16*>(im_raw);
-  const int S = Kp + 8;   // row stride (bf16): keeps 16-byte alignment, spreads the banks
+  const int Kp = q.Kp, S = Kp + 8;  // row stride (bf16), 16-byte aligned rows
+  int2* tab = reinterpret_cast<int2*>(im_raw);
+  __nv_bfloat16* tile = reinterpret_cast<__nv_bfloat16*>(im_raw + (size_t)Kp * sizeof(int2));
+  for (int k = threadIdx.x; k < Kp; k += 256) tab[k] = q.tab[k];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const long long m0 = (long long)blockIdx.x * IM2COL_ROWS;
   const long long m = m0 + lane;
-  const bool mv = m < M;
-  const int r = mv ? (int)(m / P) : 0;
-  const int pos = mv ? (int)(m - (long long)r * P) : 0;
-  const int iy = pos / g.in_w, ix = pos - (pos / g.in_w) * g.in_w;
-  const int kk = g.k * g.k, hw_out = g.out_h * g.out_w, Kr = g.out_c * kk;
-  const float* lr = Lam + (size_t)r * g.d_out;
-  for (int K = w; K < Kp; K += 8) {
-    float x = 0.f;
-    if (K < Kr) {
-      const int co = K / kk, t = K - co * kk, ky = t / g.k, kx = t - (t / g.k) * g.k;
-      const int ty = iy + g.pad - ky, tx = ix + g.pad - kx;
-      if (mv && ty >= 0 && tx >= 0 && ty % g.stride == 0 && tx % g.stride == 0) {
-        const int oy = ty / g.stride, ox = tx / g.stride;
-        if (oy < g.out_h && ox < g.out_w) x = lr[(size_t)co * hw_out + oy * g.out_w + ox];
-      }
+  const bool mv = m < q.M;
+  const int r = mv ? (int)(m / q.Pm) : 0;
+  const int pp = mv ? (int)(m - (long long)r * q.Pm) : 0;
+  const int i = pp / q.nJ, j = pp - (pp / q.nJ) * q.nJ;
+  const int y0 = i * q.ms + q.cy, x0 = j * q.ms + q.cx;
+  const float* sr = src + (size_t)r * q.d_src;
+  __syncthreads();
+  for (int K = 2 * w; K < Kp; K += 16) {
+    float v[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int2 t = tab[K + e];
+      const int y = y0 + (int)(short)(t.y & 0xffff), x = x0 + (t.y >> 16);
+      v[e] = (mv && t.x >= 0 && (unsigned)y < (unsigned)q.Hs && (unsigned)x < (unsigned)q.Ws)
+                 ? sr[t.x + y * q.Ws + x]
+                 : 0.f;
     }
-    tile[lane * S + K] = __float2bfloat16_rn(x);
+    *reinterpret_cast<__nv_bfloat162*>(tile + lane * S + K) = __floats2bfloat162_rn(v[0], v[1]);
   }
   __syncthreads();
   const int cpr = Kp / 8;
-  for (int e = threadIdx.x; e < IM2COL_ROWS * cpr; e += 256) {
-    const int row = e / cpr, c = e - (e / cpr) * cpr;
-    if (m0 + row < M)
-      *reinterpret_cast<uint4*>(col + (m0 + row) * Kp + c * 8) = *reinterpret_cast<const uint4*>(tile + row * S + c * 8);
+  for (int row = w; row < IM2COL_ROWS; row += 8) {
+    if (m0 + row >= q.M) break;
+    uint4* dst = reinterpret_cast<uint4*>(col + (m0 + row) * Kp);
+    const uint4* sv = reinterpret_cast<const uint4*>(tile + row * S);
+    for (int c = lane; c < cpr; c += 32) dst[c] = sv[c];
   }
 }
 
-__global__ void k_im2col_fwd(long long M, int P, LayerGeom g, int Kp, const float* __restrict__ h,
-                             __nv_bfloat16* __restrict__ col) {
-  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int kc = Kp / 8;
-  if (id >= M * kc) return;
-  const long long m = id / kc;
-  const int K0 = (int)(id - m * kc) * 8;
-  const int r = (int)(m / P), pos = (int)(m - (long long)r * P);
-  const int oy = pos / g.out_w, ox = pos - (pos / g.out_w) * g.out_w;
-  const int kk = g.k * g.k, hw_in = g.in_h * g.in_w;
-  const float* hr = h + (size_t)r * g.d_in;
-  uint32_t pk[4];
-#pragma unroll
-  for (int e = 0; e < 8; e += 2) {
-    float v[2];
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int K = K0 + e + q;
-      float x = 0.f;
-      if (K < g.in_c * kk) {
-        const int ci = K / kk, t = K - ci * kk, ky = t / g.k, kx = t - (t / g.k) * g.k;
-        const int iy = oy * g.stride - g.pad + ky, ix = ox * g.stride - g.pad + kx;
-        if (iy >= 0 && iy < g.in_h && ix >= 0 && ix < g.in_w) x = hr[(size_t)ci * hw_in + iy * g.in_w + ix];
-      }
-      v[q] = x;
-    }
-    __nv_bfloat162 b2 = __floats2bfloat162_rn(v[0], v[1]);
-    pk[e >> 1] = *reinterpret_cast<uint32_t*>(&b2);
-  }
-  *reinterpret_cast<uint4*>(col + m * Kp + K0) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-}
+// Where k_tcg writes: row m = (r, pp), pp = i * nJ + j, goes to position
+// p = (a + so * i) * Wo + (b + so * j) of out[r * stride + n * P + p] (+ bias[n * P + p]).
+struct TcgOut {
+  long long M;
+  int N, Np, nkb, brow;  // brow: first row of the weight operand's tile in its tensor map
+  int Pm, nJ, a, b, so, Wo, P;
+  long long stride;
+};
 
 // Bounded wait for k_tcg (same limit and error reporting as mbar_wait).
 __device__ __forceinline__ bool tcg_wait(uint64_t* b, uint32_t parity, volatile int* abort, int* status) {
@@ -1328,10 +1324,11 @@ __device__ __forceinline__ bool tcg_wait(uint64_t* b, uint32_t parity, volatile 
 
 // out[r * stride + n * P + p] = (Col x W^T)[m = r * P + p][n] (+ bias[n * P + p]) for n < N.
 __global__ void __launch_bounds__(TCG_THREADS, 1) k_tcg(const __grid_constant__ CUtensorMap mapA,
-                                                        const __grid_constant__ CUtensorMap mapB, long long M, int N,
-                                                        int Np, int nkb, int P, long long stride,
+                                                        const __grid_constant__ CUtensorMap mapB, TcgOut o,
                                                         float* __restrict__ out, const float* __restrict__ bias,
                                                         int* status) {
+  const long long M = o.M;
+  const int N = o.N, Np = o.Np, nkb = o.nkb;
   extern __shared__ __align__(1024) uint8_t tsm_raw[];
   const uint32_t pad = (1024u - (su32(tsm_raw) & 1023u)) & 1023u;
   uint8_t* base = tsm_raw + pad;
@@ -1383,7 +1380,7 @@ __global__ void __launch_bounds__(TCG_THREADS, 1) k_tcg(const __grid_constant__ 
           }
           mbar_expect_tx(&full[st], 16384u + (uint32_t)bbytes);
           tma_load_2d(sA + st * 16384, &mapA, kb * 64, (int)(tile * 128), &full[st]);
-          tma_load_2d(sB + st * bbytes, &mapB, kb * 64, 0, &full[st]);
+          tma_load_2d(sB + st * bbytes, &mapB, kb * 64, o.brow, &full[st]);
         }
       if (!ok) {
         for (uint32_t q = (seq > TCG_NS ? seq - TCG_NS : 0); q < seq; ++q) {
@@ -1429,9 +1426,11 @@ __global__ void __launch_bounds__(TCG_THREADS, 1) k_tcg(const __grid_constant__ 
       tc_fence_after();
       const long long m = tile * 128 + 32 * warp + lane;
       const bool min_ = m < M;
-      const long long r = min_ ? m / P : 0;
-      const int p = min_ ? (int)(m - r * P) : 0;
-      float* orow = out + r * stride + p;
+      const long long r = min_ ? m / o.Pm : 0;
+      const int pp = min_ ? (int)(m - r * o.Pm) : 0;
+      const int i = pp / o.nJ, j = pp - (pp / o.nJ) * o.nJ;
+      const int p = (o.a + o.so * i) * o.Wo + o.b + o.so * j;
+      float* orow = out + r * o.stride + p;
       for (int n0 = 0; n0 < Np; n0 += 16) {
         float v[16];
         tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(buf * Np + n0), v);
@@ -1439,7 +1438,7 @@ __global__ void __launch_bounds__(TCG_THREADS, 1) k_tcg(const __grid_constant__ 
 #pragma unroll
           for (int e = 0; e < 16; ++e) {
             const int n = n0 + e;
-            if (n < N) orow[(size_t)n * P] = v[e] + (bias ? bias[(size_t)n * P + p] : 0.f);
+            if (n < N) orow[(size_t)n * o.P] = v[e] + (bias ? bias[(size_t)n * o.P + p] : 0.f);
           }
         }
       }
@@ -1476,7 +1475,8 @@ struct TcNet {
   bool conv_ready = false;
   struct ConvW {
     int Np_b = 0, Kp_b = 0, Np_f = 0, Kp_f = 0;
-    CUtensorMap mb, mf;
+    CUtensorMap mb, mf;              // mb: the s * s phase matrices stacked, Np_b rows each
+    int2 *tab_b = nullptr, *tab_f = nullptr;  // gather tables: [s * s][Kp_b], [Kp_f]
   } conv[MAXL + 1];
 };
 
@@ -1703,6 +1703,27 @@ int tc_bound(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* bt, 
 // ---------------------------------------------------------------- conv layers on tensor cores
 static int pad_to(int x, int m) { return (x + m - 1) / m * m; }
 
+// Phase a of one spatial axis of a stride-s transposed convolution: the taps ky0 + s * dy
+// (dy < nk) that reach the stride grid from input rows a + s * i (i < n), whose source row is
+// i + off - dy.
+struct ConvPhase {
+  int k0, nk, off, n;
+};
+static ConvPhase conv_phase(int a, int k, int s, int pad, int in) {
+  ConvPhase c;
+  c.k0 = (a + pad) % s;
+  c.nk = c.k0 < k ? (k - c.k0 + s - 1) / s : 0;
+  c.off = (a + pad - c.k0) / s;
+  c.n = a < in ? (in - a + s - 1) / s : 0;
+  return c;
+}
+static int taps_per_axis(const LayerDev& l) { return (l.k + l.stride - 1) / l.stride; }
+static int kp_bwd(const LayerDev& l) { return pad_to(l.out_c * taps_per_axis(l) * taps_per_axis(l), 64); }
+static int kp_fwd(const LayerDev& l) { return pad_to(l.in_c * l.k * l.k, 64); }
+static int2 tab_entry(int chan_off, int dy, int dx) {
+  return make_int2(chan_off, (int)(((uint32_t)dy & 0xffffu) | ((uint32_t)dx << 16)));
+}
+
 bool tcg_supported(const bcrown_net* net) {
   bool conv = false;
   for (int i = 0; i < net->L; ++i) {
@@ -1710,7 +1731,7 @@ bool tcg_supported(const bcrown_net* net) {
     if (l.kind != BCROWN_LAYER_CONV) continue;
     conv = true;
     if (pad_to(l.in_c, 16) > 256 || pad_to(l.out_c, 16) > 256) return false;
-    if (pad_to(l.out_c * l.k * l.k, 64) > IM2COL_MAX_KP) return false;
+    if (kp_bwd(l) > IM2COL_MAX_KP || kp_fwd(l) > IM2COL_MAX_KP) return false;
   }
   if (!conv) return false;
   int dev = 0, major = 0, minor = 0;
@@ -1726,9 +1747,9 @@ size_t tcg_col_bytes_per_row(const bcrown_net* net) {
   for (int i = 0; i < net->L; ++i) {
     const LayerDev& l = net->ly[i];
     if (l.kind != BCROWN_LAYER_CONV) continue;
-    const size_t kk = (size_t)l.k * l.k;
-    const size_t bwd = (size_t)l.in_h * l.in_w * pad_to((int)(l.out_c * kk), 64);
-    const size_t fwd = (size_t)l.out_h * l.out_w * pad_to((int)(l.in_c * kk), 64);
+    const size_t ph = (size_t)((l.in_h + l.stride - 1) / l.stride) * ((l.in_w + l.stride - 1) / l.stride);
+    const size_t bwd = ph * kp_bwd(l);
+    const size_t fwd = (size_t)l.out_h * l.out_w * kp_fwd(l);
     b = std::max(b, std::max(bwd, fwd) * sizeof(__nv_bfloat16));
   }
   return b;
@@ -1739,40 +1760,85 @@ static int tcg_prepare(bcrown_net* net, TcNet* t) {
   for (int i = 1; i <= net->L; ++i) {
     const LayerDev& l = net->ly[i - 1];
     if (l.kind != BCROWN_LAYER_CONV) continue;
-    const int kk = l.k * l.k;
+    const int kk = l.k * l.k, s = l.stride, T = taps_per_axis(l);
     std::vector<float> w((size_t)l.out_c * l.in_c * kk);
     if (cudaMemcpy(w.data(), l.W, w.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
       return fail(BCROWN_ERR_CUDA, "copy of conv weights");
     TcNet::ConvW& c = t->conv[i];
     c.Np_b = pad_to(l.in_c, 16);
-    c.Kp_b = pad_to(l.out_c * kk, 64);
+    c.Kp_b = kp_bwd(l);
     c.Np_f = pad_to(l.out_c, 16);
-    c.Kp_f = pad_to(l.in_c * kk, 64);
-    std::vector<__nv_bfloat16> wb((size_t)c.Np_b * c.Kp_b, __float2bfloat16_rn(0.f));
-    std::vector<__nv_bfloat16> wf((size_t)c.Np_f * c.Kp_f, __float2bfloat16_rn(0.f));
+    c.Kp_f = kp_fwd(l);
+    const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
+    std::vector<__nv_bfloat16> wb((size_t)s * s * c.Np_b * c.Kp_b, zero);
+    std::vector<__nv_bfloat16> wf((size_t)c.Np_f * c.Kp_f, zero);
+    std::vector<int2> tb((size_t)s * s * c.Kp_b, make_int2(-1, 0)), tf((size_t)c.Kp_f, make_int2(-1, 0));
+    // forward: K = (ci, ky, kx), source (oy * s - pad + ky, ox * s - pad + kx) of channel ci
     for (int co = 0; co < l.out_c; ++co)
       for (int ci = 0; ci < l.in_c; ++ci)
-        for (int q = 0; q < kk; ++q) {
-          const __nv_bfloat16 v = __float2bfloat16_rn(w[((size_t)co * l.in_c + ci) * kk + q]);
-          wb[(size_t)ci * c.Kp_b + co * kk + q] = v;   // backward: K = (co, tap)
-          wf[(size_t)co * c.Kp_f + ci * kk + q] = v;   // forward:  K = (ci, tap)
-        }
+        for (int q = 0; q < kk; ++q)
+          wf[(size_t)co * c.Kp_f + ci * kk + q] = __float2bfloat16_rn(w[((size_t)co * l.in_c + ci) * kk + q]);
+    for (int ci = 0; ci < l.in_c; ++ci)
+      for (int q = 0; q < kk; ++q) tf[ci * kk + q] = tab_entry(ci * l.in_h * l.in_w, q / l.k, q % l.k);
+    // backward, phase (a, b): K = (co, dy, dx), tap (ky0 + s dy, kx0 + s dx), source q = (i + off - dy, ...)
+    for (int a = 0; a < s; ++a)
+      for (int b = 0; b < s; ++b) {
+        const ConvPhase py = conv_phase(a, l.k, s, l.pad, l.in_h), px = conv_phase(b, l.k, s, l.pad, l.in_w);
+        const size_t ph = (size_t)a * s + b;
+        for (int co = 0; co < l.out_c; ++co)
+          for (int dy = 0; dy < py.nk; ++dy)
+            for (int dx = 0; dx < px.nk; ++dx) {
+              const int K = co * T * T + dy * T + dx;
+              const int ky = py.k0 + s * dy, kx = px.k0 + s * dx;
+              tb[ph * c.Kp_b + K] = tab_entry(co * l.out_h * l.out_w, -dy, -dx);
+              for (int ci = 0; ci < l.in_c; ++ci)
+                wb[(ph * c.Np_b + ci) * c.Kp_b + K] =
+                    __float2bfloat16_rn(w[((size_t)co * l.in_c + ci) * kk + ky * l.k + kx]);
+            }
+      }
     __nv_bfloat16 *db = nullptr, *df = nullptr;
-    if (cudaMalloc(&db, wb.size() * 2) != cudaSuccess || cudaMalloc(&df, wf.size() * 2) != cudaSuccess)
+    if (cudaMalloc(&db, wb.size() * 2) != cudaSuccess || cudaMalloc(&df, wf.size() * 2) != cudaSuccess ||
+        cudaMalloc(&c.tab_b, tb.size() * sizeof(int2)) != cudaSuccess ||
+        cudaMalloc(&c.tab_f, tf.size() * sizeof(int2)) != cudaSuccess)
       return fail(BCROWN_ERR_OOM, "bf16 conv weights");
     t->bufs.push_back(db);
     t->bufs.push_back(df);
+    t->bufs.push_back(reinterpret_cast<__nv_bfloat16*>(c.tab_b));
+    t->bufs.push_back(reinterpret_cast<__nv_bfloat16*>(c.tab_f));
     if (cudaMemcpy(db, wb.data(), wb.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(df, wf.data(), wf.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess)
+        cudaMemcpy(df, wf.data(), wf.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c.tab_b, tb.data(), tb.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c.tab_f, tf.data(), tf.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess)
       return fail(BCROWN_ERR_CUDA, "bf16 conv weights upload");
-    BC_CHECK(encode_map(&c.mb, db, c.Np_b, c.Kp_b, c.Np_b));
+    BC_CHECK(encode_map(&c.mb, db, s * s * c.Np_b, c.Kp_b, c.Np_b));
     BC_CHECK(encode_map(&c.mf, df, c.Np_f, c.Kp_f, c.Np_f));
   }
   const int smem = 1024 + TCG_NS * (16384 + 256 * 128) + 256;
   BC_CUDA(cudaFuncSetAttribute(k_tcg, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  BC_CUDA(cudaFuncSetAttribute(k_im2col_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               IM2COL_ROWS * (IM2COL_MAX_KP + 8) * (int)sizeof(__nv_bfloat16)));
+  BC_CUDA(cudaFuncSetAttribute(k_im2col, cudaFuncAttributeMaxDynamicSharedMemorySize, im2col_smem(IM2COL_MAX_KP)));
   t->conv_ready = true;
+  return BCROWN_OK;
+}
+
+// One im2col + GEMM pass (a phase of a backward layer, or the forward layer).
+static int tcg_pass(bcrown_net* net, const Im2colPass& q, const CUtensorMap& mB, const TcgOut& o, const float* src,
+                    float* dst, const float* bias, char* col, size_t col_bytes, cudaStream_t s) {
+  if (q.M <= 0) return BCROWN_OK;
+  if ((size_t)q.M * q.Kp * sizeof(__nv_bfloat16) > col_bytes) return fail(BCROWN_ERR_OOM, "im2col workspace too small");
+  __nv_bfloat16* cb = reinterpret_cast<__nv_bfloat16*>(col);
+  k_im2col<<<(unsigned)((q.M + IM2COL_ROWS - 1) / IM2COL_ROWS), 256, im2col_smem(q.Kp), s>>>(q, src, cb);
+  ++g_launches;
+  CUtensorMap mA;
+  BC_CHECK(encode_map(&mA, cb, (int)q.M, q.Kp, 128));
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long ntiles = (q.M + 127) / 128;
+  const int grid = (int)std::min<long long>(ntiles, 2LL * sms);
+  const int smem = 1024 + TCG_NS * (16384 + o.Np * 128) + 256;
+  k_tcg<<<grid, TCG_THREADS, smem, s>>>(mA, mB, o, dst, bias, net->status);
+  ++g_launches;
+  BC_CUDA(cudaGetLastError());
   return BCROWN_OK;
 }
 
@@ -1781,37 +1847,27 @@ int tcg_conv(bcrown_net* net, int i, bool fwd, int R, const float* src, float* d
   TcNet* t = tc_of(net);
   BC_CHECK(tcg_prepare(net, t));
   const LayerDev& l = net->ly[i - 1];
-  const LayerGeom g = geom_of(l);
   const TcNet::ConvW& c = t->conv[i];
-  const int P = fwd ? l.out_h * l.out_w : l.in_h * l.in_w;
-  const int N = fwd ? l.out_c : l.in_c;
-  const int Np = fwd ? c.Np_f : c.Np_b;
-  const int Kp = fwd ? c.Kp_f : c.Kp_b;
-  const long long M = (long long)R * P;
-  if (M <= 0) return BCROWN_OK;
-  if ((size_t)M * Kp * sizeof(__nv_bfloat16) > col_bytes) return fail(BCROWN_ERR_OOM, "im2col workspace too small");
-  __nv_bfloat16* cb = reinterpret_cast<__nv_bfloat16*>(col);
-  const long long nthr = M * (Kp / 8);
+  if (R <= 0) return BCROWN_OK;
   if (fwd) {
-    k_im2col_fwd<<<(unsigned)((nthr + 255) / 256), 256, 0, s>>>(M, P, g, Kp, src, cb);
-  } else {
-    const int smem = IM2COL_ROWS * (Kp + 8) * (int)sizeof(__nv_bfloat16);
-    k_im2col_bwd<<<(unsigned)((M + IM2COL_ROWS - 1) / IM2COL_ROWS), 256, smem, s>>>(M, P, g, Kp, src, cb);
+    const int P = l.out_h * l.out_w;
+    const Im2colPass q{(long long)R * P, P, l.out_w, l.stride, -l.pad, -l.pad, l.in_h, l.in_w, l.d_in, c.Kp_f, c.tab_f};
+    const TcgOut o{q.M, l.out_c, c.Np_f, c.Kp_f / 64, 0, P, l.out_w, 0, 0, 1, l.out_w, P, (long long)l.d_out};
+    return tcg_pass(net, q, c.mf, o, src, dst, bias, col, col_bytes, s);
   }
-  ++g_launches;
-  CUtensorMap mA;
-  BC_CHECK(encode_map(&mA, cb, (int)M, Kp, 128));
-  int dev = 0, sms = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const long long ntiles = (M + 127) / 128;
-  const int grid = (int)std::min<long long>(ntiles, 2LL * sms);
-  const int smem = 1024 + TCG_NS * (16384 + Np * 128) + 256;
-  k_tcg<<<grid, TCG_THREADS, smem, s>>>(mA, fwd ? c.mf : c.mb, M, N, Np, Kp / 64, P,
-                                        fwd ? (long long)l.d_out : (long long)l.d_in, dst, fwd ? bias : nullptr,
-                                        net->status);
-  ++g_launches;
-  BC_CUDA(cudaGetLastError());
+  const int st = l.stride;
+  for (int a = 0; a < st; ++a)
+    for (int b = 0; b < st; ++b) {
+      const ConvPhase py = conv_phase(a, l.k, st, l.pad, l.in_h), px = conv_phase(b, l.k, st, l.pad, l.in_w);
+      const int Pm = py.n * px.n;
+      if (Pm == 0) continue;
+      const int ph = a * st + b;
+      const Im2colPass q{(long long)R * Pm, Pm, px.n, 1, py.off, px.off, l.out_h, l.out_w, l.d_out, c.Kp_b,
+                         c.tab_b + (size_t)ph * c.Kp_b};
+      const TcgOut o{q.M, l.in_c, c.Np_b, c.Kp_b / 64, ph * c.Np_b, Pm, px.n, a, b, st, l.in_w,
+                     l.in_h * l.in_w, (long long)l.d_in};
+      BC_CHECK(tcg_pass(net, q, c.mb, o, src, dst, nullptr, col, col_bytes, s));
+    }
   return BCROWN_OK;
 }
 

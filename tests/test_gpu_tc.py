@@ -164,17 +164,26 @@ def test_batching_64_properties_sampled():
     assert np.all(lbc[rows] <= ref_opt + 1e-12 * np.abs(ref_opt))
 
 
-def _tiny_conv():
-    layers = wl.conv_layers((2, 6, 6), [(3, 3, 2, 1), (4, 3, 1, 1)], [8, 4], 3)
+_TINY_CONVS = {
+    "tiny": ((2, 6, 6), [(3, 3, 2, 1), (4, 3, 1, 1)]),
+    "tiny_odd": ((2, 7, 5), [(3, 3, 2, 1), (4, 4, 2, 1)]),   # odd maps: phases of unequal size
+    "tiny_s3": ((2, 9, 8), [(3, 5, 3, 2), (4, 3, 1, 1)]),    # stride 3: nine phases
+}
+
+
+def _tiny_conv(which="tiny"):
+    shape, convs = _TINY_CONVS[which]
+    layers = wl.conv_layers(shape, convs, [8, 4], 3)
     return wl.make_problem("tinyconv", layers, 2, 0.1, 3, 3)
 
 
-@pytest.mark.parametrize("which", ["tiny", "c3"])
+@pytest.mark.parametrize("which", ["tiny", "tiny_odd", "tiny_s3", "c3"])
 def test_bf16_conv_bound_and_gradient_close_to_oracle(which):
-    """Conv layers as BF16 tensor-core GEMMs over an im2col operand: a tiny net (channel counts
-    and K far below one tile, stride 2, two properties) and the c3 net (4x4 kernels, stride 2)."""
-    if which == "tiny":
-        pb = _tiny_conv()
+    """Conv layers as BF16 tensor-core GEMMs over an im2col operand, the transposed convolutions
+    split into stride phases: tiny nets (channel counts and K far below one tile, strides 1-3,
+    odd map sizes, two properties) and the c3 net (4x4 kernels, stride 2)."""
+    if which != "c3":
+        pb = _tiny_conv(which)
         onet, props, unst = oracle_setup(pb)
         batch = wl.random_batch(pb, unst, 24, 0, 4, 1, props=np.arange(24) % 2)
     else:
