@@ -58,11 +58,13 @@ enum { BCROWN_LAYER_FC = 0, BCROWN_LAYER_CONV = 1 };
  *  BF16    : A.W contractions with BF16 operands and FP32 accumulation on the
  *            tensor cores; everything else FP32.  Fully connected networks (hidden
  *            widths <= 256, at most 1536 hidden neurons, input <= 1024) run one fused
- *            kernel per call; networks with conv layers (<= 256 channels) run their
- *            conv layers as tensor-core GEMMs over an im2col operand and their fully
- *            connected layers in FP32.  Any alpha, beta gives a valid bound (Section
- *            3.1), so this is used for the optimisation iterations.  Other networks
- *            get BCROWN_ERR_UNIMPLEMENTED.
+ *            kernel per call; other networks (conv layers of <= 256 channels with
+ *            channels x taps <= 2048, fc layers of <= 65536 neurons) run every
+ *            contraction as a tensor-core GEMM (conv layers over an im2col operand,
+ *            transposed convolutions split into stride phases) and the relaxation in
+ *            FP32.  Any alpha, beta gives a valid bound (Section 3.1), so this is used
+ *            for the optimisation iterations.  Other networks get
+ *            BCROWN_ERR_UNIMPLEMENTED.
  *  CERTIFY : FP32 contractions plus a priori rounding-error terms, upper-chord
  *            constants rounded outward and sums rounded down (error terms rounded
  *            up); the result is a lower bound of the exact-arithmetic bound at the

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "conv_tc.cuh"
 #include "fused_tc.cuh"
 #include "simt.cuh"
 
@@ -11,7 +12,7 @@ using namespace bcrown;
 
 namespace bcrown {
 
-static const size_t kChunkBytes = size_t(2) << 30;  // per-chunk workspace target
+static const size_t kChunkBytes = size_t(8) << 30;  // per-chunk workspace target
 
 static int check_domain(const bcrown_net* net, const bcrown_domain* dom) {
   if (!dom || dom->n_props < 1 || !dom->x_lo || !dom->x_hi || (net->H > 0 && (!dom->l || !dom->u)))
@@ -158,15 +159,15 @@ static RowsCtx ctx_of(bcrown_net* net, const bcrown_domain* dom, const bcrown_ba
 }
 
 // Backward contraction of layer i: Aout = Lam W^(i) (fc) or transposed convolution.
-// tc: conv layers as BF16 tensor-core GEMMs over an im2col operand in pl.col (BF16 precision).
+// tc: BF16 tensor-core GEMMs (over an im2col operand for conv layers) with the operand in pl.col.
 static int contract_bwd(bcrown_net* net, int i, int Rc, const float* Lam, float* Aout, cudaStream_t s,
                         const Plan* tc = nullptr) {
   ProfScope ps(net, BCROWN_PROF_CONTRACT, s);
   const LayerDev& l = net->ly[i - 1];
+  if (tc)
+    return tcg_conv(net, i, false, Rc, Lam, Aout, nullptr, tc->col, tc->col_bytes, s);
   if (l.kind == BCROWN_LAYER_FC)
     launch_sgemm(Rc, l.d_in, l.d_out, Lam, l.d_out, l.W, l.d_in, Aout, l.d_in, nullptr, s);
-  else if (tc)
-    return tcg_conv(net, i, false, Rc, Lam, Aout, nullptr, tc->col, tc->col_bytes, s);
   else
     launch_conv_bwd(Rc, geom_of(l), Lam, l.W, Aout, s);
   return BCROWN_OK;
@@ -177,10 +178,10 @@ static int contract_fwd(bcrown_net* net, int i, int Rc, const float* h, float* Z
                         const Plan* tc = nullptr) {
   ProfScope ps(net, BCROWN_PROF_CONTRACT, s);
   const LayerDev& l = net->ly[i - 1];
+  if (tc)
+    return tcg_conv(net, i, true, Rc, h, Z, l.b, tc->col, tc->col_bytes, s);
   if (l.kind == BCROWN_LAYER_FC)
     launch_sgemm(Rc, l.d_out, l.d_in, h, l.d_in, l.Wt, l.d_out, Z, l.d_out, l.b, s);
-  else if (tc)
-    return tcg_conv(net, i, true, Rc, h, Z, l.b, tc->col, tc->col_bytes, s);
   else
     launch_conv_fwd(Rc, geom_of(l), h, l.W, l.b, Z, s);
   return BCROWN_OK;
@@ -189,8 +190,8 @@ static int contract_fwd(bcrown_net* net, int i, int Rc, const float* h, float* Z
 // One chunk of rows: bound (and optionally the gradient) with the SIMT path.
 static int chunk_simt(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* bt, Plan& pl, int r0, int Rc,
                       bool cert, bool grad, const float* alpha, const float* beta, float* lb, float* dalpha,
-                      float* dbeta, cudaStream_t s, bool tc_conv = false) {
-  const Plan* tc = tc_conv ? &pl : nullptr;
+                      float* dbeta, cudaStream_t s, bool tc_layers = false) {
+  const Plan* tc = tc_layers ? &pl : nullptr;
   RowsCtx c = ctx_of(net, dom, bt, pl, r0, Rc);
   const int L = net->L;
   long long hoff_top = L >= 2 ? net->hoff[L - 2] : -1;
@@ -231,14 +232,19 @@ static int run_bound(bcrown_net* net, const bcrown_domain* dom, const bcrown_bat
     return tc_bound(net, dom, bt, pl.tb, pl.tc_ws, pl.tc_ws_bytes, grad, tc_plan, alpha, beta, lb, dalpha, dbeta, s);
   }
   bool cert = precision == BCROWN_CERTIFY;
-  // BF16 on a conv net: conv contractions on the tensor cores (the rest of the layer-by-layer path
-  // stays FP32); planned when the plan has an im2col buffer
-  const bool tc_conv = precision == BCROWN_BF16 && pl.col != nullptr;
+  // BF16 beyond the fused kernel (conv layers, wide fc layers): the contractions on the tensor
+  // cores, the rest of the layer-by-layer path in FP32; planned when the plan has an im2col buffer
+  const bool tc_layers = precision == BCROWN_BF16 && pl.col != nullptr;
   for (int r0 = 0; r0 < R; r0 += pl.Rc) {
     int Rc = std::min(pl.Rc, R - r0);
-    BC_CHECK(chunk_simt(net, dom, bt, pl, r0, Rc, cert, grad, alpha, beta, lb, dalpha, dbeta, s, tc_conv));
+    BC_CHECK(chunk_simt(net, dom, bt, pl, r0, Rc, cert, grad, alpha, beta, lb, dalpha, dbeta, s, tc_layers));
   }
   return BCROWN_OK;
+}
+
+// im2col bytes per row for the BF16 layer-by-layer path (0: not taken; the fused kernel or FP32).
+static size_t layer_tc_col(bcrown_net* net, int precision) {
+  return precision == BCROWN_BF16 && !tc_supported(net) && tcg_supported(net) ? tcg_col_bytes_per_row(net) : 0;
 }
 
 static int check_precision(bcrown_net* net, int precision, bool grad) {
@@ -247,8 +253,8 @@ static int check_precision(bcrown_net* net, int precision, bool grad) {
   if (grad && precision == BCROWN_CERTIFY) return fail(BCROWN_ERR_ARG, "gradient in CERTIFY precision is not offered");
   if (precision == BCROWN_BF16 && !tc_supported(net) && !tcg_supported(net))
     return fail(BCROWN_ERR_UNIMPLEMENTED,
-                "BF16 tensor-core path needs a fully connected network with supported widths or conv layers of at "
-                "most 256 channels");
+                "BF16 tensor-core path needs conv layers of at most 256 channels (and K = channels x taps <= 2048) "
+                "and fc layers of at most 65536 neurons");
   return BCROWN_OK;
 }
 
@@ -268,7 +274,7 @@ extern "C" int bcrown_bound(bcrown_net* net, const bcrown_domain* dom, const bcr
   int R = batch->B * net->K;
   size_t tcb = precision == BCROWN_BF16 ? tc_workspace_bytes(net, batch->B, dom->n_props, false) : 0;
   BC_CHECK(make_plan(net, dom->n_props, R, precision == BCROWN_CERTIFY, false, 0, 0, tcb, pl,
-                     precision == BCROWN_BF16 && tcg_supported(net) ? tcg_col_bytes_per_row(net) : 0));
+                     layer_tc_col(net, precision)));
   build_tables(net, dom, pl, s);
   if (precision == BCROWN_CERTIFY) build_wm(net, dom, pl, s);
   BC_CHECK(run_bound(net, dom, batch, pl, precision, false, alpha, beta, lb, nullptr, nullptr, s));
@@ -292,7 +298,7 @@ extern "C" int bcrown_bound_grad(bcrown_net* net, const bcrown_domain* dom, cons
   int R = batch->B * net->K;
   size_t tcb = precision == BCROWN_BF16 ? tc_workspace_bytes(net, batch->B, dom->n_props, true) : 0;
   BC_CHECK(make_plan(net, dom->n_props, R, false, false, 0, 0, tcb, pl,
-                     precision == BCROWN_BF16 && tcg_supported(net) ? tcg_col_bytes_per_row(net) : 0));
+                     layer_tc_col(net, precision)));
   build_tables(net, dom, pl, s);
   BC_CHECK(run_bound(net, dom, batch, pl, precision, true, alpha, beta, lb, dalpha, dbeta, s));
   BC_CUDA(cudaGetLastError());
@@ -317,7 +323,7 @@ extern "C" int bcrown_optimize(bcrown_net* net, const bcrown_domain* dom, const 
   size_t tcb = cfg->precision == BCROWN_BF16 ? tc_workspace_bytes(net, batch->B, dom->n_props, true) : 0;
   bool cert = cfg->certify != 0;
   BC_CHECK(make_plan(net, dom->n_props, R, cert, true, na, nb, tcb, pl,
-                     cfg->precision == BCROWN_BF16 && tcg_supported(net) ? tcg_col_bytes_per_row(net) : 0));
+                     layer_tc_col(net, cfg->precision)));
   build_tables(net, dom, pl, s);
   if (cert) build_wm(net, dom, pl, s);
   if (na) {

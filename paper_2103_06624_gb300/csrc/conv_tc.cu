@@ -1,0 +1,606 @@
+// Convolution layers as tcgen05 GEMMs (sm_103a) for the BF16 precision of the layer-by-layer
+// path: Eq. definition_A's contraction A^(i-1) = Lambda^(i) W^(i) is the transposed
+// convolution, and the adjoint's zhat^(i) = W^(i) h^(i-1) + b^(i) the convolution itself.
+// Both become GEMMs over an im2col operand gathered into BF16, multiplied on the tensor cores
+// with FP32 accumulation in TMEM.
+//
+// Every mbarrier wait is bounded; on expiry the kernel records BCROWN_ERR_TIMEOUT, raises its
+// abort flag, waits (bounded) for its copies in flight, frees TMEM and returns.
+#include <algorithm>
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+#include "conv_tc.cuh"
+#include "tc_ptx.cuh"
+
+namespace bcrown {
+
+extern std::atomic<long long> g_launches;
+
+namespace tc {
+
+// Convolutions on the tensor cores (BF16 precision of the layer-by-layer path): the contraction
+// of a conv layer as GEMMs over an im2col operand.
+//   forward:   Z[r][co][p] = sum_K Col[(r, p)][K] Wf[co][K] + b,   K = (ci, ky, kx)
+//   backward:  the transposed convolution Ain[r][ci][p] = sum Lambda[r][co][q] W[co][ci][tap]
+//              over the (q, tap) with p = q * s - pad + tap.  For stride s the input positions
+//              fall into s x s phases (p_y mod s, p_x mod s); within a phase only the taps
+//              ky = ky0 + s * dy (dy < ceil(k / s)) reach the stride grid, and the source
+//              position is q_y = i + off - dy for the phase's i-th row.  Each phase is one GEMM
+//              with K = (co, dy, dx) and its own weight matrix, so the operand holds no
+//              structural zeros of the stride.
+// Col is gathered into BF16 by k_im2col from a per-K table (source channel offset, signed tap
+// offsets: no divisions in the inner loop); k_tcg multiplies it with the BF16 weights:
+// M = rows x positions (tiles of 128 on the TMEM lanes), N = channels (padded to 16), K in
+// blocks of 64 streamed by TMA.
+// ------------------------------------------------------------------------------------------
+constexpr int TCG_NS = 4;         // pipeline stages (A: 128 x 64, B: Np x 64)
+constexpr int TCG_EPI = 8;        // epilogue warps: TMEM lane quadrant warp % 4, column chunks of parity warp / 4
+constexpr int TCG_TMA_WARP = TCG_EPI, TCG_MMA_WARP = TCG_EPI + 1;
+constexpr int TCG_THREADS = (TCG_EPI + 2) * 32;
+constexpr int TCG_BIAS_MAX = 4096;  // channel biases staged in shared memory up to this many
+// Dynamic shared memory of k_tcg: 1 KB alignment slack, the stages, barriers, staged biases.
+inline int tcg_smem(int Np, int N, bool bias) {
+  return 1024 + TCG_NS * (16384 + Np * 128) + 256 + (bias && N <= TCG_BIAS_MAX ? (N + 3) / 4 * 16 : 0);
+}
+
+// One gather: row m = (r, pp), pp = i * nJ + j; source position (y0 + dy_K, x0 + dx_K) with
+// y0 = i * ms + cy, x0 = j * ms + cx, in a [C][Hs][Ws] map of row r (d_src floats per row).
+struct Im2colPass {
+  long long M;
+  int Pm, nJ, ms, cy, cx, Hs, Ws, d_src, Kp;
+  const int2* tab;  // [Kp]: {channel offset C * Hs * Ws, or -1 for a zero column; (dy & 0xffff) | dx << 16}
+};
+
+// 32 consecutive rows m per block.  Lanes walk the 32 rows for 16 K at a time (K uniform per
+// warp: coalesced source reads) into a shared tile [32][Kp + 8], whose rows then leave in
+// 16-byte stores.
+constexpr int IM2COL_ROWS = 32;
+constexpr int IM2COL_MAX_KP = 2048;
+inline int im2col_smem(int Kp) { return Kp * (int)sizeof(int2) + IM2COL_ROWS * (Kp + 8) * 2; }
+__global__ void __launch_bounds__(256) k_im2col(Im2colPass q, const float* __restrict__ src,
+                                                __nv_bfloat16* __restrict__ col) {
+  extern __shared__ __align__(16) uint8_t im_raw[];
+  const int Kp = q.Kp, S = Kp + 8;  // row stride (bf16), 16-byte aligned rows
+  int2* tab = reinterpret_cast<int2*>(im_raw);
+  __nv_bfloat16* tile = reinterpret_cast<__nv_bfloat16*>(im_raw + (size_t)Kp * sizeof(int2));
+  for (int k = threadIdx.x; k < Kp; k += 256) tab[k] = q.tab[k];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long m0 = (long long)blockIdx.x * IM2COL_ROWS;
+  const long long m = m0 + lane;
+  const bool mv = m < q.M;
+  const int r = mv ? (int)(m / q.Pm) : 0;
+  const int pp = mv ? (int)(m - (long long)r * q.Pm) : 0;
+  const int i = pp / q.nJ, j = pp - (pp / q.nJ) * q.nJ;
+  const int y0 = i * q.ms + q.cy, x0 = j * q.ms + q.cx;
+  const float* sr = src + (size_t)r * q.d_src;
+  __syncthreads();
+  // 16 K per lane per step: 16 independent loads in flight before the first use
+  for (int K0 = 16 * w; K0 < Kp; K0 += 128) {
+    float v[16];
+#pragma unroll
+    for (int e = 0; e < 16; e += 2) {
+      const int4 t2 = *reinterpret_cast<const int4*>(tab + K0 + e);
+      const int y0a = y0 + (int)(short)(t2.y & 0xffff), x0a = x0 + (t2.y >> 16);
+      const int y0b = y0 + (int)(short)(t2.w & 0xffff), x0b = x0 + (t2.w >> 16);
+      v[e] = (mv && t2.x >= 0 && (unsigned)y0a < (unsigned)q.Hs && (unsigned)x0a < (unsigned)q.Ws)
+                 ? sr[t2.x + y0a * q.Ws + x0a]
+                 : 0.f;
+      v[e + 1] = (mv && t2.z >= 0 && (unsigned)y0b < (unsigned)q.Hs && (unsigned)x0b < (unsigned)q.Ws)
+                     ? sr[t2.z + y0b * q.Ws + x0b]
+                     : 0.f;
+    }
+    uint32_t pk[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+      pk[e] = *reinterpret_cast<uint32_t*>(&b2);
+    }
+    uint4* d = reinterpret_cast<uint4*>(tile + lane * S + K0);
+    d[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    d[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+  }
+  __syncthreads();
+  const int cpr = Kp / 8;
+  for (int row = w; row < IM2COL_ROWS; row += 8) {
+    if (m0 + row >= q.M) break;
+    uint4* dst = reinterpret_cast<uint4*>(col + (m0 + row) * Kp);
+    const uint4* sv = reinterpret_cast<const uint4*>(tile + row * S);
+    for (int c = lane; c < cpr; c += 32) dst[c] = sv[c];
+  }
+}
+
+// Fully connected operand: row r of src (d floats) to BF16 [M][Kp], zero past d.  One thread per
+// 8 columns (one 16-byte store); consecutive threads walk a row.
+__global__ void k_rows_bf16(long long M, int d, int Kp, const float* __restrict__ src,
+                            __nv_bfloat16* __restrict__ col) {
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int cpr = Kp / 8;
+  if (id >= M * cpr) return;
+  const long long r = id / cpr;
+  const int k0 = (int)(id - r * cpr) * 8;
+  const float* sr = src + r * d;
+  float v[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) v[e] = k0 + e < d ? sr[k0 + e] : 0.f;
+  uint32_t pk[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    __nv_bfloat162 b2 = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+    pk[e] = *reinterpret_cast<uint32_t*>(&b2);
+  }
+  *reinterpret_cast<uint4*>(col + r * Kp + k0) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+}
+
+// Where k_tcg writes: row m = (r, pp), pp = i * nJ + j, goes to position
+// p = (a + so * i) * Wo + (b + so * j) of out[r * stride + n * P + p] (+ bias[n * P + p]).
+// A fully connected layer is the case P = 1 (one position per row).
+struct TcgOut {
+  long long M;
+  int N, Np, ntn, nkb, brow;  // N in ntn tiles of Np; brow: first row of the weight operand in its map
+  int Pm, nJ, a, b, so, Wo, P;
+  long long stride;
+};
+
+// Bounded wait for k_tcg (same limit and error reporting as mbar_wait).
+__device__ __forceinline__ bool tcg_wait(uint64_t* b, uint32_t parity, volatile int* abort, int* status) {
+  if (mbar_try(b, parity)) return true;
+  long long t0 = clock64();
+  while (true) {
+    if (mbar_try_sleep(b, parity, 20000u)) return true;
+    if (*abort) return false;
+    if (clock64() - t0 > 4000000000LL) {
+      atomicCAS(status, 0, BCROWN_ERR_TIMEOUT);
+      *abort = 1;
+      return false;
+    }
+  }
+}
+
+// out[r * stride + n * P + p] = (Col x W^T)[m = r * P + p][n] (+ bias[n * P + p]) for n < N.
+// The bias is per channel (constant over the positions p, as conv biases are stored): it is
+// read at p = 0, into shared memory when N <= TCG_BIAS_MAX.
+__global__ void __launch_bounds__(TCG_THREADS, 1) k_tcg(const __grid_constant__ CUtensorMap mapA,
+                                                        const __grid_constant__ CUtensorMap mapB, TcgOut o,
+                                                        float* __restrict__ out, const float* __restrict__ bias,
+                                                        int* status) {
+  const long long M = o.M;
+  const int N = o.N, Np = o.Np, nkb = o.nkb;
+  extern __shared__ __align__(1024) uint8_t tsm_raw[];
+  const uint32_t pad = (1024u - (su32(tsm_raw) & 1023u)) & 1023u;
+  uint8_t* base = tsm_raw + pad;
+  const int bbytes = Np * 128;
+  uint8_t* sA = base;                                  // TCG_NS x 16 KB
+  uint8_t* sB = base + TCG_NS * 16384;                 // TCG_NS x Np*128
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + TCG_NS * bbytes);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + TCG_NS;
+  uint64_t* acc_full = bars + 2 * TCG_NS;
+  uint64_t* acc_empty = bars + 2 * TCG_NS + 2;
+  uint32_t* tbase_sm = reinterpret_cast<uint32_t*>(bars + 2 * TCG_NS + 4);
+  volatile int* abort = reinterpret_cast<volatile int*>(tbase_sm + 1);
+  float* sbias = reinterpret_cast<float*>(bars + 32);  // 256 bytes past the barriers
+  const bool stage_bias = bias != nullptr && N <= TCG_BIAS_MAX;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long ntiles = (M + 127) / 128 * o.ntn;   // tile = m tile * ntn + n tile
+  // two accumulators of Np columns, allocated as a power of two >= 32
+  const uint32_t tcols = Np <= 16 ? 32u : (Np <= 32 ? 64u : (Np <= 64 ? 128u : (Np <= 128 ? 256u : 512u)));
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < TCG_NS; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&acc_full[i], 1);
+      mbar_init(&acc_empty[i], TCG_EPI);
+    }
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == TCG_MMA_WARP) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tbase_sm)), "r"(tcols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tbase_sm;
+  if (warp == TCG_TMA_WARP) {
+    if (lane == 0) {
+      uint32_t seq = 0;
+      bool ok = true;
+      for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x)
+        for (int kb = 0; kb < nkb; ++kb, ++seq) {
+          const int st = seq % TCG_NS;
+          if (!tcg_wait(&empty[st], ((seq / TCG_NS) & 1) ^ 1, abort, status)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&full[st], 16384u + (uint32_t)bbytes);
+          tma_load_2d(sA + st * 16384, &mapA, kb * 64, (int)(tile / o.ntn * 128), &full[st]);
+          tma_load_2d(sB + st * bbytes, &mapB, kb * 64, o.brow + (int)(tile % o.ntn) * Np, &full[st]);
+        }
+      if (!ok) {
+        for (uint32_t q = (seq > TCG_NS ? seq - TCG_NS : 0); q < seq; ++q) {
+          long long t0 = clock64();
+          while (!mbar_try(&full[q % TCG_NS], (q / TCG_NS) & 1) && clock64() - t0 < 200000000LL) {
+          }
+        }
+      }
+    }
+  } else if (warp == TCG_MMA_WARP) {
+    if (lane == 0) {
+      uint32_t seq = 0, accseq = 0;
+      bool ok = true;
+      const uint32_t idesc = idesc_bf16(Np);
+      for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++accseq) {
+        const int buf = accseq & 1;
+        if (!tcg_wait(&acc_empty[buf], ((accseq >> 1) & 1) ^ 1, abort, status)) break;
+        tc_fence_after();
+        const uint32_t dt = tmem + (uint32_t)(buf * Np);
+        for (int kb = 0; kb < nkb; ++kb, ++seq) {
+          const int st = seq % TCG_NS;
+          if (!tcg_wait(&full[st], (seq / TCG_NS) & 1, abort, status)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          umma_kblock(dt, sdesc(su32(sA + st * 16384)), sdesc(su32(sB + st * bbytes)), idesc, kb != 0 ? 1u : 0u);
+          umma_commit(&empty[st]);
+        }
+        if (!ok) break;
+        umma_commit(&acc_full[buf]);
+      }
+    }
+  } else {
+    // epilogue: warp w reads TMEM lanes (tile rows) 32 (w % 4) .. + 31, column chunks of parity w / 4
+    const int q4 = warp & 3, half = warp >> 2;
+    if (stage_bias) {
+      for (int n = threadIdx.x; n < N; n += TCG_EPI * 32) sbias[n] = bias[(size_t)n * o.P];
+      asm volatile("bar.sync 1, %0;" ::"n"(TCG_EPI * 32) : "memory");
+    }
+    const bool vec = o.P == 1 && (o.stride & 3) == 0 &&
+                     ((reinterpret_cast<uintptr_t>(out) | (stage_bias ? 0 : reinterpret_cast<uintptr_t>(bias))) &
+                      15) == 0;
+    uint32_t accseq = 0;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++accseq) {
+      const int buf = accseq & 1;
+      int okw = 1;
+      if (lane == 0) okw = tcg_wait(&acc_full[buf], (accseq >> 1) & 1, abort, status) ? 1 : 0;
+      okw = __shfl_sync(0xffffffffu, okw, 0);
+      if (!okw) break;
+      tc_fence_after();
+      const long long m = tile / o.ntn * 128 + 32 * q4 + lane;
+      const int nb = (int)(tile % o.ntn) * Np;
+      const bool min_ = m < M;
+      const long long r = min_ ? m / o.Pm : 0;
+      const int pp = min_ ? (int)(m - r * o.Pm) : 0;
+      const int i = pp / o.nJ, j = pp - (pp / o.nJ) * o.nJ;
+      const int p = (o.a + o.so * i) * o.Wo + o.b + o.so * j;
+      float* orow = out + r * o.stride + p;
+      for (int n0 = 16 * half; n0 < Np; n0 += 32) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(buf * Np + n0), v);
+        if (min_) {
+          if (vec && nb + n0 + 16 <= N) {
+            // one position per row: the 16 channels are contiguous
+#pragma unroll
+            for (int e = 0; e < 16; e += 4) {
+              const int n = nb + n0 + e;
+              float4 x = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+              if (bias) {
+                const float4 bb = stage_bias ? *reinterpret_cast<const float4*>(sbias + n)
+                                             : *reinterpret_cast<const float4*>(bias + n);
+                x.x += bb.x, x.y += bb.y, x.z += bb.z, x.w += bb.w;
+              }
+              *reinterpret_cast<float4*>(orow + n) = x;
+            }
+          } else {
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+              const int n = nb + n0 + e;
+              if (n < N)
+                orow[(size_t)n * o.P] =
+                    v[e] + (stage_bias ? sbias[n] : (bias ? bias[(size_t)n * o.P] : 0.f));
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[buf]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == TCG_MMA_WARP) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols) : "memory");
+  }
+}
+
+}  // namespace tc
+
+using namespace tc;
+
+namespace {
+
+// Per-layer BF16 weights, gather tables and tensor maps of one net, built on first use.
+struct ConvTc {
+  struct ConvW {
+    int Np_b = 0, Kp_b = 0, Np_f = 0, Kp_f = 0, ntn_b = 1, ntn_f = 1;  // N in ntn tiles of Np
+    CUtensorMap mb, mf;              // mb: the s * s phase matrices stacked, Np_b rows each
+    int2 *tab_b = nullptr, *tab_f = nullptr;  // gather tables: [s * s][Kp_b], [Kp_f]
+    __nv_bfloat16 *wb = nullptr, *wf = nullptr;  // fc: the B operands behind mb, mf
+  };
+  std::vector<ConvW> conv;  // conv[i]: paper layer i
+  std::vector<void*> bufs;
+  bool ready = false;
+};
+
+std::mutex g_conv_mu;
+std::vector<std::pair<const bcrown_net*, ConvTc*>> g_conv;
+
+ConvTc* conv_of(const bcrown_net* net) {
+  std::lock_guard<std::mutex> g(g_conv_mu);
+  for (auto& e : g_conv)
+    if (e.first == net) return e.second;
+  ConvTc* t = new ConvTc();
+  g_conv.push_back({net, t});
+  return t;
+}
+
+int pad_to(int x, int m) { return (x + m - 1) / m * m; }
+
+}  // namespace
+
+// Phase a of one spatial axis of a stride-s transposed convolution: the taps ky0 + s * dy
+// (dy < nk) that reach the stride grid from input rows a + s * i (i < n), whose source row is
+// i + off - dy.
+struct ConvPhase {
+  int k0, nk, off, n;
+};
+static ConvPhase conv_phase(int a, int k, int s, int pad, int in) {
+  ConvPhase c;
+  c.k0 = (a + pad) % s;
+  c.nk = c.k0 < k ? (k - c.k0 + s - 1) / s : 0;
+  c.off = (a + pad - c.k0) / s;
+  c.n = a < in ? (in - a + s - 1) / s : 0;
+  return c;
+}
+static int taps_per_axis(const LayerDev& l) { return (l.k + l.stride - 1) / l.stride; }
+static int kp_bwd(const LayerDev& l) { return pad_to(l.out_c * taps_per_axis(l) * taps_per_axis(l), 64); }
+static int kp_fwd(const LayerDev& l) { return pad_to(l.in_c * l.k * l.k, 64); }
+static int2 tab_entry(int chan_off, int dy, int dx) {
+  return make_int2(chan_off, (int)(((uint32_t)dy & 0xffffu) | ((uint32_t)dx << 16)));
+}
+
+// N tile of a GEMM with N outputs: the whole of N up to 256, else tiles of 256.
+static void n_tiles(int N, int* Np, int* ntn) {
+  *Np = N <= 256 ? pad_to(N, 16) : 256;
+  *ntn = (N + *Np - 1) / *Np;
+}
+
+bool tcg_supported(const bcrown_net* net) {
+  for (int i = 0; i < net->L - 1; ++i) {
+    const LayerDev& l = net->ly[i];
+    if (l.kind != BCROWN_LAYER_CONV) {
+      if (l.d_in > 65536 || l.d_out > 65536) return false;
+      continue;
+    }
+    if (pad_to(l.in_c, 16) > 256 || pad_to(l.out_c, 16) > 256) return false;
+    if (kp_bwd(l) > IM2COL_MAX_KP || kp_fwd(l) > IM2COL_MAX_KP) return false;
+  }
+  int dev = 0, major = 0, minor = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  cudaGetLastError();
+  return major == 10 && minor == 3;
+}
+
+size_t tcg_col_bytes_per_row(const bcrown_net* net) {
+  size_t b = 0;
+  for (int i = 0; i < net->L - 1; ++i) {
+    const LayerDev& l = net->ly[i];
+    if (l.kind != BCROWN_LAYER_CONV) {
+      b = std::max(b, (size_t)std::max(pad_to(l.d_in, 64), pad_to(l.d_out, 64)) * sizeof(__nv_bfloat16));
+      continue;
+    }
+    const size_t ph = (size_t)((l.in_h + l.stride - 1) / l.stride) * ((l.in_w + l.stride - 1) / l.stride);
+    const size_t bwd = ph * kp_bwd(l);
+    const size_t fwd = (size_t)l.out_h * l.out_w * kp_fwd(l);
+    b = std::max(b, std::max(bwd, fwd) * sizeof(__nv_bfloat16));
+  }
+  return b;
+}
+
+// Fully connected layer i as the case of one position per row: B operands W^(i)^T (backward,
+// [d_in][d_out]) and W^(i) (forward, [d_out][d_in]) in BF16, K padded to 64, N to whole tiles.
+static int fc_prepare(const LayerDev& l, ConvTc* t, ConvTc::ConvW& c) {
+  std::vector<float> w((size_t)l.d_out * l.d_in);
+  if (cudaMemcpy(w.data(), l.W, w.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(BCROWN_ERR_CUDA, "copy of fc weights");
+  n_tiles(l.d_in, &c.Np_b, &c.ntn_b);
+  n_tiles(l.d_out, &c.Np_f, &c.ntn_f);
+  c.Kp_b = pad_to(l.d_out, 64);
+  c.Kp_f = pad_to(l.d_in, 64);
+  const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
+  std::vector<__nv_bfloat16> wb((size_t)c.ntn_b * c.Np_b * c.Kp_b, zero), wf((size_t)c.ntn_f * c.Np_f * c.Kp_f, zero);
+  for (int o = 0; o < l.d_out; ++o)
+    for (int n = 0; n < l.d_in; ++n) {
+      const __nv_bfloat16 v = __float2bfloat16_rn(w[(size_t)o * l.d_in + n]);
+      wb[(size_t)n * c.Kp_b + o] = v;
+      wf[(size_t)o * c.Kp_f + n] = v;
+    }
+  __nv_bfloat16 *db = nullptr, *df = nullptr;
+  if (cudaMalloc(&db, wb.size() * 2) != cudaSuccess || cudaMalloc(&df, wf.size() * 2) != cudaSuccess)
+    return fail(BCROWN_ERR_OOM, "bf16 fc weights");
+  t->bufs.push_back(db);
+  t->bufs.push_back(df);
+  if (cudaMemcpy(db, wb.data(), wb.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(df, wf.data(), wf.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail(BCROWN_ERR_CUDA, "bf16 fc weights upload");
+  BC_CHECK(encode_map(&c.mb, db, c.ntn_b * c.Np_b, c.Kp_b, c.Np_b));
+  BC_CHECK(encode_map(&c.mf, df, c.ntn_f * c.Np_f, c.Kp_f, c.Np_f));
+  c.wb = db;
+  c.wf = df;
+  return BCROWN_OK;
+}
+
+static int tcg_prepare(bcrown_net* net, ConvTc* t) {
+  if (t->ready) return BCROWN_OK;
+  t->conv.assign(net->L + 1, ConvTc::ConvW());
+  // layers 1 .. L-1 (the last one enters only through C W^(L))
+  for (int i = 1; i <= net->L - 1; ++i) {
+    const LayerDev& l = net->ly[i - 1];
+    if (l.kind != BCROWN_LAYER_CONV) {
+      BC_CHECK(fc_prepare(l, t, t->conv[i]));
+      continue;
+    }
+    const int kk = l.k * l.k, s = l.stride, T = taps_per_axis(l);
+    std::vector<float> w((size_t)l.out_c * l.in_c * kk);
+    if (cudaMemcpy(w.data(), l.W, w.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(BCROWN_ERR_CUDA, "copy of conv weights");
+    ConvTc::ConvW& c = t->conv[i];
+    c.Np_b = pad_to(l.in_c, 16);
+    c.Kp_b = kp_bwd(l);
+    c.Np_f = pad_to(l.out_c, 16);
+    c.Kp_f = kp_fwd(l);
+    const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
+    std::vector<__nv_bfloat16> wb((size_t)s * s * c.Np_b * c.Kp_b, zero);
+    std::vector<__nv_bfloat16> wf((size_t)c.Np_f * c.Kp_f, zero);
+    std::vector<int2> tb((size_t)s * s * c.Kp_b, make_int2(-1, 0)), tf((size_t)c.Kp_f, make_int2(-1, 0));
+    // forward: K = (ci, ky, kx), source (oy * s - pad + ky, ox * s - pad + kx) of channel ci
+    for (int co = 0; co < l.out_c; ++co)
+      for (int ci = 0; ci < l.in_c; ++ci)
+        for (int q = 0; q < kk; ++q)
+          wf[(size_t)co * c.Kp_f + ci * kk + q] = __float2bfloat16_rn(w[((size_t)co * l.in_c + ci) * kk + q]);
+    for (int ci = 0; ci < l.in_c; ++ci)
+      for (int q = 0; q < kk; ++q) tf[ci * kk + q] = tab_entry(ci * l.in_h * l.in_w, q / l.k, q % l.k);
+    // backward, phase (a, b): K = (co, dy, dx), tap (ky0 + s dy, kx0 + s dx), source q = (i + off - dy, ...)
+    for (int a = 0; a < s; ++a)
+      for (int b = 0; b < s; ++b) {
+        const ConvPhase py = conv_phase(a, l.k, s, l.pad, l.in_h), px = conv_phase(b, l.k, s, l.pad, l.in_w);
+        const size_t ph = (size_t)a * s + b;
+        for (int co = 0; co < l.out_c; ++co)
+          for (int dy = 0; dy < py.nk; ++dy)
+            for (int dx = 0; dx < px.nk; ++dx) {
+              const int K = co * T * T + dy * T + dx;
+              const int ky = py.k0 + s * dy, kx = px.k0 + s * dx;
+              tb[ph * c.Kp_b + K] = tab_entry(co * l.out_h * l.out_w, -dy, -dx);
+              for (int ci = 0; ci < l.in_c; ++ci)
+                wb[(ph * c.Np_b + ci) * c.Kp_b + K] =
+                    __float2bfloat16_rn(w[((size_t)co * l.in_c + ci) * kk + ky * l.k + kx]);
+            }
+      }
+    __nv_bfloat16 *db = nullptr, *df = nullptr;
+    if (cudaMalloc(&db, wb.size() * 2) != cudaSuccess || cudaMalloc(&df, wf.size() * 2) != cudaSuccess ||
+        cudaMalloc(&c.tab_b, tb.size() * sizeof(int2)) != cudaSuccess ||
+        cudaMalloc(&c.tab_f, tf.size() * sizeof(int2)) != cudaSuccess)
+      return fail(BCROWN_ERR_OOM, "bf16 conv weights");
+    t->bufs.push_back(db);
+    t->bufs.push_back(df);
+    t->bufs.push_back(c.tab_b);
+    t->bufs.push_back(c.tab_f);
+    if (cudaMemcpy(db, wb.data(), wb.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(df, wf.data(), wf.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c.tab_b, tb.data(), tb.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c.tab_f, tf.data(), tf.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail(BCROWN_ERR_CUDA, "bf16 conv weights upload");
+    BC_CHECK(encode_map(&c.mb, db, s * s * c.Np_b, c.Kp_b, c.Np_b));
+    BC_CHECK(encode_map(&c.mf, df, c.Np_f, c.Kp_f, c.Np_f));
+  }
+  BC_CUDA(cudaFuncSetAttribute(k_tcg, cudaFuncAttributeMaxDynamicSharedMemorySize, tcg_smem(256, TCG_BIAS_MAX, true)));
+  BC_CUDA(cudaFuncSetAttribute(k_im2col, cudaFuncAttributeMaxDynamicSharedMemorySize, im2col_smem(IM2COL_MAX_KP)));
+  t->ready = true;
+  return BCROWN_OK;
+}
+
+// One im2col + GEMM pass (a phase of a backward layer, or the forward layer; for a fully
+// connected layer, q.tab == nullptr, the operand is the source row converted to BF16).
+static int tcg_pass(bcrown_net* net, const Im2colPass& q, const CUtensorMap& mB, const TcgOut& o, const float* src,
+                    float* dst, const float* bias, char* col, size_t col_bytes, cudaStream_t s) {
+  if (q.M <= 0) return BCROWN_OK;
+  if ((size_t)q.M * q.Kp * sizeof(__nv_bfloat16) > col_bytes) return fail(BCROWN_ERR_OOM, "im2col workspace too small");
+  __nv_bfloat16* cb = reinterpret_cast<__nv_bfloat16*>(col);
+  if (q.tab)
+    k_im2col<<<(unsigned)((q.M + IM2COL_ROWS - 1) / IM2COL_ROWS), 256, im2col_smem(q.Kp), s>>>(q, src, cb);
+  else
+    k_rows_bf16<<<(unsigned)((q.M * (q.Kp / 8) + 255) / 256), 256, 0, s>>>(q.M, q.d_src, q.Kp, src, cb);
+  ++g_launches;
+  CUtensorMap mA;
+  BC_CHECK(encode_map(&mA, cb, (int)q.M, q.Kp, 128));
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long ntiles = (q.M + 127) / 128 * o.ntn;
+  const int grid = (int)std::min<long long>(ntiles, 2LL * sms);
+  const int smem = tcg_smem(o.Np, o.N, bias != nullptr);
+  k_tcg<<<grid, TCG_THREADS, smem, s>>>(mA, mB, o, dst, bias, net->status);
+  ++g_launches;
+  BC_CUDA(cudaGetLastError());
+  return BCROWN_OK;
+}
+
+int tcg_conv(bcrown_net* net, int i, bool fwd, int R, const float* src, float* dst, const float* bias, char* col,
+             size_t col_bytes, cudaStream_t s) {
+  ConvTc* t = conv_of(net);
+  BC_CHECK(tcg_prepare(net, t));
+  const LayerDev& l = net->ly[i - 1];
+  const ConvTc::ConvW& c = t->conv[i];
+  if (R <= 0) return BCROWN_OK;
+  if (l.kind != BCROWN_LAYER_CONV) {
+    const int dsrc = fwd ? l.d_in : l.d_out, ddst = fwd ? l.d_out : l.d_in;
+    const int Kp = fwd ? c.Kp_f : c.Kp_b;
+    const Im2colPass q{(long long)R, 1, 1, 0, 0, 0, 1, 1, dsrc, Kp, nullptr};
+    // Few row tiles (a small chunk, a long K): narrower N tiles until the grid covers the SMs;
+    // each halving still divides the padded rows of the weight operand.
+    int Np = fwd ? c.Np_f : c.Np_b;
+    const int rows = Np * (fwd ? c.ntn_f : c.ntn_b);
+    const long long mt = ((long long)R + 127) / 128;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    while (Np % 32 == 0 && Np > 32 && mt * ((ddst + Np - 1) / Np) < sms) Np /= 2;
+    CUtensorMap mB = fwd ? c.mf : c.mb;
+    if (Np != (fwd ? c.Np_f : c.Np_b)) BC_CHECK(encode_map(&mB, fwd ? c.wf : c.wb, rows, Kp, Np));
+    const TcgOut o{q.M, ddst, Np, (ddst + Np - 1) / Np, Kp / 64, 0, 1, 1, 0, 0, 1, 1, 1, (long long)ddst};
+    return tcg_pass(net, q, mB, o, src, dst, fwd ? bias : nullptr, col, col_bytes, s);
+  }
+  if (fwd) {
+    const int P = l.out_h * l.out_w;
+    const Im2colPass q{(long long)R * P, P, l.out_w, l.stride, -l.pad, -l.pad, l.in_h, l.in_w, l.d_in, c.Kp_f, c.tab_f};
+    const TcgOut o{q.M, l.out_c, c.Np_f, 1, c.Kp_f / 64, 0, P, l.out_w, 0, 0, 1, l.out_w, P, (long long)l.d_out};
+    return tcg_pass(net, q, c.mf, o, src, dst, bias, col, col_bytes, s);
+  }
+  const int st = l.stride;
+  for (int a = 0; a < st; ++a)
+    for (int b = 0; b < st; ++b) {
+      const ConvPhase py = conv_phase(a, l.k, st, l.pad, l.in_h), px = conv_phase(b, l.k, st, l.pad, l.in_w);
+      const int Pm = py.n * px.n;
+      if (Pm == 0) continue;
+      const int ph = a * st + b;
+      const Im2colPass q{(long long)R * Pm, Pm, px.n, 1, py.off, px.off, l.out_h, l.out_w, l.d_out, c.Kp_b,
+                         c.tab_b + (size_t)ph * c.Kp_b};
+      const TcgOut o{q.M, l.in_c, c.Np_b, 1, c.Kp_b / 64, ph * c.Np_b, Pm, px.n, a, b, st, l.in_w,
+                     l.in_h * l.in_w, (long long)l.d_in};
+      BC_CHECK(tcg_pass(net, q, c.mb, o, src, dst, nullptr, col, col_bytes, s));
+    }
+  return BCROWN_OK;
+}
+
+void tcg_release(const bcrown_net* net) {
+  std::lock_guard<std::mutex> g(g_conv_mu);
+  for (size_t i = 0; i < g_conv.size(); ++i)
+    if (g_conv[i].first == net) {
+      for (void* b : g_conv[i].second->bufs) cudaFree(b);
+      delete g_conv[i].second;
+      g_conv.erase(g_conv.begin() + i);
+      return;
+    }
+}
+
+}  // namespace bcrown

@@ -31,6 +31,7 @@
 #include <cstring>
 
 #include "fused_tc.cuh"
+#include "tc_ptx.cuh"
 
 namespace bcrown {
 
@@ -40,7 +41,6 @@ namespace tc {
 
 constexpr int TR = 64;            // rows per tile = MMA N
 constexpr int MCH = 128;          // neurons per M chunk = MMA M
-constexpr int KBLK = 64;          // bf16 per K block (128 bytes, one swizzle row)
 constexpr int NSLOT = 8;          // activation (B operand) ring
 constexpr int NSTAGE = 4;         // weight (A operand) ring
 constexpr int NACC = 4;           // accumulator ring (TR columns each)
@@ -130,40 +130,7 @@ struct Maps {
 // ------------------------------------------------------------------------------------------
 // PTX helpers
 // ------------------------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
-  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(su32(b)) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
-  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(su32(b)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(su32(b)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// As mbar_try, but a thread whose phase is not complete yet is suspended (for at most about
-// `ns` nanoseconds) until it completes, instead of returning at once: waiting threads then
-// leave the issue slots and the shared-memory pipe to the warps doing work.
-__device__ __forceinline__ bool mbar_try_sleep(uint64_t* b, uint32_t parity, uint32_t ns) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(su32(b)), "r"(parity), "r"(ns)
-      : "memory");
-  return ok != 0;
-}
 // Bounded wait (about 2 s of SM clock); on expiry records a timeout and raises the abort flag.
 // Inlined: as a called function it cost the single-thread MMA and TMA loops ~0.2 us per wait.
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, Smem* sm, int* status) {
@@ -196,90 +163,12 @@ __device__ __forceinline__ bool epi_sync(Smem* sm, uint32_t& seq, int* status) {
   ++seq;
   return ok;
 }
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          su32(dst)),
-      "l"((uint64_t)map), "r"(x), "r"(y), "r"(su32(bar))
-      : "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 // Barrier among the 16 epilogue warps built on an mbarrier, so that a warp that gives up
 // after a timeout cannot leave the others blocked: every wait here is bounded.
 __device__ __forceinline__ bool epi_sync(Smem* sm, uint32_t& seq, int* status);
 
-// Shared-memory matrix descriptor, K-major, 128-byte swizzle, 8-row groups 1024 B apart.
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)1 << 16;                 // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset
-  d |= (uint64_t)1 << 46;                 // descriptor version
-  d |= (uint64_t)2 << 61;                 // SWIZZLE_128B
-  return d;
-}
-// Instruction descriptor: BF16 x BF16 -> FP32, both K-major, M = 128, N = n.
-__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(MCH >> 4) << 24);
-}
-// One 64-wide K block: four MMAs of K = 16.  Descriptors of consecutive 16-element K steps
-// differ by 32 bytes in the start address (field unit 16 bytes: +2); `acc` = 0 starts the
-// accumulator with the first MMA.
-__device__ __forceinline__ void umma_kblock(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %4, 0;\n\tsetp.eq.b32 q, 0, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %5, %6, %3, q;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %7, %8, %3, q;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %9, %10, %3, q;\n\t}" ::"r"(dtmem),
-      "l"(ad), "l"(bd), "r"(idesc), "r"(acc), "l"(ad + 2), "l"(bd + 2), "l"(ad + 4), "l"(bd + 4), "l"(ad + 6),
-      "l"(bd + 6)
-      : "memory");
-}
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
-               : "memory");
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr)
-      : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
 
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
-  uint32_t r[8];
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-               : "r"(taddr)
-               : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
-}
 
-// Split form of tmem_ld8: the load, then the wait.  The wait names the registers as in-out
-// operands, so no use of them can be scheduled before it.
-__device__ __forceinline__ void tmem_ld8_issue(uint32_t taddr, uint32_t (&r)[8]) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-               : "r"(taddr)
-               : "memory");
-}
-__device__ __forceinline__ void tmem_wait8(uint32_t (&r)[8]) {
-  asm volatile("tcgen05.wait::ld.sync.aligned;"
-               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7])
-               :
-               : "memory");
-}
 
 // Loads issued where they are written (volatile asm keeps them ahead of the barrier waits that
 // follow, instead of letting the compiler sink them to their first use); 0 when pred is false.
@@ -1227,234 +1116,6 @@ __global__ void k_plan_rows(int max_tiles, int K, int P, const int* __restrict__
 }
 
 // ------------------------------------------------------------------------------------------
-// Convolutions on the tensor cores (BF16 precision of the layer-by-layer path): the contraction
-// of a conv layer as GEMMs over an im2col operand.
-//   forward:   Z[r][co][p] = sum_K Col[(r, p)][K] Wf[co][K] + b,   K = (ci, ky, kx)
-//   backward:  the transposed convolution Ain[r][ci][p] = sum Lambda[r][co][q] W[co][ci][tap]
-//              over the (q, tap) with p = q * s - pad + tap.  For stride s the input positions
-//              fall into s x s phases (p_y mod s, p_x mod s); within a phase only the taps
-//              ky = ky0 + s * dy (dy < ceil(k / s)) reach the stride grid, and the source
-//              position is q_y = i + off - dy for the phase's i-th row.  Each phase is one GEMM
-//              with K = (co, dy, dx) and its own weight matrix, so the operand holds no
-//              structural zeros of the stride.
-// Col is gathered into BF16 by k_im2col from a per-K table (source channel offset, signed tap
-// offsets: no divisions in the inner loop); k_tcg multiplies it with the BF16 weights:
-// M = rows x positions (tiles of 128 on the TMEM lanes), N = channels (padded to 16), K in
-// blocks of 64 streamed by TMA.
-// ------------------------------------------------------------------------------------------
-constexpr int TCG_NS = 4;         // pipeline stages (A: 128 x 64, B: Np x 64)
-constexpr int TCG_THREADS = 192;  // warps 0-3 epilogue, 4 TMA, 5 MMA
-
-// One gather: row m = (r, pp), pp = i * nJ + j; source position (y0 + dy_K, x0 + dx_K) with
-// y0 = i * ms + cy, x0 = j * ms + cx, in a [C][Hs][Ws] map of row r (d_src floats per row).
-struct Im2colPass {
-  long long M;
-  int Pm, nJ, ms, cy, cx, Hs, Ws, d_src, Kp;
-  const int2* tab;  // [Kp]: {channel offset C * Hs * Ws, or -1 for a zero column; (dy & 0xffff) | dx << 16}
-};
-
-// 32 consecutive rows m per block.  Lanes walk the 32 rows for one pair of K at a time (K
-// uniform per warp: coalesced source reads) into a shared tile [32][Kp + 8], whose rows then
-// leave in 16-byte stores.
-constexpr int IM2COL_ROWS = 32;
-constexpr int IM2COL_MAX_KP = 2048;
-inline int im2col_smem(int Kp) { return Kp * (int)sizeof(int2) + IM2COL_ROWS * (Kp + 8) * 2; }
-__global__ void __launch_bounds__(256) k_im2col(Im2colPass q, const float* __restrict__ src,
-                                                __nv_bfloat16* __restrict__ col) {
-  extern __shared__ __align__(16) uint8_t im_raw[];
-  const int Kp = q.Kp, S = Kp + 8;  // row stride (bf16), 16-byte aligned rows
-  int2* tab = reinterpret_cast<int2*>(im_raw);
-  __nv_bfloat16* tile = reinterpret_cast<__nv_bfloat16*>(im_raw + (size_t)Kp * sizeof(int2));
-  for (int k = threadIdx.x; k < Kp; k += 256) tab[k] = q.tab[k];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const long long m0 = (long long)blockIdx.x * IM2COL_ROWS;
-  const long long m = m0 + lane;
-  const bool mv = m < q.M;
-  const int r = mv ? (int)(m / q.Pm) : 0;
-  const int pp = mv ? (int)(m - (long long)r * q.Pm) : 0;
-  const int i = pp / q.nJ, j = pp - (pp / q.nJ) * q.nJ;
-  const int y0 = i * q.ms + q.cy, x0 = j * q.ms + q.cx;
-  const float* sr = src + (size_t)r * q.d_src;
-  __syncthreads();
-  for (int K = 2 * w; K < Kp; K += 16) {
-    float v[2];
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      const int2 t = tab[K + e];
-      const int y = y0 + (int)(short)(t.y & 0xffff), x = x0 + (t.y >> 16);
-      v[e] = (mv && t.x >= 0 && (unsigned)y < (unsigned)q.Hs && (unsigned)x < (unsigned)q.Ws)
-                 ? sr[t.x + y * q.Ws + x]
-                 : 0.f;
-    }
-    *reinterpret_cast<__nv_bfloat162*>(tile + lane * S + K) = __floats2bfloat162_rn(v[0], v[1]);
-  }
-  __syncthreads();
-  const int cpr = Kp / 8;
-  for (int row = w; row < IM2COL_ROWS; row += 8) {
-    if (m0 + row >= q.M) break;
-    uint4* dst = reinterpret_cast<uint4*>(col + (m0 + row) * Kp);
-    const uint4* sv = reinterpret_cast<const uint4*>(tile + row * S);
-    for (int c = lane; c < cpr; c += 32) dst[c] = sv[c];
-  }
-}
-
-// Where k_tcg writes: row m = (r, pp), pp = i * nJ + j, goes to position
-// p = (a + so * i) * Wo + (b + so * j) of out[r * stride + n * P + p] (+ bias[n * P + p]).
-struct TcgOut {
-  long long M;
-  int N, Np, nkb, brow;  // brow: first row of the weight operand's tile in its tensor map
-  int Pm, nJ, a, b, so, Wo, P;
-  long long stride;
-};
-
-// Bounded wait for k_tcg (same limit and error reporting as mbar_wait).
-__device__ __forceinline__ bool tcg_wait(uint64_t* b, uint32_t parity, volatile int* abort, int* status) {
-  if (mbar_try(b, parity)) return true;
-  long long t0 = clock64();
-  while (true) {
-    if (mbar_try_sleep(b, parity, 20000u)) return true;
-    if (*abort) return false;
-    if (clock64() - t0 > 4000000000LL) {
-      atomicCAS(status, 0, BCROWN_ERR_TIMEOUT);
-      *abort = 1;
-      return false;
-    }
-  }
-}
-
-// out[r * stride + n * P + p] = (Col x W^T)[m = r * P + p][n] (+ bias[n * P + p]) for n < N.
-__global__ void __launch_bounds__(TCG_THREADS, 1) k_tcg(const __grid_constant__ CUtensorMap mapA,
-                                                        const __grid_constant__ CUtensorMap mapB, TcgOut o,
-                                                        float* __restrict__ out, const float* __restrict__ bias,
-                                                        int* status) {
-  const long long M = o.M;
-  const int N = o.N, Np = o.Np, nkb = o.nkb;
-  extern __shared__ __align__(1024) uint8_t tsm_raw[];
-  const uint32_t pad = (1024u - (su32(tsm_raw) & 1023u)) & 1023u;
-  uint8_t* base = tsm_raw + pad;
-  const int bbytes = Np * 128;
-  uint8_t* sA = base;                                  // TCG_NS x 16 KB
-  uint8_t* sB = base + TCG_NS * 16384;                 // TCG_NS x Np*128
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + TCG_NS * bbytes);
-  uint64_t* full = bars;
-  uint64_t* empty = bars + TCG_NS;
-  uint64_t* acc_full = bars + 2 * TCG_NS;
-  uint64_t* acc_empty = bars + 2 * TCG_NS + 2;
-  uint32_t* tbase_sm = reinterpret_cast<uint32_t*>(bars + 2 * TCG_NS + 4);
-  volatile int* abort = reinterpret_cast<volatile int*>(tbase_sm + 1);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long ntiles = (M + 127) / 128;
-  // two accumulators of Np columns, allocated as a power of two >= 32
-  const uint32_t tcols = Np <= 16 ? 32u : (Np <= 32 ? 64u : (Np <= 64 ? 128u : (Np <= 128 ? 256u : 512u)));
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < TCG_NS; ++i) {
-      mbar_init(&full[i], 1);
-      mbar_init(&empty[i], 1);
-    }
-    for (int i = 0; i < 2; ++i) {
-      mbar_init(&acc_full[i], 1);
-      mbar_init(&acc_empty[i], 4);
-    }
-    *abort = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 5) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tbase_sm)), "r"(tcols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = *tbase_sm;
-  if (warp == 4) {
-    if (lane == 0) {
-      uint32_t seq = 0;
-      bool ok = true;
-      for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x)
-        for (int kb = 0; kb < nkb; ++kb, ++seq) {
-          const int st = seq % TCG_NS;
-          if (!tcg_wait(&empty[st], ((seq / TCG_NS) & 1) ^ 1, abort, status)) {
-            ok = false;
-            break;
-          }
-          mbar_expect_tx(&full[st], 16384u + (uint32_t)bbytes);
-          tma_load_2d(sA + st * 16384, &mapA, kb * 64, (int)(tile * 128), &full[st]);
-          tma_load_2d(sB + st * bbytes, &mapB, kb * 64, o.brow, &full[st]);
-        }
-      if (!ok) {
-        for (uint32_t q = (seq > TCG_NS ? seq - TCG_NS : 0); q < seq; ++q) {
-          long long t0 = clock64();
-          while (!mbar_try(&full[q % TCG_NS], (q / TCG_NS) & 1) && clock64() - t0 < 200000000LL) {
-          }
-        }
-      }
-    }
-  } else if (warp == 5) {
-    if (lane == 0) {
-      uint32_t seq = 0, accseq = 0;
-      bool ok = true;
-      const uint32_t idesc = idesc_bf16(Np);
-      for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++accseq) {
-        const int buf = accseq & 1;
-        if (!tcg_wait(&acc_empty[buf], ((accseq >> 1) & 1) ^ 1, abort, status)) break;
-        tc_fence_after();
-        const uint32_t dt = tmem + (uint32_t)(buf * Np);
-        for (int kb = 0; kb < nkb; ++kb, ++seq) {
-          const int st = seq % TCG_NS;
-          if (!tcg_wait(&full[st], (seq / TCG_NS) & 1, abort, status)) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          umma_kblock(dt, sdesc(su32(sA + st * 16384)), sdesc(su32(sB + st * bbytes)), idesc, kb != 0 ? 1u : 0u);
-          umma_commit(&empty[st]);
-        }
-        if (!ok) break;
-        umma_commit(&acc_full[buf]);
-      }
-    }
-  } else {
-    // epilogue: warp w owns TMEM lanes (tile rows) 32w..32w+31
-    uint32_t accseq = 0;
-    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++accseq) {
-      const int buf = accseq & 1;
-      int okw = 1;
-      if (lane == 0) okw = tcg_wait(&acc_full[buf], (accseq >> 1) & 1, abort, status) ? 1 : 0;
-      okw = __shfl_sync(0xffffffffu, okw, 0);
-      if (!okw) break;
-      tc_fence_after();
-      const long long m = tile * 128 + 32 * warp + lane;
-      const bool min_ = m < M;
-      const long long r = min_ ? m / o.Pm : 0;
-      const int pp = min_ ? (int)(m - r * o.Pm) : 0;
-      const int i = pp / o.nJ, j = pp - (pp / o.nJ) * o.nJ;
-      const int p = (o.a + o.so * i) * o.Wo + o.b + o.so * j;
-      float* orow = out + r * o.stride + p;
-      for (int n0 = 0; n0 < Np; n0 += 16) {
-        float v[16];
-        tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(buf * Np + n0), v);
-        if (min_) {
-#pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            const int n = n0 + e;
-            if (n < N) orow[(size_t)n * o.P] = v[e] + (bias ? bias[(size_t)n * o.P + p] : 0.f);
-          }
-        }
-      }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&acc_empty[buf]);
-    }
-  }
-  tc_fence_before();
-  __syncthreads();
-  if (warp == 5) {
-    tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols) : "memory");
-  }
-}
-
 }  // namespace tc
 
 // ------------------------------------------------------------------------------------------
@@ -1473,11 +1134,6 @@ struct TcNet {
   // conv layers on the tensor cores: BF16 weight matrices [Np][Kp] for the backward (rows =
   // input channels) and the forward (rows = output channels), with their TMA maps
   bool conv_ready = false;
-  struct ConvW {
-    int Np_b = 0, Kp_b = 0, Np_f = 0, Kp_f = 0;
-    CUtensorMap mb, mf;              // mb: the s * s phase matrices stacked, Np_b rows each
-    int2 *tab_b = nullptr, *tab_f = nullptr;  // gather tables: [s * s][Kp_b], [Kp_f]
-  } conv[MAXL + 1];
 };
 
 static std::mutex g_tc_mu;
@@ -1549,25 +1205,6 @@ size_t tc_workspace_bytes(const bcrown_net* net, int B, int P, bool grad) {
   return carve(nullptr, B, net->K, P, net->H, grad, nullptr);
 }
 
-static int encode_map(CUtensorMap* m, void* base, int rows, int kp, int box_rows) {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-        !p)
-      return fail(BCROWN_ERR_CUDA, "cuTensorMapEncodeTiled not available");
-    fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-  }
-  cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)kp * 2};
-  cuuint32_t box[2] = {(cuuint32_t)KBLK, (cuuint32_t)box_rows};
-  cuuint32_t es[2] = {1, 1};
-  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) return fail(BCROWN_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
-  return BCROWN_OK;
-}
 
 // BF16 copy of a [rows][cols] FP32 matrix with the row length padded to a multiple of 64.
 static int padded_bf16(const float* src_dev, int rows, int cols, __nv_bfloat16** out, int* kp) {
@@ -1698,177 +1335,6 @@ int tc_bound(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* bt, 
   A.dalpha16 = dalpha16;
   A.dbeta = dbeta;
   return tc_launch(net, dom, bt, tb, A, ws, ws_bytes, !grad ? 0 : (dalpha16 ? 2 : 1), plan, s);
-}
-
-// ---------------------------------------------------------------- conv layers on tensor cores
-static int pad_to(int x, int m) { return (x + m - 1) / m * m; }
-
-// Phase a of one spatial axis of a stride-s transposed convolution: the taps ky0 + s * dy
-// (dy < nk) that reach the stride grid from input rows a + s * i (i < n), whose source row is
-// i + off - dy.
-struct ConvPhase {
-  int k0, nk, off, n;
-};
-static ConvPhase conv_phase(int a, int k, int s, int pad, int in) {
-  ConvPhase c;
-  c.k0 = (a + pad) % s;
-  c.nk = c.k0 < k ? (k - c.k0 + s - 1) / s : 0;
-  c.off = (a + pad - c.k0) / s;
-  c.n = a < in ? (in - a + s - 1) / s : 0;
-  return c;
-}
-static int taps_per_axis(const LayerDev& l) { return (l.k + l.stride - 1) / l.stride; }
-static int kp_bwd(const LayerDev& l) { return pad_to(l.out_c * taps_per_axis(l) * taps_per_axis(l), 64); }
-static int kp_fwd(const LayerDev& l) { return pad_to(l.in_c * l.k * l.k, 64); }
-static int2 tab_entry(int chan_off, int dy, int dx) {
-  return make_int2(chan_off, (int)(((uint32_t)dy & 0xffffu) | ((uint32_t)dx << 16)));
-}
-
-bool tcg_supported(const bcrown_net* net) {
-  bool conv = false;
-  for (int i = 0; i < net->L; ++i) {
-    const LayerDev& l = net->ly[i];
-    if (l.kind != BCROWN_LAYER_CONV) continue;
-    conv = true;
-    if (pad_to(l.in_c, 16) > 256 || pad_to(l.out_c, 16) > 256) return false;
-    if (kp_bwd(l) > IM2COL_MAX_KP || kp_fwd(l) > IM2COL_MAX_KP) return false;
-  }
-  if (!conv) return false;
-  int dev = 0, major = 0, minor = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return false;
-  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
-  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
-  cudaGetLastError();
-  return major == 10 && minor == 3;
-}
-
-size_t tcg_col_bytes_per_row(const bcrown_net* net) {
-  size_t b = 0;
-  for (int i = 0; i < net->L; ++i) {
-    const LayerDev& l = net->ly[i];
-    if (l.kind != BCROWN_LAYER_CONV) continue;
-    const size_t ph = (size_t)((l.in_h + l.stride - 1) / l.stride) * ((l.in_w + l.stride - 1) / l.stride);
-    const size_t bwd = ph * kp_bwd(l);
-    const size_t fwd = (size_t)l.out_h * l.out_w * kp_fwd(l);
-    b = std::max(b, std::max(bwd, fwd) * sizeof(__nv_bfloat16));
-  }
-  return b;
-}
-
-static int tcg_prepare(bcrown_net* net, TcNet* t) {
-  if (t->conv_ready) return BCROWN_OK;
-  for (int i = 1; i <= net->L; ++i) {
-    const LayerDev& l = net->ly[i - 1];
-    if (l.kind != BCROWN_LAYER_CONV) continue;
-    const int kk = l.k * l.k, s = l.stride, T = taps_per_axis(l);
-    std::vector<float> w((size_t)l.out_c * l.in_c * kk);
-    if (cudaMemcpy(w.data(), l.W, w.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
-      return fail(BCROWN_ERR_CUDA, "copy of conv weights");
-    TcNet::ConvW& c = t->conv[i];
-    c.Np_b = pad_to(l.in_c, 16);
-    c.Kp_b = kp_bwd(l);
-    c.Np_f = pad_to(l.out_c, 16);
-    c.Kp_f = kp_fwd(l);
-    const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
-    std::vector<__nv_bfloat16> wb((size_t)s * s * c.Np_b * c.Kp_b, zero);
-    std::vector<__nv_bfloat16> wf((size_t)c.Np_f * c.Kp_f, zero);
-    std::vector<int2> tb((size_t)s * s * c.Kp_b, make_int2(-1, 0)), tf((size_t)c.Kp_f, make_int2(-1, 0));
-    // forward: K = (ci, ky, kx), source (oy * s - pad + ky, ox * s - pad + kx) of channel ci
-    for (int co = 0; co < l.out_c; ++co)
-      for (int ci = 0; ci < l.in_c; ++ci)
-        for (int q = 0; q < kk; ++q)
-          wf[(size_t)co * c.Kp_f + ci * kk + q] = __float2bfloat16_rn(w[((size_t)co * l.in_c + ci) * kk + q]);
-    for (int ci = 0; ci < l.in_c; ++ci)
-      for (int q = 0; q < kk; ++q) tf[ci * kk + q] = tab_entry(ci * l.in_h * l.in_w, q / l.k, q % l.k);
-    // backward, phase (a, b): K = (co, dy, dx), tap (ky0 + s dy, kx0 + s dx), source q = (i + off - dy, ...)
-    for (int a = 0; a < s; ++a)
-      for (int b = 0; b < s; ++b) {
-        const ConvPhase py = conv_phase(a, l.k, s, l.pad, l.in_h), px = conv_phase(b, l.k, s, l.pad, l.in_w);
-        const size_t ph = (size_t)a * s + b;
-        for (int co = 0; co < l.out_c; ++co)
-          for (int dy = 0; dy < py.nk; ++dy)
-            for (int dx = 0; dx < px.nk; ++dx) {
-              const int K = co * T * T + dy * T + dx;
-              const int ky = py.k0 + s * dy, kx = px.k0 + s * dx;
-              tb[ph * c.Kp_b + K] = tab_entry(co * l.out_h * l.out_w, -dy, -dx);
-              for (int ci = 0; ci < l.in_c; ++ci)
-                wb[(ph * c.Np_b + ci) * c.Kp_b + K] =
-                    __float2bfloat16_rn(w[((size_t)co * l.in_c + ci) * kk + ky * l.k + kx]);
-            }
-      }
-    __nv_bfloat16 *db = nullptr, *df = nullptr;
-    if (cudaMalloc(&db, wb.size() * 2) != cudaSuccess || cudaMalloc(&df, wf.size() * 2) != cudaSuccess ||
-        cudaMalloc(&c.tab_b, tb.size() * sizeof(int2)) != cudaSuccess ||
-        cudaMalloc(&c.tab_f, tf.size() * sizeof(int2)) != cudaSuccess)
-      return fail(BCROWN_ERR_OOM, "bf16 conv weights");
-    t->bufs.push_back(db);
-    t->bufs.push_back(df);
-    t->bufs.push_back(reinterpret_cast<__nv_bfloat16*>(c.tab_b));
-    t->bufs.push_back(reinterpret_cast<__nv_bfloat16*>(c.tab_f));
-    if (cudaMemcpy(db, wb.data(), wb.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(df, wf.data(), wf.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(c.tab_b, tb.data(), tb.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(c.tab_f, tf.data(), tf.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess)
-      return fail(BCROWN_ERR_CUDA, "bf16 conv weights upload");
-    BC_CHECK(encode_map(&c.mb, db, s * s * c.Np_b, c.Kp_b, c.Np_b));
-    BC_CHECK(encode_map(&c.mf, df, c.Np_f, c.Kp_f, c.Np_f));
-  }
-  const int smem = 1024 + TCG_NS * (16384 + 256 * 128) + 256;
-  BC_CUDA(cudaFuncSetAttribute(k_tcg, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  BC_CUDA(cudaFuncSetAttribute(k_im2col, cudaFuncAttributeMaxDynamicSharedMemorySize, im2col_smem(IM2COL_MAX_KP)));
-  t->conv_ready = true;
-  return BCROWN_OK;
-}
-
-// One im2col + GEMM pass (a phase of a backward layer, or the forward layer).
-static int tcg_pass(bcrown_net* net, const Im2colPass& q, const CUtensorMap& mB, const TcgOut& o, const float* src,
-                    float* dst, const float* bias, char* col, size_t col_bytes, cudaStream_t s) {
-  if (q.M <= 0) return BCROWN_OK;
-  if ((size_t)q.M * q.Kp * sizeof(__nv_bfloat16) > col_bytes) return fail(BCROWN_ERR_OOM, "im2col workspace too small");
-  __nv_bfloat16* cb = reinterpret_cast<__nv_bfloat16*>(col);
-  k_im2col<<<(unsigned)((q.M + IM2COL_ROWS - 1) / IM2COL_ROWS), 256, im2col_smem(q.Kp), s>>>(q, src, cb);
-  ++g_launches;
-  CUtensorMap mA;
-  BC_CHECK(encode_map(&mA, cb, (int)q.M, q.Kp, 128));
-  int dev = 0, sms = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const long long ntiles = (q.M + 127) / 128;
-  const int grid = (int)std::min<long long>(ntiles, 2LL * sms);
-  const int smem = 1024 + TCG_NS * (16384 + o.Np * 128) + 256;
-  k_tcg<<<grid, TCG_THREADS, smem, s>>>(mA, mB, o, dst, bias, net->status);
-  ++g_launches;
-  BC_CUDA(cudaGetLastError());
-  return BCROWN_OK;
-}
-
-int tcg_conv(bcrown_net* net, int i, bool fwd, int R, const float* src, float* dst, const float* bias, char* col,
-             size_t col_bytes, cudaStream_t s) {
-  TcNet* t = tc_of(net);
-  BC_CHECK(tcg_prepare(net, t));
-  const LayerDev& l = net->ly[i - 1];
-  const TcNet::ConvW& c = t->conv[i];
-  if (R <= 0) return BCROWN_OK;
-  if (fwd) {
-    const int P = l.out_h * l.out_w;
-    const Im2colPass q{(long long)R * P, P, l.out_w, l.stride, -l.pad, -l.pad, l.in_h, l.in_w, l.d_in, c.Kp_f, c.tab_f};
-    const TcgOut o{q.M, l.out_c, c.Np_f, c.Kp_f / 64, 0, P, l.out_w, 0, 0, 1, l.out_w, P, (long long)l.d_out};
-    return tcg_pass(net, q, c.mf, o, src, dst, bias, col, col_bytes, s);
-  }
-  const int st = l.stride;
-  for (int a = 0; a < st; ++a)
-    for (int b = 0; b < st; ++b) {
-      const ConvPhase py = conv_phase(a, l.k, st, l.pad, l.in_h), px = conv_phase(b, l.k, st, l.pad, l.in_w);
-      const int Pm = py.n * px.n;
-      if (Pm == 0) continue;
-      const int ph = a * st + b;
-      const Im2colPass q{(long long)R * Pm, Pm, px.n, 1, py.off, px.off, l.out_h, l.out_w, l.d_out, c.Kp_b,
-                         c.tab_b + (size_t)ph * c.Kp_b};
-      const TcgOut o{q.M, l.in_c, c.Np_b, c.Kp_b / 64, ph * c.Np_b, Pm, px.n, a, b, st, l.in_w,
-                     l.in_h * l.in_w, (long long)l.d_in};
-      BC_CHECK(tcg_pass(net, q, c.mb, o, src, dst, nullptr, col, col_bytes, s));
-    }
-  return BCROWN_OK;
 }
 
 void tc_release(const bcrown_net* net) {

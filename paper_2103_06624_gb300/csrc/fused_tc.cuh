@@ -19,13 +19,6 @@ int tc_bound(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* bt, 
              size_t ws_bytes, bool grad, bool plan, const float* alpha, const float* beta, float* lb, float* dalpha,
              float* dbeta, cudaStream_t s, __nv_bfloat16* dalpha16 = nullptr);
 
-// Conv layers on the tensor cores (BF16 operands, FP32 accumulation) for the layer-by-layer
-// path: im2col of the operand into `col` (tcg_col_bytes_per_row bytes per row at most), then one
-// tcgen05 GEMM.  fwd = false: dst = A^(i-1) from src = Lambda^(i); fwd = true: dst = W h + b.
-bool tcg_supported(const bcrown_net* net);
-size_t tcg_col_bytes_per_row(const bcrown_net* net);
-int tcg_conv(bcrown_net* net, int i, bool fwd, int R, const float* src, float* dst, const float* bias, char* col,
-             size_t col_bytes, cudaStream_t s);
 void tc_release(const bcrown_net* net);
 
 }  // namespace bcrown

@@ -6,6 +6,7 @@
 #include <cstring>
 
 #include "bcrown_internal.cuh"
+#include "conv_tc.cuh"
 #include "fused_tc.cuh"
 
 namespace bcrown {
@@ -103,6 +104,7 @@ extern "C" void bcrown_free_net(bcrown_net* net) {
   if (!net) return;
   cudaDeviceSynchronize();
   tc_release(net);
+  tcg_release(net);
   for (auto& l : net->ly) {
     cudaFree(l.W);
     cudaFree(l.Wt);

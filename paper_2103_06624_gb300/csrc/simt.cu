@@ -15,26 +15,65 @@ std::atomic<long long> g_launches{0};
 // ----------------------------------------------------------------------------------------
 // Per-property tables from l, u: code, unstable rank, upper chord (Lemma 2.1)
 // ----------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_tables(int H, const float* __restrict__ l,
+// Property p's neurons in segments of TAB_SEG, one block per (property, segment).  With more
+// than one segment the unstable ranks need each segment's offset: k_tables_count counts a
+// segment's unstable neurons into the first rank slot of the segment, k_tables_scan turns
+// those counts into exclusive offsets in place (and U[p] = the total), and k_tables starts
+// from the offset in its first slot, which only its own block reads and overwrites.
+constexpr int TAB_SEG = 4096;
+
+__device__ __forceinline__ bool is_unstable(float lv, float uv) { return lv < 0.f && uv > 0.f; }
+
+__global__ void __launch_bounds__(1024) k_tables_count(int H, const float* __restrict__ l,
+                                                       const float* __restrict__ u, int32_t* rank) {
+  __shared__ int tot;
+  const int p = blockIdx.x, seg = blockIdx.y;
+  if (threadIdx.x == 0) tot = 0;
+  __syncthreads();
+  int c = 0;
+  const int end = min(H, (seg + 1) * TAB_SEG);
+  for (int n = seg * TAB_SEG + threadIdx.x; n < end; n += blockDim.x)
+    c += is_unstable(l[(size_t)p * H + n], u[(size_t)p * H + n]) ? 1 : 0;
+  c = __reduce_add_sync(0xffffffffu, c);
+  if ((threadIdx.x & 31) == 0) atomicAdd(&tot, c);
+  __syncthreads();
+  if (threadIdx.x == 0) rank[(size_t)p * H + (size_t)seg * TAB_SEG] = tot;
+}
+
+__global__ void k_tables_scan(int H, int nseg, int32_t* rank, int32_t* U) {
+  const int p = blockIdx.x;
+  if (threadIdx.x != 0) return;
+  int run = 0;
+  for (int q = 0; q < nseg; ++q) {
+    int32_t* slot = rank + (size_t)p * H + (size_t)q * TAB_SEG;
+    const int c = *slot;
+    *slot = run;
+    run += c;
+  }
+  U[p] = run;
+}
+
+__global__ void __launch_bounds__(1024) k_tables(int H, int nseg, const float* __restrict__ l,
                                                  const float* __restrict__ u, uint8_t* code,
                                                  int32_t* rank, float* slope, float* icpt,
                                                  int32_t* U) {
   __shared__ int warp_tot[32];
   __shared__ int running;
-  const int p = blockIdx.x;
+  const int p = blockIdx.x, seg = blockIdx.y;
   const float* lp = l + (size_t)p * H;
   const float* up = u + (size_t)p * H;
-  if (threadIdx.x == 0) running = 0;
+  if (threadIdx.x == 0) running = nseg > 1 ? rank[(size_t)p * H + (size_t)seg * TAB_SEG] : 0;
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int base = 0; base < H; base += blockDim.x) {
+  const int end = min(H, (seg + 1) * TAB_SEG);
+  for (int base = seg * TAB_SEG; base < end; base += blockDim.x) {
     int n = base + threadIdx.x;
     float lv = 0.f, uv = 0.f;
     bool un = false;
-    if (n < H) {
+    if (n < end) {
       lv = lp[n];
       uv = up[n];
-      un = (lv < 0.f) && (uv > 0.f);
+      un = is_unstable(lv, uv);
     }
     unsigned m = __ballot_sync(0xffffffffu, un);
     int pre = __popc(m & ((1u << lane) - 1u));
@@ -45,7 +84,7 @@ __global__ void __launch_bounds__(1024) k_tables(int H, const float* __restrict_
       if (q < w) woff += warp_tot[q];
       tot += warp_tot[q];
     }
-    if (n < H) {
+    if (n < end) {
       size_t g = (size_t)p * H + n;
       uint8_t c = un ? CODE_UNSTABLE : (lv >= 0.f ? CODE_ACTIVE : CODE_INACTIVE);
       code[g] = c;
@@ -64,7 +103,7 @@ __global__ void __launch_bounds__(1024) k_tables(int H, const float* __restrict_
     if (threadIdx.x == 0) running += tot;
     __syncthreads();
   }
-  if (threadIdx.x == 0) U[p] = running;
+  if (nseg == 1 && threadIdx.x == 0) U[p] = running;
 }
 
 // M^(i)_m: bound on |h^(i)_m| (max(u,0) for hidden layers, max(|x_lo|,|x_hi|) at the input)
@@ -1055,7 +1094,16 @@ __global__ void k_count_unstable(int P, int H, const int32_t* __restrict__ U, in
 // ----------------------------------------------------------------------------------------
 void launch_tables(int P, int H, const float* l, const float* u, Tables& t, uint8_t* code, int32_t* rank,
                    float* slope, float* icpt, int32_t* U, cudaStream_t s) {
-  if (P > 0) { k_tables<<<P, 1024, 0, s>>>(H, l, u, code, rank, slope, icpt, U); ++g_launches; }
+  if (P > 0) {
+    const int nseg = std::max(1, (H + TAB_SEG - 1) / TAB_SEG);
+    if (nseg > 1) {
+      k_tables_count<<<dim3(P, nseg), 1024, 0, s>>>(H, l, u, rank);
+      k_tables_scan<<<P, 32, 0, s>>>(H, nseg, rank, U);
+      g_launches += 2;
+    }
+    k_tables<<<dim3(P, nseg), 1024, 0, s>>>(H, nseg, l, u, code, rank, slope, icpt, U);
+    ++g_launches;
+  }
   t.P = P;
   t.H = H;
   t.code = code;

@@ -220,3 +220,33 @@ def test_bf16_conv_optimize_is_certified():
     assert np.all(lb <= ref + 1e-12 * np.abs(ref))
     init = O.bound(onet, props, batch, a0, b0)
     assert np.mean(lb - init) > 0
+
+
+def test_bf16_wide_mlp_runs_every_contraction_as_a_tensor_core_gemm():
+    """Hidden widths above the fused kernel's 256 (and an odd input width): BF16 takes the
+    layer-by-layer path with each fully connected contraction a tcgen05 GEMM (N split into
+    tiles of 256, unaligned rows written element by element)."""
+    layers = wl.mlp_layers([37, 300, 260, 5], 11)
+    pb = wl.make_problem("wide_mlp", layers, 2, 0.05, 4, 11)
+    onet, props, unst = oracle_setup(pb)
+    batch = wl.random_batch(pb, unst, 40, 0, 5, 2, props=np.arange(40) % 2)
+    a, b = wl.random_alpha_beta(batch, 5, 1.0)
+    net, dom, db = _gpu(pb, props, batch)
+    lb = bc.bound(net, dom, db, _t(a), _t(b), bc.BF16).cpu().numpy()
+    assert bc.status(net) == 0
+    ref = O.bound(onet, props, batch, a, b)
+    err = np.abs(lb - ref) / _scale(ref)
+    print("bf16 wide mlp bound: max err / median|lb| = %.3e" % err.max())
+    assert err.max() <= BF16_TOL
+    _, da, dbeta = bc.bound_grad(net, dom, db, _t(a), _t(b), bc.BF16)
+    assert bc.status(net) == 0
+    _, da_ref, db_ref = O.grad(onet, props, batch, a.astype(np.float64), b.astype(np.float64))
+    for g, gr in ((da.cpu().numpy(), da_ref), (dbeta.cpu().numpy(), db_ref)):
+        rel = np.linalg.norm(g - gr) / max(np.linalg.norm(gr), 1e-12)
+        assert rel <= 5e-2
+    a0, b0 = wl.initial_alpha_beta(batch)
+    at, bt = _t(a0), _t(b0)
+    lbc = bc.optimize(net, dom, db, at, bt, bc.OptCfg(precision=bc.BF16, certify=True)).cpu().numpy()
+    assert bc.status(net) == 0
+    ref_opt = O.bound(onet, props, batch, at.cpu().numpy(), bt.cpu().numpy())
+    assert np.all(lbc <= ref_opt + 1e-12 * np.abs(ref_opt))
