@@ -2,9 +2,13 @@
 
 One step = one call of bcrown_optimize on a batch of subdomains: 20 projected-
 Adam iterations on alpha, beta (each a bound pass plus its adjoint) and the
-final certifying pass.  Workload (default): the ReLU MLP 784-256x6-10 (He
-init, seeded), x0 ~ U[0,1]^784, eps = 0.015, 9 margin specs, 1024 subdomains
-that are the leaves of a random branch-and-bound tree of depth <= 12.
+final certifying pass.  Workload (default, --workload mlp784): the ReLU MLP
+784-256x6-10 (He init, seeded), x0 ~ U[0,1]^784, eps = 0.015, 9 margin specs,
+1024 subdomains that are the leaves of a random branch-and-bound tree of depth
+<= 12.  Other workloads (--workload): batching (the same net, 64 properties
+with log-uniform 16-4096 subdomains each, depth <= 20), conv_small and
+conv_big (the two CIFAR-shaped conv nets, 2048 and 4096 subdomains, depth <= 16
+and 24).
 
 Prints one JSON line (rank 0).  Under torchrun each rank bounds its own batch
 (weak scaling, no collective on the data path); the barrier and the maximum
@@ -37,26 +41,74 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
-    ap.add_argument("--subdomains", type=int, default=1024)
+    ap.add_argument("--workload", default="mlp784", choices=sorted(WORKLOADS))
+    ap.add_argument("--subdomains", type=int, default=None, help="per property (default: the workload's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32-form", action="store_true", help="skip timing the plain FP32 form beside BF16")
-    ap.add_argument("--cpu-sample", type=int, default=640, help="subdomains timed on the oracle (about 10-20 s)")
-    return ap.parse_args()
+    ap.add_argument("--cpu-sample", type=int, default=None,
+                    help="subdomains timed on the oracle (default: the workload's, about 10-25 s)")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    if args.subdomains is None:
+        args.subdomains = w["subdomains"]
+    if args.cpu_sample is None:
+        args.cpu_sample = w["cpu_sample"]
+    return args
 
 
 # ------------------------------------------------------------------------------ workload
 
-def build_workload(seed, n_sub, torch, bc, wl):
-    pb = wl.problem_mlp_784(seed=seed)
+# subdomains: per property (batching: the upper end of the log-uniform range is fixed instead)
+WORKLOADS = {
+    "mlp784": {"subdomains": 1024, "depth": 12, "cpu_sample": 640,
+               "desc": "mlp_784_256x6_10 eps=0.015, {n} BaB-tree subdomains (depth<=12), 9 specs"},
+    "batching": {"subdomains": None, "depth": 20, "cpu_sample": 640,
+                 "desc": "mlp_784_256x6_10 eps=0.015, 64 properties x log-uniform 16-4096 BaB-tree subdomains "
+                         "({n} in all, depth<=20), 9 specs"},
+    "conv_small": {"subdomains": 2048, "depth": 16, "cpu_sample": 16,
+                   "desc": "conv_3x32x32_c32_c64_fc512_512_10 eps=2/255, {n} BaB-tree subdomains (depth<=16), 9 specs"},
+    "conv_big": {"subdomains": 4096, "depth": 24, "cpu_sample": 2,
+                 "desc": "conv_3x32x32_c64_c64_c128_c128_fc512_10 eps=2/255, {n} BaB-tree subdomains (depth<=24), "
+                         "9 specs"},
+}
+
+
+def make_problem(workload, seed, wl):
+    if workload == "batching":
+        return wl.problem_mlp_784(seed=seed, n_props=64)
+    if workload == "conv_small":
+        return wl.problem_conv_small(seed=seed)
+    if workload == "conv_big":
+        return wl.problem_conv_big(seed=seed)
+    return wl.problem_mlp_784(seed=seed)
+
+
+def make_batch(workload, pb, unst, n_sub, seed, wl):
+    w = WORKLOADS[workload]
+    counts = wl.loguniform_counts(pb.P, 16, 4096, seed) if workload == "batching" else [n_sub]
+    return wl.tree_batch(pb, unst, counts, w["depth"], seed + 1)
+
+
+def build_workload(workload, seed, n_sub, torch, bc, wl):
+    pb = make_problem(workload, seed, wl)
     net = bc.load_net(pb.layers, pb.C)
     x_lo = torch.as_tensor(pb.x_lo).cuda()
     x_hi = torch.as_tensor(pb.x_hi).cuda()
     l, u, cnt = bc.root_bounds(net, x_lo, x_hi, bc.ALPHA_ADAPTIVE, 0.5, bc.CERTIFY)
     l_h, u_h = l.cpu().numpy(), u.cpu().numpy()
     unst = [np.nonzero((l_h[p] < 0) & (u_h[p] > 0))[0] for p in range(pb.P)]
-    batch = wl.tree_batch(pb, unst, [n_sub], 12, seed + 1)
+    batch = make_batch(workload, pb, unst, n_sub, seed, wl)
     dom = bc.Domain(x_lo, x_hi, l, u)
     return pb, net, dom, batch, unst, (l_h, u_h)
+
+
+def layer_path_bytes_per_row_iter(pb, U, depth):
+    """Algorithmic bytes of one row and one iteration on the layer-by-layer path: the alpha,
+    Adam m and v state (read + write, FP32), the beta state, the split list, the stash of A at
+    the unstable neurons, lb, and the conv layers' outputs materialised once per direction in
+    BF16 (written and read back)."""
+    conv_out = sum(int(np.prod(ly.out_shape)) for ly in pb.layers[:-1] if ly.kind == "conv")
+    return 24 * U + 24 * depth + 6 * depth + 8 * U + 4 + conv_out * 2 * 2 * 2
 
 
 class Clocks:
@@ -191,7 +243,7 @@ def main():
     from paper_2103_06624_gb300 import workloads as wl
 
     prec = bc.BF16 if args.precision == "bf16" else bc.FP32
-    pb, net, dom, hbatch, unst, lu = build_workload(0, args.subdomains, torch, bc, wl)
+    pb, net, dom, hbatch, unst, lu = build_workload(args.workload, 0, args.subdomains, torch, bc, wl)
     if prec == bc.BF16:
         try:
             _probe = bc.DeviceBatch.from_host(wl.tree_batch(pb, unst, [2], 2, 0))
@@ -315,6 +367,23 @@ def main():
         if tr is not None:
             roof["traffic"] = tr["dram_bytes_per_launch"]
             roof["traffic_note"] = tr
+    elif prec == bc.BF16:
+        # layer-by-layer BF16 path (conv nets): the whole step against the HBM roofline, bytes
+        # from the per-row model (the certifying pass is left out of the algorithmic bytes)
+        U = np.array([len(u) for u in unst])[hbatch.prop_of].astype(np.float64)
+        per_row = layer_path_bytes_per_row_iter(pb, U, hbatch.split_cnt.astype(np.float64))
+        bytes_per_step = float(np.sum(per_row)) * pb.K * cfg.iters
+        achieved = bytes_per_step / (ms_per_step / 1e3) / 1e9
+        peak = peaks.get("hbm_gbs_sustained", peaks.get("hbm_gbs", 6800.0))
+        roof = {"bound": "hbm", "kernel": "whole step (layer path: k_im2col + k_tcg tcgen05 GEMMs, k_relax, "
+                                          "k_fwd_epi, k_adam; FP32 certifying pass)",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": "of measured (MEASURED_PEAKS.json)",
+                "algorithmic_bytes_per_step": bytes_per_step,
+                "bytes_model": "per row and iteration: 24 B x unstable (alpha, m, v) + 30 B x splits + 8 B x unstable "
+                               "(stash) + 4 B + 8 B x conv outputs (BF16 written and read, both directions)",
+                "step_ms_by_class": {n: prof[c][0] / args.steps for c, n in enumerate(
+                    ["contract", "relax", "concretize", "adjoint", "adam", "fused"])}}
     else:
         ms, nl = prof[0]
         flops = rows * f_row * (2 * cfg.iters + 1) * args.steps
@@ -336,14 +405,16 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16" if prec == bc.BF16 else "f32", "data": "synthetic",
-            "config": {"workload": "mlp_784_256x6_10 eps=0.015, 1024 BaB-tree subdomains (depth<=12), 9 specs, "
-                                   "20 Adam iters + certify pass",
+            "config": {"workload": WORKLOADS[args.workload]["desc"].format(n=hbatch.B) +
+                                   ", 20 Adam iters + certify pass",
                        "subdomains_per_gpu": hbatch.B, "specs": pb.K, "rows_per_gpu": rows,
                        "unstable_neurons": U, "iters": cfg.iters, "precision": args.precision if prec == bc.BF16 else "fp32",
                        "l2": "flushed (256 MB write between timed steps)"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk, "forms": forms,
         }
+        if args.workload != "mlp784":
+            line["config"]["name"] = args.workload
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -407,12 +478,13 @@ def run_reference(args, world):
     import torch
     from oracle import bcrown_oracle as O
     from paper_2103_06624_gb300 import workloads as wl
-    pb = wl.problem_mlp_784(seed=0)
+    pb = make_problem(args.workload, 0, wl)
     onet = O.OracleNet(pb.layers, pb.C)
-    l, u = O.root_bounds(onet, pb.x_lo, pb.x_hi)
+    # CROWN root bounds; for the 123k-neuron conv net the oracle's interval bounds (valid, looser)
+    l, u = (O.interval_bounds if args.workload == "conv_big" else O.root_bounds)(onet, pb.x_lo, pb.x_hi)
     l, u = l.astype(np.float32), u.astype(np.float32)
     unst = [np.nonzero((l[p] < 0) & (u[p] > 0))[0] for p in range(pb.P)]
-    batch = wl.tree_batch(pb, unst, [args.subdomains], 12, 1)
+    batch = make_batch(args.workload, pb, unst, args.subdomains, 0, wl)
     times = []
     rate = None
     for i in range(args.warmup + args.steps):
@@ -425,8 +497,8 @@ def run_reference(args, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "mlp_784_256x6_10 eps=0.015, BaB-tree subdomains (depth<=12), 9 specs, "
-                                   "20 Adam iters + final bound", "sample_subdomains": args.cpu_sample},
+            "config": {"workload": WORKLOADS[args.workload]["desc"].format(n=batch.B) +
+                                   ", 20 Adam iters + final bound", "sample_subdomains": args.cpu_sample},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     _ = torch
