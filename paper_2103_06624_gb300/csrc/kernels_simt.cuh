@@ -69,6 +69,18 @@ __device__ __forceinline__ int stage_splits(const RowsCtx& c, int b, int layer, 
   return *n_slots;
 }
 
+// Per-row bitmask of the layer's split neurons (bit j of mask[j / 32]), so that the per-neuron
+// test is one shared-memory load instead of a scan of the split list; the list is scanned only
+// for neurons whose bit is set.  Block-wide: words [0, ceil(d / 32)) are written.
+constexpr int SPLIT_MASK_WORDS = 8192;  // layers of up to 262144 neurons; wider ones scan the list
+__device__ __forceinline__ void split_mask_block(const SplitSlot* slots, int ns, int d, uint32_t* mask) {
+  for (int w = threadIdx.x; w < (d + 31) / 32; w += blockDim.x) mask[w] = 0u;
+  __syncthreads();
+  for (int q = threadIdx.x; q < ns; q += blockDim.x) atomicOr(&mask[slots[q].idx >> 5], 1u << (slots[q].idx & 31));
+  __syncthreads();
+}
+__device__ __forceinline__ bool split_bit(const uint32_t* mask, int j) { return (mask[j >> 5] >> (j & 31)) & 1u; }
+
 // Valid-layer check for splits across all layers (done once per row by the init kernel).
 __device__ __forceinline__ bool row_prop(const RowsCtx& c, int rl, int* b, int* k, int* p) {
   int r = c.r0 + rl;

@@ -106,6 +106,34 @@ __global__ void __launch_bounds__(1024) k_tables(int H, int nseg, const float* _
   if (nseg == 1 && threadIdx.x == 0) U[p] = running;
 }
 
+// Loads issued where they are written (volatile asm keeps a batch of independent loads ahead
+// of the code that uses them instead of letting the compiler sink each to its first use);
+// 0 when pred is false.
+__device__ __forceinline__ float ld_f32(const float* p, bool pred) {
+  float v;
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\tmov.f32 %0, 0f00000000;\n\t@q ld.global.f32 %0, [%1];\n\t}"
+               : "=f"(v)
+               : "l"(p), "r"((uint32_t)pred)
+               : "memory");
+  return v;
+}
+__device__ __forceinline__ int32_t ld_s32(const int32_t* p, bool pred) {
+  int32_t v;
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\tmov.s32 %0, 0;\n\t@q ld.global.s32 %0, [%1];\n\t}"
+               : "=r"(v)
+               : "l"(p), "r"((uint32_t)pred)
+               : "memory");
+  return v;
+}
+__device__ __forceinline__ uint32_t ld_u8(const uint8_t* p, bool pred, uint32_t dflt) {
+  uint32_t v;
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\tmov.u32 %0, %3;\n\t@q ld.global.u8 %0, [%1];\n\t}"
+               : "=r"(v)
+               : "l"(p), "r"((uint32_t)pred), "r"(dflt)
+               : "memory");
+  return v;
+}
+
 // M^(i)_m: bound on |h^(i)_m| (max(u,0) for hidden layers, max(|x_lo|,|x_hi|) at the input)
 __device__ __forceinline__ float hmax_hidden(float uv) { return fmaxf(uv, 0.f); }
 
@@ -203,6 +231,10 @@ __global__ void __launch_bounds__(32 * RELAX_WARPS) k_relax(RowsCtx c, int layer
   constexpr int RPB = RELAX_WARPS / WPR;   // rows per block
   __shared__ SplitSlot slots[RPB][BCROWN_MAX_SPLITS];
   __shared__ int nslots[RPB];
+  // split bitmask per row slot: a whole block's row up to SPLIT_MASK_WORDS * 32 neurons, or
+  // 2048 neurons for each warp's own row
+  constexpr int MW = WPR > 1 ? SPLIT_MASK_WORDS : 64;
+  __shared__ uint32_t smask[RPB][MW];
   __shared__ float red[RELAX_WARPS][3];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rs = w / WPR, sub = w - rs * WPR;   // row slot in the block, warp within the row
@@ -243,10 +275,24 @@ __global__ void __launch_bounds__(32 * RELAX_WARPS) k_relax(RowsCtx c, int layer
   }
   if (WPR > 1) __syncthreads();
   else __syncwarp();
+  const bool use_mask = d <= MW * 32;
+  if (use_mask) {
+    if (live)
+      for (int q = sub * 32 + lane; q < (d + 31) / 32; q += 32 * WPR) smask[rs][q] = 0u;
+    if (WPR > 1) __syncthreads();
+    else __syncwarp();
+    if (live)
+      for (int q = sub * 32 + lane; q < nslots[rs]; q += 32 * WPR) {
+        const int jj = slots[rs][q].idx;
+        atomicOr(&smask[rs][jj >> 5], 1u << (jj & 31));
+      }
+    if (WPR > 1) __syncthreads();
+    else __syncwarp();
+  }
   float acc = 0.f, e1 = 0.f, e2 = 0.f;
   if (live) {
     const int ns = nslots[rs];
-    const SplitSlot* sl = slots[rs];
+    const SplitSlot* sl_ = slots[rs];
     const int Up = c.tb.U[p];
     const long long abase = c.bt.alpha_off[b] + (long long)k * Up;
     const long long bbase = (long long)off * c.K + (long long)k * cnt;
@@ -254,54 +300,84 @@ __global__ void __launch_bounds__(32 * RELAX_WARPS) k_relax(RowsCtx c, int layer
     float* lam_row = Lam + (size_t)rl * d;
     // CERT: acc is a lower bound of sum_j Lambda_j b_j + A_j lambda_j (every operation rounded
     // down); e1, e2 are upper bounds (rounded up) of the error terms below.
-#pragma unroll 4
-    for (int j = sub * 32 + lane; j < d; j += 32 * WPR) {
-      const float a = a_row[j];
-      const size_t n = (size_t)p * c.tb.H + hoff + j;
-      int s = 0;
-      float bet = 0.f;
-      for (int q = 0; q < ns; ++q)
-        if (sl[q].idx == j) {
-          s = sl[q].sign;
-          const long long bi = bbase + sl[q].t;
-          if (bi >= 0 && bi < n_beta) bet = fmaxf(beta[bi], 0.f);
-          else flag(c.status, BCROWN_ERR_ARG);
-        }
-      float D = 0.f, lm = 0.f;
-      const uint8_t code = c.tb.code[n];
-      if (s == -1) D = 1.f;
-      else if (s == 1) D = 0.f;
-      else if (code == CODE_ACTIVE) D = 1.f;
-      else if (code == CODE_INACTIVE) D = 0.f;
-      else if (a >= 0.f) {
-        const long long ai = abase + c.tb.rank[n];
-        if (ai < 0 || ai >= n_alpha) {
-          flag(c.status, BCROWN_ERR_ARG);
-          D = 0.f;
-        } else {
-          D = fminf(fmaxf(alpha[ai], 0.f), 1.f);
-        }
-      } else {
-        // upper chord, slope and intercept rounded up (outward) in the tables
-        D = c.tb.slope[n];
-        lm = c.tb.icpt[n];
+    const size_t n0 = (size_t)p * c.tb.H + hoff;
+    // RELAX_V neurons per lane per step, their loads issued in three rounds (A, code, bias; then
+    // the unstable neurons' rank and chord; then alpha) instead of one dependent chain each
+    constexpr int RELAX_V = 4;
+    for (int j0 = sub * 32 + lane; j0 < d; j0 += RELAX_V * 32 * WPR) {
+      float av[RELAX_V], bv[RELAX_V], sl[RELAX_V], ic[RELAX_V], al[RELAX_V];
+      uint8_t cv[RELAX_V];
+      int32_t rk[RELAX_V];
+#pragma unroll
+      for (int v = 0; v < RELAX_V; ++v) {
+        const int j = j0 + v * 32 * WPR;
+        const bool in = j < d;
+        av[v] = ld_f32(a_row + j, in);
+        bv[v] = ld_f32(bias + j, in);
+        cv[v] = (uint8_t)ld_u8(c.tb.code + n0 + j, in, CODE_INACTIVE);
       }
-      const float L = fmaf(a, D, bet * (float)s);
-      lam_row[j] = L;
-      const float bj = bias[j];
-      if (CERT) {
-        acc = __fadd_rd(acc, __fadd_rd(__fmul_rd(L, bj), __fmul_rd(a, lm)));
-        const bool exact = (s == 0) && (D == 0.f || D == 1.f);
-        if (!exact) {
-          // Lambda_j was rounded once: |error| <= 2^-23 |Lambda_j| (+ an underflow margin),
-          // acting on |z_j| <= max(|l_j|, |u_j|)
-          const float zmax = fmaxf(fabsf(c.l[n]), fabsf(c.u[n]));
-          const float er = __fmaf_ru(fabsf(L), 0x1p-23f, 0x1p-140f);
-          e1 = __fadd_ru(e1, __fmul_ru(er, zmax));
+#pragma unroll
+      for (int v = 0; v < RELAX_V; ++v) {
+        const int j = j0 + v * 32 * WPR;
+        const bool un = cv[v] == CODE_UNSTABLE;
+        rk[v] = ld_s32(c.tb.rank + n0 + j, un && av[v] >= 0.f);
+        sl[v] = ld_f32(c.tb.slope + n0 + j, un && av[v] < 0.f);
+        ic[v] = ld_f32(c.tb.icpt + n0 + j, un && av[v] < 0.f);
+      }
+#pragma unroll
+      for (int v = 0; v < RELAX_V; ++v) {
+        al[v] = 0.f;
+        if (cv[v] == CODE_UNSTABLE && av[v] >= 0.f) {
+          const long long ai = abase + rk[v];
+          if (ai < 0 || ai >= n_alpha) flag(c.status, BCROWN_ERR_ARG);
+          else al[v] = fminf(fmaxf(alpha[ai], 0.f), 1.f);
         }
-        e2 = __fadd_ru(e2, __fmul_ru(fabsf(L), wm[n]));
-      } else {
-        acc = fmaf(L, bj, fmaf(a, lm, acc));
+      }
+#pragma unroll
+      for (int v = 0; v < RELAX_V; ++v) {
+        const int j = j0 + v * 32 * WPR;
+        if (j >= d) break;
+        const float a = av[v];
+        const size_t n = n0 + j;
+        int s = 0;
+        float bet = 0.f;
+        if (ns > 0 && (!use_mask || split_bit(smask[rs], j)))
+          for (int q = 0; q < ns; ++q)
+            if (sl_[q].idx == j) {
+              s = sl_[q].sign;
+              const long long bi = bbase + sl_[q].t;
+              if (bi >= 0 && bi < n_beta) bet = fmaxf(beta[bi], 0.f);
+              else flag(c.status, BCROWN_ERR_ARG);
+            }
+        float D = 0.f, lm = 0.f;
+        const uint8_t code = cv[v];
+        if (s == -1) D = 1.f;
+        else if (s == 1) D = 0.f;
+        else if (code == CODE_ACTIVE) D = 1.f;
+        else if (code == CODE_INACTIVE) D = 0.f;
+        else if (a >= 0.f) D = al[v];
+        else {
+          // upper chord, slope and intercept rounded up (outward) in the tables
+          D = sl[v];
+          lm = ic[v];
+        }
+        const float L = fmaf(a, D, bet * (float)s);
+        lam_row[j] = L;
+        const float bj = bv[v];
+        if (CERT) {
+          acc = __fadd_rd(acc, __fadd_rd(__fmul_rd(L, bj), __fmul_rd(a, lm)));
+          const bool exact = (s == 0) && (D == 0.f || D == 1.f);
+          if (!exact) {
+            // Lambda_j was rounded once: |error| <= 2^-23 |Lambda_j| (+ an underflow margin),
+            // acting on |z_j| <= max(|l_j|, |u_j|)
+            const float zmax = fmaxf(fabsf(c.l[n]), fabsf(c.u[n]));
+            const float er = __fmaf_ru(fabsf(L), 0x1p-23f, 0x1p-140f);
+            e1 = __fadd_ru(e1, __fmul_ru(er, zmax));
+          }
+          e2 = __fadd_ru(e2, __fmul_ru(fabsf(L), wm[n]));
+        } else {
+          acc = fmaf(L, bj, fmaf(a, lm, acc));
+        }
       }
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -622,48 +698,83 @@ __global__ void __launch_bounds__(256) k_fwd_epi(RowsCtx c, int layer, int d, lo
   int b, k, p;
   if (!row_prop(c, rl, &b, &k, &p)) p = 0;
   int ns = stage_splits(c, b, layer, d, slots, &n_slots);
+  __shared__ uint32_t smask[SPLIT_MASK_WORDS];
+  const bool use_mask = ns > 0 && d <= SPLIT_MASK_WORDS * 32;
+  if (use_mask) split_mask_block(slots, ns, d, smask);   // ns is uniform over the block
   int cnt = c.bt.split_cnt[b];
   int Up = c.tb.U[p];
   long long abase = c.bt.alpha_off[b] + (long long)k * Up;
   long long bbase = (long long)c.bt.split_off[b] * c.K + (long long)k * cnt;
   float* z_row = Z + (size_t)rl * d;
   const float* a_row = Ai + (size_t)rl * d;
-  for (int j = threadIdx.x; j < d; j += blockDim.x) {
-    float z = z_row[j];
-    float a = a_row[j];
-    size_t n = (size_t)p * c.tb.H + hoff + j;
-    int s = 0, t = -1;
-    for (int q = 0; q < ns; ++q)
-      if (slots[q].idx == j) {
-        s = slots[q].sign;
-        t = slots[q].t;
+  const size_t n0 = (size_t)p * c.tb.H + hoff;
+  // EPI_V neurons per thread per step, their loads issued in three rounds (z, A, code; then the
+  // unstable neurons' rank and chord; then alpha) instead of one dependent chain per neuron
+  constexpr int EPI_V = 4;
+  for (int j0 = threadIdx.x; j0 < d; j0 += EPI_V * blockDim.x) {
+    float z[EPI_V], a[EPI_V], sl[EPI_V], ic[EPI_V], al[EPI_V];
+    uint8_t code[EPI_V];
+    int32_t rk[EPI_V];
+#pragma unroll
+    for (int v = 0; v < EPI_V; ++v) {
+      const int j = j0 + v * blockDim.x;
+      const bool in = j < d;
+      z[v] = ld_f32(z_row + j, in);
+      a[v] = ld_f32(a_row + j, in);
+      code[v] = (uint8_t)ld_u8(c.tb.code + n0 + j, in, CODE_INACTIVE);
+    }
+#pragma unroll
+    for (int v = 0; v < EPI_V; ++v) {
+      const int j = j0 + v * blockDim.x;
+      const bool un = code[v] == CODE_UNSTABLE;
+      rk[v] = un ? ld_s32(c.tb.rank + n0 + j, true) : -1;
+      sl[v] = ld_f32(c.tb.slope + n0 + j, un && a[v] < 0.f);
+      ic[v] = ld_f32(c.tb.icpt + n0 + j, un && a[v] < 0.f);
+    }
+    long long ai[EPI_V];
+#pragma unroll
+    for (int v = 0; v < EPI_V; ++v) {
+      ai[v] = -1;
+      al[v] = 0.f;
+      if (code[v] == CODE_UNSTABLE) {
+        ai[v] = abase + rk[v];
+        if (ai[v] < 0 || ai[v] >= n_alpha) {
+          flag(c.status, BCROWN_ERR_ARG);
+          ai[v] = -1;
+        } else if (a[v] >= 0.f) {
+          al[v] = alpha[ai[v]];
+        }
       }
-    uint8_t code = c.tb.code[n];
-    float D = 0.f, lm = 0.f;
-    long long ai = -1;
-    if (code == CODE_UNSTABLE) {
-      ai = abase + c.tb.rank[n];
-      if (ai < 0 || ai >= n_alpha) {
-        flag(c.status, BCROWN_ERR_ARG);
-        ai = -1;
+    }
+#pragma unroll
+    for (int v = 0; v < EPI_V; ++v) {
+      const int j = j0 + v * blockDim.x;
+      if (j >= d) break;
+      int s = 0, t = -1;
+      if (ns > 0 && (!use_mask || split_bit(smask, j)))
+        for (int q = 0; q < ns; ++q)
+          if (slots[q].idx == j) {
+            s = slots[q].sign;
+            t = slots[q].t;
+          }
+      float D = 0.f, lm = 0.f;
+      if (s == -1) D = 1.f;
+      else if (s == 1) D = 0.f;
+      else if (code[v] == CODE_ACTIVE) D = 1.f;
+      else if (code[v] == CODE_INACTIVE) D = 0.f;
+      else if (a[v] >= 0.f) D = ai[v] >= 0 ? fminf(fmaxf(al[v], 0.f), 1.f) : 0.f;
+      else {
+        D = sl[v];
+        lm = ic[v];
       }
+      if (ai[v] >= 0) dalpha[ai[v]] = (s == 0 && a[v] >= 0.f) ? a[v] * z[v] : 0.f;
+      if (s != 0) {
+        long long bi = bbase + t;
+        if (bi >= 0 && bi < n_beta) dbeta[bi] = (float)s * z[v];
+        else flag(c.status, BCROWN_ERR_ARG);
+      }
+      z_row[j] = fmaf(D, z[v], lm);
     }
-    if (s == -1) D = 1.f;
-    else if (s == 1) D = 0.f;
-    else if (code == CODE_ACTIVE) D = 1.f;
-    else if (code == CODE_INACTIVE) D = 0.f;
-    else if (a >= 0.f) D = ai >= 0 ? fminf(fmaxf(alpha[ai], 0.f), 1.f) : 0.f;
-    else {
-      D = c.tb.slope[n];
-      lm = c.tb.icpt[n];
-    }
-    if (ai >= 0) dalpha[ai] = (s == 0 && a >= 0.f) ? a * z : 0.f;
-    if (s != 0) {
-      long long bi = bbase + t;
-      if (bi >= 0 && bi < n_beta) dbeta[bi] = (float)s * z;
-      else flag(c.status, BCROWN_ERR_ARG);
-    }
-    z_row[j] = fmaf(D, z, lm);
   }
 }
 
