@@ -244,7 +244,10 @@ static int run_bound(bcrown_net* net, const bcrown_domain* dom, const bcrown_bat
 
 // im2col bytes per row for the BF16 layer-by-layer path (0: not taken; the fused kernel or FP32).
 static size_t layer_tc_col(bcrown_net* net, int precision) {
-  return precision == BCROWN_BF16 && !tc_supported(net) && tcg_supported(net) ? tcg_col_bytes_per_row(net) : 0;
+  // at least 16 bytes, so that the plan's col pointer also marks the path taken
+  return precision == BCROWN_BF16 && !tc_supported(net) && tcg_supported(net)
+             ? std::max<size_t>(tcg_col_bytes_per_row(net), 16)
+             : 0;
 }
 
 static int check_precision(bcrown_net* net, int precision, bool grad) {

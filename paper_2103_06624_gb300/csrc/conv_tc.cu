@@ -36,13 +36,24 @@ namespace tc {
 // blocks of 64 streamed by TMA.
 // ------------------------------------------------------------------------------------------
 constexpr int TCG_NS = 4;         // pipeline stages (A: 128 x 64, B: Np x 64)
-constexpr int TCG_EPI = 8;        // epilogue warps: TMEM lane quadrant warp % 4, column chunks of parity warp / 4
-constexpr int TCG_TMA_WARP = TCG_EPI, TCG_MMA_WARP = TCG_EPI + 1;
-constexpr int TCG_THREADS = (TCG_EPI + 2) * 32;
+// Warp roles of k_tcg: epilogue warps 0 .. EPI-1 (TMEM lane quadrant warp % 4, column chunks
+// warp / 4 + EPI / 4 * i), the TMA warp EPI, the MMA warp EPI + 1, and in gather mode the warps
+// from EPI + 2 on, which build the A operand in shared memory (gather warp w fills the chunks
+// 8 / GPS * (w / NS) .. of ring slot w % NS), so the im2col operand never goes through HBM.
+template <bool GATHER>
+struct TcgRoles {
+  static constexpr int EPI = GATHER ? 4 : 8;
+  static constexpr int TMA = EPI, MMA = EPI + 1, GATHER0 = EPI + 2;
+  static constexpr int GPS = 4;                          // gather warps per ring slot
+  static constexpr int GW = GATHER ? GPS * TCG_NS : 0;
+  static constexpr int THREADS = (EPI + 2 + GW) * 32;
+};
 constexpr int TCG_BIAS_MAX = 4096;  // channel biases staged in shared memory up to this many
-// Dynamic shared memory of k_tcg: 1 KB alignment slack, the stages, barriers, staged biases.
-inline int tcg_smem(int Np, int N, bool bias) {
-  return 1024 + TCG_NS * (16384 + Np * 128) + 256 + (bias && N <= TCG_BIAS_MAX ? (N + 3) / 4 * 16 : 0);
+// Dynamic shared memory of k_tcg: 1 KB alignment slack, the stages, barriers, staged biases,
+// and in gather mode the K table (kp_gather entries).
+__host__ __device__ inline int tcg_bias_bytes(int N, bool bias) { return bias && N <= TCG_BIAS_MAX ? (N + 3) / 4 * 16 : 0; }
+inline int tcg_smem(int Np, int N, bool bias, int kp_gather = 0) {
+  return 1024 + TCG_NS * (16384 + Np * 128) + 256 + tcg_bias_bytes(N, bias) + kp_gather * (int)sizeof(int2);
 }
 
 // One gather: row m = (r, pp), pp = i * nJ + j; source position (y0 + dy_K, x0 + dx_K) with
@@ -158,15 +169,61 @@ __device__ __forceinline__ bool tcg_wait(uint64_t* b, uint32_t parity, volatile 
   }
 }
 
+// Predicated FP32 load issued where it is written (0 when pred is false).
+__device__ __forceinline__ float ld_f32_pred(const float* p, bool pred) {
+  float v;
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\tmov.f32 %0, 0f00000000;\n\t@q ld.global.f32 %0, [%1];\n\t}"
+               : "=f"(v)
+               : "l"(p), "r"((uint32_t)pred)
+               : "memory");
+  return v;
+}
+
+// One 8-K chunk of gather mode: rows ln + 32 q (q < 4) of the A stage, K = K0 .. K0 + 7, from
+// the table entries t[0..7]; written in the 128-byte-swizzled K-major layout (16-byte chunk c
+// of row m at chunk position c ^ (m & 7)).
+__device__ __forceinline__ void gather_chunk(uint8_t* stage, int c, int ln, const int4 (&t4)[4],
+                                             const float* const (&sr)[4], const int (&y0)[4], const int (&x0)[4],
+                                             const bool (&mv)[4], int Hs, int Ws) {
+  float v[4][8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const int4 tt = t4[e >> 1];
+    const int ch = (e & 1) ? tt.z : tt.x;
+    const int pk = (e & 1) ? tt.w : tt.y;
+    const int dy = (int)(short)(pk & 0xffff), dx = pk >> 16;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int y = y0[q] + dy, x = x0[q] + dx;
+      const bool ok = mv[q] && ch >= 0 && (unsigned)y < (unsigned)Hs && (unsigned)x < (unsigned)Ws;
+      v[q][e] = ld_f32_pred(sr[q] + (ok ? ch + y * Ws + x : 0), ok);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    uint32_t pk[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      __nv_bfloat162 b2 = __floats2bfloat162_rn(v[q][2 * e], v[q][2 * e + 1]);
+      pk[e] = *reinterpret_cast<uint32_t*>(&b2);
+    }
+    const int m = ln + 32 * q;
+    *reinterpret_cast<uint4*>(stage + m * 128 + ((c ^ (m & 7)) << 4)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+  }
+}
+
 // out[r * stride + n * P + p] = (Col x W^T)[m = r * P + p][n] (+ bias[n * P + p]) for n < N.
 // The bias is per channel (constant over the positions p, as conv biases are stored): it is
 // read at p = 0, into shared memory when N <= TCG_BIAS_MAX.
-__global__ void __launch_bounds__(TCG_THREADS, 1) k_tcg(const __grid_constant__ CUtensorMap mapA,
-                                                        const __grid_constant__ CUtensorMap mapB, TcgOut o,
-                                                        float* __restrict__ out, const float* __restrict__ bias,
-                                                        int* status) {
+// GATHER = false: Col is read by TMA through mapA.  GATHER = true: Col is never stored; gather
+// warps build each A stage from src with the im2col pass q (mapA unused).
+template <bool GATHER>
+__global__ void __launch_bounds__(TcgRoles<GATHER>::THREADS, 1)
+    k_tcg(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcgOut o, Im2colPass gq,
+          const float* __restrict__ src, float* __restrict__ out, const float* __restrict__ bias, int* status) {
   const long long M = o.M;
   const int N = o.N, Np = o.Np, nkb = o.nkb;
+  using R = TcgRoles<GATHER>;
   extern __shared__ __align__(1024) uint8_t tsm_raw[];
   const uint32_t pad = (1024u - (su32(tsm_raw) & 1023u)) & 1023u;
   uint8_t* base = tsm_raw + pad;
@@ -182,23 +239,24 @@ __global__ void __launch_bounds__(TCG_THREADS, 1) k_tcg(const __grid_constant__ 
   volatile int* abort = reinterpret_cast<volatile int*>(tbase_sm + 1);
   float* sbias = reinterpret_cast<float*>(bars + 32);  // 256 bytes past the barriers
   const bool stage_bias = bias != nullptr && N <= TCG_BIAS_MAX;
+  int2* stab = reinterpret_cast<int2*>(reinterpret_cast<uint8_t*>(sbias) + tcg_bias_bytes(N, bias != nullptr));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long ntiles = (M + 127) / 128 * o.ntn;   // tile = m tile * ntn + n tile
   // two accumulators of Np columns, allocated as a power of two >= 32
   const uint32_t tcols = Np <= 16 ? 32u : (Np <= 32 ? 64u : (Np <= 64 ? 128u : (Np <= 128 ? 256u : 512u)));
   if (threadIdx.x == 0) {
     for (int i = 0; i < TCG_NS; ++i) {
-      mbar_init(&full[i], 1);
+      mbar_init(&full[i], 1 + R::GPS * GATHER);   // the TMA transaction (+ the gather warps' arrivals)
       mbar_init(&empty[i], 1);
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&acc_full[i], 1);
-      mbar_init(&acc_empty[i], TCG_EPI);
+      mbar_init(&acc_empty[i], R::EPI);
     }
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == TCG_MMA_WARP) {
+  if (warp == R::MMA) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tbase_sm)), "r"(tcols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -207,7 +265,7 @@ __global__ void __launch_bounds__(TCG_THREADS, 1) k_tcg(const __grid_constant__ 
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tbase_sm;
-  if (warp == TCG_TMA_WARP) {
+  if (warp == R::TMA) {
     if (lane == 0) {
       uint32_t seq = 0;
       bool ok = true;
@@ -218,8 +276,8 @@ __global__ void __launch_bounds__(TCG_THREADS, 1) k_tcg(const __grid_constant__ 
             ok = false;
             break;
           }
-          mbar_expect_tx(&full[st], 16384u + (uint32_t)bbytes);
-          tma_load_2d(sA + st * 16384, &mapA, kb * 64, (int)(tile / o.ntn * 128), &full[st]);
+          mbar_expect_tx(&full[st], (GATHER ? 0u : 16384u) + (uint32_t)bbytes);
+          if (!GATHER) tma_load_2d(sA + st * 16384, &mapA, kb * 64, (int)(tile / o.ntn * 128), &full[st]);
           tma_load_2d(sB + st * bbytes, &mapB, kb * 64, o.brow + (int)(tile % o.ntn) * Np, &full[st]);
         }
       if (!ok) {
@@ -230,7 +288,7 @@ __global__ void __launch_bounds__(TCG_THREADS, 1) k_tcg(const __grid_constant__ 
         }
       }
     }
-  } else if (warp == TCG_MMA_WARP) {
+  } else if (warp == R::MMA) {
     if (lane == 0) {
       uint32_t seq = 0, accseq = 0;
       bool ok = true;
@@ -254,12 +312,60 @@ __global__ void __launch_bounds__(TCG_THREADS, 1) k_tcg(const __grid_constant__ 
         umma_commit(&acc_full[buf]);
       }
     }
+  } else if (GATHER && warp >= R::GATHER0) {
+    // ring slot g takes sequence numbers g, g + TCG_NS, ... of the (tile, K block) order the
+    // MMA warp consumes; this warp fills its share of the slot's 8 chunks
+    const int g = (warp - R::GATHER0) % TCG_NS, part = (warp - R::GATHER0) / TCG_NS;
+    constexpr int CPW = 8 / R::GPS;   // chunks per gather warp
+    for (int k = threadIdx.x - R::GATHER0 * 32; k < gq.Kp; k += R::GW * 32) stab[k] = gq.tab[k];
+    asm volatile("bar.sync 2, %0;" ::"n"(R::GW * 32) : "memory");
+    uint32_t seq = 0;
+    bool ok = true;
+    for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+      // this lane's rows ln + 32 q of the tile
+      const float* sr[4];
+      int y0[4], x0[4];
+      bool mv[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const long long m = tile / o.ntn * 128 + lane + 32 * q;
+        mv[q] = m < M;
+        const long long r = mv[q] ? m / gq.Pm : 0;
+        const int pp = mv[q] ? (int)(m - r * gq.Pm) : 0;
+        const int i = pp / gq.nJ, j = pp - (pp / gq.nJ) * gq.nJ;
+        y0[q] = i * gq.ms + gq.cy;
+        x0[q] = j * gq.ms + gq.cx;
+        sr[q] = src + r * gq.d_src;
+      }
+      for (int kb = 0; kb < nkb; ++kb, ++seq) {
+        if ((int)(seq % TCG_NS) != g) continue;
+        int okw = 1;
+        if (lane == 0) okw = tcg_wait(&empty[g], ((seq / TCG_NS) & 1) ^ 1, abort, status) ? 1 : 0;
+        okw = __shfl_sync(0xffffffffu, okw, 0);
+        if (!okw) {
+          ok = false;
+          break;
+        }
+        uint8_t* stage = sA + g * 16384;
+#pragma unroll 1
+        for (int c = CPW * part; c < CPW * part + CPW; ++c) {
+          int4 t4[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) t4[e] = reinterpret_cast<const int4*>(stab + kb * 64 + c * 8)[e];
+          gather_chunk(stage, c, lane, t4, sr, y0, x0, mv, gq.Hs, gq.Ws);
+        }
+        fence_proxy_async();   // the stage's generic-proxy stores, before the MMA reads it
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&full[g]);
+      }
+    }
   } else {
-    // epilogue: warp w reads TMEM lanes (tile rows) 32 (w % 4) .. + 31, column chunks of parity w / 4
+    // epilogue: warp w reads TMEM lanes (tile rows) 32 (w % 4) .. + 31, column chunks w / 4,
+    // w / 4 + EPI / 4, ...
     const int q4 = warp & 3, half = warp >> 2;
     if (stage_bias) {
-      for (int n = threadIdx.x; n < N; n += TCG_EPI * 32) sbias[n] = bias[(size_t)n * o.P];
-      asm volatile("bar.sync 1, %0;" ::"n"(TCG_EPI * 32) : "memory");
+      for (int n = threadIdx.x; n < N; n += R::EPI * 32) sbias[n] = bias[(size_t)n * o.P];
+      asm volatile("bar.sync 1, %0;" ::"n"(R::EPI * 32) : "memory");
     }
     const bool vec = o.P == 1 && (o.stride & 3) == 0 &&
                      ((reinterpret_cast<uintptr_t>(out) | (stage_bias ? 0 : reinterpret_cast<uintptr_t>(bias))) &
@@ -280,7 +386,7 @@ __global__ void __launch_bounds__(TCG_THREADS, 1) k_tcg(const __grid_constant__ 
       const int i = pp / o.nJ, j = pp - (pp / o.nJ) * o.nJ;
       const int p = (o.a + o.so * i) * o.Wo + o.b + o.so * j;
       float* orow = out + r * o.stride + p;
-      for (int n0 = 16 * half; n0 < Np; n0 += 32) {
+      for (int n0 = 16 * half; n0 < Np; n0 += 16 * (R::EPI / 4)) {
         float v[16];
         tmem_ld16(tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(buf * Np + n0), v);
         if (min_) {
@@ -315,7 +421,7 @@ __global__ void __launch_bounds__(TCG_THREADS, 1) k_tcg(const __grid_constant__ 
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == TCG_MMA_WARP) {
+  if (warp == R::MMA) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols) : "memory");
   }
@@ -324,6 +430,13 @@ __global__ void __launch_bounds__(TCG_THREADS, 1) k_tcg(const __grid_constant__ 
 }  // namespace tc
 
 using namespace tc;
+
+// Conv passes gather their operand inside the GEMM kernel (true) or through an im2col buffer
+// in HBM (false; BCROWN_CONV_IM2COL=1 in the environment selects it, for comparison).
+static const bool g_tcg_gather = [] {
+  const char* e = getenv("BCROWN_CONV_IM2COL");
+  return !(e && e[0] == '1');
+}();
 
 namespace {
 
@@ -409,6 +522,7 @@ size_t tcg_col_bytes_per_row(const bcrown_net* net) {
       b = std::max(b, (size_t)std::max(pad_to(l.d_in, 64), pad_to(l.d_out, 64)) * sizeof(__nv_bfloat16));
       continue;
     }
+    if (g_tcg_gather) continue;   // conv operands are gathered in shared memory
     const size_t ph = (size_t)((l.in_h + l.stride - 1) / l.stride) * ((l.in_w + l.stride - 1) / l.stride);
     const size_t bwd = ph * kp_bwd(l);
     const size_t fwd = (size_t)l.out_h * l.out_w * kp_fwd(l);
@@ -513,7 +627,10 @@ static int tcg_prepare(bcrown_net* net, ConvTc* t) {
     BC_CHECK(encode_map(&c.mb, db, s * s * c.Np_b, c.Kp_b, c.Np_b));
     BC_CHECK(encode_map(&c.mf, df, c.Np_f, c.Kp_f, c.Np_f));
   }
-  BC_CUDA(cudaFuncSetAttribute(k_tcg, cudaFuncAttributeMaxDynamicSharedMemorySize, tcg_smem(256, TCG_BIAS_MAX, true)));
+  BC_CUDA(cudaFuncSetAttribute(k_tcg<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               tcg_smem(256, TCG_BIAS_MAX, true)));
+  BC_CUDA(cudaFuncSetAttribute(k_tcg<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               tcg_smem(256, 256, true, IM2COL_MAX_KP)));
   BC_CUDA(cudaFuncSetAttribute(k_im2col, cudaFuncAttributeMaxDynamicSharedMemorySize, im2col_smem(IM2COL_MAX_KP)));
   t->ready = true;
   return BCROWN_OK;
@@ -524,6 +641,19 @@ static int tcg_prepare(bcrown_net* net, ConvTc* t) {
 static int tcg_pass(bcrown_net* net, const Im2colPass& q, const CUtensorMap& mB, const TcgOut& o, const float* src,
                     float* dst, const float* bias, char* col, size_t col_bytes, cudaStream_t s) {
   if (q.M <= 0) return BCROWN_OK;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long ntiles = (q.M + 127) / 128 * o.ntn;
+  const int grid = (int)std::min<long long>(ntiles, 2LL * sms);
+  if (q.tab && g_tcg_gather) {
+    // conv layers: the gather warps build the operand in shared memory (mapA unused)
+    const int smem = tcg_smem(o.Np, o.N, bias != nullptr, q.Kp);
+    k_tcg<true><<<grid, TcgRoles<true>::THREADS, smem, s>>>(mB, mB, o, q, src, dst, bias, net->status);
+    ++g_launches;
+    BC_CUDA(cudaGetLastError());
+    return BCROWN_OK;
+  }
   if ((size_t)q.M * q.Kp * sizeof(__nv_bfloat16) > col_bytes) return fail(BCROWN_ERR_OOM, "im2col workspace too small");
   __nv_bfloat16* cb = reinterpret_cast<__nv_bfloat16*>(col);
   if (q.tab)
@@ -533,13 +663,8 @@ static int tcg_pass(bcrown_net* net, const Im2colPass& q, const CUtensorMap& mB,
   ++g_launches;
   CUtensorMap mA;
   BC_CHECK(encode_map(&mA, cb, (int)q.M, q.Kp, 128));
-  int dev = 0, sms = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const long long ntiles = (q.M + 127) / 128 * o.ntn;
-  const int grid = (int)std::min<long long>(ntiles, 2LL * sms);
   const int smem = tcg_smem(o.Np, o.N, bias != nullptr);
-  k_tcg<<<grid, TCG_THREADS, smem, s>>>(mA, mB, o, dst, bias, net->status);
+  k_tcg<false><<<grid, TcgRoles<false>::THREADS, smem, s>>>(mA, mB, o, q, src, dst, bias, net->status);
   ++g_launches;
   BC_CUDA(cudaGetLastError());
   return BCROWN_OK;

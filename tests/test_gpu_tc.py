@@ -250,3 +250,34 @@ def test_bf16_wide_mlp_runs_every_contraction_as_a_tensor_core_gemm():
     assert bc.status(net) == 0
     ref_opt = O.bound(onet, props, batch, at.cpu().numpy(), bt.cpu().numpy())
     assert np.all(lbc <= ref_opt + 1e-12 * np.abs(ref_opt))
+
+
+def test_bf16_conv_im2col_buffer_path_matches_oracle():
+    """The comparison path for conv layers (BCROWN_CONV_IM2COL=1: the im2col operand written to
+    HBM by one kernel and read by TMA in the GEMM, instead of gathered inside the GEMM) on the
+    tiny conv nets, in a child process since the switch is read when the library loads."""
+    import os
+    import subprocess
+    import sys
+    script = (
+        "import numpy as np, torch\n"
+        "from tests.test_gpu_tc import _tiny_conv, _gpu, _t, _scale, BF16_TOL\n"
+        "from tests.helpers import oracle_setup\n"
+        "from oracle import bcrown_oracle as O\n"
+        "from paper_2103_06624_gb300 import bcrown as bc, workloads as wl\n"
+        "for which in ['tiny', 'tiny_odd', 'tiny_s3']:\n"
+        "    pb = _tiny_conv(which)\n"
+        "    onet, props, unst = oracle_setup(pb)\n"
+        "    batch = wl.random_batch(pb, unst, 24, 0, 4, 1, props=np.arange(24) % 2)\n"
+        "    a, b = wl.random_alpha_beta(batch, 3, 1.0)\n"
+        "    net, dom, db = _gpu(pb, props, batch)\n"
+        "    lb = bc.bound(net, dom, db, _t(a), _t(b), bc.BF16).cpu().numpy()\n"
+        "    assert bc.status(net) == 0\n"
+        "    ref = O.bound(onet, props, batch, a, b)\n"
+        "    assert (np.abs(lb - ref) / _scale(ref)).max() <= BF16_TOL, which\n"
+        "print('ok')\n")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, BCROWN_CONV_IM2COL="1")
+    r = subprocess.run([sys.executable, "-c", script], cwd=root, env=env, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
