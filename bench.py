@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--subdomains", type=int, default=None, help="per property (default: the workload's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32-form", action="store_true", help="skip timing the plain FP32 form beside BF16")
+    ap.add_argument("--profile-timed", action="store_true",
+                    help="open a CUDA profiler range around the timed steps only (ncu --profile-from-start off)")
     ap.add_argument("--cpu-sample", type=int, default=None,
                     help="subdomains timed on the oracle (default: the workload's, about 10-25 s)")
     args = ap.parse_args()
@@ -278,12 +280,16 @@ def main():
     launches0 = bc.kernel_launches()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     torch.cuda.synchronize()
+    if args.profile_timed:
+        torch.cuda.profiler.start()
     for i in range(args.steps):
         flush.fill_(float(i))                      # write 256 MB > L2 between timed steps
         ev[i][0].record(stream)
         step()
         ev[i][1].record(stream)
     torch.cuda.synchronize()
+    if args.profile_timed:
+        torch.cuda.profiler.stop()
     launches = bc.kernel_launches() - launches0
     clk = clocks.stop()
     prof = {c: bc.profile_read(net, c) for c in range(6)}

@@ -61,7 +61,9 @@ inline int tcg_smem(int Np, int N, bool bias, int kp_gather = 0) {
 struct Im2colPass {
   long long M;
   int Pm, nJ, ms, cy, cx, Hs, Ws, d_src, Kp;
-  const int2* tab;  // [Kp]: {channel offset C * Hs * Ws, or -1 for a zero column; (dy & 0xffff) | dx << 16}
+  // [Kp]: {source offset c * Hs * Ws + dy * Ws + dx; (dy & 0xffff) | dx << 16}, a zero column
+  // (K padding, a tap off the stride grid) with dy = -32768, which no bounds test passes
+  const int2* tab;
 };
 
 // 32 consecutive rows m per block.  Lanes walk the 32 rows for 16 K at a time (K uniform per
@@ -84,8 +86,9 @@ __global__ void __launch_bounds__(256) k_im2col(Im2colPass q, const float* __res
   const int r = mv ? (int)(m / q.Pm) : 0;
   const int pp = mv ? (int)(m - (long long)r * q.Pm) : 0;
   const int i = pp / q.nJ, j = pp - (pp / q.nJ) * q.nJ;
-  const int y0 = i * q.ms + q.cy, x0 = j * q.ms + q.cx;
-  const float* sr = src + (size_t)r * q.d_src;
+  // a row past M gets y0 = -32768: no bounds test passes
+  const int y0 = mv ? i * q.ms + q.cy : -32768, x0 = j * q.ms + q.cx;
+  const float* sr = src + (size_t)r * q.d_src + (mv ? y0 * q.Ws + x0 : 0);
   __syncthreads();
   // 16 K per lane per step: 16 independent loads in flight before the first use
   for (int K0 = 16 * w; K0 < Kp; K0 += 128) {
@@ -93,14 +96,10 @@ __global__ void __launch_bounds__(256) k_im2col(Im2colPass q, const float* __res
 #pragma unroll
     for (int e = 0; e < 16; e += 2) {
       const int4 t2 = *reinterpret_cast<const int4*>(tab + K0 + e);
-      const int y0a = y0 + (int)(short)(t2.y & 0xffff), x0a = x0 + (t2.y >> 16);
-      const int y0b = y0 + (int)(short)(t2.w & 0xffff), x0b = x0 + (t2.w >> 16);
-      v[e] = (mv && t2.x >= 0 && (unsigned)y0a < (unsigned)q.Hs && (unsigned)x0a < (unsigned)q.Ws)
-                 ? sr[t2.x + y0a * q.Ws + x0a]
-                 : 0.f;
-      v[e + 1] = (mv && t2.z >= 0 && (unsigned)y0b < (unsigned)q.Hs && (unsigned)x0b < (unsigned)q.Ws)
-                     ? sr[t2.z + y0b * q.Ws + x0b]
-                     : 0.f;
+      const int ya = y0 + (int)(short)(t2.y & 0xffff), xa = x0 + (t2.y >> 16);
+      const int yb = y0 + (int)(short)(t2.w & 0xffff), xb = x0 + (t2.w >> 16);
+      v[e] = ((unsigned)ya < (unsigned)q.Hs && (unsigned)xa < (unsigned)q.Ws) ? sr[t2.x] : 0.f;
+      v[e + 1] = ((unsigned)yb < (unsigned)q.Hs && (unsigned)xb < (unsigned)q.Ws) ? sr[t2.z] : 0.f;
     }
     uint32_t pk[8];
 #pragma unroll
@@ -180,23 +179,23 @@ __device__ __forceinline__ float ld_f32_pred(const float* p, bool pred) {
 }
 
 // One 8-K chunk of gather mode: rows ln + 32 q (q < 4) of the A stage, K = K0 .. K0 + 7, from
-// the table entries t[0..7]; written in the 128-byte-swizzled K-major layout (16-byte chunk c
+// the table entries t[0..7] (sr[q]: the row's source at its base position (y0, x0), which a
+// row past M sets to y0 = -32768); written in the 128-byte-swizzled K-major layout (16-byte chunk c
 // of row m at chunk position c ^ (m & 7)).
 __device__ __forceinline__ void gather_chunk(uint8_t* stage, int c, int ln, const int4 (&t4)[4],
                                              const float* const (&sr)[4], const int (&y0)[4], const int (&x0)[4],
-                                             const bool (&mv)[4], int Hs, int Ws) {
+                                             int Hs, int Ws) {
   float v[4][8];
 #pragma unroll
   for (int e = 0; e < 8; ++e) {
     const int4 tt = t4[e >> 1];
-    const int ch = (e & 1) ? tt.z : tt.x;
+    const int off = (e & 1) ? tt.z : tt.x;
     const int pk = (e & 1) ? tt.w : tt.y;
     const int dy = (int)(short)(pk & 0xffff), dx = pk >> 16;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int y = y0[q] + dy, x = x0[q] + dx;
-      const bool ok = mv[q] && ch >= 0 && (unsigned)y < (unsigned)Hs && (unsigned)x < (unsigned)Ws;
-      v[q][e] = ld_f32_pred(sr[q] + (ok ? ch + y * Ws + x : 0), ok);
+      const bool ok = (unsigned)(y0[q] + dy) < (unsigned)Hs && (unsigned)(x0[q] + dx) < (unsigned)Ws;
+      v[q][e] = ld_f32_pred(sr[q] + off, ok);
     }
   }
 #pragma unroll
@@ -325,17 +324,16 @@ __global__ void __launch_bounds__(TcgRoles<GATHER>::THREADS, 1)
       // this lane's rows ln + 32 q of the tile
       const float* sr[4];
       int y0[4], x0[4];
-      bool mv[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const long long m = tile / o.ntn * 128 + lane + 32 * q;
-        mv[q] = m < M;
-        const long long r = mv[q] ? m / gq.Pm : 0;
-        const int pp = mv[q] ? (int)(m - r * gq.Pm) : 0;
+        const bool mv = m < M;
+        const long long r = mv ? m / gq.Pm : 0;
+        const int pp = mv ? (int)(m - r * gq.Pm) : 0;
         const int i = pp / gq.nJ, j = pp - (pp / gq.nJ) * gq.nJ;
-        y0[q] = i * gq.ms + gq.cy;
+        y0[q] = mv ? i * gq.ms + gq.cy : -32768;
         x0[q] = j * gq.ms + gq.cx;
-        sr[q] = src + r * gq.d_src;
+        sr[q] = src + r * gq.d_src + (mv ? y0[q] * gq.Ws + x0[q] : 0);
       }
       for (int kb = 0; kb < nkb; ++kb, ++seq) {
         if ((int)(seq % TCG_NS) != g) continue;
@@ -352,7 +350,7 @@ __global__ void __launch_bounds__(TcgRoles<GATHER>::THREADS, 1)
           int4 t4[4];
 #pragma unroll
           for (int e = 0; e < 4; ++e) t4[e] = reinterpret_cast<const int4*>(stab + kb * 64 + c * 8)[e];
-          gather_chunk(stage, c, lane, t4, sr, y0, x0, mv, gq.Hs, gq.Ws);
+          gather_chunk(stage, c, lane, t4, sr, y0, x0, gq.Hs, gq.Ws);
         }
         fence_proxy_async();   // the stage's generic-proxy stores, before the MMA reads it
         __syncwarp();
@@ -486,9 +484,12 @@ static ConvPhase conv_phase(int a, int k, int s, int pad, int in) {
 static int taps_per_axis(const LayerDev& l) { return (l.k + l.stride - 1) / l.stride; }
 static int kp_bwd(const LayerDev& l) { return pad_to(l.out_c * taps_per_axis(l) * taps_per_axis(l), 64); }
 static int kp_fwd(const LayerDev& l) { return pad_to(l.in_c * l.k * l.k, 64); }
-static int2 tab_entry(int chan_off, int dy, int dx) {
-  return make_int2(chan_off, (int)(((uint32_t)dy & 0xffffu) | ((uint32_t)dx << 16)));
+// Gather table entry: source offset chan_off + dy * Ws + dx from a row's base position, and the
+// tap offsets for the bounds test; kNoTap marks a zero column.
+static int2 tab_entry(int chan_off, int dy, int dx, int Ws) {
+  return make_int2(chan_off + dy * Ws + dx, (int)(((uint32_t)dy & 0xffffu) | ((uint32_t)dx << 16)));
 }
+static const int2 kNoTap = make_int2(0, 0x8000);   // dy = -32768
 
 // N tile of a GEMM with N outputs: the whole of N up to 256, else tiles of 256.
 static void n_tiles(int N, int* Np, int* ntn) {
@@ -586,14 +587,14 @@ static int tcg_prepare(bcrown_net* net, ConvTc* t) {
     const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
     std::vector<__nv_bfloat16> wb((size_t)s * s * c.Np_b * c.Kp_b, zero);
     std::vector<__nv_bfloat16> wf((size_t)c.Np_f * c.Kp_f, zero);
-    std::vector<int2> tb((size_t)s * s * c.Kp_b, make_int2(-1, 0)), tf((size_t)c.Kp_f, make_int2(-1, 0));
+    std::vector<int2> tb((size_t)s * s * c.Kp_b, kNoTap), tf((size_t)c.Kp_f, kNoTap);
     // forward: K = (ci, ky, kx), source (oy * s - pad + ky, ox * s - pad + kx) of channel ci
     for (int co = 0; co < l.out_c; ++co)
       for (int ci = 0; ci < l.in_c; ++ci)
         for (int q = 0; q < kk; ++q)
           wf[(size_t)co * c.Kp_f + ci * kk + q] = __float2bfloat16_rn(w[((size_t)co * l.in_c + ci) * kk + q]);
     for (int ci = 0; ci < l.in_c; ++ci)
-      for (int q = 0; q < kk; ++q) tf[ci * kk + q] = tab_entry(ci * l.in_h * l.in_w, q / l.k, q % l.k);
+      for (int q = 0; q < kk; ++q) tf[ci * kk + q] = tab_entry(ci * l.in_h * l.in_w, q / l.k, q % l.k, l.in_w);
     // backward, phase (a, b): K = (co, dy, dx), tap (ky0 + s dy, kx0 + s dx), source q = (i + off - dy, ...)
     for (int a = 0; a < s; ++a)
       for (int b = 0; b < s; ++b) {
@@ -604,7 +605,7 @@ static int tcg_prepare(bcrown_net* net, ConvTc* t) {
             for (int dx = 0; dx < px.nk; ++dx) {
               const int K = co * T * T + dy * T + dx;
               const int ky = py.k0 + s * dy, kx = px.k0 + s * dx;
-              tb[ph * c.Kp_b + K] = tab_entry(co * l.out_h * l.out_w, -dy, -dx);
+              tb[ph * c.Kp_b + K] = tab_entry(co * l.out_h * l.out_w, -dy, -dx, l.out_w);
               for (int ci = 0; ci < l.in_c; ++ci)
                 wb[(ph * c.Np_b + ci) * c.Kp_b + K] =
                     __float2bfloat16_rn(w[((size_t)co * l.in_c + ci) * kk + ky * l.k + kx]);
