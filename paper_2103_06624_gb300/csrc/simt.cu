@@ -219,6 +219,47 @@ __global__ void __launch_bounds__(256) k_init_top(RowsCtx c, int dtop, const flo
 // CERT: outward chord constants (from the tables), c summed rounded down, error terms rounded up.
 // ----------------------------------------------------------------------------------------
 constexpr int RELAX_WARPS = 8;   // warps per block; WPR of them share a row (wide layers: all 8)
+// One neuron of the relaxation (FP32 form), every load on its own chain: the slow path of the
+// vectorised loop, taken by groups that hold an unstable or a split neuron.  Returns Lambda_j
+// and adds Lambda_j b_j + A_j lambda_j to acc.
+__device__ __forceinline__ float relax_one(const RowsCtx& c, int j, size_t n, float a, uint8_t code, float bj,
+                                           bool check, int ns, const SplitSlot* sl, long long abase,
+                                           long long bbase, const float* __restrict__ alpha, int64_t n_alpha,
+                                           const float* __restrict__ beta, int64_t n_beta, float& acc) {
+  int s = 0;
+  float bet = 0.f;
+  if (check)
+    for (int q = 0; q < ns; ++q)
+      if (sl[q].idx == j) {
+        s = sl[q].sign;
+        const long long bi = bbase + sl[q].t;
+        if (bi >= 0 && bi < n_beta) bet = fmaxf(beta[bi], 0.f);
+        else flag(c.status, BCROWN_ERR_ARG);
+      }
+  float D = 0.f, lm = 0.f;
+  if (s == -1) D = 1.f;
+  else if (s == 1) D = 0.f;
+  else if (code == CODE_ACTIVE) D = 1.f;
+  else if (code == CODE_INACTIVE) D = 0.f;
+  else if (a >= 0.f) {
+    const long long ai = abase + c.tb.rank[n];
+    if (ai < 0 || ai >= n_alpha) flag(c.status, BCROWN_ERR_ARG);
+    else D = fminf(fmaxf(alpha[ai], 0.f), 1.f);
+  } else {
+    D = c.tb.slope[n];
+    lm = c.tb.icpt[n];
+  }
+  const float L = fmaf(a, D, bet * (float)s);
+  acc = fmaf(L, bj, fmaf(a, lm, acc));
+  return L;
+}
+
+// All four codes stable (active or inactive): no alpha, chord or split term.
+__device__ __forceinline__ bool stable4(uchar4 c4) {
+  return c4.x != CODE_UNSTABLE && c4.y != CODE_UNSTABLE && c4.z != CODE_UNSTABLE && c4.w != CODE_UNSTABLE;
+}
+__device__ __forceinline__ float d01(unsigned char code) { return code == CODE_ACTIVE ? 1.f : 0.f; }
+
 template <bool CERT, int WPR>
 __global__ void __launch_bounds__(32 * RELAX_WARPS) k_relax(RowsCtx c, int layer, int d, long long hoff,
                                                            const float* __restrict__ Ain, float* __restrict__ Lam,
@@ -301,10 +342,46 @@ __global__ void __launch_bounds__(32 * RELAX_WARPS) k_relax(RowsCtx c, int layer
     // CERT: acc is a lower bound of sum_j Lambda_j b_j + A_j lambda_j (every operation rounded
     // down); e1, e2 are upper bounds (rounded up) of the error terms below.
     const size_t n0 = (size_t)p * c.tb.H + hoff;
+    // FP32 form with 16-byte aligned rows: 4 consecutive neurons per lane (float4 A, bias and
+    // Lambda, uchar4 codes); a group of stable, unsplit neurons needs no other load
+    const bool vec4 = !CERT && ((d | (int)(n0 & 3)) & 3) == 0 &&
+                      ((reinterpret_cast<uintptr_t>(a_row) | reinterpret_cast<uintptr_t>(lam_row) |
+                        reinterpret_cast<uintptr_t>(bias)) & 15) == 0;
+    if (vec4) {
+      const uchar4* code4 = reinterpret_cast<const uchar4*>(c.tb.code + n0);
+      for (int q = sub * 32 + lane; q < d / 4; q += 32 * WPR) {
+        const int j = 4 * q;
+        const float4 a4 = reinterpret_cast<const float4*>(a_row)[q];
+        const float4 b4 = reinterpret_cast<const float4*>(bias)[q];
+        const uchar4 c4 = code4[q];
+        const uint32_t sb = ns == 0 ? 0u : (use_mask ? (smask[rs][j >> 5] >> (j & 31)) & 0xFu : 0xFu);
+        float4 L;
+        if (sb == 0u && stable4(c4)) {
+          L.x = fmaf(a4.x, d01(c4.x), 0.f);
+          L.y = fmaf(a4.y, d01(c4.y), 0.f);
+          L.z = fmaf(a4.z, d01(c4.z), 0.f);
+          L.w = fmaf(a4.w, d01(c4.w), 0.f);
+          acc = fmaf(L.x, b4.x, fmaf(a4.x, 0.f, acc));
+          acc = fmaf(L.y, b4.y, fmaf(a4.y, 0.f, acc));
+          acc = fmaf(L.z, b4.z, fmaf(a4.z, 0.f, acc));
+          acc = fmaf(L.w, b4.w, fmaf(a4.w, 0.f, acc));
+        } else {
+          L.x = relax_one(c, j, n0 + j, a4.x, c4.x, b4.x, (sb & 1u) != 0, ns, sl_, abase, bbase, alpha, n_alpha, beta,
+                          n_beta, acc);
+          L.y = relax_one(c, j + 1, n0 + j + 1, a4.y, c4.y, b4.y, (sb & 2u) != 0, ns, sl_, abase, bbase, alpha,
+                          n_alpha, beta, n_beta, acc);
+          L.z = relax_one(c, j + 2, n0 + j + 2, a4.z, c4.z, b4.z, (sb & 4u) != 0, ns, sl_, abase, bbase, alpha,
+                          n_alpha, beta, n_beta, acc);
+          L.w = relax_one(c, j + 3, n0 + j + 3, a4.w, c4.w, b4.w, (sb & 8u) != 0, ns, sl_, abase, bbase, alpha,
+                          n_alpha, beta, n_beta, acc);
+        }
+        reinterpret_cast<float4*>(lam_row)[q] = L;
+      }
+    }
     // RELAX_V neurons per lane per step, their loads issued in three rounds (A, code, bias; then
     // the unstable neurons' rank and chord; then alpha) instead of one dependent chain each
     constexpr int RELAX_V = 4;
-    for (int j0 = sub * 32 + lane; j0 < d; j0 += RELAX_V * 32 * WPR) {
+    for (int j0 = sub * 32 + lane; !vec4 && j0 < d; j0 += RELAX_V * 32 * WPR) {
       float av[RELAX_V], bv[RELAX_V], sl[RELAX_V], ic[RELAX_V], al[RELAX_V];
       uint8_t cv[RELAX_V];
       int32_t rk[RELAX_V];
@@ -687,6 +764,47 @@ __global__ void k_xstar(RowsCtx c, int d0, const float* __restrict__ A0, float* 
 // Adjoint epilogue of hidden layer i: zhat = Z (+ bias already added); gradients
 //   dalpha_j = A_j zhat_j (alpha in use), dbeta_j = S_jj zhat_j ; then h = D zhat + lambda.
 // ----------------------------------------------------------------------------------------
+// One neuron of the adjoint epilogue, every load on its own chain (the vectorised loop's slow
+// path): dalpha, dbeta for this neuron; returns h = D zhat + lambda.
+__device__ __forceinline__ float fwd_epi_one(const RowsCtx& c, int j, size_t n, float z, float a, uint8_t code,
+                                             bool check, int ns, const SplitSlot* slots, long long abase,
+                                             long long bbase, const float* __restrict__ alpha, int64_t n_alpha,
+                                             float* __restrict__ dalpha, float* __restrict__ dbeta,
+                                             int64_t n_beta) {
+  int s = 0, t = -1;
+  if (check)
+    for (int q = 0; q < ns; ++q)
+      if (slots[q].idx == j) {
+        s = slots[q].sign;
+        t = slots[q].t;
+      }
+  float D = 0.f, lm = 0.f;
+  long long ai = -1;
+  if (code == CODE_UNSTABLE) {
+    ai = abase + c.tb.rank[n];
+    if (ai < 0 || ai >= n_alpha) {
+      flag(c.status, BCROWN_ERR_ARG);
+      ai = -1;
+    }
+  }
+  if (s == -1) D = 1.f;
+  else if (s == 1) D = 0.f;
+  else if (code == CODE_ACTIVE) D = 1.f;
+  else if (code == CODE_INACTIVE) D = 0.f;
+  else if (a >= 0.f) D = ai >= 0 ? fminf(fmaxf(alpha[ai], 0.f), 1.f) : 0.f;
+  else {
+    D = c.tb.slope[n];
+    lm = c.tb.icpt[n];
+  }
+  if (ai >= 0) dalpha[ai] = (s == 0 && a >= 0.f) ? a * z : 0.f;
+  if (s != 0) {
+    const long long bi = bbase + t;
+    if (bi >= 0 && bi < n_beta) dbeta[bi] = (float)s * z;
+    else flag(c.status, BCROWN_ERR_ARG);
+  }
+  return fmaf(D, z, lm);
+}
+
 __global__ void __launch_bounds__(256) k_fwd_epi(RowsCtx c, int layer, int d, long long hoff,
                                                  float* __restrict__ Z, const float* __restrict__ Ai,
                                                  const float* __restrict__ alpha, int64_t n_alpha,
@@ -708,6 +826,37 @@ __global__ void __launch_bounds__(256) k_fwd_epi(RowsCtx c, int layer, int d, lo
   float* z_row = Z + (size_t)rl * d;
   const float* a_row = Ai + (size_t)rl * d;
   const size_t n0 = (size_t)p * c.tb.H + hoff;
+  // 16-byte aligned rows: 4 consecutive neurons per thread (float4 zhat and A, uchar4 codes); a
+  // group of stable, unsplit neurons writes h = D zhat and nothing else
+  const bool vec4 = ((d | (int)(n0 & 3)) & 3) == 0 &&
+                    ((reinterpret_cast<uintptr_t>(z_row) | reinterpret_cast<uintptr_t>(a_row)) & 15) == 0;
+  if (vec4) {
+    const uchar4* code4 = reinterpret_cast<const uchar4*>(c.tb.code + n0);
+    for (int q = threadIdx.x; q < d / 4; q += blockDim.x) {
+      const int j = 4 * q;
+      float4 z4 = reinterpret_cast<const float4*>(z_row)[q];
+      const float4 a4 = reinterpret_cast<const float4*>(a_row)[q];
+      const uchar4 c4 = code4[q];
+      const uint32_t sb = ns == 0 ? 0u : (use_mask ? (smask[j >> 5] >> (j & 31)) & 0xFu : 0xFu);
+      if (sb == 0u && stable4(c4)) {
+        z4.x = fmaf(d01(c4.x), z4.x, 0.f);
+        z4.y = fmaf(d01(c4.y), z4.y, 0.f);
+        z4.z = fmaf(d01(c4.z), z4.z, 0.f);
+        z4.w = fmaf(d01(c4.w), z4.w, 0.f);
+      } else {
+        z4.x = fwd_epi_one(c, j, n0 + j, z4.x, a4.x, c4.x, (sb & 1u) != 0, ns, slots, abase, bbase, alpha, n_alpha,
+                           dalpha, dbeta, n_beta);
+        z4.y = fwd_epi_one(c, j + 1, n0 + j + 1, z4.y, a4.y, c4.y, (sb & 2u) != 0, ns, slots, abase, bbase, alpha,
+                           n_alpha, dalpha, dbeta, n_beta);
+        z4.z = fwd_epi_one(c, j + 2, n0 + j + 2, z4.z, a4.z, c4.z, (sb & 4u) != 0, ns, slots, abase, bbase, alpha,
+                           n_alpha, dalpha, dbeta, n_beta);
+        z4.w = fwd_epi_one(c, j + 3, n0 + j + 3, z4.w, a4.w, c4.w, (sb & 8u) != 0, ns, slots, abase, bbase, alpha,
+                           n_alpha, dalpha, dbeta, n_beta);
+      }
+      reinterpret_cast<float4*>(z_row)[q] = z4;
+    }
+    return;
+  }
   // EPI_V neurons per thread per step, their loads issued in three rounds (z, A, code; then the
   // unstable neurons' rank and chord; then alpha) instead of one dependent chain per neuron
   constexpr int EPI_V = 4;
