@@ -179,14 +179,24 @@ def fp32_simt_peak_tflops(sm_mhz):
 
 def measured_traffic(name, algorithmic_bytes):
     """DRAM bytes per launch of a kernel from the committed ncu summary profiles/<name>.json, or
-    None when the kernel source has changed since those counters were taken."""
+    None when the kernel's sources (the files it lists, hashed in order) have changed since
+    those counters were taken."""
     import hashlib
     path = os.path.join(ROOT, "profiles", name + ".json")
     if not os.path.exists(path):
         return None
-    rec = json.load(open(path))
-    src = os.path.join(ROOT, rec["source"])
-    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["source_sha256"]:
+    try:
+        rec = json.load(open(path))
+        srcs = [os.path.join(ROOT, f) for f in rec["sources"]]
+        rec["sources_sha256"], rec["dram_bytes_per_launch"]
+    except (OSError, ValueError, KeyError, TypeError):
+        return None   # an unreadable or older record: no measured traffic
+    if not all(os.path.exists(f) for f in srcs):
+        return None
+    h = hashlib.sha256()
+    for f in srcs:
+        h.update(open(f, "rb").read())
+    if h.hexdigest() != rec["sources_sha256"]:
         return None
     return {"dram_bytes_per_launch": rec["dram_bytes_per_launch"],
             "vs_algorithmic": rec["dram_bytes_per_launch"] / algorithmic_bytes,
