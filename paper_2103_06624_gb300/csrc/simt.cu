@@ -272,9 +272,8 @@ __global__ void __launch_bounds__(32 * RELAX_WARPS) k_relax(RowsCtx c, int layer
   constexpr int RPB = RELAX_WARPS / WPR;   // rows per block
   __shared__ SplitSlot slots[RPB][BCROWN_MAX_SPLITS];
   __shared__ int nslots[RPB];
-  // split bitmask per row slot: a whole block's row up to SPLIT_MASK_WORDS * 32 neurons, or
-  // 2048 neurons for each warp's own row
-  constexpr int MW = WPR > 1 ? SPLIT_MASK_WORDS : 64;
+  // split bitmask of a wide row (a whole block's row, up to SPLIT_MASK_WORDS * 32 neurons)
+  constexpr int MW = WPR > 1 ? SPLIT_MASK_WORDS : 1;
   __shared__ uint32_t smask[RPB][MW];
   __shared__ float red[RELAX_WARPS][3];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -316,7 +315,7 @@ __global__ void __launch_bounds__(32 * RELAX_WARPS) k_relax(RowsCtx c, int layer
   }
   if (WPR > 1) __syncthreads();
   else __syncwarp();
-  const bool use_mask = d <= MW * 32;
+  const bool use_mask = WPR > 1 && d <= MW * 32;
   if (use_mask) {
     if (live)
       for (int q = sub * 32 + lane; q < (d + 31) / 32; q += 32 * WPR) smask[rs][q] = 0u;
@@ -342,9 +341,64 @@ __global__ void __launch_bounds__(32 * RELAX_WARPS) k_relax(RowsCtx c, int layer
     // CERT: acc is a lower bound of sum_j Lambda_j b_j + A_j lambda_j (every operation rounded
     // down); e1, e2 are upper bounds (rounded up) of the error terms below.
     const size_t n0 = (size_t)p * c.tb.H + hoff;
+    // Rows of up to 2048 neurons (one warp each): one neuron per lane per step, the split list
+    // scanned per neuron (short for these rows); measured faster there than the wide-row code
+    // below, which the wide (conv) layers need.
+    if (WPR == 1) {
+  #pragma unroll 4
+      for (int j = sub * 32 + lane; j < d; j += 32 * WPR) {
+        const float a = a_row[j];
+        const size_t n = (size_t)p * c.tb.H + hoff + j;
+        int s = 0;
+        float bet = 0.f;
+        for (int q = 0; q < ns; ++q)
+          if (sl_[q].idx == j) {
+            s = sl_[q].sign;
+            const long long bi = bbase + sl_[q].t;
+            if (bi >= 0 && bi < n_beta) bet = fmaxf(beta[bi], 0.f);
+            else flag(c.status, BCROWN_ERR_ARG);
+          }
+        float D = 0.f, lm = 0.f;
+        const uint8_t code = c.tb.code[n];
+        if (s == -1) D = 1.f;
+        else if (s == 1) D = 0.f;
+        else if (code == CODE_ACTIVE) D = 1.f;
+        else if (code == CODE_INACTIVE) D = 0.f;
+        else if (a >= 0.f) {
+          const long long ai = abase + c.tb.rank[n];
+          if (ai < 0 || ai >= n_alpha) {
+            flag(c.status, BCROWN_ERR_ARG);
+            D = 0.f;
+          } else {
+            D = fminf(fmaxf(alpha[ai], 0.f), 1.f);
+          }
+        } else {
+          // upper chord, slope and intercept rounded up (outward) in the tables
+          D = c.tb.slope[n];
+          lm = c.tb.icpt[n];
+        }
+        const float L = fmaf(a, D, bet * (float)s);
+        lam_row[j] = L;
+        const float bj = bias[j];
+        if (CERT) {
+          acc = __fadd_rd(acc, __fadd_rd(__fmul_rd(L, bj), __fmul_rd(a, lm)));
+          const bool exact = (s == 0) && (D == 0.f || D == 1.f);
+          if (!exact) {
+            // Lambda_j was rounded once: |error| <= 2^-23 |Lambda_j| (+ an underflow margin),
+            // acting on |z_j| <= max(|l_j|, |u_j|)
+            const float zmax = fmaxf(fabsf(c.l[n]), fabsf(c.u[n]));
+            const float er = __fmaf_ru(fabsf(L), 0x1p-23f, 0x1p-140f);
+            e1 = __fadd_ru(e1, __fmul_ru(er, zmax));
+          }
+          e2 = __fadd_ru(e2, __fmul_ru(fabsf(L), wm[n]));
+        } else {
+          acc = fmaf(L, bj, fmaf(a, lm, acc));
+        }
+      }
+    }
     // FP32 form with 16-byte aligned rows: 4 consecutive neurons per lane (float4 A, bias and
     // Lambda, uchar4 codes); a group of stable, unsplit neurons needs no other load
-    const bool vec4 = !CERT && ((d | (int)(n0 & 3)) & 3) == 0 &&
+    const bool vec4 = WPR > 1 && !CERT && ((d | (int)(n0 & 3)) & 3) == 0 &&
                       ((reinterpret_cast<uintptr_t>(a_row) | reinterpret_cast<uintptr_t>(lam_row) |
                         reinterpret_cast<uintptr_t>(bias)) & 15) == 0;
     if (vec4) {
@@ -381,7 +435,7 @@ __global__ void __launch_bounds__(32 * RELAX_WARPS) k_relax(RowsCtx c, int layer
     // RELAX_V neurons per lane per step, their loads issued in three rounds (A, code, bias; then
     // the unstable neurons' rank and chord; then alpha) instead of one dependent chain each
     constexpr int RELAX_V = 4;
-    for (int j0 = sub * 32 + lane; !vec4 && j0 < d; j0 += RELAX_V * 32 * WPR) {
+    for (int j0 = sub * 32 + lane; WPR > 1 && !vec4 && j0 < d; j0 += RELAX_V * 32 * WPR) {
       float av[RELAX_V], bv[RELAX_V], sl[RELAX_V], ic[RELAX_V], al[RELAX_V];
       uint8_t cv[RELAX_V];
       int32_t rk[RELAX_V];
@@ -805,6 +859,9 @@ __device__ __forceinline__ float fwd_epi_one(const RowsCtx& c, int j, size_t n, 
   return fmaf(D, z, lm);
 }
 
+// WIDE: rows of more than 2048 neurons (conv layers); the narrow instantiation keeps only the
+// simple loop, and with it the register count of that loop.
+template <bool WIDE>
 __global__ void __launch_bounds__(256) k_fwd_epi(RowsCtx c, int layer, int d, long long hoff,
                                                  float* __restrict__ Z, const float* __restrict__ Ai,
                                                  const float* __restrict__ alpha, int64_t n_alpha,
@@ -816,8 +873,8 @@ __global__ void __launch_bounds__(256) k_fwd_epi(RowsCtx c, int layer, int d, lo
   int b, k, p;
   if (!row_prop(c, rl, &b, &k, &p)) p = 0;
   int ns = stage_splits(c, b, layer, d, slots, &n_slots);
-  __shared__ uint32_t smask[SPLIT_MASK_WORDS];
-  const bool use_mask = ns > 0 && d <= SPLIT_MASK_WORDS * 32;
+  extern __shared__ uint32_t smask[];   // ceil(d / 32) words for wide rows (the launch sizes it)
+  const bool use_mask = WIDE && ns > 0 && d <= SPLIT_MASK_WORDS * 32;
   if (use_mask) split_mask_block(slots, ns, d, smask);   // ns is uniform over the block
   int cnt = c.bt.split_cnt[b];
   int Up = c.tb.U[p];
@@ -826,6 +883,47 @@ __global__ void __launch_bounds__(256) k_fwd_epi(RowsCtx c, int layer, int d, lo
   float* z_row = Z + (size_t)rl * d;
   const float* a_row = Ai + (size_t)rl * d;
   const size_t n0 = (size_t)p * c.tb.H + hoff;
+  if constexpr (!WIDE) {
+    // narrow rows: one neuron per thread, the split list scanned per neuron (measured faster
+    // there than the wide-row code below)
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+      float z = z_row[j];
+      float a = a_row[j];
+      size_t n = (size_t)p * c.tb.H + hoff + j;
+      int s = 0, t = -1;
+      for (int q = 0; q < ns; ++q)
+        if (slots[q].idx == j) {
+          s = slots[q].sign;
+          t = slots[q].t;
+        }
+      uint8_t code = c.tb.code[n];
+      float D = 0.f, lm = 0.f;
+      long long ai = -1;
+      if (code == CODE_UNSTABLE) {
+        ai = abase + c.tb.rank[n];
+        if (ai < 0 || ai >= n_alpha) {
+          flag(c.status, BCROWN_ERR_ARG);
+          ai = -1;
+        }
+      }
+      if (s == -1) D = 1.f;
+      else if (s == 1) D = 0.f;
+      else if (code == CODE_ACTIVE) D = 1.f;
+      else if (code == CODE_INACTIVE) D = 0.f;
+      else if (a >= 0.f) D = ai >= 0 ? fminf(fmaxf(alpha[ai], 0.f), 1.f) : 0.f;
+      else {
+        D = c.tb.slope[n];
+        lm = c.tb.icpt[n];
+      }
+      if (ai >= 0) dalpha[ai] = (s == 0 && a >= 0.f) ? a * z : 0.f;
+      if (s != 0) {
+        long long bi = bbase + t;
+        if (bi >= 0 && bi < n_beta) dbeta[bi] = (float)s * z;
+        else flag(c.status, BCROWN_ERR_ARG);
+      }
+      z_row[j] = fmaf(D, z, lm);
+    }
+  } else {
   // 16-byte aligned rows: 4 consecutive neurons per thread (float4 zhat and A, uchar4 codes); a
   // group of stable, unsplit neurons writes h = D zhat and nothing else
   const bool vec4 = ((d | (int)(n0 & 3)) & 3) == 0 &&
@@ -924,6 +1022,7 @@ __global__ void __launch_bounds__(256) k_fwd_epi(RowsCtx c, int layer, int d, lo
       }
       z_row[j] = fmaf(D, z[v], lm);
     }
+  }
   }
 }
 
@@ -1454,7 +1553,13 @@ void launch_fwd_epi(const RowsCtx& c, int layer, int d, long long hoff, float* Z
                     const float* alpha, int64_t n_alpha, float* dalpha, float* dbeta, int64_t n_beta,
                     cudaStream_t s) {
   if (c.R <= 0) return;
-  { k_fwd_epi<<<c.R, 256, 0, s>>>(c, layer, d, hoff, Z, Ai, alpha, n_alpha, dalpha, dbeta, n_beta); ++g_launches; }
+  if (d <= 2048) {
+    k_fwd_epi<false><<<c.R, 256, 0, s>>>(c, layer, d, hoff, Z, Ai, alpha, n_alpha, dalpha, dbeta, n_beta);
+  } else {
+    const size_t smem = d <= SPLIT_MASK_WORDS * 32 ? (size_t)(d + 31) / 32 * sizeof(uint32_t) : 0;
+    k_fwd_epi<true><<<c.R, 256, smem, s>>>(c, layer, d, hoff, Z, Ai, alpha, n_alpha, dalpha, dbeta, n_beta);
+  }
+  ++g_launches;
 }
 
 void launch_adam(int R, int K, const BatchView& bt, const int32_t* U, int P, const float* lb_t, float* best_lb,
