@@ -61,8 +61,10 @@ enum { BCROWN_LAYER_FC = 0, BCROWN_LAYER_CONV = 1 };
  *            kernel per call; other networks (conv layers of <= 256 channels with
  *            channels x taps <= 2048, fc layers of <= 65536 neurons) run every
  *            contraction as a tensor-core GEMM (conv layers over an im2col operand,
- *            transposed convolutions split into stride phases) and the relaxation in
- *            FP32.  Any alpha, beta gives a valid bound (Section 3.1), so this is used
+ *            transposed convolutions split into stride phases; the operand gathered
+ *            in shared memory, or written to an HBM buffer first when the environment
+ *            holds BCROWN_CONV_IM2COL=1 at library load, for comparison) and the
+ *            relaxation in FP32.  Any alpha, beta gives a valid bound (Section 3.1), so this is used
  *            for the optimisation iterations.  Other networks get
  *            BCROWN_ERR_UNIMPLEMENTED.
  *  CERTIFY : FP32 contractions plus a priori rounding-error terms, upper-chord
