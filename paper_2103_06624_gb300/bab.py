@@ -1,0 +1,190 @@
+"""Branch and bound around the batched bound (Algorithm 1): the driver that decides a property.
+
+A property is verified when every margin spec k has c_k^T f(x) > 0 on the whole input box.
+The driver keeps a pool of subdomains (split assignments of root-unstable neurons, Eq. 3), takes
+the ones with the lowest certified bound in batches, splits each on one neuron into its two
+children (z >= 0 and z <= 0; the parent's alpha is inherited and the new split's beta starts at
+0, as batch_split does), bounds the children with the optimised beta-CROWN bound (Theorem 3.1,
+Eq. opt_alpha_beta; one engine call per batch) and drops those whose bound is positive for every
+spec (Domain_Filter).  The property is
+
+  verified  when the pool empties;
+  violated  when an input of the box has a negative margin: searched among random points of the
+            box and the box centre before branching (the witness is re-checked in FP64);
+  unknown   when the budget (rounds, bounded subdomains, time) runs out, or only fully split
+            subdomains remain open (their bound after a finite number of Adam steps need not
+            have reached the exact subdomain minimum of Theorem 3.3).
+
+Branching rule: the paper names BaBSR and FSB but does not define their scores, so a static
+rule stands in: the unsplit root-unstable neuron with the widest triangle relaxation, measured
+by the intercept of its upper chord, u (-l) / (u - l).
+
+The engine does the bounding: engine.optimize(subdomains, alpha, beta) -> (lb, alpha, beta) on
+one batch (subdomains as (property, neuron indices, signs)), engine.margins(x) -> C f(x) in FP64
+for rows of inputs.  GpuEngine runs bcrown_optimize (BF16 iterations and the certifying pass).
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import workloads as wl
+
+
+@dataclass
+class Domain:
+    splits: np.ndarray   # global hidden-neuron indices, in split order
+    signs: np.ndarray    # int8: -1 for z >= 0 (active), +1 for z <= 0 (inactive)
+    alpha: np.ndarray    # [K * U] float32, layout [k][unstable rank]
+    beta: np.ndarray     # [K * len(splits)] float32, layout [k][split]
+    lb: np.ndarray       # [K] certified lower bounds of the margins
+
+    @property
+    def depth(self) -> int:
+        return len(self.splits)
+
+
+@dataclass
+class BabResult:
+    status: str                          # "verified", "violated" or "unknown"
+    rounds: int = 0
+    bounded: int = 0                     # subdomains bounded (the root included)
+    max_depth: int = 0
+    open_domains: int = 0
+    min_lb: float = float("inf")         # lowest bound among open subdomains at exit
+    witness: np.ndarray | None = None    # an input with a negative margin (violated)
+    witness_margins: np.ndarray | None = None
+    seconds: float = 0.0
+    history: list = field(default_factory=list)   # per round: (open domains, min lb)
+
+
+def branching_scores(l, u):
+    """Upper-chord intercept u (-l) / (u - l) of root-unstable neurons, -inf for stable ones."""
+    l = np.asarray(l, np.float64)
+    u = np.asarray(u, np.float64)
+    un = (l < 0) & (u > 0)
+    s = np.full(l.shape, -np.inf)
+    s[un] = u[un] * (-l[un]) / (u[un] - l[un])
+    return s
+
+
+def _children(parent, j, K):
+    """The two subdomains of splitting neuron j: alpha inherited, beta of the new split 0."""
+    cnt = parent.depth
+    b = parent.beta.reshape(K, cnt)
+    beta = np.concatenate([b, np.zeros((K, 1), np.float32)], axis=1).reshape(-1)
+    splits = np.append(parent.splits, j).astype(np.int64)
+    kids = []
+    for sign in (-1, 1):
+        kids.append(Domain(splits, np.append(parent.signs, sign).astype(np.int8), parent.alpha.copy(),
+                           beta.copy(), parent.lb))
+    return kids
+
+
+def _falsify(engine, x_lo, x_hi, n_samples, rng):
+    """Random points of the box and its centre; returns (x, margins) of the worst one."""
+    pts = [0.5 * (x_lo + x_hi)]
+    if n_samples > 0:
+        pts.append(rng.uniform(x_lo, x_hi, size=(n_samples, x_lo.shape[0])))
+    x = np.vstack([np.atleast_2d(p) for p in pts])
+    m = engine.margins(x)
+    i = int(np.argmin(m.min(axis=1)))
+    return x[i], m[i]
+
+
+def bab(engine, prop, l, u, x_lo, x_hi, batch_size=512, max_rounds=50, max_bounded=1_000_000,
+        n_samples=256, seed=0, time_limit=None, alpha_init=0.5):
+    """Decide property `prop` (its box x_lo, x_hi and root bounds l, u over all hidden neurons)."""
+    t0 = time.perf_counter()
+    K = engine.K
+    x_lo = np.asarray(x_lo, np.float64)
+    x_hi = np.asarray(x_hi, np.float64)
+    scores = branching_scores(l, u)
+    U = int(np.isfinite(scores).sum())
+    order = np.argsort(-scores, kind="stable")[:U]   # root-unstable neurons, widest first
+    res = BabResult("unknown")
+
+    x, m = _falsify(engine, x_lo, x_hi, n_samples, np.random.default_rng(seed))
+    if m.min() < 0:
+        res.status, res.witness, res.witness_margins = "violated", x, m
+        res.seconds = time.perf_counter() - t0
+        return res
+
+    root = Domain(np.zeros(0, np.int64), np.zeros(0, np.int8), np.full(K * U, alpha_init, np.float32),
+                  np.zeros(0, np.float32), np.full(K, -np.inf, np.float32))
+    lb, a, b = engine.optimize([(prop, root.splits, root.signs)], root.alpha, root.beta)
+    root.lb, root.alpha, root.beta = np.asarray(lb, np.float32), np.asarray(a, np.float32), np.asarray(b, np.float32)
+    res.bounded = 1
+    pool = [] if root.lb.min() > 0 else [root]
+    exhausted = []
+    while pool:
+        if res.rounds >= max_rounds or res.bounded >= max_bounded or (
+                time_limit is not None and time.perf_counter() - t0 > time_limit):
+            break
+        res.rounds += 1
+        pool.sort(key=lambda d: float(d.lb.min()))
+        take, pool = pool[:batch_size], pool[batch_size:]
+        kids = []
+        for d in take:
+            used = set(d.splits.tolist())
+            j = next((int(n) for n in order if int(n) not in used), None)
+            if j is None:
+                exhausted.append(d)
+                continue
+            kids.extend(_children(d, j, K))
+        if kids:
+            subs = [(prop, k.splits, k.signs) for k in kids]
+            lb, a, b = engine.optimize(subs, np.concatenate([k.alpha for k in kids]),
+                                       np.concatenate([k.beta for k in kids]))
+            lb = np.asarray(lb, np.float32).reshape(len(kids), K)
+            a = np.asarray(a, np.float32).reshape(len(kids), K * U)
+            cnts = np.array([k.depth for k in kids])
+            boff = np.concatenate([[0], np.cumsum(cnts * K)])
+            b = np.asarray(b, np.float32)
+            for i, k in enumerate(kids):
+                k.lb, k.alpha, k.beta = lb[i], a[i], b[boff[i]:boff[i + 1]]
+                res.max_depth = max(res.max_depth, k.depth)
+                if k.lb.min() <= 0:      # Domain_Filter: keep the subdomains not yet verified
+                    pool.append(k)
+            res.bounded += len(kids)
+        res.history.append((len(pool) + len(exhausted), min([float(d.lb.min()) for d in pool + exhausted],
+                                                           default=float("inf"))))
+    open_ = pool + exhausted
+    res.open_domains = len(open_)
+    res.min_lb = min([float(d.lb.min()) for d in open_], default=float("inf"))
+    res.status = "verified" if not open_ else "unknown"
+    res.seconds = time.perf_counter() - t0
+    return res
+
+
+class GpuEngine:
+    """Bounds through the library: bcrown_optimize with BF16 iterations (the tensor-core path)
+    and the FP32 certifying pass, on the GPU; margins C f(x) in FP64 on the host."""
+
+    def __init__(self, problem, net, dom, unstable_counts, precision=None, iters=20):
+        from . import bcrown as bc
+        self.bc = bc
+        self.pb = problem
+        self.net = net
+        self.dom = dom
+        self.K = problem.K
+        self.U = list(unstable_counts)
+        self.cfg = bc.OptCfg(iters=iters, precision=bc.BF16 if precision is None else precision, certify=True)
+
+    def optimize(self, subs, alpha, beta):
+        import torch
+        batch = wl.pack_batch(self.pb.hidden_widths, self.K, self.U, subs)
+        db = self.bc.DeviceBatch.from_host(batch)
+        at = torch.as_tensor(np.ascontiguousarray(alpha, np.float32)).cuda()
+        bt = torch.as_tensor(np.ascontiguousarray(beta, np.float32)).cuda()
+        lb = self.bc.optimize(self.net, self.dom, db, at, bt, self.cfg)
+        st = self.bc.status(self.net)
+        if st != 0:
+            raise RuntimeError(f"bcrown device status {st}")
+        return lb.cpu().numpy(), at.cpu().numpy(), bt.cpu().numpy()
+
+    def margins(self, x):
+        f = wl.reference_forward(self.pb.layers, x)
+        return np.atleast_2d(f) @ self.pb.C.astype(np.float64).T

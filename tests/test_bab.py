@@ -1,0 +1,109 @@
+"""Branch-and-bound driver (Algorithm 1) on the oracle: its verdicts against the exact minimum of
+each margin over the box (all activation patterns enumerated, one LP each), and its host logic."""
+import numpy as np
+import pytest
+
+from oracle import bcrown_oracle as O
+from oracle import lp_pins as LP
+from paper_2103_06624_gb300 import bab
+from paper_2103_06624_gb300 import workloads as wl
+from tests.helpers import oracle_setup
+
+
+class OracleEngine:
+    """The driver's engine interface on the FP64 oracle (projected Adam, 20 iterations)."""
+
+    def __init__(self, pb, props, U):
+        self.pb, self.props, self.U = pb, props, list(U)
+        self.onet = O.OracleNet(pb.layers, pb.C)
+        self.K = pb.K
+        self.calls = 0
+
+    def optimize(self, subs, alpha, beta):
+        self.calls += 1
+        batch = wl.pack_batch(self.pb.hidden_widths, self.K, self.U, subs)
+        lb, a, b, _ = O.optimize(self.onet, self.props, batch, alpha, beta)
+        return lb, a, b
+
+    def margins(self, x):
+        return np.atleast_2d(wl.reference_forward(self.pb.layers, x)) @ self.pb.C.astype(np.float64).T
+
+
+# (widths, seed, eps): the expected verdict follows from the exact minima computed in the test
+CASES = {
+    "verified_at_root": ([5, 10, 10, 4], 2, 0.1),
+    "verified_by_branching_a": ([5, 10, 10, 4], 1, 0.15),
+    "verified_by_branching_b": ([5, 10, 10, 4], 4, 0.15),
+    "violated": ([5, 8, 8, 4], 0, 0.2),
+    "negative_min_missed_by_sampling": ([4, 8, 6, 4], 4, 0.4),
+}
+
+
+def make_case(name):
+    widths, seed, eps = CASES[name]
+    pb = wl.make_problem(name, wl.mlp_layers(widths, seed), 1, eps, 3, seed)
+    onet, props, unst = oracle_setup(pb)
+    exact = np.array([LP.exact_min(onet, pb.x_lo[0], pb.x_hi[0], props["l"][0], props["u"][0], [], k)
+                      for k in range(pb.K)])
+    return pb, props, unst, exact
+
+
+def run_case(name, engine_factory, **kw):
+    pb, props, unst, exact = make_case(name)
+    eng = engine_factory(pb, props, [len(u) for u in unst])
+    res = bab.bab(eng, 0, props["l"][0], props["u"][0], pb.x_lo[0], pb.x_hi[0], **kw)
+    return pb, exact, res
+
+
+def check_verdict(name, pb, exact, res):
+    """Soundness in every case; the expected verdict where the exact minima decide it."""
+    if res.status == "verified":
+        assert exact.min() > 0, (name, exact)
+    if res.status == "violated":
+        x = res.witness
+        assert np.all(x >= pb.x_lo[0] - 1e-12) and np.all(x <= pb.x_hi[0] + 1e-12)
+        m = np.atleast_2d(wl.reference_forward(pb.layers, x)) @ pb.C.astype(np.float64).T
+        assert m.min() < 0 and exact.min() < 0
+    if name.startswith("verified"):
+        assert res.status == "verified", (name, res.status, res.min_lb)
+    elif name == "violated":
+        assert res.status == "violated"
+    else:
+        # the exact minimum is negative but random points of the box all have positive margins:
+        # branching can never verify it (soundness), so the budget runs out
+        assert exact.min() < 0 and res.status == "unknown"
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_bab_on_the_oracle_agrees_with_exact_minima(name):
+    pb, exact, res = run_case(name, OracleEngine, batch_size=256, max_rounds=12, n_samples=256)
+    check_verdict(name, pb, exact, res)
+    if name == "verified_at_root":
+        assert res.rounds == 0 and res.bounded == 1
+    if name.startswith("verified_by_branching"):
+        assert res.rounds >= 1 and res.max_depth >= 1
+        # every round's open subdomains have a lowest bound no better than the exact minimum
+        assert all(mlb <= exact.min() + 1e-9 for _, mlb in res.history if np.isfinite(mlb))
+
+
+def test_children_inherit_alpha_and_start_the_new_beta_at_zero():
+    K = 3
+    parent = bab.Domain(np.array([7, 2]), np.array([-1, 1], np.int8), np.arange(K * 5, dtype=np.float32),
+                        np.arange(K * 2, dtype=np.float32) + 1, np.zeros(K, np.float32))
+    kids = bab._children(parent, 4, K)
+    assert [k.signs.tolist() for k in kids] == [[-1, 1, -1], [-1, 1, 1]]
+    for k in kids:
+        assert k.splits.tolist() == [7, 2, 4]
+        np.testing.assert_array_equal(k.alpha, parent.alpha)
+        # beta layout [k][split]: the parent's two betas per spec, then 0 for the new split
+        np.testing.assert_array_equal(k.beta.reshape(K, 3), [[1, 2, 0], [3, 4, 0], [5, 6, 0]])
+        assert k.alpha is not parent.alpha
+
+
+def test_branching_scores_rank_the_widest_relaxations_first():
+    l = np.array([-1.0, 0.5, -2.0, -0.5, -3.0])
+    u = np.array([1.0, 2.0, 1.0, -0.1, 0.1])
+    s = bab.branching_scores(l, u)
+    assert np.isneginf(s[1]) and np.isneginf(s[3])       # stable neurons are never split
+    np.testing.assert_allclose(s[[0, 2, 4]], [0.5, 2.0 / 3.0, 0.3 / 3.1])
+    assert list(np.argsort(-s)[:3]) == [2, 0, 4]

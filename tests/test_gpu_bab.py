@@ -1,0 +1,57 @@
+"""Branch and bound through the library (needs a GB300): the driver of Algorithm 1 on the GPU
+engine (BF16 iterations, FP32 certifying pass) reaches the verdicts the exact minima fix, like
+the oracle engine; and the ablation settings of the optimiser (alpha only, beta only)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import bcrown_oracle as O
+from paper_2103_06624_gb300 import bab
+from paper_2103_06624_gb300 import bcrown as bc
+from paper_2103_06624_gb300 import workloads as wl
+from tests.helpers import oracle_setup
+from tests.test_bab import CASES, OracleEngine, check_verdict, run_case
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_engine(pb, props, U):
+    net = bc.load_net(pb.layers, pb.C)
+    dom = bc.domain_from_host(props["x_lo"], props["x_hi"], props["l"], props["u"])
+    return bab.GpuEngine(pb, net, dom, U)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_bab_on_the_gpu_reaches_the_exact_verdict(name):
+    pb, exact, res = run_case(name, gpu_engine, batch_size=256, max_rounds=12, n_samples=256)
+    print("%s: %s, rounds %d, subdomains %d, depth %d" % (name, res.status, res.rounds, res.bounded, res.max_depth))
+    check_verdict(name, pb, exact, res)
+    _, _, ref = run_case(name, OracleEngine, batch_size=256, max_rounds=12, n_samples=256)
+    assert res.status == ref.status
+
+
+@pytest.mark.parametrize("frozen", ["alpha", "beta"])
+def test_ablation_settings_freeze_one_set_of_variables(frozen):
+    """lr_alpha = 0 keeps alpha (the beta-only variant), lr_beta = 0 keeps beta (alpha only);
+    the bound at the returned variables stays certified."""
+    pb = wl.problem_mlp_small()
+    onet, props, unst = oracle_setup(pb)
+    batch = wl.random_batch(pb, unst, 32, 1, 4, 1)
+    a0, b0 = wl.random_alpha_beta(batch, 7, 0.5)
+    net = bc.load_net(pb.layers, pb.C)
+    dom = bc.domain_from_host(props["x_lo"], props["x_hi"], props["l"], props["u"])
+    db = bc.DeviceBatch.from_host(batch)
+    at, bt = torch.as_tensor(a0).cuda(), torch.as_tensor(b0).cuda()
+    cfg = bc.OptCfg(lr_alpha=0.0 if frozen == "alpha" else 0.1, lr_beta=0.0 if frozen == "beta" else 0.05,
+                    precision=bc.BF16, certify=True)
+    lb = bc.optimize(net, dom, db, at, bt, cfg).cpu().numpy()
+    assert bc.status(net) == 0
+    a, b = at.cpu().numpy(), bt.cpu().numpy()
+    if frozen == "alpha":
+        np.testing.assert_array_equal(a, a0)
+        assert np.abs(b - b0).max() > 0
+    else:
+        np.testing.assert_array_equal(b, b0)
+        assert np.abs(a - a0).max() > 0
+    ref = O.bound(onet, props, batch, a, b)
+    assert np.all(lb <= ref + 1e-12 * np.abs(ref))
