@@ -30,10 +30,12 @@ namespace tc {
 //              position is q_y = i + off - dy for the phase's i-th row.  Each phase is one GEMM
 //              with K = (co, dy, dx) and its own weight matrix, so the operand holds no
 //              structural zeros of the stride.
-// Col is gathered into BF16 by k_im2col from a per-K table (source channel offset, signed tap
-// offsets: no divisions in the inner loop); k_tcg multiplies it with the BF16 weights:
-// M = rows x positions (tiles of 128 on the TMEM lanes), N = channels (padded to 16), K in
-// blocks of 64 streamed by TMA.
+// k_tcg<true> multiplies Col with the BF16 weights without storing Col: gather warps build each
+// 128 x 64 K block of it in shared memory from a per-K table (source offset and tap offsets: no
+// divisions in the inner loop) while TMA streams the weights; M = rows x positions (tiles of
+// 128 on the TMEM lanes), N = channels (padded to 16).  k_im2col + k_tcg<false> is the same
+// product with Col written to an HBM buffer and read back by TMA (fully connected layers, and
+// conv layers when BCROWN_CONV_IM2COL=1 selects it for comparison).
 // ------------------------------------------------------------------------------------------
 constexpr int TCG_NS = 4;         // pipeline stages (A: 128 x 64, B: Np x 64)
 // Warp roles of k_tcg: epilogue warps 0 .. EPI-1 (TMEM lane quadrant warp % 4, column chunks
