@@ -281,3 +281,45 @@ def test_bf16_conv_im2col_buffer_path_matches_oracle():
     r = subprocess.run([sys.executable, "-c", script], cwd=root, env=env, capture_output=True, text=True,
                        timeout=600)
     assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
+
+
+def test_bf16_conv_at_the_size_limits_matches_oracle():
+    """A conv layer at the limits of the tensor-core path: 256 output channels (N = 256, the
+    whole 512-column TMEM for two accumulators) and K = 128 x 4 x 4 = 2048 (the largest gather
+    table); the stride-2 backward pass split into 4 phases of K = 256 x 2 x 2."""
+    layers = wl.conv_layers((128, 8, 8), [(256, 4, 2, 1)], [16, 4], 5)
+    pb = wl.make_problem("conv_limits", layers, 1, 0.02, 3, 5)
+    onet = O.OracleNet(pb.layers, pb.C)
+    l, u = O.interval_bounds(onet, pb.x_lo, pb.x_hi)
+    l, u = l.astype(np.float32), u.astype(np.float32)
+    unst = [np.nonzero(O.unstable_mask(l[0], u[0]))[0]]
+    props = dict(x_lo=pb.x_lo, x_hi=pb.x_hi, l=l, u=u)
+    batch = wl.random_batch(pb, unst, 6, 0, 4, 2)
+    a, b = wl.random_alpha_beta(batch, 4, 1.0)
+    net, dom, db = _gpu(pb, props, batch)
+    lb = bc.bound(net, dom, db, _t(a), _t(b), bc.BF16).cpu().numpy()
+    assert bc.status(net) == 0
+    ref = O.bound(onet, props, batch, a, b)
+    err = np.abs(lb - ref) / _scale(ref)
+    print("bf16 conv at the limits: max err / median|lb| = %.3e" % err.max())
+    assert err.max() <= BF16_TOL
+    _, da, _ = bc.bound_grad(net, dom, db, _t(a), _t(b), bc.BF16)
+    _, da_ref, _ = O.grad(onet, props, batch, a.astype(np.float64), b.astype(np.float64))
+    rel = np.linalg.norm(da.cpu().numpy() - da_ref) / max(np.linalg.norm(da_ref), 1e-12)
+    assert rel <= 5e-2
+
+
+def test_bf16_conv_beyond_the_channel_limit_is_refused():
+    """272 output channels exceed the tensor-core path: BF16 is refused (BCROWN_ERR_UNIMPLEMENTED)
+    while FP32 bounds the same net."""
+    layers = wl.conv_layers((2, 4, 4), [(272, 3, 1, 1)], [4], 6)
+    pb = wl.make_problem("conv_wide", layers, 1, 0.05, 3, 6)
+    onet, props, unst = oracle_setup(pb)
+    batch = wl.random_batch(pb, unst, 4, 0, 2, 3)
+    a, b = wl.random_alpha_beta(batch, 5, 1.0)
+    net, dom, db = _gpu(pb, props, batch)
+    with pytest.raises(bc.BcrownError) as ei:
+        bc.bound(net, dom, db, _t(a), _t(b), bc.BF16)
+    assert ei.value.code == -6
+    lb = bc.bound(net, dom, db, _t(a), _t(b), bc.FP32).cpu().numpy()
+    assert np.max(rel_err(lb, O.bound(onet, props, batch, a, b))) <= RTOL
