@@ -1,0 +1,79 @@
+"""Host-side logic of bench.py (no GPU): the byte models behind the roofline numbers, the
+workload table, and when a committed DRAM-traffic record is used."""
+import hashlib
+import json
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+from paper_2103_06624_gb300 import workloads as wl  # noqa: E402
+
+
+def test_conv_byte_model_matches_the_per_row_figures():
+    """Conv outputs materialised once per direction in BF16, written and read: 2 * 2 * 2 bytes
+    per output neuron per row and iteration, which is 98 KB for the small conv net
+    ((8192 + 4096) outputs) and 983 KB for the large one ((65536 + 16384 + 32768 + 8192))."""
+    zero = np.zeros(1)
+    for pb, outputs in ((wl.problem_conv_small(), 8192 + 4096), (wl.problem_conv_big(), 65536 + 16384 + 32768 + 8192)):
+        assert bench.layer_path_bytes_per_row_iter(pb, zero, zero)[0] == 4 + 8 * outputs
+    # state: 24 B per alpha (value, m, v read and written), 8 B per alpha of stash, 30 B per split
+    pb = wl.problem_conv_small()
+    b = bench.layer_path_bytes_per_row_iter(pb, np.array([10.0]), np.array([3.0]))[0]
+    assert b == 4 + 8 * (8192 + 4096) + 32 * 10 + 30 * 3
+
+
+def test_fused_flop_model():
+    # 784-256x6-10: one backward pass of one row contracts layers 1..L-1
+    widths = wl.problem_mlp_784().widths
+    f = bench.algorithmic_flops_per_row_pass(widths)
+    assert f == 2 * (784 * 256 + 5 * 256 * 256)
+
+
+def test_workload_table_builds_each_problem():
+    for name, w in bench.WORKLOADS.items():
+        pb = bench.make_problem(name, 0, wl)
+        assert pb.K == 9
+        assert "{n}" in w["desc"]
+        if name == "batching":
+            assert pb.P == 64
+            counts = wl.loguniform_counts(pb.P, 16, 4096, 0)
+            assert counts.min() >= 16 and counts.max() <= 4096
+        else:
+            assert pb.P == 1 and w["subdomains"] > 0
+
+
+def _record(tmp, sources, data=b"kernel source", sha=None):
+    os.makedirs(os.path.join(tmp, "profiles"), exist_ok=True)
+    for f in sources:
+        p = os.path.join(tmp, f)
+        os.makedirs(os.path.dirname(p), exist_ok=True)
+        open(p, "wb").write(data)
+    h = hashlib.sha256()
+    for _ in sources:
+        h.update(data)
+    rec = {"sources": sources, "sources_sha256": sha or h.hexdigest(), "dram_bytes_per_launch": 1000.0}
+    json.dump(rec, open(os.path.join(tmp, "profiles", "k.json"), "w"))
+
+
+def test_traffic_record_is_used_only_while_its_sources_are_unchanged(tmp_path, monkeypatch):
+    tmp = str(tmp_path)
+    monkeypatch.setattr(bench, "ROOT", tmp)
+    assert bench.measured_traffic("k", 500.0) is None                     # no record
+    _record(tmp, ["a.cu", "b.cuh"])
+    tr = bench.measured_traffic("k", 500.0)
+    assert tr["dram_bytes_per_launch"] == 1000.0 and tr["vs_algorithmic"] == 2.0
+    open(os.path.join(tmp, "b.cuh"), "ab").write(b" changed")            # a source changed
+    assert bench.measured_traffic("k", 500.0) is None
+    json.dump({"source": "a.cu", "source_sha256": "x"}, open(os.path.join(tmp, "profiles", "k.json"), "w"))
+    assert bench.measured_traffic("k", 500.0) is None                     # older record format
+
+
+def test_committed_fused_record_names_existing_sources():
+    rec = json.load(open(os.path.join(ROOT, "profiles", "k_fused_grad.json")))
+    assert all(os.path.exists(os.path.join(ROOT, f)) for f in rec["sources"])
+    assert rec["dram_bytes_per_launch"] == rec["dram_bytes_read_per_launch"] + rec["dram_bytes_write_per_launch"]
