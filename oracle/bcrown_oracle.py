@@ -34,7 +34,7 @@ Functions and what pins them (tests under ``tests/test_oracle_*.py``):
 * ``batch_split``    -- children of a split (Algorithm 1, batch_split).  Pinned
                         by its definition on hand-written cases.
 
-Readings of points the paper leaves open (each is listed in the design doc):
+Readings of points the paper leaves open:
 split overrides stability; l >= 0 is active, u <= 0 inactive, l < 0 < u
 unstable; a tie A_j = 0 takes the alpha branch; each (subdomain, spec) row has
 its own alpha and beta; x* takes x_lo where A^(0)_m = 0.
