@@ -9,8 +9,9 @@ Eq. opt_alpha_beta; one engine call per batch) and drops those whose bound is po
 spec (Domain_Filter).  The property is
 
   verified  when the pool empties;
-  violated  when an input of the box has a negative margin: searched among random points of the
-            box and the box centre before branching (the witness is re-checked in FP64);
+  violated  when an input of the box has a negative margin: searched before branching among
+            random points of the box and its centre, then by projected sign-gradient descent
+            on the lowest margin from the best of them (the witness is re-checked in FP64);
   unknown   when the budget (rounds, bounded subdomains, time) runs out, or only fully split
             subdomains remain open (their bound after a finite number of Adam steps need not
             have reached the exact subdomain minimum of Theorem 3.3).
@@ -83,19 +84,70 @@ def _children(parent, j, K):
     return kids
 
 
-def _falsify(engine, x_lo, x_hi, n_samples, rng):
-    """Random points of the box and its centre; returns (x, margins) of the worst one."""
+def _margin_fn(problem):
+    """Differentiable margins C f(x) of rows of inputs (float64 torch on the host)."""
+    import torch
+    import torch.nn.functional as F
+    layers = [(ly.kind, torch.as_tensor(np.asarray(ly.W, np.float64)), torch.as_tensor(np.asarray(ly.b, np.float64)),
+               tuple(ly.in_shape), ly.stride, ly.pad) for ly in problem.layers]
+    C = torch.as_tensor(np.asarray(problem.C, np.float64))
+
+    def f(x):
+        h, n = x, x.shape[0]
+        for i, (kind, W, b, shape, stride, pad) in enumerate(layers):
+            if kind == "fc":
+                z = h.reshape(n, -1) @ W.T + b
+            else:
+                z = F.conv2d(h.reshape((n,) + shape), W, b, stride=stride, padding=pad).reshape(n, -1)
+            h = torch.relu(z) if i < len(layers) - 1 else z
+        return h @ C.T
+    return f
+
+
+def _pgd(problem, starts, x_lo, x_hi, steps, step_frac=0.25):
+    """Projected sign-gradient descent on min_k margin_k(x) over the box from each start; returns
+    the visited point with the lowest margin."""
+    import torch
+    f = _margin_fn(problem)
+    lo = torch.as_tensor(x_lo)
+    hi = torch.as_tensor(x_hi)
+    x = torch.as_tensor(np.asarray(starts, np.float64)).clone()
+    best_x, best_m = None, np.inf
+    for t in range(steps):
+        x.requires_grad_(True)
+        m = f(x).min(dim=1).values
+        md = m.detach()
+        i = int(torch.argmin(md))
+        if float(md[i]) < best_m:
+            best_m, best_x = float(md[i]), x[i].detach().clone().numpy()
+        (g,) = torch.autograd.grad(m.sum(), x)
+        step = step_frac * (1.0 - t / steps) * (hi - lo)
+        x = torch.minimum(torch.maximum(x.detach() - step * torch.sign(g), lo), hi)
+    return best_x
+
+
+def _falsify(engine, x_lo, x_hi, n_samples, rng, pgd_steps=0, pgd_starts=8):
+    """Random points of the box and its centre, then projected gradient descent from the best
+    of them; returns (x, margins) of the worst point found (margins from engine.margins)."""
     pts = [0.5 * (x_lo + x_hi)]
     if n_samples > 0:
         pts.append(rng.uniform(x_lo, x_hi, size=(n_samples, x_lo.shape[0])))
     x = np.vstack([np.atleast_2d(p) for p in pts])
     m = engine.margins(x)
-    i = int(np.argmin(m.min(axis=1)))
+    worst = m.min(axis=1)
+    if worst.min() >= 0 and pgd_steps > 0:
+        starts = x[np.argsort(worst)[:pgd_starts]]
+        xp = _pgd(engine.pb, starts, x_lo, x_hi, pgd_steps)
+        if xp is not None:
+            x = np.vstack([x, xp[None]])
+            m = np.vstack([m, engine.margins(xp[None])])
+            worst = m.min(axis=1)
+    i = int(np.argmin(worst))
     return x[i], m[i]
 
 
 def bab(engine, prop, l, u, x_lo, x_hi, batch_size=512, max_rounds=50, max_bounded=1_000_000,
-        n_samples=256, seed=0, time_limit=None, alpha_init=0.5):
+        n_samples=256, seed=0, time_limit=None, alpha_init=0.5, pgd_steps=20):
     """Decide property `prop` (its box x_lo, x_hi and root bounds l, u over all hidden neurons)."""
     t0 = time.perf_counter()
     K = engine.K
@@ -106,7 +158,7 @@ def bab(engine, prop, l, u, x_lo, x_hi, batch_size=512, max_rounds=50, max_bound
     order = np.argsort(-scores, kind="stable")[:U]   # root-unstable neurons, widest first
     res = BabResult("unknown")
 
-    x, m = _falsify(engine, x_lo, x_hi, n_samples, np.random.default_rng(seed))
+    x, m = _falsify(engine, x_lo, x_hi, n_samples, np.random.default_rng(seed), pgd_steps)
     if m.min() < 0:
         res.status, res.witness, res.witness_margins = "violated", x, m
         res.seconds = time.perf_counter() - t0

@@ -35,7 +35,7 @@ CASES = {
     "verified_by_branching_a": ([5, 10, 10, 4], 1, 0.15),
     "verified_by_branching_b": ([5, 10, 10, 4], 4, 0.15),
     "violated": ([5, 8, 8, 4], 0, 0.2),
-    "negative_min_missed_by_sampling": ([4, 8, 6, 4], 4, 0.4),
+    "violated_found_by_descent": ([4, 8, 6, 4], 4, 0.4),   # random points of the box all miss it
 }
 
 
@@ -66,12 +66,8 @@ def check_verdict(name, pb, exact, res):
         assert m.min() < 0 and exact.min() < 0
     if name.startswith("verified"):
         assert res.status == "verified", (name, res.status, res.min_lb)
-    elif name == "violated":
-        assert res.status == "violated"
     else:
-        # the exact minimum is negative but random points of the box all have positive margins:
-        # branching can never verify it (soundness), so the budget runs out
-        assert exact.min() < 0 and res.status == "unknown"
+        assert res.status == "violated", (name, res.status)
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -84,6 +80,16 @@ def test_bab_on_the_oracle_agrees_with_exact_minima(name):
         assert res.rounds >= 1 and res.max_depth >= 1
         # every round's open subdomains have a lowest bound no better than the exact minimum
         assert all(mlb <= exact.min() + 1e-9 for _, mlb in res.history if np.isfinite(mlb))
+
+
+def test_a_negative_minimum_is_never_verified_when_no_witness_is_found():
+    """Random points of the box all have positive margins and gradient descent is switched off:
+    branching must not verify the property (its exact minimum is negative), so every split is
+    made and the fully split subdomains stay open: unknown."""
+    pb, exact, res = run_case("violated_found_by_descent", OracleEngine, batch_size=256, max_rounds=12,
+                              n_samples=256, pgd_steps=0)
+    assert exact.min() < 0
+    assert res.status == "unknown" and res.open_domains > 0 and res.min_lb <= 0
 
 
 def test_children_inherit_alpha_and_start_the_new_beta_at_zero():
