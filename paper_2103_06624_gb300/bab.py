@@ -147,8 +147,11 @@ def _falsify(engine, x_lo, x_hi, n_samples, rng, pgd_steps=0, pgd_starts=8):
 
 
 def bab(engine, prop, l, u, x_lo, x_hi, batch_size=512, max_rounds=50, max_bounded=1_000_000,
-        n_samples=256, seed=0, time_limit=None, alpha_init=0.5, pgd_steps=20):
-    """Decide property `prop` (its box x_lo, x_hi and root bounds l, u over all hidden neurons)."""
+        n_samples=256, seed=0, time_limit=None, alpha_init=0.5, pgd_steps=20, start=None):
+    """Decide property `prop` (its box x_lo, x_hi and root bounds l, u over all hidden neurons).
+
+    start: subdomains to begin from instead of the whole box, as (neuron indices, signs) pairs;
+    "verified" then covers their union only (a witness of "violated" may lie anywhere in the box)."""
     t0 = time.perf_counter()
     K = engine.K
     x_lo = np.asarray(x_lo, np.float64)
@@ -164,12 +167,24 @@ def bab(engine, prop, l, u, x_lo, x_hi, batch_size=512, max_rounds=50, max_bound
         res.seconds = time.perf_counter() - t0
         return res
 
-    root = Domain(np.zeros(0, np.int64), np.zeros(0, np.int8), np.full(K * U, alpha_init, np.float32),
-                  np.zeros(0, np.float32), np.full(K, -np.inf, np.float32))
-    lb, a, b = engine.optimize([(prop, root.splits, root.signs)], root.alpha, root.beta)
-    root.lb, root.alpha, root.beta = np.asarray(lb, np.float32), np.asarray(a, np.float32), np.asarray(b, np.float32)
-    res.bounded = 1
-    pool = [] if root.lb.min() > 0 else [root]
+    if start is None:
+        start = [(np.zeros(0, np.int64), np.zeros(0, np.int8))]
+    first = [Domain(np.asarray(sp, np.int64), np.asarray(sg, np.int8), np.full(K * U, alpha_init, np.float32),
+                    np.zeros(K * len(sp), np.float32), np.full(K, -np.inf, np.float32)) for sp, sg in start]
+    pool = []
+    if first:
+        lb, a, b = engine.optimize([(prop, d.splits, d.signs) for d in first],
+                                   np.concatenate([d.alpha for d in first]), np.concatenate([d.beta for d in first]))
+        lb = np.asarray(lb, np.float32).reshape(len(first), K)
+        a = np.asarray(a, np.float32).reshape(len(first), K * U)
+        boff = np.concatenate([[0], np.cumsum([K * d.depth for d in first])])
+        b = np.asarray(b, np.float32)
+        for i, d in enumerate(first):
+            d.lb, d.alpha, d.beta = lb[i], a[i], b[boff[i]:boff[i + 1]]
+            res.max_depth = max(res.max_depth, d.depth)
+            if d.lb.min() <= 0:
+                pool.append(d)
+        res.bounded = len(first)
     exhausted = []
     while pool:
         if res.rounds >= max_rounds or res.bounded >= max_bounded or (
@@ -209,6 +224,50 @@ def bab(engine, prop, l, u, x_lo, x_hi, batch_size=512, max_rounds=50, max_bound
     res.status = "verified" if not open_ else "unknown"
     res.seconds = time.perf_counter() - t0
     return res
+
+
+_CODE = {"verified": 0, "unknown": 1, "violated": 2}
+
+
+def rank_starts(l, u, rank, world):
+    """The subdomains rank `rank` of `world` starts from: the sign patterns r, r + world, ... of
+    the first k = ceil(log2 world) neurons of the branching order (fewer if fewer are unstable)."""
+    scores = branching_scores(l, u)
+    U = int(np.isfinite(scores).sum())
+    order = np.argsort(-scores, kind="stable")[:U]
+    k = min(int(np.ceil(np.log2(world))) if world > 1 else 0, U)
+    top = order[:k].astype(np.int64)
+    patterns = [np.array([(-1 if (p >> i) & 1 == 0 else 1) for i in range(k)], np.int8) for p in range(1 << k)]
+    return [(top, sg) for sg in patterns[rank::world]]
+
+
+def bab_ranks(engine, prop, l, u, x_lo, x_hi, rank, world, dist, seed=0, **kw):
+    """One property decided by `world` ranks (one process per GPU, torch.distributed `dist`).
+
+    The first k = ceil(log2 world) neurons of the (static) branching order give 2^k subdomains;
+    rank r decides those with index r, r + world, ... on its own, with its own sampling seed.
+    The verdicts then combine in one all-reduce: violated if any rank found a witness (which the
+    lowest such rank broadcasts), verified if every rank verified its share, unknown otherwise.
+    There is no exchange while the ranks branch."""
+    import torch
+    mine = rank_starts(l, u, rank, world)
+    res = bab(engine, prop, l, u, x_lo, x_hi, seed=seed + rank, start=mine, **kw)
+    t = torch.tensor([_CODE[res.status]], dtype=torch.int64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    status = {v: s for s, v in _CODE.items()}[int(t.item())]
+    tot = torch.tensor([res.bounded, res.rounds], dtype=torch.int64)
+    dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+    out = BabResult(status, rounds=int(tot[1]), bounded=int(tot[0]), max_depth=res.max_depth,
+                    open_domains=res.open_domains, min_lb=res.min_lb, seconds=res.seconds)
+    if status == "violated":
+        src = torch.tensor([rank if res.status == "violated" else world], dtype=torch.int64)
+        dist.all_reduce(src, op=dist.ReduceOp.MIN)
+        w = torch.zeros(len(x_lo) + engine.K, dtype=torch.float64)
+        if int(src) == rank:
+            w = torch.as_tensor(np.concatenate([res.witness, res.witness_margins]).astype(np.float64))
+        dist.broadcast(w, int(src))
+        out.witness, out.witness_margins = w[:len(x_lo)].numpy(), w[len(x_lo):].numpy()
+    return out
 
 
 class GpuEngine:
