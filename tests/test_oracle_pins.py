@@ -347,3 +347,50 @@ def test_planted_mistakes_fail_a_pin(monkeypatch):
     sb = wl.Batch(**{**batch.__dict__, "split_sign": (-batch.split_sign).astype(np.int8)})
     lb_flip = O.bound(net, props, sb, a, b)
     assert np.max(np.abs(lb_flip - ref)) > 1e-6
+
+
+def test_infeasible_split_has_an_unbounded_dual():
+    """A split that contradicts stability (z_j <= 0 on a layer-1 neuron whose exact interval has
+    l_j > 0) leaves an empty subdomain: the LP of Eq. lp_verify_split is infeasible and the
+    bound grows without limit in beta.  Once beta dominates, the growth per unit of beta is the
+    minimum of z_j over the box (the exact layer-1 interval)."""
+    from tests.helpers import oracle_setup
+    pb = wl.problem_mlp_small()
+    onet, props, unst = oracle_setup(pb)
+    l = props["l"][0].astype(np.float64)
+    d1 = pb.hidden_widths[0]
+    j = int(np.argmax(l[:d1]))
+    assert l[j] > 0.5
+    lps = [LP.lp_value(onet, pb.x_lo[0], pb.x_hi[0], props["l"][0], props["u"][0], [(1, j, 1)], k)
+           for k in range(pb.K)]
+    assert all(np.isinf(v) for v in lps)
+    batch = wl.pack_batch(pb.hidden_widths, pb.K, [len(x) for x in unst], [(0, np.array([j]), np.array([1], np.int8))])
+    a = np.full(batch.n_alpha, 0.5)
+    lb = {t: O.bound(onet, props, batch, a, np.full(batch.n_beta, float(t))) for t in (0, 10, 100, 1000)}
+    assert np.all(lb[10] > lb[0]) and np.all(lb[100] > lb[10]) and np.all(lb[1000] > lb[100])
+    # min over the box of z_j = W_j x + b_j, written out in FP64
+    W = pb.layers[0].W.astype(np.float64)[j]
+    zmin = np.sum(np.minimum(W * pb.x_lo[0], W * pb.x_hi[0])) + float(pb.layers[0].b[j])
+    np.testing.assert_allclose((lb[1000] - lb[100]) / 900.0, zmin, rtol=1e-9)
+
+
+def test_split_children_cover_the_parent():
+    """Branching is sound: a subdomain's exact minimum is the smaller of its two children's
+    (z_j >= 0 and z_j <= 0 cover every point), on the root and on a depth-1 parent."""
+    from tests.helpers import oracle_setup
+    pb = wl.make_problem("cover", wl.mlp_layers([5, 10, 10, 4], 1), 1, 0.15, 3, 1)
+    onet, props, unst = oracle_setup(pb)
+    offs = np.concatenate([[0], np.cumsum(pb.hidden_widths)])
+
+    def lj(g):
+        i = int(np.searchsorted(offs, g, side="right"))
+        return i, int(g - offs[i - 1])
+
+    un = [lj(g) for g in unst[0][:2]]
+    args = (onet, pb.x_lo[0], pb.x_hi[0], props["l"][0], props["u"][0])
+    for parent in ([], [(un[0][0], un[0][1], 1)]):
+        i, j = un[1]
+        for k in range(pb.K):
+            p = LP.exact_min(*args, parent, k)
+            c = [LP.exact_min(*args, parent + [(i, j, s)], k) for s in (-1, 1)]
+            np.testing.assert_allclose(p, min(c), rtol=1e-9, atol=1e-12)
