@@ -41,6 +41,7 @@ class Domain:
     alpha: np.ndarray    # [K * U] float32, layout [k][unstable rank]
     beta: np.ndarray     # [K * len(splits)] float32, layout [k][split]
     lb: np.ndarray       # [K] certified lower bounds of the margins
+    owner: int = 0       # which of the properties being decided (bab_many) it belongs to
 
     @property
     def depth(self) -> int:
@@ -80,7 +81,7 @@ def _children(parent, j, K):
     kids = []
     for sign in (-1, 1):
         kids.append(Domain(splits, np.append(parent.signs, sign).astype(np.int8), parent.alpha.copy(),
-                           beta.copy(), parent.lb))
+                           beta.copy(), parent.lb, parent.owner))
     return kids
 
 
@@ -152,77 +153,103 @@ def bab(engine, prop, l, u, x_lo, x_hi, batch_size=512, max_rounds=50, max_bound
 
     start: subdomains to begin from instead of the whole box, as (neuron indices, signs) pairs;
     "verified" then covers their union only (a witness of "violated" may lie anywhere in the box)."""
+    return bab_many(engine, [(prop, l, u, x_lo, x_hi)], batch_size=batch_size, max_rounds=max_rounds,
+                    max_bounded=max_bounded, n_samples=n_samples, seed=seed, time_limit=time_limit,
+                    alpha_init=alpha_init, pgd_steps=pgd_steps, starts=None if start is None else [start])[0]
+
+
+def _bound(engine, doms, cases, K, Us):
+    """One engine call on a list of subdomains (of any of the properties); results written back."""
+    lb, a, b = engine.optimize([(cases[d.owner][0], d.splits, d.signs) for d in doms],
+                               np.concatenate([d.alpha for d in doms]), np.concatenate([d.beta for d in doms]))
+    lb = np.asarray(lb, np.float32).reshape(len(doms), K)
+    a = np.asarray(a, np.float32)
+    b = np.asarray(b, np.float32)
+    aoff = np.concatenate([[0], np.cumsum([K * Us[d.owner] for d in doms])])
+    boff = np.concatenate([[0], np.cumsum([K * d.depth for d in doms])])
+    for i, d in enumerate(doms):
+        d.lb, d.alpha, d.beta = lb[i], a[aoff[i]:aoff[i + 1]], b[boff[i]:boff[i + 1]]
+
+
+def bab_many(engine, cases, batch_size=512, max_rounds=50, max_bounded=1_000_000, n_samples=256, seed=0,
+             time_limit=None, alpha_init=0.5, pgd_steps=20, starts=None):
+    """Decide several properties at once: cases = [(prop, l, u, x_lo, x_hi), ...].  Their open
+    subdomains share one pool, so each engine call bounds the lowest-bound subdomains of all the
+    properties still open together (one batch of mixed properties).  Returns one BabResult per
+    case; starts, if given, holds each case's start subdomains (see bab)."""
     t0 = time.perf_counter()
     K = engine.K
-    x_lo = np.asarray(x_lo, np.float64)
-    x_hi = np.asarray(x_hi, np.float64)
-    scores = branching_scores(l, u)
-    U = int(np.isfinite(scores).sum())
-    order = np.argsort(-scores, kind="stable")[:U]   # root-unstable neurons, widest first
-    res = BabResult("unknown")
+    n = len(cases)
+    res = [BabResult("unknown") for _ in range(n)]
+    orders, Us = [], []
+    for c, (prop, l, u, x_lo, x_hi) in enumerate(cases):
+        scores = branching_scores(l, u)
+        Us.append(int(np.isfinite(scores).sum()))
+        orders.append(np.argsort(-scores, kind="stable")[:Us[-1]])   # root-unstable, widest first
+    open_case = [True] * n
+    for c, (prop, l, u, x_lo, x_hi) in enumerate(cases):
+        x, m = _falsify(engine, np.asarray(x_lo, np.float64), np.asarray(x_hi, np.float64), n_samples,
+                        np.random.default_rng(seed + c), pgd_steps)
+        if m.min() < 0:
+            res[c].status, res[c].witness, res[c].witness_margins = "violated", x, m
+            open_case[c] = False
 
-    x, m = _falsify(engine, x_lo, x_hi, n_samples, np.random.default_rng(seed), pgd_steps)
-    if m.min() < 0:
-        res.status, res.witness, res.witness_margins = "violated", x, m
-        res.seconds = time.perf_counter() - t0
-        return res
-
-    if start is None:
-        start = [(np.zeros(0, np.int64), np.zeros(0, np.int8))]
-    first = [Domain(np.asarray(sp, np.int64), np.asarray(sg, np.int8), np.full(K * U, alpha_init, np.float32),
-                    np.zeros(K * len(sp), np.float32), np.full(K, -np.inf, np.float32)) for sp, sg in start]
-    pool = []
+    first = []
+    for c in range(n):
+        if not open_case[c]:
+            continue
+        st = [(np.zeros(0, np.int64), np.zeros(0, np.int8))] if starts is None else starts[c]
+        first += [Domain(np.asarray(sp, np.int64), np.asarray(sg, np.int8), np.full(K * Us[c], alpha_init, np.float32),
+                         np.zeros(K * len(sp), np.float32), np.full(K, -np.inf, np.float32), c) for sp, sg in st]
+    pool, exhausted = [], []
     if first:
-        lb, a, b = engine.optimize([(prop, d.splits, d.signs) for d in first],
-                                   np.concatenate([d.alpha for d in first]), np.concatenate([d.beta for d in first]))
-        lb = np.asarray(lb, np.float32).reshape(len(first), K)
-        a = np.asarray(a, np.float32).reshape(len(first), K * U)
-        boff = np.concatenate([[0], np.cumsum([K * d.depth for d in first])])
-        b = np.asarray(b, np.float32)
-        for i, d in enumerate(first):
-            d.lb, d.alpha, d.beta = lb[i], a[i], b[boff[i]:boff[i + 1]]
-            res.max_depth = max(res.max_depth, d.depth)
+        _bound(engine, first, cases, K, Us)
+        for d in first:
+            res[d.owner].bounded += 1
+            res[d.owner].max_depth = max(res[d.owner].max_depth, d.depth)
             if d.lb.min() <= 0:
                 pool.append(d)
-        res.bounded = len(first)
-    exhausted = []
+    rounds = bounded = 0
     while pool:
-        if res.rounds >= max_rounds or res.bounded >= max_bounded or (
+        if rounds >= max_rounds or bounded >= max_bounded or (
                 time_limit is not None and time.perf_counter() - t0 > time_limit):
             break
-        res.rounds += 1
+        rounds += 1
         pool.sort(key=lambda d: float(d.lb.min()))
         take, pool = pool[:batch_size], pool[batch_size:]
         kids = []
+        for c in {d.owner for d in take}:
+            res[c].rounds += 1
         for d in take:
             used = set(d.splits.tolist())
-            j = next((int(n) for n in order if int(n) not in used), None)
+            j = next((int(v) for v in orders[d.owner] if int(v) not in used), None)
             if j is None:
                 exhausted.append(d)
                 continue
             kids.extend(_children(d, j, K))
         if kids:
-            subs = [(prop, k.splits, k.signs) for k in kids]
-            lb, a, b = engine.optimize(subs, np.concatenate([k.alpha for k in kids]),
-                                       np.concatenate([k.beta for k in kids]))
-            lb = np.asarray(lb, np.float32).reshape(len(kids), K)
-            a = np.asarray(a, np.float32).reshape(len(kids), K * U)
-            cnts = np.array([k.depth for k in kids])
-            boff = np.concatenate([[0], np.cumsum(cnts * K)])
-            b = np.asarray(b, np.float32)
-            for i, k in enumerate(kids):
-                k.lb, k.alpha, k.beta = lb[i], a[i], b[boff[i]:boff[i + 1]]
-                res.max_depth = max(res.max_depth, k.depth)
+            _bound(engine, kids, cases, K, Us)
+            bounded += len(kids)
+            for k in kids:
+                r = res[k.owner]
+                r.bounded += 1
+                r.max_depth = max(r.max_depth, k.depth)
                 if k.lb.min() <= 0:      # Domain_Filter: keep the subdomains not yet verified
                     pool.append(k)
-            res.bounded += len(kids)
-        res.history.append((len(pool) + len(exhausted), min([float(d.lb.min()) for d in pool + exhausted],
-                                                           default=float("inf"))))
-    open_ = pool + exhausted
-    res.open_domains = len(open_)
-    res.min_lb = min([float(d.lb.min()) for d in open_], default=float("inf"))
-    res.status = "verified" if not open_ else "unknown"
-    res.seconds = time.perf_counter() - t0
+        for c in range(n):
+            if open_case[c]:
+                left = [float(d.lb.min()) for d in pool + exhausted if d.owner == c]
+                res[c].history.append((len(left), min(left, default=float("inf"))))
+    for c in range(n):
+        if not open_case[c]:
+            continue
+        left = [d for d in pool + exhausted if d.owner == c]
+        res[c].open_domains = len(left)
+        res[c].min_lb = min([float(d.lb.min()) for d in left], default=float("inf"))
+        res[c].status = "verified" if not left else "unknown"
+    dt = time.perf_counter() - t0
+    for r in res:
+        r.seconds = dt
     return res
 
 
