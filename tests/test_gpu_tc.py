@@ -323,3 +323,33 @@ def test_bf16_conv_beyond_the_channel_limit_is_refused():
     assert ei.value.code == -6
     lb = bc.bound(net, dom, db, _t(a), _t(b), bc.FP32).cpu().numpy()
     assert np.max(rel_err(lb, O.bound(onet, props, batch, a, b))) <= RTOL
+
+
+@pytest.mark.parametrize("which", ["conv_small", "conv_big"])
+def test_bf16_conv_full_size_sampled(which):
+    """The conv workloads at their full sizes in BF16 (the bench's configuration: 2048 and 4096
+    BaB-tree subdomains x 9 specs in one bound pass); sampled subdomains recomputed by the
+    oracle one by one."""
+    if which == "conv_small":
+        pb = wl.problem_conv_small()
+        onet, props, unst = oracle_setup(pb)
+        n, depth, n_check = 2048, 16, 12
+    else:
+        pb = wl.problem_conv_big()
+        onet = O.OracleNet(pb.layers, pb.C)
+        l, u = O.interval_bounds(onet, pb.x_lo, pb.x_hi)
+        l, u = l.astype(np.float32), u.astype(np.float32)
+        unst = [np.nonzero(O.unstable_mask(l[0], u[0]))[0]]
+        props = dict(x_lo=pb.x_lo, x_hi=pb.x_hi, l=l, u=u)
+        n, depth, n_check = 4096, 24, 3
+    batch = wl.tree_batch(pb, unst, [n], depth, 1)
+    a, b = wl.random_alpha_beta(batch, 6, 1.0)
+    net, dom, db = _gpu(pb, props, batch)
+    lb = bc.bound(net, dom, db, _t(a), _t(b), bc.BF16).cpu().numpy().reshape(batch.B, pb.K)
+    assert bc.status(net) == 0 and batch.B == n
+    idx = np.sort(np.random.default_rng(0).choice(batch.B, size=n_check, replace=False))
+    sb, sa, sbeta = repack(pb, batch, [len(x) for x in unst], idx, a, b)
+    ref = O.bound(onet, props, sb, sa, sbeta).reshape(len(idx), pb.K)
+    err = np.abs(lb[idx] - ref) / _scale(ref)
+    print("%s full size, %d sampled subdomains: max err / median|lb| = %.3e" % (which, n_check, err.max()))
+    assert err.max() <= BF16_TOL
