@@ -73,16 +73,27 @@ def branching_scores(l, u):
 
 
 def _children(parent, j, K):
-    """The two subdomains of splitting neuron j: alpha inherited, beta of the new split 0."""
+    """The two subdomains of splitting neuron j: alpha inherited, beta of the new split 0.
+
+    The children share their parent's alpha and beta arrays: nothing writes them in place (a
+    bounding call replaces them with views of its own results)."""
     cnt = parent.depth
-    b = parent.beta.reshape(K, cnt)
-    beta = np.concatenate([b, np.zeros((K, 1), np.float32)], axis=1).reshape(-1)
-    splits = np.append(parent.splits, j).astype(np.int64)
-    kids = []
-    for sign in (-1, 1):
-        kids.append(Domain(splits, np.append(parent.signs, sign).astype(np.int8), parent.alpha.copy(),
-                           beta.copy(), parent.lb, parent.owner))
-    return kids
+    beta = np.zeros((K, cnt + 1), np.float32)
+    beta[:, :cnt] = parent.beta.reshape(K, cnt)
+    beta = beta.reshape(-1)
+    splits = np.append(parent.splits, j)
+    return [Domain(splits, np.append(parent.signs, np.int8(sign)), parent.alpha, beta, parent.lb, parent.owner)
+            for sign in (-1, 1)]
+
+
+def _next_neuron(d, order):
+    """The first neuron of the branching order that d has not split.  With the static order a
+    subdomain's splits are a prefix of it, so that is order[depth]; otherwise scan."""
+    if d.depth < len(order) and (d.depth == 0 or d.splits[-1] == order[d.depth - 1]) and \
+            int(order[d.depth]) not in d.splits[:d.depth]:
+        return int(order[d.depth])
+    used = set(d.splits.tolist())
+    return next((int(v) for v in order if int(v) not in used), None)
 
 
 def _margin_fn(problem):
@@ -221,8 +232,7 @@ def bab_many(engine, cases, batch_size=512, max_rounds=50, max_bounded=1_000_000
         for c in {d.owner for d in take}:
             res[c].rounds += 1
         for d in take:
-            used = set(d.splits.tolist())
-            j = next((int(v) for v in orders[d.owner] if int(v) not in used), None)
+            j = _next_neuron(d, orders[d.owner])
             if j is None:
                 exhausted.append(d)
                 continue

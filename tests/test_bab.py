@@ -103,7 +103,8 @@ def test_children_inherit_alpha_and_start_the_new_beta_at_zero():
         np.testing.assert_array_equal(k.alpha, parent.alpha)
         # beta layout [k][split]: the parent's two betas per spec, then 0 for the new split
         np.testing.assert_array_equal(k.beta.reshape(K, 3), [[1, 2, 0], [3, 4, 0], [5, 6, 0]])
-        assert k.alpha is not parent.alpha
+    # the parent is left as it was
+    assert parent.splits.tolist() == [7, 2] and parent.beta.tolist() == list(np.arange(K * 2) + 1.0)
 
 
 def test_branching_scores_rank_the_widest_relaxations_first():
