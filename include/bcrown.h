@@ -174,7 +174,8 @@ int bcrown_bound_grad(bcrown_net* net, const bcrown_domain* dom, const bcrown_ba
  * best lb and its theta, then steps uphill with lr0*decay^t, Adam moments
  * (beta1, beta2, eps) with bias correction, and clamps alpha to [0,1], beta to
  * >= 0.  At the end one BCROWN_CERTIFY pass (if certify != 0, else FP32) at the
- * best theta writes lb_out [B*K].  alpha, beta: in = initial values, out = best. */
+ * best theta writes lb_out [B*K].  alpha, beta: in = initial values (or, when
+ * resuming, the best theta so far), out = best. */
 typedef struct {
   int iters;
   float lr_alpha, lr_beta, decay;
@@ -183,9 +184,34 @@ typedef struct {
   int certify;   /* final pass: nonzero = BCROWN_CERTIFY, 0 = FP32 */
 } bcrown_opt_cfg;
 
+/* Optimiser state, for continuing an ascent across calls (checkpoint / resume, or a caller
+ * that keeps stepping the same batch).  Caller-owned FP32 device arrays in the batch's alpha
+ * and beta layouts, plus a host iteration counter:
+ *   alpha_cur [n_alpha], beta_cur [n_beta]   the current iterate theta_t (the next point evaluated)
+ *   m_alpha, v_alpha [n_alpha]; m_beta, v_beta [n_beta]   Adam's first and second moments
+ *   best_lb [B*K]                            best lb seen per row (-inf before any iteration)
+ *   t                                        iterations taken so far
+ * With t == 0 on entry the arrays are not read: the ascent starts at alpha, beta with zero
+ * moments.  With t > 0 they are read, alpha and beta must hold the best theta so far, and the
+ * learning rate and bias corrections continue from iteration t.  On return every array holds
+ * the state after the call and t has grown by cfg->iters.  The BF16 precision keeps alpha's
+ * moments in BF16 inside a call (they are rounded to BF16 on entry and widened on return), so
+ * a run split into several calls reproduces an uninterrupted run bit for bit in both precisions. */
+typedef struct {
+  float* alpha_cur;
+  float* beta_cur;
+  float* m_alpha;
+  float* v_alpha;
+  float* m_beta;
+  float* v_beta;
+  float* best_lb;
+  int t;
+} bcrown_opt_state;
+
+/* state may be NULL (a fresh ascent whose state is discarded). */
 int bcrown_optimize(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* batch,
                     const bcrown_opt_cfg* cfg, float* alpha, float* beta, float* lb_out,
-                    void* stream);
+                    bcrown_opt_state* state, void* stream);
 
 /* batch_split of Algorithm 1: parent b splits neuron (pick_layer[b], pick_idx[b]).
  * Child 2b is C^l (z >= 0, S = -1), child 2b+1 is C^u (z < 0, S = +1).  Each
@@ -229,14 +255,20 @@ int bcrown_profile_read(bcrown_net* net, int cls, double* total_ms, long long* l
 /* Number of kernels this library has launched in the process so far (all nets). */
 long long bcrown_kernel_launches(void);
 
+/* Peak-rate probe for the rooflines of the SIMT kernels (not part of the method): kind 0 runs
+ * independent FP32 FFMA chains, kind 1 FP64 DFMA chains, in 8 blocks of 256 threads per SM for
+ * `iters` x 128 FMAs per thread; the launch is timed with CUDA events on `stream` (the call
+ * synchronises it) and *tflops receives the measured rate, 2 flops per FMA. */
+int bcrown_peak_probe(int kind, int iters, double* tflops, void* stream);
+
 /* Size in bytes of the fixed device scratch of bcrown_bound_static (set when the library is built). */
 #define BCROWN_STATIC_SCRATCH_BYTES (16u << 20)
 
 /* bcrown_bound_static -- the FP32 bound pass of bcrown_bound (BCROWN_FP32), for callers that
  * cannot allocate device memory.  The paper has no counterpart: this entry point exists for
- * hosts that must not call cudaMalloc while the pass runs -- a program capturing the stream
- * into a CUDA graph, a real-time loop that cannot take cudaMalloc's implicit synchronisation,
- * a process confined to a device-memory budget handed out by its own allocator.
+ * hosts that must not call cudaMalloc while the pass runs -- a real-time loop that cannot take
+ * cudaMalloc's implicit synchronisation, a process confined to a device-memory budget handed
+ * out by its own allocator.
  *
  * It allocates nothing.  Its scratch (per-neuron tables and row-chunk buffers) is one
  * file-scope device array of BCROWN_STATIC_SCRATCH_BYTES bytes that every GPU loading the
@@ -247,7 +279,9 @@ long long bcrown_kernel_launches(void);
  * with BCROWN_ERR_ARG and a message naming the limit; larger batches are processed in row
  * chunks that fit.  Every call shares the one array and it keeps the last call's contents
  * (each call writes every part of it that it reads, so nothing needs clearing): calls that
- * overlap on the GPU -- on different streams, or from different host threads -- race. */
+ * overlap on the GPU -- on different streams, or from different host threads, on any net --
+ * race.  Like the other entry points it takes the net's lock while it enqueues.  Its kernels
+ * are left out of bcrown_profile's totals (recording them could create CUDA events). */
 int bcrown_bound_static(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* batch,
                         const float* alpha, const float* beta, float* lb, void* stream);
 

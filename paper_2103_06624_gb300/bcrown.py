@@ -197,13 +197,34 @@ class OptCfg:
                         self.adam_eps, self.precision, 1 if self.certify else 0)
 
 
-def optimize(net, dom, batch, alpha, beta, cfg=OptCfg(), out=None, stream=None):
-    """Runs the ascent; alpha, beta are overwritten with the per-row best values. Returns lb [B*K]."""
+class OptState:
+    """Adam state of an ascent (bcrown_opt_state): the current iterate, both moments of alpha and
+    beta (FP32, in the alpha/beta layouts), the best lb per row and the iteration count t."""
+
+    def __init__(self, batch, K):
+        def z(n):
+            return torch.zeros(max(int(n), 0), device="cuda", dtype=torch.float32)
+        self.alpha_cur, self.m_alpha, self.v_alpha = z(batch.n_alpha), z(batch.n_alpha), z(batch.n_alpha)
+        self.beta_cur, self.m_beta, self.v_beta = z(batch.n_beta), z(batch.n_beta), z(batch.n_beta)
+        self.best_lb = torch.full((batch.B * K,), -float("inf"), device="cuda")
+        self.t = 0
+
+    def c(self):
+        return N.OptState(_ptr(self.alpha_cur), _ptr(self.beta_cur), _ptr(self.m_alpha), _ptr(self.v_alpha),
+                          _ptr(self.m_beta), _ptr(self.v_beta), _ptr(self.best_lb), self.t)
+
+
+def optimize(net, dom, batch, alpha, beta, cfg=OptCfg(), out=None, stream=None, state=None):
+    """Runs the ascent; alpha, beta are overwritten with the per-row best values. Returns lb [B*K].
+    state (OptState, optional) is read when state.t > 0 and holds the state after the call."""
     lib = N.load()
     lb = out if out is not None else torch.empty(batch.B * net.K, device="cuda", dtype=torch.float32)
     d, b, cc = dom.c(), batch.c(), cfg.c()
+    st = state.c() if state is not None else None
     N.check(lib.bcrown_optimize(net.handle, C.byref(d), C.byref(b), C.byref(cc), _ptr(alpha), _ptr(beta),
-                                _ptr(lb), _stream(stream)))
+                                _ptr(lb), C.byref(st) if st is not None else None, _stream(stream)))
+    if state is not None:
+        state.t = st.t
     return lb
 
 
@@ -284,6 +305,13 @@ def profile_read(net, cls):
     n = C.c_longlong()
     N.check(N.load().bcrown_profile_read(net.handle, cls, C.byref(t), C.byref(n)))
     return t.value, n.value
+
+
+def peak_probe(kind, iters=2000, stream=None):
+    """Measured FP32 (kind 0) or FP64 (kind 1) FMA throughput of this GPU in TFLOP/s."""
+    t = C.c_double()
+    N.check(N.load().bcrown_peak_probe(kind, iters, C.byref(t), _stream(stream)))
+    return t.value
 
 
 def kernel_launches():

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libbcrown.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["net.cu", "simt.cu", "api.cu", "fused_tc.cu", "conv_tc.cu", "static_scratch.cu"]
+SOURCES = ["net.cu", "simt.cu", "api.cu", "fused_tc.cu", "conv_tc.cu", "static_scratch.cu", "probe.cu"]
 
 
 def nvcc():

@@ -309,7 +309,8 @@ extern "C" int bcrown_bound_grad(bcrown_net* net, const bcrown_domain* dom, cons
 }
 
 extern "C" int bcrown_optimize(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* batch,
-                               const bcrown_opt_cfg* cfg, float* alpha, float* beta, float* lb_out, void* stream) {
+                               const bcrown_opt_cfg* cfg, float* alpha, float* beta, float* lb_out,
+                               bcrown_opt_state* state, void* stream) {
   if (!net || !cfg) return fail(BCROWN_ERR_ARG, "optimize: null net or cfg");
   BC_CHECK(check_domain(net, dom));
   BC_CHECK(check_batch(batch));
@@ -318,6 +319,10 @@ extern "C" int bcrown_optimize(bcrown_net* net, const bcrown_domain* dom, const 
   if (batch->B == 0) return BCROWN_OK;
   if (!lb_out || (batch->n_alpha && !alpha) || (batch->n_beta && !beta))
     return fail(BCROWN_ERR_ARG, "optimize: null buffer");
+  if (state && state->t < 0) return fail(BCROWN_ERR_ARG, "optimize: negative state iteration count");
+  if (state && ((batch->n_alpha && (!state->alpha_cur || !state->m_alpha || !state->v_alpha)) ||
+                (batch->n_beta && (!state->beta_cur || !state->m_beta || !state->v_beta)) || !state->best_lb))
+    return fail(BCROWN_ERR_ARG, "optimize: state with a null array");
   std::lock_guard<std::mutex> g(net->mu);
   cudaStream_t s = (cudaStream_t)stream;
   const int R = batch->B * net->K;
@@ -329,45 +334,86 @@ extern "C" int bcrown_optimize(bcrown_net* net, const bcrown_domain* dom, const 
                      layer_tc_col(net, cfg->precision)));
   build_tables(net, dom, pl, s);
   if (cert) build_wm(net, dom, pl, s);
+  const bool fused16 = cfg->precision == BCROWN_BF16 && tc_supported(net);
+  // the BF16 path keeps alpha's gradient and moments in BF16 (the first half of each buffer)
+  __nv_bfloat16* ma16 = reinterpret_cast<__nv_bfloat16*>(pl.ma);
+  __nv_bfloat16* va16 = reinterpret_cast<__nv_bfloat16*>(pl.va);
+  const bool resume = state && state->t > 0;
+  const int t0 = state ? state->t : 0;
   if (na) {
-    BC_CUDA(cudaMemcpyAsync(pl.a_cur, alpha, na * 4, cudaMemcpyDeviceToDevice, s));
-    // the BF16 path keeps alpha's gradient and moments in BF16 (the first half of each buffer)
-    const size_t st = (cfg->precision == BCROWN_BF16 && tc_supported(net)) ? 2 : 4;
-    BC_CUDA(cudaMemsetAsync(pl.ma, 0, na * st, s));
-    BC_CUDA(cudaMemsetAsync(pl.va, 0, na * st, s));
+    const size_t st = fused16 ? 2 : 4;
+    BC_CUDA(cudaMemcpyAsync(pl.a_cur, resume ? state->alpha_cur : alpha, na * 4, cudaMemcpyDeviceToDevice, s));
+    if (resume && fused16) {
+      launch_f32_to_bf16(state->m_alpha, ma16, na, s);
+      launch_f32_to_bf16(state->v_alpha, va16, na, s);
+    } else if (resume) {
+      BC_CUDA(cudaMemcpyAsync(pl.ma, state->m_alpha, na * 4, cudaMemcpyDeviceToDevice, s));
+      BC_CUDA(cudaMemcpyAsync(pl.va, state->v_alpha, na * 4, cudaMemcpyDeviceToDevice, s));
+    } else {
+      BC_CUDA(cudaMemsetAsync(pl.ma, 0, na * st, s));
+      BC_CUDA(cudaMemsetAsync(pl.va, 0, na * st, s));
+    }
     BC_CUDA(cudaMemsetAsync(pl.ga, 0, na * st, s));
   }
   if (nb) {
-    BC_CUDA(cudaMemcpyAsync(pl.b_cur, beta, nb * 4, cudaMemcpyDeviceToDevice, s));
-    BC_CUDA(cudaMemsetAsync(pl.mb, 0, nb * 4, s));
-    BC_CUDA(cudaMemsetAsync(pl.vb, 0, nb * 4, s));
+    BC_CUDA(cudaMemcpyAsync(pl.b_cur, resume ? state->beta_cur : beta, nb * 4, cudaMemcpyDeviceToDevice, s));
+    if (resume) {
+      BC_CUDA(cudaMemcpyAsync(pl.mb, state->m_beta, nb * 4, cudaMemcpyDeviceToDevice, s));
+      BC_CUDA(cudaMemcpyAsync(pl.vb, state->v_beta, nb * 4, cudaMemcpyDeviceToDevice, s));
+    } else {
+      BC_CUDA(cudaMemsetAsync(pl.mb, 0, nb * 4, s));
+      BC_CUDA(cudaMemsetAsync(pl.vb, 0, nb * 4, s));
+    }
     BC_CUDA(cudaMemsetAsync(pl.gb, 0, nb * 4, s));
   }
-  launch_fill(pl.best_lb, R, -INFINITY, s);
+  if (resume)
+    BC_CUDA(cudaMemcpyAsync(pl.best_lb, state->best_lb, (size_t)R * 4, cudaMemcpyDeviceToDevice, s));
+  else
+    launch_fill(pl.best_lb, R, -INFINITY, s);
   BatchView bv = view_of(batch);
-  const bool fused16 = cfg->precision == BCROWN_BF16 && tc_supported(net);
-  for (int t = 0; t < cfg->iters; ++t) {
+  for (int it = 0; it < cfg->iters; ++it) {
+    const int t = t0 + it;   // iteration index of the whole ascent (learning-rate decay, bias correction)
     float fac = std::pow(cfg->decay, (float)t);
     float bc1 = 1.f - std::pow(cfg->adam_beta1, (float)(t + 1));
     float bc2 = 1.f - std::pow(cfg->adam_beta2, (float)(t + 1));
     if (fused16) {
       // BF16 path: gradient and Adam moments of alpha in BF16 (the FP32 buffers hold them)
       __nv_bfloat16* ga16 = reinterpret_cast<__nv_bfloat16*>(pl.ga);
-      BC_CHECK(tc_bound(net, dom, batch, pl.tb, pl.tc_ws, pl.tc_ws_bytes, true, t == 0, pl.a_cur, pl.b_cur, pl.lb_t,
+      BC_CHECK(tc_bound(net, dom, batch, pl.tb, pl.tc_ws, pl.tc_ws_bytes, true, it == 0, pl.a_cur, pl.b_cur, pl.lb_t,
                         nullptr, pl.gb, s, ga16));
       ProfScope ps(net, BCROWN_PROF_ADAM, s);
       launch_adam16(R, net->K, bv, pl.U, dom->n_props, pl.lb_t, pl.best_lb, pl.a_cur, alpha, ga16,
-                    reinterpret_cast<__nv_bfloat16*>(pl.ma), reinterpret_cast<__nv_bfloat16*>(pl.va), pl.b_cur, beta,
+                    ma16, va16, pl.b_cur, beta,
                     pl.gb, pl.mb, pl.vb, cfg->lr_alpha * fac, cfg->lr_beta * fac, cfg->adam_beta1, cfg->adam_beta2,
                     cfg->adam_eps, bc1, bc2, na, nb, s);
       continue;
     }
     BC_CHECK(run_bound(net, dom, batch, pl, cfg->precision, true, pl.a_cur, pl.b_cur, pl.lb_t, pl.ga, pl.gb, s,
-                       t == 0));
+                       it == 0));
     ProfScope ps(net, BCROWN_PROF_ADAM, s);
     launch_adam(R, net->K, bv, pl.U, dom->n_props, pl.lb_t, pl.best_lb, pl.a_cur, alpha, pl.ga, pl.ma, pl.va,
                 pl.b_cur, beta, pl.gb, pl.mb, pl.vb, cfg->lr_alpha * fac, cfg->lr_beta * fac, cfg->adam_beta1,
                 cfg->adam_beta2, cfg->adam_eps, bc1, bc2, na, nb, s);
+  }
+  if (state) {
+    // the state after this call's iterations, for the next call to continue from
+    if (na) {
+      BC_CUDA(cudaMemcpyAsync(state->alpha_cur, pl.a_cur, na * 4, cudaMemcpyDeviceToDevice, s));
+      if (fused16) {
+        launch_bf16_to_f32(ma16, state->m_alpha, na, s);
+        launch_bf16_to_f32(va16, state->v_alpha, na, s);
+      } else {
+        BC_CUDA(cudaMemcpyAsync(state->m_alpha, pl.ma, na * 4, cudaMemcpyDeviceToDevice, s));
+        BC_CUDA(cudaMemcpyAsync(state->v_alpha, pl.va, na * 4, cudaMemcpyDeviceToDevice, s));
+      }
+    }
+    if (nb) {
+      BC_CUDA(cudaMemcpyAsync(state->beta_cur, pl.b_cur, nb * 4, cudaMemcpyDeviceToDevice, s));
+      BC_CUDA(cudaMemcpyAsync(state->m_beta, pl.mb, nb * 4, cudaMemcpyDeviceToDevice, s));
+      BC_CUDA(cudaMemcpyAsync(state->v_beta, pl.vb, nb * 4, cudaMemcpyDeviceToDevice, s));
+    }
+    BC_CUDA(cudaMemcpyAsync(state->best_lb, pl.best_lb, (size_t)R * 4, cudaMemcpyDeviceToDevice, s));
+    state->t = t0 + cfg->iters;
   }
   BC_CHECK(run_bound(net, dom, batch, pl, cert ? BCROWN_CERTIFY : BCROWN_FP32, false, alpha, beta, lb_out, nullptr,
                      nullptr, s));

@@ -1638,6 +1638,22 @@ void launch_fill(float* p, long long n, float v, cudaStream_t s) {
   if (n > 0) { k_fill<<<grid1d(n, 256), 256, 0, s>>>(p, n, v); ++g_launches; }
 }
 
+// FP32 <-> BF16 copies (the BF16 optimiser keeps alpha's moments in BF16 inside a call).
+__global__ void k_f32_to_bf16(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = __float2bfloat16_rn(src[i]);
+}
+__global__ void k_bf16_to_f32(const __nv_bfloat16* __restrict__ src, float* __restrict__ dst, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = __bfloat162float(src[i]);
+}
+void launch_f32_to_bf16(const float* src, __nv_bfloat16* dst, long long n, cudaStream_t s) {
+  if (n > 0) { k_f32_to_bf16<<<grid1d(n, 256), 256, 0, s>>>(src, dst, n); ++g_launches; }
+}
+void launch_bf16_to_f32(const __nv_bfloat16* src, float* dst, long long n, cudaStream_t s) {
+  if (n > 0) { k_bf16_to_f32<<<grid1d(n, 256), 256, 0, s>>>(src, dst, n); ++g_launches; }
+}
+
 void launch_copy_count(int P, int H, const int32_t* U, int32_t* out, cudaStream_t s) {
   if (P > 0 && out) { k_count_unstable<<<grid1d(P, 128), 128, 0, s>>>(P, H, U, out); ++g_launches; }
 }

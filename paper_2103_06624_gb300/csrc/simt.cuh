@@ -49,6 +49,8 @@ void launch_concretize_root(bool cert, int q0, int Rc, int p, int d0, int d_top,
                             const float* x_lo, const float* x_hi, const float* A0, const float* cf, const double* cd,
                             const double* E, float* l, float* u, cudaStream_t s);
 void launch_fill(float* p, long long n, float v, cudaStream_t s);
+void launch_f32_to_bf16(const float* src, __nv_bfloat16* dst, long long n, cudaStream_t s);
+void launch_bf16_to_f32(const __nv_bfloat16* src, float* dst, long long n, cudaStream_t s);
 void launch_copy_count(int P, int H, const int32_t* U, int32_t* out, cudaStream_t s);
 
 }  // namespace bcrown

@@ -3,11 +3,10 @@
 // file-scope device array of fixed size instead of the net's cudaMalloc'd workspace.
 //
 // Who needs this: a host that must not call cudaMalloc while it runs this pass -- for example
-// a program that is capturing the stream into a CUDA graph and must keep allocation out of
-// the captured region, a real-time loop that cannot afford cudaMalloc's implicit device
-// synchronisation and latency, or an embedding process that runs under a fixed device-memory
-// budget handed out by its own allocator.  They pass inputs and outputs as usual; this entry
-// point allocates nothing.
+// a real-time loop that cannot afford cudaMalloc's implicit device synchronisation and
+// latency, or an embedding process that runs under a fixed device-memory budget handed out by
+// its own allocator and may not grow it behind that allocator's back.  They pass inputs and
+// outputs as usual; this entry point allocates nothing.
 #include <algorithm>
 #include <mutex>
 
@@ -79,6 +78,9 @@ extern "C" int bcrown_bound_static(bcrown_net* net, const bcrown_domain* dom, co
 
   void* base = nullptr;
   BC_CHECK(static_scratch_address(&base));
+  // the net's lock, as every other entry point takes it: calls on one net are serialised on
+  // the host (the net's status word is shared); the static array itself is shared by all nets
+  std::lock_guard<std::mutex> g(net->mu);
   cudaStream_t s = (cudaStream_t)stream;
   Arena ar{(char*)base};
   uint8_t* code = ar.take<uint8_t>(PH);
@@ -92,7 +94,8 @@ extern "C" int bcrown_bound_static(bcrown_net* net, const bcrown_domain* dom, co
   float* cf = ar.take<float>((size_t)Rc);
   if (ar.off > (size_t)BCROWN_STATIC_SCRATCH_BYTES) return fail(BCROWN_ERR_ARG, "bound_static: scratch plan overflow");
 
-  // Every buffer below is fully written before it is read, so nothing needs clearing.
+  // Every buffer below is fully written before it is read, so nothing needs clearing.  The
+  // kernels are not timed by bcrown_profile: its event pairs may have to be created.
   Tables tb;
   launch_tables(dom->n_props, net->H, dom->l, dom->u, tb, code, rank, slope, icpt, U, s);
   RowsCtx c;

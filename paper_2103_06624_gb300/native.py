@@ -20,7 +20,7 @@ MAX_SPLITS = 64
 EXPORTS = ["bcrown_load_net", "bcrown_free_net", "bcrown_net_info", "bcrown_root_bounds", "bcrown_bound",
            "bcrown_bound_grad", "bcrown_optimize", "bcrown_batch_split", "bcrown_neuron_codes",
            "bcrown_status", "bcrown_last_error", "bcrown_profile", "bcrown_profile_read",
-           "bcrown_kernel_launches", "bcrown_bound_static"]
+           "bcrown_kernel_launches", "bcrown_bound_static", "bcrown_peak_probe"]
 PROF_CONTRACT, PROF_RELAX, PROF_CONCRETIZE, PROF_ADJOINT, PROF_ADAM, PROF_FUSED = range(6)
 
 
@@ -48,6 +48,12 @@ class OptCfg(C.Structure):
                 ("precision", C.c_int), ("certify", C.c_int)]
 
 
+class OptState(C.Structure):
+    _fields_ = [("alpha_cur", C.c_void_p), ("beta_cur", C.c_void_p), ("m_alpha", C.c_void_p),
+                ("v_alpha", C.c_void_p), ("m_beta", C.c_void_p), ("v_beta", C.c_void_p),
+                ("best_lb", C.c_void_p), ("t", C.c_int)]
+
+
 class BcrownError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"bcrown error {code}: {msg}")
@@ -73,7 +79,8 @@ def load(path=LIB_PATH):
         "bcrown_root_bounds": ([vp, i32, vp, vp, i32, f32, i32, vp, vp, vp, vp], i32),
         "bcrown_bound": ([vp, C.POINTER(Domain), C.POINTER(Batch), vp, vp, i32, vp, vp], i32),
         "bcrown_bound_grad": ([vp, C.POINTER(Domain), C.POINTER(Batch), vp, vp, i32, vp, vp, vp, vp], i32),
-        "bcrown_optimize": ([vp, C.POINTER(Domain), C.POINTER(Batch), C.POINTER(OptCfg), vp, vp, vp, vp], i32),
+        "bcrown_optimize": ([vp, C.POINTER(Domain), C.POINTER(Batch), C.POINTER(OptCfg), vp, vp, vp,
+                             C.POINTER(OptState), vp], i32),
         "bcrown_batch_split": ([vp, C.POINTER(Domain), C.POINTER(Batch), vp, vp, vp, vp,
                                 vp, vp, vp, vp, vp, vp, vp, vp, vp, vp], i32),
         "bcrown_neuron_codes": ([vp, C.POINTER(Domain), C.POINTER(Batch), vp, vp], i32),
@@ -83,6 +90,7 @@ def load(path=LIB_PATH):
         "bcrown_profile_read": ([vp, i32, C.POINTER(C.c_double), C.POINTER(C.c_longlong)], i32),
         "bcrown_kernel_launches": ([], C.c_longlong),
         "bcrown_bound_static": ([vp, C.POINTER(Domain), C.POINTER(Batch), vp, vp, vp, vp], i32),
+        "bcrown_peak_probe": ([i32, i32, C.POINTER(C.c_double), vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)

@@ -40,3 +40,30 @@ def repack(pb, batch, U, idx, alpha, beta):
         b_parts.append(beta[o * K:(o + c) * K])
     nb = wl.pack_batch(pb.hidden_widths, K, U, subs)
     return nb, np.concatenate(a_parts) if a_parts else np.zeros(0), np.concatenate(b_parts) if b_parts else np.zeros(0)
+
+
+def grad_groups(net, batch, props):
+    """Hidden layer of every alpha and every beta entry (for per-layer gradient comparisons)."""
+    rows = O.expand_rows(net, batch, props["l"], props["u"])
+    la = np.zeros(batch.n_alpha, np.int64)
+    lb = np.zeros(batch.n_beta, np.int64)
+    for i in range(1, net.L):
+        ai = rows.alpha_idx[i]
+        la[ai[ai >= 0]] = i
+        bi = rows.beta_idx[i]
+        lb[bi[bi >= 0]] = i
+    return la, lb
+
+
+def grad_agreement(g, g_ref, layer, tol, floor=1e-2):
+    """Per hidden layer: the fraction of entries with |g - g_ref| <= tol (|g_ref| + floor * max |g_ref|)
+    (the max taken over the layer's entries), and the cosine of the layer's gradient vectors."""
+    out = {}
+    for i in np.unique(layer):
+        m = layer == i
+        gi, ri = np.asarray(g, np.float64)[m], np.asarray(g_ref, np.float64)[m]
+        sc = np.abs(ri).max(initial=0.0)
+        ok = np.abs(gi - ri) <= tol * (np.abs(ri) + floor * sc)
+        den = np.linalg.norm(gi) * np.linalg.norm(ri)
+        out[int(i)] = (float(ok.mean()) if ok.size else 1.0, float(gi @ ri / den) if den > 0 else 1.0, int(m.sum()))
+    return out

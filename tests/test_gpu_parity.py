@@ -154,9 +154,11 @@ def test_root_bounds_parity(maker):
     net = bc.load_net(pb.layers, pb.C)
     l, u, cnt = bc.root_bounds(net, _t(pb.x_lo), _t(pb.x_hi), bc.ALPHA_ADAPTIVE, 0.5, bc.FP32)
     l, u = l.cpu().numpy(), u.cpu().numpy()
+    # FP32 back-substitution against FP64, every layer at the 1e-5 bar (measured on a GB300: at
+    # most 1.2e-6 relative to max(|bound|, 1), on the deepest layer of the 784-256x6 net)
     scale = np.maximum(np.abs(l_ref), 1.0)
-    assert np.max(np.abs(l - l_ref) / scale) <= 1e-4
-    assert np.max(np.abs(u - u_ref) / np.maximum(np.abs(u_ref), 1.0)) <= 1e-4
+    assert np.max(np.abs(l - l_ref) / scale) <= RTOL
+    assert np.max(np.abs(u - u_ref) / np.maximum(np.abs(u_ref), 1.0)) <= RTOL
     assert np.array_equal(cnt.cpu().numpy(), ((l < 0) & (u > 0)).sum(axis=1))
     lc, uc, _ = bc.root_bounds(net, _t(pb.x_lo), _t(pb.x_hi), bc.ALPHA_ADAPTIVE, 0.5, bc.CERTIFY)
     lc, uc = lc.cpu().numpy(), uc.cpu().numpy()
@@ -223,9 +225,13 @@ def test_optimize_parity(which):
     a_best, b_best = at.cpu().numpy(), bt.cpu().numpy()
     ref_at_best = O.bound(onet, props, batch, a_best, b_best)
     assert np.all(lb <= ref_at_best + 1e-12 * np.abs(ref_at_best))
-    # stated certification gap (a priori FP32 contraction error terms): about 1e-4 on the
-    # 784-256x6 net, 1e-6 on the 16-32-32-4 net
-    assert np.max(rel_err(lb, ref_at_best)) <= 5e-4
+    # stated certification gap: the a priori FP32 contraction terms gamma_n |Lambda| |W| M
+    # (Higham, Accuracy and Stability of Numerical Algorithms, 3.1) are worst-case sums of
+    # magnitudes, several times |lb| on these nets; measured on a GB300: 1.02e-4 (784-256x6,
+    # 64 subdomains) and 7.7e-5 (16-32-32-4) of max(|lb|, 1)
+    gap = np.max(rel_err(lb, ref_at_best))
+    print("certified gap at the optimised alpha, beta (%s): %.3e" % (which, gap))
+    assert gap <= 2e-4
     init = O.bound(onet, props, batch, a0, b0)
     assert np.all(ref_at_best >= init - 1e-5 * np.maximum(np.abs(init), 1))
     ref_opt, _, _, _ = O.optimize(onet, props, batch, a0, b0)

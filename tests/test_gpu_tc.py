@@ -6,13 +6,35 @@ import torch
 from oracle import bcrown_oracle as O
 from paper_2103_06624_gb300 import bcrown as bc
 from paper_2103_06624_gb300 import workloads as wl
-from tests.helpers import RTOL, oracle_setup, rel_err, repack
+from tests.helpers import RTOL, grad_agreement, grad_groups, oracle_setup, rel_err, repack
 
 pytestmark = pytest.mark.gpu
 
-# BF16 operands (8-bit significand) with FP32 accumulation: the bound at fixed alpha, beta
-# moves by a few units of 2^-9 relative to the scale of the terms it sums.
-BF16_TOL = 3e-2
+# BF16 operands (8-bit significand) with FP32 accumulation: the bound at fixed alpha, beta moves by
+# a few units of 2^-9 relative to the scale of the terms it sums.  Tolerances are per network, about
+# 3x the largest error measured on a GB300 (max |lb - oracle| / median |oracle|):
+BF16_TOL = {
+    "mlp_small": 4.5e-2,      # measured 1.0e-2 and 1.4e-2 (16-32-32-4: bounds near 0, few terms per sum)
+    "mlp_784": 1.5e-3,        # measured 4.4e-4 (200 subdomains) and 4.9e-4 (the full 1024)
+    "mlp_784_mixed": 1.5e-3,  # measured 4.1e-4 (3 properties), 5.1e-4 (64 properties)
+    "tiny": 3.5e-2,           # measured 1.0e-2
+    "tiny_odd": 2e-2,         # measured 6.2e-3
+    "tiny_s3": 2e-2,          # measured 5.8e-3
+    "c3": 3e-3,               # conv_small: measured 7.9e-4 (24 subdomains), 1.0e-3 at full size
+    "conv_small": 3e-3,
+    "conv_big": 6e-5,         # measured 1.9e-5 at full size
+    "wide_mlp": 4.5e-2,       # measured 1.4e-2
+    "conv_limits": 1e-3,      # measured 3.0e-4
+}
+# BF16 gradients entry by entry, per hidden layer: the share of entries within GRAD_TOL of the
+# oracle's (relative to |g| plus 1 % of the layer's largest |g|), and the cosine between the layer's
+# gradient vectors.  BF16 rounding of x*, h and the stash moves zhat by a few 2^-9 of sum |W||h|,
+# which is large against |zhat| where zhat is near 0, and can flip a relaxation choice where A or
+# A^(0) is near 0: hence a share, not every entry.  Measured on a GB300 over every case below:
+# share >= 0.9365 (the first layer's dbeta of conv_small; 0.98 or more elsewhere) and cosine
+# >= 0.99891.  A zeroed or sign-flipped layer, or wrong entries on a few percent of the rows,
+# fails both.
+GRAD_TOL, GRAD_SHARE, GRAD_COS = 0.25, 0.9, 0.997
 
 
 def _t(x):
@@ -45,9 +67,9 @@ def test_bf16_bound_close_to_oracle(which):
     assert bc.status(net) == 0
     ref = O.bound(onet, props, batch, a, b)
     err = np.abs(lb - ref) / _scale(ref)
-    print("bf16 bound: max err / median|lb| = %.3e" % err.max())
+    print("bf16 bound %s: max err / median|lb| = %.3e" % (which, err.max()))
     assert np.all(np.isfinite(lb))
-    assert err.max() <= BF16_TOL
+    assert err.max() <= BF16_TOL["mlp_small" if which == "small" else "mlp_784"]
 
 
 def test_bf16_ragged_rows_and_multi_property():
@@ -64,7 +86,20 @@ def test_bf16_ragged_rows_and_multi_property():
     lb = bc.bound(net, dom, db, _t(a), _t(b), bc.BF16).cpu().numpy()
     ref = O.bound(onet, props, batch, a, b)
     assert bc.status(net) == 0
-    assert (np.abs(lb - ref) / _scale(ref)).max() <= BF16_TOL
+    err = (np.abs(lb - ref) / _scale(ref)).max()
+    print("bf16 bound ragged/multi-property: max err / median|lb| = %.3e" % err)
+    assert err <= BF16_TOL["mlp_784_mixed"]
+
+
+def _check_grad(pb, onet, props, batch, da, dbeta, da_ref, db_ref, tag):
+    """Entry-by-entry agreement of a BF16 gradient with the oracle's, per hidden layer."""
+    la, lb_ = grad_groups(onet, batch, props)
+    for kind, g, gr, lay in (("dalpha", da, da_ref, la), ("dbeta", dbeta, db_ref, lb_)):
+        for i, (share, cos, n) in grad_agreement(g, gr, lay, GRAD_TOL).items():
+            print("bf16 gradient %s %s layer %d: %d entries, share within tol %.4f, cosine %.6f"
+                  % (tag, kind, i, n, share, cos))
+            if n >= 20:
+                assert share >= GRAD_SHARE and cos >= GRAD_COS, (tag, kind, i, share, cos)
 
 
 @pytest.mark.parametrize("which", ["small", "784", "mixed"])
@@ -92,12 +127,9 @@ def test_bf16_gradient_close_to_oracle(which):
     lb, da, dbeta = bc.bound_grad(net, dom, db, _t(a), _t(b), bc.BF16)
     assert bc.status(net) == 0
     ref, da_ref, db_ref = O.grad(onet, props, batch, a.astype(np.float64), b.astype(np.float64))
-    assert (np.abs(lb.cpu().numpy() - ref) / _scale(ref)).max() <= BF16_TOL
-    for g, gr in ((da.cpu().numpy(), da_ref), (dbeta.cpu().numpy(), db_ref)):
-        # relative error of the gradient vector (BF16 rounding of x*, h and the stash)
-        rel = np.linalg.norm(g - gr) / max(np.linalg.norm(gr), 1e-12)
-        print("bf16 gradient relative error %.3e" % rel)
-        assert rel <= 5e-2
+    key = {"small": "mlp_small", "784": "mlp_784", "mixed": "mlp_784_mixed"}[which]
+    assert (np.abs(lb.cpu().numpy() - ref) / _scale(ref)).max() <= BF16_TOL[key]
+    _check_grad(pb, onet, props, batch, da.cpu().numpy(), dbeta.cpu().numpy(), da_ref, db_ref, which)
     lb_fp32, da32, db32 = bc.bound_grad(net, dom, db, _t(a), _t(b), bc.FP32)
     assert np.max(rel_err(lb_fp32.cpu().numpy(), ref)) <= RTOL
 
@@ -152,7 +184,9 @@ def test_batching_64_properties_sampled():
     lb16 = bc.bound(net, dom, db, _t(a), _t(b), bc.BF16).cpu().numpy()
     assert bc.status(net) == 0
     assert np.all(np.isfinite(lb16))
-    assert (np.abs(lb16[rows] - ref) / _scale(ref)).max() <= BF16_TOL
+    err = (np.abs(lb16[rows] - ref) / _scale(ref)).max()
+    print("bf16 batching workload: max err / median|lb| = %.3e" % err)
+    assert err <= BF16_TOL["mlp_784_mixed"]
     lb32 = bc.bound(net, dom, db, _t(a), _t(b), bc.FP32).cpu().numpy()
     assert np.max(rel_err(lb32[rows], ref)) <= RTOL
     a0, b0 = wl.initial_alpha_beta(batch)
@@ -196,15 +230,12 @@ def test_bf16_conv_bound_and_gradient_close_to_oracle(which):
     assert bc.status(net) == 0
     ref = O.bound(onet, props, batch, a, b)
     err = np.abs(lb - ref) / _scale(ref)
-    print("bf16 conv bound: max err / median|lb| = %.3e" % err.max())
-    assert err.max() <= BF16_TOL
+    print("bf16 conv bound %s: max err / median|lb| = %.3e" % (which, err.max()))
+    assert err.max() <= BF16_TOL[which]
     lbg, da, dbeta = bc.bound_grad(net, dom, db, _t(a), _t(b), bc.BF16)
     assert bc.status(net) == 0
     ref_g, da_ref, db_ref = O.grad(onet, props, batch, a.astype(np.float64), b.astype(np.float64))
-    for g, gr in ((da.cpu().numpy(), da_ref), (dbeta.cpu().numpy(), db_ref)):
-        rel = np.linalg.norm(g - gr) / max(np.linalg.norm(gr), 1e-12)
-        print("bf16 conv gradient relative error %.3e" % rel)
-        assert rel <= 5e-2
+    _check_grad(pb, onet, props, batch, da.cpu().numpy(), dbeta.cpu().numpy(), da_ref, db_ref, "conv " + which)
 
 
 def test_bf16_conv_optimize_is_certified():
@@ -237,13 +268,11 @@ def test_bf16_wide_mlp_runs_every_contraction_as_a_tensor_core_gemm():
     ref = O.bound(onet, props, batch, a, b)
     err = np.abs(lb - ref) / _scale(ref)
     print("bf16 wide mlp bound: max err / median|lb| = %.3e" % err.max())
-    assert err.max() <= BF16_TOL
+    assert err.max() <= BF16_TOL["wide_mlp"]
     _, da, dbeta = bc.bound_grad(net, dom, db, _t(a), _t(b), bc.BF16)
     assert bc.status(net) == 0
     _, da_ref, db_ref = O.grad(onet, props, batch, a.astype(np.float64), b.astype(np.float64))
-    for g, gr in ((da.cpu().numpy(), da_ref), (dbeta.cpu().numpy(), db_ref)):
-        rel = np.linalg.norm(g - gr) / max(np.linalg.norm(gr), 1e-12)
-        assert rel <= 5e-2
+    _check_grad(pb, onet, props, batch, da.cpu().numpy(), dbeta.cpu().numpy(), da_ref, db_ref, "wide mlp")
     a0, b0 = wl.initial_alpha_beta(batch)
     at, bt = _t(a0), _t(b0)
     lbc = bc.optimize(net, dom, db, at, bt, bc.OptCfg(precision=bc.BF16, certify=True)).cpu().numpy()
@@ -274,7 +303,7 @@ def test_bf16_conv_im2col_buffer_path_matches_oracle():
         "    lb = bc.bound(net, dom, db, _t(a), _t(b), bc.BF16).cpu().numpy()\n"
         "    assert bc.status(net) == 0\n"
         "    ref = O.bound(onet, props, batch, a, b)\n"
-        "    assert (np.abs(lb - ref) / _scale(ref)).max() <= BF16_TOL, which\n"
+        "    assert (np.abs(lb - ref) / _scale(ref)).max() <= BF16_TOL[which], which\n"
         "print('ok')\n")
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     env = dict(os.environ, BCROWN_CONV_IM2COL="1")
@@ -302,11 +331,10 @@ def test_bf16_conv_at_the_size_limits_matches_oracle():
     ref = O.bound(onet, props, batch, a, b)
     err = np.abs(lb - ref) / _scale(ref)
     print("bf16 conv at the limits: max err / median|lb| = %.3e" % err.max())
-    assert err.max() <= BF16_TOL
-    _, da, _ = bc.bound_grad(net, dom, db, _t(a), _t(b), bc.BF16)
-    _, da_ref, _ = O.grad(onet, props, batch, a.astype(np.float64), b.astype(np.float64))
-    rel = np.linalg.norm(da.cpu().numpy() - da_ref) / max(np.linalg.norm(da_ref), 1e-12)
-    assert rel <= 5e-2
+    assert err.max() <= BF16_TOL["conv_limits"]
+    _, da, dbeta = bc.bound_grad(net, dom, db, _t(a), _t(b), bc.BF16)
+    _, da_ref, db_ref = O.grad(onet, props, batch, a.astype(np.float64), b.astype(np.float64))
+    _check_grad(pb, onet, props, batch, da.cpu().numpy(), dbeta.cpu().numpy(), da_ref, db_ref, "conv limits")
 
 
 def test_bf16_conv_beyond_the_channel_limit_is_refused():
@@ -352,4 +380,4 @@ def test_bf16_conv_full_size_sampled(which):
     ref = O.bound(onet, props, sb, sa, sbeta).reshape(len(idx), pb.K)
     err = np.abs(lb[idx] - ref) / _scale(ref)
     print("%s full size, %d sampled subdomains: max err / median|lb| = %.3e" % (which, n_check, err.max()))
-    assert err.max() <= BF16_TOL
+    assert err.max() <= BF16_TOL[which]

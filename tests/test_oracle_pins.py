@@ -394,3 +394,127 @@ def test_split_children_cover_the_parent():
             p = LP.exact_min(*args, parent, k)
             c = [LP.exact_min(*args, parent + [(i, j, s)], k) for s in (-1, 1)]
             np.testing.assert_allclose(p, min(c), rtol=1e-9, atol=1e-12)
+
+
+# ------------------------------------------------------------------ root bounds beyond layer 1
+
+def _truncated(pb, i, props):
+    """The network cut after layer i with C = [I; -I] (2 d_i specs: +z_j and -z_j), and the
+    properties restricted to the hidden layers below i."""
+    d = pb.layers[i - 1].d_out
+    C = np.concatenate([np.eye(d), -np.eye(d)]).astype(np.float32)
+    tnet = O.OracleNet(pb.layers[:i], C)
+    h = int(sum(pb.hidden_widths[:i - 1]))
+    tprops = dict(x_lo=pb.x_lo, x_hi=pb.x_hi, l=props["l"][:, :h], u=props["u"][:, :h])
+    return tnet, tprops, d
+
+
+def _relaxation_gap_area(alpha, l, u, n=4001):
+    """Area between ReLU and the lower line alpha * z over [l, u] (trapezoid rule)."""
+    z = np.linspace(l, u, n)
+    return np.trapezoid(np.maximum(z, 0.0) - alpha * z, z)
+
+
+@pytest.mark.parametrize("maker", [lambda: tiny_problem(widths=(3, 6, 6, 5, 3), eps=0.3), tiny_conv_problem])
+def test_root_bounds_equal_the_dual_form_on_the_truncated_net(maker):
+    """Layer i >= 2 root bounds are CROWN's: on the net cut after layer i with the specs +-e_j,
+    the dual objective of Theorem 3.2 at beta = 0 and the same lower slopes alpha' gives l_j and
+    -u_j (the dual form is a second formula, not the back-substitution loop of root_bounds).
+    FIXED rules use alpha' = v everywhere; the ADAPTIVE rule's alpha' is recomputed here as the
+    lower line (z or 0) whose gap to ReLU over [l, u] has the smaller area."""
+    pb = maker()
+    net = O.OracleNet(pb.layers, pb.C)
+    for rule, value in ((O.ALPHA_FIXED, 0.0), (O.ALPHA_FIXED, 0.3), (O.ALPHA_FIXED, 1.0), (O.ALPHA_ADAPTIVE, 0.5)):
+        l, u = O.root_bounds(net, pb.x_lo, pb.x_hi, rule, value)
+        props = dict(x_lo=pb.x_lo, x_hi=pb.x_hi, l=l, u=u)
+        for i in range(2, net.L):
+            tnet, tprops, d = _truncated(pb, i, props)
+            _, U = O.unstable_ranks(tnet, tprops["l"], tprops["u"])
+            unst = [np.nonzero(O.unstable_mask(tprops["l"][p], tprops["u"][p]))[0] for p in range(pb.P)]
+            subs = [(p, np.zeros(0, np.int64), np.zeros(0, np.int8)) for p in range(pb.P)]
+            batch = wl.pack_batch(pb.hidden_widths[:i - 1], 2 * d, U, subs)
+            alpha = np.zeros(batch.n_alpha)
+            for p in range(pb.P):
+                if rule == O.ALPHA_FIXED:
+                    ap = np.full(len(unst[p]), value)
+                else:
+                    ap = np.array([1.0 if _relaxation_gap_area(1.0, tprops["l"][p, j], tprops["u"][p, j])
+                                   <= _relaxation_gap_area(0.0, tprops["l"][p, j], tprops["u"][p, j]) else 0.0
+                                   for j in unst[p]])
+                off = int(batch.alpha_off[p])
+                alpha[off:off + 2 * d * len(ap)] = np.tile(ap, 2 * d)
+            g = O.bound_dual(tnet, tprops, batch, alpha, np.zeros(0)).reshape(pb.P, 2 * d)
+            lo, hi = net.hoff[i - 1], net.hoff[i]
+            np.testing.assert_allclose(g[:, :d], l[:, lo:hi], rtol=1e-10, atol=1e-10)
+            np.testing.assert_allclose(-g[:, d:], u[:, lo:hi], rtol=1e-10, atol=1e-10)
+
+
+def test_root_bounds_contain_the_exact_range_and_lie_below_the_lp():
+    """Every root bound is sound and no tighter than the LP relaxation allows: on a tiny net,
+    l_j <= p*_LP(z_j) <= min z_j (exact, by activation patterns) and u_j >= the matching maxima,
+    for every neuron of layers 2 and 3 (Corollary 3.1 applied to the truncated net)."""
+    pb = tiny_problem(widths=(3, 5, 5, 4, 2), eps=0.3)
+    net, props, _ = _setup(pb)
+    l, u = props["l"], props["u"]
+    for i in range(2, net.L):
+        tnet, tprops, d = _truncated(pb, i, props)
+        lo = net.hoff[i - 1]
+        args = (tnet, pb.x_lo[0].astype(np.float64), pb.x_hi[0].astype(np.float64), tprops["l"][0], tprops["u"][0], [])
+        for j in range(d):
+            zmin = LP.exact_min(*args, j)
+            zmax = -LP.exact_min(*args, d + j)
+            pmin = LP.lp_value(*args, j)
+            pmax = -LP.lp_value(*args, d + j)
+            assert l[0, lo + j] <= pmin + 1e-9 and pmin <= zmin + 1e-9
+            assert u[0, lo + j] >= pmax - 1e-9 and pmax >= zmax - 1e-9
+            assert zmin <= zmax + 1e-12
+
+
+# ------------------------------------------------------------------ neuron codes
+
+def test_neuron_codes_hand_derived_cases():
+    """Codes for hand-picked l, u (boundaries l = 0, u = 0, l = u = 0) and split lists, including
+    splits on stable neurons, written out by hand in tests/golden/neuron_codes_cases.json."""
+    g = json.load(open(os.path.join(GOLD, "neuron_codes_cases.json")))
+    H = len(g["l"])
+    layers = wl.mlp_layers([3, H, 2], 0)
+    net = O.OracleNet(layers, np.eye(2, dtype=np.float32)[:1])
+    l = np.array([g["l"]], np.float64)
+    u = np.array([g["u"]], np.float64)
+    _, U = O.unstable_ranks(net, l, u)
+    subs = [(0, np.array([s[0] for s in r["splits"]], np.int64), np.array([s[1] for s in r["splits"]], np.int8))
+            for r in g["rows"]]
+    batch = wl.pack_batch([H], 1, U, subs)
+    rows = O.expand_rows(net, batch, l, u)
+    codes = O.neuron_codes(net, rows, l, u)[1]
+    assert np.array_equal(codes, np.array([r["codes"] for r in g["rows"]], np.int8))
+
+
+def test_neuron_codes_agree_with_the_relaxation():
+    """The code of each (row, neuron) matches the slope the relaxation applies: D = 1 and no
+    intercept for codes 1 and 3, D = 0 and no intercept for 0 and 4, and alpha (A >= 0) or the
+    upper chord (A < 0) for code 2."""
+    pb = wl.problem_mlp_small(seed=2)
+    net, props, unst = _setup(pb)
+    batch = wl.random_batch(pb, unst, 20, 0, 4, 9)
+    a, _ = wl.random_alpha_beta(batch, 1)
+    rows = O.expand_rows(net, batch, props["l"], props["u"])
+    codes = O.neuron_codes(net, rows, props["l"], props["u"])
+    rng = np.random.default_rng(0)
+    for i in range(1, net.L):
+        lo, hi = net.hoff[i - 1], net.hoff[i]
+        li, ui = props["l"][rows.prop][:, lo:hi], props["u"][rows.prop][:, lo:hi]
+        al = np.where(rows.alpha_idx[i] >= 0, a[np.maximum(rows.alpha_idx[i], 0)], 0.0)
+        A = rng.normal(size=li.shape)
+        D, lam = O.relax(A, li, ui, al, rows.sign[i])
+        c = codes[i]
+        one = (c == 1) | (c == 3)
+        zero = (c == 0) | (c == 4)
+        assert np.all(D[one] == 1.0) and np.all(lam[one] == 0.0)
+        assert np.all(D[zero] == 0.0) and np.all(lam[zero] == 0.0)
+        two = c == 2
+        assert np.all(np.where(two & (A >= 0), D == al, True))
+        chord = ui / np.where(two, ui - li, 1.0)
+        assert np.all(np.where(two & (A < 0), np.isclose(D, chord, rtol=1e-15), True))
+        assert np.all(np.where(two & (A < 0), lam > 0, True))
+        assert np.all((c == 2).sum(axis=1) <= len(unst[0]))
