@@ -2,13 +2,16 @@
 
 One step = one call of bcrown_optimize on a batch of subdomains: 20 projected-
 Adam iterations on alpha, beta (each a bound pass plus its adjoint) and the
-final certifying pass.  Workload (default, --workload mlp784): the ReLU MLP
-784-256x6-10 (He init, seeded), x0 ~ U[0,1]^784, eps = 0.015, 9 margin specs,
-1024 subdomains that are the leaves of a random branch-and-bound tree of depth
-<= 12.  Other workloads (--workload): batching (the same net, 64 properties
-with log-uniform 16-4096 subdomains each, depth <= 20), conv_small and
-conv_big (the two CIFAR-shaped conv nets, 2048 and 4096 subdomains, depth <= 16
-and 24).
+final certifying pass.  Workload (default, --workload conv_big, the largest
+single-GPU configuration): the CIFAR-shaped conv net 3x32x32 -> conv
+64,64,128,128 (3x3, strides 1,2,1,2) -> fc 8192-512-10 (He init, seeded),
+eps = 2/255, 9 margin specs, 4096 subdomains that are the leaves of a random
+branch-and-bound tree of depth <= 24; BF16 iterations and an FP32 certifying
+pass.  Other workloads (--workload): mlp784 (the ReLU MLP 784-256x6-10,
+x0 ~ U[0,1]^784, eps = 0.015, 1024 subdomains, depth <= 12), batching (the same
+MLP, 64 properties with log-uniform 16-4096 subdomains each, depth <= 20) and
+conv_small (3x32x32 -> conv 32,64 (4x4, stride 2) -> fc 4096-512-512-10, 2048
+subdomains, depth <= 16).
 
 Prints one JSON line (rank 0).  Under torchrun each rank bounds its own batch
 (weak scaling, no collective on the data path); the barrier and the maximum
@@ -41,10 +44,14 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
-    ap.add_argument("--workload", default="mlp784", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="conv_big", choices=sorted(WORKLOADS))
     ap.add_argument("--subdomains", type=int, default=None, help="per property (default: the workload's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32-form", action="store_true", help="skip timing the plain FP32 form beside BF16")
+    ap.add_argument("--fp32-steps", type=int, default=10, help="timed steps of the plain FP32 form")
+    ap.add_argument("--no-autotune", action="store_true", help="skip the launch-configuration tuner")
+    ap.add_argument("--no-graph", action="store_true", help="launch the timed steps eagerly instead of replaying "
+                                                             "one captured CUDA graph")
     ap.add_argument("--profile-timed", action="store_true",
                     help="open a CUDA profiler range around the timed steps only (ncu --profile-from-start off)")
     ap.add_argument("--cpu-sample", type=int, default=None,
@@ -62,14 +69,16 @@ def parse():
 
 # subdomains: per property (batching: the upper end of the log-uniform range is fixed instead)
 WORKLOADS = {
-    "mlp784": {"subdomains": 1024, "depth": 12, "cpu_sample": 640,
+# cpu_sample: subdomains of the oracle leg of our arm (about 10-25 s); ref_sample: subdomains per
+# step of the --impl reference arm (so that 25 steps end within a few minutes)
+    "mlp784": {"subdomains": 1024, "depth": 12, "cpu_sample": 640, "ref_sample": 256,
                "desc": "mlp_784_256x6_10 eps=0.015, {n} BaB-tree subdomains (depth<=12), 9 specs"},
-    "batching": {"subdomains": None, "depth": 20, "cpu_sample": 640,
+    "batching": {"subdomains": None, "depth": 20, "cpu_sample": 640, "ref_sample": 256,
                  "desc": "mlp_784_256x6_10 eps=0.015, 64 properties x log-uniform 16-4096 BaB-tree subdomains "
                          "({n} in all, depth<=20), 9 specs"},
-    "conv_small": {"subdomains": 2048, "depth": 16, "cpu_sample": 16,
+    "conv_small": {"subdomains": 2048, "depth": 16, "cpu_sample": 16, "ref_sample": 8,
                    "desc": "conv_3x32x32_c32_c64_fc512_512_10 eps=2/255, {n} BaB-tree subdomains (depth<=16), 9 specs"},
-    "conv_big": {"subdomains": 4096, "depth": 24, "cpu_sample": 2,
+    "conv_big": {"subdomains": 4096, "depth": 24, "cpu_sample": 2, "ref_sample": 1,
                  "desc": "conv_3x32x32_c64_c64_c128_c128_fc512_10 eps=2/255, {n} BaB-tree subdomains (depth<=24), "
                          "9 specs"},
 }
@@ -102,15 +111,6 @@ def build_workload(workload, seed, n_sub, torch, bc, wl):
     batch = make_batch(workload, pb, unst, n_sub, seed, wl)
     dom = bc.Domain(x_lo, x_hi, l, u)
     return pb, net, dom, batch, unst, (l_h, u_h)
-
-
-def layer_path_bytes_per_row_iter(pb, U, depth):
-    """Algorithmic bytes of one row and one iteration on the layer-by-layer path: the alpha,
-    Adam m and v state (read + write, FP32), the beta state, the split list, the stash of A at
-    the unstable neurons, lb, and the conv layers' outputs materialised once per direction in
-    BF16 (written and read back)."""
-    conv_out = sum(int(np.prod(ly.out_shape)) for ly in pb.layers[:-1] if ly.kind == "conv")
-    return 24 * U + 24 * depth + 6 * depth + 8 * U + 4 + conv_out * 2 * 2 * 2
 
 
 class Clocks:
@@ -165,9 +165,29 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def algorithmic_flops_per_row_pass(widths):
-    """FLOPs of one backward pass of one row: sum over layers i = 1..L-1 of 2 d_i d_{i-1}."""
-    return sum(2 * widths[i] * widths[i - 1] for i in range(1, len(widths) - 1))
+def algorithmic_flops_per_row_pass(layers):
+    """FLOPs of one backward pass of one row: the contractions of layers 1..L-1 (the last layer is
+    merged with the specification into the top of the recursion): 2 d_i d_{i-1} for a fully
+    connected layer, 2 C_out H_out W_out C_in k^2 for a convolution (no work on the zero padding)."""
+    f = 0
+    for ly in layers[:-1]:
+        if ly.kind == "conv":
+            cout, ho, wo = ly.out_shape
+            f += 2 * cout * ho * wo * ly.in_shape[0] * ly.k * ly.k
+        else:
+            f += 2 * ly.d_out * ly.d_in
+    return f
+
+
+def layer_gemm_bytes_per_row_iter(pb, U, depth):
+    """Algorithmic bytes of the BF16 layer path's GEMM launches for one row and one iteration:
+    every hidden layer's Lambda (backward) and h (forward) written once and read once in BF16, x*
+    written and read once (BF16), A at the unstable neurons stashed and read back (BF16), alpha
+    read in both passes (FP32) and its gradient written (FP32), beta read and its gradient written
+    (FP32), per split."""
+    hidden = sum(int(np.prod(ly.out_shape)) for ly in pb.layers[:-1])
+    d0 = int(np.prod(pb.layers[0].in_shape))
+    return 8 * hidden + 4 * d0 + U * (2 + 2 + 4 + 4 + 4) + depth * 8
 
 
 def fp32_simt_peak_tflops(sm_mhz):
@@ -274,6 +294,20 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, device="cuda")
     stream = torch.cuda.current_stream()
 
+    # ---------------------------------------------------------------- launch configuration
+    # the tuner times every BF16 path (and grid) the net can take on this batch, outside the
+    # timed region, and keeps the fastest for the batch's row-count bucket
+    launch = None
+    if prec == bc.BF16:
+        if not args.no_autotune:
+            best, cands = bc.autotune(net, dom, db, a_init, b_init, reps=2)
+            launch = {"path": bc.N.PATH_NAMES[best[0]], "grid_per_sm": best[1], "chosen_by": "autotune",
+                      "candidates_ms_per_bound_grad": {"%s/%d" % (bc.N.PATH_NAMES[c[0]], c[1]): ms
+                                                       for c, ms in cands}}
+        else:
+            p_, g_ = bc.get_launch(net, hbatch.B * pb.K)
+            launch = {"path": bc.N.PATH_NAMES[p_], "grid_per_sm": g_, "chosen_by": "built-in order"}
+
     def step():
         alpha.copy_(a_init)
         beta.copy_(b_init)
@@ -282,11 +316,24 @@ def main():
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    # one step captured into a CUDA graph (with the profiling scopes as event nodes), replayed
+    # once per timed step; the first call above made every allocation and table the step needs
+    bc.profile(net, True)
+    launches0 = bc.kernel_launches()
+    graph = None
+    if not args.no_graph:
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step()
+        torch.cuda.synchronize()
+        launches_per_step = bc.kernel_launches() - launches0
+        graph.replay()                             # untimed first replay
+        torch.cuda.synchronize()
+    run = graph.replay if graph is not None else step
     if world > 1:
         dist.barrier()
     clocks = Clocks(local)
     clocks.start()
-    bc.profile(net, True)
     launches0 = bc.kernel_launches()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     torch.cuda.synchronize()
@@ -295,15 +342,17 @@ def main():
     for i in range(args.steps):
         flush.fill_(float(i))                      # write 256 MB > L2 between timed steps
         ev[i][0].record(stream)
-        step()
+        run()
         ev[i][1].record(stream)
     torch.cuda.synchronize()
     if args.profile_timed:
         torch.cuda.profiler.stop()
-    launches = bc.kernel_launches() - launches0
+    launches = launches_per_step * args.steps if graph is not None else bc.kernel_launches() - launches0
     clk = clocks.stop()
-    prof = {c: bc.profile_read(net, c) for c in range(6)}
+    prof = {c: bc.profile_read(net, c) for c in range(7)}
     bc.profile(net, False)
+    # with the graph, the profile holds the latest replay: one step (eager: every timed step)
+    prof_steps = 1 if graph is not None else args.steps
     t_ms = sum(a.elapsed_time(b) for a, b in ev)
     if world > 1:
         tt = torch.tensor([t_ms], device="cuda")
@@ -313,6 +362,14 @@ def main():
     units = hbatch.B * world
     value = units / (ms_per_step / 1e3)
     assert bc.status(net) == 0, "device status reported an error"
+
+    # ---------------------------------------------------------------- root bounds, once per property
+    # (outside the timed step: bcrown_root_bounds in the certified precision the step uses)
+    rb_ms = time_root_bounds(bc, torch, net, dom, pb.P)
+
+    # ---------------------------------------------------------------- measured FP32 / FP64 peaks
+    probes = {"fp32_tflops": bc.peak_probe(0), "fp64_tflops": bc.peak_probe(1, iters=200),
+              "how": "bcrown_peak_probe: independent FMA chains, 8 x 256 threads per SM, CUDA events"}
 
     # ---------------------------------------------------------------- end to end (host buffers)
     e2e = measure_e2e(args, bc, torch, net, dom, hbatch, a0, b0, cfg, pb, world)
@@ -331,20 +388,21 @@ def main():
             beta.copy_(b_init)
             bc.optimize(net, dom, db, alpha, beta, cfg32, out=lb32)
 
-        step32()
-        torch.cuda.synchronize()
-        n32 = 2
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        flush.fill_(0.0)
-        e0.record(stream)
-        for _ in range(n32):
+        for _ in range(3):
             step32()
-        e1.record(stream)
         torch.cuda.synchronize()
-        ms32 = e0.elapsed_time(e1) / n32
+        n32 = max(1, args.fp32_steps)
+        ev32 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n32)]
+        for i in range(n32):
+            flush.fill_(float(i))                  # L2 flushed before every timed FP32 step
+            ev32[i][0].record(stream)
+            step32()
+            ev32[i][1].record(stream)
+        torch.cuda.synchronize()
+        ms32 = sum(a.elapsed_time(b) for a, b in ev32) / n32
         d = (lb_main - lb32).double().cpu().numpy()
         forms = {"fp32": {"value": hbatch.B * world / (ms32 / 1e3), "unit": UNIT, "ms_per_step": ms32,
-                          "steps": n32},
+                          "steps": n32, "warmup": 3, "l2": "flushed before every step"},
                  "bf16_over_fp32": (ms32 / ms_per_step),
                  "certified_lb_bf16_minus_fp32": {"mean": float(d.mean()), "min": float(d.min()),
                                                   "max": float(d.max())},
@@ -353,7 +411,7 @@ def main():
     # ---------------------------------------------------------------- roofline of the dominant kernel
     widths = pb.widths
     rows = hbatch.B * pb.K
-    f_row = algorithmic_flops_per_row_pass(widths)
+    f_row = algorithmic_flops_per_row_pass(pb.layers)
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     sm_mhz = clk.get("sm_mhz") or 1432.0
@@ -376,41 +434,61 @@ def main():
                                "splits (beta read, dbeta write) + 4 B (lb)",
                 "tensor_tflops": tflops, "tensor_frac": tflops / tpeak,
                 "tensor_peak_source": "of measured (MEASURED_PEAKS.json bf16_tflops_sustained)",
-                "kernel_ms_per_step": ms / args.steps, "launches_per_step": nl / args.steps,
-                "step_ms_by_class": {n: prof[c][0] / args.steps for c, n in enumerate(
-                    ["contract", "relax", "concretize", "adjoint", "adam", "fused"])}}
+                "kernel_ms_per_step": ms / prof_steps, "launches_per_step": nl / prof_steps,
+                "step_ms_by_class": {n: prof[c][0] / prof_steps for c, n in enumerate(
+                    ["contract", "relax", "concretize", "adjoint", "adam", "fused", "layer_gemm"])}}
         # the record was taken on the default workload at its default size
         tr = measured_traffic("k_fused_grad", bytes_per_launch) if (args.workload, args.subdomains) == (
             "mlp784", WORKLOADS["mlp784"]["subdomains"]) else None
         if tr is not None:
             roof["traffic"] = tr["dram_bytes_per_launch"]
             roof["traffic_note"] = tr
-    elif prec == bc.BF16:
-        # layer-by-layer BF16 path (conv nets): the whole step against the HBM roofline, bytes
-        # from the per-row model (the certifying pass is left out of the algorithmic bytes)
+    elif prec == bc.BF16 and prof[6][1] > 0:
+        # BF16 layer path (conv nets): its tcgen05 GEMM launches with fused epilogues (both passes
+        # of every iteration), against the HBM roofline (bytes of the model below) and the tensor
+        # roofline (the contractions' algorithmic flops); the bound is the larger fraction
+        ms, nl = prof[6]
         U = np.array([len(u) for u in unst])[hbatch.prop_of].astype(np.float64)
-        per_row = layer_path_bytes_per_row_iter(pb, U, hbatch.split_cnt.astype(np.float64))
-        bytes_per_step = float(np.sum(per_row)) * pb.K * cfg.iters
-        achieved = bytes_per_step / (ms_per_step / 1e3) / 1e9
-        peak = peaks.get("hbm_gbs_sustained", peaks.get("hbm_gbs", 6800.0))
-        roof = {"bound": "hbm", "kernel": "whole step (layer path: k_im2col + k_tcg tcgen05 GEMMs, k_relax, "
-                                          "k_fwd_epi, k_adam; FP32 certifying pass)",
-                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": "of measured (MEASURED_PEAKS.json)",
-                "algorithmic_bytes_per_step": bytes_per_step,
-                "bytes_model": "per row and iteration: 24 B x unstable (alpha, m, v) + 30 B x splits + 8 B x unstable "
-                               "(stash) + 4 B + 8 B x conv outputs (BF16 written and read, both directions)",
-                "step_ms_by_class": {n: prof[c][0] / args.steps for c, n in enumerate(
-                    ["contract", "relax", "concretize", "adjoint", "adam", "fused"])}}
+        per_row = layer_gemm_bytes_per_row_iter(pb, U, hbatch.split_cnt.astype(np.float64))
+        bytes_all = float(np.sum(per_row)) * pb.K * cfg.iters * prof_steps
+        flops_all = float(rows) * 2 * f_row * cfg.iters * prof_steps
+        gbs = bytes_all / (ms / 1e3) / 1e9
+        tfl = flops_all / (ms / 1e3) / 1e12
+        peak = peaks.get("hbm_gbs", 6800.0)
+        tpeak = peaks.get("bf16_tflops_sustained", 1700.0)
+        hbm_frac, ten_frac = gbs / peak, tfl / tpeak
+        if launch and launch["path"] == "layer_epi":
+            kern = ("k_lt (tcgen05 GEMMs of the BF16 layer path, relaxation / concretisation / adjoint fused in "
+                    "the epilogue)")
+        else:
+            kern = ("k_tcg (tcgen05 GEMMs of the BF16 layer path, conv operand gathered in shared memory or read "
+                    "from an im2col buffer; relaxation and adjoint in FP32 kernels between them)")
+        if hbm_frac >= ten_frac:
+            roof = {"bound": "hbm", "kernel": kern, "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": hbm_frac,
+                    "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)"}
+        else:
+            roof = {"bound": "tensor", "kernel": kern, "achieved": tfl, "peak": tpeak, "unit": "TFLOP/s",
+                    "frac": ten_frac, "peak_source": "of measured (MEASURED_PEAKS.json bf16_tflops_sustained)"}
+        roof.update({"traffic": None, "hbm_gbs": gbs, "hbm_frac": hbm_frac, "tensor_tflops": tfl,
+                     "tensor_frac": ten_frac, "algorithmic_bytes_per_launch": bytes_all / nl,
+                     "algorithmic_flops_per_launch": flops_all / nl,
+                     "bytes_model": "per row and iteration: 8 B x hidden neurons (Lambda and h, BF16, written and "
+                                    "read) + 4 B x inputs (x*) + 16 B x unstable (stash 2+2, alpha 4+4, dalpha 4) + "
+                                    "8 B x splits",
+                     "flops_model": "2 x (backward + adjoint) contractions per row and iteration: fc 2 d_i d_(i-1), "
+                                    "conv 2 C_out H_out W_out C_in k^2",
+                     "kernel_ms_per_step": ms / prof_steps, "launches_per_step": nl / prof_steps,
+                     "step_ms_by_class": {n: prof[c][0] / prof_steps for c, n in enumerate(
+                         ["contract", "relax", "concretize", "adjoint", "adam", "fused", "layer_gemm"])}})
     else:
         ms, nl = prof[0]
-        flops = rows * f_row * (2 * cfg.iters + 1) * args.steps
-        peak = fp32_simt_peak_tflops(sm_mhz)
+        flops = rows * f_row * (2 * cfg.iters + 1) * prof_steps
+        peak = probes["fp32_tflops"]
         achieved = flops / (ms / 1e3) / 1e12 if ms > 0 else None
         roof = {"bound": "alu", "kernel": "k_sgemm (FP32 SIMT contractions)", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
-                "peak_source": f"152 SMs x 128 FP32 FMA x 2 x {sm_mhz:.0f} MHz (median SM clock under load)",
-                "kernel_ms_per_step": ms / args.steps, "launches_per_step": nl / args.steps}
+                "peak_source": "of measured (bcrown_peak_probe FFMA throughput on this GPU)",
+                "kernel_ms_per_step": ms / prof_steps, "launches_per_step": nl / prof_steps}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -427,15 +505,40 @@ def main():
                                    ", 20 Adam iters + certify pass",
                        "subdomains_per_gpu": hbatch.B, "specs": pb.K, "rows_per_gpu": rows,
                        "unstable_neurons": U, "iters": cfg.iters, "precision": args.precision if prec == bc.BF16 else "fp32",
-                       "l2": "flushed (256 MB write between timed steps)"},
+                       "l2": "flushed (256 MB write between timed steps)",
+                       "graph": "one captured CUDA graph replayed per step" if graph is not None else "eager launches",
+                       "launch": launch},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk, "forms": forms,
+            "root_bounds": {"ms_per_property": rb_ms, "precision": "certify",
+                            "note": "once per property, outside the timed step"},
+            "measured_peaks": probes,
         }
-        if args.workload != "mlp784":
-            line["config"]["name"] = args.workload
+        if forms is not None:
+            forms["fp32"]["frac_of_fp32_peak"] = (
+                rows * f_row * (2 * cfg.iters + 1) / (forms["fp32"]["ms_per_step"] / 1e3) / 1e12
+                / probes["fp32_tflops"]) if probes["fp32_tflops"] else None
+        line["config"]["name"] = args.workload
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def time_root_bounds(bc, torch, net, dom, P, reps=3):
+    """Device milliseconds per property of bcrown_root_bounds (CROWN intermediate bounds with the
+    outward-rounded arithmetic), median of reps calls after one warm-up."""
+    x_lo, x_hi = dom.x_lo, dom.x_hi
+    bc.root_bounds(net, x_lo, x_hi, bc.ALPHA_ADAPTIVE, 0.5, bc.CERTIFY)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        bc.root_bounds(net, x_lo, x_hi, bc.ALPHA_ADAPTIVE, 0.5, bc.CERTIFY)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts) / P
 
 
 def measure_e2e(args, bc, torch, net, dom, hbatch, a0, b0, cfg, pb, world):
@@ -505,18 +608,20 @@ def run_reference(args, world):
     batch = make_batch(args.workload, pb, unst, args.subdomains, 0, wl)
     times = []
     rate = None
+    n_ref = WORKLOADS[args.workload]["ref_sample"]
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        rate, cores, sample = cpu_oracle_rate(pb, (l, u), batch, args.cpu_sample)
+        rate, cores, sample = cpu_oracle_rate(pb, (l, u), batch, n_ref)
         if i >= args.warmup:
             times.append(time.perf_counter() - t0)
     ms = 1e3 * statistics.mean(times)
-    value = args.cpu_sample / (ms / 1e3)
+    value = n_ref / (ms / 1e3)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload]["desc"].format(n=batch.B) +
-                                   ", 20 Adam iters + final bound", "sample_subdomains": args.cpu_sample},
+                                   ", 20 Adam iters + final bound", "sample_subdomains": n_ref,
+                       "name": args.workload},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     _ = torch

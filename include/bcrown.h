@@ -182,7 +182,13 @@ typedef struct {
   float adam_beta1, adam_beta2, adam_eps;
   int precision; /* of the iterations: BCROWN_FP32 or BCROWN_BF16 */
   int certify;   /* final pass: nonzero = BCROWN_CERTIFY, 0 = FP32 */
+  int freeze;    /* BCROWN_FREEZE_* bits: groups held at their inputs (Table A4's ablations):
+                    bcrown_optimize steps them with a zero learning rate (entries inside their
+                    boxes stay bit for bit), bcrown_optimize_joint does not step them */
 } bcrown_opt_cfg;
+
+#define BCROWN_FREEZE_ALPHA 1 /* alpha (and alpha' of bcrown_optimize_joint): the beta-only ablation */
+#define BCROWN_FREEZE_BETA 2  /* beta (and beta'): the alpha-only ablation */
 
 /* Optimiser state, for continuing an ascent across calls (checkpoint / resume, or a caller
  * that keeps stepping the same batch).  Caller-owned FP32 device arrays in the batch's alpha
@@ -229,6 +235,17 @@ int bcrown_batch_split(bcrown_net* net, const bcrown_domain* dom, const bcrown_b
                        int64_t* child_alpha_off, float* child_alpha, float* child_beta,
                        void* stream);
 
+/* The bound of bcrown_bound (FP32) and, per row, the point x* of the box that minimises the
+ * row's linear bound over it (Theorem 3.1: x_lo where A^(0)_m >= 0, else x_hi).  Evaluating
+ * the network there gives an upper bound of the row's minimum over the box (Appendix B.1,
+ * Algorithm 1's upper bound f(x*)).  lb [B*K], xstar [B*K][d_0] device outputs. */
+int bcrown_bound_xstar(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* batch,
+                       const float* alpha, const float* beta, float* lb, float* xstar, void* stream);
+
+/* The network itself with the specifications merged (Eq. 1, Section 2.1): out[r][k] =
+ * c_k^T f(x_r) for n inputs x [n][d_0] (device), FP32; out [n][K] device. */
+int bcrown_forward(bcrown_net* net, int n, const float* x, float* out, void* stream);
+
 /* Per (row, hidden neuron) relaxation code as the kernels use it: 0 inactive
  * (u <= 0), 1 active (l >= 0), 2 unstable, 3 split z >= 0, 4 split z < 0
  * (split overrides stability).  codes: device [B*K][H] int8. */
@@ -239,7 +256,9 @@ int bcrown_neuron_codes(bcrown_net* net, const bcrown_domain* dom, const bcrown_
  * launching stream around each of its kernels of the classes below; enable = 0
  * stops recording.  Either call discards earlier records.  bcrown_profile_read
  * waits for the recorded events and returns the summed device milliseconds and
- * the launch count of one class. */
+ * the launch count of one class.  Calls enqueued while the stream is being captured
+ * into a CUDA graph record their pairs as event nodes of the graph: after replays,
+ * the read gives the latest replay's times (the pairs stay valid while the net lives). */
 enum {
   BCROWN_PROF_CONTRACT = 0,   /* A.W contractions (dense or convolution), both directions */
   BCROWN_PROF_RELAX = 1,      /* relaxation + beta + bias epilogue */
@@ -247,7 +266,8 @@ enum {
   BCROWN_PROF_ADJOINT = 3,    /* adjoint epilogue (gradients) */
   BCROWN_PROF_ADAM = 4,       /* projected Adam */
   BCROWN_PROF_FUSED = 5,      /* fused tensor-core iteration kernel */
-  BCROWN_PROF_NCLASS = 6
+  BCROWN_PROF_LAYER_GEMM = 6, /* tensor-core GEMMs of the BF16 layer paths (LAYER_EPI: with the fused epilogues) */
+  BCROWN_PROF_NCLASS = 7
 };
 int bcrown_profile(bcrown_net* net, int enable);
 int bcrown_profile_read(bcrown_net* net, int cls, double* total_ms, long long* launches);
@@ -260,6 +280,113 @@ long long bcrown_kernel_launches(void);
  * `iters` x 128 FMAs per thread; the launch is timed with CUDA events on `stream` (the call
  * synchronises it) and *tflops receives the measured rate, 2 flops per FMA. */
 int bcrown_peak_probe(int kind, int iters, double* tflops, void* stream);
+
+/* ---- Joint optimisation of intermediate-layer bounds (Section 3.3, Eq. opt_non_convex) ----
+ *
+ * Fully connected networks (BCROWN_ERR_UNIMPLEMENTED otherwise), FP32.  Per subdomain, the
+ * bounds l^(T), u^(T) of every hidden layer T = 2..L-1 are recomputed by the bound of Theorem
+ * 3.1 with the objective z^(T)_j (for l) and -z^(T)_j (for u = -bound), from the subdomain's
+ * bounds of layers 1..T-1 (layer 1: the domain's), its split constraints and free variables
+ * alpha' in [0,1], beta' >= 0 shared by all target neurons of layer T (the O(L^2 d) variant);
+ * each is intersected with the domain's bound (both are valid on the subdomain).  The rows'
+ * bounds then use these l, u.  A neuron the tighter bounds make stable takes D = 1 or 0; its
+ * alpha entries stay in the layout.
+ *
+ * Layout of alpha' (subdomain b of property p, first[p][T] = the domain-unstable neurons of p
+ * in layers 1..T-1, rank = a neuron's rank among p's unstable neurons in layer-major order):
+ * subdomain b's block starts after the earlier subdomains' blocks (2 sum_{T=2}^{L-1}
+ * first[p][T] entries each); inside it, target layers T = 2..L-1 in order, for each the lower
+ * direction (dir 0) then the upper (dir 1), first[p][T] entries indexed by rank.  beta' of
+ * (b, T, dir) holds split_cnt[b] entries at 2 (L-2) split_off[b] + (2 (T-2) + dir) split_cnt[b]
+ * indexed by the split's position in b's list (entries of splits in layers >= T are unused).
+ * alpha, beta as in bcrown_bound.  All arrays are device memory; n_alpha_p, n_beta_p are the
+ * caller's array lengths (indices beyond them set BCROWN_ERR_ARG in the status word). */
+
+/* The lengths of alpha' and beta' for the batch (synchronises the stream). */
+int bcrown_joint_sizes(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* batch,
+                       int64_t* n_alpha_p, int64_t* n_beta_p, void* stream);
+
+/* alpha' at the rule the root bounds use (1 where u >= -l, else 0, per source neuron), so that
+ * with beta' = 0 and no split the recomputed bounds are the domain's. */
+int bcrown_joint_init_alpha(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* batch,
+                            float* alpha_p, int64_t n_alpha_p, void* stream);
+
+/* The bound of every row (lb [B*K]) with the recomputed intermediate bounds, which are written
+ * to l_out, u_out [B][H] (either may be NULL). */
+int bcrown_bound_joint(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* batch,
+                       const float* alpha, const float* beta, const float* alpha_p, int64_t n_alpha_p,
+                       const float* beta_p, int64_t n_beta_p, float* lb, float* l_out, float* u_out,
+                       void* stream);
+
+/* lb and the gradient of the sum of all rows' bounds with respect to alpha, beta, alpha' and
+ * beta' (the adjoint of each pass, chained through the recomputed bounds). */
+int bcrown_bound_joint_grad(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* batch,
+                            const float* alpha, const float* beta, const float* alpha_p, int64_t n_alpha_p,
+                            const float* beta_p, int64_t n_beta_p, float* lb, float* dalpha, float* dbeta,
+                            float* dalpha_p, float* dbeta_p, void* stream);
+
+/* Projected Adam on (alpha, beta, alpha', beta') with cfg's iterations, learning rates (alpha'
+ * at lr_alpha, beta' at lr_beta), decay and freeze bits; cfg->precision must be BCROWN_FP32 and
+ * cfg->certify 0.  Per subdomain, the iterate with the largest sum of its spec bounds is kept
+ * (the intermediate bounds belong to the subdomain); on return alpha .. beta_p hold it, lb_out
+ * its bounds and l_out, u_out (may be NULL) its intermediate bounds.  Allocates its optimiser
+ * state with cudaMalloc and synchronises the stream. */
+int bcrown_optimize_joint(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* batch,
+                          const bcrown_opt_cfg* cfg, float* alpha, float* beta, float* alpha_p, int64_t n_alpha_p,
+                          float* beta_p, int64_t n_beta_p, float* lb_out, float* l_out, float* u_out,
+                          void* stream);
+
+/* ---- BF16 launch configuration and its tuner (the paper has no counterpart: these choose
+ * among this library's own kernels for the same computation) ----
+ *
+ * The BF16 precision of bcrown_bound, bcrown_bound_grad and bcrown_optimize can run the bound
+ * pass (Theorem 3.1) and its adjoint on one of these paths; they compute the same quantities
+ * and differ only in rounding order and speed:
+ *   BCROWN_PATH_FUSED         fully connected nets up to the fused kernel's limits: the whole
+ *                             backward recursion and adjoint of a 64-row tile in one persistent
+ *                             tcgen05 kernel
+ *   BCROWN_PATH_LAYER_EPI     layer by layer: one tcgen05 GEMM per contraction (conv operands
+ *                             gathered in shared memory), the relaxation, beta shift, bias sums,
+ *                             concretisation and adjoint applied in the GEMM's epilogue
+ *   BCROWN_PATH_LAYER_GATHER  layer by layer: tcgen05 GEMMs (conv operands gathered in shared
+ *                             memory), FP32 CUDA-core kernels for the steps between them
+ *   BCROWN_PATH_LAYER_IM2COL  as LAYER_GATHER with the conv operands written to an im2col
+ *                             buffer in HBM and read by TMA
+ * grid_per_sm: persistent CTAs per SM for the LAYER_GATHER / LAYER_IM2COL GEMMs (0 = 2); the
+ * other paths run one CTA per SM and ignore it. */
+#define BCROWN_PATH_DEFAULT 0
+#define BCROWN_PATH_FUSED 1
+#define BCROWN_PATH_LAYER_EPI 2
+#define BCROWN_PATH_LAYER_GATHER 3
+#define BCROWN_PATH_LAYER_IM2COL 4
+
+typedef struct {
+  int path;        /* BCROWN_PATH_*; DEFAULT = the first supported of FUSED, LAYER_EPI, LAYER_GATHER */
+  int grid_per_sm; /* 0 = the path's default */
+} bcrown_launch_cfg;
+
+/* 1 if the net can take `path` on this device, else 0 (unknown paths: 0). */
+int bcrown_path_supported(bcrown_net* net, int path);
+
+/* The configuration used from now on for every row count the tuner has no choice for.
+ * BCROWN_ERR_ARG for an unknown path, BCROWN_ERR_UNIMPLEMENTED for one the net cannot take. */
+int bcrown_set_launch(bcrown_net* net, const bcrown_launch_cfg* cfg);
+
+/* The configuration a BF16 call with `rows` rows (subdomains x specs) takes: the tuner's choice
+ * for rows' bucket, else the one set, else the built-in order (path resolved, never DEFAULT). */
+int bcrown_get_launch(bcrown_net* net, int rows, bcrown_launch_cfg* cfg);
+
+/* Autotuner: times every supported configuration on the caller's batch and keeps the fastest
+ * for the batch's row-count bucket (rows rounded up to a power of two), which every later BF16
+ * call with rows in that bucket takes.  Each candidate runs bcrown_bound_grad (BCROWN_BF16) at
+ * `alpha`, `beta` (device, the batch's layouts) once untimed, then `reps` >= 1 times timed with
+ * CUDA events on `stream`; the call synchronises the stream and allocates (then frees) its own
+ * device outputs.  cands / ms (host, max_cands entries each, either may be NULL) receive the
+ * candidates and their mean milliseconds per call; *n_cands their count; *best the choice.
+ * Errors of a candidate end the call with that error. */
+int bcrown_autotune(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* batch,
+                    const float* alpha, const float* beta, int reps, bcrown_launch_cfg* cands, double* ms,
+                    int max_cands, int* n_cands, bcrown_launch_cfg* best, void* stream);
 
 /* Size in bytes of the fixed device scratch of bcrown_bound_static (set when the library is built). */
 #define BCROWN_STATIC_SCRATCH_BYTES (16u << 20)

@@ -9,20 +9,30 @@ Eq. opt_alpha_beta; one engine call per batch) and drops those whose bound is po
 spec (Domain_Filter).  The property is
 
   verified  when the pool empties;
-  violated  when an input of the box has a negative margin: searched before branching among
-            random points of the box and its centre, then by projected sign-gradient descent
-            on the lowest margin from the best of them (the witness is re-checked in FP64);
-  unknown   when the budget (rounds, bounded subdomains, time) runs out, or only fully split
-            subdomains remain open (their bound after a finite number of Adam steps need not
-            have reached the exact subdomain minimum of Theorem 3.3).
+  violated  when an input of the box has a negative margin (re-checked in FP64): searched before
+            branching among random points of the box and its centre, then by projected
+            sign-gradient descent on the lowest margin from the best of them; and, as branching
+            goes on, at the point x* that minimises each bounded subdomain's linear bound (the
+            upper bound f(x*) that Algorithm 1 keeps beside the lower bound, Appendix B.1);
+  unknown   when the budget (rounds, bounded subdomains, time) runs out.
+
+A subdomain with every root-unstable neuron split is linear on its region, so its bound is
+concave in beta alone (Theorem 3.3): the driver then maximises it by projected gradient ascent
+with a backtracking line search until the step vanishes (the bound then equals the subdomain's
+exact minimum, Corollary 3.1) or the bound turns positive, which also catches the subdomains
+whose splits contradict each other (an empty region makes the dual unbounded, Appendix B.3).
+A negative converged bound is turned into a witness by evaluating the network at x*; without
+one the subdomain stays open and the verdict unknown.
 
 Branching rule: the paper names BaBSR and FSB but does not define their scores, so a static
 rule stands in: the unsplit root-unstable neuron with the widest triangle relaxation, measured
 by the intercept of its upper chord, u (-l) / (u - l).
 
 The engine does the bounding: engine.optimize(subdomains, alpha, beta) -> (lb, alpha, beta) on
-one batch (subdomains as (property, neuron indices, signs)), engine.margins(x) -> C f(x) in FP64
-for rows of inputs.  GpuEngine runs bcrown_optimize (BF16 iterations and the certifying pass).
+one batch (subdomains as (property, neuron indices, signs)); engine.bound_grad(...) -> (lb,
+dlb/dalpha, dlb/dbeta) and engine.certify(...) -> lb at fixed alpha, beta; engine.xstar(...) ->
+(x*, C f(x*)) per row; engine.margins(x) -> C f(x) in FP64 for rows of inputs.  GpuEngine runs
+the library (BF16 iterations and the certifying pass; FP32 for the line search and x*).
 """
 from __future__ import annotations
 
@@ -60,6 +70,9 @@ class BabResult:
     witness_margins: np.ndarray | None = None
     seconds: float = 0.0
     history: list = field(default_factory=list)   # per round: (open domains, min lb)
+    upper: float = float("inf")          # lowest margin found at an input of the box (f-bar)
+    line_searched: int = 0               # fully split subdomains maximised over beta alone
+    infeasible: int = 0                  # of those, the ones whose bound grew past zero
 
 
 def branching_scores(l, u):
@@ -87,11 +100,12 @@ def _children(parent, j, K):
 
 
 def _next_neuron(d, order):
-    """The first neuron of the branching order that d has not split.  With the static order a
-    subdomain's splits are a prefix of it, so that is order[depth]; otherwise scan."""
-    if d.depth < len(order) and (d.depth == 0 or d.splits[-1] == order[d.depth - 1]) and \
-            int(order[d.depth]) not in d.splits[:d.depth]:
-        return int(order[d.depth])
+    """The first neuron of the branching order that d has not split.  Where d's splits are exactly
+    the first depth neurons of the order (every subdomain the driver grows from the root), that is
+    order[depth]; otherwise (subdomains given as starting points) scan."""
+    k = d.depth
+    if k < len(order) and np.array_equal(d.splits, order[:k]):
+        return int(order[k])
     used = set(d.splits.tolist())
     return next((int(v) for v in order if int(v) not in used), None)
 
@@ -158,15 +172,78 @@ def _falsify(engine, x_lo, x_hi, n_samples, rng, pgd_steps=0, pgd_starts=8):
     return x[i], m[i]
 
 
+def _upper(engine, doms, cases, res):
+    """f(x*) for every row of the bounded subdomains: the lowest margin at the points that minimise
+    their linear bounds.  A negative one (re-checked in FP64) decides its property: violated."""
+    if not doms:
+        return
+    subs = [(cases[d.owner][0], d.splits, d.signs) for d in doms]
+    xs, m = engine.xstar(subs, np.concatenate([d.alpha for d in doms]), np.concatenate([d.beta for d in doms]))
+    K = engine.K
+    worst = m.min(axis=1).reshape(len(doms), K)
+    for i, d in enumerate(doms):
+        r = res[d.owner]
+        j = int(np.argmin(worst[i]))
+        if worst[i, j] < r.upper or worst[i, j] < 0:
+            x = np.asarray(xs[i * K + j], np.float64)
+            m64 = engine.margins(x[None])[0]
+            r.upper = min(r.upper, float(m64.min()))
+            if m64.min() < 0 and r.status != "violated":
+                r.status, r.witness, r.witness_margins = "violated", x, m64
+
+
+LINE_SEARCH_LRS = (0.05, 0.2, 1.0)   # initial step sizes of the beta ascent tried per subdomain
+
+
+def _line_search(engine, doms, cases, K, iters=500, decay=0.99, lrs=LINE_SEARCH_LRS, tol=1e-6):
+    """Fully split subdomains (no alpha left in their bound): the bound is concave and piecewise
+    linear in beta (Theorem 3.3), so ascent on beta alone reaches its maximum, the exact minimum
+    of the region (Corollary 3.1).  The paper suggests a line search so that convergence does not
+    hang on a preset learning rate; along a supergradient of this piecewise-linear function a
+    backtracking search stalls at the kinks (measured on the tiny nets: a few percent short after
+    200 steps), so the search here is over the step size of the projected Adam ascent on beta:
+    one FP32 run per initial step size in `lrs` (decayed by `decay` per step), keeping per row
+    the best certified bound.  A row is converged when its bound turned positive (verified; an
+    empty region, whose dual is unbounded, ends here too, Appendix B.3) or the runs agree to
+    within tol.  Returns (certified lb [n, K], converged [n])."""
+    subs = [(cases[d.owner][0], d.splits, d.signs) for d in doms]
+    alpha = np.concatenate([d.alpha for d in doms])
+    beta0 = np.concatenate([d.beta for d in doms])
+    boff = np.concatenate([[0], np.cumsum([K * d.depth for d in doms])]).astype(np.int64)
+    rows = np.repeat(np.arange(len(doms) * K), np.repeat([d.depth for d in doms], K))   # row of each beta
+    best = lo = None
+    best_beta = None
+    for lr in lrs:
+        lb, _, b = engine.optimize(subs, alpha, beta0, iters=iters, lr_alpha=0.0, lr_beta=lr, decay=decay,
+                                   fp32=True)
+        lb = np.asarray(lb, np.float64)
+        b = np.asarray(b, np.float32)
+        if best is None:
+            best, lo, best_beta = lb.copy(), lb.copy(), b.copy()
+            continue
+        better = lb > best
+        best = np.where(better, lb, best)
+        lo = np.minimum(lo, lb)
+        best_beta = np.where(better[rows], b, best_beta)
+    conv = (best > 0) | (best - lo <= tol * np.maximum(1.0, np.abs(best)))
+    cert = best.reshape(len(doms), K)
+    for i, d in enumerate(doms):
+        d.beta = best_beta[boff[i]:boff[i + 1]]
+        d.lb = cert[i].astype(np.float32)
+    return cert, conv.reshape(len(doms), K).all(axis=1)
+
+
 def bab(engine, prop, l, u, x_lo, x_hi, batch_size=512, max_rounds=50, max_bounded=1_000_000,
-        n_samples=256, seed=0, time_limit=None, alpha_init=0.5, pgd_steps=20, start=None):
+        n_samples=256, seed=0, time_limit=None, alpha_init=0.5, pgd_steps=20, start=None, upper=True,
+        line_search=True):
     """Decide property `prop` (its box x_lo, x_hi and root bounds l, u over all hidden neurons).
 
     start: subdomains to begin from instead of the whole box, as (neuron indices, signs) pairs;
     "verified" then covers their union only (a witness of "violated" may lie anywhere in the box)."""
     return bab_many(engine, [(prop, l, u, x_lo, x_hi)], batch_size=batch_size, max_rounds=max_rounds,
                     max_bounded=max_bounded, n_samples=n_samples, seed=seed, time_limit=time_limit,
-                    alpha_init=alpha_init, pgd_steps=pgd_steps, starts=None if start is None else [start])[0]
+                    alpha_init=alpha_init, pgd_steps=pgd_steps, starts=None if start is None else [start],
+                    upper=upper, line_search=line_search)[0]
 
 
 def _bound(engine, doms, cases, K, Us):
@@ -183,11 +260,13 @@ def _bound(engine, doms, cases, K, Us):
 
 
 def bab_many(engine, cases, batch_size=512, max_rounds=50, max_bounded=1_000_000, n_samples=256, seed=0,
-             time_limit=None, alpha_init=0.5, pgd_steps=20, starts=None):
+             time_limit=None, alpha_init=0.5, pgd_steps=20, starts=None, upper=True, line_search=True):
     """Decide several properties at once: cases = [(prop, l, u, x_lo, x_hi), ...].  Their open
     subdomains share one pool, so each engine call bounds the lowest-bound subdomains of all the
     properties still open together (one batch of mixed properties).  Returns one BabResult per
-    case; starts, if given, holds each case's start subdomains (see bab)."""
+    case; starts, if given, holds each case's start subdomains (see bab).  upper: evaluate the
+    network at every bounded subdomain's x*; line_search: take fully split subdomains to their
+    exact minimum over beta (both on by default; off, the driver is the plain Algorithm 1 loop)."""
     t0 = time.perf_counter()
     K = engine.K
     n = len(cases)
@@ -215,13 +294,19 @@ def bab_many(engine, cases, batch_size=512, max_rounds=50, max_bounded=1_000_000
     pool, exhausted = [], []
     if first:
         _bound(engine, first, cases, K, Us)
+        if upper:
+            _upper(engine, first, cases, res)
         for d in first:
             res[d.owner].bounded += 1
             res[d.owner].max_depth = max(res[d.owner].max_depth, d.depth)
             if d.lb.min() <= 0:
                 pool.append(d)
+    for c in range(n):
+        if open_case[c] and res[c].status == "violated":
+            open_case[c] = False
+    pool = [d for d in pool if open_case[d.owner]]
     rounds = bounded = 0
-    while pool:
+    while pool or any(open_case[d.owner] and not getattr(d, "searched", False) for d in exhausted):
         if rounds >= max_rounds or bounded >= max_bounded or (
                 time_limit is not None and time.perf_counter() - t0 > time_limit):
             break
@@ -239,6 +324,8 @@ def bab_many(engine, cases, batch_size=512, max_rounds=50, max_bounded=1_000_000
             kids.extend(_children(d, j, K))
         if kids:
             _bound(engine, kids, cases, K, Us)
+            if upper:
+                _upper(engine, kids, cases, res)
             bounded += len(kids)
             for k in kids:
                 r = res[k.owner]
@@ -246,12 +333,38 @@ def bab_many(engine, cases, batch_size=512, max_rounds=50, max_bounded=1_000_000
                 r.max_depth = max(r.max_depth, k.depth)
                 if k.lb.min() <= 0:      # Domain_Filter: keep the subdomains not yet verified
                     pool.append(k)
+        # a property with a witness is decided: its subdomains leave the pool
+        for c in range(n):
+            if open_case[c] and res[c].status == "violated":
+                open_case[c] = False
+        pool = [d for d in pool if open_case[d.owner]]
+        # fully split subdomains: beta alone, to the exact subdomain minimum (Theorem 3.3)
+        fresh = [d for d in exhausted if open_case[d.owner] and not getattr(d, "searched", False)]
+        if fresh and not line_search:
+            for d in fresh:
+                d.searched = True
+        elif fresh:
+            cert, conv = _line_search(engine, fresh, cases, K)
+            _upper(engine, fresh, cases, res)   # x* of the maximised bound: the witness of a negative minimum
+            keep = []
+            for d, ok in zip(fresh, conv):
+                d.searched = True
+                res[d.owner].line_searched += 1
+                if d.lb.min() > 0:
+                    res[d.owner].infeasible += int(not ok)   # grew past zero before converging
+                else:
+                    keep.append(d)
+            exhausted = [d for d in exhausted if not getattr(d, "searched", False)] + keep
+            for c in range(n):
+                if open_case[c] and res[c].status == "violated":
+                    open_case[c] = False
+        exhausted = [d for d in exhausted if open_case[d.owner]]
         for c in range(n):
             if open_case[c]:
                 left = [float(d.lb.min()) for d in pool + exhausted if d.owner == c]
                 res[c].history.append((len(left), min(left, default=float("inf"))))
     for c in range(n):
-        if not open_case[c]:
+        if not open_case[c] or res[c].status == "violated":
             continue
         left = [d for d in pool + exhausted if d.owner == c]
         res[c].open_domains = len(left)
@@ -321,17 +434,52 @@ class GpuEngine:
         self.U = list(unstable_counts)
         self.cfg = bc.OptCfg(iters=iters, precision=bc.BF16 if precision is None else precision, certify=True)
 
-    def optimize(self, subs, alpha, beta):
+    def optimize(self, subs, alpha, beta, iters=None, lr_alpha=None, lr_beta=None, decay=None, fp32=False):
+        """The optimised, certified bound (bcrown_optimize); the keywords override the engine's
+        settings for one call (fp32: FP32 iterations instead of BF16)."""
+        import dataclasses
+        db, at, bt = self._args(subs, alpha, beta)
+        cfg = dataclasses.replace(self.cfg, **{k: v for k, v in dict(iters=iters, lr_alpha=lr_alpha, lr_beta=lr_beta,
+                                                                      decay=decay).items() if v is not None})
+        if fp32:
+            cfg = dataclasses.replace(cfg, precision=self.bc.FP32)
+        lb = self.bc.optimize(self.net, self.dom, db, at, bt, cfg)
+        st = self.bc.status(self.net)
+        if st != 0:
+            raise RuntimeError(f"bcrown device status {st}")
+        return lb.cpu().numpy(), at.cpu().numpy(), bt.cpu().numpy()
+
+    def _args(self, subs, alpha, beta):
         import torch
         batch = wl.pack_batch(self.pb.hidden_widths, self.K, self.U, subs)
         db = self.bc.DeviceBatch.from_host(batch)
         at = torch.as_tensor(np.ascontiguousarray(alpha, np.float32)).cuda()
         bt = torch.as_tensor(np.ascontiguousarray(beta, np.float32)).cuda()
-        lb = self.bc.optimize(self.net, self.dom, db, at, bt, self.cfg)
+        return db, at, bt
+
+    def _check(self):
         st = self.bc.status(self.net)
         if st != 0:
             raise RuntimeError(f"bcrown device status {st}")
-        return lb.cpu().numpy(), at.cpu().numpy(), bt.cpu().numpy()
+
+    def bound_grad(self, subs, alpha, beta):
+        db, at, bt = self._args(subs, alpha, beta)
+        lb, da, dbeta = self.bc.bound_grad(self.net, self.dom, db, at, bt, self.bc.FP32)
+        self._check()
+        return lb.cpu().numpy(), da.cpu().numpy(), dbeta.cpu().numpy()
+
+    def certify(self, subs, alpha, beta):
+        db, at, bt = self._args(subs, alpha, beta)
+        lb = self.bc.bound(self.net, self.dom, db, at, bt, self.bc.CERTIFY)
+        self._check()
+        return lb.cpu().numpy()
+
+    def xstar(self, subs, alpha, beta):
+        db, at, bt = self._args(subs, alpha, beta)
+        _, xs = self.bc.bound_xstar(self.net, self.dom, db, at, bt)
+        m = self.bc.forward(self.net, xs)
+        self._check()
+        return xs.cpu().numpy(), m.cpu().numpy()
 
     def margins(self, x):
         f = wl.reference_forward(self.pb.layers, x)

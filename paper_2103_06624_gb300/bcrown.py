@@ -63,6 +63,7 @@ class Net:
         self.widths = [layers[0].d_in] + [ly.d_out for ly in layers]
         self.hidden_widths = self.widths[1:self.L]
         self.H = int(sum(self.hidden_widths))
+        self.d0 = int(self.widths[0])
 
     @property
     def handle(self):
@@ -191,10 +192,13 @@ class OptCfg:
     adam_eps: float = 1e-8
     precision: int = FP32
     certify: bool = True
+    freeze_alpha: bool = False   # the beta-only ablation (Table A4)
+    freeze_beta: bool = False    # the alpha-only ablation
 
     def c(self):
+        fr = (N.FREEZE_ALPHA if self.freeze_alpha else 0) | (N.FREEZE_BETA if self.freeze_beta else 0)
         return N.OptCfg(self.iters, self.lr_alpha, self.lr_beta, self.decay, self.adam_beta1, self.adam_beta2,
-                        self.adam_eps, self.precision, 1 if self.certify else 0)
+                        self.adam_eps, self.precision, 1 if self.certify else 0, fr)
 
 
 class OptState:
@@ -307,6 +311,26 @@ def profile_read(net, cls):
     return t.value, n.value
 
 
+def bound_xstar(net, dom, batch, alpha, beta, stream=None):
+    """FP32 bound of every row and the box point x* minimising its linear bound: (lb [B*K], x* [B*K, d0])."""
+    lib = N.load()
+    lb = torch.empty(batch.B * net.K, device="cuda", dtype=torch.float32)
+    xs = torch.empty((batch.B * net.K, net.d0), device="cuda", dtype=torch.float32)
+    d, b = dom.c(), batch.c()
+    N.check(lib.bcrown_bound_xstar(net.handle, C.byref(d), C.byref(b), _ptr(alpha), _ptr(beta), _ptr(lb), _ptr(xs),
+                                   _stream(stream)))
+    return lb, xs
+
+
+def forward(net, x, stream=None):
+    """c_k^T f(x) for rows of x [n, d0] (FP32): the network's specification outputs."""
+    lib = N.load()
+    x = x.contiguous()
+    out = torch.empty((x.shape[0], net.K), device="cuda", dtype=torch.float32)
+    N.check(lib.bcrown_forward(net.handle, int(x.shape[0]), _ptr(x), _ptr(out), _stream(stream)))
+    return out
+
+
 def peak_probe(kind, iters=2000, stream=None):
     """Measured FP32 (kind 0) or FP64 (kind 1) FMA throughput of this GPU in TFLOP/s."""
     t = C.c_double()
@@ -316,3 +340,93 @@ def peak_probe(kind, iters=2000, stream=None):
 
 def kernel_launches():
     return int(N.load().bcrown_kernel_launches())
+
+
+# ---- BF16 launch configuration and the autotuner ----
+
+def path_supported(net, path):
+    return bool(N.load().bcrown_path_supported(net.handle, int(path)))
+
+
+def set_launch(net, path, grid_per_sm=0):
+    cfg = N.LaunchCfg(int(path), int(grid_per_sm))
+    N.check(N.load().bcrown_set_launch(net.handle, C.byref(cfg)))
+
+
+def get_launch(net, rows):
+    """(path, grid_per_sm) a BF16 call with `rows` rows takes."""
+    cfg = N.LaunchCfg()
+    N.check(N.load().bcrown_get_launch(net.handle, int(rows), C.byref(cfg)))
+    return cfg.path, cfg.grid_per_sm
+
+
+def autotune(net, dom, batch, alpha, beta, reps=3, stream=None):
+    """Times every supported BF16 configuration on this batch and keeps the fastest for its
+    row-count bucket.  Returns ((path, grid_per_sm) chosen, [((path, grid_per_sm), ms), ...])."""
+    lib = N.load()
+    cands = (N.LaunchCfg * 16)()
+    ms = (C.c_double * 16)()
+    n = C.c_int()
+    best = N.LaunchCfg()
+    d, b = dom.c(), batch.c()
+    N.check(lib.bcrown_autotune(net.handle, C.byref(d), C.byref(b), _ptr(alpha), _ptr(beta), int(reps), cands, ms,
+                                16, C.byref(n), C.byref(best), _stream(stream)))
+    return (best.path, best.grid_per_sm), [((cands[i].path, cands[i].grid_per_sm), ms[i]) for i in range(n.value)]
+
+
+# ---- joint optimisation of intermediate-layer bounds (Section 3.3) ----
+
+def joint_sizes(net, dom, batch, stream=None):
+    """(n_alpha', n_beta') of the batch (synchronises)."""
+    na, nb = C.c_int64(), C.c_int64()
+    d, b = dom.c(), batch.c()
+    N.check(N.load().bcrown_joint_sizes(net.handle, C.byref(d), C.byref(b), C.byref(na), C.byref(nb),
+                                        _stream(stream)))
+    return na.value, nb.value
+
+
+def joint_init_alpha(net, dom, batch, stream=None):
+    """alpha' at the root bounds' rule and beta' = 0 (device tensors)."""
+    na, nb = joint_sizes(net, dom, batch, stream)
+    ap = torch.zeros(max(na, 1), device="cuda", dtype=torch.float32)[:na]
+    bp = torch.zeros(max(nb, 1), device="cuda", dtype=torch.float32)[:nb]
+    d, b = dom.c(), batch.c()
+    N.check(N.load().bcrown_joint_init_alpha(net.handle, C.byref(d), C.byref(b), _ptr(ap), na, _stream(stream)))
+    return ap, bp
+
+
+def bound_joint(net, dom, batch, alpha, beta, alpha_p, beta_p, stream=None):
+    """(lb [B*K], l [B, H], u [B, H]) with the intermediate bounds recomputed per subdomain."""
+    lb = torch.empty(batch.B * net.K, device="cuda", dtype=torch.float32)
+    l = torch.empty((batch.B, net.H), device="cuda", dtype=torch.float32)
+    u = torch.empty_like(l)
+    d, b = dom.c(), batch.c()
+    N.check(N.load().bcrown_bound_joint(net.handle, C.byref(d), C.byref(b), _ptr(alpha), _ptr(beta), _ptr(alpha_p),
+                                        int(alpha_p.numel()), _ptr(beta_p), int(beta_p.numel()), _ptr(lb), _ptr(l),
+                                        _ptr(u), _stream(stream)))
+    return lb, l, u
+
+
+def bound_joint_grad(net, dom, batch, alpha, beta, alpha_p, beta_p, stream=None):
+    """(lb, d/dalpha, d/dbeta, d/dalpha', d/dbeta') of the sum of all rows' bounds."""
+    lb = torch.empty(batch.B * net.K, device="cuda", dtype=torch.float32)
+    g = [torch.empty_like(t) for t in (alpha, beta, alpha_p, beta_p)]
+    d, b = dom.c(), batch.c()
+    N.check(N.load().bcrown_bound_joint_grad(net.handle, C.byref(d), C.byref(b), _ptr(alpha), _ptr(beta),
+                                             _ptr(alpha_p), int(alpha_p.numel()), _ptr(beta_p), int(beta_p.numel()),
+                                             _ptr(lb), *[_ptr(t) for t in g], _stream(stream)))
+    return (lb, *g)
+
+
+def optimize_joint(net, dom, batch, alpha, beta, alpha_p, beta_p, cfg=None, stream=None):
+    """Projected Adam on (alpha, beta, alpha', beta') (FP32); the four are overwritten with the kept
+    iterate.  Returns (lb, l, u) there."""
+    cfg = cfg or OptCfg(certify=False)
+    lb = torch.empty(batch.B * net.K, device="cuda", dtype=torch.float32)
+    l = torch.empty((batch.B, net.H), device="cuda", dtype=torch.float32)
+    u = torch.empty_like(l)
+    d, b, cc = dom.c(), batch.c(), cfg.c()
+    N.check(N.load().bcrown_optimize_joint(net.handle, C.byref(d), C.byref(b), C.byref(cc), _ptr(alpha), _ptr(beta),
+                                           _ptr(alpha_p), int(alpha_p.numel()), _ptr(beta_p), int(beta_p.numel()),
+                                           _ptr(lb), _ptr(l), _ptr(u), _stream(stream)))
+    return lb, l, u

@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libbcrown.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["net.cu", "simt.cu", "api.cu", "fused_tc.cu", "conv_tc.cu", "static_scratch.cu", "probe.cu"]
+SOURCES = ["net.cu", "simt.cu", "api.cu", "fused_tc.cu", "conv_tc.cu", "static_scratch.cu", "probe.cu", "layer_tc.cu",
+           "conv_f32.cu", "joint.cu"]
 
 
 def nvcc():

@@ -6,6 +6,7 @@
 
 #include "conv_tc.cuh"
 #include "fused_tc.cuh"
+#include "layer_tc.cuh"
 #include "simt.cuh"
 
 using namespace bcrown;
@@ -62,6 +63,9 @@ struct Plan {
   float *a_cur, *ma, *va, *ga, *b_cur, *mb, *vb, *gb, *best_lb, *lb_t;
   char* tc_ws;
   size_t tc_ws_bytes;
+  // BF16 layer-by-layer path (null when unused)
+  char* lt_ws = nullptr;
+  size_t lt_ws_bytes = 0;
   // BF16 conv layers on the tensor cores: the im2col operand of one chunk (null when unused)
   char* col = nullptr;
   size_t col_bytes = 0;
@@ -75,7 +79,7 @@ static size_t row_bytes(const bcrown_net* net) {
 }
 
 static int make_plan(bcrown_net* net, int P, int R, bool cert, bool opt, int64_t n_alpha, int64_t n_beta,
-                     size_t tc_bytes, Plan& pl, size_t col_per_row = 0) {
+                     size_t tc_bytes, Plan& pl, size_t col_per_row = 0, size_t lt_bytes = 0) {
   pl.P = P;
   pl.H = net->H;
   pl.R = R;
@@ -88,7 +92,7 @@ static int make_plan(bcrown_net* net, int P, int R, bool cert, bool opt, int64_t
   if (cert) bytes += align_up(PH * 4);
   bytes += (size_t)pl.Rc * rb + 16 * 256;
   if (opt) bytes += align_up((size_t)n_alpha * 4) * 4 + align_up((size_t)n_beta * 4) * 4 + align_up((size_t)R * 4) * 2;
-  bytes += align_up(tc_bytes);
+  bytes += align_up(tc_bytes) + align_up(lt_bytes);
   int st;
   void* base = ws_get(net, bytes, &st);
   if (!base) return st;
@@ -125,8 +129,48 @@ static int make_plan(bcrown_net* net, int P, int R, bool cert, bool opt, int64_t
   }
   pl.tc_ws = tc_bytes ? ar.take<char>(tc_bytes) : nullptr;
   pl.tc_ws_bytes = tc_bytes;
+  pl.lt_ws = lt_bytes ? ar.take<char>(lt_bytes) : nullptr;
+  pl.lt_ws_bytes = lt_bytes;
   if (ar.off > net->ws.size) return fail(BCROWN_ERR_OOM, "workspace plan overflow");
   return BCROWN_OK;
+}
+
+// ---- BF16 launch configuration (bcrown_set_launch, bcrown_autotune) ----
+static bool path_ok(const bcrown_net* net, int path) {
+  switch (path) {
+    case BCROWN_PATH_FUSED: return tc_supported(net);
+    case BCROWN_PATH_LAYER_EPI: return lt_supported(net);
+    case BCROWN_PATH_LAYER_GATHER:
+    case BCROWN_PATH_LAYER_IM2COL: return tcg_supported(net);
+    default: return false;
+  }
+}
+
+static int bucket_of(long long rows) {
+  int b = 0;
+  while ((1LL << b) < rows) ++b;
+  return b;
+}
+
+// The configuration a BF16 call with `rows` rows takes (path 0: the net takes none).
+static bcrown_net::Launch resolve_launch(const bcrown_net* net, long long rows) {
+  const int bk = bucket_of(rows);
+  for (const auto& t : net->tuned)
+    if (t.first == bk && path_ok(net, t.second.path)) return t.second;
+  if (net->launch_set.path && path_ok(net, net->launch_set.path)) return net->launch_set;
+  bcrown_net::Launch l;
+  l.grid_per_sm = net->launch_set.grid_per_sm;
+  for (int p : {BCROWN_PATH_FUSED, BCROWN_PATH_LAYER_EPI, BCROWN_PATH_LAYER_GATHER, BCROWN_PATH_LAYER_IM2COL})
+    if (path_ok(net, p)) {
+      l.path = p;
+      return l;
+    }
+  l.path = 0;
+  return l;
+}
+
+static int bf16_path(const bcrown_net* net, int precision, long long rows) {
+  return precision == BCROWN_BF16 ? resolve_launch(net, rows).path : 0;
 }
 
 static void build_tables(bcrown_net* net, const bcrown_domain* dom, Plan& pl, cudaStream_t s) {
@@ -162,12 +206,14 @@ static RowsCtx ctx_of(bcrown_net* net, const bcrown_domain* dom, const bcrown_ba
 // tc: BF16 tensor-core GEMMs (over an im2col operand for conv layers) with the operand in pl.col.
 static int contract_bwd(bcrown_net* net, int i, int Rc, const float* Lam, float* Aout, cudaStream_t s,
                         const Plan* tc = nullptr) {
-  ProfScope ps(net, BCROWN_PROF_CONTRACT, s);
+  ProfScope ps(net, tc ? BCROWN_PROF_LAYER_GEMM : BCROWN_PROF_CONTRACT, s);
   const LayerDev& l = net->ly[i - 1];
   if (tc)
     return tcg_conv(net, i, false, Rc, Lam, Aout, nullptr, tc->col, tc->col_bytes, s);
   if (l.kind == BCROWN_LAYER_FC)
     launch_sgemm(Rc, l.d_in, l.d_out, Lam, l.d_out, l.W, l.d_in, Aout, l.d_in, nullptr, s);
+  else if (sconv_supported(net, i))
+    return sconv_bwd(net, i, Rc, Lam, Aout, s);
   else
     launch_conv_bwd(Rc, geom_of(l), Lam, l.W, Aout, s);
   return BCROWN_OK;
@@ -176,12 +222,14 @@ static int contract_bwd(bcrown_net* net, int i, int Rc, const float* Lam, float*
 // Forward contraction of layer i: Z = h W^(i)^T + b^(i).
 static int contract_fwd(bcrown_net* net, int i, int Rc, const float* h, float* Z, cudaStream_t s,
                         const Plan* tc = nullptr) {
-  ProfScope ps(net, BCROWN_PROF_CONTRACT, s);
+  ProfScope ps(net, tc ? BCROWN_PROF_LAYER_GEMM : BCROWN_PROF_CONTRACT, s);
   const LayerDev& l = net->ly[i - 1];
   if (tc)
     return tcg_conv(net, i, true, Rc, h, Z, l.b, tc->col, tc->col_bytes, s);
   if (l.kind == BCROWN_LAYER_FC)
     launch_sgemm(Rc, l.d_out, l.d_in, h, l.d_in, l.Wt, l.d_out, Z, l.d_out, l.b, s);
+  else if (sconv_supported(net, i))
+    return sconv_fwd(net, i, Rc, h, Z, l.b, s);
   else
     launch_conv_fwd(Rc, geom_of(l), h, l.W, l.b, Z, s);
   return BCROWN_OK;
@@ -190,7 +238,7 @@ static int contract_fwd(bcrown_net* net, int i, int Rc, const float* h, float* Z
 // One chunk of rows: bound (and optionally the gradient) with the SIMT path.
 static int chunk_simt(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* bt, Plan& pl, int r0, int Rc,
                       bool cert, bool grad, const float* alpha, const float* beta, float* lb, float* dalpha,
-                      float* dbeta, cudaStream_t s, bool tc_layers = false) {
+                      float* dbeta, cudaStream_t s, bool tc_layers = false, float* xstar = nullptr) {
   const Plan* tc = tc_layers ? &pl : nullptr;
   RowsCtx c = ctx_of(net, dom, bt, pl, r0, Rc);
   const int L = net->L;
@@ -209,6 +257,7 @@ static int chunk_simt(bcrown_net* net, const bcrown_domain* dom, const bcrown_ba
     ProfScope ps(net, BCROWN_PROF_CONCRETIZE, s);
     launch_concretize(cert, c, net->d[0], pl.Abuf[0], pl.cf, pl.cd, pl.E, lb, s);
   }
+  if (xstar) launch_xstar(c, net->d[0], pl.Abuf[0], xstar + (size_t)r0 * net->d[0], s);
   if (!grad) return BCROWN_OK;
   launch_xstar(c, net->d[0], pl.Abuf[0], pl.Z0, s);
   float* h = pl.Z0;
@@ -228,9 +277,13 @@ static int run_bound(bcrown_net* net, const bcrown_domain* dom, const bcrown_bat
                      bool grad, const float* alpha, const float* beta, float* lb, float* dalpha, float* dbeta,
                      cudaStream_t s, bool tc_plan = true) {
   const int R = bt->B * net->K;
-  if (precision == BCROWN_BF16 && tc_supported(net)) {
+  net->launch_now = precision == BCROWN_BF16 ? resolve_launch(net, R) : bcrown_net::Launch{};
+  const int path = net->launch_now.path;
+  if (path == BCROWN_PATH_FUSED) {
     return tc_bound(net, dom, bt, pl.tb, pl.tc_ws, pl.tc_ws_bytes, grad, tc_plan, alpha, beta, lb, dalpha, dbeta, s);
   }
+  if (path == BCROWN_PATH_LAYER_EPI && pl.lt_ws)
+    return lt_bound(net, dom, bt, pl.tb, pl.lt_ws, pl.lt_ws_bytes, grad, alpha, beta, lb, dalpha, dbeta, s);
   bool cert = precision == BCROWN_CERTIFY;
   // BF16 beyond the fused kernel (conv layers, wide fc layers): the contractions on the tensor
   // cores, the rest of the layer-by-layer path in FP32; planned when the plan has an im2col buffer
@@ -242,11 +295,25 @@ static int run_bound(bcrown_net* net, const bcrown_domain* dom, const bcrown_bat
   return BCROWN_OK;
 }
 
-// im2col bytes per row for the BF16 layer-by-layer path (0: not taken; the fused kernel or FP32).
-static size_t layer_tc_col(bcrown_net* net, int precision) {
+// The BF16 layer-by-layer path with fused epilogues: workspace bytes (0: not taken).
+static size_t layer_lt_bytes(bcrown_net* net, int precision, int R, int P, int64_t n_alpha, bool grad) {
+  return bf16_path(net, precision, R) == BCROWN_PATH_LAYER_EPI ? lt_workspace_bytes(net, R, P, n_alpha, grad) : 0;
+}
+
+// im2col bytes per row for the older BF16 layer path (GEMMs only, FP32 epilogue kernels), taken
+// for networks the fused-epilogue path does not take (0: not taken).
+static size_t layer_tc_col(bcrown_net* net, int precision, int R) {
   // at least 16 bytes, so that the plan's col pointer also marks the path taken
-  return precision == BCROWN_BF16 && !tc_supported(net) && tcg_supported(net)
-             ? std::max<size_t>(tcg_col_bytes_per_row(net), 16)
+  const int path = bf16_path(net, precision, R);
+  return path == BCROWN_PATH_LAYER_GATHER || path == BCROWN_PATH_LAYER_IM2COL
+             ? std::max<size_t>(tcg_col_bytes_per_row(net, path == BCROWN_PATH_LAYER_GATHER), 16)
+             : 0;
+}
+
+// Workspace of the fused kernel (0 unless the call takes it).
+static size_t fused_bytes(bcrown_net* net, int precision, const bcrown_batch* bt, int P, bool grad) {
+  return bf16_path(net, precision, (long long)bt->B * net->K) == BCROWN_PATH_FUSED
+             ? tc_workspace_bytes(net, bt->B, P, grad)
              : 0;
 }
 
@@ -254,7 +321,7 @@ static int check_precision(bcrown_net* net, int precision, bool grad) {
   if (precision != BCROWN_FP32 && precision != BCROWN_BF16 && precision != BCROWN_CERTIFY)
     return fail(BCROWN_ERR_ARG, "unknown precision");
   if (grad && precision == BCROWN_CERTIFY) return fail(BCROWN_ERR_ARG, "gradient in CERTIFY precision is not offered");
-  if (precision == BCROWN_BF16 && !tc_supported(net) && !tcg_supported(net))
+  if (precision == BCROWN_BF16 && resolve_launch(net, 1).path == 0)
     return fail(BCROWN_ERR_UNIMPLEMENTED,
                 "BF16 tensor-core path needs conv layers of at most 256 channels (and K = channels x taps <= 2048) "
                 "and fc layers of at most 65536 neurons");
@@ -275,9 +342,9 @@ extern "C" int bcrown_bound(bcrown_net* net, const bcrown_domain* dom, const bcr
   cudaStream_t s = (cudaStream_t)stream;
   Plan pl;
   int R = batch->B * net->K;
-  size_t tcb = precision == BCROWN_BF16 ? tc_workspace_bytes(net, batch->B, dom->n_props, false) : 0;
+  size_t tcb = fused_bytes(net, precision, batch, dom->n_props, false);
   BC_CHECK(make_plan(net, dom->n_props, R, precision == BCROWN_CERTIFY, false, 0, 0, tcb, pl,
-                     layer_tc_col(net, precision)));
+                     layer_tc_col(net, precision, R), layer_lt_bytes(net, precision, R, dom->n_props, batch->n_alpha, false)));
   build_tables(net, dom, pl, s);
   if (precision == BCROWN_CERTIFY) build_wm(net, dom, pl, s);
   BC_CHECK(run_bound(net, dom, batch, pl, precision, false, alpha, beta, lb, nullptr, nullptr, s));
@@ -299,9 +366,9 @@ extern "C" int bcrown_bound_grad(bcrown_net* net, const bcrown_domain* dom, cons
   cudaStream_t s = (cudaStream_t)stream;
   Plan pl;
   int R = batch->B * net->K;
-  size_t tcb = precision == BCROWN_BF16 ? tc_workspace_bytes(net, batch->B, dom->n_props, true) : 0;
+  size_t tcb = fused_bytes(net, precision, batch, dom->n_props, true);
   BC_CHECK(make_plan(net, dom->n_props, R, false, false, 0, 0, tcb, pl,
-                     layer_tc_col(net, precision)));
+                     layer_tc_col(net, precision, R), layer_lt_bytes(net, precision, R, dom->n_props, batch->n_alpha, true)));
   build_tables(net, dom, pl, s);
   BC_CHECK(run_bound(net, dom, batch, pl, precision, true, alpha, beta, lb, dalpha, dbeta, s));
   BC_CUDA(cudaGetLastError());
@@ -328,13 +395,13 @@ extern "C" int bcrown_optimize(bcrown_net* net, const bcrown_domain* dom, const 
   const int R = batch->B * net->K;
   const int64_t na = batch->n_alpha, nb = batch->n_beta;
   Plan pl;
-  size_t tcb = cfg->precision == BCROWN_BF16 ? tc_workspace_bytes(net, batch->B, dom->n_props, true) : 0;
+  size_t tcb = fused_bytes(net, cfg->precision, batch, dom->n_props, true);
   bool cert = cfg->certify != 0;
   BC_CHECK(make_plan(net, dom->n_props, R, cert, true, na, nb, tcb, pl,
-                     layer_tc_col(net, cfg->precision)));
+                     layer_tc_col(net, cfg->precision, R), layer_lt_bytes(net, cfg->precision, R, dom->n_props, na, true)));
   build_tables(net, dom, pl, s);
   if (cert) build_wm(net, dom, pl, s);
-  const bool fused16 = cfg->precision == BCROWN_BF16 && tc_supported(net);
+  const bool fused16 = bf16_path(net, cfg->precision, R) == BCROWN_PATH_FUSED;
   // the BF16 path keeps alpha's gradient and moments in BF16 (the first half of each buffer)
   __nv_bfloat16* ma16 = reinterpret_cast<__nv_bfloat16*>(pl.ma);
   __nv_bfloat16* va16 = reinterpret_cast<__nv_bfloat16*>(pl.va);
@@ -371,6 +438,9 @@ extern "C" int bcrown_optimize(bcrown_net* net, const bcrown_domain* dom, const 
   else
     launch_fill(pl.best_lb, R, -INFINITY, s);
   BatchView bv = view_of(batch);
+  // a frozen group takes zero steps (the Adam kernels then leave an iterate inside its box as it was)
+  const float lr_a0 = (cfg->freeze & BCROWN_FREEZE_ALPHA) ? 0.f : cfg->lr_alpha;
+  const float lr_b0 = (cfg->freeze & BCROWN_FREEZE_BETA) ? 0.f : cfg->lr_beta;
   for (int it = 0; it < cfg->iters; ++it) {
     const int t = t0 + it;   // iteration index of the whole ascent (learning-rate decay, bias correction)
     float fac = std::pow(cfg->decay, (float)t);
@@ -384,7 +454,7 @@ extern "C" int bcrown_optimize(bcrown_net* net, const bcrown_domain* dom, const 
       ProfScope ps(net, BCROWN_PROF_ADAM, s);
       launch_adam16(R, net->K, bv, pl.U, dom->n_props, pl.lb_t, pl.best_lb, pl.a_cur, alpha, ga16,
                     ma16, va16, pl.b_cur, beta,
-                    pl.gb, pl.mb, pl.vb, cfg->lr_alpha * fac, cfg->lr_beta * fac, cfg->adam_beta1, cfg->adam_beta2,
+                    pl.gb, pl.mb, pl.vb, lr_a0 * fac, lr_b0 * fac, cfg->adam_beta1, cfg->adam_beta2,
                     cfg->adam_eps, bc1, bc2, na, nb, s);
       continue;
     }
@@ -392,7 +462,7 @@ extern "C" int bcrown_optimize(bcrown_net* net, const bcrown_domain* dom, const 
                        it == 0));
     ProfScope ps(net, BCROWN_PROF_ADAM, s);
     launch_adam(R, net->K, bv, pl.U, dom->n_props, pl.lb_t, pl.best_lb, pl.a_cur, alpha, pl.ga, pl.ma, pl.va,
-                pl.b_cur, beta, pl.gb, pl.mb, pl.vb, cfg->lr_alpha * fac, cfg->lr_beta * fac, cfg->adam_beta1,
+                pl.b_cur, beta, pl.gb, pl.mb, pl.vb, lr_a0 * fac, lr_b0 * fac, cfg->adam_beta1,
                 cfg->adam_beta2, cfg->adam_eps, bc1, bc2, na, nb, s);
   }
   if (state) {
@@ -513,5 +583,164 @@ extern "C" int bcrown_batch_split(bcrown_net* net, const bcrown_domain* dom, con
   launch_split(view_of(parent), net->K, pl.U, dom->n_props, pick_layer, pick_idx, alpha, beta, c_prop, c_off, c_cnt,
                c_aoff, c_layer, c_idx, c_sign, c_alpha, c_beta, net->status, s);
   BC_CUDA(cudaGetLastError());
+  return BCROWN_OK;
+}
+
+extern "C" int bcrown_bound_xstar(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* batch,
+                                  const float* alpha, const float* beta, float* lb, float* xstar, void* stream) {
+  if (!net) return fail(BCROWN_ERR_ARG, "bound_xstar: null net");
+  BC_CHECK(check_domain(net, dom));
+  BC_CHECK(check_batch(batch));
+  if (batch->B == 0) return BCROWN_OK;
+  if (!lb || !xstar) return fail(BCROWN_ERR_ARG, "bound_xstar: null output");
+  std::lock_guard<std::mutex> g(net->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  Plan pl;
+  const int R = batch->B * net->K;
+  BC_CHECK(make_plan(net, dom->n_props, R, false, false, 0, 0, 0, pl));
+  build_tables(net, dom, pl, s);
+  for (int r0 = 0; r0 < R; r0 += pl.Rc) {
+    const int Rc = std::min(pl.Rc, R - r0);
+    BC_CHECK(chunk_simt(net, dom, batch, pl, r0, Rc, false, false, alpha, beta, lb, nullptr, nullptr, s, false, xstar));
+  }
+  BC_CUDA(cudaGetLastError());
+  return BCROWN_OK;
+}
+
+extern "C" int bcrown_forward(bcrown_net* net, int n, const float* x, float* out, void* stream) {
+  if (!net || n < 0) return fail(BCROWN_ERR_ARG, "forward: bad argument");
+  if (n == 0) return BCROWN_OK;
+  if (!x || !out) return fail(BCROWN_ERR_ARG, "forward: null pointer");
+  std::lock_guard<std::mutex> g(net->mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  Plan pl;
+  BC_CHECK(make_plan(net, 1, n, false, false, 0, 0, 0, pl));
+  const int L = net->L;
+  for (int r0 = 0; r0 < n; r0 += pl.Rc) {
+    const int Rc = std::min(pl.Rc, n - r0);
+    const float* h = x + (size_t)r0 * net->d[0];
+    float* z = pl.Z0;
+    float* other = pl.Z1;
+    for (int i = 1; i <= L - 1; ++i) {
+      BC_CHECK(contract_fwd(net, i, Rc, h, z, s));
+      launch_relu(z, (long long)Rc * net->d[i], s);
+      h = z;
+      std::swap(z, other);
+    }
+    launch_spec_out(Rc, net->K, net->d[L - 1], h, net->Wbar, net->bbar, out + (size_t)r0 * net->K, s);
+  }
+  BC_CUDA(cudaGetLastError());
+  return BCROWN_OK;
+}
+
+// ---- launch configuration and the autotuner ----
+
+static bool known_path(int path) { return path >= BCROWN_PATH_DEFAULT && path <= BCROWN_PATH_LAYER_IM2COL; }
+
+extern "C" int bcrown_path_supported(bcrown_net* net, int path) {
+  if (!net || !known_path(path) || path == BCROWN_PATH_DEFAULT) return 0;
+  return path_ok(net, path) ? 1 : 0;
+}
+
+extern "C" int bcrown_set_launch(bcrown_net* net, const bcrown_launch_cfg* cfg) {
+  if (!net || !cfg) return fail(BCROWN_ERR_ARG, "set_launch: null argument");
+  if (!known_path(cfg->path) || cfg->grid_per_sm < 0 || cfg->grid_per_sm > 32)
+    return fail(BCROWN_ERR_ARG, "set_launch: unknown path or grid_per_sm outside 0..32");
+  if (cfg->path != BCROWN_PATH_DEFAULT && !path_ok(net, cfg->path))
+    return fail(BCROWN_ERR_UNIMPLEMENTED, "set_launch: the net cannot take this path");
+  std::lock_guard<std::mutex> g(net->mu);
+  net->launch_set.path = cfg->path;
+  net->launch_set.grid_per_sm = cfg->grid_per_sm;
+  return BCROWN_OK;
+}
+
+extern "C" int bcrown_get_launch(bcrown_net* net, int rows, bcrown_launch_cfg* cfg) {
+  if (!net || !cfg || rows < 0) return fail(BCROWN_ERR_ARG, "get_launch: bad argument");
+  std::lock_guard<std::mutex> g(net->mu);
+  const bcrown_net::Launch l = resolve_launch(net, std::max(rows, 1));
+  cfg->path = l.path;
+  cfg->grid_per_sm = l.grid_per_sm;
+  return BCROWN_OK;
+}
+
+extern "C" int bcrown_autotune(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* batch,
+                               const float* alpha, const float* beta, int reps, bcrown_launch_cfg* cands,
+                               double* ms, int max_cands, int* n_cands, bcrown_launch_cfg* best, void* stream) {
+  if (!net || !batch || !best || reps < 1 || max_cands < 0) return fail(BCROWN_ERR_ARG, "autotune: bad argument");
+  BC_CHECK(check_domain(net, dom));
+  BC_CHECK(check_batch(batch));
+  if (batch->B == 0) return fail(BCROWN_ERR_ARG, "autotune: empty batch");
+  const long long R = (long long)batch->B * net->K;
+  // candidates: every supported path; the layer GEMM paths with 1 and 2 CTAs per SM
+  std::vector<bcrown_net::Launch> cand;
+  for (int p : {BCROWN_PATH_FUSED, BCROWN_PATH_LAYER_EPI, BCROWN_PATH_LAYER_GATHER, BCROWN_PATH_LAYER_IM2COL}) {
+    if (!path_ok(net, p)) continue;
+    const bool grid = p == BCROWN_PATH_LAYER_GATHER || p == BCROWN_PATH_LAYER_IM2COL;
+    for (int g : grid ? std::vector<int>{1, 2} : std::vector<int>{0}) {
+      bcrown_net::Launch l;
+      l.path = p;
+      l.grid_per_sm = g;
+      cand.push_back(l);
+    }
+  }
+  if (cand.empty()) return fail(BCROWN_ERR_UNIMPLEMENTED, "autotune: the net takes no BF16 path");
+  cudaStream_t s = (cudaStream_t)stream;
+  float *lb = nullptr, *da = nullptr, *dbt = nullptr;
+  BC_CUDA(cudaMalloc(&lb, (size_t)R * 4));
+  if (cudaMalloc(&da, std::max<size_t>(batch->n_alpha, 1) * 4) != cudaSuccess ||
+      cudaMalloc(&dbt, std::max<size_t>(batch->n_beta, 1) * 4) != cudaSuccess) {
+    cudaFree(lb);
+    cudaFree(da);
+    return fail(BCROWN_ERR_OOM, "autotune: outputs");
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const bcrown_net::Launch saved = net->launch_set;
+  std::vector<double> t(cand.size(), 0.0);
+  int rc = BCROWN_OK;
+  for (size_t c = 0; c < cand.size() && rc == BCROWN_OK; ++c) {
+    {
+      std::lock_guard<std::mutex> g(net->mu);
+      net->launch_set = cand[c];
+      // the tuner's earlier choice for this bucket would take precedence: drop it while timing
+      const int bk = bucket_of(R);
+      net->tuned.erase(std::remove_if(net->tuned.begin(), net->tuned.end(),
+                                      [bk](const std::pair<int, bcrown_net::Launch>& x) { return x.first == bk; }),
+                       net->tuned.end());
+    }
+    rc = bcrown_bound_grad(net, dom, batch, alpha, beta, BCROWN_BF16, lb, da, dbt, stream);   // untimed
+    if (rc != BCROWN_OK) break;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < reps && rc == BCROWN_OK; ++r)
+      rc = bcrown_bound_grad(net, dom, batch, alpha, beta, BCROWN_BF16, lb, da, dbt, stream);
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) rc = fail(BCROWN_ERR_CUDA, "autotune: timing");
+    float el = 0.f;
+    cudaEventElapsedTime(&el, e0, e1);
+    t[c] = (double)el / reps;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(lb);
+  cudaFree(da);
+  cudaFree(dbt);
+  std::lock_guard<std::mutex> g(net->mu);
+  net->launch_set = saved;
+  if (rc != BCROWN_OK) return rc;
+  size_t bi = 0;
+  for (size_t c = 1; c < cand.size(); ++c)
+    if (t[c] < t[bi]) bi = c;
+  net->tuned.emplace_back(bucket_of(R), cand[bi]);
+  best->path = cand[bi].path;
+  best->grid_per_sm = cand[bi].grid_per_sm;
+  for (size_t c = 0; c < cand.size() && (int)c < max_cands; ++c) {
+    if (cands) {
+      cands[c].path = cand[c].path;
+      cands[c].grid_per_sm = cand[c].grid_per_sm;
+    }
+    if (ms) ms[c] = t[c];
+  }
+  if (n_cands) *n_cands = (int)cand.size();
   return BCROWN_OK;
 }

@@ -81,6 +81,15 @@ struct bcrown_net {
   float* Wbar_err = nullptr;          // [K][d_{L-1}], bound on |Wbar - exact C W^(L)|
   __nv_bfloat16* Wbar_bf = nullptr;   // [K][d_{L-1}]
   int* status = nullptr;              // device status word
+  // BF16 launch configuration: the caller's choice (bcrown_set_launch; path 0 = the built-in
+  // order) and the tuner's per row-count bucket (bcrown_autotune), looked up on every call
+  struct Launch {
+    int path = 0;
+    int grid_per_sm = 0;
+  };
+  Launch launch_set;
+  std::vector<std::pair<int, Launch>> tuned;   // (bucket = ceil(log2 rows), choice)
+  Launch launch_now;                           // the configuration of the call in progress
   bcrown::Workspace ws;
   std::mutex mu;
   // timing hook (bcrown_profile)

@@ -431,12 +431,9 @@ __global__ void __launch_bounds__(TcgRoles<GATHER>::THREADS, 1)
 
 using namespace tc;
 
-// Conv passes gather their operand inside the GEMM kernel (true) or through an im2col buffer
-// in HBM (false; BCROWN_CONV_IM2COL=1 in the environment selects it, for comparison).
-static const bool g_tcg_gather = [] {
-  const char* e = getenv("BCROWN_CONV_IM2COL");
-  return !(e && e[0] == '1');
-}();
+// Conv passes gather their operand inside the GEMM kernel, except on BCROWN_PATH_LAYER_IM2COL
+// (an im2col buffer in HBM read by TMA), the configuration of the call in progress.
+static bool tcg_gather(const bcrown_net* net) { return net->launch_now.path != BCROWN_PATH_LAYER_IM2COL; }
 
 namespace {
 
@@ -517,7 +514,7 @@ bool tcg_supported(const bcrown_net* net) {
   return major == 10 && minor == 3;
 }
 
-size_t tcg_col_bytes_per_row(const bcrown_net* net) {
+size_t tcg_col_bytes_per_row(const bcrown_net* net, bool gather) {
   size_t b = 0;
   for (int i = 0; i < net->L - 1; ++i) {
     const LayerDev& l = net->ly[i];
@@ -525,7 +522,7 @@ size_t tcg_col_bytes_per_row(const bcrown_net* net) {
       b = std::max(b, (size_t)std::max(pad_to(l.d_in, 64), pad_to(l.d_out, 64)) * sizeof(__nv_bfloat16));
       continue;
     }
-    if (g_tcg_gather) continue;   // conv operands are gathered in shared memory
+    if (gather) continue;   // conv operands are gathered in shared memory
     const size_t ph = (size_t)((l.in_h + l.stride - 1) / l.stride) * ((l.in_w + l.stride - 1) / l.stride);
     const size_t bwd = ph * kp_bwd(l);
     const size_t fwd = (size_t)l.out_h * l.out_w * kp_fwd(l);
@@ -648,8 +645,9 @@ static int tcg_pass(bcrown_net* net, const Im2colPass& q, const CUtensorMap& mB,
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const long long ntiles = (q.M + 127) / 128 * o.ntn;
-  const int grid = (int)std::min<long long>(ntiles, 2LL * sms);
-  if (q.tab && g_tcg_gather) {
+  const int gps = net->launch_now.grid_per_sm > 0 ? net->launch_now.grid_per_sm : 2;   // CTAs per SM
+  const int grid = (int)std::min<long long>(ntiles, (long long)gps * sms);
+  if (q.tab && tcg_gather(net)) {
     // conv layers: the gather warps build the operand in shared memory (mapA unused)
     const int smem = tcg_smem(o.Np, o.N, bias != nullptr, q.Kp);
     k_tcg<true><<<grid, TcgRoles<true>::THREADS, smem, s>>>(mB, mB, o, q, src, dst, bias, net->status);

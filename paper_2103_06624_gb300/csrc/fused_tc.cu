@@ -9,7 +9,7 @@
 // The weight tile is the MMA's A operand (loaded by TMA, 128B swizzle, K-major) and the
 // activations Lambda^T are its B operand (written to shared memory by the epilogue in the
 // same swizzled layout).  Putting neurons on TMEM lanes makes every epilogue access to
-// alpha, the per-neuron tables, Adam state and the stash coalesced across a warp.
+// alpha, the per-neuron tables, the gradients and the stash coalesced across a warp.
 //
 // The epilogue (16 warps) reads the accumulator with tcgen05.ld, applies the relaxation of
 // Lemma 2.1 / Eq. definition_D (split overriding stability), the beta shift and the bias
@@ -17,8 +17,9 @@
 // as the next contraction's operand.  The last contraction is concretised over the box
 // (Eq. beta_crown_lp).  With a gradient requested the adjoint pass follows in the same
 // launch: zhat^(i) = W^(i) h^(i-1) + b^(i) along h^(0) = x*, dalpha = A zhat, dbeta = S zhat,
-// h = D zhat + lambda; in optimiser mode the projected Adam step (Appendix C.1) and the
-// per-row best tracking are applied to alpha and beta in that epilogue.
+// h = D zhat + lambda.  The kernel writes the gradients only: the projected Adam step
+// (Appendix C.1) and the per-row best tracking run afterwards in a separate element-wise
+// kernel over alpha and beta.
 //
 // Roles: warps 0-15 epilogue, warp 16 TMA producer, warp 17 MMA issuer (one lane each).
 // Every mbarrier wait is bounded; on expiry the kernel records BCROWN_ERR_TIMEOUT, stops

@@ -8,6 +8,8 @@
 #include "bcrown_internal.cuh"
 #include "conv_tc.cuh"
 #include "fused_tc.cuh"
+#include "layer_tc.cuh"
+#include "simt.cuh"
 
 namespace bcrown {
 
@@ -53,16 +55,27 @@ static cudaEvent_t pool_event(bcrown_net* net) {
   return e;
 }
 
+// Under stream capture an ordinary record only orders the captured work; an external record
+// becomes an event node of the graph, recorded at every replay (so that a scope captured into
+// a graph times the kernels of the latest replay).
+static void prof_record(cudaEvent_t e, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+    cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+  else
+    cudaEventRecord(e, s);
+}
+
 ProfScope::ProfScope(bcrown_net* n, int cls, cudaStream_t st) : net(n), s(st) {
   if (!net->prof_on) return;
   bcrown_net::ProfRec r{cls, pool_event(net), pool_event(net)};
-  cudaEventRecord(r.a, s);
+  prof_record(r.a, s);
   net->prof.push_back(r);
   idx = (int)net->prof.size() - 1;
 }
 
 ProfScope::~ProfScope() {
-  if (idx >= 0) cudaEventRecord(net->prof[idx].b, s);
+  if (idx >= 0) prof_record(net->prof[idx].b, s);
 }
 
 static void prof_clear(bcrown_net* net) {
@@ -105,6 +118,8 @@ extern "C" void bcrown_free_net(bcrown_net* net) {
   cudaDeviceSynchronize();
   tc_release(net);
   tcg_release(net);
+  lt_release(net);
+  sconv_release(net);
   for (auto& l : net->ly) {
     cudaFree(l.W);
     cudaFree(l.Wt);
@@ -249,6 +264,9 @@ extern "C" int bcrown_load_net(const bcrown_layer* layers, int n_layers, const f
     if (e == cudaSuccess) e = cudaMemset(net->status, 0, sizeof(int));
     if (e != cudaSuccess) st = fail(BCROWN_ERR_CUDA, std::string("status word: ") + cudaGetErrorString(e));
   }
+  // the FP32 convolutions' phase weights and gather tables, built here so that no later call
+  // (the allocation-free bound included) allocates them
+  if (st == BCROWN_OK) st = sconv_load(net);
   if (st != BCROWN_OK) {
     bcrown_free_net(net);
     return st;

@@ -1638,6 +1638,34 @@ void launch_fill(float* p, long long n, float v, cudaStream_t s) {
   if (n > 0) { k_fill<<<grid1d(n, 256), 256, 0, s>>>(p, n, v); ++g_launches; }
 }
 
+// ReLU in place (the plain network evaluation of bcrown_forward).
+__global__ void k_relu(float* __restrict__ z, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) z[i] = fmaxf(z[i], 0.f);
+}
+void launch_relu(float* z, long long n, cudaStream_t s) {
+  if (n > 0) { k_relu<<<grid1d(n, 256), 256, 0, s>>>(z, n); ++g_launches; }
+}
+
+// out[r][k] = bbar_k + sum_j h[r][j] Wbar[k][j] (the specifications merged into the last layer):
+// one warp per (row, spec).
+__global__ void k_spec_out(int R, int K, int d, const float* __restrict__ h, const float* __restrict__ Wbar,
+                           const float* __restrict__ bbar, float* __restrict__ out) {
+  const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= (long long)R * K) return;
+  const int r = (int)(w / K), k = (int)(w - (long long)r * K);
+  float acc = 0.f;
+  for (int j = lane; j < d; j += 32) acc = fmaf(h[(size_t)r * d + j], Wbar[(size_t)k * d + j], acc);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) out[w] = acc + bbar[k];
+}
+void launch_spec_out(int R, int K, int d, const float* h, const float* Wbar, const float* bbar, float* out,
+                     cudaStream_t s) {
+  const long long n = (long long)R * K * 32;
+  if (n > 0) { k_spec_out<<<grid1d(n, 256), 256, 0, s>>>(R, K, d, h, Wbar, bbar, out); ++g_launches; }
+}
+
 // FP32 <-> BF16 copies (the BF16 optimiser keeps alpha's moments in BF16 inside a call).
 __global__ void k_f32_to_bf16(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst, long long n) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;

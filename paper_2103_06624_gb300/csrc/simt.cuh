@@ -49,6 +49,17 @@ void launch_concretize_root(bool cert, int q0, int Rc, int p, int d0, int d_top,
                             const float* x_lo, const float* x_hi, const float* A0, const float* cf, const double* cd,
                             const double* E, float* l, float* u, cudaStream_t s);
 void launch_fill(float* p, long long n, float v, cudaStream_t s);
+// FP32 implicit-GEMM convolutions (conv_f32.cu): the transposed convolution of conv layer i split
+// into stride phases (backward), and the convolution plus bias (forward), for R rows.
+constexpr int SCONV_MAX_K = 4096;   // terms per output the staged gather table holds
+bool sconv_supported(const bcrown_net* net, int i);
+int sconv_load(bcrown_net* net);   // builds the tables (at bcrown_load_net)
+int sconv_bwd(bcrown_net* net, int i, int R, const float* Lam, float* Ain, cudaStream_t s);
+int sconv_fwd(bcrown_net* net, int i, int R, const float* h, float* Z, const float* bias, cudaStream_t s);
+void sconv_release(const bcrown_net* net);
+void launch_relu(float* z, long long n, cudaStream_t s);
+void launch_spec_out(int R, int K, int d, const float* h, const float* Wbar, const float* bbar, float* out,
+                     cudaStream_t s);
 void launch_f32_to_bf16(const float* src, __nv_bfloat16* dst, long long n, cudaStream_t s);
 void launch_bf16_to_f32(const __nv_bfloat16* src, float* dst, long long n, cudaStream_t s);
 void launch_copy_count(int P, int H, const int32_t* U, int32_t* out, cudaStream_t s);

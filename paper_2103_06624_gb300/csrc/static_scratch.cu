@@ -121,6 +121,8 @@ extern "C" int bcrown_bound_static(bcrown_net* net, const bcrown_domain* dom, co
                    batch->n_beta, cf, nullptr, nullptr, nullptr, 0.0, s);
       if (ly.kind == BCROWN_LAYER_FC)
         launch_sgemm(c.R, ly.d_in, ly.d_out, Lam, ly.d_out, ly.W, ly.d_in, A[i - 1], ly.d_in, nullptr, s);
+      else if (sconv_supported(net, i))
+        BC_CHECK(sconv_bwd(net, i, c.R, Lam, A[i - 1], s));   // tables built at load: no allocation
       else
         launch_conv_bwd(c.R, geom_of(ly), Lam, ly.W, A[i - 1], s);
     }

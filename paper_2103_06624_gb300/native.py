@@ -20,8 +20,15 @@ MAX_SPLITS = 64
 EXPORTS = ["bcrown_load_net", "bcrown_free_net", "bcrown_net_info", "bcrown_root_bounds", "bcrown_bound",
            "bcrown_bound_grad", "bcrown_optimize", "bcrown_batch_split", "bcrown_neuron_codes",
            "bcrown_status", "bcrown_last_error", "bcrown_profile", "bcrown_profile_read",
-           "bcrown_kernel_launches", "bcrown_bound_static", "bcrown_peak_probe"]
-PROF_CONTRACT, PROF_RELAX, PROF_CONCRETIZE, PROF_ADJOINT, PROF_ADAM, PROF_FUSED = range(6)
+           "bcrown_kernel_launches", "bcrown_bound_static", "bcrown_peak_probe", "bcrown_bound_xstar",
+           "bcrown_forward", "bcrown_path_supported", "bcrown_set_launch", "bcrown_get_launch",
+           "bcrown_autotune", "bcrown_joint_sizes", "bcrown_joint_init_alpha", "bcrown_bound_joint",
+           "bcrown_bound_joint_grad", "bcrown_optimize_joint"]
+FREEZE_ALPHA, FREEZE_BETA = 1, 2
+PATH_DEFAULT, PATH_FUSED, PATH_LAYER_EPI, PATH_LAYER_GATHER, PATH_LAYER_IM2COL = range(5)
+PATH_NAMES = {PATH_FUSED: "fused", PATH_LAYER_EPI: "layer_epi", PATH_LAYER_GATHER: "layer_gather",
+              PATH_LAYER_IM2COL: "layer_im2col"}
+PROF_CONTRACT, PROF_RELAX, PROF_CONCRETIZE, PROF_ADJOINT, PROF_ADAM, PROF_FUSED, PROF_LAYER_GEMM = range(7)
 
 
 class Layer(C.Structure):
@@ -45,13 +52,17 @@ class Batch(C.Structure):
 class OptCfg(C.Structure):
     _fields_ = [("iters", C.c_int), ("lr_alpha", C.c_float), ("lr_beta", C.c_float), ("decay", C.c_float),
                 ("adam_beta1", C.c_float), ("adam_beta2", C.c_float), ("adam_eps", C.c_float),
-                ("precision", C.c_int), ("certify", C.c_int)]
+                ("precision", C.c_int), ("certify", C.c_int), ("freeze", C.c_int)]
 
 
 class OptState(C.Structure):
     _fields_ = [("alpha_cur", C.c_void_p), ("beta_cur", C.c_void_p), ("m_alpha", C.c_void_p),
                 ("v_alpha", C.c_void_p), ("m_beta", C.c_void_p), ("v_beta", C.c_void_p),
                 ("best_lb", C.c_void_p), ("t", C.c_int)]
+
+
+class LaunchCfg(C.Structure):
+    _fields_ = [("path", C.c_int), ("grid_per_sm", C.c_int)]
 
 
 class BcrownError(RuntimeError):
@@ -91,6 +102,22 @@ def load(path=LIB_PATH):
         "bcrown_kernel_launches": ([], C.c_longlong),
         "bcrown_bound_static": ([vp, C.POINTER(Domain), C.POINTER(Batch), vp, vp, vp, vp], i32),
         "bcrown_peak_probe": ([i32, i32, C.POINTER(C.c_double), vp], i32),
+        "bcrown_bound_xstar": ([vp, C.POINTER(Domain), C.POINTER(Batch), vp, vp, vp, vp, vp], i32),
+        "bcrown_forward": ([vp, i32, vp, vp, vp], i32),
+        "bcrown_path_supported": ([vp, i32], i32),
+        "bcrown_set_launch": ([vp, C.POINTER(LaunchCfg)], i32),
+        "bcrown_get_launch": ([vp, i32, C.POINTER(LaunchCfg)], i32),
+        "bcrown_autotune": ([vp, C.POINTER(Domain), C.POINTER(Batch), vp, vp, i32, C.POINTER(LaunchCfg),
+                             C.POINTER(C.c_double), i32, C.POINTER(i32), C.POINTER(LaunchCfg), vp], i32),
+        "bcrown_joint_sizes": ([vp, C.POINTER(Domain), C.POINTER(Batch), C.POINTER(C.c_int64),
+                                C.POINTER(C.c_int64), vp], i32),
+        "bcrown_joint_init_alpha": ([vp, C.POINTER(Domain), C.POINTER(Batch), vp, C.c_int64, vp], i32),
+        "bcrown_bound_joint": ([vp, C.POINTER(Domain), C.POINTER(Batch), vp, vp, vp, C.c_int64, vp, C.c_int64,
+                                vp, vp, vp, vp], i32),
+        "bcrown_bound_joint_grad": ([vp, C.POINTER(Domain), C.POINTER(Batch), vp, vp, vp, C.c_int64, vp,
+                                     C.c_int64, vp, vp, vp, vp, vp, vp], i32),
+        "bcrown_optimize_joint": ([vp, C.POINTER(Domain), C.POINTER(Batch), C.POINTER(OptCfg), vp, vp, vp,
+                                   C.c_int64, vp, C.c_int64, vp, vp, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)

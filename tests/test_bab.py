@@ -19,11 +19,35 @@ class OracleEngine:
         self.K = pb.K
         self.calls = 0
 
-    def optimize(self, subs, alpha, beta):
+    def optimize(self, subs, alpha, beta, iters=None, lr_alpha=None, lr_beta=None, decay=None, fp32=False):
         self.calls += 1
+        import dataclasses
+        cfg = dataclasses.replace(O.AdamCfg(), **{k: v for k, v in dict(iters=iters, lr_alpha=lr_alpha,
+                                                                         lr_beta=lr_beta, decay=decay).items()
+                                                   if v is not None})
         batch = wl.pack_batch(self.pb.hidden_widths, self.K, self.U, subs)
-        lb, a, b, _ = O.optimize(self.onet, self.props, batch, alpha, beta)
+        lb, a, b, _ = O.optimize(self.onet, self.props, batch, alpha, beta, cfg)
         return lb, a, b
+
+    def _batch(self, subs):
+        return wl.pack_batch(self.pb.hidden_widths, self.K, self.U, subs)
+
+    def bound_grad(self, subs, alpha, beta):
+        lb, da, db = O.grad(self.onet, self.props, self._batch(subs), np.asarray(alpha, np.float64),
+                            np.asarray(beta, np.float64))
+        return lb, da, db
+
+    def certify(self, subs, alpha, beta):
+        return O.bound(self.onet, self.props, self._batch(subs), alpha, beta)
+
+    def xstar(self, subs, alpha, beta):
+        batch = self._batch(subs)
+        rows = O.expand_rows(self.onet, batch, self.props["l"], self.props["u"])
+        _, tr = O.bound(self.onet, self.props, batch, alpha, beta, rows=rows, trace=True)
+        xlo = np.asarray(self.props["x_lo"], np.float64)[rows.prop]
+        xhi = np.asarray(self.props["x_hi"], np.float64)[rows.prop]
+        xs = np.where(tr.A[0] >= 0, xlo, xhi)
+        return xs, self.margins(xs)
 
     def margins(self, x):
         return np.atleast_2d(wl.reference_forward(self.pb.layers, x)) @ self.pb.C.astype(np.float64).T
@@ -83,13 +107,65 @@ def test_bab_on_the_oracle_agrees_with_exact_minima(name):
 
 
 def test_a_negative_minimum_is_never_verified_when_no_witness_is_found():
-    """Random points of the box all have positive margins and gradient descent is switched off:
-    branching must not verify the property (its exact minimum is negative), so every split is
-    made and the fully split subdomains stay open: unknown."""
+    """Random points of the box all have positive margins; gradient descent, the x* upper bound and
+    the line search are switched off: branching must not verify the property (its exact minimum
+    is negative), so every split is made and the fully split subdomains stay open: unknown."""
     pb, exact, res = run_case("violated_found_by_descent", OracleEngine, batch_size=256, max_rounds=12,
-                              n_samples=256, pgd_steps=0)
+                              n_samples=256, pgd_steps=0, upper=False, line_search=False)
     assert exact.min() < 0
     assert res.status == "unknown" and res.open_domains > 0 and res.min_lb <= 0
+
+
+@pytest.mark.parametrize("mechanism", ["upper", "line_search"])
+def test_the_upper_bound_or_the_line_search_finds_the_violation_sampling_misses(mechanism):
+    """The same net with no sampled point and no descent: the violation is found at x* of a bounded
+    subdomain (Algorithm 1's upper bound f(x*), Appendix B.1), or -- with that switched off during
+    branching -- once the fully split subdomains are maximised over beta (Theorem 3.3)."""
+    pb, exact, res = run_case("violated_found_by_descent", OracleEngine, batch_size=256, max_rounds=12,
+                              n_samples=0, pgd_steps=0, upper=(mechanism == "upper"),
+                              line_search=(mechanism == "line_search"))
+    check_verdict("violated_found_by_descent", pb, exact, res)
+    if mechanism == "line_search":
+        assert res.line_searched > 0
+
+
+def test_line_search_reaches_the_exact_minimum_of_fully_split_subdomains():
+    """Every unstable neuron split (a linear region): the beta-only ascent with its step-size search
+    reaches the exact minimum of each spec over the region (Theorem 3.3, Corollary 3.1) -- the
+    minimum found by scipy's LP over the region -- and never goes above it; rows whose minimum is
+    positive end verified, and regions whose splits contradict each other (empty) end with a
+    positive bound (Appendix B.3)."""
+    pb, props, unst, _ = make_case("violated")
+    onet = O.OracleNet(pb.layers, pb.C)
+    l, u = props["l"][0], props["u"][0]
+    U = len(unst[0])
+    offs = np.concatenate([[0], np.cumsum(pb.hidden_widths)])
+    rng = np.random.default_rng(0)
+    # the activation patterns of sampled inputs (feasible regions), and random patterns (mostly empty)
+    xs = rng.uniform(pb.x_lo[0], pb.x_hi[0], size=(8, pb.x_lo.shape[1]))
+    z = np.concatenate([zi for zi in onet.preacts(xs)[1:]], axis=1)[:, unst[0]]
+    patterns = [np.where(zi >= 0, -1, 1).astype(np.int8) for zi in z]
+    patterns += [rng.choice([-1, 1], size=U).astype(np.int8) for _ in range(6)]
+    doms = [bab.Domain(unst[0].astype(np.int64), sg, np.full(pb.K * U, 0.5, np.float32),
+                       np.zeros(pb.K * U, np.float32), np.zeros(pb.K, np.float32), 0) for sg in patterns]
+    eng = OracleEngine(pb, props, [U])
+    cert, conv = bab._line_search(eng, doms, [(0, l, u, pb.x_lo[0], pb.x_hi[0])], pb.K)
+    assert conv.all()
+    n_neg = n_empty = 0
+    for d, c in zip(doms, cert):
+        layer = np.searchsorted(offs, d.splits, side="right")
+        splits = [(int(i), int(g - offs[i - 1]), int(s)) for i, g, s in zip(layer, d.splits, d.signs)]
+        for k in range(pb.K):
+            ex = LP.exact_min(onet, pb.x_lo[0], pb.x_hi[0], l, u, splits, k)
+            if not np.isfinite(ex):
+                assert c[k] > 0      # an empty region: the dual grew without bound past zero
+                n_empty += 1
+            elif ex > 0:
+                assert 0 < c[k] <= ex + 1e-9
+            else:
+                assert ex - 1e-6 * max(1.0, abs(ex)) <= c[k] <= ex + 1e-9, (k, c[k], ex)
+                n_neg += 1
+    assert n_neg > 0 and n_empty > 0
 
 
 def test_children_inherit_alpha_and_start_the_new_beta_at_zero():

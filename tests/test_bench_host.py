@@ -14,24 +14,28 @@ import bench  # noqa: E402
 from paper_2103_06624_gb300 import workloads as wl  # noqa: E402
 
 
-def test_conv_byte_model_matches_the_per_row_figures():
-    """Conv outputs materialised once per direction in BF16, written and read: 2 * 2 * 2 bytes
-    per output neuron per row and iteration, which is 98 KB for the small conv net
-    ((8192 + 4096) outputs) and 983 KB for the large one ((65536 + 16384 + 32768 + 8192))."""
+def test_layer_path_byte_model_matches_the_per_row_figures():
+    """Lambda (backward) and h (forward) of every hidden neuron written and read once in BF16: 8 bytes
+    per hidden neuron per row and iteration, 4 per input (x*), 16 per unstable neuron and 8 per
+    split: 98 KB of activations for the small conv net ((8192 + 4096 + 512 + 512) hidden neurons)
+    and 987 KB for the large one ((65536 + 16384 + 32768 + 8192 + 512))."""
     zero = np.zeros(1)
-    for pb, outputs in ((wl.problem_conv_small(), 8192 + 4096), (wl.problem_conv_big(), 65536 + 16384 + 32768 + 8192)):
-        assert bench.layer_path_bytes_per_row_iter(pb, zero, zero)[0] == 4 + 8 * outputs
-    # state: 24 B per alpha (value, m, v read and written), 8 B per alpha of stash, 30 B per split
+    for pb, hidden in ((wl.problem_conv_small(), 8192 + 4096 + 512 + 512),
+                       (wl.problem_conv_big(), 65536 + 16384 + 32768 + 8192 + 512)):
+        assert bench.layer_gemm_bytes_per_row_iter(pb, zero, zero)[0] == 8 * hidden + 4 * 3072
     pb = wl.problem_conv_small()
-    b = bench.layer_path_bytes_per_row_iter(pb, np.array([10.0]), np.array([3.0]))[0]
-    assert b == 4 + 8 * (8192 + 4096) + 32 * 10 + 30 * 3
+    b = bench.layer_gemm_bytes_per_row_iter(pb, np.array([10.0]), np.array([3.0]))[0]
+    assert b == 8 * (8192 + 4096 + 1024) + 4 * 3072 + 16 * 10 + 8 * 3
 
 
-def test_fused_flop_model():
+def test_flop_models():
     # 784-256x6-10: one backward pass of one row contracts layers 1..L-1
-    widths = wl.problem_mlp_784().widths
-    f = bench.algorithmic_flops_per_row_pass(widths)
-    assert f == 2 * (784 * 256 + 5 * 256 * 256)
+    assert bench.algorithmic_flops_per_row_pass(wl.problem_mlp_784().layers) == 2 * (784 * 256 + 5 * 256 * 256)
+    # the precision workload's conv net: 87.4 MFLOP per row and pass (conv 3->64, 64->64 s2,
+    # 64->128, 128->128 s2, all 3x3, then fc 8192->512)
+    f = bench.algorithmic_flops_per_row_pass(wl.problem_conv_big().layers)
+    assert f == 2 * (64 * 1024 * 3 * 9 + 64 * 256 * 64 * 9 + 128 * 256 * 64 * 9 + 128 * 64 * 128 * 9 + 512 * 8192)
+    assert abs(f - 87.4e6) < 0.1e6
 
 
 def test_workload_table_builds_each_problem():

@@ -281,35 +281,63 @@ def test_bf16_wide_mlp_runs_every_contraction_as_a_tensor_core_gemm():
     assert np.all(lbc <= ref_opt + 1e-12 * np.abs(ref_opt))
 
 
-def test_bf16_conv_im2col_buffer_path_matches_oracle():
-    """The comparison path for conv layers (BCROWN_CONV_IM2COL=1: the im2col operand written to
-    HBM by one kernel and read by TMA in the GEMM, instead of gathered inside the GEMM) on the
-    tiny conv nets, in a child process since the switch is read when the library loads."""
-    import os
-    import subprocess
-    import sys
-    script = (
-        "import numpy as np, torch\n"
-        "from tests.test_gpu_tc import _tiny_conv, _gpu, _t, _scale, BF16_TOL\n"
-        "from tests.helpers import oracle_setup\n"
-        "from oracle import bcrown_oracle as O\n"
-        "from paper_2103_06624_gb300 import bcrown as bc, workloads as wl\n"
-        "for which in ['tiny', 'tiny_odd', 'tiny_s3']:\n"
-        "    pb = _tiny_conv(which)\n"
-        "    onet, props, unst = oracle_setup(pb)\n"
-        "    batch = wl.random_batch(pb, unst, 24, 0, 4, 1, props=np.arange(24) % 2)\n"
-        "    a, b = wl.random_alpha_beta(batch, 3, 1.0)\n"
-        "    net, dom, db = _gpu(pb, props, batch)\n"
-        "    lb = bc.bound(net, dom, db, _t(a), _t(b), bc.BF16).cpu().numpy()\n"
-        "    assert bc.status(net) == 0\n"
-        "    ref = O.bound(onet, props, batch, a, b)\n"
-        "    assert (np.abs(lb - ref) / _scale(ref)).max() <= BF16_TOL[which], which\n"
-        "print('ok')\n")
-    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    env = dict(os.environ, BCROWN_CONV_IM2COL="1")
-    r = subprocess.run([sys.executable, "-c", script], cwd=root, env=env, capture_output=True, text=True,
-                       timeout=600)
-    assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
+LAYER_PATHS = {"layer_epi": bc.N.PATH_LAYER_EPI, "layer_gather": bc.N.PATH_LAYER_GATHER,
+               "layer_im2col": bc.N.PATH_LAYER_IM2COL}
+
+
+@pytest.mark.parametrize("path", list(LAYER_PATHS))
+def test_every_layer_path_matches_oracle_on_the_tiny_conv_nets(path):
+    """Each BF16 layer path chosen explicitly (GEMM epilogues; gather GEMMs with FP32 kernels between
+    them; the im2col buffer in HBM read by TMA): bound and gradient against the oracle."""
+    for which in ["tiny", "tiny_odd", "tiny_s3"]:
+        pb = _tiny_conv(which)
+        onet, props, unst = oracle_setup(pb)
+        batch = wl.random_batch(pb, unst, 24, 0, 4, 1, props=np.arange(24) % 2)
+        a, b = wl.random_alpha_beta(batch, 3, 1.0)
+        net, dom, db = _gpu(pb, props, batch)
+        assert bc.path_supported(net, LAYER_PATHS[path])
+        bc.set_launch(net, LAYER_PATHS[path])
+        assert bc.get_launch(net, batch.B * pb.K)[0] == LAYER_PATHS[path]
+        lb = bc.bound(net, dom, db, _t(a), _t(b), bc.BF16).cpu().numpy()
+        assert bc.status(net) == 0
+        ref = O.bound(onet, props, batch, a, b)
+        err = np.abs(lb - ref) / _scale(ref)
+        print("bf16 %s %s: max err / median|lb| = %.3e" % (path, which, err.max()))
+        assert err.max() <= BF16_TOL[which], which
+        _, da, dbeta = bc.bound_grad(net, dom, db, _t(a), _t(b), bc.BF16)
+        assert bc.status(net) == 0
+        _, da_ref, db_ref = O.grad(onet, props, batch, a.astype(np.float64), b.astype(np.float64))
+        _check_grad(pb, onet, props, batch, da.cpu().numpy(), dbeta.cpu().numpy(), da_ref, db_ref,
+                    "%s %s" % (path, which))
+
+
+def test_autotune_times_every_candidate_and_its_choice_is_taken():
+    """The tuner's candidates are the supported paths (the GEMM paths at 1 and 2 CTAs per SM); the
+    choice is the fastest, later calls with rows in the same power-of-two bucket take it, and a
+    bound under it equals the bound with that configuration set by hand, bit for bit."""
+    pb = wl.problem_conv_small()
+    onet, props, unst = oracle_setup(pb)
+    batch = wl.random_batch(pb, unst, 48, 1, 8, 2)
+    a, b = wl.random_alpha_beta(batch, 5, 1.0)
+    net, dom, db = _gpu(pb, props, batch)
+    best, cands = bc.autotune(net, dom, db, _t(a), _t(b), reps=2)
+    assert bc.status(net) == 0
+    paths = {c[0][0] for c in cands}
+    assert paths == {bc.N.PATH_LAYER_EPI, bc.N.PATH_LAYER_GATHER, bc.N.PATH_LAYER_IM2COL}
+    assert len(cands) == 5 and all(ms > 0 for _, ms in cands)
+    assert best == min(cands, key=lambda c: c[1])[0]
+    print("autotune conv_small (48 subdomains): " + ", ".join("%s/%d %.3f ms" % (bc.N.PATH_NAMES[c[0]], c[1], ms)
+                                                             for c, ms in cands))
+    R = batch.B * pb.K
+    assert bc.get_launch(net, R) == best
+    assert bc.get_launch(net, R + 1)[0] in paths            # another bucket: the built-in order
+    lb_tuned = bc.bound(net, dom, db, _t(a), _t(b), bc.BF16).cpu().numpy()
+    net2, dom2, db2 = _gpu(pb, props, batch)
+    bc.set_launch(net2, *best)
+    lb_set = bc.bound(net2, dom2, db2, _t(a), _t(b), bc.BF16).cpu().numpy()
+    assert np.array_equal(lb_tuned, lb_set)
+    ref = O.bound(onet, props, batch, a, b)
+    assert (np.abs(lb_tuned - ref) / _scale(ref)).max() <= BF16_TOL["conv_small"]
 
 
 def test_bf16_conv_at_the_size_limits_matches_oracle():
