@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--no-fp32-form", action="store_true", help="skip timing the plain FP32 form beside BF16")
     ap.add_argument("--fp32-steps", type=int, default=10, help="timed steps of the plain FP32 form")
     ap.add_argument("--no-autotune", action="store_true", help="skip the launch-configuration tuner")
+    ap.add_argument("--no-joint", action="store_true", help="skip the joint intermediate-bound measurement")
+    ap.add_argument("--joint-subdomains", type=int, default=64,
+                    help="subdomains of the joint intermediate-bound measurement (784-256x6-10 MLP)")
     ap.add_argument("--no-graph", action="store_true", help="launch the timed steps eagerly instead of replaying "
                                                              "one captured CUDA graph")
     ap.add_argument("--profile-timed", action="store_true",
@@ -519,9 +522,84 @@ def main():
                 rows * f_row * (2 * cfg.iters + 1) / (forms["fp32"]["ms_per_step"] / 1e3) / 1e12
                 / probes["fp32_tflops"]) if probes["fp32_tflops"] else None
         line["config"]["name"] = args.workload
+        line["joint"] = None if args.no_joint else measure_joint(args, bc, torch, wl, probes)
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def joint_flops_per_subdomain_iter(widths, K):
+    """Algorithmic FLOPs of one joint iteration of one subdomain (fully connected net): for every
+    target layer T = 2..L-1, 2 d_T rows back-substituted through layers T-1..1 and their adjoint
+    forward pass (2 d_m d_(m-1) each per row and direction), and the K spec rows through all
+    hidden layers; the backward recomputation of the target passes for the gradient included."""
+    L = len(widths) - 1
+    chain = [0] + [2 * widths[m] * widths[m - 1] for m in range(1, L)]   # chain[m]: one layer, one row
+    f = 0
+    for T in range(2, L):
+        f += 2 * widths[T] * sum(chain[1:T]) * 3        # backward, recomputed backward, adjoint
+    f += K * sum(chain[1:L]) * 2                        # spec rows: backward and adjoint
+    return f
+
+
+def measure_joint(args, bc, torch, wl, probes, iters=20):
+    """Joint optimisation of intermediate bounds (Section 3.3) on the 784-256x6-10 MLP with
+    args.joint_subdomains BaB-tree subdomains (FP32, 20 iterations): subdomains/s against the
+    plain FP32 optimiser on the same batch, and the ablations of Table A4 -- alpha and/or beta
+    optimised, joint on or off -- as the mean bound each reaches."""
+    pb, net, dom, hbatch, unst, _ = build_workload("mlp784", 0, args.joint_subdomains, torch, bc, wl)
+    db = bc.DeviceBatch.from_host(hbatch)
+    a0, b0 = wl.initial_alpha_beta(hbatch)
+    a_init, b_init = torch.as_tensor(a0).cuda(), torch.as_tensor(b0).cuda()
+    ap_init, bp_init = bc.joint_init_alpha(net, dom, db)
+    K, B = pb.K, hbatch.B
+
+    def run(joint, fa=False, fb=False):
+        cfg = bc.OptCfg(iters=iters, precision=bc.FP32, certify=False, freeze_alpha=fa, freeze_beta=fb)
+        a, b = a_init.clone(), b_init.clone()
+        if joint:
+            ap, bp = ap_init.clone(), bp_init.clone()
+            lb, _, _ = bc.optimize_joint(net, dom, db, a, b, ap, bp, cfg=cfg)
+        else:
+            lb = bc.optimize(net, dom, db, a, b, cfg)
+        return lb
+
+    def timed(joint, reps=3):
+        run(joint)                                  # warm: workspace and tables
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            lb = run(joint)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts), lb
+
+    ms_joint, lb_joint = timed(True)
+    ms_plain, lb_plain = timed(False)
+    assert bc.status(net) == 0, "device status reported an error (joint)"
+    flops = joint_flops_per_subdomain_iter(pb.widths, K) * B * iters
+    tfl = flops / (ms_joint / 1e3) / 1e12
+    ablation = {}
+    for joint in (False, True):
+        for name, fa, fb in (("alpha", False, True), ("beta", True, False), ("alpha+beta", False, False)):
+            lb = run(joint, fa, fb).double().cpu().numpy()
+            ablation[("joint " if joint else "") + name] = {"mean_lb": float(lb.mean()),
+                                                             "verified_rows": int((lb > 0).sum())}
+    assert bc.status(net) == 0, "device status reported an error (ablation)"
+    return {"workload": "mlp_784_256x6_10 eps=0.015, %d BaB-tree subdomains (depth<=12), 9 specs, 20 Adam iters, "
+                        "FP32, intermediate bounds of layers 2-6 recomputed per subdomain" % B,
+            "value": B / (ms_joint / 1e3), "unit": UNIT, "ms_per_step": ms_joint,
+            "plain_fp32": {"value": B / (ms_plain / 1e3), "ms_per_step": ms_plain},
+            "mean_lb": {"joint": float(lb_joint.double().mean()), "plain": float(lb_plain.double().mean())},
+            "roofline": {"bound": "alu", "achieved": tfl, "peak": probes["fp32_tflops"], "unit": "TFLOP/s",
+                         "frac": tfl / probes["fp32_tflops"] if probes["fp32_tflops"] else None,
+                         "scope": "the whole joint optimisation (SIMT GEMMs and epilogues), algorithmic FLOPs "
+                                  "(joint_flops_per_subdomain_iter) over its CUDA-event time",
+                         "peak_source": "of measured (bcrown_peak_probe FFMA throughput)"},
+            "ablation_table_A4": ablation}
 
 
 def time_root_bounds(bc, torch, net, dom, P, reps=3):

@@ -851,6 +851,8 @@ extern "C" int bcrown_optimize_joint(bcrown_net* net, const bcrown_domain* dom, 
           cudaMemsetAsync(vv[q], 0, n[q] * 4, s);
         }
       launch_fill(best, B, -INFINITY, s);
+      // entries no subdomain owns (gaps the caller's alpha_off may leave) read subdomain 0
+      for (int q = 0; q < 4; ++q) cudaMemsetAsync(own[q], 0, std::max<int64_t>(n[q], 1) * 4, s);
       k_owner<<<B, 256, 0, s>>>(w.v, own[0], n[0], own[1], n[1], own[2], n[2], own[3], n[3]);
       ++g_launches;
       const bool frozen[4] = {(cfg->freeze & BCROWN_FREEZE_ALPHA) != 0, (cfg->freeze & BCROWN_FREEZE_BETA) != 0,

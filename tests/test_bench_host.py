@@ -81,3 +81,13 @@ def test_committed_fused_record_names_existing_sources():
     rec = json.load(open(os.path.join(ROOT, "profiles", "k_fused_grad.json")))
     assert all(os.path.exists(os.path.join(ROOT, f)) for f in rec["sources"])
     assert rec["dram_bytes_per_launch"] == rec["dram_bytes_read_per_launch"] + rec["dram_bytes_write_per_launch"]
+
+
+def test_joint_flop_model():
+    """784-256x6-10: target layer T (2..6) back-substitutes 512 rows through T-1 layers (the
+    first 784x256, the rest 256x256) three times (backward, recomputed backward, adjoint); the 9
+    spec rows go through all six hidden layers twice."""
+    w = [784] + [256] * 6 + [10]
+    first, rest = 2 * 256 * 784, 2 * 256 * 256
+    expect = sum(512 * (first + (T - 2) * rest) * 3 for T in range(2, 7)) + 9 * (first + 5 * rest) * 2
+    assert bench.joint_flops_per_subdomain_iter(w, 9) == expect
