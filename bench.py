@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-fp32-form", action="store_true", help="skip timing the plain FP32 form beside BF16")
     ap.add_argument("--fp32-steps", type=int, default=10, help="timed steps of the plain FP32 form")
     ap.add_argument("--no-autotune", action="store_true", help="skip the launch-configuration tuner")
+    ap.add_argument("--launch-path", default=None, choices=["fused", "layer_epi", "layer_gather", "layer_im2col"],
+                    help="take this BF16 path instead of tuning (for profiling one path)")
     ap.add_argument("--no-joint", action="store_true", help="skip the joint intermediate-bound measurement")
     ap.add_argument("--joint-subdomains", type=int, default=64,
                     help="subdomains of the joint intermediate-bound measurement (784-256x6-10 MLP)")
@@ -193,6 +195,16 @@ def layer_gemm_bytes_per_row_iter(pb, U, depth):
     return 8 * hidden + 4 * d0 + U * (2 + 2 + 4 + 4 + 4) + depth * 8
 
 
+def tcg_bytes_per_row_iter(widths):
+    """Algorithmic bytes of the layer-path GEMMs alone (BCROWN_PATH_LAYER_GATHER / IM2COL) per row
+    and iteration: each hidden layer's backward contraction reads Lambda^(i) (FP32) and writes
+    A^(i-1) (FP32), its forward contraction reads h^(i-1) and writes zhat^(i): 8 (d_i + d_(i-1))
+    bytes per layer i = 1..L-1 (each operand element counted once, however often the gather
+    re-reads it from L1)."""
+    L = len(widths) - 1
+    return 8 * sum(widths[i] + widths[i - 1] for i in range(1, L))
+
+
 def fp32_simt_peak_tflops(sm_mhz):
     """152 SMs x 128 FP32 lanes x 2 flop per FMA x clock."""
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
@@ -302,7 +314,11 @@ def main():
     # timed region, and keeps the fastest for the batch's row-count bucket
     launch = None
     if prec == bc.BF16:
-        if not args.no_autotune:
+        if args.launch_path:
+            code = {v: k for k, v in bc.N.PATH_NAMES.items()}[args.launch_path]
+            bc.set_launch(net, code)
+            launch = {"path": args.launch_path, "grid_per_sm": 0, "chosen_by": "--launch-path"}
+        elif not args.no_autotune:
             best, cands = bc.autotune(net, dom, db, a_init, b_init, reps=2)
             launch = {"path": bc.N.PATH_NAMES[best[0]], "grid_per_sm": best[1], "chosen_by": "autotune",
                       "candidates_ms_per_bound_grad": {"%s/%d" % (bc.N.PATH_NAMES[c[0]], c[1]): ms
@@ -452,8 +468,12 @@ def main():
         # roofline (the contractions' algorithmic flops); the bound is the larger fraction
         ms, nl = prof[6]
         U = np.array([len(u) for u in unst])[hbatch.prop_of].astype(np.float64)
-        per_row = layer_gemm_bytes_per_row_iter(pb, U, hbatch.split_cnt.astype(np.float64))
-        bytes_all = float(np.sum(per_row)) * pb.K * cfg.iters * prof_steps
+        epi = bool(launch and launch["path"] == "layer_epi")
+        if epi:
+            per_row = layer_gemm_bytes_per_row_iter(pb, U, hbatch.split_cnt.astype(np.float64))
+            bytes_all = float(np.sum(per_row)) * pb.K * cfg.iters * prof_steps
+        else:
+            bytes_all = float(tcg_bytes_per_row_iter(pb.widths)) * rows * cfg.iters * prof_steps
         flops_all = float(rows) * 2 * f_row * cfg.iters * prof_steps
         gbs = bytes_all / (ms / 1e3) / 1e9
         tfl = flops_all / (ms / 1e3) / 1e12
@@ -475,9 +495,12 @@ def main():
         roof.update({"traffic": None, "hbm_gbs": gbs, "hbm_frac": hbm_frac, "tensor_tflops": tfl,
                      "tensor_frac": ten_frac, "algorithmic_bytes_per_launch": bytes_all / nl,
                      "algorithmic_flops_per_launch": flops_all / nl,
-                     "bytes_model": "per row and iteration: 8 B x hidden neurons (Lambda and h, BF16, written and "
-                                    "read) + 4 B x inputs (x*) + 16 B x unstable (stash 2+2, alpha 4+4, dalpha 4) + "
-                                    "8 B x splits",
+                     "bytes_model": ("per row and iteration: 8 B x hidden neurons (Lambda and h, BF16, written and "
+                                     "read) + 4 B x inputs (x*) + 16 B x unstable (stash 2+2, alpha 4+4, dalpha 4) + "
+                                     "8 B x splits") if epi else
+                                    ("per row and iteration, the GEMMs' own operands: per hidden layer i, backward "
+                                     "Lambda^(i) read + A^(i-1) written, forward h^(i-1) read + zhat^(i) written, "
+                                     "FP32: 8 (d_i + d_(i-1)) B"),
                      "flops_model": "2 x (backward + adjoint) contractions per row and iteration: fc 2 d_i d_(i-1), "
                                     "conv 2 C_out H_out W_out C_in k^2",
                      "kernel_ms_per_step": ms / prof_steps, "launches_per_step": nl / prof_steps,

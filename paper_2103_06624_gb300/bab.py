@@ -246,6 +246,13 @@ def bab(engine, prop, l, u, x_lo, x_hi, batch_size=512, max_rounds=50, max_bound
                     upper=upper, line_search=line_search)[0]
 
 
+def _own(d):
+    """A subdomain that stays in the pool gets its own alpha and beta (they are slices of the
+    batch-wide result arrays, which would otherwise stay alive as long as any descendant does)."""
+    d.alpha, d.beta = d.alpha.copy(), d.beta.copy()
+    return d
+
+
 def _bound(engine, doms, cases, K, Us):
     """One engine call on a list of subdomains (of any of the properties); results written back."""
     lb, a, b = engine.optimize([(cases[d.owner][0], d.splits, d.signs) for d in doms],
@@ -300,7 +307,7 @@ def bab_many(engine, cases, batch_size=512, max_rounds=50, max_bounded=1_000_000
             res[d.owner].bounded += 1
             res[d.owner].max_depth = max(res[d.owner].max_depth, d.depth)
             if d.lb.min() <= 0:
-                pool.append(d)
+                pool.append(_own(d))
     for c in range(n):
         if open_case[c] and res[c].status == "violated":
             open_case[c] = False
@@ -332,7 +339,7 @@ def bab_many(engine, cases, batch_size=512, max_rounds=50, max_bounded=1_000_000
                 r.bounded += 1
                 r.max_depth = max(r.max_depth, k.depth)
                 if k.lb.min() <= 0:      # Domain_Filter: keep the subdomains not yet verified
-                    pool.append(k)
+                    pool.append(_own(k))
         # a property with a witness is decided: its subdomains leave the pool
         for c in range(n):
             if open_case[c] and res[c].status == "violated":

@@ -345,9 +345,10 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int prop = ri.w & 0x7FFFFFFF;
       const bool rv = mv && (ri.w < 0);
       // the row's splits in this layer that fall on this thread's elements of the tile
-      int kc_[MAX_KEEP], ks_[MAX_KEEP], kt_[MAX_KEEP];
+      // kept splits, packed: n | t << 20 | (S == +1) << 27 (n < 2^20, t < 64); -1: none
+      int kp_[MAX_KEEP];
 #pragma unroll
-      for (int q = 0; q < MAX_KEEP; ++q) kc_[q] = ks_[q] = kt_[q] = -1;
+      for (int q = 0; q < MAX_KEEP; ++q) kp_[q] = -1;
       int nkeep = 0;
       bool many = false;
       int s0 = 0, s1 = 0;
@@ -367,9 +368,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
           for (int u = 0; u < MAX_KEEP; ++u)
             if (u == nkeep) {
-              kc_[u] = nn;
-              ks_[u] = sp_s(e);
-              kt_[u] = sp_t(e);
+              kp_[u] = nn | (sp_t(e) << 20) | ((sp_s(e) == 1 ? 1 : 0) << 27);
             }
           if (nkeep < MAX_KEEP) ++nkeep;
           else many = true;
@@ -389,18 +388,20 @@ __global__ void __launch_bounds__(THREADS, 1)
       const uint32_t* tab_p = MODE == EPI_CONCRETIZE ? nullptr : ps.ntab + (size_t)prop * cx.NH;
       // the chunk's NHWC index: conv, (pm, channels nb ..); fully connected over a map, nb itself
       auto nhwc = [&](int nb) -> long long { return ps.npos ? (long long)nb : (long long)pm * ps.Cpo + nb; };
-      for (int n0 = 0; n0 < Np; n0 += 16) {
-        float v[16];
-        tmem_ld16(tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(buf * Np + n0), v);
+      for (int n0 = 0; n0 < Np; n0 += 8) {
+        // 8 columns per step (one 16-byte chunk of the BF16 NHWC output): the element loop's
+        // registers fit the 96 a thread has at 18 warps per SM
+        float v[8];
+        tmem_ld8(tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(buf * Np + n0), v);
         const int nb = nlo + n0;   // first n of the chunk
         if (mv && nb < ps.N) {
-        uint32_t o2[8];            // the chunk's results, packed in BF16 pairs
+        uint32_t o2[4];            // the chunk's results, packed in BF16 pairs
         const long long nn0 = nhwc(nb);
         const int lim = ps.npos ? ps.N : ps.Cpo;   // elements of the chunk that exist in the map
         if (MODE == EPI_CONCRETIZE) {
-          float o[16];
+          float o[8];
 #pragma unroll
-          for (int e = 0; e < 16; ++e) {
+          for (int e = 0; e < 8; ++e) {
             const int n = nb + e;
             o[e] = 0.f;
             if (!rv || n >= ps.Co) continue;
@@ -411,54 +412,51 @@ __global__ void __launch_bounds__(THREADS, 1)
             o[e] = a >= 0.f ? xl : xh;   // x* minimises A^(0) x over the box
           }
 #pragma unroll
-          for (int e = 0; e < 8; ++e) o2[e] = pack2(o[2 * e], o[2 * e + 1]);
+          for (int e = 0; e < 4; ++e) o2[e] = pack2(o[2 * e], o[2 * e + 1]);
         } else {
-          // the 16 elements' neuron entries (four 16-byte loads)
-          uint32_t ent[16];
+          // the 8 elements' neuron entries (two 16-byte loads)
+          uint32_t ent[8];
           {
             const uint4* tp = reinterpret_cast<const uint4*>(tab_p + nn0);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const uint4 t4 = tp[q];
-              ent[4 * q] = t4.x, ent[4 * q + 1] = t4.y, ent[4 * q + 2] = t4.z, ent[4 * q + 3] = t4.w;
-            }
+            const uint4 t0 = tp[0], t1 = tp[1];
+            ent[0] = t0.x, ent[1] = t0.y, ent[2] = t0.z, ent[3] = t0.w;
+            ent[4] = t1.x, ent[5] = t1.y, ent[6] = t1.z, ent[7] = t1.w;
           }
           // elements of the chunk with a split of the row (all of them when the row's list overflowed)
-          uint32_t smask = many ? 0xFFFFu : 0u;
+          uint32_t smask = many ? 0xFFu : 0u;
 #pragma unroll
           for (int q = 0; q < MAX_KEEP; ++q)
-            if (q < nkeep && (unsigned)(kc_[q] - nb) < 16u) smask |= 1u << (kc_[q] - nb);
+            if (q < nkeep && (unsigned)((kp_[q] & 0xFFFFF) - nb) < 8u) smask |= 1u << ((kp_[q] & 0xFFFFF) - nb);
+          float o[8];
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            // the unstable elements' operands, issued together before any is used: alpha, the
-            // chord and, in the adjoint, the stash
-            float al[8], st[8];
-            float2 ch[8];
-            float bv[8];
+          for (int hb = 0; hb < 8; hb += 4) {
+            // the unstable elements' operands of 4 elements, issued together before any is used:
+            // alpha, the chord and, in the adjoint, the stash
+            float al[4], st[4], bv[4];
+            float2 ch[4];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              const int e = 8 * h + u;
-              const bool un = rv && nb + e < lim && (ent[e] & 3u) == CODE_UNSTABLE;
-              const int rk = (int)(ent[e] >> 2);
-              al[u] = un ? alpha_r[rk] : 0.f;
-              ch[u] = un ? chord_p[rk] : make_float2(0.f, 0.f);
-              st[u] = (MODE == EPI_FWD && un) ? __bfloat162float(stash_r[rk]) : 0.f;
+            for (int uu = 0; uu < 4; ++uu) {
+              const int u = hb + uu;
+              const bool un = rv && nb + u < lim && (ent[u] & 3u) == CODE_UNSTABLE;
+              const int rk = (int)(ent[u] >> 2);
+              al[uu] = un ? alpha_r[rk] : 0.f;
+              ch[uu] = un ? chord_p[rk] : make_float2(0.f, 0.f);
+              st[uu] = (MODE == EPI_FWD && un) ? __bfloat162float(stash_r[rk]) : 0.f;
               // biases: a conv layer's are per channel (shared memory, up to MAX_NP channels); a
               // fully connected pass's per n, and a wider layer's channels from global memory
-              bv[u] = ps.npos ? ps.bnhwc[nn0 + e]
-                              : (sb_smem ? sbias[min(nb + e, MAX_NP - 1)] : (nb + e < lim ? ps.bnhwc[nb + e] : 0.f));
+              bv[uu] = ps.npos ? ps.bnhwc[nn0 + u]
+                               : (sb_smem ? sbias[min(nb + u, MAX_NP - 1)] : (nb + u < lim ? ps.bnhwc[nb + u] : 0.f));
             }
-            float o[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              const int e = 8 * h + u;
-              const int n = nb + e;
+            for (int uu = 0; uu < 4; ++uu) {
+              const int u = hb + uu;
+              const int n = nb + u;
               const bool valid = rv && n < lim;
-              const int code = (int)(ent[e] & 3u);
-              const int rk = (int)(ent[e] >> 2);
+              const int code = (int)(ent[u] & 3u);
+              const int rk = (int)(ent[u] >> 2);
               // split of this element (sign s, list position t): rare
               int s = 0, ts = 0;
-              if (valid && ((smask >> e) & 1u)) {
+              if (valid && ((smask >> u) & 1u)) {
                 int c = n, p = pm;
                 if (ps.npos) {
                   p = n / ps.Cpo;
@@ -467,9 +465,9 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const int jl = c * ps.HWo + p;   // neuron of the layer (channel-major)
 #pragma unroll
                 for (int q = 0; q < MAX_KEEP; ++q)
-                  if (q < nkeep && kc_[q] == n) {
-                    s = ks_[q];
-                    ts = kt_[q];
+                  if (q < nkeep && (kp_[q] & 0xFFFFF) == n) {
+                    s = (kp_[q] >> 27) & 1 ? 1 : -1;
+                    ts = (kp_[q] >> 20) & 127;
                   }
                 if (many && s == 0)
                   for (int q = s0; q < s1; ++q) {
@@ -482,14 +480,14 @@ __global__ void __launch_bounds__(THREADS, 1)
               }
               const bool unst = valid && s == 0 && code == CODE_UNSTABLE;
               if (MODE == EPI_RELAX) {
-                const float a = v[e];
+                const float a = v[u];
                 float D = code == CODE_ACTIVE ? 1.f : 0.f, lm = 0.f, bs = 0.f;
                 if (unst) {
                   if (a >= 0.f) {
-                    D = __saturatef(al[u]);
+                    D = __saturatef(al[uu]);
                   } else {
-                    D = ch[u].x;
-                    lm = ch[u].y;
+                    D = ch[uu].x;
+                    lm = ch[uu].y;
                   }
                   if (stash_r) stash_r[rk] = bf16_signed(a);
                 }
@@ -500,17 +498,17 @@ __global__ void __launch_bounds__(THREADS, 1)
                   else atomicCAS(cx.status, 0, BCROWN_ERR_ARG);
                 }
                 const float L = valid ? fmaf(a, D, bs) : 0.f;
-                acc = fmaf(L, bv[u], fmaf(valid ? a : 0.f, lm, acc));
+                acc = fmaf(L, bv[uu], fmaf(valid ? a : 0.f, lm, acc));
                 o[u] = L;
               } else {   // EPI_FWD
-                const float z = v[e] + bv[u];
+                const float z = v[u] + bv[uu];
                 float hv = code == CODE_ACTIVE ? z : 0.f;
                 if (unst) {
-                  if (st[u] >= 0.f) {
-                    hv = __saturatef(al[u]) * z;
-                    dalpha_r[rk] = st[u] * z;
+                  if (st[uu] >= 0.f) {
+                    hv = __saturatef(al[uu]) * z;
+                    dalpha_r[rk] = st[uu] * z;
                   } else {
-                    hv = fmaf(ch[u].x, z, ch[u].y);
+                    hv = fmaf(ch[uu].x, z, ch[uu].y);
                     dalpha_r[rk] = 0.f;
                   }
                 }
@@ -525,18 +523,14 @@ __global__ void __launch_bounds__(THREADS, 1)
                 o[u] = valid ? hv : 0.f;
               }
             }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) o2[4 * h + u] = pack2(o[2 * u], o[2 * u + 1]);
           }
-        }
-        if (ps.dst) {
-          // the chunk's elements are contiguous in the NHWC output
-          const long long o0 = (long long)rl * ps.dst_stride + nn0;
 #pragma unroll
-          for (int h = 0; h < 2; ++h)
-            if (nb + 8 * h + 8 <= lim)
-              *reinterpret_cast<uint4*>(ps.dst + o0 + 8 * h) =
-                  make_uint4(o2[4 * h], o2[4 * h + 1], o2[4 * h + 2], o2[4 * h + 3]);
+          for (int u = 0; u < 4; ++u) o2[u] = pack2(o[2 * u], o[2 * u + 1]);
+        }
+        if (ps.dst && nb + 8 <= lim) {
+          // the chunk's elements are contiguous in the NHWC output
+          *reinterpret_cast<uint4*>(ps.dst + (long long)rl * ps.dst_stride + nn0) =
+              make_uint4(o2[0], o2[1], o2[2], o2[3]);
         }
         }
       }

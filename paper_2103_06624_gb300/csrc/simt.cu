@@ -219,46 +219,49 @@ __global__ void __launch_bounds__(256) k_init_top(RowsCtx c, int dtop, const flo
 // CERT: outward chord constants (from the tables), c summed rounded down, error terms rounded up.
 // ----------------------------------------------------------------------------------------
 constexpr int RELAX_WARPS = 8;   // warps per block; WPR of them share a row (wide layers: all 8)
-// One neuron of the relaxation (FP32 form), every load on its own chain: the slow path of the
-// vectorised loop, taken by groups that hold an unstable or a split neuron.  Returns Lambda_j
-// and adds Lambda_j b_j + A_j lambda_j to acc.
-__device__ __forceinline__ float relax_one(const RowsCtx& c, int j, size_t n, float a, uint8_t code, float bj,
-                                           bool check, int ns, const SplitSlot* sl, long long abase,
-                                           long long bbase, const float* __restrict__ alpha, int64_t n_alpha,
-                                           const float* __restrict__ beta, int64_t n_beta, float& acc) {
-  int s = 0;
-  float bet = 0.f;
-  if (check)
-    for (int q = 0; q < ns; ++q)
-      if (sl[q].idx == j) {
-        s = sl[q].sign;
-        const long long bi = bbase + sl[q].t;
-        if (bi >= 0 && bi < n_beta) bet = fmaxf(beta[bi], 0.f);
-        else flag(c.status, BCROWN_ERR_ARG);
-      }
-  float D = 0.f, lm = 0.f;
-  if (s == -1) D = 1.f;
-  else if (s == 1) D = 0.f;
-  else if (code == CODE_ACTIVE) D = 1.f;
-  else if (code == CODE_INACTIVE) D = 0.f;
-  else if (a >= 0.f) {
-    const long long ai = abase + c.tb.rank[n];
-    if (ai < 0 || ai >= n_alpha) flag(c.status, BCROWN_ERR_ARG);
-    else D = fminf(fmaxf(alpha[ai], 0.f), 1.f);
-  } else {
-    D = c.tb.slope[n];
-    lm = c.tb.icpt[n];
-  }
-  const float L = fmaf(a, D, bet * (float)s);
-  acc = fmaf(L, bj, fmaf(a, lm, acc));
-  return L;
-}
-
 // All four codes stable (active or inactive): no alpha, chord or split term.
 __device__ __forceinline__ bool stable4(uchar4 c4) {
   return c4.x != CODE_UNSTABLE && c4.y != CODE_UNSTABLE && c4.z != CODE_UNSTABLE && c4.w != CODE_UNSTABLE;
 }
 __device__ __forceinline__ float d01(unsigned char code) { return code == CODE_ACTIVE ? 1.f : 0.f; }
+
+// Relaxation of 4 consecutive neurons n .. n + 3 (n a multiple of 4, rows 16-byte aligned) of a
+// group that holds an unstable or a split neuron, the group's loads issued together: the 4 ranks
+// (one 16-byte load) where a neuron is unstable, the 4 chords where one takes the chord, then
+// the alphas.  (The vectorised loops branch to it only for such groups: a version without the
+// branch, every lane running these loads under predicates, measured 20 % slower.)
+// alpha_row: the row's alpha block, checked against the array once per row (null: none).
+// D, lambda per neuron (split neurons are left to the caller) and rk = the rank of an unstable
+// neuron, -1 otherwise.
+__device__ __forceinline__ void group4(const Tables& tb, size_t n, const float a[4], const uchar4 c4,
+                                       const float* __restrict__ alpha_row, float D[4], float lm[4], int rk[4]) {
+  const uint8_t cd[4] = {c4.x, c4.y, c4.z, c4.w};
+  bool un[4], any_un = false, any_ch = false;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    un[v] = cd[v] == CODE_UNSTABLE;
+    any_un |= un[v];
+    any_ch |= un[v] && a[v] < 0.f;
+  }
+  int4 r4 = make_int4(-1, -1, -1, -1);
+  float4 s4 = make_float4(0.f, 0.f, 0.f, 0.f), i4 = s4;
+  if (any_un) r4 = __ldg(reinterpret_cast<const int4*>(tb.rank + n));
+  if (any_ch) {
+    s4 = __ldg(reinterpret_cast<const float4*>(tb.slope + n));
+    i4 = __ldg(reinterpret_cast<const float4*>(tb.icpt + n));
+  }
+  const int r[4] = {r4.x, r4.y, r4.z, r4.w};
+  const float sl[4] = {s4.x, s4.y, s4.z, s4.w}, ic[4] = {i4.x, i4.y, i4.z, i4.w};
+  float al[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) al[v] = (un[v] && a[v] >= 0.f && alpha_row != nullptr) ? alpha_row[r[v]] : 0.f;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    rk[v] = un[v] ? r[v] : -1;
+    D[v] = cd[v] == CODE_ACTIVE ? 1.f : (un[v] ? (a[v] >= 0.f ? fminf(fmaxf(al[v], 0.f), 1.f) : sl[v]) : 0.f);
+    lm[v] = (un[v] && a[v] < 0.f) ? ic[v] : 0.f;
+  }
+}
 
 template <bool CERT, int WPR>
 __global__ void __launch_bounds__(32 * RELAX_WARPS) k_relax(RowsCtx c, int layer, int d, long long hoff,
@@ -403,6 +406,9 @@ __global__ void __launch_bounds__(32 * RELAX_WARPS) k_relax(RowsCtx c, int layer
                         reinterpret_cast<uintptr_t>(bias)) & 15) == 0;
     if (vec4) {
       const uchar4* code4 = reinterpret_cast<const uchar4*>(c.tb.code + n0);
+      // the row's alpha block, checked once against the array
+      const float* alpha_row = (abase >= 0 && abase + Up <= n_alpha) ? alpha + abase : nullptr;
+      if (!alpha_row && Up > 0 && lane == 0 && sub == 0) flag(c.status, BCROWN_ERR_ARG);
       for (int q = sub * 32 + lane; q < d / 4; q += 32 * WPR) {
         const int j = 4 * q;
         const float4 a4 = reinterpret_cast<const float4*>(a_row)[q];
@@ -420,14 +426,26 @@ __global__ void __launch_bounds__(32 * RELAX_WARPS) k_relax(RowsCtx c, int layer
           acc = fmaf(L.z, b4.z, fmaf(a4.z, 0.f, acc));
           acc = fmaf(L.w, b4.w, fmaf(a4.w, 0.f, acc));
         } else {
-          L.x = relax_one(c, j, n0 + j, a4.x, c4.x, b4.x, (sb & 1u) != 0, ns, sl_, abase, bbase, alpha, n_alpha, beta,
-                          n_beta, acc);
-          L.y = relax_one(c, j + 1, n0 + j + 1, a4.y, c4.y, b4.y, (sb & 2u) != 0, ns, sl_, abase, bbase, alpha,
-                          n_alpha, beta, n_beta, acc);
-          L.z = relax_one(c, j + 2, n0 + j + 2, a4.z, c4.z, b4.z, (sb & 4u) != 0, ns, sl_, abase, bbase, alpha,
-                          n_alpha, beta, n_beta, acc);
-          L.w = relax_one(c, j + 3, n0 + j + 3, a4.w, c4.w, b4.w, (sb & 8u) != 0, ns, sl_, abase, bbase, alpha,
-                          n_alpha, beta, n_beta, acc);
+          const float av[4] = {a4.x, a4.y, a4.z, a4.w}, bv[4] = {b4.x, b4.y, b4.z, b4.w};
+          float D[4], lm[4], Lv[4];
+          int rk[4];
+          group4(c.tb, n0 + j, av, c4, alpha_row, D, lm, rk);
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            float bs = 0.f;
+            if ((sb >> v) & 1u)   // a split of the row may sit here
+              for (int qq = 0; qq < ns; ++qq)
+                if (sl_[qq].idx == j + v) {
+                  const long long bi = bbase + sl_[qq].t;
+                  if (bi >= 0 && bi < n_beta) bs = fmaxf(beta[bi], 0.f) * (float)sl_[qq].sign;
+                  else flag(c.status, BCROWN_ERR_ARG);
+                  D[v] = sl_[qq].sign == -1 ? 1.f : 0.f;
+                  lm[v] = 0.f;
+                }
+            Lv[v] = fmaf(av[v], D[v], bs);
+            acc = fmaf(Lv[v], bv[v], fmaf(av[v], lm[v], acc));
+          }
+          L = make_float4(Lv[0], Lv[1], Lv[2], Lv[3]);
         }
         reinterpret_cast<float4*>(lam_row)[q] = L;
       }
@@ -818,47 +836,6 @@ __global__ void k_xstar(RowsCtx c, int d0, const float* __restrict__ A0, float* 
 // Adjoint epilogue of hidden layer i: zhat = Z (+ bias already added); gradients
 //   dalpha_j = A_j zhat_j (alpha in use), dbeta_j = S_jj zhat_j ; then h = D zhat + lambda.
 // ----------------------------------------------------------------------------------------
-// One neuron of the adjoint epilogue, every load on its own chain (the vectorised loop's slow
-// path): dalpha, dbeta for this neuron; returns h = D zhat + lambda.
-__device__ __forceinline__ float fwd_epi_one(const RowsCtx& c, int j, size_t n, float z, float a, uint8_t code,
-                                             bool check, int ns, const SplitSlot* slots, long long abase,
-                                             long long bbase, const float* __restrict__ alpha, int64_t n_alpha,
-                                             float* __restrict__ dalpha, float* __restrict__ dbeta,
-                                             int64_t n_beta) {
-  int s = 0, t = -1;
-  if (check)
-    for (int q = 0; q < ns; ++q)
-      if (slots[q].idx == j) {
-        s = slots[q].sign;
-        t = slots[q].t;
-      }
-  float D = 0.f, lm = 0.f;
-  long long ai = -1;
-  if (code == CODE_UNSTABLE) {
-    ai = abase + c.tb.rank[n];
-    if (ai < 0 || ai >= n_alpha) {
-      flag(c.status, BCROWN_ERR_ARG);
-      ai = -1;
-    }
-  }
-  if (s == -1) D = 1.f;
-  else if (s == 1) D = 0.f;
-  else if (code == CODE_ACTIVE) D = 1.f;
-  else if (code == CODE_INACTIVE) D = 0.f;
-  else if (a >= 0.f) D = ai >= 0 ? fminf(fmaxf(alpha[ai], 0.f), 1.f) : 0.f;
-  else {
-    D = c.tb.slope[n];
-    lm = c.tb.icpt[n];
-  }
-  if (ai >= 0) dalpha[ai] = (s == 0 && a >= 0.f) ? a * z : 0.f;
-  if (s != 0) {
-    const long long bi = bbase + t;
-    if (bi >= 0 && bi < n_beta) dbeta[bi] = (float)s * z;
-    else flag(c.status, BCROWN_ERR_ARG);
-  }
-  return fmaf(D, z, lm);
-}
-
 // WIDE: rows of more than 2048 neurons (conv layers); the narrow instantiation keeps only the
 // simple loop, and with it the register count of that loop.
 template <bool WIDE>
@@ -930,28 +907,49 @@ __global__ void __launch_bounds__(256) k_fwd_epi(RowsCtx c, int layer, int d, lo
                     ((reinterpret_cast<uintptr_t>(z_row) | reinterpret_cast<uintptr_t>(a_row)) & 15) == 0;
   if (vec4) {
     const uchar4* code4 = reinterpret_cast<const uchar4*>(c.tb.code + n0);
+    // the row's alpha and dalpha blocks, checked once against the arrays
+    const bool arow_ok = abase >= 0 && abase + Up <= n_alpha;
+    const float* alpha_row = arow_ok ? alpha + abase : nullptr;
+    float* dalpha_row = arow_ok ? dalpha + abase : nullptr;
+    if (!arow_ok && Up > 0 && threadIdx.x == 0) flag(c.status, BCROWN_ERR_ARG);
     for (int q = threadIdx.x; q < d / 4; q += blockDim.x) {
       const int j = 4 * q;
-      float4 z4 = reinterpret_cast<const float4*>(z_row)[q];
+      const float4 z4 = reinterpret_cast<const float4*>(z_row)[q];
       const float4 a4 = reinterpret_cast<const float4*>(a_row)[q];
       const uchar4 c4 = code4[q];
       const uint32_t sb = ns == 0 ? 0u : (use_mask ? (smask[j >> 5] >> (j & 31)) & 0xFu : 0xFu);
       if (sb == 0u && stable4(c4)) {
-        z4.x = fmaf(d01(c4.x), z4.x, 0.f);
-        z4.y = fmaf(d01(c4.y), z4.y, 0.f);
-        z4.z = fmaf(d01(c4.z), z4.z, 0.f);
-        z4.w = fmaf(d01(c4.w), z4.w, 0.f);
-      } else {
-        z4.x = fwd_epi_one(c, j, n0 + j, z4.x, a4.x, c4.x, (sb & 1u) != 0, ns, slots, abase, bbase, alpha, n_alpha,
-                           dalpha, dbeta, n_beta);
-        z4.y = fwd_epi_one(c, j + 1, n0 + j + 1, z4.y, a4.y, c4.y, (sb & 2u) != 0, ns, slots, abase, bbase, alpha,
-                           n_alpha, dalpha, dbeta, n_beta);
-        z4.z = fwd_epi_one(c, j + 2, n0 + j + 2, z4.z, a4.z, c4.z, (sb & 4u) != 0, ns, slots, abase, bbase, alpha,
-                           n_alpha, dalpha, dbeta, n_beta);
-        z4.w = fwd_epi_one(c, j + 3, n0 + j + 3, z4.w, a4.w, c4.w, (sb & 8u) != 0, ns, slots, abase, bbase, alpha,
-                           n_alpha, dalpha, dbeta, n_beta);
+        const float4 h4 = make_float4(fmaf(d01(c4.x), z4.x, 0.f), fmaf(d01(c4.y), z4.y, 0.f),
+                                      fmaf(d01(c4.z), z4.z, 0.f), fmaf(d01(c4.w), z4.w, 0.f));
+        reinterpret_cast<float4*>(z_row)[q] = h4;
+        continue;
       }
-      reinterpret_cast<float4*>(z_row)[q] = z4;
+      const float zv[4] = {z4.x, z4.y, z4.z, z4.w}, av[4] = {a4.x, a4.y, a4.z, a4.w};
+      float D[4], lm[4], hv[4];
+      int rk[4];
+      group4(c.tb, n0 + j, av, c4, alpha_row, D, lm, rk);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        int s = 0;
+        if ((sb >> v) & 1u) {   // a split of the row may sit here
+          int t = -1;
+          for (int qq = 0; qq < ns; ++qq)
+            if (slots[qq].idx == j + v) {
+              s = slots[qq].sign;
+              t = slots[qq].t;
+            }
+          if (s != 0) {
+            D[v] = s == -1 ? 1.f : 0.f;
+            lm[v] = 0.f;
+            const long long bi = bbase + t;
+            if (bi >= 0 && bi < n_beta) dbeta[bi] = (float)s * zv[v];
+            else flag(c.status, BCROWN_ERR_ARG);
+          }
+        }
+        if (rk[v] >= 0 && dalpha_row) dalpha_row[rk[v]] = (s == 0 && av[v] >= 0.f) ? av[v] * zv[v] : 0.f;
+        hv[v] = fmaf(D[v], zv[v], lm[v]);
+      }
+      reinterpret_cast<float4*>(z_row)[q] = make_float4(hv[0], hv[1], hv[2], hv[3]);
     }
     return;
   }

@@ -91,3 +91,12 @@ def test_joint_flop_model():
     first, rest = 2 * 256 * 784, 2 * 256 * 256
     expect = sum(512 * (first + (T - 2) * rest) * 3 for T in range(2, 7)) + 9 * (first + 5 * rest) * 2
     assert bench.joint_flops_per_subdomain_iter(w, 9) == expect
+
+
+def test_layer_gemm_operand_byte_model():
+    """conv_big: hidden layers of 65536, 16384, 32768, 8192 and 512 neurons over a 3072-input
+    image; each contraction's FP32 operand read and output written once per direction."""
+    w = wl.problem_conv_big().widths
+    assert w[:6] == [3072, 65536, 16384, 32768, 8192, 512]
+    expect = 8 * ((65536 + 3072) + (16384 + 65536) + (32768 + 16384) + (8192 + 32768) + (512 + 8192))
+    assert bench.tcg_bytes_per_row_iter(w) == expect == 1994752
