@@ -235,7 +235,7 @@ def _line_search(engine, doms, cases, K, iters=500, decay=0.99, lrs=LINE_SEARCH_
 
 def bab(engine, prop, l, u, x_lo, x_hi, batch_size=512, max_rounds=50, max_bounded=1_000_000,
         n_samples=256, seed=0, time_limit=None, alpha_init=0.5, pgd_steps=20, start=None, upper=True,
-        line_search=True):
+        line_search=True, joint=False):
     """Decide property `prop` (its box x_lo, x_hi and root bounds l, u over all hidden neurons).
 
     start: subdomains to begin from instead of the whole box, as (neuron indices, signs) pairs;
@@ -243,7 +243,7 @@ def bab(engine, prop, l, u, x_lo, x_hi, batch_size=512, max_rounds=50, max_bound
     return bab_many(engine, [(prop, l, u, x_lo, x_hi)], batch_size=batch_size, max_rounds=max_rounds,
                     max_bounded=max_bounded, n_samples=n_samples, seed=seed, time_limit=time_limit,
                     alpha_init=alpha_init, pgd_steps=pgd_steps, starts=None if start is None else [start],
-                    upper=upper, line_search=line_search)[0]
+                    upper=upper, line_search=line_search, joint=joint)[0]
 
 
 def _own(d):
@@ -253,10 +253,13 @@ def _own(d):
     return d
 
 
-def _bound(engine, doms, cases, K, Us):
-    """One engine call on a list of subdomains (of any of the properties); results written back."""
-    lb, a, b = engine.optimize([(cases[d.owner][0], d.splits, d.signs) for d in doms],
-                               np.concatenate([d.alpha for d in doms]), np.concatenate([d.beta for d in doms]))
+def _bound(engine, doms, cases, K, Us, joint=False):
+    """One engine call on a list of subdomains (of any of the properties); results written back.
+    joint: the intermediate bounds are recomputed per subdomain and optimised with alpha, beta
+    (Section 3.3; alpha' starts at the root rule and beta' at 0 for every call)."""
+    opt = engine.optimize_joint if joint else engine.optimize
+    lb, a, b = opt([(cases[d.owner][0], d.splits, d.signs) for d in doms],
+                   np.concatenate([d.alpha for d in doms]), np.concatenate([d.beta for d in doms]))
     lb = np.asarray(lb, np.float32).reshape(len(doms), K)
     a = np.asarray(a, np.float32)
     b = np.asarray(b, np.float32)
@@ -267,13 +270,15 @@ def _bound(engine, doms, cases, K, Us):
 
 
 def bab_many(engine, cases, batch_size=512, max_rounds=50, max_bounded=1_000_000, n_samples=256, seed=0,
-             time_limit=None, alpha_init=0.5, pgd_steps=20, starts=None, upper=True, line_search=True):
+             time_limit=None, alpha_init=0.5, pgd_steps=20, starts=None, upper=True, line_search=True, joint=False):
     """Decide several properties at once: cases = [(prop, l, u, x_lo, x_hi), ...].  Their open
     subdomains share one pool, so each engine call bounds the lowest-bound subdomains of all the
     properties still open together (one batch of mixed properties).  Returns one BabResult per
     case; starts, if given, holds each case's start subdomains (see bab).  upper: evaluate the
     network at every bounded subdomain's x*; line_search: take fully split subdomains to their
-    exact minimum over beta (both on by default; off, the driver is the plain Algorithm 1 loop)."""
+    exact minimum over beta (both on by default; off, the driver is the plain Algorithm 1 loop).
+    joint: bound every subdomain with its intermediate bounds recomputed and optimised jointly
+    (Section 3.3, engine.optimize_joint; FP32 bounds, the certifying pass is not applied)."""
     t0 = time.perf_counter()
     K = engine.K
     n = len(cases)
@@ -300,7 +305,7 @@ def bab_many(engine, cases, batch_size=512, max_rounds=50, max_bounded=1_000_000
                          np.zeros(K * len(sp), np.float32), np.full(K, -np.inf, np.float32), c) for sp, sg in st]
     pool, exhausted = [], []
     if first:
-        _bound(engine, first, cases, K, Us)
+        _bound(engine, first, cases, K, Us, joint)
         if upper:
             _upper(engine, first, cases, res)
         for d in first:
@@ -330,7 +335,7 @@ def bab_many(engine, cases, batch_size=512, max_rounds=50, max_bounded=1_000_000
                 continue
             kids.extend(_children(d, j, K))
         if kids:
-            _bound(engine, kids, cases, K, Us)
+            _bound(engine, kids, cases, K, Us, joint)
             if upper:
                 _upper(engine, kids, cases, res)
             bounded += len(kids)
@@ -454,6 +459,17 @@ class GpuEngine:
         st = self.bc.status(self.net)
         if st != 0:
             raise RuntimeError(f"bcrown device status {st}")
+        return lb.cpu().numpy(), at.cpu().numpy(), bt.cpu().numpy()
+
+    def optimize_joint(self, subs, alpha, beta):
+        """The bound with the intermediate bounds recomputed per subdomain and optimised jointly with
+        alpha, beta (bcrown_optimize_joint, FP32); alpha' starts at the root rule, beta' at 0."""
+        import dataclasses
+        db, at, bt = self._args(subs, alpha, beta)
+        ap, bp = self.bc.joint_init_alpha(self.net, self.dom, db)
+        cfg = dataclasses.replace(self.cfg, precision=self.bc.FP32, certify=False)
+        lb, _, _ = self.bc.optimize_joint(self.net, self.dom, db, at, bt, ap, bp, cfg=cfg)
+        self._check()
         return lb.cpu().numpy(), at.cpu().numpy(), bt.cpu().numpy()
 
     def _args(self, subs, alpha, beta):

@@ -437,6 +437,34 @@ static bool tcg_gather(const bcrown_net* net) { return net->launch_now.path != B
 
 namespace {
 
+// col2im of the scatter form: A[r][ci][yi][xi] = sum over (ky, kx), in that order, of
+// P[r][(ci k + ky) k + kx][y][x] where yi = y s + ky - pad and xi = x s + kx - pad.
+struct Col2im {
+  int C, H, W, k, s, pad, oh, ow;
+};
+__global__ void __launch_bounds__(256) k_col2im(long long total, Col2im g, const float* __restrict__ P,
+                                                float* __restrict__ out, int d_in) {
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= total) return;
+  const long long r = id / d_in;
+  const int e = (int)(id - r * d_in);
+  const int HW = g.H * g.W, ci = e / HW, rem = e - ci * HW, yi = rem / g.W, xi = rem - (rem / g.W) * g.W;
+  const int OP = g.oh * g.ow;
+  const float* pr = P + (size_t)r * g.C * g.k * g.k * OP;
+  float acc = 0.f;
+  for (int ky = 0; ky < g.k; ++ky) {
+    const int yy = yi + g.pad - ky;
+    if (yy < 0 || yy % g.s != 0 || yy / g.s >= g.oh) continue;
+    const int y = yy / g.s;
+    for (int kx = 0; kx < g.k; ++kx) {
+      const int xx = xi + g.pad - kx;
+      if (xx < 0 || xx % g.s != 0 || xx / g.s >= g.ow) continue;
+      acc += pr[(size_t)((ci * g.k + ky) * g.k + kx) * OP + y * g.ow + xx / g.s];
+    }
+  }
+  out[id] = acc;
+}
+
 // Per-layer BF16 weights, gather tables and tensor maps of one net, built on first use.
 struct ConvTc {
   struct ConvW {
@@ -444,6 +472,12 @@ struct ConvTc {
     CUtensorMap mb, mf;              // mb: the s * s phase matrices stacked, Np_b rows each
     int2 *tab_b = nullptr, *tab_f = nullptr;  // gather tables: [s * s][Kp_b], [Kp_f]
     __nv_bfloat16 *wb = nullptr, *wf = nullptr;  // fc: the B operands behind mb, mf
+    // scatter form of the backward pass (layers with in_c k^2 <= SCATTER_MAX_N): one GEMM
+    // P = Lambda^T W' over the output channels (K = out_c, N = in_c k^2), then col2im
+    bool scat = false;
+    int Np_s = 0, Kp_s = 0;
+    CUtensorMap ms;
+    int2* tab_s = nullptr;
   };
   std::vector<ConvW> conv;  // conv[i]: paper layer i
   std::vector<void*> bufs;
@@ -483,6 +517,15 @@ static ConvPhase conv_phase(int a, int k, int s, int pad, int in) {
 static int taps_per_axis(const LayerDev& l) { return (l.k + l.stride - 1) / l.stride; }
 static int kp_bwd(const LayerDev& l) { return pad_to(l.out_c * taps_per_axis(l) * taps_per_axis(l), 64); }
 static int kp_fwd(const LayerDev& l) { return pad_to(l.in_c * l.k * l.k, 64); }
+// The transposed convolution of a layer with few input channels is computed as
+//   P[(y, x)][(ci, ky, kx)] = sum_co Lambda[co][y][x] W[co][ci][ky][kx]   (one GEMM, K = out_c)
+//   A[ci][yi][xi] = sum over the taps (ky, kx) that reach (yi, xi) of P[(y, x)][(ci, ky, kx)]
+// instead of gathering out_c x taps source values per input position: for conv_big's first
+// layer (3 input channels, 3x3) that is K = 64 gathered values per position instead of 576.
+constexpr int SCATTER_MAX_N = 64;
+static bool scatter_form(const LayerDev& l) {
+  return l.kind == BCROWN_LAYER_CONV && l.in_c * l.k * l.k <= SCATTER_MAX_N && l.out_c <= 256;
+}
 // Gather table entry: source offset chan_off + dy * Ws + dx from a row's base position, and the
 // tap offsets for the bounds test; kNoTap marks a zero column.
 static int2 tab_entry(int chan_off, int dy, int dx, int Ws) {
@@ -522,7 +565,10 @@ size_t tcg_col_bytes_per_row(const bcrown_net* net, bool gather) {
       b = std::max(b, (size_t)std::max(pad_to(l.d_in, 64), pad_to(l.d_out, 64)) * sizeof(__nv_bfloat16));
       continue;
     }
-    if (gather) continue;   // conv operands are gathered in shared memory
+    if (gather) {   // conv operands are gathered in shared memory; the scatter form keeps P here
+      if (scatter_form(l)) b = std::max(b, (size_t)l.in_c * l.k * l.k * l.out_h * l.out_w * sizeof(float));
+      continue;
+    }
     const size_t ph = (size_t)((l.in_h + l.stride - 1) / l.stride) * ((l.in_w + l.stride - 1) / l.stride);
     const size_t bwd = ph * kp_bwd(l);
     const size_t fwd = (size_t)l.out_h * l.out_w * kp_fwd(l);
@@ -626,6 +672,29 @@ static int tcg_prepare(bcrown_net* net, ConvTc* t) {
       return fail(BCROWN_ERR_CUDA, "bf16 conv weights upload");
     BC_CHECK(encode_map(&c.mb, db, s * s * c.Np_b, c.Kp_b, c.Np_b));
     BC_CHECK(encode_map(&c.mf, df, c.Np_f, c.Kp_f, c.Np_f));
+    if (scatter_form(l)) {
+      // B operand [n = (ci, ky, kx)][K = co], K-major; gather table: channel co at the position itself
+      c.scat = true;
+      c.Np_s = pad_to(l.in_c * kk, 16);
+      c.Kp_s = pad_to(l.out_c, 64);
+      std::vector<__nv_bfloat16> ws((size_t)c.Np_s * c.Kp_s, zero);
+      std::vector<int2> ts((size_t)c.Kp_s, kNoTap);
+      for (int co = 0; co < l.out_c; ++co) {
+        ts[co] = tab_entry(co * l.out_h * l.out_w, 0, 0, l.out_w);
+        for (int ci = 0; ci < l.in_c; ++ci)
+          for (int q = 0; q < kk; ++q)
+            ws[(size_t)(ci * kk + q) * c.Kp_s + co] = __float2bfloat16_rn(w[((size_t)co * l.in_c + ci) * kk + q]);
+      }
+      __nv_bfloat16* dws = nullptr;
+      if (cudaMalloc(&dws, ws.size() * 2) != cudaSuccess || cudaMalloc(&c.tab_s, ts.size() * sizeof(int2)) != cudaSuccess)
+        return fail(BCROWN_ERR_OOM, "bf16 conv weights (scatter form)");
+      t->bufs.push_back(dws);
+      t->bufs.push_back(c.tab_s);
+      if (cudaMemcpy(dws, ws.data(), ws.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess ||
+          cudaMemcpy(c.tab_s, ts.data(), ts.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(BCROWN_ERR_CUDA, "bf16 conv weights upload (scatter form)");
+      BC_CHECK(encode_map(&c.ms, dws, c.Np_s, c.Kp_s, c.Np_s));
+    }
   }
   BC_CUDA(cudaFuncSetAttribute(k_tcg<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                tcg_smem(256, TCG_BIAS_MAX, true)));
@@ -701,6 +770,20 @@ int tcg_conv(bcrown_net* net, int i, bool fwd, int R, const float* src, float* d
     const Im2colPass q{(long long)R * P, P, l.out_w, l.stride, -l.pad, -l.pad, l.in_h, l.in_w, l.d_in, c.Kp_f, c.tab_f};
     const TcgOut o{q.M, l.out_c, c.Np_f, 1, c.Kp_f / 64, 0, P, l.out_w, 0, 0, 1, l.out_w, P, (long long)l.d_out};
     return tcg_pass(net, q, c.mf, o, src, dst, bias, col, col_bytes, s);
+  }
+  if (c.scat && tcg_gather(net)) {
+    const int P = l.out_h * l.out_w, Ns = l.in_c * l.k * l.k;
+    if ((size_t)R * Ns * P * sizeof(float) > col_bytes) return fail(BCROWN_ERR_OOM, "scatter-form workspace too small");
+    float* tmp = reinterpret_cast<float*>(col);
+    const Im2colPass q{(long long)R * P, P, l.out_w, 1, 0, 0, l.out_h, l.out_w, l.d_out, c.Kp_s, c.tab_s};
+    const TcgOut o{q.M, Ns, c.Np_s, 1, c.Kp_s / 64, 0, P, l.out_w, 0, 0, 1, l.out_w, P, (long long)Ns * P};
+    BC_CHECK(tcg_pass(net, q, c.ms, o, src, tmp, nullptr, col, col_bytes, s));
+    const Col2im g{l.in_c, l.in_h, l.in_w, l.k, l.stride, l.pad, l.out_h, l.out_w};
+    const long long total = (long long)R * l.d_in;
+    k_col2im<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(total, g, tmp, dst, l.d_in);
+    ++g_launches;
+    BC_CUDA(cudaGetLastError());
+    return BCROWN_OK;
   }
   const int st = l.stride;
   for (int a = 0; a < st; ++a)

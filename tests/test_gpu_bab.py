@@ -1,6 +1,7 @@
 """Branch and bound through the library (needs a GB300): the driver of Algorithm 1 on the GPU
 engine (BF16 iterations, FP32 certifying pass) reaches the verdicts the exact minima fix, like
-the oracle engine; and the ablation settings of the optimiser (alpha only, beta only)."""
+the oracle engine; the ablation settings of the optimiser (alpha only, beta only); and the
+driver with the joint intermediate-bound optimisation."""
 import numpy as np
 import pytest
 import torch
@@ -55,3 +56,16 @@ def test_ablation_settings_freeze_one_set_of_variables(frozen):
         assert np.abs(a - a0).max() > 0
     ref = O.bound(onet, props, batch, a, b)
     assert np.all(lb <= ref + 1e-12 * np.abs(ref))
+
+
+@pytest.mark.parametrize("name", ["verified_by_branching_a", "verified_by_branching_b"])
+def test_joint_mode_on_the_gpu_reaches_the_oracle_verdict_with_no_more_branching(name):
+    """The driver with the joint intermediate-bound optimisation on the GPU engine
+    (bcrown_optimize_joint): the verdict of the exact minima, and no more bounded subdomains than
+    the fixed-bound driver on the same engine."""
+    pb, exact, plain = run_case(name, gpu_engine, batch_size=256, max_rounds=12, n_samples=256)
+    _, _, joint = run_case(name, gpu_engine, batch_size=256, max_rounds=12, n_samples=256, joint=True)
+    print("%s: fixed bounds %d subdomains in %d rounds, joint %d in %d" % (name, plain.bounded, plain.rounds,
+                                                                          joint.bounded, joint.rounds))
+    check_verdict(name, pb, exact, joint)
+    assert joint.bounded <= plain.bounded

@@ -381,11 +381,13 @@ def test_bf16_conv_beyond_the_channel_limit_is_refused():
     assert np.max(rel_err(lb, O.bound(onet, props, batch, a, b))) <= RTOL
 
 
+@pytest.mark.parametrize("path", ["layer_gather", "layer_epi"])
 @pytest.mark.parametrize("which", ["conv_small", "conv_big"])
-def test_bf16_conv_full_size_sampled(which):
+def test_bf16_conv_full_size_sampled(which, path):
     """The conv workloads at their full sizes in BF16 (the bench's configuration: 2048 and 4096
-    BaB-tree subdomains x 9 specs in one bound pass); sampled subdomains recomputed by the
-    oracle one by one."""
+    BaB-tree subdomains x 9 specs in one bound pass), on the gather GEMMs the autotuner picks for
+    the bench and on the fused-epilogue GEMMs; sampled subdomains recomputed by the oracle one by
+    one."""
     if which == "conv_small":
         pb = wl.problem_conv_small()
         onet, props, unst = oracle_setup(pb)
@@ -401,11 +403,12 @@ def test_bf16_conv_full_size_sampled(which):
     batch = wl.tree_batch(pb, unst, [n], depth, 1)
     a, b = wl.random_alpha_beta(batch, 6, 1.0)
     net, dom, db = _gpu(pb, props, batch)
+    bc.set_launch(net, LAYER_PATHS[path])
     lb = bc.bound(net, dom, db, _t(a), _t(b), bc.BF16).cpu().numpy().reshape(batch.B, pb.K)
     assert bc.status(net) == 0 and batch.B == n
     idx = np.sort(np.random.default_rng(0).choice(batch.B, size=n_check, replace=False))
     sb, sa, sbeta = repack(pb, batch, [len(x) for x in unst], idx, a, b)
     ref = O.bound(onet, props, sb, sa, sbeta).reshape(len(idx), pb.K)
     err = np.abs(lb[idx] - ref) / _scale(ref)
-    print("%s full size, %d sampled subdomains: max err / median|lb| = %.3e" % (which, n_check, err.max()))
+    print("%s %s full size, %d sampled subdomains: max err / median|lb| = %.3e" % (which, path, n_check, err.max()))
     assert err.max() <= BF16_TOL[which]
