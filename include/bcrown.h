@@ -412,6 +412,13 @@ int bcrown_autotune(bcrown_net* net, const bcrown_domain* dom, const bcrown_batc
 int bcrown_bound_static(bcrown_net* net, const bcrown_domain* dom, const bcrown_batch* batch,
                         const float* alpha, const float* beta, float* lb, void* stream);
 
+/* The net's device workspace, which every call reuses (it grows when a call needs more; the
+ * growth synchronises the device and reallocates it): grows it to at least reserve_bytes (0:
+ * leaves it), then reports its address and size in *ptr, *bytes (either may be NULL).  A CUDA
+ * graph captured from calls on this net refers to the workspace: it stays valid while the
+ * address reported here is unchanged. */
+int bcrown_workspace(bcrown_net* net, int64_t reserve_bytes, void** ptr, int64_t* bytes);
+
 /* Synchronise `stream`, return the device status word of the net (BCROWN_OK or
  * the first device-detected error since the last call) and clear it. */
 int bcrown_status(bcrown_net* net, void* stream);

@@ -436,7 +436,7 @@ class GpuEngine:
     """Bounds through the library: bcrown_optimize with BF16 iterations (the tensor-core path)
     and the FP32 certifying pass, on the GPU; margins C f(x) in FP64 on the host."""
 
-    def __init__(self, problem, net, dom, unstable_counts, precision=None, iters=20):
+    def __init__(self, problem, net, dom, unstable_counts, precision=None, iters=20, graphs=False):
         from . import bcrown as bc
         self.bc = bc
         self.pb = problem
@@ -445,11 +445,17 @@ class GpuEngine:
         self.K = problem.K
         self.U = list(unstable_counts)
         self.cfg = bc.OptCfg(iters=iters, precision=bc.BF16 if precision is None else precision, certify=True)
+        # graphs: optimisation calls at the engine's settings replay a CUDA graph per batch-size bucket
+        self.graphs = bc.GraphOptimizer(net, dom, self.cfg, self.U) if graphs else None
 
     def optimize(self, subs, alpha, beta, iters=None, lr_alpha=None, lr_beta=None, decay=None, fp32=False):
         """The optimised, certified bound (bcrown_optimize); the keywords override the engine's
         settings for one call (fp32: FP32 iterations instead of BF16)."""
         import dataclasses
+        if self.graphs is not None and not fp32 and all(v is None for v in (iters, lr_alpha, lr_beta, decay)):
+            lb, a, b = self.graphs(wl.pack_batch(self.pb.hidden_widths, self.K, self.U, subs), alpha, beta)
+            self._check()
+            return lb, a, b
         db, at, bt = self._args(subs, alpha, beta)
         cfg = dataclasses.replace(self.cfg, **{k: v for k, v in dict(iters=iters, lr_alpha=lr_alpha, lr_beta=lr_beta,
                                                                       decay=decay).items() if v is not None})

@@ -430,3 +430,116 @@ def optimize_joint(net, dom, batch, alpha, beta, alpha_p, beta_p, cfg=None, stre
                                            _ptr(alpha_p), int(alpha_p.numel()), _ptr(beta_p), int(beta_p.numel()),
                                            _ptr(lb), _ptr(l), _ptr(u), _stream(stream)))
     return lb, l, u
+
+
+# ---- optimisation steps replayed from CUDA graphs, per bucket of the batch size ----
+
+def workspace(net, reserve=0):
+    """(address, bytes) of the net's device workspace after growing it to `reserve` bytes."""
+    p, n = C.c_void_p(), C.c_int64()
+    N.check(N.load().bcrown_workspace(net.handle, int(reserve), C.byref(p), C.byref(n)))
+    return p.value, n.value
+
+
+def bucket(n):
+    """n rounded up to a multiple of 2^(floor(log2 n) - 3): 8 buckets per power of two, at most
+    12.5 % padding (n <= 8 stays as it is)."""
+    n = int(n)
+    if n <= 8:
+        return max(n, 1)
+    g = 1 << (n.bit_length() - 4)
+    return (n + g - 1) // g * g
+
+
+class GraphOptimizer:
+    """bcrown_optimize replayed from a CUDA graph captured once per bucket of the batch sizes.
+
+    A batch of B subdomains is padded to bucket(B) subdomains with copies of its last one (their
+    rows are computed and dropped: rows are independent), and its alpha, beta and split arrays to
+    capacities that only the bucket fixes (K U_max alphas, K MAX_SPLITS betas and MAX_SPLITS split
+    entries per subdomain; entries past the real ones are referenced by no subdomain).  The first
+    batch of a bucket runs once eagerly (which sizes the net's workspace, converts weights and
+    builds tables), then one call is captured; later batches of the bucket copy their arrays into
+    the captured buffers and replay.  A graph refers to the net's workspace, so one whose
+    workspace has since been reallocated (a larger call on the same net) is captured again."""
+
+    def __init__(self, net, dom, cfg, unstable_counts):
+        self.net, self.dom, self.cfg = net, dom, cfg
+        self.U = np.asarray(unstable_counts, np.int64)
+        self.K = net.K
+        self.entries = {}
+        self.captures = 0
+
+    def _pad(self, hb, alpha, beta):
+        B, K = hb.B, self.K
+        Bb = bucket(B)
+        last = B - 1
+        o, c = int(hb.split_off[last]), int(hb.split_cnt[last])
+        na_last = int(self.U[hb.prop_of[last]]) * K
+        extra = Bb - B
+        prop = np.concatenate([hb.prop_of, np.full(extra, hb.prop_of[last], np.int32)]).astype(np.int32)
+        cnt = np.concatenate([hb.split_cnt, np.full(extra, c, np.int32)]).astype(np.int32)
+        off = np.concatenate([[0], np.cumsum(cnt)[:-1]]).astype(np.int32)
+        aoff = np.concatenate([hb.alpha_off, int(hb.alpha_off[last]) + na_last * np.arange(1, extra + 1)]).astype(np.int64)
+        lay = np.concatenate([hb.split_layer] + [hb.split_layer[o:o + c]] * extra)
+        idx = np.concatenate([hb.split_idx] + [hb.split_idx[o:o + c]] * extra)
+        sgn = np.concatenate([hb.split_sign] + [hb.split_sign[o:o + c]] * extra)
+        a_last = np.asarray(alpha[int(hb.alpha_off[last]):int(hb.alpha_off[last]) + na_last], np.float32)
+        b_last = np.asarray(beta[o * K:(o + c) * K], np.float32)
+        a = np.concatenate([np.asarray(alpha, np.float32)] + [a_last] * extra)
+        b = np.concatenate([np.asarray(beta, np.float32)] + [b_last] * extra)
+        # capacities fixed by the bucket alone (one graph per bucket, whatever the batch holds):
+        # K U_max alphas and K MAX_SPLITS betas per subdomain, MAX_SPLITS split entries
+        caps = (Bb, Bb * K * int(self.U.max(initial=0)), Bb * K * N.MAX_SPLITS, Bb * N.MAX_SPLITS)
+        return caps, dict(prop_of=prop, split_off=off, split_cnt=cnt, alpha_off=aoff, split_layer=lay,
+                          split_idx=idx, split_sign=sgn), a, b
+
+    def _capture(self, caps, arrays, a, b):
+        Bb, na, nb, ns = caps
+        dev = {"prop_of": torch.zeros(Bb, dtype=torch.int32, device="cuda"),
+               "split_off": torch.zeros(Bb, dtype=torch.int32, device="cuda"),
+               "split_cnt": torch.zeros(Bb, dtype=torch.int32, device="cuda"),
+               "alpha_off": torch.zeros(Bb, dtype=torch.int64, device="cuda"),
+               "split_layer": torch.zeros(max(ns, 1), dtype=torch.uint8, device="cuda"),
+               "split_idx": torch.zeros(max(ns, 1), dtype=torch.int32, device="cuda"),
+               "split_sign": torch.zeros(max(ns, 1), dtype=torch.int8, device="cuda")}
+        e = {"dev": dev, "alpha": torch.zeros(max(na, 1), device="cuda"), "beta": torch.zeros(max(nb, 1), device="cuda"),
+             "lb": torch.empty(Bb * self.K, device="cuda")}
+        e["db"] = DeviceBatch(dev["prop_of"], dev["split_off"], dev["split_cnt"], dev["split_layer"], dev["split_idx"],
+                              dev["split_sign"], dev["alpha_off"], na, nb)
+        self._load(e, arrays, a, b)
+        optimize(self.net, self.dom, e["db"], e["alpha"], e["beta"], self.cfg, out=e["lb"])   # sizes everything
+        torch.cuda.synchronize()
+        ws = workspace(self.net)[0]
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            optimize(self.net, self.dom, e["db"], e["alpha"], e["beta"], self.cfg, out=e["lb"])
+        torch.cuda.synchronize()
+        if workspace(self.net)[0] != ws:
+            raise RuntimeError("workspace reallocated during capture")
+        e["graph"], e["ws"] = g, ws
+        self.entries[caps] = e
+        self.captures += 1
+        return e
+
+    @staticmethod
+    def _load(e, arrays, a, b):
+        for k, v in arrays.items():
+            t = torch.from_numpy(np.ascontiguousarray(v.astype(np.int32) if k == "split_idx" else v))
+            e["dev"][k][:len(v)].copy_(t)
+        e["alpha"][:len(a)].copy_(torch.from_numpy(a))
+        e["beta"][:len(b)].copy_(torch.from_numpy(b))
+
+    def __call__(self, hb, alpha, beta):
+        """The optimised bounds (B K rows), alpha and beta of host batch hb (numpy outputs)."""
+        caps, arrays, a, b = self._pad(hb, alpha, beta)
+        e = self.entries.get(caps)
+        if e is not None and e["ws"] != workspace(self.net)[0]:
+            e = None
+        if e is None:
+            e = self._capture(caps, arrays, a, b)
+        self._load(e, arrays, a, b)
+        e["graph"].replay()
+        n = hb.B * self.K
+        return (e["lb"][:n].cpu().numpy(), e["alpha"][:hb.n_alpha].cpu().numpy(),
+                e["beta"][:hb.n_beta].cpu().numpy())

@@ -324,3 +324,15 @@ extern "C" int bcrown_profile_read(bcrown_net* net, int cls, double* total_ms, l
 }
 
 extern "C" long long bcrown_kernel_launches(void) { return g_launches.load(); }
+
+extern "C" int bcrown_workspace(bcrown_net* net, int64_t reserve_bytes, void** ptr, int64_t* bytes) {
+  if (!net || reserve_bytes < 0) return fail(BCROWN_ERR_ARG, "workspace: bad argument");
+  std::lock_guard<std::mutex> g(net->mu);
+  if (reserve_bytes > 0) {
+    int st = BCROWN_OK;
+    if (!ws_get(net, (size_t)reserve_bytes, &st)) return st;
+  }
+  if (ptr) *ptr = net->ws.ptr;
+  if (bytes) *bytes = (int64_t)net->ws.size;
+  return BCROWN_OK;
+}

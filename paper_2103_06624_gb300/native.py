@@ -23,7 +23,7 @@ EXPORTS = ["bcrown_load_net", "bcrown_free_net", "bcrown_net_info", "bcrown_root
            "bcrown_kernel_launches", "bcrown_bound_static", "bcrown_peak_probe", "bcrown_bound_xstar",
            "bcrown_forward", "bcrown_path_supported", "bcrown_set_launch", "bcrown_get_launch",
            "bcrown_autotune", "bcrown_joint_sizes", "bcrown_joint_init_alpha", "bcrown_bound_joint",
-           "bcrown_bound_joint_grad", "bcrown_optimize_joint"]
+           "bcrown_bound_joint_grad", "bcrown_optimize_joint", "bcrown_workspace"]
 FREEZE_ALPHA, FREEZE_BETA = 1, 2
 PATH_DEFAULT, PATH_FUSED, PATH_LAYER_EPI, PATH_LAYER_GATHER, PATH_LAYER_IM2COL = range(5)
 PATH_NAMES = {PATH_FUSED: "fused", PATH_LAYER_EPI: "layer_epi", PATH_LAYER_GATHER: "layer_gather",
@@ -109,6 +109,7 @@ def load(path=LIB_PATH):
         "bcrown_get_launch": ([vp, i32, C.POINTER(LaunchCfg)], i32),
         "bcrown_autotune": ([vp, C.POINTER(Domain), C.POINTER(Batch), vp, vp, i32, C.POINTER(LaunchCfg),
                              C.POINTER(C.c_double), i32, C.POINTER(i32), C.POINTER(LaunchCfg), vp], i32),
+        "bcrown_workspace": ([vp, C.c_int64, C.POINTER(vp), C.POINTER(C.c_int64)], i32),
         "bcrown_joint_sizes": ([vp, C.POINTER(Domain), C.POINTER(Batch), C.POINTER(C.c_int64),
                                 C.POINTER(C.c_int64), vp], i32),
         "bcrown_joint_init_alpha": ([vp, C.POINTER(Domain), C.POINTER(Batch), vp, C.c_int64, vp], i32),

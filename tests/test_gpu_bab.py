@@ -69,3 +69,20 @@ def test_joint_mode_on_the_gpu_reaches_the_oracle_verdict_with_no_more_branching
                                                                           joint.bounded, joint.rounds))
     check_verdict(name, pb, exact, joint)
     assert joint.bounded <= plain.bounded
+
+
+def test_graph_replayed_engine_gives_the_same_decisions():
+    """GpuEngine(graphs=True): every optimisation call at the engine's settings replays a CUDA
+    graph captured per batch-size bucket; the driver's verdict, round count and bounded subdomains
+    equal those of the eager engine."""
+    name = "verified_by_branching_a"
+
+    def graph_engine(pb, props, U):
+        net = bc.load_net(pb.layers, pb.C)
+        dom = bc.domain_from_host(props["x_lo"], props["x_hi"], props["l"], props["u"])
+        return bab.GpuEngine(pb, net, dom, U, graphs=True)
+
+    pb, exact, eager = run_case(name, gpu_engine, batch_size=256, max_rounds=12, n_samples=256)
+    _, _, replay = run_case(name, graph_engine, batch_size=256, max_rounds=12, n_samples=256)
+    check_verdict(name, pb, exact, replay)
+    assert (replay.status, replay.rounds, replay.bounded) == (eager.status, eager.rounds, eager.bounded)

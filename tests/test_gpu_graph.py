@@ -66,3 +66,30 @@ def test_optimize_replays_from_a_captured_graph(which):
     ref = O.bound(onet, props, batch, alpha.cpu().numpy(), beta.cpu().numpy())
     got = lb.cpu().numpy()
     assert np.all(got <= ref + 1e-9 * np.abs(ref))
+
+
+@pytest.mark.parametrize("which", ["mlp784", "tinyconv"])
+def test_bucketed_graph_replay_equals_the_eager_call(which):
+    """GraphOptimizer pads a batch to its size bucket (copies of its last subdomain; alpha, beta and
+    the split lists to bucketed capacities), captures bcrown_optimize once per bucket and replays
+    it.  Rows are independent, so every real row's bound, alpha and beta equal the eager call on
+    the unpadded batch bit for bit; batches of the same bucket share one graph."""
+    pb, props, _ = _problem(which)
+    net = bc.load_net(pb.layers, pb.C)
+    dom = bc.domain_from_host(props["x_lo"], props["x_hi"], props["l"], props["u"])
+    unst = [np.nonzero(O.unstable_mask(props["l"][p], props["u"][p]))[0] for p in range(pb.P)]
+    U = [len(u) for u in unst]
+    cfg = bc.OptCfg(precision=bc.BF16, certify=True)
+    go = bc.GraphOptimizer(net, dom, cfg, U)
+    sizes = (97, 100, 97, 120) if which == "mlp784" else (17, 18, 17, 24)
+    for n, seed in zip(sizes, (1, 2, 3, 4)):
+        hb = wl.random_batch(pb, unst, n, 0, 6, seed, props=np.arange(n) % pb.P)
+        a0, b0 = wl.random_alpha_beta(hb, seed, 0.5)
+        lb, a, b = go(hb, a0, b0)
+        at, bt = torch.as_tensor(a0).cuda(), torch.as_tensor(b0).cuda()
+        ref = bc.optimize(net, dom, bc.DeviceBatch.from_host(hb), at, bt, cfg).cpu().numpy()
+        assert bc.status(net) == 0
+        assert np.array_equal(lb, ref), (which, n, np.abs(lb - ref).max())
+        assert np.array_equal(a, at.cpu().numpy()) and np.array_equal(b, bt.cpu().numpy())
+        assert bc.bucket(n) >= n
+    assert go.captures == 2
