@@ -20,7 +20,9 @@
 // GEMM operand -- rows = (subdomain row, output position), K = (tap, channel) -- is gathered into
 // shared memory in 16-byte pieces of 8 channels, one load each; gather warps write it in the
 // 128-byte-swizzled K-major layout the MMA reads, TMA streams the weights, one thread issues the
-// MMAs into a double-buffered TMEM accumulator, and epilogue warps read it with tcgen05.ld.
+// MMAs into one of three TMEM accumulators (two for 256-column tiles), and three groups of 4
+// epilogue warps read them with tcgen05.ld, each group every third tile, so that up to three
+// tiles' epilogues run at once (576 threads: 12 epilogue, 1 TMA, 1 MMA and 4 gather warps).
 // The bias sums of each row are written as partial sums (one slot per position block and column
 // group) and added in a fixed order at the end, so the result does not depend on scheduling.
 // A at the unstable neurons is stashed in BF16, laid out like alpha, for the adjoint pass; its
@@ -45,8 +47,9 @@ namespace lt {
 using namespace tc;
 
 constexpr int NS = 4;                       // pipeline stages (A: 128 x 64, B: Np x 64)
-constexpr int EPI = 8;                      // epilogue warps: two groups of 4 (alternate tiles)
-constexpr int GPS = 2;                      // gather warps per stage
+constexpr int EPI = 12;                     // epilogue warps: three groups of 4 (every third tile)
+constexpr int NGRP = EPI / 4;               // epilogue groups, one TMEM accumulator each
+constexpr int GPS = 1;                      // gather warps per stage
 constexpr int GW = GPS * NS;
 constexpr int TMA_W = EPI, MMA_W = EPI + 1, GATHER0 = EPI + 2;
 constexpr int THREADS = (EPI + 2 + GW) * 32;
@@ -173,22 +176,26 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint64_t* full = bars;
   uint64_t* empty = bars + NS;
   uint64_t* acc_full = bars + 2 * NS;
-  uint64_t* acc_empty = bars + 2 * NS + 2;
-  uint32_t* tbase_sm = reinterpret_cast<uint32_t*>(bars + 2 * NS + 4);
+  uint64_t* acc_empty = bars + 2 * NS + NGRP;
+  uint32_t* tbase_sm = reinterpret_cast<uint32_t*>(bars + 2 * NS + 2 * NGRP);
   volatile int* abort = reinterpret_cast<volatile int*>(tbase_sm + 1);
   int2* stab = reinterpret_cast<int2*>(bars + 32);     // 256 bytes past the barriers
   float* sbias = reinterpret_cast<float*>(stab + MAX_KP / 8);   // conv passes: the layer's channel biases
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long ntiles = (M + 127) / 128 * ps.ntn;   // tile = m tile * ntn + n tile
-  const uint32_t tcols = Np <= 16 ? 32u : (Np <= 32 ? 64u : (Np <= 64 ? 128u : (Np <= 128 ? 256u : 512u)));
+  // accumulators in use: one per epilogue group, as many groups as NGRP x Np columns of TMEM
+  // allow (512 columns): all three up to Np = 160, two beyond (the third group then idles)
+  const int ngrp = NGRP * Np <= 512 ? NGRP : 2;
+  const uint32_t need = (uint32_t)(ngrp * Np);
+  const uint32_t tcols = need <= 32 ? 32u : (need <= 64 ? 64u : (need <= 128 ? 128u : (need <= 256 ? 256u : 512u)));
   if (threadIdx.x == 0) {
     for (int i = 0; i < NS; ++i) {
       mbar_init(&full[i], 1 + GPS);   // the TMA transaction and the stage's gather warps
       mbar_init(&empty[i], 1);
     }
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < NGRP; ++i) {
       mbar_init(&acc_full[i], 1);
-      mbar_init(&acc_empty[i], EPI / 2);   // the 4 warps of the epilogue group of buffer i
+      mbar_init(&acc_empty[i], 4);   // the 4 warps of the epilogue group of buffer i
     }
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -233,8 +240,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       bool ok = true;
       const uint32_t idesc = idesc_bf16(Np);
       for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++accseq) {
-        const int buf = accseq & 1;
-        if (!lt_wait(&acc_empty[buf], ((accseq >> 1) & 1) ^ 1, abort, cx.status)) break;
+        const int buf = (int)(accseq % (uint32_t)ngrp);
+        if (!lt_wait(&acc_empty[buf], ((accseq / (uint32_t)ngrp) & 1) ^ 1, abort, cx.status)) break;
         tc_fence_after();
         const uint32_t dt = tmem + (uint32_t)(buf * Np);
         for (int kb = 0; kb < nkb; ++kb, ++seq) {
@@ -254,7 +261,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else if (warp >= GATHER0) {
     // ------------------------------------------------------------ operand (A) gather
     // ring slot g takes sequence numbers g, g + NS, ... of the (tile, K block) order; this warp
-    // writes chunks 4 part .. 4 part + 3 (of 8 per row) of its slot's stages
+    // writes chunks CPW part .. CPW part + CPW - 1 (of 8 per row) of its slot's stages
     const int g = (warp - GATHER0) % NS, part = (warp - GATHER0) / NS;
     constexpr int CPW = 8 / GPS;
     const bool linear = ps.tab == nullptr;
@@ -287,25 +294,29 @@ __global__ void __launch_bounds__(THREADS, 1)
           break;
         }
         uint8_t* stage = sA + g * 16384;
-        uint4 v[CPW][4];
+        // 4 chunks (of 4 rows each) in flight at a time: 16 loads of 16 bytes per lane
 #pragma unroll
-        for (int cc = 0; cc < CPW; ++cc) {
-          const int kc = kb * 8 + CPW * part + cc;
-          const int2 t = kc < ps.kchunks ? (linear ? make_int2(8 * kc, 0) : stab[kc]) : make_int2(0, 0x8000);
-          const int dy = (int)(short)(t.y & 0xffff), dx = t.y >> 16;
+        for (int c0 = 0; c0 < CPW; c0 += 4) {
+          uint4 v[4][4];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const bool in = (unsigned)(y0[q] + dy) < (unsigned)ps.Hs && (unsigned)(x0[q] + dx) < (unsigned)ps.Ws;
-            v[cc][q] = ldg_nc_v4(srow[q] + t.x, in);
+          for (int cc = 0; cc < 4; ++cc) {
+            const int kc = kb * 8 + CPW * part + c0 + cc;
+            const int2 t = kc < ps.kchunks ? (linear ? make_int2(8 * kc, 0) : stab[kc]) : make_int2(0, 0x8000);
+            const int dy = (int)(short)(t.y & 0xffff), dx = t.y >> 16;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const bool in = (unsigned)(y0[q] + dy) < (unsigned)ps.Hs && (unsigned)(x0[q] + dx) < (unsigned)ps.Ws;
+              v[cc][q] = ldg_nc_v4(srow[q] + t.x, in);
+            }
           }
-        }
 #pragma unroll
-        for (int cc = 0; cc < CPW; ++cc) {
-          const int c = CPW * part + cc;
+          for (int cc = 0; cc < 4; ++cc) {
+            const int c = CPW * part + c0 + cc;
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int m = lane + 32 * q;
-            *reinterpret_cast<uint4*>(stage + m * 128 + ((c ^ (m & 7)) << 4)) = v[cc][q];
+            for (int q = 0; q < 4; ++q) {
+              const int m = lane + 32 * q;
+              *reinterpret_cast<uint4*>(stage + m * 128 + ((c ^ (m & 7)) << 4)) = v[cc][q];
+            }
           }
         }
         fence_proxy_async();   // generic-proxy stores of the stage, before the MMA reads it
@@ -315,11 +326,11 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
   } else {
     // ------------------------------------------------------------ epilogue
-    // two groups of 4 warps take alternate tiles (group g: accumulator buffer g), so that two
-    // tiles' epilogues overlap; warp w of a group reads TMEM lanes 32 (w % 4) .. + 31 (M rows)
-    // and every column chunk of 16
+    // ngrp groups of 4 warps take every ngrp-th tile (group g: accumulator buffer g), so that
+    // their tiles' epilogues overlap; warp w of a group reads TMEM lanes 32 (w % 4) .. + 31 (M
+    // rows) and every column chunk of 8
     const int q4 = warp & 3, eg = warp >> 2;
-    uint32_t accseq = eg;
+    uint32_t accseq = eg;   // this group takes the CTA's tiles eg, eg + ngrp, ...
     const bool sb_smem = MODE != EPI_CONCRETIZE && !ps.npos && ps.Cpo <= MAX_NP;
     if (sb_smem) {
       // a conv layer's bias is per channel: bnhwc at position 0
@@ -327,8 +338,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       asm volatile("bar.sync 1, %0;" ::"n"(EPI * 32) : "memory");
     }
     const bool warp_sum_ok = (ps.Pm & 31) == 0;   // 32 lanes = 32 positions of one row
-    for (long long tile = blockIdx.x + (long long)eg * gridDim.x; tile < ntiles; tile += 2LL * gridDim.x, accseq += 2) {
-      const int buf = accseq & 1;
+    for (long long tile = blockIdx.x + (long long)eg * gridDim.x; eg < ngrp && tile < ntiles;
+         tile += (long long)ngrp * gridDim.x, accseq += ngrp) {
+      const int buf = eg;
       const int nt = (int)(tile % ps.ntn);
       const long long m = tile / ps.ntn * 128 + 32 * q4 + lane;
       const bool mv = m < M;
@@ -375,7 +387,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
       }
       int okw = 1;
-      if (lane == 0) okw = lt_wait(&acc_full[buf], (accseq >> 1) & 1, abort, cx.status) ? 1 : 0;
+      if (lane == 0) okw = lt_wait(&acc_full[buf], (accseq / (uint32_t)ngrp) & 1, abort, cx.status) ? 1 : 0;
       okw = __shfl_sync(0xffffffffu, okw, 0);
       if (!okw) break;
       tc_fence_after();
