@@ -47,12 +47,17 @@ namespace lt {
 using namespace tc;
 
 constexpr int NS = 4;                       // pipeline stages (A: 128 x 64, B: Np x 64)
-constexpr int EPI = 12;                     // epilogue warps: three groups of 4 (every third tile)
-constexpr int NGRP = EPI / 4;               // epilogue groups, one TMEM accumulator each
-constexpr int GPS = 1;                      // gather warps per stage
-constexpr int GW = GPS * NS;
-constexpr int TMA_W = EPI, MMA_W = EPI + 1, GATHER0 = EPI + 2;
-constexpr int THREADS = (EPI + 2 + GW) * 32;
+// Warp roles.  Gathered A operand: 12 epilogue warps (three groups of 4, every third tile) and 4
+// gather warps (one per ring slot).  A operand by TMA: 16 epilogue warps (four groups).  Both with
+// the TMA and the MMA warp: 18 warps, which leaves 96 registers a thread.
+template <bool TA>
+struct LtRoles {
+  static constexpr int EPI = TA ? 16 : 12;   // epilogue warps
+  static constexpr int NGRP = EPI / 4;       // epilogue groups, one TMEM accumulator each
+  static constexpr int GW = TA ? 0 : NS;     // gather warps, one per ring slot
+  static constexpr int TMA_W = EPI, MMA_W = EPI + 1, GATHER0 = EPI + 2;
+};
+constexpr int THREADS = 18 * 32;
 constexpr int MAX_NP = 256;
 constexpr int MAX_KP = 2048;
 constexpr int MAX_KEEP = 6;                 // splits of a row kept in registers per tile
@@ -84,6 +89,11 @@ struct Pass {
   const uint32_t* ntab;      // its neurons in NHWC order, property 0 (stride Ctx::NH per property):
                              // code (0 inactive, 1 active, 2 unstable) | rank among the unstable << 2
   int slot0;                 // first partial-sum slot of this pass
+  // A operand by TMA instead of the gather warps: 0 gathered; 4: one box [64 channels][bw][bh][br]
+  // of the NHWC source per (tap, 64-channel block) -- an M tile is br rows x bh x bw positions;
+  // 2: one box [64][128 rows] of a fully connected pass's linear source
+  int ta = 0, bw = 0, bh = 0, br = 0;
+  const int4* ktab = nullptr;   // ta == 4: per K block {first channel, dy, dx, tap in use}
 };
 
 // Per-call context of the epilogues.
@@ -161,9 +171,11 @@ __device__ __forceinline__ float lt_warp_sum(float v) {
   return v;
 }
 
-template <int MODE>
+template <int MODE, bool TA>
 __global__ void __launch_bounds__(THREADS, 1)
-    k_lt(const __grid_constant__ CUtensorMap mapB, const Pass ps, const Ctx cx) {
+    k_lt(const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapA, const Pass ps,
+         const Ctx cx) {
+  using RL = LtRoles<TA>;
   const long long M = ps.M;
   const int Np = ps.Np, nkb = ps.nkb;
   extern __shared__ __align__(1024) uint8_t lsm_raw[];
@@ -175,32 +187,32 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint64_t* bars = reinterpret_cast<uint64_t*>(sB + NS * bbytes);
   uint64_t* full = bars;
   uint64_t* empty = bars + NS;
-  uint64_t* acc_full = bars + 2 * NS;
-  uint64_t* acc_empty = bars + 2 * NS + NGRP;
-  uint32_t* tbase_sm = reinterpret_cast<uint32_t*>(bars + 2 * NS + 2 * NGRP);
+  uint64_t* acc_full = bars + 2 * NS;        // up to 4 accumulators
+  uint64_t* acc_empty = bars + 2 * NS + 4;
+  uint32_t* tbase_sm = reinterpret_cast<uint32_t*>(bars + 2 * NS + 8);
   volatile int* abort = reinterpret_cast<volatile int*>(tbase_sm + 1);
   int2* stab = reinterpret_cast<int2*>(bars + 32);     // 256 bytes past the barriers
   float* sbias = reinterpret_cast<float*>(stab + MAX_KP / 8);   // conv passes: the layer's channel biases
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long ntiles = (M + 127) / 128 * ps.ntn;   // tile = m tile * ntn + n tile
-  // accumulators in use: one per epilogue group, as many groups as NGRP x Np columns of TMEM
-  // allow (512 columns): all three up to Np = 160, two beyond (the third group then idles)
-  const int ngrp = NGRP * Np <= 512 ? NGRP : 2;
+  // accumulators in use: one per epilogue group, as many groups as their Np columns each fit in
+  // TMEM's 512 (the other groups then idle)
+  const int ngrp = RL::NGRP * Np <= 512 ? RL::NGRP : (3 * Np <= 512 ? 3 : 2);
   const uint32_t need = (uint32_t)(ngrp * Np);
   const uint32_t tcols = need <= 32 ? 32u : (need <= 64 ? 64u : (need <= 128 ? 128u : (need <= 256 ? 256u : 512u)));
   if (threadIdx.x == 0) {
     for (int i = 0; i < NS; ++i) {
-      mbar_init(&full[i], 1 + GPS);   // the TMA transaction and the stage's gather warps
+      mbar_init(&full[i], TA ? 1 : 2);   // the TMA transaction (and the stage's gather warp)
       mbar_init(&empty[i], 1);
     }
-    for (int i = 0; i < NGRP; ++i) {
+    for (int i = 0; i < RL::NGRP; ++i) {
       mbar_init(&acc_full[i], 1);
       mbar_init(&acc_empty[i], 4);   // the 4 warps of the epilogue group of buffer i
     }
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == MMA_W) {
+  if (warp == RL::MMA_W) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tbase_sm)), "r"(tcols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -210,8 +222,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   tc_fence_after();
   const uint32_t tmem = *tbase_sm;
 
-  if (warp == TMA_W) {
-    // ------------------------------------------------------------ weights (B operand) by TMA
+  if (warp == RL::TMA_W) {
+    // ------------------------------------------------------------ weights (B) by TMA, and A with TA
     if (lane == 0) {
       uint32_t seq = 0;
       bool ok = true;
@@ -222,7 +234,22 @@ __global__ void __launch_bounds__(THREADS, 1)
             ok = false;
             break;
           }
-          mbar_expect_tx(&full[st], (uint32_t)bbytes);
+          mbar_expect_tx(&full[st], (TA ? 16384u : 0u) + (uint32_t)bbytes);
+          if constexpr (TA) {
+            const long long m0 = tile / ps.ntn * 128;
+            if (ps.ta == 2) {
+              tma_load_2d(sA + st * 16384, &mapA, kb * 64, (int)m0, &full[st]);
+            } else {
+              // the tile's first position (i0, j0) of row r0; the box starts at its source
+              const long long r0 = m0 / ps.Pm;
+              const int pp0 = (int)(m0 - r0 * ps.Pm);
+              const int i0 = pp0 / ps.nJ, j0 = pp0 - i0 * ps.nJ;
+              const int4 kt = ps.ktab[kb];
+              // a K block past the phase's taps reads a box outside the map: zeros
+              const int y = kt.w ? i0 + ps.cy + kt.y : -(1 << 20);
+              tma_load_4d(sA + st * 16384, &mapA, kt.x, j0 + ps.cx + kt.z, y, (int)r0, &full[st]);
+            }
+          }
           tma_load_2d(sB + st * bbytes, &mapB, kb * 64, ps.brow + (int)(tile % ps.ntn) * Np, &full[st]);
         }
       if (!ok) {
@@ -233,7 +260,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
       }
     }
-  } else if (warp == MMA_W) {
+  } else if (warp == RL::MMA_W) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       uint32_t seq = 0, accseq = 0;
@@ -258,15 +285,16 @@ __global__ void __launch_bounds__(THREADS, 1)
         umma_commit(&acc_full[buf]);
       }
     }
-  } else if (warp >= GATHER0) {
+  } else if (!TA && warp >= RL::GATHER0) {
     // ------------------------------------------------------------ operand (A) gather
     // ring slot g takes sequence numbers g, g + NS, ... of the (tile, K block) order; this warp
     // writes chunks CPW part .. CPW part + CPW - 1 (of 8 per row) of its slot's stages
-    const int g = (warp - GATHER0) % NS, part = (warp - GATHER0) / NS;
-    constexpr int CPW = 8 / GPS;
+    const int g = (warp - RL::GATHER0) % NS, part = 0;
+    constexpr int CPW = 8;
+    constexpr int GW = RL::GW > 0 ? RL::GW : 1;
     const bool linear = ps.tab == nullptr;
     if (!linear)
-      for (int k = threadIdx.x - GATHER0 * 32; k < ps.kchunks; k += GW * 32) stab[k] = ps.tab[k];
+      for (int k = threadIdx.x - RL::GATHER0 * 32; k < ps.kchunks; k += GW * 32) stab[k] = ps.tab[k];
     asm volatile("bar.sync 2, %0;" ::"n"(GW * 32) : "memory");
     uint32_t seq = 0;
     bool ok = true;
@@ -334,8 +362,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     const bool sb_smem = MODE != EPI_CONCRETIZE && !ps.npos && ps.Cpo <= MAX_NP;
     if (sb_smem) {
       // a conv layer's bias is per channel: bnhwc at position 0
-      for (int c = threadIdx.x; c < MAX_NP; c += EPI * 32) sbias[c] = c < ps.Cpo ? ps.bnhwc[c] : 0.f;
-      asm volatile("bar.sync 1, %0;" ::"n"(EPI * 32) : "memory");
+      for (int c = threadIdx.x; c < MAX_NP; c += RL::EPI * 32) sbias[c] = c < ps.Cpo ? ps.bnhwc[c] : 0.f;
+      asm volatile("bar.sync 1, %0;" ::"n"(RL::EPI * 32) : "memory");
     }
     const bool warp_sum_ok = (ps.Pm & 31) == 0;   // 32 lanes = 32 positions of one row
     for (long long tile = blockIdx.x + (long long)eg * gridDim.x; eg < ngrp && tile < ntiles;
@@ -563,7 +591,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == MMA_W) {
+  if (warp == RL::MMA_W) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols) : "memory");
   }
@@ -882,6 +910,33 @@ int prepare(bcrown_net* net, LtNet* t) {
       BC_CHECK(upload(t, tab.data(), tab.size() * sizeof(int2), &d));
       pp.tab = reinterpret_cast<int2*>(d);
       pp.p.tab = pp.tab;
+      // The A operand by TMA where an M tile is one box of the NHWC source (whole rows of the
+      // pass's position grid, or whole grids of consecutive subdomain rows) and each K block is
+      // one tap's 64-channel block (source channels a multiple of 64, unit position step).
+      Pass& q = pp.p;
+      int bw = 0, bh = 0, br = 0;
+      if (q.ms == 1 && q.Cps % 64 == 0 && q.nJ > 0 && q.Pm > 0) {
+        if (q.Pm % 128 == 0) {
+          if (q.nJ <= 128 && 128 % q.nJ == 0) bw = q.nJ, bh = 128 / q.nJ, br = 1;
+          else if (q.nJ % 128 == 0) bw = 128, bh = 1, br = 1;
+        } else if (128 % q.Pm == 0 && q.Pm % q.nJ == 0) {
+          bw = q.nJ, bh = q.Pm / q.nJ, br = 128 / q.Pm;
+        }
+      }
+      if (bw > 0 && bw * bh * br == 128 && (size_t)q.nkb * 8 == tab.size()) {
+        const int cpb = q.Cps / 64;
+        std::vector<int4> kt((size_t)q.nkb);
+        for (int kb = 0; kb < q.nkb; ++kb) {
+          const int2 e = tab[(size_t)kb * 8];
+          const int dy = (int)(short)(e.y & 0xffff), dx = e.y >> 16;
+          const bool used = dy != -32768;
+          kt[kb] = make_int4((kb % cpb) * 64, used ? dy : 0, used ? dx : 0, used ? 1 : 0);
+        }
+        void* dk = nullptr;
+        BC_CHECK(upload(t, kt.data(), kt.size() * sizeof(int4), &dk));
+        q.ktab = reinterpret_cast<const int4*>(dk);
+        q.ta = 4, q.bw = bw, q.bh = bh, q.br = br;
+      }
       return BCROWN_OK;
     };
     if (l.kind == BCROWN_LAYER_CONV) {
@@ -923,7 +978,6 @@ int prepare(bcrown_net* net, LtNet* t) {
           q.layer = i - 1;
           q.hoff = i >= 2 ? net->hoff[i - 2] : 0;
           q.bias = i >= 2 ? net->ly[i - 2].b : nullptr;
-      q.bnhwc = i >= 2 ? t->bnhwc[i - 1] : nullptr;
           q.bnhwc = i >= 2 ? t->bnhwc[i - 1] : nullptr;
           std::vector<int2> tab((size_t)kp / 8, kNoChunk);
           for (int dy = 0; dy < py.nk; ++dy)
@@ -1036,6 +1090,7 @@ int prepare(bcrown_net* net, LtNet* t) {
       q.bnhwc = i >= 2 ? t->bnhwc[i - 1] : nullptr;
       q.kchunks = mi.Cp / 8;   // K chunks past the layer's padded width read as zero
       q.tab = nullptr;
+      q.ta = 2;   // the linear source: the A operand by TMA, 64 x 128-row boxes
       q.slot0 = slot;
       slot += ntn;
       P.bwd.push_back(pp);
@@ -1060,6 +1115,7 @@ int prepare(bcrown_net* net, LtNet* t) {
       f.Cps = mo.Cp;
       f.kchunks = din_n / 8;
       f.tab = nullptr;
+      f.ta = 2;
       f.npos = 0;
       f.Co = mi.C;
       f.HWo = 1;
@@ -1082,9 +1138,14 @@ int prepare(bcrown_net* net, LtNet* t) {
     BC_CHECK(upload(t, wd.data(), wd.size() * sizeof(int), &d));
     t->width = reinterpret_cast<int*>(d);
   }
-  BC_CUDA(cudaFuncSetAttribute(k_lt<EPI_RELAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, lt_smem(MAX_NP)));
-  BC_CUDA(cudaFuncSetAttribute(k_lt<EPI_CONCRETIZE>, cudaFuncAttributeMaxDynamicSharedMemorySize, lt_smem(MAX_NP)));
-  BC_CUDA(cudaFuncSetAttribute(k_lt<EPI_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, lt_smem(MAX_NP)));
+  BC_CUDA(cudaFuncSetAttribute(k_lt<EPI_RELAX, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lt_smem(MAX_NP)));
+  BC_CUDA(cudaFuncSetAttribute(k_lt<EPI_CONCRETIZE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               lt_smem(MAX_NP)));
+  BC_CUDA(cudaFuncSetAttribute(k_lt<EPI_FWD, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lt_smem(MAX_NP)));
+  BC_CUDA(cudaFuncSetAttribute(k_lt<EPI_RELAX, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lt_smem(MAX_NP)));
+  BC_CUDA(cudaFuncSetAttribute(k_lt<EPI_CONCRETIZE, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               lt_smem(MAX_NP)));
+  BC_CUDA(cudaFuncSetAttribute(k_lt<EPI_FWD, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lt_smem(MAX_NP)));
   t->ready = true;
   return BCROWN_OK;
 }
@@ -1099,9 +1160,28 @@ int launch_pass(bcrown_net* net, const CUtensorMap& mB, Pass q, int mode, const 
   const int grid = (int)std::min<long long>(ntiles, sms);
   const int smem = lt_smem(q.Np);
   ProfScope pr(net, BCROWN_PROF_LAYER_GEMM, s);
-  if (mode == EPI_RELAX) k_lt<EPI_RELAX><<<grid, THREADS, smem, s>>>(mB, q, cx);
-  else if (mode == EPI_CONCRETIZE) k_lt<EPI_CONCRETIZE><<<grid, THREADS, smem, s>>>(mB, q, cx);
-  else k_lt<EPI_FWD><<<grid, THREADS, smem, s>>>(mB, q, cx);
+  // the A operand's map for this launch (the source buffer and the rows of this chunk)
+  CUtensorMap mA = mB;   // unused by the gathering kernel
+  if (q.ta == 4) {
+    const cuuint64_t dims[4] = {(cuuint64_t)q.Cps, (cuuint64_t)q.Ws, (cuuint64_t)q.Hs, (cuuint64_t)cx.R};
+    const cuuint64_t strides[3] = {(cuuint64_t)q.Cps * 2, (cuuint64_t)q.Ws * q.Cps * 2, (cuuint64_t)q.src_stride * 2};
+    const cuuint32_t box[4] = {64, (cuuint32_t)q.bw, (cuuint32_t)q.bh, (cuuint32_t)q.br};
+    BC_CHECK(encode_map_nd(&mA, const_cast<__nv_bfloat16*>(q.src), 4, dims, strides, box));
+  } else if (q.ta == 2) {
+    const cuuint64_t dims[2] = {(cuuint64_t)q.kchunks * 8, (cuuint64_t)cx.R};
+    const cuuint64_t strides[1] = {(cuuint64_t)q.src_stride * 2};
+    const cuuint32_t box[2] = {64, 128};
+    BC_CHECK(encode_map_nd(&mA, const_cast<__nv_bfloat16*>(q.src), 2, dims, strides, box));
+  }
+  if (q.ta) {
+    if (mode == EPI_RELAX) k_lt<EPI_RELAX, true><<<grid, THREADS, smem, s>>>(mB, mA, q, cx);
+    else if (mode == EPI_CONCRETIZE) k_lt<EPI_CONCRETIZE, true><<<grid, THREADS, smem, s>>>(mB, mA, q, cx);
+    else k_lt<EPI_FWD, true><<<grid, THREADS, smem, s>>>(mB, mA, q, cx);
+  } else {
+    if (mode == EPI_RELAX) k_lt<EPI_RELAX, false><<<grid, THREADS, smem, s>>>(mB, mA, q, cx);
+    else if (mode == EPI_CONCRETIZE) k_lt<EPI_CONCRETIZE, false><<<grid, THREADS, smem, s>>>(mB, mA, q, cx);
+    else k_lt<EPI_FWD, false><<<grid, THREADS, smem, s>>>(mB, mA, q, cx);
+  }
   ++g_launches;
   BC_CUDA(cudaGetLastError());
   return BCROWN_OK;
