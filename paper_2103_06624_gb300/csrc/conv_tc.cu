@@ -270,7 +270,10 @@ __global__ void __launch_bounds__(TcgRoles<GATHER>::THREADS, 1)
     if (lane == 0) {
       uint32_t seq = 0;
       bool ok = true;
-      for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x)
+      for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        // the tile's coordinates once per tile: the K loop of this one thread holds no division
+        const long long mt = tile / o.ntn;
+        const int arow = (int)(mt * 128), brow = o.brow + (int)(tile - mt * o.ntn) * Np;
         for (int kb = 0; kb < nkb; ++kb, ++seq) {
           const int st = seq % TCG_NS;
           if (!tcg_wait(&empty[st], ((seq / TCG_NS) & 1) ^ 1, abort, status)) {
@@ -278,9 +281,10 @@ __global__ void __launch_bounds__(TcgRoles<GATHER>::THREADS, 1)
             break;
           }
           mbar_expect_tx(&full[st], (GATHER ? 0u : 16384u) + (uint32_t)bbytes);
-          if (!GATHER) tma_load_2d(sA + st * 16384, &mapA, kb * 64, (int)(tile / o.ntn * 128), &full[st]);
-          tma_load_2d(sB + st * bbytes, &mapB, kb * 64, o.brow + (int)(tile % o.ntn) * Np, &full[st]);
+          if (!GATHER) tma_load_2d(sA + st * 16384, &mapA, kb * 64, arow, &full[st]);
+          tma_load_2d(sB + st * bbytes, &mapB, kb * 64, brow, &full[st]);
         }
+      }
       if (!ok) {
         for (uint32_t q = (seq > TCG_NS ? seq - TCG_NS : 0); q < seq; ++q) {
           long long t0 = clock64();

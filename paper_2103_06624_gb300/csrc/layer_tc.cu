@@ -224,34 +224,56 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   if (warp == RL::TMA_W) {
     // ------------------------------------------------------------ weights (B) by TMA, and A with TA
+    // One thread issues every copy, so its loop holds no division and no global load per K
+    // block: the tile's coordinates are worked out once per tile, the tap table is in shared
+    // memory (the gathering kernel's table space).
+    int4* sktab = reinterpret_cast<int4*>(stab);
+    if (TA && ps.ta == 4) {
+      for (int k = lane; k < nkb; k += 32) sktab[k] = ps.ktab[k];
+      __syncwarp();
+    }
     if (lane == 0) {
       uint32_t seq = 0;
+      int st = 0;
+      uint32_t ph = 0;   // parity of the current pass over the ring
       bool ok = true;
-      for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x)
+      for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const long long mt = tile / ps.ntn;
+        const int brow = ps.brow + (int)(tile - mt * ps.ntn) * Np;
+        int ax = 0, ay = 0, ar = 0;   // TA: the box origin of the tile's first position, tap 0
+        if constexpr (TA) {
+          const long long m0 = mt * 128;
+          if (ps.ta == 2) {
+            ar = (int)m0;
+          } else {
+            const long long r0 = m0 / ps.Pm;
+            const int pp0 = (int)(m0 - r0 * ps.Pm);
+            const int i0 = pp0 / ps.nJ;
+            ax = pp0 - i0 * ps.nJ + ps.cx;
+            ay = i0 + ps.cy;
+            ar = (int)r0;
+          }
+        }
         for (int kb = 0; kb < nkb; ++kb, ++seq) {
-          const int st = seq % NS;
-          if (!lt_wait(&empty[st], ((seq / NS) & 1) ^ 1, abort, cx.status)) {
+          if (!lt_wait(&empty[st], ph ^ 1, abort, cx.status)) {
             ok = false;
             break;
           }
           mbar_expect_tx(&full[st], (TA ? 16384u : 0u) + (uint32_t)bbytes);
           if constexpr (TA) {
-            const long long m0 = tile / ps.ntn * 128;
             if (ps.ta == 2) {
-              tma_load_2d(sA + st * 16384, &mapA, kb * 64, (int)m0, &full[st]);
+              tma_load_2d(sA + st * 16384, &mapA, kb * 64, ar, &full[st]);
             } else {
-              // the tile's first position (i0, j0) of row r0; the box starts at its source
-              const long long r0 = m0 / ps.Pm;
-              const int pp0 = (int)(m0 - r0 * ps.Pm);
-              const int i0 = pp0 / ps.nJ, j0 = pp0 - i0 * ps.nJ;
-              const int4 kt = ps.ktab[kb];
+              const int4 kt = sktab[kb];
               // a K block past the phase's taps reads a box outside the map: zeros
-              const int y = kt.w ? i0 + ps.cy + kt.y : -(1 << 20);
-              tma_load_4d(sA + st * 16384, &mapA, kt.x, j0 + ps.cx + kt.z, y, (int)r0, &full[st]);
+              const int y = kt.w ? ay + kt.y : -(1 << 20);
+              tma_load_4d(sA + st * 16384, &mapA, kt.x, ax + kt.z, y, ar, &full[st]);
             }
           }
-          tma_load_2d(sB + st * bbytes, &mapB, kb * 64, ps.brow + (int)(tile % ps.ntn) * Np, &full[st]);
+          tma_load_2d(sB + st * bbytes, &mapB, kb * 64, brow, &full[st]);
+          if (++st == NS) st = 0, ph ^= 1;
         }
+      }
       if (!ok) {
         for (uint32_t q = (seq > NS ? seq - NS : 0); q < seq; ++q) {
           long long t0 = clock64();
