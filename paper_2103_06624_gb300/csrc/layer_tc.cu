@@ -50,14 +50,19 @@ constexpr int NS = 4;                       // pipeline stages (A: 128 x 64, B: 
 // Warp roles.  Gathered A operand: 12 epilogue warps (three groups of 4, every third tile) and 4
 // gather warps (one per ring slot).  A operand by TMA: 16 epilogue warps (four groups).  Both with
 // the TMA and the MMA warp: 18 warps, which leaves 96 registers a thread.
+// LT_TA_GROUPS: epilogue groups of the TMA form (4: 18 warps, 96 registers a thread -- 5 warps on
+// two of the SM's four schedulers; 3: 14 warps, 128 registers).
+#ifndef LT_TA_GROUPS
+#define LT_TA_GROUPS 4
+#endif
 template <bool TA>
 struct LtRoles {
-  static constexpr int EPI = TA ? 16 : 12;   // epilogue warps
+  static constexpr int EPI = TA ? 4 * LT_TA_GROUPS : 12;   // epilogue warps
   static constexpr int NGRP = EPI / 4;       // epilogue groups, one TMEM accumulator each
   static constexpr int GW = TA ? 0 : NS;     // gather warps, one per ring slot
   static constexpr int TMA_W = EPI, MMA_W = EPI + 1, GATHER0 = EPI + 2;
+  static constexpr int THREADS = (EPI + 2 + GW) * 32;
 };
-constexpr int THREADS = 18 * 32;
 constexpr int MAX_NP = 256;
 constexpr int MAX_KP = 2048;
 constexpr int MAX_KEEP = 6;                 // splits of a row kept in registers per tile
@@ -172,7 +177,7 @@ __device__ __forceinline__ float lt_warp_sum(float v) {
 }
 
 template <int MODE, bool TA>
-__global__ void __launch_bounds__(THREADS, 1)
+__global__ void __launch_bounds__(LtRoles<TA>::THREADS, 1)
     k_lt(const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapA, const Pass ps,
          const Ctx cx) {
   using RL = LtRoles<TA>;
@@ -197,7 +202,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   const long long ntiles = (M + 127) / 128 * ps.ntn;   // tile = m tile * ntn + n tile
   // accumulators in use: one per epilogue group, as many groups as their Np columns each fit in
   // TMEM's 512 (the other groups then idle)
-  const int ngrp = RL::NGRP * Np <= 512 ? RL::NGRP : (3 * Np <= 512 ? 3 : 2);
+  const int ngrp = RL::NGRP * Np <= 512 ? RL::NGRP : (3 * Np <= 512 ? min(3, RL::NGRP) : 2);
   const uint32_t need = (uint32_t)(ngrp * Np);
   const uint32_t tcols = need <= 32 ? 32u : (need <= 64 ? 64u : (need <= 128 ? 128u : (need <= 256 ? 256u : 512u)));
   if (threadIdx.x == 0) {
@@ -249,8 +254,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             const long long r0 = m0 / ps.Pm;
             const int pp0 = (int)(m0 - r0 * ps.Pm);
             const int i0 = pp0 / ps.nJ;
-            ax = pp0 - i0 * ps.nJ + ps.cx;
-            ay = i0 + ps.cy;
+            ax = (pp0 - i0 * ps.nJ) * ps.ms + ps.cx;
+            ay = i0 * ps.ms + ps.cy;
             ar = (int)r0;
           }
         }
@@ -450,9 +455,21 @@ __global__ void __launch_bounds__(THREADS, 1)
       const uint32_t* tab_p = MODE == EPI_CONCRETIZE ? nullptr : ps.ntab + (size_t)prop * cx.NH;
       // the chunk's NHWC index: conv, (pm, channels nb ..); fully connected over a map, nb itself
       auto nhwc = [&](int nb) -> long long { return ps.npos ? (long long)nb : (long long)pm * ps.Cpo + nb; };
+      // the neuron entries of a chunk are loaded one chunk ahead, so that the dependent loads of
+      // the unstable elements' operands do not wait for them as well
+      uint4 tn0 = make_uint4(0, 0, 0, 0), tn1 = tn0;
+      if (MODE != EPI_CONCRETIZE && mv && nlo < ps.N) {
+        const uint4* tp = reinterpret_cast<const uint4*>(tab_p + nhwc(nlo));
+        tn0 = tp[0], tn1 = tp[1];
+      }
       for (int n0 = 0; n0 < Np; n0 += 8) {
         // 8 columns per step (one 16-byte chunk of the BF16 NHWC output): the element loop's
         // registers fit the 96 a thread has at 18 warps per SM
+        const uint4 t0 = tn0, t1 = tn1;
+        if (MODE != EPI_CONCRETIZE && mv && n0 + 8 < Np && nlo + n0 + 8 < ps.N) {
+          const uint4* tp = reinterpret_cast<const uint4*>(tab_p + nhwc(nlo + n0 + 8));
+          tn0 = tp[0], tn1 = tp[1];
+        }
         float v[8];
         tmem_ld8(tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(buf * Np + n0), v);
         const int nb = nlo + n0;   // first n of the chunk
@@ -476,14 +493,10 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
           for (int e = 0; e < 4; ++e) o2[e] = pack2(o[2 * e], o[2 * e + 1]);
         } else {
-          // the 8 elements' neuron entries (two 16-byte loads)
+          // the 8 elements' neuron entries (loaded with the previous chunk)
           uint32_t ent[8];
-          {
-            const uint4* tp = reinterpret_cast<const uint4*>(tab_p + nn0);
-            const uint4 t0 = tp[0], t1 = tp[1];
-            ent[0] = t0.x, ent[1] = t0.y, ent[2] = t0.z, ent[3] = t0.w;
-            ent[4] = t1.x, ent[5] = t1.y, ent[6] = t1.z, ent[7] = t1.w;
-          }
+          ent[0] = t0.x, ent[1] = t0.y, ent[2] = t0.z, ent[3] = t0.w;
+          ent[4] = t1.x, ent[5] = t1.y, ent[6] = t1.z, ent[7] = t1.w;
           // elements of the chunk with a split of the row (all of them when the row's list overflowed)
           uint32_t smask = many ? 0xFFu : 0u;
 #pragma unroll
@@ -934,10 +947,12 @@ int prepare(bcrown_net* net, LtNet* t) {
       pp.p.tab = pp.tab;
       // The A operand by TMA where an M tile is one box of the NHWC source (whole rows of the
       // pass's position grid, or whole grids of consecutive subdomain rows) and each K block is
-      // one tap's 64-channel block (source channels a multiple of 64, unit position step).
+      // one tap's 64-channel block (source channels a multiple of 64).  A position step ms > 1
+      // (a strided convolution's forward pass) is the box's traversal step in x and y: the box
+      // spans ms times the positions it holds.
       Pass& q = pp.p;
       int bw = 0, bh = 0, br = 0;
-      if (q.ms == 1 && q.Cps % 64 == 0 && q.nJ > 0 && q.Pm > 0) {
+      if (q.ms >= 1 && q.ms <= 8 && q.Cps % 64 == 0 && q.nJ > 0 && q.Pm > 0) {
         if (q.Pm % 128 == 0) {
           if (q.nJ <= 128 && 128 % q.nJ == 0) bw = q.nJ, bh = 128 / q.nJ, br = 1;
           else if (q.nJ % 128 == 0) bw = 128, bh = 1, br = 1;
@@ -945,7 +960,7 @@ int prepare(bcrown_net* net, LtNet* t) {
           bw = q.nJ, bh = q.Pm / q.nJ, br = 128 / q.Pm;
         }
       }
-      if (bw > 0 && bw * bh * br == 128 && (size_t)q.nkb * 8 == tab.size()) {
+      if (bw > 0 && bw * bh * br == 128 && bw * q.ms <= 256 && bh * q.ms <= 256 && (size_t)q.nkb * 8 == tab.size()) {
         const int cpb = q.Cps / 64;
         std::vector<int4> kt((size_t)q.nkb);
         for (int kb = 0; kb < q.nkb; ++kb) {
@@ -1187,8 +1202,10 @@ int launch_pass(bcrown_net* net, const CUtensorMap& mB, Pass q, int mode, const 
   if (q.ta == 4) {
     const cuuint64_t dims[4] = {(cuuint64_t)q.Cps, (cuuint64_t)q.Ws, (cuuint64_t)q.Hs, (cuuint64_t)cx.R};
     const cuuint64_t strides[3] = {(cuuint64_t)q.Cps * 2, (cuuint64_t)q.Ws * q.Cps * 2, (cuuint64_t)q.src_stride * 2};
-    const cuuint32_t box[4] = {64, (cuuint32_t)q.bw, (cuuint32_t)q.bh, (cuuint32_t)q.br};
-    BC_CHECK(encode_map_nd(&mA, const_cast<__nv_bfloat16*>(q.src), 4, dims, strides, box));
+    // a strided pass: boxes of ms bw x ms bh source positions, every ms-th one loaded (bw x bh)
+    const cuuint32_t box[4] = {64, (cuuint32_t)(q.bw * q.ms), (cuuint32_t)(q.bh * q.ms), (cuuint32_t)q.br};
+    const cuuint32_t es[4] = {1, (cuuint32_t)q.ms, (cuuint32_t)q.ms, 1};
+    BC_CHECK(encode_map_nd(&mA, const_cast<__nv_bfloat16*>(q.src), 4, dims, strides, box, es));
   } else if (q.ta == 2) {
     const cuuint64_t dims[2] = {(cuuint64_t)q.kchunks * 8, (cuuint64_t)cx.R};
     const cuuint64_t strides[1] = {(cuuint64_t)q.src_stride * 2};
@@ -1196,13 +1213,13 @@ int launch_pass(bcrown_net* net, const CUtensorMap& mB, Pass q, int mode, const 
     BC_CHECK(encode_map_nd(&mA, const_cast<__nv_bfloat16*>(q.src), 2, dims, strides, box));
   }
   if (q.ta) {
-    if (mode == EPI_RELAX) k_lt<EPI_RELAX, true><<<grid, THREADS, smem, s>>>(mB, mA, q, cx);
-    else if (mode == EPI_CONCRETIZE) k_lt<EPI_CONCRETIZE, true><<<grid, THREADS, smem, s>>>(mB, mA, q, cx);
-    else k_lt<EPI_FWD, true><<<grid, THREADS, smem, s>>>(mB, mA, q, cx);
+    if (mode == EPI_RELAX) k_lt<EPI_RELAX, true><<<grid, LtRoles<true>::THREADS, smem, s>>>(mB, mA, q, cx);
+    else if (mode == EPI_CONCRETIZE) k_lt<EPI_CONCRETIZE, true><<<grid, LtRoles<true>::THREADS, smem, s>>>(mB, mA, q, cx);
+    else k_lt<EPI_FWD, true><<<grid, LtRoles<true>::THREADS, smem, s>>>(mB, mA, q, cx);
   } else {
-    if (mode == EPI_RELAX) k_lt<EPI_RELAX, false><<<grid, THREADS, smem, s>>>(mB, mA, q, cx);
-    else if (mode == EPI_CONCRETIZE) k_lt<EPI_CONCRETIZE, false><<<grid, THREADS, smem, s>>>(mB, mA, q, cx);
-    else k_lt<EPI_FWD, false><<<grid, THREADS, smem, s>>>(mB, mA, q, cx);
+    if (mode == EPI_RELAX) k_lt<EPI_RELAX, false><<<grid, LtRoles<false>::THREADS, smem, s>>>(mB, mA, q, cx);
+    else if (mode == EPI_CONCRETIZE) k_lt<EPI_CONCRETIZE, false><<<grid, LtRoles<false>::THREADS, smem, s>>>(mB, mA, q, cx);
+    else k_lt<EPI_FWD, false><<<grid, LtRoles<false>::THREADS, smem, s>>>(mB, mA, q, cx);
   }
   ++g_launches;
   BC_CUDA(cudaGetLastError());

@@ -162,9 +162,11 @@ inline int encode_map(CUtensorMap* m, void* base, int rows, int kp, int box_rows
 // Tensor map of a BF16 tensor of `rank` dimensions (innermost first: dims[0] elements of 2 bytes,
 // strides[d - 1] bytes between consecutive indices of dimension d), boxes of box[0..rank), with
 // the 128-byte swizzle (box[0] = 64: one 128-byte row per index of the outer dimensions).
-// Coordinates outside the tensor read as zero.
+// Coordinates outside the tensor read as zero.  estride (optional): the traversal step of each
+// dimension; a box then holds ceil(box[d] / estride[d]) elements of dimension d, every
+// estride[d]-th from its start coordinate.
 inline int encode_map_nd(CUtensorMap* m, void* base, int rank, const cuuint64_t* dims, const cuuint64_t* strides,
-                         const cuuint32_t* box) {
+                         const cuuint32_t* box, const cuuint32_t* estride = nullptr) {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
     void* p = nullptr;
@@ -175,6 +177,8 @@ inline int encode_map_nd(CUtensorMap* m, void* base, int rank, const cuuint64_t*
     fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
   }
   cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  if (estride)
+    for (int d = 0; d < rank; ++d) es[d] = estride[d];
   CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, base, dims, strides, box, es,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);

@@ -340,10 +340,12 @@ def test_autotune_times_every_candidate_and_its_choice_is_taken():
     assert (np.abs(lb_tuned - ref) / _scale(ref)).max() <= BF16_TOL["conv_small"]
 
 
-def test_bf16_conv_at_the_size_limits_matches_oracle():
+@pytest.mark.parametrize("path", ["layer_gather", "layer_epi"])
+def test_bf16_conv_at_the_size_limits_matches_oracle(path):
     """A conv layer at the limits of the tensor-core path: 256 output channels (N = 256, the
     whole 512-column TMEM for two accumulators) and K = 128 x 4 x 4 = 2048 (the largest gather
-    table); the stride-2 backward pass split into 4 phases of K = 256 x 2 x 2."""
+    table); the stride-2 backward pass split into 4 phases of K = 256 x 2 x 2.  On the
+    fused-epilogue path the stride-2 forward pass reads its operand by strided TMA boxes."""
     layers = wl.conv_layers((128, 8, 8), [(256, 4, 2, 1)], [16, 4], 5)
     pb = wl.make_problem("conv_limits", layers, 1, 0.02, 3, 5)
     onet = O.OracleNet(pb.layers, pb.C)
@@ -354,11 +356,12 @@ def test_bf16_conv_at_the_size_limits_matches_oracle():
     batch = wl.random_batch(pb, unst, 6, 0, 4, 2)
     a, b = wl.random_alpha_beta(batch, 4, 1.0)
     net, dom, db = _gpu(pb, props, batch)
+    bc.set_launch(net, LAYER_PATHS[path])
     lb = bc.bound(net, dom, db, _t(a), _t(b), bc.BF16).cpu().numpy()
     assert bc.status(net) == 0
     ref = O.bound(onet, props, batch, a, b)
     err = np.abs(lb - ref) / _scale(ref)
-    print("bf16 conv at the limits: max err / median|lb| = %.3e" % err.max())
+    print("bf16 conv at the limits (%s): max err / median|lb| = %.3e" % (path, err.max()))
     assert err.max() <= BF16_TOL["conv_limits"]
     _, da, dbeta = bc.bound_grad(net, dom, db, _t(a), _t(b), bc.BF16)
     _, da_ref, db_ref = O.grad(onet, props, batch, a.astype(np.float64), b.astype(np.float64))
