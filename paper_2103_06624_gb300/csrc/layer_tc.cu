@@ -55,6 +55,9 @@ constexpr int NS = 4;                       // pipeline stages (A: 128 x 64, B: 
 #ifndef LT_TA_GROUPS
 #define LT_TA_GROUPS 4
 #endif
+#ifndef LT_FWD_PREFETCH
+#define LT_FWD_PREFETCH 0
+#endif
 template <bool TA>
 struct LtRoles {
   static constexpr int EPI = TA ? 4 * LT_TA_GROUPS : 12;   // epilogue warps
@@ -96,9 +99,11 @@ struct Pass {
   int slot0;                 // first partial-sum slot of this pass
   // A operand by TMA instead of the gather warps: 0 gathered; 4: one box [64 channels][bw][bh][br]
   // of the NHWC source per (tap, 64-channel block) -- an M tile is br rows x bh x bw positions;
-  // 2: one box [64][128 rows] of a fully connected pass's linear source
+  // 2: one box [64][128 rows] of a fully connected pass's linear source; 8: a source of 8 (padded)
+  // channels, one unswizzled box [8][bw][bh][br] per tap, 8 taps per K block
   int ta = 0, bw = 0, bh = 0, br = 0;
-  const int4* ktab = nullptr;   // ta == 4: per K block {first channel, dy, dx, tap in use}
+  const int4* ktab = nullptr;   // ta == 4: per K block {first channel, dy, dx, tap in use};
+                                // ta == 8: the same per tap (8 per K block)
 };
 
 // Per-call context of the epilogues.
@@ -233,8 +238,8 @@ __global__ void __launch_bounds__(LtRoles<TA>::THREADS, 1)
     // block: the tile's coordinates are worked out once per tile, the tap table is in shared
     // memory (the gathering kernel's table space).
     int4* sktab = reinterpret_cast<int4*>(stab);
-    if (TA && ps.ta == 4) {
-      for (int k = lane; k < nkb; k += 32) sktab[k] = ps.ktab[k];
+    if (TA && (ps.ta == 4 || ps.ta == 8)) {
+      for (int k = lane; k < (ps.ta == 8 ? 8 * nkb : nkb); k += 32) sktab[k] = ps.ktab[k];
       __syncwarp();
     }
     if (lane == 0) {
@@ -268,6 +273,14 @@ __global__ void __launch_bounds__(LtRoles<TA>::THREADS, 1)
           if constexpr (TA) {
             if (ps.ta == 2) {
               tma_load_2d(sA + st * 16384, &mapA, kb * 64, ar, &full[st]);
+            } else if (ps.ta == 8) {
+              // 8 channels per tap: the K block is 8 taps, one box of 16-byte rows each, 2 KB apart
+#pragma unroll 1
+              for (int j = 0; j < 8; ++j) {
+                const int4 kt = sktab[kb * 8 + j];
+                const int y = kt.w ? ay + kt.y : -(1 << 20);
+                tma_load_4d(sA + st * 16384 + j * 2048, &mapA, 0, ax + kt.z, y, ar, &full[st]);
+              }
             } else {
               const int4 kt = sktab[kb];
               // a K block past the phase's taps reads a box outside the map: zeros
@@ -305,7 +318,11 @@ __global__ void __launch_bounds__(LtRoles<TA>::THREADS, 1)
             break;
           }
           tc_fence_after();
-          umma_kblock(dt, sdesc(su32(sA + st * 16384)), sdesc(su32(sB + st * bbytes)), idesc, kb != 0 ? 1u : 0u);
+          if (TA && ps.ta == 8)   // A without swizzle: core matrices 128 B apart along M, 2 KB along K
+            umma_kblock_astep(dt, sdesc_plain(su32(sA + st * 16384), 2048, 128), sdesc(su32(sB + st * bbytes)),
+                              idesc, kb != 0 ? 1u : 0u, 4096 >> 4);
+          else
+            umma_kblock(dt, sdesc(su32(sA + st * 16384)), sdesc(su32(sB + st * bbytes)), idesc, kb != 0 ? 1u : 0u);
           umma_commit(&empty[st]);
         }
         if (!ok) break;
@@ -457,18 +474,25 @@ __global__ void __launch_bounds__(LtRoles<TA>::THREADS, 1)
       auto nhwc = [&](int nb) -> long long { return ps.npos ? (long long)nb : (long long)pm * ps.Cpo + nb; };
       // the neuron entries of a chunk are loaded one chunk ahead, so that the dependent loads of
       // the unstable elements' operands do not wait for them as well
+      // (not in the adjoint epilogue unless LT_FWD_PREFETCH: its registers are at the limit, and
+      // the spills it then needs cost more than the prefetch gains: 3.03k against 3.12k subdomains/s)
+      constexpr bool PF = MODE == EPI_RELAX || (MODE == EPI_FWD && LT_FWD_PREFETCH);
       uint4 tn0 = make_uint4(0, 0, 0, 0), tn1 = tn0;
-      if (MODE != EPI_CONCRETIZE && mv && nlo < ps.N) {
+      if (PF && mv && nlo < ps.N) {
         const uint4* tp = reinterpret_cast<const uint4*>(tab_p + nhwc(nlo));
         tn0 = tp[0], tn1 = tp[1];
       }
       for (int n0 = 0; n0 < Np; n0 += 8) {
         // 8 columns per step (one 16-byte chunk of the BF16 NHWC output): the element loop's
         // registers fit the 96 a thread has at 18 warps per SM
-        const uint4 t0 = tn0, t1 = tn1;
-        if (MODE != EPI_CONCRETIZE && mv && n0 + 8 < Np && nlo + n0 + 8 < ps.N) {
+        uint4 t0 = tn0, t1 = tn1;
+        if (PF && mv && n0 + 8 < Np && nlo + n0 + 8 < ps.N) {
           const uint4* tp = reinterpret_cast<const uint4*>(tab_p + nhwc(nlo + n0 + 8));
           tn0 = tp[0], tn1 = tp[1];
+        }
+        if (!PF && MODE != EPI_CONCRETIZE && mv && nlo + n0 < ps.N) {
+          const uint4* tp = reinterpret_cast<const uint4*>(tab_p + nhwc(nlo + n0));
+          t0 = tp[0], t1 = tp[1];
         }
         float v[8];
         tmem_ld8(tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(buf * Np + n0), v);
@@ -952,7 +976,8 @@ int prepare(bcrown_net* net, LtNet* t) {
       // spans ms times the positions it holds.
       Pass& q = pp.p;
       int bw = 0, bh = 0, br = 0;
-      if (q.ms >= 1 && q.ms <= 8 && q.Cps % 64 == 0 && q.nJ > 0 && q.Pm > 0) {
+      const bool narrow = q.Cps == 8 && q.nkb <= 16;   // 8 channels: one box per tap
+      if (q.ms >= 1 && q.ms <= 8 && (q.Cps % 64 == 0 || narrow) && q.nJ > 0 && q.Pm > 0) {
         if (q.Pm % 128 == 0) {
           if (q.nJ <= 128 && 128 % q.nJ == 0) bw = q.nJ, bh = 128 / q.nJ, br = 1;
           else if (q.nJ % 128 == 0) bw = 128, bh = 1, br = 1;
@@ -960,7 +985,20 @@ int prepare(bcrown_net* net, LtNet* t) {
           bw = q.nJ, bh = q.Pm / q.nJ, br = 128 / q.Pm;
         }
       }
-      if (bw > 0 && bw * bh * br == 128 && bw * q.ms <= 256 && bh * q.ms <= 256 && (size_t)q.nkb * 8 == tab.size()) {
+      if (bw > 0 && bw * bh * br == 128 && bw * q.ms <= 256 && bh * q.ms <= 256 && (size_t)q.nkb * 8 == tab.size() &&
+          narrow) {
+        std::vector<int4> kt(tab.size());
+        for (size_t kc = 0; kc < tab.size(); ++kc) {
+          const int dy = (int)(short)(tab[kc].y & 0xffff), dx = tab[kc].y >> 16;
+          const bool used = dy != -32768;
+          kt[kc] = make_int4(0, used ? dy : 0, used ? dx : 0, used ? 1 : 0);
+        }
+        void* dk = nullptr;
+        BC_CHECK(upload(t, kt.data(), kt.size() * sizeof(int4), &dk));
+        q.ktab = reinterpret_cast<const int4*>(dk);
+        q.ta = 8, q.bw = bw, q.bh = bh, q.br = br;
+      } else if (bw > 0 && bw * bh * br == 128 && bw * q.ms <= 256 && bh * q.ms <= 256 &&
+                 (size_t)q.nkb * 8 == tab.size()) {
         const int cpb = q.Cps / 64;
         std::vector<int4> kt((size_t)q.nkb);
         for (int kb = 0; kb < q.nkb; ++kb) {
@@ -1199,13 +1237,14 @@ int launch_pass(bcrown_net* net, const CUtensorMap& mB, Pass q, int mode, const 
   ProfScope pr(net, BCROWN_PROF_LAYER_GEMM, s);
   // the A operand's map for this launch (the source buffer and the rows of this chunk)
   CUtensorMap mA = mB;   // unused by the gathering kernel
-  if (q.ta == 4) {
+  if (q.ta == 4 || q.ta == 8) {
     const cuuint64_t dims[4] = {(cuuint64_t)q.Cps, (cuuint64_t)q.Ws, (cuuint64_t)q.Hs, (cuuint64_t)cx.R};
     const cuuint64_t strides[3] = {(cuuint64_t)q.Cps * 2, (cuuint64_t)q.Ws * q.Cps * 2, (cuuint64_t)q.src_stride * 2};
     // a strided pass: boxes of ms bw x ms bh source positions, every ms-th one loaded (bw x bh)
-    const cuuint32_t box[4] = {64, (cuuint32_t)(q.bw * q.ms), (cuuint32_t)(q.bh * q.ms), (cuuint32_t)q.br};
+    const cuuint32_t box[4] = {q.ta == 8 ? 8u : 64u, (cuuint32_t)(q.bw * q.ms), (cuuint32_t)(q.bh * q.ms),
+                               (cuuint32_t)q.br};
     const cuuint32_t es[4] = {1, (cuuint32_t)q.ms, (cuuint32_t)q.ms, 1};
-    BC_CHECK(encode_map_nd(&mA, const_cast<__nv_bfloat16*>(q.src), 4, dims, strides, box, es));
+    BC_CHECK(encode_map_nd(&mA, const_cast<__nv_bfloat16*>(q.src), 4, dims, strides, box, es, q.ta == 4));
   } else if (q.ta == 2) {
     const cuuint64_t dims[2] = {(cuuint64_t)q.kchunks * 8, (cuuint64_t)cx.R};
     const cuuint64_t strides[1] = {(cuuint64_t)q.src_stride * 2};

@@ -96,6 +96,29 @@ __device__ __forceinline__ void umma_kblock(uint32_t dtmem, uint64_t ad, uint64_
       "l"(bd + 6)
       : "memory");
 }
+// Shared-memory descriptor, K-major, no swizzle: 8-row x 16-byte core matrices stored as 128
+// contiguous bytes, `sbo` bytes apart along M and `lbo` bytes apart along K.
+__device__ __forceinline__ uint64_t sdesc_plain(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;                 // descriptor version; layout type 0 (no swizzle)
+  return d;
+}
+// As umma_kblock, with the A descriptor advanced by `astep` (16-byte units) per K step of 16.
+__device__ __forceinline__ void umma_kblock_astep(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                                  uint32_t acc, uint32_t astep) {
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %4, 0;\n\tsetp.eq.b32 q, 0, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %5, %6, %3, q;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %7, %8, %3, q;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %9, %10, %3, q;\n\t}" ::"r"(dtmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc), "l"(ad + astep), "l"(bd + 2), "l"(ad + 2 * astep), "l"(bd + 4),
+      "l"(ad + 3 * astep), "l"(bd + 6)
+      : "memory");
+}
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
                : "memory");
@@ -164,9 +187,10 @@ inline int encode_map(CUtensorMap* m, void* base, int rows, int kp, int box_rows
 // the 128-byte swizzle (box[0] = 64: one 128-byte row per index of the outer dimensions).
 // Coordinates outside the tensor read as zero.  estride (optional): the traversal step of each
 // dimension; a box then holds ceil(box[d] / estride[d]) elements of dimension d, every
-// estride[d]-th from its start coordinate.
+// estride[d]-th from its start coordinate.  swizzle = false: no swizzle (a box of 16-byte rows
+// lands as consecutive 16-byte rows).
 inline int encode_map_nd(CUtensorMap* m, void* base, int rank, const cuuint64_t* dims, const cuuint64_t* strides,
-                         const cuuint32_t* box, const cuuint32_t* estride = nullptr) {
+                         const cuuint32_t* box, const cuuint32_t* estride = nullptr, bool swizzle = true) {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
     void* p = nullptr;
@@ -180,7 +204,8 @@ inline int encode_map_nd(CUtensorMap* m, void* base, int rank, const cuuint64_t*
   if (estride)
     for (int d = 0; d < rank; ++d) es[d] = estride[d];
   CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, base, dims, strides, box, es,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(BCROWN_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
   return BCROWN_OK;
