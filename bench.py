@@ -53,6 +53,11 @@ def parse():
     ap.add_argument("--launch-path", default=None, choices=["fused", "layer_epi", "layer_gather", "layer_im2col"],
                     help="take this BF16 path instead of tuning (for profiling one path)")
     ap.add_argument("--no-joint", action="store_true", help="skip the joint intermediate-bound measurement")
+    ap.add_argument("--bab", action="store_true",
+                    help="instead of the bound throughput: host and engine time per child of the two branch-and-"
+                         "bound drivers (array pool, list pool) on the workload's first property")
+    ap.add_argument("--bab-rounds", type=int, default=14)
+    ap.add_argument("--bab-batch", type=int, default=512)
     ap.add_argument("--joint-subdomains", type=int, default=64,
                     help="subdomains of the joint intermediate-bound measurement (784-256x6-10 MLP)")
     ap.add_argument("--no-graph", action="store_true", help="launch the timed steps eagerly instead of replaying "
@@ -291,6 +296,9 @@ def main():
 
     prec = bc.BF16 if args.precision == "bf16" else bc.FP32
     pb, net, dom, hbatch, unst, lu = build_workload(args.workload, 0, args.subdomains, torch, bc, wl)
+    if args.bab:
+        measure_bab(args, torch, pb, net, dom, unst, lu)
+        return
     if prec == bc.BF16:
         try:
             _probe = bc.DeviceBatch.from_host(wl.tree_batch(pb, unst, [2], 2, 0))
@@ -623,6 +631,53 @@ def measure_joint(args, bc, torch, wl, probes, iters=20):
                                   "(joint_flops_per_subdomain_iter) over its CUDA-event time",
                          "peak_source": "of measured (bcrown_peak_probe FFMA throughput)"},
             "ablation_table_A4": ablation}
+
+
+def measure_bab(args, torch, pb, net, dom, unst, lu):
+    """Branch and bound on property 0 for a fixed number of rounds (no sampling, no descent, no line
+    search, so the pool grows to the batch size): wall time of each driver, the time spent inside its
+    engine calls (each ends with a device synchronisation), and the rest -- the driver's host time --
+    per bounded child.  Prints one JSON line."""
+    from paper_2103_06624_gb300 import bab, bab_pool
+
+    class Timed(bab.GpuEngine):
+        t = 0.0
+
+        def _timed(self, f, *a, **k):
+            t0 = time.perf_counter()
+            r = f(*a, **k)
+            torch.cuda.synchronize()
+            self.t += time.perf_counter() - t0
+            return r
+
+        def optimize(self, *a, **k):
+            return self._timed(super().optimize, *a, **k)
+
+        def xstar(self, *a, **k):
+            return self._timed(super().xstar, *a, **k)
+
+        def optimize_rows(self, *a, **k):
+            return self._timed(super().optimize_rows, *a, **k)
+
+        def xstar_rows(self, *a, **k):
+            return self._timed(super().xstar_rows, *a, **k)
+
+    case = (0, lu[0][0], lu[1][0], pb.x_lo[0], pb.x_hi[0])
+    out = {}
+    for name, fn in (("array_pool", bab_pool.bab_pool), ("list_pool", bab.bab_many)):
+        for rep in range(2):   # the first run warms up (library workspaces, launch tuning)
+            eng = Timed(pb, net, dom, [len(unst[0])])
+            t0 = time.perf_counter()
+            r = fn(eng, [case], batch_size=args.bab_batch, max_rounds=args.bab_rounds, n_samples=0, pgd_steps=0,
+                   line_search=False)[0]
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+        out[name] = {"rounds": r.rounds, "bounded": r.bounded, "status": r.status, "wall_s": wall,
+                     "engine_s": eng.t, "host_us_per_child": 1e6 * (wall - eng.t) / max(1, r.bounded),
+                     "engine_us_per_child": 1e6 * eng.t / max(1, r.bounded)}
+    print(json.dumps({"bab": out, "workload": pb.name, "batch_size": args.bab_batch, "K": pb.K,
+                      "unstable": int(len(unst[0])), "engine": "BF16 iterations (20) + FP32 certifying pass, "
+                      "x* and f(x*) per child"}))
 
 
 def time_root_bounds(bc, torch, net, dom, P, reps=3):

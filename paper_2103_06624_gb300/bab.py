@@ -478,6 +478,24 @@ class GpuEngine:
         self._check()
         return lb.cpu().numpy(), at.cpu().numpy(), bt.cpu().numpy()
 
+    # the array-pool driver's interface (bab_pool): alpha [B, K * Umax] and compact beta stay on the
+    # device; only the batch's split lists (a few bytes per subdomain) are copied to it
+    def optimize_rows(self, batch, alpha, beta):
+        """The optimised, certified bound of a host batch; alpha and beta (device tensors) are
+        overwritten with the per-row best values.  Returns lb [B*K] on the device."""
+        db = self.bc.DeviceBatch.from_host(batch)
+        lb = self.bc.optimize(self.net, self.dom, db, alpha, beta, self.cfg)
+        self._check()
+        return lb
+
+    def xstar_rows(self, batch, alpha, beta):
+        """Per row, the box point x* that minimises its linear bound and C f(x*) (device tensors)."""
+        db = self.bc.DeviceBatch.from_host(batch)
+        _, xs = self.bc.bound_xstar(self.net, self.dom, db, alpha, beta)
+        m = self.bc.forward(self.net, xs)
+        self._check()
+        return xs, m
+
     def _args(self, subs, alpha, beta):
         import torch
         batch = wl.pack_batch(self.pb.hidden_widths, self.K, self.U, subs)

@@ -2,6 +2,7 @@
 each margin over the box (all activation patterns enumerated, one LP each), and its host logic."""
 import numpy as np
 import pytest
+import torch
 
 from oracle import bcrown_oracle as O
 from oracle import lp_pins as LP
@@ -60,6 +61,24 @@ class OracleEngine:
 
     def margins(self, x):
         return np.atleast_2d(wl.reference_forward(self.pb.layers, x)) @ self.pb.C.astype(np.float64).T
+
+    # the array-pool driver's interface: batches in the C-ABI layout, alpha and beta as tensors
+    def optimize_rows(self, batch, alpha_t, beta_t):
+        self.calls += 1
+        lb, a, b, _ = O.optimize(self.onet, self.props, batch, alpha_t.reshape(-1).numpy().astype(np.float64),
+                                 beta_t.numpy().astype(np.float64), O.AdamCfg())
+        alpha_t.copy_(torch.as_tensor(np.asarray(a, np.float32)).reshape(alpha_t.shape))
+        beta_t.copy_(torch.as_tensor(np.asarray(b, np.float32)))
+        return torch.as_tensor(np.asarray(lb, np.float64))
+
+    def xstar_rows(self, batch, alpha_t, beta_t):
+        rows = O.expand_rows(self.onet, batch, self.props["l"], self.props["u"])
+        _, tr = O.bound(self.onet, self.props, batch, alpha_t.reshape(-1).numpy().astype(np.float64),
+                        beta_t.numpy().astype(np.float64), rows=rows, trace=True)
+        xlo = np.asarray(self.props["x_lo"], np.float64)[rows.prop]
+        xhi = np.asarray(self.props["x_hi"], np.float64)[rows.prop]
+        xs = np.where(tr.A[0] >= 0, xlo, xhi)
+        return torch.as_tensor(xs), torch.as_tensor(self.margins(xs))
 
 
 # (widths, seed, eps): the expected verdict follows from the exact minima computed in the test
@@ -235,3 +254,65 @@ def test_joint_mode_reaches_the_exact_verdicts_with_no_more_branching(name):
     _, _, joint = run_case(name, OracleEngine, batch_size=256, max_rounds=12, n_samples=256, joint=True)
     check_verdict(name, pb, exact, joint)
     assert joint.bounded <= plain.bounded, (joint.bounded, plain.bounded)
+
+
+def _same_result(a, b):
+    assert a.status == b.status
+    assert (a.rounds, a.bounded, a.max_depth, a.open_domains) == (b.rounds, b.bounded, b.max_depth, b.open_domains)
+    assert (a.line_searched, a.infeasible) == (b.line_searched, b.infeasible)
+    assert a.min_lb == b.min_lb and a.upper == b.upper
+    assert a.history == b.history
+    if a.status == "violated":
+        assert np.array_equal(a.witness, b.witness)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_array_pool_driver_takes_the_same_steps_as_the_list_driver(name):
+    """The driver with the pool in arrays (alpha, beta as tensors, split lists implicit in the
+    branching order) against the list driver on the same deterministic engine: the same rounds,
+    counts, per-round pool sizes and lowest bounds, upper bound and verdict, on every tiny case
+    (verified at the root, by branching with line searches of fully split subdomains, violated)."""
+    from paper_2103_06624_gb300 import bab_pool
+    pb, props, unst, exact = make_case(name)
+    U = [len(u) for u in unst]
+    case = (0, props["l"][0], props["u"][0], pb.x_lo[0], pb.x_hi[0])
+    ref = bab.bab_many(OracleEngine(pb, props, U), [case], batch_size=8, max_rounds=30, n_samples=64)[0]
+    got = bab_pool.bab_pool(OracleEngine(pb, props, U), [case], batch_size=8, max_rounds=30, n_samples=64,
+                            device="cpu")[0]
+    _same_result(ref, got)
+    check_verdict(name, pb, exact, got)
+
+
+def test_array_pool_driver_with_several_properties():
+    """Three properties in one pool (their own orders and unstable counts, alpha rows padded to the
+    largest): the same per-property results as the list driver."""
+    from paper_2103_06624_gb300 import bab_pool
+    pb = wl.make_problem("multi", wl.mlp_layers([5, 10, 10, 4], 1), 3, 0.15, 3, 1)
+    onet, props, unst = oracle_setup(pb)
+    U = [len(u) for u in unst]
+    cases = [(p, props["l"][p], props["u"][p], pb.x_lo[p], pb.x_hi[p]) for p in range(pb.P)]
+    ref = bab.bab_many(OracleEngine(pb, props, U), cases, batch_size=8, max_rounds=20, n_samples=64)
+    got = bab_pool.bab_pool(OracleEngine(pb, props, U), cases, batch_size=8, max_rounds=20, n_samples=64,
+                            device="cpu")
+    for a, b in zip(ref, got):
+        _same_result(a, b)
+
+
+@pytest.mark.parametrize("upper,line_search", [(True, True), (False, True), (False, False)])
+def test_array_pool_driver_branches_to_full_depth_like_the_list_driver(upper, line_search):
+    """No sampled point and no descent on the net whose violation sampling misses: the violation is
+    found at x* during branching, or by the line search of the fully split subdomains, or (both off)
+    the verdict stays unknown with fully split subdomains open -- the same steps in both drivers."""
+    from paper_2103_06624_gb300 import bab_pool
+    pb, props, unst, exact = make_case("violated_found_by_descent")
+    U = [len(u) for u in unst]
+    case = (0, props["l"][0], props["u"][0], pb.x_lo[0], pb.x_hi[0])
+    kw = dict(batch_size=256, max_rounds=12, n_samples=0, pgd_steps=0, upper=upper, line_search=line_search)
+    ref = bab.bab_many(OracleEngine(pb, props, U), [case], **kw)[0]
+    got = bab_pool.bab_pool(OracleEngine(pb, props, U), [case], device="cpu", **kw)[0]
+    _same_result(ref, got)
+    if not upper:
+        assert got.max_depth == U[0]   # every neuron split before the verdict
+    if line_search and not upper:
+        assert got.line_searched > 0
+    assert got.status == ("unknown" if not (upper or line_search) else "violated")

@@ -11,7 +11,7 @@ from paper_2103_06624_gb300 import bab
 from paper_2103_06624_gb300 import bcrown as bc
 from paper_2103_06624_gb300 import workloads as wl
 from tests.helpers import oracle_setup
-from tests.test_bab import CASES, OracleEngine, check_verdict, run_case
+from tests.test_bab import CASES, OracleEngine, check_verdict, make_case, run_case
 
 pytestmark = pytest.mark.gpu
 
@@ -86,3 +86,34 @@ def test_graph_replayed_engine_gives_the_same_decisions():
     _, _, replay = run_case(name, graph_engine, batch_size=256, max_rounds=12, n_samples=256)
     check_verdict(name, pb, exact, replay)
     assert (replay.status, replay.rounds, replay.bounded) == (eager.status, eager.rounds, eager.bounded)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_array_pool_driver_on_the_gpu_reaches_the_exact_verdict(name):
+    """The driver with alpha and beta resident on the device (bab_pool) through the library: the
+    verdicts the exact minima fix, and those of the list driver on the same engine."""
+    from paper_2103_06624_gb300 import bab_pool
+    pb, props, unst, exact = make_case(name)
+    U = [len(u) for u in unst]
+    case = (0, props["l"][0], props["u"][0], pb.x_lo[0], pb.x_hi[0])
+    res = bab_pool.bab_pool(gpu_engine(pb, props, U), [case], batch_size=256, max_rounds=12, n_samples=256)[0]
+    print("%s: %s, rounds %d, subdomains %d, depth %d" % (name, res.status, res.rounds, res.bounded, res.max_depth))
+    check_verdict(name, pb, exact, res)
+    ref = bab.bab_many(gpu_engine(pb, props, U), [case], batch_size=256, max_rounds=12, n_samples=256)[0]
+    assert res.status == ref.status
+
+
+@pytest.mark.parametrize("upper,line_search", [(True, False), (False, True)])
+def test_array_pool_driver_on_the_gpu_finds_the_violation_sampling_misses(upper, line_search):
+    """No sampled point and no descent: the violation is found at x* of a bounded subdomain, or by
+    the line search of the fully split subdomains (their alpha and beta read back from the device)."""
+    from paper_2103_06624_gb300 import bab_pool
+    pb, props, unst, exact = make_case("violated_found_by_descent")
+    U = [len(u) for u in unst]
+    case = (0, props["l"][0], props["u"][0], pb.x_lo[0], pb.x_hi[0])
+    res = bab_pool.bab_pool(gpu_engine(pb, props, U), [case], batch_size=256, max_rounds=12, n_samples=0,
+                            pgd_steps=0, upper=upper, line_search=line_search)[0]
+    check_verdict("violated_found_by_descent", pb, exact, res)
+    assert res.status == "violated"
+    if line_search:
+        assert res.line_searched > 0
