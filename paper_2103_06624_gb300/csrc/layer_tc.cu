@@ -523,9 +523,11 @@ __global__ void __launch_bounds__(LtRoles<TA>::THREADS, 1)
           ent[4] = t1.x, ent[5] = t1.y, ent[6] = t1.z, ent[7] = t1.w;
           // elements of the chunk with a split of the row (all of them when the row's list overflowed)
           uint32_t smask = many ? 0xFFu : 0u;
+          if (nkeep > 0) {   // most threads hold no split in the tile: skip the scan
 #pragma unroll
-          for (int q = 0; q < MAX_KEEP; ++q)
-            if (q < nkeep && (unsigned)((kp_[q] & 0xFFFFF) - nb) < 8u) smask |= 1u << ((kp_[q] & 0xFFFFF) - nb);
+            for (int q = 0; q < MAX_KEEP; ++q)
+              if (q < nkeep && (unsigned)((kp_[q] & 0xFFFFF) - nb) < 8u) smask |= 1u << ((kp_[q] & 0xFFFFF) - nb);
+          }
           float o[8];
 #pragma unroll
           for (int hb = 0; hb < 8; hb += 4) {
@@ -543,8 +545,15 @@ __global__ void __launch_bounds__(LtRoles<TA>::THREADS, 1)
               st[uu] = (MODE == EPI_FWD && un) ? __bfloat162float(stash_r[rk]) : 0.f;
               // biases: a conv layer's are per channel (shared memory, up to MAX_NP channels); a
               // fully connected pass's per n, and a wider layer's channels from global memory
-              bv[uu] = ps.npos ? ps.bnhwc[nn0 + u]
-                               : (sb_smem ? sbias[min(nb + u, MAX_NP - 1)] : (nb + u < lim ? ps.bnhwc[nb + u] : 0.f));
+              if (MODE != EPI_FWD || !sb_smem)
+                bv[uu] = ps.npos ? ps.bnhwc[nn0 + u]
+                                 : (sb_smem ? sbias[min(nb + u, MAX_NP - 1)] : (nb + u < lim ? ps.bnhwc[nb + u] : 0.f));
+            }
+            if (MODE == EPI_FWD && sb_smem) {
+              // the adjoint: 4 channel biases in one shared-memory load (nb + hb + 3 < MAX_NP); in the
+              // relaxation the 4 registers this holds at once would spill
+              const float4 b4 = *reinterpret_cast<const float4*>(sbias + nb + hb);
+              bv[0] = b4.x, bv[1] = b4.y, bv[2] = b4.z, bv[3] = b4.w;
             }
 #pragma unroll
             for (int uu = 0; uu < 4; ++uu) {
