@@ -137,6 +137,79 @@ __global__ void __launch_bounds__(SC_THREADS) k_sconv(SconvPass q, const float* 
   }
 }
 
+// Passes with at most 4 output channels (the backward pass of a first layer over 1-4 input
+// channels): a 128 x 16 tile would spend most of its FMAs on padding and its shared-memory reads
+// would outnumber them, and no operand value is reused across output channels anyway.  Each
+// thread computes 4 rows (m, m + 256, m + 512, m + 768 of its block, so every load of a warp is
+// one contiguous run of positions) times the N channels, loading its operand straight from
+// global memory; the K loop reads the tap table and the N weights of each term from shared
+// memory (one broadcast load each).  Each output is the same sequential FMA chain in K order as
+// in k_sconv, so the result is the same bit for bit and the same a priori error bound holds.
+constexpr int SN_THREADS = 256, SN_TM = 4;
+
+template <int N>
+__global__ void __launch_bounds__(SN_THREADS) k_sconv_narrow(SconvPass q, const float* __restrict__ src,
+                                                            long long sstride, float* __restrict__ out,
+                                                            long long ostride, const float* __restrict__ bias) {
+  extern __shared__ __align__(16) uint8_t sn_raw[];
+  int4* stab = reinterpret_cast<int4*>(sn_raw);
+  float4* sB = reinterpret_cast<float4*>(sn_raw + (size_t)q.K * sizeof(int4));
+  const int tid = threadIdx.x;
+  for (int k = tid; k < q.K; k += SN_THREADS) {
+    stab[k] = q.tab[k];
+    const float* b = q.B + (size_t)k * N;
+    sB[k] = make_float4(b[0], N > 1 ? b[1] : 0.f, N > 2 ? b[2] : 0.f, N > 3 ? b[3] : 0.f);
+  }
+  const float* srow[SN_TM];
+  int y0[SN_TM], x0[SN_TM];
+  long long mrow[SN_TM];
+#pragma unroll
+  for (int i = 0; i < SN_TM; ++i) {
+    const long long m = (long long)blockIdx.x * (SN_THREADS * SN_TM) + i * SN_THREADS + tid;
+    const bool mv = m < q.M;
+    const long long r = mv ? m / q.Pm : 0;
+    const int pp = mv ? (int)(m - r * q.Pm) : 0;
+    const int pi = pp / q.nJ, pj = pp - (pp / q.nJ) * q.nJ;
+    y0[i] = mv ? pi * q.ms + q.cy : -32768;
+    x0[i] = pj * q.ms + q.cx;
+    srow[i] = src + r * sstride + (mv ? (long long)y0[i] * q.Ws + x0[i] : 0);
+    mrow[i] = mv ? m : -1;
+  }
+  __syncthreads();
+  float acc[SN_TM][N];
+#pragma unroll
+  for (int i = 0; i < SN_TM; ++i)
+#pragma unroll
+    for (int j = 0; j < N; ++j) acc[i][j] = 0.f;
+#pragma unroll 2
+  for (int k = 0; k < q.K; ++k) {
+    const int4 t = stab[k];
+    const float4 b4 = sB[k];
+    const float bv[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+    for (int i = 0; i < SN_TM; ++i) {
+      const bool in = (unsigned)(y0[i] + t.y) < (unsigned)q.Hs && (unsigned)(x0[i] + t.z) < (unsigned)q.Ws;
+      const float v = in ? srow[i][t.x] : 0.f;
+#pragma unroll
+      for (int j = 0; j < N; ++j) acc[i][j] = fmaf(v, bv[j], acc[i][j]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < SN_TM; ++i) {
+    const long long m = mrow[i];
+    if (m < 0) continue;
+    const long long rr = m / q.Pm;
+    const int p2 = (int)(m - rr * q.Pm);
+    const int ii = p2 / q.nJ, jj = p2 - (p2 / q.nJ) * q.nJ;
+    const long long p = (long long)(q.oa + q.os * ii) * q.Wo + q.ob + q.os * jj;
+    float* orow = out + rr * ostride + p;
+#pragma unroll
+    for (int j = 0; j < N; ++j) orow[(size_t)j * q.HWo] = acc[i][j] + (bias ? bias[(size_t)j * q.HWo + p] : 0.f);
+  }
+}
+
+int sconv_narrow_smem(int K) { return K * (int)(sizeof(int4) + sizeof(float4)); }
+
 int sconv_smem(int BN, int K) { return 2 * SC_BK * (SC_BM + 4) * 4 + 2 * SC_BK * (BN + 4) * 4 + K * (int)sizeof(int4); }
 
 struct LayerF32 {
@@ -263,6 +336,15 @@ int sc_prepare(bcrown_net* net, SconvNet* t) {
     f.B = reinterpret_cast<const float*>(dB);
     P.fwd = f;
   }
+  {
+    const int smem = sconv_narrow_smem(SCONV_MAX_K);
+    for (cudaError_t e : {cudaFuncSetAttribute(k_sconv_narrow<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+                          cudaFuncSetAttribute(k_sconv_narrow<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+                          cudaFuncSetAttribute(k_sconv_narrow<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+                          cudaFuncSetAttribute(k_sconv_narrow<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)})
+      if (e != cudaSuccess)
+        return fail(BCROWN_ERR_CUDA, std::string("FP32 conv: smem attribute: ") + cudaGetErrorString(e));
+  }
   for (int BN : {16, 32, 64, 128}) {
     const int smem = sconv_smem(BN, SCONV_MAX_K);
     cudaError_t e = BN == 16    ? cudaFuncSetAttribute(k_sconv<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
@@ -280,6 +362,16 @@ int sc_launch(const SconvPass& q0, int R, const float* src, long long sstride, f
   SconvPass q = q0;
   q.M = (long long)R * q.Pm;
   if (q.M <= 0) return BCROWN_OK;
+  if (q.N <= 4) {
+    const unsigned nb = (unsigned)((q.M + SN_THREADS * SN_TM - 1) / (SN_THREADS * SN_TM));
+    const int smem = sconv_narrow_smem(q.K);
+    if (q.N == 1) k_sconv_narrow<1><<<nb, SN_THREADS, smem, s>>>(q, src, sstride, out, ostride, bias);
+    else if (q.N == 2) k_sconv_narrow<2><<<nb, SN_THREADS, smem, s>>>(q, src, sstride, out, ostride, bias);
+    else if (q.N == 3) k_sconv_narrow<3><<<nb, SN_THREADS, smem, s>>>(q, src, sstride, out, ostride, bias);
+    else k_sconv_narrow<4><<<nb, SN_THREADS, smem, s>>>(q, src, sstride, out, ostride, bias);
+    ++g_launches;
+    return BCROWN_OK;
+  }
   const int BN = q.N <= 16 ? 16 : q.N <= 32 ? 32 : q.N <= 64 ? 64 : 128;
   const dim3 grid((unsigned)((q.M + SC_BM - 1) / SC_BM), (unsigned)((q.N + BN - 1) / BN));
   const int smem = sconv_smem(BN, q.K);
