@@ -386,6 +386,9 @@ def main():
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_ms = float(tt.item())
     ms_per_step = t_ms / args.steps
+    step_ms = sorted(a.elapsed_time(b) for a, b in ev)
+    ms_median = step_ms[len(step_ms) // 2] if len(step_ms) % 2 else 0.5 * (
+        step_ms[len(step_ms) // 2 - 1] + step_ms[len(step_ms) // 2])
     units = hbatch.B * world
     value = units / (ms_per_step / 1e3)
     assert bc.status(net) == 0, "device status reported an error"
@@ -534,6 +537,7 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step_median": ms_median, "rows_per_s": value * pb.K,
             "vs_baseline": None, "dtype": "bf16" if prec == bc.BF16 else "f32", "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload]["desc"].format(n=hbatch.B) +
                                    ", 20 Adam iters + certify pass",
