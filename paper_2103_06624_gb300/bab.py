@@ -403,8 +403,10 @@ def rank_starts(l, u, rank, world):
     return [(top, sg) for sg in patterns[rank::world]]
 
 
-def bab_ranks(engine, prop, l, u, x_lo, x_hi, rank, world, dist, seed=0, **kw):
+def bab_ranks(engine, prop, l, u, x_lo, x_hi, rank, world, dist, seed=0, driver="list", **kw):
     """One property decided by `world` ranks (one process per GPU, torch.distributed `dist`).
+    driver: "list" (bab) or "pool" (bab_pool.bab_pool, the pool in arrays; alpha and beta on the
+    device the engine computes on).
 
     The first k = ceil(log2 world) neurons of the (static) branching order give 2^k subdomains;
     rank r decides those with index r, r + world, ... on its own, with its own sampling seed.
@@ -413,7 +415,11 @@ def bab_ranks(engine, prop, l, u, x_lo, x_hi, rank, world, dist, seed=0, **kw):
     There is no exchange while the ranks branch."""
     import torch
     mine = rank_starts(l, u, rank, world)
-    res = bab(engine, prop, l, u, x_lo, x_hi, seed=seed + rank, start=mine, **kw)
+    if driver == "pool":
+        from . import bab_pool
+        res = bab_pool.bab_pool(engine, [(prop, l, u, x_lo, x_hi)], seed=seed + rank, starts=[mine], **kw)[0]
+    else:
+        res = bab(engine, prop, l, u, x_lo, x_hi, seed=seed + rank, start=mine, **kw)
     t = torch.tensor([_CODE[res.status]], dtype=torch.int64)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     status = {v: s for s, v in _CODE.items()}[int(t.item())]

@@ -190,10 +190,12 @@ def _domain(ctx, p, i):
 
 
 def bab_pool(engine, cases, batch_size=512, max_rounds=50, max_bounded=1_000_000, n_samples=256, seed=0,
-             time_limit=None, alpha_init=0.5, pgd_steps=20, upper=True, line_search=True, device=None):
-    """Decide properties cases = [(prop, l, u, x_lo, x_hi), ...] from the whole box, as
-    bab.bab_many does, with the pool in arrays and alpha, beta on `device` (default: CUDA when
-    available).  Returns one bab.BabResult per case."""
+             time_limit=None, alpha_init=0.5, pgd_steps=20, starts=None, upper=True, line_search=True, device=None):
+    """Decide properties cases = [(prop, l, u, x_lo, x_hi), ...], as bab.bab_many does, with the
+    pool in arrays and alpha, beta on `device` (default: CUDA when available).  starts, if given,
+    holds each case's start subdomains as (neuron indices, signs) pairs whose neurons are the first
+    ones of the case's branching order (as bab.rank_starts gives them); "verified" then covers their
+    union.  Returns one bab.BabResult per case."""
     t0 = time.perf_counter()
     dev = torch.device(device if device is not None else ("cuda" if torch.cuda.is_available() else "cpu"))
     K = engine.K
@@ -222,12 +224,21 @@ def bab_pool(engine, cases, batch_size=512, max_rounds=50, max_bounded=1_000_000
 
     bounded_per = np.zeros(n, np.int64)
     pool = _Pool(K, ctx.Umax, D, dev)
-    first = np.nonzero(open_case)[0]
+    first = []   # (owner, depth, signs) of the start subdomains
+    for c in np.nonzero(open_case)[0]:
+        for sp, sg in ([(np.zeros(0, np.int64), np.zeros(0, np.int8))] if starts is None else starts[c]):
+            sp = np.asarray(sp, np.int64)
+            d = len(sp)
+            if d > min(D, ctx.U[c]) or not np.array_equal(sp, ctx.orders[c, :d]):
+                raise ValueError("a start subdomain must split the first neurons of its property's branching order")
+            first.append((c, d, np.asarray(sg, np.int8)))
     if len(first):
         f = _Pool(K, ctx.Umax, D, dev)
-        f.depth = np.zeros(len(first), np.int32)
-        f.owner = first.astype(np.int32)
+        f.depth = np.array([d for _, d, _ in first], np.int32)
+        f.owner = np.array([c for c, _, _ in first], np.int32)
         f.signs = np.zeros((len(first), D), np.int8)
+        for i, (_, d, sg) in enumerate(first):
+            f.signs[i, :d] = sg
         f.lb = np.full((len(first), K), -np.inf, np.float32)
         f.alpha = torch.full((len(first), K * ctx.Umax), alpha_init, dtype=torch.float32, device=dev)
         f.beta = torch.zeros((len(first), K, D), dtype=torch.float32, device=dev)

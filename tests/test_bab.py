@@ -316,3 +316,24 @@ def test_array_pool_driver_branches_to_full_depth_like_the_list_driver(upper, li
     if line_search and not upper:
         assert got.line_searched > 0
     assert got.status == ("unknown" if not (upper or line_search) else "violated")
+
+
+def test_array_pool_driver_from_start_subdomains():
+    """Start subdomains on the first branching neurons (one rank's share of two): the same steps as
+    the list driver from the same starts; a start that skips a neuron of the order is refused."""
+    from paper_2103_06624_gb300 import bab_pool
+    pb, props, unst, exact = make_case("verified_by_branching_a")
+    U = [len(u) for u in unst]
+    l, u = props["l"][0], props["u"][0]
+    case = (0, l, u, pb.x_lo[0], pb.x_hi[0])
+    for rank in range(2):
+        mine = bab.rank_starts(l, u, rank, 4)
+        ref = bab.bab_many(OracleEngine(pb, props, U), [case], batch_size=8, max_rounds=30, n_samples=64,
+                           starts=[mine])[0]
+        got = bab_pool.bab_pool(OracleEngine(pb, props, U), [case], batch_size=8, max_rounds=30, n_samples=64,
+                                starts=[mine], device="cpu")[0]
+        _same_result(ref, got)
+    order = np.argsort(-bab.branching_scores(l, u), kind="stable")
+    with pytest.raises(ValueError):
+        bab_pool.bab_pool(OracleEngine(pb, props, U), [case], starts=[[(order[1:2], np.array([1], np.int8))]],
+                          n_samples=0, pgd_steps=0, device="cpu")

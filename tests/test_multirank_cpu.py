@@ -77,7 +77,7 @@ def test_two_rank_gloo_matches_single_process():
     assert span == (0, 19)
 
 
-def _bab_worker(rank, world, port, q, name):
+def _bab_worker(rank, world, port, q, name, driver):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
@@ -85,23 +85,26 @@ def _bab_worker(rank, world, port, q, name):
     from tests.test_bab import OracleEngine, make_case
     pb, props, unst, exact = make_case(name)
     eng = OracleEngine(pb, props, [len(u) for u in unst])
+    kw = dict(device="cpu") if driver == "pool" else {}
     res = bab.bab_ranks(eng, 0, props["l"][0], props["u"][0], pb.x_lo[0], pb.x_hi[0], rank, world, dist,
-                        batch_size=256, max_rounds=12, n_samples=128)
+                        batch_size=256, max_rounds=12, n_samples=128, driver=driver, **kw)
     q.put((rank, res.status, res.bounded, res.witness, exact))
     dist.barrier()
     dist.destroy_process_group()
 
 
+@pytest.mark.parametrize("driver", ["list", "pool"])
 @pytest.mark.parametrize("name,world", [("verified_by_branching_a", 2), ("verified_by_branching_b", 3),
                                         ("violated", 2)])
-def test_bab_across_ranks_reaches_the_single_process_verdict(name, world):
+def test_bab_across_ranks_reaches_the_single_process_verdict(name, world, driver):
     """Each rank decides its share of the subdomains below the first ceil(log2 world) splits,
     with no exchange while branching; one all-reduce combines the verdicts (and the lowest
-    finding rank broadcasts a witness)."""
+    finding rank broadcasts a witness).  Both drivers: the list pool, and the array pool whose
+    start subdomains are the rank's sign patterns of the first branching neurons."""
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_bab_worker, args=(r, world, port, q, name)) for r in range(world)]
+    procs = [ctx.Process(target=_bab_worker, args=(r, world, port, q, name, driver)) for r in range(world)]
     for p in procs:
         p.start()
     out = [q.get(timeout=600) for _ in range(world)]
