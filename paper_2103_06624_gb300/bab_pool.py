@@ -103,7 +103,7 @@ class _Pool:
         self.beta = torch.cat([self.beta, o.beta])
 
 
-def _children(par, orders_len):
+def _children(par):
     """The two children of every row of pool `par` (split on the next neuron of the order):
     rows 2i (z >= 0, sign -1) and 2i + 1 (z <= 0, sign +1); alpha and beta rows copied, the new
     split's beta slot is the parent's unused (zero) slot."""
@@ -268,7 +268,7 @@ def bab_pool(engine, cases, batch_size=512, max_rounds=50, max_bounded=1_000_000
         par = pool.take(take[~full])
         pool = pool.take(rest)
         if par.n:
-            kids = _children(par, ctx.orders.shape[1])
+            kids = _children(par)
             hb, a, bcmp = _bound_rows(engine, ctx, kids)
             if upper:
                 _upper_rows(engine, ctx, kids, hb, a, bcmp, res)
