@@ -100,3 +100,25 @@ def test_layer_gemm_operand_byte_model():
     assert w[:6] == [3072, 65536, 16384, 32768, 8192, 512]
     expect = 8 * ((65536 + 3072) + (16384 + 65536) + (32768 + 16384) + (8192 + 32768) + (512 + 8192))
     assert bench.tcg_bytes_per_row_iter(w) == expect == 1994752
+
+
+def test_end_to_end_parts_are_the_batch_in_order():
+    """The parts the end-to-end measurement pipelines: contiguous ranges of subdomains whose
+    rebased split lists, alpha and beta slices put back together give the whole batch."""
+    pb = wl.problem_mlp_small()
+    unst = [np.arange(40)]
+    hb = wl.tree_batch(pb, unst, [37], 6, 3)
+    K = pb.K
+    parts = bench._split_host_batch(hb, K, 4)
+    assert len(parts) == 4 and parts[0][1][0] == 0 and parts[-1][1][1] == hb.B
+    for (sub, (b0, b1), (a0, a1), (s0, s1)), nxt in zip(parts, parts[1:] + [None]):
+        assert sub.B == b1 - b0 and sub.n_alpha == a1 - a0 and sub.n_beta == s1 - s0
+        np.testing.assert_array_equal(sub.split_off + hb.split_off[b0], hb.split_off[b0:b1])
+        np.testing.assert_array_equal(sub.alpha_off + hb.alpha_off[b0], hb.alpha_off[b0:b1])
+        S0 = int(hb.split_off[b0])
+        np.testing.assert_array_equal(sub.split_idx, hb.split_idx[S0:S0 + len(sub.split_idx)])
+        np.testing.assert_array_equal(sub.split_sign, hb.split_sign[S0:S0 + len(sub.split_sign)])
+        assert s0 == S0 * K
+        if nxt is not None:
+            assert nxt[1][0] == b1 and nxt[2][0] == a1 and nxt[3][0] == s1
+    assert parts[-1][2][1] == hb.n_alpha and parts[-1][3][1] == hb.n_beta
