@@ -814,7 +814,8 @@ def measure_e2e(args, bc, torch, net, dom, hbatch, a0, b0, cfg, pb, world, parts
         ms = float(tt.item())
     return {"value": hbatch.B * world / (ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "ms_per_step": ms, "parts": len(P),
-            "overlap": "inputs copied in on one stream, parts optimised on a second, results copied out on a third"}
+            "overlap": ("inputs copied in on one stream, parts optimised on a second, results copied out on a third"
+                        if len(P) > 1 else "none: one part, copies in, optimisation and copies out in sequence")}
 
 
 def run_reference(args, world):
