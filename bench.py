@@ -670,9 +670,11 @@ def measure_bab(args, torch, pb, net, dom, unst, lu):
 
     case = (0, lu[0][0], lu[1][0], pb.x_lo[0], pb.x_hi[0])
     out = {}
-    for name, fn in (("array_pool", bab_pool.bab_pool), ("list_pool", bab.bab_many)):
-        for rep in range(2):   # the first run warms up (library workspaces, launch tuning)
-            eng = Timed(pb, net, dom, [len(unst[0])])
+    for name, fn, graphs in (("array_pool", bab_pool.bab_pool, False), ("list_pool", bab.bab_many, False),
+                             ("array_pool_graphs", bab_pool.bab_pool, True), ("list_pool_graphs", bab.bab_many, True)):
+        eng = Timed(pb, net, dom, [len(unst[0])], graphs=graphs)
+        for rep in range(2):   # the first run warms up (library workspaces, launch tuning, graph captures)
+            eng.t = 0.0
             t0 = time.perf_counter()
             r = fn(eng, [case], batch_size=args.bab_batch, max_rounds=args.bab_rounds, n_samples=0, pgd_steps=0,
                    line_search=False)[0]

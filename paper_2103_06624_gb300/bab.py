@@ -489,6 +489,10 @@ class GpuEngine:
     def optimize_rows(self, batch, alpha, beta):
         """The optimised, certified bound of a host batch; alpha and beta (device tensors) are
         overwritten with the per-row best values.  Returns lb [B*K] on the device."""
+        if self.graphs is not None:
+            lb = self.graphs.rows(batch, alpha, beta)
+            self._check()
+            return lb
         db = self.bc.DeviceBatch.from_host(batch)
         lb = self.bc.optimize(self.net, self.dom, db, alpha, beta, self.cfg)
         self._check()

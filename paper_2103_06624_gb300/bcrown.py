@@ -470,7 +470,8 @@ class GraphOptimizer:
         self.entries = {}
         self.captures = 0
 
-    def _pad(self, hb, alpha, beta):
+    def _pad_batch(self, hb):
+        """The batch arrays padded to the bucket, and the capacities that key its graph."""
         B, K = hb.B, self.K
         Bb = bucket(B)
         last = B - 1
@@ -484,17 +485,26 @@ class GraphOptimizer:
         lay = np.concatenate([hb.split_layer] + [hb.split_layer[o:o + c]] * extra)
         idx = np.concatenate([hb.split_idx] + [hb.split_idx[o:o + c]] * extra)
         sgn = np.concatenate([hb.split_sign] + [hb.split_sign[o:o + c]] * extra)
-        a_last = np.asarray(alpha[int(hb.alpha_off[last]):int(hb.alpha_off[last]) + na_last], np.float32)
-        b_last = np.asarray(beta[o * K:(o + c) * K], np.float32)
-        a = np.concatenate([np.asarray(alpha, np.float32)] + [a_last] * extra)
-        b = np.concatenate([np.asarray(beta, np.float32)] + [b_last] * extra)
         # capacities fixed by the bucket alone (one graph per bucket, whatever the batch holds):
         # K U_max alphas and K MAX_SPLITS betas per subdomain, MAX_SPLITS split entries
         caps = (Bb, Bb * K * int(self.U.max(initial=0)), Bb * K * N.MAX_SPLITS, Bb * N.MAX_SPLITS)
         return caps, dict(prop_of=prop, split_off=off, split_cnt=cnt, alpha_off=aoff, split_layer=lay,
-                          split_idx=idx, split_sign=sgn), a, b
+                          split_idx=idx, split_sign=sgn)
 
-    def _capture(self, caps, arrays, a, b):
+    def _pad(self, hb, alpha, beta):
+        B, K = hb.B, self.K
+        last = B - 1
+        o, c = int(hb.split_off[last]), int(hb.split_cnt[last])
+        na_last = int(self.U[hb.prop_of[last]]) * K
+        extra = bucket(B) - B
+        caps, arrays = self._pad_batch(hb)
+        a_last = np.asarray(alpha[int(hb.alpha_off[last]):int(hb.alpha_off[last]) + na_last], np.float32)
+        b_last = np.asarray(beta[o * K:(o + c) * K], np.float32)
+        a = np.concatenate([np.asarray(alpha, np.float32)] + [a_last] * extra)
+        b = np.concatenate([np.asarray(beta, np.float32)] + [b_last] * extra)
+        return caps, arrays, a, b
+
+    def _capture(self, caps, load):
         Bb, na, nb, ns = caps
         dev = {"prop_of": torch.zeros(Bb, dtype=torch.int32, device="cuda"),
                "split_off": torch.zeros(Bb, dtype=torch.int32, device="cuda"),
@@ -507,7 +517,7 @@ class GraphOptimizer:
              "lb": torch.empty(Bb * self.K, device="cuda")}
         e["db"] = DeviceBatch(dev["prop_of"], dev["split_off"], dev["split_cnt"], dev["split_layer"], dev["split_idx"],
                               dev["split_sign"], dev["alpha_off"], na, nb)
-        self._load(e, arrays, a, b)
+        load(e)
         optimize(self.net, self.dom, e["db"], e["alpha"], e["beta"], self.cfg, out=e["lb"])   # sizes everything
         torch.cuda.synchronize()
         ws = workspace(self.net)[0]
@@ -530,16 +540,47 @@ class GraphOptimizer:
         e["alpha"][:len(a)].copy_(torch.from_numpy(a))
         e["beta"][:len(b)].copy_(torch.from_numpy(b))
 
-    def __call__(self, hb, alpha, beta):
-        """The optimised bounds (B K rows), alpha and beta of host batch hb (numpy outputs)."""
-        caps, arrays, a, b = self._pad(hb, alpha, beta)
+    def _replay(self, caps, load):
         e = self.entries.get(caps)
         if e is not None and e["ws"] != workspace(self.net)[0]:
             e = None
         if e is None:
-            e = self._capture(caps, arrays, a, b)
-        self._load(e, arrays, a, b)
+            e = self._capture(caps, load)
+        load(e)
         e["graph"].replay()
+        return e
+
+    def rows(self, hb, alpha, beta):
+        """As a call, for a host batch whose alpha (device tensor) and compact beta (device tensor)
+        stay on the device: they are copied into the captured buffers, and the per-row best values
+        back into them.  Returns lb [B K] on the device."""
+        B, K = hb.B, self.K
+        last = B - 1
+        o, c = int(hb.split_off[last]), int(hb.split_cnt[last])
+        a0, na_last = int(hb.alpha_off[last]), int(self.U[hb.prop_of[last]]) * K
+        extra = bucket(B) - B
+        caps, arrays = self._pad_batch(hb)
+        av, bv = alpha.reshape(-1), beta.reshape(-1)
+
+        def load(e):
+            e["alpha"][:hb.n_alpha].copy_(av[:hb.n_alpha])
+            if extra:   # the padding subdomains' copies of the last one's alpha and beta
+                e["alpha"][a0 + na_last:a0 + na_last * (extra + 1)].copy_(av[a0:a0 + na_last].repeat(extra))
+                e["beta"][hb.n_beta:hb.n_beta + extra * c * K].copy_(bv[o * K:(o + c) * K].repeat(extra))
+            e["beta"][:hb.n_beta].copy_(bv[:hb.n_beta])
+            for k, v in arrays.items():
+                t = torch.from_numpy(np.ascontiguousarray(v.astype(np.int32) if k == "split_idx" else v))
+                e["dev"][k][:len(v)].copy_(t)
+
+        e = self._replay(caps, load)
+        av.copy_(e["alpha"][:hb.n_alpha])
+        bv.copy_(e["beta"][:hb.n_beta])
+        return e["lb"][:B * K].clone()
+
+    def __call__(self, hb, alpha, beta):
+        """The optimised bounds (B K rows), alpha and beta of host batch hb (numpy outputs)."""
+        caps, arrays, a, b = self._pad(hb, alpha, beta)
+        e = self._replay(caps, lambda e: self._load(e, arrays, a, b))
         n = hb.B * self.K
         return (e["lb"][:n].cpu().numpy(), e["alpha"][:hb.n_alpha].cpu().numpy(),
                 e["beta"][:hb.n_beta].cpu().numpy())

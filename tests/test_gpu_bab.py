@@ -117,3 +117,30 @@ def test_array_pool_driver_on_the_gpu_finds_the_violation_sampling_misses(upper,
     assert res.status == "violated"
     if line_search:
         assert res.line_searched > 0
+
+
+@pytest.mark.parametrize("name", ["verified_by_branching_a", "violated_found_by_descent"])
+def test_array_pool_driver_with_graph_replay_takes_the_same_steps(name):
+    """GpuEngine(graphs=True) under the array pool: alpha and beta are copied device to device into
+    the bucket's captured buffers (the padding subdomains get copies of the last one's) and the
+    graph replayed; the same verdict, rounds, subdomain counts and per-round bounds as the eager
+    engine, and, for the net whose violation sampling misses, the violation found at x*."""
+    from paper_2103_06624_gb300 import bab_pool
+    pb, props, unst, exact = make_case(name)
+    U = [len(u) for u in unst]
+    case = (0, props["l"][0], props["u"][0], pb.x_lo[0], pb.x_hi[0])
+
+    def engine(graphs):
+        net = bc.load_net(pb.layers, pb.C)
+        dom = bc.domain_from_host(props["x_lo"], props["x_hi"], props["l"], props["u"])
+        return bab.GpuEngine(pb, net, dom, U, graphs=graphs)
+
+    kw = dict(batch_size=48, max_rounds=12, n_samples=0, pgd_steps=0, line_search=False)
+    eager = bab_pool.bab_pool(engine(False), [case], **kw)[0]
+    eng = engine(True)
+    replay = bab_pool.bab_pool(eng, [case], **kw)[0]
+    check_verdict(name, pb, exact, replay)
+    assert eng.graphs.captures >= 1
+    assert (replay.status, replay.rounds, replay.bounded, replay.max_depth) == (
+        eager.status, eager.rounds, eager.bounded, eager.max_depth)
+    assert replay.history == eager.history
