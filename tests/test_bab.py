@@ -337,3 +337,30 @@ def test_array_pool_driver_from_start_subdomains():
     with pytest.raises(ValueError):
         bab_pool.bab_pool(OracleEngine(pb, props, U), [case], starts=[[(order[1:2], np.array([1], np.int8))]],
                           n_samples=0, pgd_steps=0, device="cpu")
+
+
+def test_pool_batch_equals_the_packed_split_lists():
+    """The array pool's vectorised batch builder against workloads.pack_batch on the same
+    subdomains (split lists = prefixes of each property's branching order): the same properties,
+    offsets, counts, layers, indices and signs; alpha blocks K * max U apart."""
+    from paper_2103_06624_gb300 import bab_pool
+    rng = np.random.default_rng(5)
+    hw = [7, 5, 9]
+    K = 3
+    H = sum(hw)
+    orders = np.stack([rng.permutation(H)[:10] for _ in range(2)]).astype(np.int64)
+    U = [10, 8]
+    n = 40
+    owner = rng.integers(0, 2, n).astype(np.int32)
+    depth = np.array([rng.integers(0, U[o] + 1) for o in owner], np.int32)
+    signs = rng.choice(np.array([-1, 1], np.int8), size=(n, 10))
+    props = np.array([4, 1], np.int32)
+    got = bab_pool.pool_batch(hw, K, max(U), orders, props, depth, owner, signs)
+    subs = [(int(props[o]), orders[o, :d], signs[i, :d]) for i, (o, d) in enumerate(zip(owner, depth))]
+    Up = np.zeros(5, np.int64)
+    Up[props] = U
+    ref = wl.pack_batch(hw, K, Up, subs)
+    for f in ("prop_of", "split_off", "split_cnt", "split_layer", "split_idx", "split_sign"):
+        np.testing.assert_array_equal(getattr(got, f), getattr(ref, f), err_msg=f)
+    np.testing.assert_array_equal(got.alpha_off, np.arange(n) * K * max(U))
+    assert got.n_alpha == n * K * max(U) and got.n_beta == ref.n_beta
